@@ -1,0 +1,1078 @@
+/*
+ * Plain, slow FP64 CPU oracle for the spherical Biot-Savart velocity sum and the spherical
+ * tree code of Chen & Jablonowski, "Fast Summation on the Sphere with Applications to the
+ * Barotropic Vorticity Equation" (arXiv 2401.07361).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline legs of the
+ * benchmark call it; the product (the CUDA library and its binding) never does.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.  No FMA contraction, no fast
+ * math: every floating-point decision (face, child, MAC) is taken by the IEEE-754 double
+ * operations written out below, in the order written (sums left to right).
+ *
+ * What each part follows:
+ *   bs_term / or_direct   the midpoint-rule particle system (Sec. 2, the discrete dx_i/dt),
+ *                         with 1 - x.y written as |x - y|^2 / 2 (Eq. altkernel) and
+ *                         x_i x x_j = x_i x (x_j - x_i).
+ *   ico_build             the icosahedron whose faces are refined into the tree (Sec. 3,
+ *                         "Grids on a Sphere").  Orientation and vertex order are not given
+ *                         in the paper; the reading used is stated at the function.
+ *   or_tree_build         iterative 4-way refinement of the faces (Sec. 3); a triangle is a
+ *                         leaf when it holds at most N_T particles or sits at the depth limit.
+ *   mac                   (r_t + r_s)/R < theta (Sec. 3.4, "Dual Tree Traversal").
+ *   or_tree_lists         target-leaf traversal from the 20 roots (Sec. 3.4), PC + PP only.
+ *   afp_points            approximate Fekete points (Sec. 3.2); construction not given in the
+ *                         paper, read as greedy column-pivoted QR on a barycentric lattice.
+ *   sbb                   the SBB basis B_ijk = b1^i b2^j b3^k, i+j+k = d (Sec. 3.2).
+ *   cluster_weights       omega_k = sum_j B_k(y_j) q_j A_j and the proxy-point form of the PC
+ *                         interaction (Sec. 3.3.2): W = V_s^{-T} omega.
+ *   pc_literal            the PC interaction exactly as printed: solve V alpha = G(x, y~),
+ *                         then sum_k alpha_k omega_k (Sec. 3.3.2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_MEM (-2)
+#define OR_PI 3.14159265358979323846
+
+typedef struct { double x, y, z; } v3;
+
+static v3 mk(double x, double y, double z) { v3 r; r.x = x; r.y = y; r.z = z; return r; }
+static v3 vadd(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 vsub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static double vdot(v3 a, v3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+static v3 vcross(v3 a, v3 b)
+{
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+/* s / |s| with |s| = sqrt((sx^2 + sy^2) + sz^2) and three divisions. */
+static v3 vunit(v3 s)
+{
+    double n = sqrt(vdot(s, s));
+    return mk(s.x / n, s.y / n, s.z / n);
+}
+static v3 ld3(const double* p, int64_t i) { return mk(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+
+/* ------------------------------------------------------------------------------------- */
+/* The kernel.  Sec. 2: dx_i/dt = -(1/4pi) sum_{j != i} (x_i x x_j) zeta_j A_j / (1 - x_i.x_j).
+ * Eq. altkernel replaces 1 - x.y by |x - y|^2 / 2; x_i x x_j equals x_i x (x_j - x_i).
+ * bs_term adds w (x x d) / (|d|^2 / 2), d = y - x, to *acc.  A distinct particle at the
+ * same position (d = 0) adds nothing: the cross product vanishes with it.                 */
+static void bs_term(v3 x, v3 y, double w, v3* acc)
+{
+    v3 d = vsub(y, x);
+    double h = 0.5 * vdot(d, d);
+    if (h == 0.0) return;
+    double t = w / h;
+    v3 c = vcross(x, d);
+    acc->x += c.x * t;
+    acc->y += c.y * t;
+    acc->z += c.z * t;
+}
+
+static int set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+    return nthreads;
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* Direct summation (Sec. 2 particle system; Sec. 4.1 "direct summation").
+ * pos[n,3], zeta[n], area[n]; targets: NULL for all n targets, else nt original indices.
+ * vel[nt,3] receives u at each target.  OpenMP splits targets only, so every target's sum
+ * runs in the same order whatever the thread count.                                     */
+int or_direct(int64_t n, const double* pos, const double* zeta, const double* area,
+              int64_t nt, const int64_t* targets, double* vel, int nthreads)
+{
+    if (n < 0 || nt < 0 || (n > 0 && (!pos || !zeta || !area)) || (nt > 0 && !vel))
+        return OR_ERR_ARG;
+    if (!targets) nt = n;
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!w) return OR_ERR_MEM;
+    for (int64_t j = 0; j < n; j++) w[j] = zeta[j] * area[j];
+    const double f = -1.0 / (4.0 * OR_PI);
+    int nth = set_threads(nthreads);
+    (void)nth;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nth)
+    for (int64_t k = 0; k < nt; k++) {
+        int64_t i = targets ? targets[k] : k;
+        v3 x = ld3(pos, i);
+        v3 acc = mk(0.0, 0.0, 0.0);
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            bs_term(x, ld3(pos, j), w[j], &acc);
+        }
+        vel[3 * k] = f * acc.x;
+        vel[3 * k + 1] = f * acc.y;
+        vel[3 * k + 2] = f * acc.z;
+    }
+    free(w);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Icosahedron (Sec. 3: "We start with an icosahedron and refine its faces").  The paper
+ * gives no orientation or numbering, so this reading fixes one:
+ *   vertices: the cyclic families (0, +-1, +-g), (+-1, +-g, 0), (+-g, 0, +-1), g the golden
+ *             ratio, families in that order, sign pairs in the order (+,+), (+,-), (-,+),
+ *             (-,-); each scaled to unit length by vunit;
+ *   faces:    every i < j < k whose unscaled pairwise squared distances are all 4, in
+ *             lexicographic order of (i, j, k), stored as (i, j, k) when
+ *             det(v_i, v_j, v_k) > 0 and as (i, k, j) otherwise (counter-clockwise seen
+ *             from outside).                                                               */
+static void ico_build(v3 V[12], int F[20][3])
+{
+    const double g = (1.0 + sqrt(5.0)) / 2.0;
+    const double sg[4][2] = {{1.0, 1.0}, {1.0, -1.0}, {-1.0, 1.0}, {-1.0, -1.0}};
+    v3 raw[12];
+    int n = 0;
+    for (int fam = 0; fam < 3; fam++)
+        for (int s = 0; s < 4; s++) {
+            double a = sg[s][0], b = sg[s][1];
+            if (fam == 0) raw[n++] = mk(0.0, a * 1.0, b * g);
+            else if (fam == 1) raw[n++] = mk(a * 1.0, b * g, 0.0);
+            else raw[n++] = mk(a * g, 0.0, b * 1.0);
+        }
+    for (int i = 0; i < 12; i++) V[i] = vunit(raw[i]);
+    int nf = 0;
+    for (int i = 0; i < 12; i++)
+        for (int j = i + 1; j < 12; j++)
+            for (int k = j + 1; k < 12; k++) {
+                v3 a = vsub(raw[i], raw[j]), b = vsub(raw[i], raw[k]), c = vsub(raw[j], raw[k]);
+                if (fabs(vdot(a, a) - 4.0) > 1e-9 || fabs(vdot(b, b) - 4.0) > 1e-9 ||
+                    fabs(vdot(c, c) - 4.0) > 1e-9)
+                    continue;
+                double det = vdot(V[i], vcross(V[j], V[k]));
+                F[nf][0] = i;
+                F[nf][1] = det > 0.0 ? j : k;
+                F[nf][2] = det > 0.0 ? k : j;
+                nf++;
+            }
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Tree.  Node numbering: level by level (roots first), and within a level in key order;
+ * only non-empty triangles are nodes.  key = face index, then two bits per level (the
+ * child digit).  Children of (v1, v2, v3), with m_ab = vunit(v_a + v_b):
+ *   0 = (v1, m12, m31), 1 = (m12, v2, m23), 2 = (m31, m23, v3), 3 = (m12, m23, m31).       */
+typedef struct {
+    int32_t level, parent, first_child, nchild, leaf;
+    uint64_t key;
+    int64_t start, count;
+    v3 v[3];
+    v3 c;     /* circumcentre direction: vunit((v2 - v1) x (v3 - v1)) */
+    double r; /* chord radius |c - v1|                                 */
+} onode;
+
+typedef struct or_tree {
+    int64_t n;
+    int leaf_size, max_level, maxdepth;
+    int64_t nnodes, cap;
+    onode* nodes;
+    int64_t nleaves;
+    int32_t* leaves;  /* leaf node ids in depth-first order            */
+    int64_t* perm;    /* sorted position -> original particle index     */
+    double* pos;      /* copy of the positions, original order          */
+    /* interaction lists for one theta, per leaf in depth-first order */
+    double theta;
+    int has_lists;
+    int64_t *far_off, *near_off;
+    int32_t *far_idx, *near_idx;
+} or_tree;
+
+static int push_node(or_tree* t, const onode* nd)
+{
+    if (t->nnodes == t->cap) {
+        int64_t nc = t->cap ? 2 * t->cap : 1024;
+        onode* p = (onode*)realloc(t->nodes, sizeof(onode) * (size_t)nc);
+        if (!p) return OR_ERR_MEM;
+        t->nodes = p;
+        t->cap = nc;
+    }
+    t->nodes[t->nnodes++] = *nd;
+    return OR_OK;
+}
+
+static void node_geometry(onode* nd)
+{
+    nd->c = vunit(vcross(vsub(nd->v[1], nd->v[0]), vsub(nd->v[2], nd->v[0])));
+    v3 e = vsub(nd->c, nd->v[0]);
+    nd->r = sqrt(vdot(e, e));
+}
+
+/* Face of a particle: the first face f maximising x . c_f over the 20 face centres
+ * c_f = vunit((v_a + v_b) + v_c).  For the regular icosahedron the centres' spherical
+ * Voronoi cells are exactly the faces, so this is face containment with no gaps.          */
+static int face_of(v3 x, const v3 C[20])
+{
+    int best = 0;
+    double bd = vdot(x, C[0]);
+    for (int f = 1; f < 20; f++) {
+        double d = vdot(x, C[f]);
+        if (d > bd) {
+            bd = d;
+            best = f;
+        }
+    }
+    return best;
+}
+
+/* Child digit of x inside a triangle with edge midpoints m12, m23, m31:
+ * (m12 x m31).x >= 0 -> 0, else (m23 x m12).x >= 0 -> 1, else (m31 x m23).x >= 0 -> 2,
+ * else 3 (the centre triangle).                                                          */
+static int child_digit(v3 x, v3 n0, v3 n1, v3 n2)
+{
+    if (vdot(n0, x) >= 0.0) return 0;
+    if (vdot(n1, x) >= 0.0) return 1;
+    if (vdot(n2, x) >= 0.0) return 2;
+    return 3;
+}
+
+void or_tree_free(or_tree* t)
+{
+    if (!t) return;
+    free(t->nodes);
+    free(t->leaves);
+    free(t->perm);
+    free(t->pos);
+    free(t->far_off);
+    free(t->near_off);
+    free(t->far_idx);
+    free(t->near_idx);
+    free(t);
+}
+
+static void dfs_leaves(or_tree* t, int32_t id, int64_t* k)
+{
+    onode* nd = &t->nodes[id];
+    if (nd->leaf) {
+        t->leaves[(*k)++] = id;
+        return;
+    }
+    for (int c = 0; c < nd->nchild; c++) dfs_leaves(t, nd->first_child + c, k);
+}
+
+/* Builds the triangle tree of Sec. 3 over pos[n,3]: refine every triangle holding more
+ * than leaf_size particles, up to level max_level.  Within a triangle particles keep
+ * their original relative order, so the sorted order is the depth-first order of leaves
+ * with ties broken by original index.                                                    */
+or_tree* or_tree_build(int64_t n, const double* pos, int leaf_size, int max_level)
+{
+    if (n < 0 || (n > 0 && !pos) || leaf_size < 1 || max_level < 0 || max_level > 29) return NULL;
+    or_tree* t = (or_tree*)calloc(1, sizeof(or_tree));
+    if (!t) return NULL;
+    t->n = n;
+    t->leaf_size = leaf_size;
+    t->max_level = max_level;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    t->pos = (double*)malloc(sizeof(double) * 3 * nn);
+    t->perm = (int64_t*)malloc(sizeof(int64_t) * nn);
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * nn);  /* particles grouped by node  */
+    int64_t* nxt = (int64_t*)malloc(sizeof(int64_t) * nn);
+    int64_t* seg = NULL;  /* per node: offset of its particles in cur (this level) */
+    int* dig = (int*)malloc(sizeof(int) * nn);
+    if (!t->pos || !t->perm || !cur || !nxt || !dig) goto fail;
+    if (n > 0) memcpy(t->pos, pos, sizeof(double) * 3 * (size_t)n);
+
+    v3 V[12];
+    int F[20][3];
+    ico_build(V, F);
+    v3 C[20];
+    for (int f = 0; f < 20; f++) C[f] = vunit(vadd(vadd(V[F[f][0]], V[F[f][1]]), V[F[f][2]]));
+
+    /* level 0: faces */
+    int64_t fcount[20] = {0};
+    for (int64_t i = 0; i < n; i++) {
+        dig[i] = face_of(ld3(pos, i), C);
+        fcount[dig[i]]++;
+    }
+    int64_t foff[20], acc = 0;
+    for (int f = 0; f < 20; f++) {
+        foff[f] = acc;
+        acc += fcount[f];
+    }
+    {
+        int64_t fill[20];
+        memcpy(fill, foff, sizeof(fill));
+        for (int64_t i = 0; i < n; i++) cur[fill[dig[i]]++] = i;
+    }
+    int64_t level_first = 0;
+    for (int f = 0; f < 20; f++) {
+        if (fcount[f] == 0) continue;
+        onode nd;
+        memset(&nd, 0, sizeof(nd));
+        nd.level = 0;
+        nd.parent = -1;
+        nd.first_child = -1;
+        nd.key = (uint64_t)f;
+        nd.start = foff[f];
+        nd.count = fcount[f];
+        for (int a = 0; a < 3; a++) nd.v[a] = V[F[f][a]];
+        node_geometry(&nd);
+        if (push_node(t, &nd)) goto fail;
+    }
+    /* seg offsets at level 0 equal the starts (faces are contiguous in cur) */
+    int64_t level_end = t->nnodes;
+    seg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(level_end > 0 ? level_end : 1));
+    if (!seg) goto fail;
+    for (int64_t id = 0; id < level_end; id++) seg[id] = t->nodes[id].start;
+
+    for (int level = 0;; level++) {
+        int64_t nxt_fill = 0;
+        int64_t new_first = t->nnodes;
+        for (int64_t id = level_first; id < level_end; id++) {
+            onode nd = t->nodes[id];
+            const int64_t* mine = cur + seg[id - level_first];
+            if (nd.count <= leaf_size || nd.level >= max_level) {
+                t->nodes[id].leaf = 1;
+                for (int64_t r = 0; r < nd.count; r++) t->perm[nd.start + r] = mine[r];
+                continue;
+            }
+            v3 v1 = nd.v[0], v2 = nd.v[1], v3_ = nd.v[2];
+            v3 m12 = vunit(vadd(v1, v2)), m23 = vunit(vadd(v2, v3_)), m31 = vunit(vadd(v3_, v1));
+            v3 n0 = vcross(m12, m31), n1 = vcross(m23, m12), n2 = vcross(m31, m23);
+            int64_t cc[4] = {0, 0, 0, 0};
+            for (int64_t r = 0; r < nd.count; r++) {
+                dig[r] = child_digit(ld3(pos, mine[r]), n0, n1, n2);
+                cc[dig[r]]++;
+            }
+            int64_t coff[4], a2 = 0;
+            for (int c = 0; c < 4; c++) {
+                coff[c] = a2;
+                a2 += cc[c];
+            }
+            int64_t fill[4];
+            for (int c = 0; c < 4; c++) fill[c] = nxt_fill + coff[c];
+            for (int64_t r = 0; r < nd.count; r++) nxt[fill[dig[r]]++] = mine[r];
+            v3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3_}, {m12, m23, m31}};
+            t->nodes[id].first_child = (int32_t)t->nnodes;
+            int nchild = 0;
+            for (int c = 0; c < 4; c++) {
+                if (cc[c] == 0) continue;
+                onode ch;
+                memset(&ch, 0, sizeof(ch));
+                ch.level = nd.level + 1;
+                ch.parent = (int32_t)id;
+                ch.first_child = -1;
+                ch.key = nd.key * 4u + (uint64_t)c;
+                ch.start = nd.start + coff[c];
+                ch.count = cc[c];
+                for (int a = 0; a < 3; a++) ch.v[a] = cv[c][a];
+                node_geometry(&ch);
+                if (push_node(t, &ch)) goto fail;
+                nchild++;
+            }
+            t->nodes[id].nchild = nchild;
+            nxt_fill += nd.count;
+        }
+        int64_t new_end = t->nnodes;
+        if (new_end == new_first) break;
+        /* children are contiguous in nxt in node order: their seg offsets are cumulative */
+        free(seg);
+        seg = (int64_t*)malloc(sizeof(int64_t) * (size_t)(new_end - new_first));
+        if (!seg) goto fail;
+        int64_t off = 0;
+        for (int64_t id = new_first; id < new_end; id++) {
+            seg[id - new_first] = off;
+            off += t->nodes[id].count;
+        }
+        int64_t* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        level_first = new_first;
+        level_end = new_end;
+        t->maxdepth = level + 1;
+    }
+
+    t->nleaves = 0;
+    for (int64_t id = 0; id < t->nnodes; id++) t->nleaves += t->nodes[id].leaf;
+    t->leaves = (int32_t*)malloc(sizeof(int32_t) * (size_t)(t->nleaves > 0 ? t->nleaves : 1));
+    if (!t->leaves) goto fail;
+    {
+        int64_t k = 0;
+        for (int64_t id = 0; id < t->nnodes && t->nodes[id].level == 0; id++) dfs_leaves(t, (int32_t)id, &k);
+    }
+    free(cur);
+    free(nxt);
+    free(seg);
+    free(dig);
+    return t;
+fail:
+    free(cur);
+    free(nxt);
+    free(seg);
+    free(dig);
+    or_tree_free(t);
+    return NULL;
+}
+
+/* info: [0] n, [1] nodes, [2] leaves, [3] deepest level, [4] far list length,
+ *       [5] near list length (the last two are 0 before or_tree_lists).                  */
+int or_tree_info(const or_tree* t, int64_t* info)
+{
+    if (!t || !info) return OR_ERR_ARG;
+    info[0] = t->n;
+    info[1] = t->nnodes;
+    info[2] = t->nleaves;
+    info[3] = t->maxdepth;
+    info[4] = t->has_lists ? t->far_off[t->nleaves] : 0;
+    info[5] = t->has_lists ? t->near_off[t->nleaves] : 0;
+    return OR_OK;
+}
+
+/* Copies the tree out.  Any pointer may be NULL.  geom[nodes,13] = v1, v2, v3, c, r.     */
+int or_tree_export(const or_tree* t, int64_t* perm, int32_t* level, uint64_t* key, int32_t* parent,
+                   int32_t* first_child, int32_t* nchild, int64_t* start, int64_t* count,
+                   int32_t* leaf, int32_t* leaves, double* geom)
+{
+    if (!t) return OR_ERR_ARG;
+    if (perm) memcpy(perm, t->perm, sizeof(int64_t) * (size_t)t->n);
+    if (leaves) memcpy(leaves, t->leaves, sizeof(int32_t) * (size_t)t->nleaves);
+    for (int64_t id = 0; id < t->nnodes; id++) {
+        const onode* nd = &t->nodes[id];
+        if (level) level[id] = nd->level;
+        if (key) key[id] = nd->key;
+        if (parent) parent[id] = nd->parent;
+        if (first_child) first_child[id] = nd->first_child;
+        if (nchild) nchild[id] = nd->nchild;
+        if (start) start[id] = nd->start;
+        if (count) count[id] = nd->count;
+        if (leaf) leaf[id] = nd->leaf;
+        if (geom) {
+            double* g = geom + 13 * id;
+            for (int a = 0; a < 3; a++) {
+                g[3 * a] = nd->v[a].x;
+                g[3 * a + 1] = nd->v[a].y;
+                g[3 * a + 2] = nd->v[a].z;
+            }
+            g[9] = nd->c.x;
+            g[10] = nd->c.y;
+            g[11] = nd->c.z;
+            g[12] = nd->r;
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* MAC of Sec. 3.4: well separated iff (r_t + r_s) / R < theta, written without the
+ * division as (r_t + r_s) < theta * R, R = |c_t - c_s| (chord).  R = 0 never separates.  */
+static int mac(const onode* a, const onode* b, double theta)
+{
+    v3 e = vsub(a->c, b->c);
+    double R = sqrt(vdot(e, e));
+    return (a->r + b->r) < theta * R;
+}
+
+typedef struct {
+    int32_t* p;
+    int64_t n, cap;
+} ivec;
+
+static int ivec_push(ivec* v, int32_t x)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? 2 * v->cap : 4096;
+        int32_t* q = (int32_t*)realloc(v->p, sizeof(int32_t) * (size_t)nc);
+        if (!q) return OR_ERR_MEM;
+        v->p = q;
+        v->cap = nc;
+    }
+    v->p[v->n++] = x;
+    return OR_OK;
+}
+
+/* Traversal of Sec. 3.4 for one target leaf t over source node s (preorder):
+ *   MAC passes:  s holds more than N_T particles -> far (PC); else -> near (PP);
+ *   MAC fails:   s is a leaf -> near (PP); else descend into s's children in digit order. */
+static int traverse(const or_tree* tr, const onode* t, int32_t s, double theta, ivec* far, ivec* near)
+{
+    const onode* sn = &tr->nodes[s];
+    if (mac(t, sn, theta)) {
+        if (sn->count > tr->leaf_size) return ivec_push(far, s);
+        return ivec_push(near, s);
+    }
+    if (sn->leaf) return ivec_push(near, s);
+    for (int c = 0; c < sn->nchild; c++)
+        if (traverse(tr, t, sn->first_child + c, theta, far, near)) return OR_ERR_MEM;
+    return OR_OK;
+}
+
+int or_tree_lists(or_tree* tr, double theta)
+{
+    if (!tr || !(theta > 0.0) || !(theta < 1.0)) return OR_ERR_ARG;
+    free(tr->far_off);
+    free(tr->near_off);
+    free(tr->far_idx);
+    free(tr->near_idx);
+    tr->far_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tr->nleaves + 1));
+    tr->near_off = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tr->nleaves + 1));
+    tr->far_idx = tr->near_idx = NULL;
+    tr->has_lists = 0;
+    if (!tr->far_off || !tr->near_off) return OR_ERR_MEM;
+    ivec far = {0}, near = {0};
+    tr->far_off[0] = tr->near_off[0] = 0;
+    for (int64_t L = 0; L < tr->nleaves; L++) {
+        const onode* t = &tr->nodes[tr->leaves[L]];
+        for (int64_t id = 0; id < tr->nnodes && tr->nodes[id].level == 0; id++)
+            if (traverse(tr, t, (int32_t)id, theta, &far, &near)) {
+                free(far.p);
+                free(near.p);
+                return OR_ERR_MEM;
+            }
+        tr->far_off[L + 1] = far.n;
+        tr->near_off[L + 1] = near.n;
+    }
+    tr->far_idx = far.p ? far.p : (int32_t*)malloc(sizeof(int32_t));
+    tr->near_idx = near.p ? near.p : (int32_t*)malloc(sizeof(int32_t));
+    tr->theta = theta;
+    tr->has_lists = 1;
+    return OR_OK;
+}
+
+int or_lists_export(const or_tree* tr, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
+                    int32_t* near_idx)
+{
+    if (!tr || !tr->has_lists) return OR_ERR_ARG;
+    int64_t L = tr->nleaves;
+    if (far_off) memcpy(far_off, tr->far_off, sizeof(int64_t) * (size_t)(L + 1));
+    if (near_off) memcpy(near_off, tr->near_off, sizeof(int64_t) * (size_t)(L + 1));
+    if (far_idx) memcpy(far_idx, tr->far_idx, sizeof(int32_t) * (size_t)tr->far_off[L]);
+    if (near_idx) memcpy(near_idx, tr->near_idx, sizeof(int32_t) * (size_t)tr->near_off[L]);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* SBB basis of degree d (Sec. 3.2): B_k(b) = b1^a b2^b b3^c, a + b + c = d, enumerated as
+ * a = d..0, then b = d - a..0 (c = d - a - b).  M = (d + 1)(d + 2) / 2 functions.        */
+static int nbasis(int d) { return (d + 1) * (d + 2) / 2; }
+
+static void sbb(int d, double b1, double b2, double b3, double* B)
+{
+    double p1[33], p2[33], p3[33];
+    p1[0] = p2[0] = p3[0] = 1.0;
+    for (int e = 1; e <= d; e++) {
+        p1[e] = p1[e - 1] * b1;
+        p2[e] = p2[e - 1] * b2;
+        p3[e] = p3[e - 1] * b3;
+    }
+    int k = 0;
+    for (int a = d; a >= 0; a--)
+        for (int b = d - a; b >= 0; b--) {
+            int c = d - a - b;
+            B[k++] = (p1[a] * p2[b]) * p3[c];
+        }
+}
+
+/* Spherical barycentric coordinates of y in the triangle (v1, v2, v3) (Sec. 3.2:
+ * y = b1 v1 + b2 v2 + b3 v3), by Cramer's rule with D = v1 . (v2 x v3).                  */
+static void sph_bary(v3 y, v3 v1, v3 v2, v3 v3_, double* b)
+{
+    double D = vdot(v1, vcross(v2, v3_));
+    b[0] = vdot(y, vcross(v2, v3_)) / D;
+    b[1] = vdot(y, vcross(v3_, v1)) / D;
+    b[2] = vdot(y, vcross(v1, v2)) / D;
+}
+
+/* Approximate Fekete points of degree d on the planar reference simplex (Sec. 3.2 names
+ * them and cites their construction; the construction itself is not printed).  Reading:
+ * greedy column-pivoted Householder QR of A[k][c] = B_k(candidate c) over the barycentric
+ * lattice of resolution 3d (candidates (p, q, 3d - p - q) / 3d, p = 3d..0, q = 3d - p..0).
+ * At each step the candidate with the largest remaining column norm is taken; norms within
+ * a relative 1e-9 of the largest count as equal and the lowest candidate index wins.
+ * Writes beta[M,3] (in selection order) and the chosen candidate indices.                 */
+int or_proxy_reference(int d, double* beta, int32_t* cand)
+{
+    if (d < 1 || d > 16 || !beta) return OR_ERR_ARG;
+    const int M = nbasis(d), R = 3 * d, K = (R + 1) * (R + 2) / 2;
+    double* cb = (double*)malloc(sizeof(double) * 3 * (size_t)K);
+    double* A = (double*)malloc(sizeof(double) * (size_t)M * (size_t)K);
+    double* nrm = (double*)malloc(sizeof(double) * (size_t)K);
+    double* v = (double*)malloc(sizeof(double) * (size_t)M);
+    char* chosen = (char*)calloc((size_t)K, 1);
+    double* B = (double*)malloc(sizeof(double) * (size_t)M);
+    if (!cb || !A || !nrm || !v || !chosen || !B) {
+        free(cb); free(A); free(nrm); free(v); free(chosen); free(B);
+        return OR_ERR_MEM;
+    }
+    int c = 0;
+    for (int p = R; p >= 0; p--)
+        for (int q = R - p; q >= 0; q--) {
+            cb[3 * c] = (double)p / (double)R;
+            cb[3 * c + 1] = (double)q / (double)R;
+            cb[3 * c + 2] = (double)(R - p - q) / (double)R;
+            sbb(d, cb[3 * c], cb[3 * c + 1], cb[3 * c + 2], B);
+            for (int k = 0; k < M; k++) A[(size_t)k * K + c] = B[k];
+            c++;
+        }
+    for (int s = 0; s < M; s++) {
+        double mx = -1.0;
+        for (c = 0; c < K; c++) {
+            if (chosen[c]) continue;
+            double acc = 0.0;
+            for (int k = s; k < M; k++) acc += A[(size_t)k * K + c] * A[(size_t)k * K + c];
+            nrm[c] = acc;
+            if (acc > mx) mx = acc;
+        }
+        int pick = -1;
+        for (c = 0; c < K; c++)
+            if (!chosen[c] && nrm[c] >= mx * (1.0 - 1e-9)) {
+                pick = c;
+                break;
+            }
+        chosen[pick] = 1;
+        if (cand) cand[s] = pick;
+        beta[3 * s] = cb[3 * pick];
+        beta[3 * s + 1] = cb[3 * pick + 1];
+        beta[3 * s + 2] = cb[3 * pick + 2];
+        /* Householder reflection zeroing rows s+1.. of the picked column */
+        double sigma = sqrt(nrm[pick]);
+        double a0 = A[(size_t)s * K + pick];
+        double alpha = a0 > 0.0 ? -sigma : sigma;
+        double vn = 0.0;
+        for (int k = s; k < M; k++) v[k] = A[(size_t)k * K + pick];
+        v[s] = v[s] - alpha;
+        for (int k = s; k < M; k++) vn += v[k] * v[k];
+        if (vn > 0.0)
+            for (c = 0; c < K; c++) {
+                if (chosen[c] && c != pick) continue;
+                double tt = 0.0;
+                for (int k = s; k < M; k++) tt += v[k] * A[(size_t)k * K + c];
+                double f = 2.0 * tt / vn;
+                for (int k = s; k < M; k++) A[(size_t)k * K + c] -= f * v[k];
+            }
+    }
+    free(cb); free(A); free(nrm); free(v); free(chosen); free(B);
+    return OR_OK;
+}
+
+/* Gauss-Jordan inverse with partial pivoting, a[n,n] row-major -> inv[n,n].             */
+static int invert(int n, const double* a, double* inv)
+{
+    double* m = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(2 * n));
+    if (!m) return OR_ERR_MEM;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < 2 * n; j++)
+            m[(size_t)i * 2 * n + j] = j < n ? a[(size_t)i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int i = col + 1; i < n; i++)
+            if (fabs(m[(size_t)i * 2 * n + col]) > fabs(m[(size_t)piv * 2 * n + col])) piv = i;
+        if (m[(size_t)piv * 2 * n + col] == 0.0) {
+            free(m);
+            return OR_ERR_ARG;
+        }
+        if (piv != col)
+            for (int j = 0; j < 2 * n; j++) {
+                double tmp = m[(size_t)col * 2 * n + j];
+                m[(size_t)col * 2 * n + j] = m[(size_t)piv * 2 * n + j];
+                m[(size_t)piv * 2 * n + j] = tmp;
+            }
+        double p = m[(size_t)col * 2 * n + col];
+        for (int j = 0; j < 2 * n; j++) m[(size_t)col * 2 * n + j] /= p;
+        for (int i = 0; i < n; i++) {
+            if (i == col) continue;
+            double f = m[(size_t)i * 2 * n + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * n; j++) m[(size_t)i * 2 * n + j] -= f * m[(size_t)col * 2 * n + j];
+        }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) inv[(size_t)i * n + j] = m[(size_t)i * 2 * n + n + j];
+    free(m);
+    return OR_OK;
+}
+
+/* Solves a[n,n] x = b (Gaussian elimination, partial pivoting); b is overwritten by x.   */
+static int solve(int n, double* a, double* b, int nrhs)
+{
+    for (int col = 0; col < n; col++) {
+        int piv = col;
+        for (int i = col + 1; i < n; i++)
+            if (fabs(a[(size_t)i * n + col]) > fabs(a[(size_t)piv * n + col])) piv = i;
+        if (a[(size_t)piv * n + col] == 0.0) return OR_ERR_ARG;
+        if (piv != col) {
+            for (int j = 0; j < n; j++) {
+                double tmp = a[(size_t)col * n + j];
+                a[(size_t)col * n + j] = a[(size_t)piv * n + j];
+                a[(size_t)piv * n + j] = tmp;
+            }
+            for (int r = 0; r < nrhs; r++) {
+                double tmp = b[(size_t)col * nrhs + r];
+                b[(size_t)col * nrhs + r] = b[(size_t)piv * nrhs + r];
+                b[(size_t)piv * nrhs + r] = tmp;
+            }
+        }
+        for (int i = col + 1; i < n; i++) {
+            double f = a[(size_t)i * n + col] / a[(size_t)col * n + col];
+            if (f == 0.0) continue;
+            for (int j = col; j < n; j++) a[(size_t)i * n + j] -= f * a[(size_t)col * n + j];
+            for (int r = 0; r < nrhs; r++) b[(size_t)i * nrhs + r] -= f * b[(size_t)col * nrhs + r];
+        }
+    }
+    for (int i = n - 1; i >= 0; i--)
+        for (int r = 0; r < nrhs; r++) {
+            double acc = b[(size_t)i * nrhs + r];
+            for (int j = i + 1; j < n; j++) acc -= a[(size_t)i * n + j] * b[(size_t)j * nrhs + r];
+            b[(size_t)i * nrhs + r] = acc / a[(size_t)i * n + i];
+        }
+    return OR_OK;
+}
+
+/* Reference interpolation data for degree d: beta[M,3] and V_ref^{-1}[M,M], where
+ * V_ref[m][k] = B_k(beta_m).                                                              */
+typedef struct {
+    int d, M;
+    double* beta;
+    double* vinv;
+} refdata;
+
+static int ref_make(int d, refdata* r)
+{
+    r->d = d;
+    r->M = nbasis(d);
+    r->beta = (double*)malloc(sizeof(double) * 3 * (size_t)r->M);
+    r->vinv = (double*)malloc(sizeof(double) * (size_t)r->M * (size_t)r->M);
+    double* V = (double*)malloc(sizeof(double) * (size_t)r->M * (size_t)r->M);
+    if (!r->beta || !r->vinv || !V) {
+        free(V);
+        return OR_ERR_MEM;
+    }
+    int rc = or_proxy_reference(d, r->beta, NULL);
+    for (int m = 0; m < r->M && rc == OR_OK; m++)
+        sbb(d, r->beta[3 * m], r->beta[3 * m + 1], r->beta[3 * m + 2], V + (size_t)m * r->M);
+    if (rc == OR_OK) rc = invert(r->M, V, r->vinv);
+    free(V);
+    return rc;
+}
+
+static void ref_free(refdata* r)
+{
+    free(r->beta);
+    free(r->vinv);
+}
+
+/* V_ref^{-1} for degree d (exported for the tests).                                     */
+int or_vref_inverse(int d, double* vinv)
+{
+    if (d < 1 || d > 16 || !vinv) return OR_ERR_ARG;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc == OR_OK) memcpy(vinv, r.vinv, sizeof(double) * (size_t)r.M * (size_t)r.M);
+    ref_free(&r);
+    return rc;
+}
+
+/* Proxy points of a source triangle: y~_m = vunit(b_m1 v1 + b_m2 v2 + b_m3 v3) (the sums
+ * left to right), with rho_m = |b_m1 v1 + b_m2 v2 + b_m3 v3|.                            */
+static void proxies(const refdata* r, const v3* v, v3* yt, double* rho)
+{
+    for (int m = 0; m < r->M; m++) {
+        const double* b = r->beta + 3 * m;
+        v3 s = mk((b[0] * v[0].x + b[1] * v[1].x) + b[2] * v[2].x,
+                  (b[0] * v[0].y + b[1] * v[1].y) + b[2] * v[2].y,
+                  (b[0] * v[0].z + b[1] * v[1].z) + b[2] * v[2].z);
+        double n = sqrt(vdot(s, s));
+        if (rho) rho[m] = n;
+        yt[m] = mk(s.x / n, s.y / n, s.z / n);
+    }
+}
+
+/* Proxy weights of one source triangle (Sec. 3.3.2).  omega_k = sum_j B_k(b(y_j)) w_j with
+ * b(.) the spherical barycentric coordinates in the triangle, then W = V_s^{-T} omega with
+ * V_s[m][k] = B_k(b(y~_m)).  Because B_k is homogeneous of degree d and b(y~_m) = beta_m /
+ * rho_m, V_s = diag(rho^-d) V_ref and W_m = rho_m^d sum_k V_ref^{-1}[k][m] omega_k, so that
+ * sum_k alpha_k(x) omega_k = sum_m G(x, y~_m) W_m for every x.                           */
+static void cluster_weights(const refdata* r, const v3* v, int64_t ns, const v3* ys, const double* ws,
+                            v3* yt, double* W, double* omega)
+{
+    const int M = r->M, d = r->d;
+    double B[153], rho[153];
+    for (int k = 0; k < M; k++) omega[k] = 0.0;
+    for (int64_t j = 0; j < ns; j++) {
+        double b[3];
+        sph_bary(ys[j], v[0], v[1], v[2], b);
+        sbb(d, b[0], b[1], b[2], B);
+        for (int k = 0; k < M; k++) omega[k] += B[k] * ws[j];
+    }
+    proxies(r, v, yt, rho);
+    for (int m = 0; m < M; m++) {
+        double acc = 0.0;
+        for (int k = 0; k < M; k++) acc += r->vinv[(size_t)k * M + m] * omega[k];
+        double rd = 1.0;
+        for (int e = 0; e < d; e++) rd *= rho[m];
+        W[m] = rd * acc;
+    }
+}
+
+/* One source triangle (verts[9] = v1, v2, v3), its sources ys[ns,3] with strengths
+ * ws[ns]: writes the proxy points yt[M,3], proxy weights W[M] and moments omega[M].      */
+int or_cluster(const double* verts, int d, int64_t ns, const double* ys, const double* ws, double* yt,
+               double* W, double* omega)
+{
+    if (!verts || d < 1 || d > 16 || ns < 0 || !yt || !W || !omega) return OR_ERR_ARG;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    v3 v[3] = {ld3(verts, 0), ld3(verts, 1), ld3(verts, 2)};
+    v3* y = (v3*)malloc(sizeof(v3) * (size_t)(ns > 0 ? ns : 1));
+    v3 ytv[153];
+    for (int64_t j = 0; j < ns; j++) y[j] = ld3(ys, j);
+    cluster_weights(&r, v, ns, y, ws, ytv, W, omega);
+    for (int m = 0; m < r.M; m++) {
+        yt[3 * m] = ytv[m].x;
+        yt[3 * m + 1] = ytv[m].y;
+        yt[3 * m + 2] = ytv[m].z;
+    }
+    free(y);
+    ref_free(&r);
+    return OR_OK;
+}
+
+/* The PC interaction as printed (Sec. 3.3.2): for each velocity component c solve
+ * V_s alpha = (K_c(x, y~_1), ..., K_c(x, y~_M)) and return sum_k alpha_k omega_k, where
+ * K(x, y) = (x x y) / (|x - y|^2 / 2) is the kernel without the -1/4pi.                  */
+static int pc_literal(const refdata* r, const v3* v, const v3* yt, const double* omega, v3 x, v3* out)
+{
+    const int M = r->M, d = r->d;
+    double* Vs = (double*)malloc(sizeof(double) * (size_t)M * M);
+    double* g = (double*)malloc(sizeof(double) * (size_t)M * 3);
+    if (!Vs || !g) {
+        free(Vs);
+        free(g);
+        return OR_ERR_MEM;
+    }
+    for (int m = 0; m < M; m++) {
+        double b[3];
+        sph_bary(yt[m], v[0], v[1], v[2], b);
+        sbb(d, b[0], b[1], b[2], Vs + (size_t)m * M);
+        v3 k = mk(0.0, 0.0, 0.0);
+        bs_term(x, yt[m], 1.0, &k);
+        g[3 * m] = k.x;
+        g[3 * m + 1] = k.y;
+        g[3 * m + 2] = k.z;
+    }
+    int rc = solve(M, Vs, g, 3);
+    if (rc == OR_OK) {
+        v3 acc = mk(0.0, 0.0, 0.0);
+        for (int k = 0; k < M; k++) {
+            acc.x += g[3 * k] * omega[k];
+            acc.y += g[3 * k + 1] * omega[k];
+            acc.z += g[3 * k + 2] * omega[k];
+        }
+        *out = acc;
+    }
+    free(Vs);
+    free(g);
+    return rc;
+}
+
+/* PC interaction of one target x[3] with one source triangle, both ways: the literal
+ * alpha-solve (lit[3]) and the proxy-point form (prx[3]); both without the -1/4pi.       */
+int or_pc_pair(const double* verts, int d, int64_t ns, const double* ys, const double* ws,
+               const double* x, double* lit, double* prx)
+{
+    if (!verts || d < 1 || d > 16 || ns < 0 || !x || !lit || !prx) return OR_ERR_ARG;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    v3 v[3] = {ld3(verts, 0), ld3(verts, 1), ld3(verts, 2)};
+    v3* y = (v3*)malloc(sizeof(v3) * (size_t)(ns > 0 ? ns : 1));
+    for (int64_t j = 0; j < ns; j++) y[j] = ld3(ys, j);
+    v3 yt[153];
+    double W[153], om[153];
+    cluster_weights(&r, v, ns, y, ws, yt, W, om);
+    v3 xx = ld3(x, 0), a = mk(0.0, 0.0, 0.0), b;
+    for (int m = 0; m < r.M; m++) bs_term(xx, yt[m], W[m], &a);
+    rc = pc_literal(&r, v, yt, om, xx, &b);
+    prx[0] = a.x; prx[1] = a.y; prx[2] = a.z;
+    lit[0] = b.x; lit[1] = b.y; lit[2] = b.z;
+    free(y);
+    ref_free(&r);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Tree-code velocity (Sec. 3): PC interactions with the far triangles of each target
+ * leaf's list, PP interactions with its near triangles, j = i excluded.  literal != 0 uses
+ * the alpha-solve for every PC interaction (tiny n only).  vel[n,3] in original order.
+ * stats[0] = PC interactions (targets x proxy points), stats[1] = PP interactions
+ * (target, source) pairs with j != i.                                                    */
+int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double theta, int d,
+                     int literal, double* vel, int64_t* stats, int nthreads)
+{
+    if (!tr || d < 1 || d > 16 || !(theta > 0.0) || !(theta < 1.0) || !vel) return OR_ERR_ARG;
+    if (tr->n > 0 && (!zeta || !area)) return OR_ERR_ARG;
+    if (!tr->has_lists || tr->theta != theta) {
+        int rc = or_tree_lists(tr, theta);
+        if (rc) return rc;
+    }
+    const int64_t n = tr->n;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    const int M = r.M;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    /* sorted copies: ys[k] = x_{perm[k]}, ws[k] = zeta A at perm[k] */
+    v3* ys = (v3*)malloc(sizeof(v3) * nn);
+    double* ws = (double*)malloc(sizeof(double) * nn);
+    int32_t* slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(tr->nnodes > 0 ? tr->nnodes : 1));
+    if (!ys || !ws || !slot) {
+        free(ys); free(ws); free(slot); ref_free(&r);
+        return OR_ERR_MEM;
+    }
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = tr->perm[k];
+        ys[k] = ld3(tr->pos, i);
+        ws[k] = zeta[i] * area[i];
+    }
+    int64_t nclu = 0;
+    for (int64_t id = 0; id < tr->nnodes; id++) slot[id] = tr->nodes[id].count > tr->leaf_size ? (int32_t)nclu++ : -1;
+    v3* yt = (v3*)malloc(sizeof(v3) * (size_t)(nclu > 0 ? nclu : 1) * M);
+    double* W = (double*)malloc(sizeof(double) * (size_t)(nclu > 0 ? nclu : 1) * M);
+    double* om = (double*)malloc(sizeof(double) * (size_t)(nclu > 0 ? nclu : 1) * M);
+    if (!yt || !W || !om) {
+        free(ys); free(ws); free(slot); free(yt); free(W); free(om); ref_free(&r);
+        return OR_ERR_MEM;
+    }
+    for (int64_t id = 0; id < tr->nnodes; id++) {
+        if (slot[id] < 0) continue;
+        const onode* nd = &tr->nodes[id];
+        cluster_weights(&r, nd->v, nd->count, ys + nd->start, ws + nd->start, yt + (size_t)slot[id] * M,
+                        W + (size_t)slot[id] * M, om + (size_t)slot[id] * M);
+    }
+    const double f = -1.0 / (4.0 * OR_PI);
+    int64_t npc = 0, npp = 0;
+    int err = 0;
+    int nth = set_threads(nthreads);
+    (void)nth;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth) reduction(+ : npc, npp) reduction(| : err)
+    for (int64_t L = 0; L < tr->nleaves; L++) {
+        const onode* t = &tr->nodes[tr->leaves[L]];
+        for (int64_t k = t->start; k < t->start + t->count; k++) {
+            v3 x = ys[k];
+            v3 acc = mk(0.0, 0.0, 0.0);
+            for (int64_t q = tr->far_off[L]; q < tr->far_off[L + 1]; q++) {
+                int32_t s = tr->far_idx[q];
+                const v3* y = yt + (size_t)slot[s] * M;
+                const double* Wm = W + (size_t)slot[s] * M;
+                if (literal) {
+                    v3 b;
+                    if (pc_literal(&r, tr->nodes[s].v, y, om + (size_t)slot[s] * M, x, &b)) err = 1;
+                    acc.x += b.x;
+                    acc.y += b.y;
+                    acc.z += b.z;
+                } else {
+                    for (int m = 0; m < M; m++) bs_term(x, y[m], Wm[m], &acc);
+                }
+                npc += M;
+            }
+            for (int64_t q = tr->near_off[L]; q < tr->near_off[L + 1]; q++) {
+                const onode* s = &tr->nodes[tr->near_idx[q]];
+                for (int64_t j = s->start; j < s->start + s->count; j++) {
+                    if (j == k) continue;
+                    bs_term(x, ys[j], ws[j], &acc);
+                    npp++;
+                }
+            }
+            int64_t i = tr->perm[k];
+            vel[3 * i] = f * acc.x;
+            vel[3 * i + 1] = f * acc.y;
+            vel[3 * i + 2] = f * acc.z;
+        }
+    }
+    if (stats) {
+        stats[0] = npc;
+        stats[1] = npp;
+    }
+    free(ys); free(ws); free(slot); free(yt); free(W); free(om);
+    ref_free(&r);
+    return err ? OR_ERR_ARG : OR_OK;
+}
+
+/* Proxy points and weights of every node with more than N_T particles (the clusters), in
+ * node order: yt[C,M,3], W[C,M].  Returns C through *nclu.  Needs the same zeta, area as
+ * or_tree_velocity.                                                                       */
+int or_tree_clusters(const or_tree* tr, const double* zeta, const double* area, int d, int64_t* nclu,
+                     int32_t* node_ids, double* yt_out, double* W_out)
+{
+    if (!tr || d < 1 || d > 16 || !nclu) return OR_ERR_ARG;
+    int64_t c = 0;
+    for (int64_t id = 0; id < tr->nnodes; id++) c += tr->nodes[id].count > tr->leaf_size;
+    *nclu = c;
+    if (!yt_out && !W_out && !node_ids) return OR_OK;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    const int M = r.M;
+    const int64_t n = tr->n;
+    v3* ys = (v3*)malloc(sizeof(v3) * (size_t)(n > 0 ? n : 1));
+    double* ws = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = tr->perm[k];
+        ys[k] = ld3(tr->pos, i);
+        ws[k] = zeta[i] * area[i];
+    }
+    int64_t q = 0;
+    for (int64_t id = 0; id < tr->nnodes; id++) {
+        const onode* nd = &tr->nodes[id];
+        if (nd->count <= tr->leaf_size) continue;
+        v3 yt[153];
+        double W[153], om[153];
+        cluster_weights(&r, nd->v, nd->count, ys + nd->start, ws + nd->start, yt, W, om);
+        if (node_ids) node_ids[q] = (int32_t)id;
+        for (int m = 0; m < M; m++) {
+            if (yt_out) {
+                yt_out[((size_t)q * M + m) * 3] = yt[m].x;
+                yt_out[((size_t)q * M + m) * 3 + 1] = yt[m].y;
+                yt_out[((size_t)q * M + m) * 3 + 2] = yt[m].z;
+            }
+            if (W_out) W_out[(size_t)q * M + m] = W[m];
+        }
+        q++;
+    }
+    free(ys);
+    free(ws);
+    ref_free(&r);
+    return OR_OK;
+}
+
+/* Icosahedron of the tree (exported for the tests): V[12,3], F[20,3].                   */
+int or_icosahedron(double* V, int32_t* F)
+{
+    v3 v[12];
+    int f[20][3];
+    ico_build(v, f);
+    for (int i = 0; i < 12; i++) {
+        V[3 * i] = v[i].x;
+        V[3 * i + 1] = v[i].y;
+        V[3 * i + 2] = v[i].z;
+    }
+    for (int i = 0; i < 20; i++)
+        for (int a = 0; a < 3; a++) F[3 * i + a] = f[i][a];
+    return OR_OK;
+}
