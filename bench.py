@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the spherical tree-code velocity evaluation on synthetic spherical inputs.
+
+One step = the whole hot path of one BVE velocity evaluation from particle positions:
+the icosahedral tree build (faces, refinement, radix sort), interaction lists, sorted source
+copies, the upward pass (SBB moments, proxy weights) and the far + near evaluation, all on
+the GPU through the C ABI (``paper_2401_07361_gb300.sts``).  The default workload is the
+single-instance precision study: N = 655362 uniform random points on the unit sphere
+(seed 0), spherical-Voronoi area weights, zero-mean vorticity = random real spherical-
+harmonic series to degree 16 (coefficients N(0, 1) / l, seed 0), theta = 0.7, degree 8,
+N_T = 128, mixed precision.  The line also reports the FP64 GPU tree code, the error of the
+mixed result against the FP64 oracle tree code, the roofline of the evaluation kernel, and
+the FP64 CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BVE velocity targets/s, mixed vs FP64 tree code at ≤1e-6 rel L2; % FP32 peak"
+SMS = 152
+FP32_LANES = 128
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="rand655k_sh16")
+    ap.add_argument("--theta", type=float, default=0.7)
+    ap.add_argument("--degree", type=int, default=8)
+    ap.add_argument("--leaf", type=int, default=None)
+    ap.add_argument("--tau-c", type=float, default=0.05,
+                    help="near FP64 threshold tau = c * 4 pi / N (half squared chord)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_workload(name):
+    from paper_2401_07361_gb300 import workloads as W
+
+    return W.workload(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def profile_traffic(kernel_file):
+    """DRAM bytes per launch of the evaluation kernel from the committed ncu summary, or None
+    when the summary is missing or was taken on a different kernel source."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", "k_eval_mixed_rand655k_sh16.md")
+    if not os.path.exists(prof):
+        return None
+    with open(kernel_file, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    src_hash, traffic = None, None
+    with open(prof) as f:
+        for line in f:
+            if line.startswith("source_sha256_16:"):
+                src_hash = line.split(":", 1)[1].strip()
+            if line.startswith("dram_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].strip())
+    return traffic if src_hash == h else None
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+
+    wl = load_workload(args.workload)
+    pos, zeta, area = wl["pos"], wl["zeta"], wl["area"]
+    leaf = args.leaf or wl["leaf_size"]
+    n = len(pos)
+    cores = os.cpu_count() or 1
+
+    def step():
+        tr = O.Tree(pos, leaf, 16)
+        return tr.velocity(zeta, area, args.theta, args.degree, nthreads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    val = n / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "targets/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree,
+                   "leaf_size": leaf, "precision": "fp64", "l2": "inputs on host"},
+        "cpu_baseline": {"value": val, "unit": "targets/s", "cores": cores, "kind": "oracle",
+                         "sample": f"full workload: oracle tree build + FP64 tree-code velocity of all {n} "
+                                   f"targets per step, OpenMP over target leaves"},
+        "e2e": {"value": val, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    from paper_2401_07361_gb300 import sts
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    wl = load_workload(args.workload)
+    pos_h, zeta_h, area_h = wl["pos"], wl["zeta"], wl["area"]
+    n = len(pos_h)
+    leaf = args.leaf or wl["leaf_size"]
+    tau = args.tau_c * 4.0 * math.pi / n
+    pm = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16,
+                    precision=sts.STS_MIXED, near_fp64_tau=tau)
+    p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
+    pos = torch.from_numpy(pos_h).to(dev)
+    zeta = torch.from_numpy(zeta_h).to(dev)
+    area = torch.from_numpy(area_h).to(dev)
+    vel = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = sts.Context()
+    h = ctx.h
+
+    def step(p=pm):
+        sts.sts_tree_build(h, pos, p)
+        sts.sts_velocity(h, zeta, area, p, vel)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stats = sts.sts_stats(h)
+    info = sts.sts_tree_info(h)
+
+    # ---- device-resident timed steps ------------------------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    sts.sts_set_timing(h, True)
+    l0 = sts.sts_launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    launches = sts.sts_launch_count() - l0
+    phases = sts.sts_phase_times(h)
+    sts.sts_set_timing(h, False)
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / max(1, args.steps)
+    value = ws * n * args.steps / (total_ms / 1e3)
+    v_mixed = vel.cpu().numpy().copy()
+
+    # ---- end to end through host buffers ----------------------------------------------
+    pos_p = torch.from_numpy(pos_h).pin_memory()
+    zeta_p = torch.from_numpy(zeta_h).pin_memory()
+    area_p = torch.from_numpy(area_h).pin_memory()
+    vel_p = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    pos2 = torch.empty_like(pos)
+    zeta2 = torch.empty_like(zeta)
+    area2 = torch.empty_like(area)
+    vel2 = torch.empty_like(vel)
+    e2e_times = []
+    e2e_steps = max(3, min(args.steps, 10))
+    for it in range(e2e_steps + 1):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pos2.copy_(pos_p, non_blocking=True)
+        zeta2.copy_(zeta_p, non_blocking=True)
+        area2.copy_(area_p, non_blocking=True)
+        sts.sts_tree_build(h, pos2, pm)
+        sts.sts_velocity(h, zeta2, area2, pm, vel2)
+        vel_p.copy_(vel2, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if it > 0:
+            e2e_times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    assert np.array_equal(vel_p.numpy(), v_mixed), "end-to-end result differs from the device-resident one"
+
+    # ---- FP64 GPU tree code (same tree), error of the mixed result ------------------
+    step(p64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step(p64)
+    e1.record()
+    e1.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    v64 = vel.cpu().numpy()
+
+    def rel_l2(a, b, w):
+        num = np.sum(np.sum((a - b) ** 2, axis=1) * w)
+        den = np.sum(np.sum(b ** 2, axis=1) * w)
+        return float(math.sqrt(num / den))
+
+    def rel_max(a, b):
+        return float(np.max(np.linalg.norm(a - b, axis=1)) / np.max(np.linalg.norm(b, axis=1)))
+
+    err_vs_gpu64 = rel_l2(v_mixed, v64, area_h)
+
+    # ---- roofline of the evaluation kernel ----------------------------------------------
+    eval_ms, eval_cnt = phases["eval"]
+    eval_avg_ms = eval_ms / max(1, eval_cnt)
+    inter = stats["pc"] + stats["pp"]
+    flops = 16.0 * inter
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (eval_avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops,
+                "traffic": profile_traffic(os.path.join(ROOT, "paper_2401_07361_gb300", "csrc", "sts_eval.cu")),
+                "kernel": "k_eval_mixed", "flops_per_launch": flops,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
+                               f"(MEASURED_PEAKS sm_max_mhz); 16 flop per interaction",
+                "kernel_ms": eval_avg_ms}
+
+    # ---- CPU oracle baseline (rank 0 only) -----------------------------------------------
+    cpu = None
+    err_vs_oracle = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        tr = O.Tree(pos_h, leaf, 16)
+        ref = tr.velocity(zeta_h, area_h, args.theta, args.degree, nthreads=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
+               "sample": f"one full evaluation: oracle tree build + FP64 tree-code velocity of all {n} targets "
+                         f"(theta {args.theta}, degree {args.degree}, N_T {leaf}), OpenMP over target leaves"}
+        err_vs_oracle = {"rel_l2": rel_l2(v_mixed, ref, area_h), "rel_max": rel_max(v_mixed, ref),
+                         "fp64_gpu_rel_l2": rel_l2(v64, ref, area_h)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree,
+                       "leaf_size": leaf, "max_level": 16, "precision": "mixed (f32 pairs, f64 positions/"
+                       "contraction/near pairs below tau)", "near_fp64_tau": tau,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "targets/s",
+                    "h2d_bytes_per_step": int(pos_h.nbytes + zeta_h.nbytes + area_h.nbytes),
+                    "d2h_bytes_per_step": int(n * 3 * 8)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "error": {"mixed_vs_fp64_gpu_tree_rel_l2": err_vs_gpu64, "vs_fp64_oracle_tree": err_vs_oracle},
+            "fp64_tree": {"value": n / (fp64_ms / 1e3), "unit": "targets/s", "ms": fp64_ms},
+            "phases_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in phases.items() if v[1]},
+            "interactions_per_step": {"pc": stats["pc"], "pp": stats["pp"]},
+            "tree": info,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * sts.h -- C ABI of the GB300 spherical tree summation library (libsts.so).
+ *
+ * The library evaluates the velocity of the Lagrangian barotropic-vorticity particle system
+ * of Chen & Jablonowski, "Fast Summation on the Sphere with Applications to the Barotropic
+ * Vorticity Equation" (arXiv 2401.07361), Sec. 2 (midpoint-rule discretisation):
+ *
+ *     u(x_i) = -(1/4pi) sum_{j != i} (x_i x x_j) zeta_j A_j / (1 - x_i . x_j)
+ *
+ * with 1 - x.y evaluated as |x - y|^2 / 2 (Sec. 2, Eq. altkernel), either directly (O(N^2))
+ * or with the spherical tree code of Sec. 3: an icosahedral triangle tree, SBB
+ * interpolation at approximate Fekete proxy points (Sec. 3.2, 3.3.2) and the MAC
+ * (r_t + r_s) / R < theta (Sec. 3.4).  bve_rk4_step advances the particles with classical
+ * RK4 (Sec. 4), dzeta_i/dt = -2 Omega u_z,i.
+ *
+ * Conventions shared by every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous, FP64 unless
+ *     stated (the export calls take HOST pointers, as stated there).  Positions are
+ *     row-major [n, 3] (x, y, z of particle i at 3i .. 3i+2), points on the unit sphere.
+ *     Velocities are written row-major [n, 3] in the caller's particle order.  The library
+ *     never frees or retains caller memory beyond the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it.  Calls that say "synchronises" wait for `stream` before returning.
+ *   - Return value: STS_OK (0) or a negative STS_ERR_* code; sts_last_error() then holds a
+ *     one-line message for the calling thread.  No exception crosses the ABI.  Arguments
+ *     are checked on the host before anything is enqueued.
+ *   - A context (sts_ctx) owns every scratch buffer (tree, lists, proxy weights, staging
+ *     copies) on the device that was current at sts_create; it grows them with cudaMalloc
+ *     on demand and frees them in sts_destroy.  One context must not be used by two host
+ *     threads at once, and calls on one context must not overlap on the GPU (different
+ *     streams without ordering race on its scratch).
+ *   - n is limited to 2^31 - 2 particles.
+ */
+#ifndef STS_H
+#define STS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STS_OK 0
+#define STS_ERR_ARG (-1)       /* invalid argument (checked on the host before launch)  */
+#define STS_ERR_CUDA (-2)      /* a CUDA runtime call or kernel launch failed          */
+#define STS_ERR_CAPACITY (-3)  /* a device-side capacity was exceeded                  */
+#define STS_ERR_TIMEOUT (-4)   /* a bounded device-side wait gave up                   */
+#define STS_ERR_NONFINITE (-5) /* non-finite position                                  */
+#define STS_ERR_STATE (-6)     /* call order violated (e.g. velocity before a tree)    */
+
+#define STS_FP64 0  /* every pair term in FP64                                          */
+#define STS_MIXED 1 /* FP32 pair terms on leaf-local coordinates with compensated sums;
+                       FP64 positions, tree geometry, proxy contraction and near pairs
+                       with |x - y|^2 / 2 < near_fp64_tau                                */
+
+/* Tree-code parameters (Sec. 3.4): theta in (0, 1) is the MAC parameter; degree in [1, 16]
+ * the SBB interpolation degree d (M = (d + 1)(d + 2) / 2 proxy points per cluster);
+ * leaf_size >= 1 the threshold N_T (a triangle with more than N_T particles is refined, and
+ * a source triangle with more than N_T particles that passes the MAC is a cluster);
+ * max_level in [0, 24] the depth limit; precision STS_FP64 or STS_MIXED;
+ * near_fp64_tau >= 0 (STS_MIXED only): near pairs with |x - y|^2 / 2 < tau are evaluated in
+ * FP64 (0 disables).                                                                       */
+typedef struct sts_params {
+    double theta;
+    int32_t degree;
+    int32_t leaf_size;
+    int32_t max_level;
+    int32_t precision;
+    double near_fp64_tau;
+} sts_params;
+
+typedef struct sts_ctx sts_ctx;
+
+/* Creates an empty context on the current device.  *out is set only on success. */
+int sts_create(sts_ctx** out);
+/* Synchronises the device and frees every buffer of the context.  NULL is a no-op. */
+void sts_destroy(sts_ctx* ctx);
+/* Message of the calling thread's last error ("" if none).  Never NULL. */
+const char* sts_last_error(void);
+/* Synchronises `stream`, returns STS_OK or the error recorded in the context's device
+ * status word (STS_ERR_CAPACITY, STS_ERR_NONFINITE), and clears the word. */
+int sts_status(sts_ctx* ctx, void* stream);
+
+/* Direct summation of the Sec. 2 system (the O(N^2) sum of Sec. 4.1).
+ * pos[n,3], zeta[n], area[n] in; vel[n,3] out (u_i at every particle; j = i and any other
+ * particle at exactly the same position contribute nothing).  precision: STS_FP64, or
+ * STS_MIXED (FP32 pair terms on positions carried as FP32 hi + lo pairs, compensated
+ * sums).  n = 0 writes nothing; n = 1 writes zeros. */
+int sts_direct(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+               int64_t n, int32_t precision, double* vel, void* stream);
+
+/* Direct summation at nt targets: targets[nt] (device, int64 original indices in [0, n)),
+ * vel[nt,3] out (row t = velocity of particle targets[t]).  Same arithmetic as
+ * sts_direct.  Target indices are not range-checked on the device: the caller keeps them
+ * in [0, n). */
+int sts_direct_targets(sts_ctx* ctx, const double* pos, const double* zeta,
+                       const double* area, int64_t n, const int64_t* targets, int64_t nt,
+                       int32_t precision, double* vel, void* stream);
+
+/* Builds the icosahedral triangle tree of Sec. 3 over pos[n,3] (copied into the context):
+ * each particle is assigned to one of the 20 faces, and every triangle holding more than
+ * p->leaf_size particles below p->max_level is split into its four children.  Particles
+ * keep their original relative order inside every leaf.  Uses p->leaf_size and
+ * p->max_level; the other fields are checked but not used.  Synchronises `stream` (it reads
+ * the number of nodes of each level).  Replaces any previous tree of the context. */
+int sts_tree_build(sts_ctx* ctx, const double* pos, int64_t n, const sts_params* p,
+                   void* stream);
+
+/* Tree-code velocity (Sec. 3.3 PC + PP interactions over MAC interaction lists, Sec. 3.4)
+ * for the tree last built in ctx: zeta[n], area[n] in, vel[n,3] out in the caller's
+ * order.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau; the tree's own
+ * leaf_size and max_level apply.  Builds the proxy weights (upward pass) on every call and
+ * the interaction lists when theta or the tree changed; synchronises `stream` in that
+ * case (list sizes are read back).  STS_ERR_STATE without a tree. */
+int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
+                 double* vel, void* stream);
+
+/* One classical RK4 step (Sec. 4) of the Sec. 2 system dx_i/dt = u_i,
+ * dzeta_i/dt = -2 Omega u_z,i, in place on pos[n,3] and zeta[n]; area[n] is constant.
+ * Every stage evaluates the tree-code velocity (parameters p, tree rebuilt) at the stage
+ * positions (projected to the unit sphere) with the stage vorticities; the new positions
+ * are projected to the sphere.  Leaves the tree of the last stage in ctx.  Synchronises
+ * `stream`. */
+int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n,
+                 double dt, double Omega, const sts_params* p, void* stream);
+
+/* ---- inspection (HOST output buffers; every call synchronises `stream`) -------------- */
+/* info[8] = {n, nodes, leaves, deepest level, far entries, near entries, clusters,
+ * evaluation tasks}; the list counts are 0 before the first sts_velocity. */
+int sts_tree_info(sts_ctx* ctx, int64_t* info, void* stream);
+/* Node table in node order (level by level, key order within a level).  Any pointer may
+ * be NULL.  perm[n]: sorted slot -> original index; per node: level, key (face index, then
+ * two bits per level), parent (-1 for roots), first_child (-1 if none), nchild, start and
+ * count (slot range), leaf flag, geom[13] = v1, v2, v3, circumcentre c, chord radius r;
+ * leaves[leaves]: leaf node ids in depth-first order. */
+int sts_tree_export(sts_ctx* ctx, int64_t* perm, int32_t* level, uint64_t* key,
+                    int32_t* parent, int32_t* first_child, int32_t* nchild, int64_t* start,
+                    int64_t* count, int32_t* leaf, int32_t* leaves, double* geom,
+                    void* stream);
+/* Interaction lists of the last sts_velocity, per leaf in depth-first order (CSR):
+ * far_off[leaves+1], far_idx[far entries] (cluster node ids), near_off[leaves+1],
+ * near_idx[near entries] (source node ids).  Any pointer may be NULL. */
+int sts_lists_export(sts_ctx* ctx, int64_t* far_off, int32_t* far_idx, int64_t* near_off,
+                     int32_t* near_idx, void* stream);
+/* Clusters of the last sts_velocity in node order: node_ids[C], proxy points yt[C,M,3] and
+ * proxy weights W[C,M] (FP64 values as the evaluation uses them).  Any pointer may be NULL. */
+int sts_clusters_export(sts_ctx* ctx, int32_t* node_ids, double* yt, double* W, void* stream);
+/* Proxy reference data of degree d, computed on the host: beta[M,3] (barycentric proxy
+ * points on the reference simplex, in selection order) and vinv[M,M] (inverse of
+ * V_ref[m][k] = B_k(beta_m), row k, column m).  Either pointer may be NULL.  Needs no GPU. */
+int sts_proxy_reference(int32_t degree, double* beta, double* vinv);
+/* Interaction counts of the last sts_velocity: stats[0] = PC interactions (targets x proxy
+ * points), stats[1] = PP pairs (j != i). */
+int sts_stats(sts_ctx* ctx, int64_t* stats, void* stream);
+
+/* ---- phase timing (CUDA events recorded on the launching stream) ------------------- */
+#define STS_PHASE_BUILD 0  /* sts_tree_build, whole call                                */
+#define STS_PHASE_SORT 1   /* radix sort and leaf list inside the build                 */
+#define STS_PHASE_LISTS 2  /* interaction lists and evaluation tasks                    */
+#define STS_PHASE_PREP 3   /* sorted source copies                                      */
+#define STS_PHASE_UPWARD 4 /* SBB moments and proxy weights                             */
+#define STS_PHASE_EVAL 5   /* the far + near evaluation kernel                          */
+#define STS_PHASE_DIRECT 6 /* direct sum (all its kernels)                              */
+#define STS_NUM_PHASES 7
+/* on != 0 starts recording per-phase events and resets the totals; 0 stops. */
+int sts_set_timing(sts_ctx* ctx, int32_t on);
+/* Total milliseconds and number of timed occurrences per phase since sts_set_timing(1);
+ * ms[nph], count[nph] (host), nph <= STS_NUM_PHASES.  Synchronises the recorded events. */
+int sts_phase_times(sts_ctx* ctx, double* ms, int32_t* count, int32_t nph);
+
+/* Number of kernels this library has launched in the process so far (all contexts). */
+int sts_launch_count(int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STS_H */

@@ -1,0 +1,543 @@
+// The extern "C" entry points of libsts (declared in include/sts.h): argument checks, the
+// context and its scratch, phase timing, and the order in which the device stages run.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "sts_internal.cuh"
+
+namespace sts {
+
+static thread_local char g_err[512];
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
+{
+    if (!c->timing) return;
+    if (c->phase_open[ph]) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(c->ev[ph][1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, c->ev[ph][0], c->ev[ph][1]) == cudaSuccess) {
+            c->phase_ms[ph] += ms;
+            c->phase_count[ph] += 1;
+        }
+        c->phase_open[ph] = false;
+    }
+    cudaEventRecord(c->ev[ph][0], s);
+}
+
+void phase_end(sts_ctx* c, int ph, cudaStream_t s)
+{
+    if (!c->timing) return;
+    cudaEventRecord(c->ev[ph][1], s);
+    c->phase_open[ph] = true;
+}
+
+}  // namespace sts
+
+using namespace sts;
+
+sts_ctx::~sts_ctx()
+{
+    pos.release(); nodeof.release(); digit.release(); perm.release(); perm_tmp.release();
+    skey.release(); skey_tmp.release(); scan_tmp.release(); hist.release(); flags.release();
+    offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
+    nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
+    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_cc.release(); nd_child.release();
+    counters.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
+    cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release();
+    prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release();
+    near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
+    near_ent.release(); list_cnt.release(); tasks.release(); dsrc64.release(); dsrc32.release();
+    dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release();
+    for (RefTable* t : refs)
+        if (t) {
+            t->d_beta.release();
+            t->d_vinv.release();
+            delete t;
+        }
+    for (int p = 0; p < kNumPhases; p++)
+        for (int q = 0; q < 2; q++)
+            if (ev[p][q]) cudaEventDestroy(ev[p][q]);
+    if (d_status) cudaFree(d_status);
+    if (h_pinned) cudaFreeHost(h_pinned);
+}
+
+namespace {
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+int check_ctx(sts_ctx* c, const char* fn)
+{
+    g_err[0] = 0;
+    if (!c) {
+        set_error("%s: NULL context", fn);
+        return STS_ERR_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device) {
+        if (cudaSetDevice(c->device) != cudaSuccess) {
+            set_error("%s: cannot select the context's device %d", fn, c->device);
+            return STS_ERR_CUDA;
+        }
+    }
+    return STS_OK;
+}
+
+int check_params(const sts_params* p, const char* fn)
+{
+    if (!p) {
+        set_error("%s: NULL params", fn);
+        return STS_ERR_ARG;
+    }
+    if (!(p->theta > 0.0 && p->theta < 1.0)) {
+        set_error("%s: theta must be in (0, 1), got %g", fn, p->theta);
+        return STS_ERR_ARG;
+    }
+    if (p->degree < 1 || p->degree > kMaxDegree) {
+        set_error("%s: degree must be in [1, %d], got %d", fn, kMaxDegree, p->degree);
+        return STS_ERR_ARG;
+    }
+    if (p->leaf_size < 1) {
+        set_error("%s: leaf_size must be >= 1, got %d", fn, p->leaf_size);
+        return STS_ERR_ARG;
+    }
+    if (p->max_level < 0 || p->max_level > kMaxLevel) {
+        set_error("%s: max_level must be in [0, %d], got %d", fn, kMaxLevel, p->max_level);
+        return STS_ERR_ARG;
+    }
+    if (p->precision != STS_FP64 && p->precision != STS_MIXED) {
+        set_error("%s: precision must be STS_FP64 or STS_MIXED, got %d", fn, p->precision);
+        return STS_ERR_ARG;
+    }
+    if (!(p->near_fp64_tau >= 0.0) || !isfinite(p->near_fp64_tau)) {
+        set_error("%s: near_fp64_tau must be finite and >= 0", fn);
+        return STS_ERR_ARG;
+    }
+    return STS_OK;
+}
+
+int check_n(int64_t n, const char* fn)
+{
+    if (n < 0 || n > ((int64_t)1 << 31) - 2) {
+        set_error("%s: n must be in [0, 2^31 - 2], got %lld", fn, (long long)n);
+        return STS_ERR_ARG;
+    }
+    return STS_OK;
+}
+
+int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p,
+                  double* vel, cudaStream_t s)
+{
+    const int64_t n = c->n;
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(vel, 0, 3 * sizeof(double), s));
+        return STS_OK;
+    }
+    int rc;
+    phase_begin(c, kPhPrep, s);
+    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
+    phase_end(c, kPhPrep, s);
+    if (!c->have_lists || c->list_theta != p->theta) {
+        phase_begin(c, kPhLists, s);
+        if ((rc = build_lists(c, p->theta, s))) return rc;
+        phase_end(c, kPhLists, s);
+    }
+    phase_begin(c, kPhUpward, s);
+    if ((rc = upward_pass(c, p->degree, p->precision, s))) return rc;
+    phase_end(c, kPhUpward, s);
+    if ((rc = evaluate(c, p->degree, p->precision, p->near_fp64_tau, vel, s))) return rc;
+    c->list_degree = p->degree;
+    return STS_OK;
+}
+
+int build_impl(sts_ctx* c, const double* pos, int64_t n, const sts_params* p, cudaStream_t s)
+{
+    phase_begin(c, kPhBuild, s);
+    int rc = tree_build(c, pos, n, p->leaf_size, p->max_level, s);
+    if (rc == STS_OK && n > 0) rc = build_clusters(c, s);
+    phase_end(c, kPhBuild, s);
+    return rc;
+}
+
+}  // namespace
+
+namespace {
+template <class D, class H>
+int copy_out(H* host, const D* dev, int64_t n, cudaStream_t s)
+{
+    if (!host || n <= 0) return STS_OK;
+    std::vector<D> tmp((size_t)n);
+    STS_CUDA(cudaMemcpyAsync(tmp.data(), dev, n * sizeof(D), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n; i++) host[i] = (H)tmp[(size_t)i];
+    return STS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sts_create(sts_ctx** out)
+{
+    g_err[0] = 0;
+    if (!out) {
+        set_error("sts_create: NULL out");
+        return STS_ERR_ARG;
+    }
+    sts_ctx* c = new (std::nothrow) sts_ctx();
+    if (!c) {
+        set_error("sts_create: out of host memory");
+        return STS_ERR_ARG;
+    }
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        set_error("sts_create: %s", cudaGetErrorString(e));
+        delete c;
+        return STS_ERR_CUDA;
+    }
+    *out = c;
+    return STS_OK;
+}
+
+void sts_destroy(sts_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    delete ctx;
+}
+
+const char* sts_last_error(void) { return g_err; }
+
+int sts_status(sts_ctx* ctx, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_status");
+    if (rc) return rc;
+    STS_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+    STS_CUDA(cudaStreamSynchronize(S(stream)));
+    const int st = ((int32_t*)ctx->h_pinned)[0];
+    STS_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), S(stream)));
+    if (st & kStatusCapacity) {
+        set_error("device capacity exceeded");
+        return STS_ERR_CAPACITY;
+    }
+    if (st & kStatusNonfinite) {
+        set_error("non-finite position");
+        return STS_ERR_NONFINITE;
+    }
+    return STS_OK;
+}
+
+int sts_direct(sts_ctx* ctx, const double* pos, const double* zeta, const double* area, int64_t n,
+               int32_t precision, double* vel, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_direct");
+    if (rc || (rc = check_n(n, "sts_direct"))) return rc;
+    if (precision != STS_FP64 && precision != STS_MIXED) {
+        set_error("sts_direct: precision must be STS_FP64 or STS_MIXED");
+        return STS_ERR_ARG;
+    }
+    if (n > 0 && (!pos || !zeta || !area || !vel)) {
+        set_error("sts_direct: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(vel, 0, 3 * sizeof(double), S(stream)));
+        return STS_OK;
+    }
+    return direct_sum(ctx, pos, zeta, area, n, nullptr, n, precision, vel, S(stream));
+}
+
+int sts_direct_targets(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+                       int64_t n, const int64_t* targets, int64_t nt, int32_t precision, double* vel,
+                       void* stream)
+{
+    int rc = check_ctx(ctx, "sts_direct_targets");
+    if (rc || (rc = check_n(n, "sts_direct_targets"))) return rc;
+    if (precision != STS_FP64 && precision != STS_MIXED) {
+        set_error("sts_direct_targets: precision must be STS_FP64 or STS_MIXED");
+        return STS_ERR_ARG;
+    }
+    if (nt < 0 || (nt > 0 && (n < 1 || !targets || !vel || !pos || !zeta || !area))) {
+        set_error("sts_direct_targets: bad targets or NULL array");
+        return STS_ERR_ARG;
+    }
+    if (nt == 0) return STS_OK;
+    return direct_sum(ctx, pos, zeta, area, n, targets, nt, precision, vel, S(stream));
+}
+
+int sts_tree_build(sts_ctx* ctx, const double* pos, int64_t n, const sts_params* p, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_tree_build");
+    if (rc || (rc = check_n(n, "sts_tree_build")) || (rc = check_params(p, "sts_tree_build"))) return rc;
+    if (n > 0 && !pos) {
+        set_error("sts_tree_build: NULL pos");
+        return STS_ERR_ARG;
+    }
+    return build_impl(ctx, pos, n, p, S(stream));
+}
+
+int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p, double* vel,
+                 void* stream)
+{
+    int rc = check_ctx(ctx, "sts_velocity");
+    if (rc || (rc = check_params(p, "sts_velocity"))) return rc;
+    if (!ctx->have_tree) {
+        set_error("sts_velocity: no tree (call sts_tree_build first)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->n > 0 && (!zeta || !area || !vel)) {
+        set_error("sts_velocity: NULL array");
+        return STS_ERR_ARG;
+    }
+    return velocity_impl(ctx, zeta, area, p, vel, S(stream));
+}
+
+int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, double dt,
+                 double Omega, const sts_params* p, void* stream)
+{
+    int rc = check_ctx(ctx, "bve_rk4_step");
+    if (rc || (rc = check_n(n, "bve_rk4_step")) || (rc = check_params(p, "bve_rk4_step"))) return rc;
+    if (!isfinite(dt) || !isfinite(Omega)) {
+        set_error("bve_rk4_step: dt and Omega must be finite");
+        return STS_ERR_ARG;
+    }
+    if (n > 0 && (!pos || !zeta || !area)) {
+        set_error("bve_rk4_step: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (n == 0) return STS_OK;
+    cudaStream_t s = S(stream);
+    sts_ctx* c = ctx;
+    STS_CUDA(c->rk_x0.reserve(3 * n));
+    STS_CUDA(c->rk_z0.reserve(n));
+    STS_CUDA(c->rk_xs.reserve(3 * n));
+    STS_CUDA(c->rk_zs.reserve(n));
+    STS_CUDA(c->rk_k.reserve(3 * n));
+    STS_CUDA(c->rk_ksum.reserve(3 * n));
+    STS_CUDA(cudaMemcpyAsync(c->rk_x0.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    STS_CUDA(cudaMemcpyAsync(c->rk_z0.p, zeta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double cst[3] = {0.5, 0.5, 1.0};
+    const double bst[3] = {1.0, 2.0, 2.0};
+    const double* xs = c->rk_x0.p;
+    const double* zs = c->rk_z0.p;
+    for (int st = 0; st < 4; st++) {
+        if ((rc = build_impl(c, xs, n, p, s))) return rc;
+        if ((rc = velocity_impl(c, zs, area, p, c->rk_k.p, s))) return rc;
+        if (st < 3) {
+            rk4_stage(c->rk_x0.p, c->rk_z0.p, c->rk_k.p, cst[st] * dt, Omega, c->rk_xs.p, c->rk_zs.p,
+                      c->rk_ksum.p, bst[st], st == 0, n, s);
+            xs = c->rk_xs.p;
+            zs = c->rk_zs.p;
+        } else {
+            rk4_final(pos, zeta, c->rk_x0.p, c->rk_z0.p, c->rk_ksum.p, c->rk_k.p, dt, Omega, n, s);
+        }
+        STS_LAUNCH_CHECK();
+    }
+    return STS_OK;
+}
+
+int sts_tree_info(sts_ctx* ctx, int64_t* info, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_tree_info");
+    if (rc) return rc;
+    if (!info) {
+        set_error("sts_tree_info: NULL info");
+        return STS_ERR_ARG;
+    }
+    STS_CUDA(cudaStreamSynchronize(S(stream)));
+    info[0] = ctx->have_tree ? ctx->n : 0;
+    info[1] = ctx->nnodes;
+    info[2] = ctx->nleaves;
+    info[3] = ctx->deepest;
+    info[4] = ctx->have_lists ? ctx->nfar : 0;
+    info[5] = ctx->have_lists ? ctx->nnear : 0;
+    info[6] = ctx->nclusters;
+    info[7] = ctx->have_lists ? ctx->ntasks : 0;
+    return STS_OK;
+}
+
+int sts_tree_export(sts_ctx* ctx, int64_t* perm, int32_t* level, uint64_t* key, int32_t* parent,
+                    int32_t* first_child, int32_t* nchild, int64_t* start, int64_t* count, int32_t* leaf,
+                    int32_t* leaves, double* geom, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_tree_export");
+    if (rc) return rc;
+    if (!ctx->have_tree) {
+        set_error("sts_tree_export: no tree");
+        return STS_ERR_STATE;
+    }
+    cudaStream_t s = S(stream);
+    const int64_t nn = ctx->nnodes;
+    if ((rc = copy_out(perm, ctx->perm.p, ctx->n, s)) || (rc = copy_out(level, ctx->nd_level.p, nn, s)) ||
+        (rc = copy_out(key, ctx->nd_key.p, nn, s)) || (rc = copy_out(parent, ctx->nd_parent.p, nn, s)) ||
+        (rc = copy_out(first_child, ctx->nd_first_child.p, nn, s)) ||
+        (rc = copy_out(nchild, ctx->nd_nchild.p, nn, s)) || (rc = copy_out(start, ctx->nd_start.p, nn, s)) ||
+        (rc = copy_out(count, ctx->nd_count.p, nn, s)) || (rc = copy_out(leaf, ctx->nd_leaf.p, nn, s)) ||
+        (rc = copy_out(leaves, ctx->leaves.p, ctx->nleaves, s)) ||
+        (rc = copy_out(geom, ctx->nd_geom.p, 13 * nn, s)))
+        return rc;
+    return STS_OK;
+}
+
+int sts_lists_export(sts_ctx* ctx, int64_t* far_off, int32_t* far_idx, int64_t* near_off, int32_t* near_idx,
+                     void* stream)
+{
+    int rc = check_ctx(ctx, "sts_lists_export");
+    if (rc) return rc;
+    if (!ctx->have_lists) {
+        set_error("sts_lists_export: no lists (call sts_velocity first)");
+        return STS_ERR_STATE;
+    }
+    cudaStream_t s = S(stream);
+    const int64_t L = ctx->nleaves;
+    if ((rc = copy_out(far_off, ctx->far_off.p, L + 1, s)) || (rc = copy_out(near_off, ctx->near_off.p, L + 1, s)) ||
+        (rc = copy_out(far_idx, ctx->far_idx.p, ctx->nfar, s)) ||
+        (rc = copy_out(near_idx, ctx->near_idx.p, ctx->nnear, s)))
+        return rc;
+    return STS_OK;
+}
+
+int sts_clusters_export(sts_ctx* ctx, int32_t* node_ids, double* yt, double* W, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_clusters_export");
+    if (rc) return rc;
+    if (ctx->up_degree < 0) {
+        set_error("sts_clusters_export: no proxy weights (call sts_velocity first)");
+        return STS_ERR_STATE;
+    }
+    cudaStream_t s = S(stream);
+    const int64_t C = ctx->nclusters;
+    const int M = nbasis(ctx->up_degree);
+    if ((rc = copy_out(node_ids, ctx->cluster_node.p, C, s))) return rc;
+    if ((yt || W) && C > 0) {
+        std::vector<double4> tmp((size_t)(C * M));
+        STS_CUDA(cudaMemcpyAsync(tmp.data(), ctx->prx64.p, C * M * sizeof(double4), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        for (int64_t q = 0; q < C * M; q++) {
+            if (yt) {
+                yt[3 * q] = tmp[(size_t)q].x;
+                yt[3 * q + 1] = tmp[(size_t)q].y;
+                yt[3 * q + 2] = tmp[(size_t)q].z;
+            }
+            if (W) W[q] = 0.5 * tmp[(size_t)q].w;
+        }
+    }
+    return STS_OK;
+}
+
+int sts_proxy_reference(int32_t degree, double* beta, double* vinv)
+{
+    g_err[0] = 0;
+    if (degree < 1 || degree > kMaxDegree) {
+        set_error("sts_proxy_reference: degree must be in [1, %d]", kMaxDegree);
+        return STS_ERR_ARG;
+    }
+    RefTable t;
+    if (build_ref_table(degree, &t) != STS_OK) {
+        set_error("sts_proxy_reference: degree %d table failed", degree);
+        return STS_ERR_ARG;
+    }
+    if (beta) memcpy(beta, t.beta.data(), t.beta.size() * sizeof(double));
+    if (vinv) memcpy(vinv, t.vinv.data(), t.vinv.size() * sizeof(double));
+    return STS_OK;
+}
+
+int sts_stats(sts_ctx* ctx, int64_t* stats, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_stats");
+    if (rc) return rc;
+    if (!stats) {
+        set_error("sts_stats: NULL stats");
+        return STS_ERR_ARG;
+    }
+    if (!ctx->have_lists || ctx->list_degree < 0) {
+        set_error("sts_stats: no lists (call sts_velocity first)");
+        return STS_ERR_STATE;
+    }
+    cudaStream_t s = S(stream);
+    if ((rc = count_interactions(ctx, ctx->list_degree, s))) return rc;
+    unsigned long long h[2];
+    STS_CUDA(cudaMemcpyAsync(h, ctx->d_stats.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    stats[0] = (int64_t)h[0];
+    stats[1] = (int64_t)h[1];
+    return STS_OK;
+}
+
+int sts_set_timing(sts_ctx* ctx, int32_t on)
+{
+    int rc = check_ctx(ctx, "sts_set_timing");
+    if (rc) return rc;
+    if (on) {
+        for (int p = 0; p < kNumPhases; p++)
+            for (int q = 0; q < 2; q++)
+                if (!ctx->ev[p][q]) STS_CUDA(cudaEventCreate(&ctx->ev[p][q]));
+    }
+    for (int p = 0; p < kNumPhases; p++) {
+        ctx->phase_ms[p] = 0.f;
+        ctx->phase_count[p] = 0;
+        ctx->phase_open[p] = false;
+    }
+    ctx->timing = on != 0;
+    return STS_OK;
+}
+
+int sts_phase_times(sts_ctx* ctx, double* ms, int32_t* count, int32_t nph)
+{
+    int rc = check_ctx(ctx, "sts_phase_times");
+    if (rc) return rc;
+    if (nph < 0 || nph > kNumPhases) {
+        set_error("sts_phase_times: nph must be in [0, %d]", kNumPhases);
+        return STS_ERR_ARG;
+    }
+    for (int p = 0; p < nph; p++) {
+        if (ctx->phase_open[p]) {
+            float m = 0.f;
+            STS_CUDA(cudaEventSynchronize(ctx->ev[p][1]));
+            STS_CUDA(cudaEventElapsedTime(&m, ctx->ev[p][0], ctx->ev[p][1]));
+            ctx->phase_ms[p] += m;
+            ctx->phase_count[p] += 1;
+            ctx->phase_open[p] = false;
+        }
+        if (ms) ms[p] = ctx->phase_ms[p];
+        if (count) count[p] = ctx->phase_count[p];
+    }
+    return STS_OK;
+}
+
+int sts_launch_count(int64_t* out)
+{
+    g_err[0] = 0;
+    if (!out) {
+        set_error("sts_launch_count: NULL out");
+        return STS_ERR_ARG;
+    }
+    *out = (int64_t)g_launches.load(std::memory_order_relaxed);
+    return STS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,445 @@
+// Velocity evaluation: the tree code's far field (PC interactions with the proxy points of
+// well-separated clusters, Sec. 3.3.2) and near field (PP interactions, Sec. 3.3.1), and the
+// direct sum of the Sec. 2 particle system.  Every pair term is
+//     w_j (x_i x d) / (|d|^2 / 2),   d = y_j - x_i,   w_j = zeta_j A_j,
+// i.e. the kernel (x_i x x_j) / (1 - x_i . x_j) with 1 - x.y written as |x - y|^2 / 2
+// (Eq. altkernel) and x_i x x_j = x_i x d.  The kernels accumulate S_i = sum_j 2 w_j d /
+// |d|^2 and the epilogue forms u_i = -(1/4 pi) x_i x S_i in FP64.
+//
+// Evaluation layout: one warp per task (up to 32 consecutive targets of one leaf, lane =
+// target).  When a task has 16 or fewer targets, 2 or 4 lanes share a target and split its
+// sources; they are summed with shuffles at the end.  Source blocks (a cluster's M proxy
+// points, a near leaf's particles) are staged in shared memory by the warp with coalesced
+// 16-byte loads, each lane then streams the block with broadcast shared-memory reads.
+//
+// Mixed precision (STS_MIXED): targets, sources and proxy points are stored in FP32
+// relative to the circumcentre of their own leaf or cluster; the FP32 offset between the two
+// centres (rounded once from FP64 per list entry) is added when a block is staged, so that
+// d keeps FP32 relative accuracy at every distance the tree produces.  Per block the lane
+// sums in FP32, and the block partials go into a TwoSum-compensated accumulator.  Near pairs
+// with |d|^2 / 2 < tau are evaluated in FP64 from the FP64 positions instead.  A zero d
+// (the target itself, or a coincident particle) contributes nothing, as in the oracle:
+// |d|^2 carries an additive 1e-30 so that 2w / |d|^2 stays finite and is multiplied by 0.
+#include "sts_internal.cuh"
+
+namespace sts {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kEvalWarps = 4;
+constexpr int kPadStage = kStage + 16;
+constexpr float kEps = 1e-30f;
+constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Knuth's TwoSum: hi + lo += p with the rounding error of the add kept in lo.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float p)
+{
+    const float s = hi + p;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += e;
+}
+
+__device__ __forceinline__ void pair32(const float4 s, float tx, float ty, float tz, float& ax,
+                                       float& ay, float& az)
+{
+    const float dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
+    const float c = s.w * rcp_approx(r2);
+    ax = fmaf(c, dx, ax);
+    ay = fmaf(c, dy, ay);
+    az = fmaf(c, dz, az);
+}
+
+__device__ __forceinline__ void pair64(const double4 s, double tx, double ty, double tz, double& ax,
+                                       double& ay, double& az)
+{
+    const double dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double c = r2 > 0.0 ? s.w / r2 : 0.0;
+    ax = fma(c, dx, ax);
+    ay = fma(c, dy, ay);
+    az = fma(c, dz, az);
+}
+
+__device__ __forceinline__ void epilogue(double Sx, double Sy, double Sz, int G, bool write,
+                                         double xx, double xy, double xz, int64_t i, double* vel)
+{
+    for (int o = G; o < 32; o <<= 1) {
+        Sx += __shfl_xor_sync(kFull, Sx, o);
+        Sy += __shfl_xor_sync(kFull, Sy, o);
+        Sz += __shfl_xor_sync(kFull, Sz, o);
+    }
+    if (write) {
+        vel[3 * i] = -kInv4Pi * (xy * Sz - xz * Sy);
+        vel[3 * i + 1] = -kInv4Pi * (xz * Sx - xx * Sz);
+        vel[3 * i + 2] = -kInv4Pi * (xx * Sy - xy * Sx);
+    }
+}
+
+// ------------------------------------------------------------------------ mixed tree
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
+             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_off,
+             const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
+             const float4* __restrict__ src32, const double4* __restrict__ src64,
+             const int32_t* __restrict__ perm, float tau2, double* __restrict__ vel)
+{
+    __shared__ float4 sbuf[kEvalWarps][kPadStage];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
+    if (ti >= ntasks) return;
+    const Task tk = tasks[ti];
+    const int S = tk.nt <= 8 ? 4 : (tk.nt <= 16 ? 2 : 1);
+    const int G = 32 / S;
+    const int tg = lane & (G - 1), ph = lane / G;
+    const bool valid = tg < tk.nt;
+    const int64_t k = tk.t0 + (valid ? tg : 0);
+    const float4 t4 = src32[k];
+    const double4 x64 = src64[k];
+    const float tx = valid ? t4.x : -1e3f, ty = valid ? t4.y : -1e3f, tz = valid ? t4.z : -1e3f;
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    double ex = 0.0, ey = 0.0, ez = 0.0;
+    float4* sb = sbuf[w];
+    const int step = 4 * S;
+    const float4 dummy = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+
+    // far field: proxy points of well-separated clusters
+    for (int64_t q = far_off[tk.leaf], qe = far_off[tk.leaf + 1]; q < qe; q++) {
+        const FarEntry e = far_ent[q];
+        const float4* P = prx32 + (int64_t)e.slot * M;
+        for (int c0 = 0; c0 < M; c0 += kStage) {
+            const int nb = min(kStage, M - c0);
+            const int nbp = (nb + step - 1) / step * step;
+            __syncwarp();
+            for (int i = lane; i < nbp; i += 32) {
+                float4 v = i < nb ? P[c0 + i] : dummy;
+                v.x += e.dx;
+                v.y += e.dy;
+                v.z += e.dz;
+                sb[i] = v;
+            }
+            __syncwarp();
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int i = ph; i < nbp; i += step) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) pair32(sb[i + u * S], tx, ty, tz, px, py, pz);
+            }
+            two_sum_add(hx, lx, px);
+            two_sum_add(hy, ly, py);
+            two_sum_add(hz, lz, pz);
+        }
+    }
+    // near field: particles of the near leaves; pairs closer than tau in FP64
+    for (int64_t q = near_off[tk.leaf], qe = near_off[tk.leaf + 1]; q < qe; q++) {
+        const NearEntry e = near_ent[q];
+        for (int c0 = 0; c0 < e.count; c0 += kStage) {
+            const int nb = min(kStage, e.count - c0);
+            const int nbp = (nb + step - 1) / step * step;
+            const int64_t base = (int64_t)e.start + c0;
+            __syncwarp();
+            for (int i = lane; i < nbp; i += 32) {
+                float4 v = i < nb ? src32[base + i] : dummy;
+                v.x += e.dx;
+                v.y += e.dy;
+                v.z += e.dz;
+                sb[i] = v;
+            }
+            __syncwarp();
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int i = ph; i < nbp; i += step) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int ii = i + u * S;
+                    const float4 s = sb[ii];
+                    const float dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
+                    float c = s.w * rcp_approx(r2);
+                    if (r2 < tau2) {
+                        c = 0.f;  // padding slots (ii >= nb) carry w = 0 and are skipped
+                        const double4 y = src64[base + min(ii, nb - 1)];
+                        const double ddx = y.x - x64.x, ddy = y.y - x64.y, ddz = y.z - x64.z;
+                        const double s2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
+                        if (s2 > 0.0 && ii < nb) {
+                            const double t = y.w / s2;
+                            ex = fma(t, ddx, ex);
+                            ey = fma(t, ddy, ey);
+                            ez = fma(t, ddz, ez);
+                        }
+                    }
+                    px = fmaf(c, dx, px);
+                    py = fmaf(c, dy, py);
+                    pz = fmaf(c, dz, pz);
+                }
+            }
+            two_sum_add(hx, lx, px);
+            two_sum_add(hy, ly, py);
+            two_sum_add(hz, lz, pz);
+        }
+    }
+    const double Sx = ((double)hx + (double)lx) + ex;
+    const double Sy = ((double)hy + (double)ly) + ey;
+    const double Sz = ((double)hz + (double)lz) + ez;
+    epilogue(Sx, Sy, Sz, G, valid && ph == 0, x64.x, x64.y, x64.z, perm[k], vel);
+}
+
+// ------------------------------------------------------------------------ FP64 tree
+__global__ void __launch_bounds__(kEvalWarps * 32)
+k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
+            const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_off,
+            const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
+            const double4* __restrict__ src64, const int32_t* __restrict__ perm,
+            double* __restrict__ vel)
+{
+    __shared__ double4 sbuf[kEvalWarps][kPadStage];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
+    if (ti >= ntasks) return;
+    const Task tk = tasks[ti];
+    const int S = tk.nt <= 8 ? 4 : (tk.nt <= 16 ? 2 : 1);
+    const int G = 32 / S;
+    const int tg = lane & (G - 1), ph = lane / G;
+    const bool valid = tg < tk.nt;
+    const int64_t k = tk.t0 + (valid ? tg : 0);
+    const double4 x64 = src64[k];
+    const double tx = valid ? x64.x : -1e3, ty = valid ? x64.y : -1e3, tz = valid ? x64.z : -1e3;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    double4* sb = sbuf[w];
+    const int step = 4 * S;
+    const double4 dummy = make_double4(1e3, 1e3, 1e3, 0.0);
+
+    for (int64_t q = far_off[tk.leaf], qe = far_off[tk.leaf + 1]; q < qe; q++) {
+        const double4* P = prx64 + (int64_t)far_ent[q].slot * M;
+        for (int c0 = 0; c0 < M; c0 += kStage) {
+            const int nb = min(kStage, M - c0);
+            const int nbp = (nb + step - 1) / step * step;
+            __syncwarp();
+            for (int i = lane; i < nbp; i += 32) sb[i] = i < nb ? P[c0 + i] : dummy;
+            __syncwarp();
+            for (int i = ph; i < nbp; i += step) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) pair64(sb[i + u * S], tx, ty, tz, ax, ay, az);
+            }
+        }
+    }
+    for (int64_t q = near_off[tk.leaf], qe = near_off[tk.leaf + 1]; q < qe; q++) {
+        const NearEntry e = near_ent[q];
+        for (int c0 = 0; c0 < e.count; c0 += kStage) {
+            const int nb = min(kStage, e.count - c0);
+            const int nbp = (nb + step - 1) / step * step;
+            const int64_t base = (int64_t)e.start + c0;
+            __syncwarp();
+            for (int i = lane; i < nbp; i += 32) sb[i] = i < nb ? src64[base + i] : dummy;
+            __syncwarp();
+            for (int i = ph; i < nbp; i += step) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) pair64(sb[i + u * S], tx, ty, tz, ax, ay, az);
+            }
+        }
+    }
+    epilogue(ax, ay, az, G, valid && ph == 0, x64.x, x64.y, x64.z, perm[k], vel);
+}
+
+// ------------------------------------------------------------------------ counts
+__global__ void k_count(int64_t nleaves, const int32_t* __restrict__ leaves,
+                        const int32_t* __restrict__ count, const int64_t* __restrict__ far_off,
+                        const int64_t* __restrict__ near_off, const NearEntry* __restrict__ near_ent,
+                        int M, unsigned long long* __restrict__ stats)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaves) return;
+    const unsigned long long nl = (unsigned long long)count[leaves[L]];
+    const unsigned long long pc = nl * (unsigned long long)M * (unsigned long long)(far_off[L + 1] - far_off[L]);
+    unsigned long long ns = 0;
+    for (int64_t q = near_off[L]; q < near_off[L + 1]; q++) ns += (unsigned long long)near_ent[q].count;
+    atomicAdd(&stats[0], pc);
+    atomicAdd(&stats[1], nl * (ns - 1ull));
+}
+
+// ------------------------------------------------------------------------ direct sum
+constexpr int kDirT = 128;
+
+__global__ void k_direct_prep(const double* __restrict__ pos, const double* __restrict__ zeta,
+                              const double* __restrict__ area, int64_t n, double4* __restrict__ s64,
+                              float4* __restrict__ s32)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+    const double w2 = 2.0 * (zeta[j] * area[j]);
+    s64[j] = make_double4(x, y, z, w2);
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    s32[2 * j] = make_float4(hx, hy, hz, (float)w2);
+    s32[2 * j + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
+}
+
+__global__ void __launch_bounds__(kDirT)
+k_direct_fp64(const double4* __restrict__ s64, int64_t n, const int64_t* __restrict__ targets,
+              int64_t nt, int64_t chunk, double* __restrict__ part)
+{
+    __shared__ double4 sb[kDirT];
+    const int64_t t = (int64_t)blockIdx.x * kDirT + threadIdx.x;
+    const bool valid = t < nt;
+    const int64_t i = valid ? (targets ? targets[t] : t) : 0;
+    const double4 x = s64[i];
+    const double tx = valid ? x.x : -1e3, ty = valid ? x.y : -1e3, tz = valid ? x.z : -1e3;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int64_t b = j0; b < j1; b += kDirT) {
+        __syncthreads();
+        const int64_t j = b + threadIdx.x;
+        sb[threadIdx.x] = j < j1 ? s64[j] : make_double4(1e3, 1e3, 1e3, 0.0);
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < kDirT; q++) pair64(sb[q], tx, ty, tz, ax, ay, az);
+    }
+    if (valid) {
+        double* o = part + 3 * ((int64_t)blockIdx.y * nt + t);
+        o[0] = ax;
+        o[1] = ay;
+        o[2] = az;
+    }
+}
+
+// Mixed direct sum: positions carried as FP32 hi + lo pairs, d = (y_hi - x_hi) + (y_lo -
+// x_lo), so d keeps FP32 relative accuracy for close pairs without any tree frame.
+__global__ void __launch_bounds__(kDirT)
+k_direct_mixed(const float4* __restrict__ s32, int64_t n, const int64_t* __restrict__ targets,
+               int64_t nt, int64_t chunk, double* __restrict__ part)
+{
+    __shared__ float4 sh[kDirT], sl[kDirT];
+    const int64_t t = (int64_t)blockIdx.x * kDirT + threadIdx.x;
+    const bool valid = t < nt;
+    const int64_t i = valid ? (targets ? targets[t] : t) : 0;
+    const float4 xh = s32[2 * i], xl = s32[2 * i + 1];
+    const float hx = valid ? xh.x : -1e3f, hy = valid ? xh.y : -1e3f, hz = valid ? xh.z : -1e3f;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    float Hx = 0.f, Hy = 0.f, Hz = 0.f, Lx = 0.f, Ly = 0.f, Lz = 0.f;
+    for (int64_t b = j0; b < j1; b += kDirT) {
+        __syncthreads();
+        const int64_t j = b + threadIdx.x;
+        if (j < j1) {
+            sh[threadIdx.x] = s32[2 * j];
+            sl[threadIdx.x] = s32[2 * j + 1];
+        } else {
+            sh[threadIdx.x] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+            sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < kDirT; q++) {
+            const float4 a = sh[q], l = sl[q];
+            const float dx = (a.x - hx) + (l.x - xl.x);
+            const float dy = (a.y - hy) + (l.y - xl.y);
+            const float dz = (a.z - hz) + (l.z - xl.z);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
+            const float c = a.w * rcp_approx(r2);
+            px = fmaf(c, dx, px);
+            py = fmaf(c, dy, py);
+            pz = fmaf(c, dz, pz);
+        }
+        two_sum_add(Hx, Lx, px);
+        two_sum_add(Hy, Ly, py);
+        two_sum_add(Hz, Lz, pz);
+    }
+    if (valid) {
+        double* o = part + 3 * ((int64_t)blockIdx.y * nt + t);
+        o[0] = (double)Hx + (double)Lx;
+        o[1] = (double)Hy + (double)Ly;
+        o[2] = (double)Hz + (double)Lz;
+    }
+}
+
+__global__ void k_direct_finish(const double* __restrict__ part, int splits, int64_t nt,
+                                const int64_t* __restrict__ targets, const double4* __restrict__ s64,
+                                double* __restrict__ vel)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double Sx = 0.0, Sy = 0.0, Sz = 0.0;
+    for (int s = 0; s < splits; s++) {
+        const double* o = part + 3 * ((int64_t)s * nt + t);
+        Sx += o[0];
+        Sy += o[1];
+        Sz += o[2];
+    }
+    const double4 x = s64[targets ? targets[t] : t];
+    vel[3 * t] = -kInv4Pi * (x.y * Sz - x.z * Sy);
+    vel[3 * t + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
+    vel[3 * t + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
+}
+
+}  // namespace
+
+int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
+{
+    const int M = nbasis(degree);
+    if (c->ntasks == 0) return STS_OK;
+    const unsigned grid = blocks(c->ntasks, kEvalWarps);
+    phase_begin(c, kPhEval, s);
+    if (precision == STS_FP64) {
+        (k_eval_fp64<<<grid, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p,
+                                                     c->near_off.p, c->near_ent.p, c->prx64.p, M,
+                                                     c->src64.p, c->perm.p, vel), note_launch());
+    } else {
+        const float tau2 = (float)(2.0 * tau);
+        (k_eval_mixed<<<grid, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p,
+                                                      c->near_off.p, c->near_ent.p, c->prx32.p, M,
+                                                      c->src32.p, c->src64.p, c->perm.p, tau2, vel), note_launch());
+    }
+    phase_end(c, kPhEval, s);
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int count_interactions(sts_ctx* c, int degree, cudaStream_t s)
+{
+    STS_CUDA(c->d_stats.reserve(2));
+    STS_CUDA(cudaMemsetAsync(c->d_stats.p, 0, 2 * sizeof(unsigned long long), s));
+    if (c->nleaves > 0)
+        (k_count<<<blocks(c->nleaves, 128), 128, 0, s>>>(c->nleaves, c->leaves.p, c->nd_count.p,
+                                                       c->far_off.p, c->near_off.p, c->near_ent.p,
+                                                       nbasis(degree), c->d_stats.p), note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int direct_sum(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
+               const int64_t* targets, int64_t nt, int precision, double* vel, cudaStream_t s)
+{
+    if (nt == 0) return STS_OK;
+    STS_CUDA(c->dsrc64.reserve(n + 1));
+    STS_CUDA(c->dsrc32.reserve(2 * n + 2));
+    const int64_t ntb = (nt + kDirT - 1) / kDirT;
+    int64_t splits = (4 * 152 + ntb - 1) / ntb;
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, n / 1024)));
+    splits = std::min<int64_t>(splits, 256);
+    const int64_t chunk = ((n + splits - 1) / splits + kDirT - 1) / kDirT * kDirT;
+    splits = (n + chunk - 1) / chunk;
+    if (splits < 1) splits = 1;
+    STS_CUDA(c->dpart.reserve(3 * splits * nt + 3));
+    phase_begin(c, kPhDirect, s);
+    (k_direct_prep<<<blocks(n, 256), 256, 0, s>>>(pos, zeta, area, n, c->dsrc64.p, c->dsrc32.p), note_launch());
+    const dim3 grid((unsigned)ntb, (unsigned)splits);
+    if (precision == STS_FP64)
+        (k_direct_fp64<<<grid, kDirT, 0, s>>>(c->dsrc64.p, n, targets, nt, chunk, c->dpart.p), note_launch());
+    else
+        (k_direct_mixed<<<grid, kDirT, 0, s>>>(c->dsrc32.p, n, targets, nt, chunk, c->dpart.p), note_launch());
+    (k_direct_finish<<<blocks(nt, 256), 256, 0, s>>>(c->dpart.p, (int)splits, nt, targets, c->dsrc64.p, vel), note_launch());
+    phase_end(c, kPhDirect, s);
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+}  // namespace sts

@@ -1,0 +1,264 @@
+// Internal declarations shared by the translation units of libsts (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/sts.h"
+
+namespace sts {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxDegree = 16;
+constexpr int kMaxM = (kMaxDegree + 1) * (kMaxDegree + 2) / 2;  // 153
+constexpr int kMaxLevel = 24;
+
+// Device status word bits (ORed by kernels, read and cleared by sts_status).
+constexpr int kStatusCapacity = 1;
+constexpr int kStatusNonfinite = 2;
+
+// Evaluation tasks: one warp evaluates up to kTaskTargets consecutive targets of a leaf.
+constexpr int kTaskTargets = 32;
+// Source blocks are staged into shared memory kStage entries at a time.
+constexpr int kStage = 128;
+// Upward pass: one CTA folds kUpChunk particles of one cluster into SBB moments.
+constexpr int kUpChunk = 128;
+
+void set_error(const char* fmt, ...);
+// Counts kernel launches of the library (reported by sts_launch_count).
+void note_launch();
+
+// A device buffer that only grows.  reserve() drops the old contents; grow() keeps them.
+// cudaMalloc / cudaFree happen outside any stream capture.
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;  // elements
+    cudaError_t reserve(size_t n)
+    {
+        if (n <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = n + n / 8 + 16;
+        cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    cudaError_t grow(size_t n, size_t keep, cudaStream_t s)
+    {
+        if (n <= cap) return cudaSuccess;
+        size_t want = n + n / 2 + 16;
+        T* q = nullptr;
+        cudaError_t e = cudaMalloc((void**)&q, want * sizeof(T));
+        if (e != cudaSuccess) return e;
+        if (p && keep) {
+            e = cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                return e;
+            }
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                cudaFree(q);
+                return e;
+            }
+        }
+        if (p) cudaFree(p);
+        p = q;
+        cap = want;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+// Reference interpolation data for one degree (host computed, copied to the device).
+struct RefTable {
+    int degree = 0, M = 0;
+    std::vector<double> beta;  // [M,3] barycentric proxy points on the reference simplex
+    std::vector<double> vinv;  // [M,M], vinv[k*M+m] = (V_ref^{-1})[k][m]
+    DevBuf<double> d_beta, d_vinv;
+};
+
+// Far-field list entry as the evaluation kernel reads it: proxy block of cluster `slot`
+// and the offset c_cluster - c_target_leaf rounded to FP32 (mixed precision).
+struct FarEntry {
+    int32_t slot;
+    float dx, dy, dz;
+};
+// Near-field list entry: sorted source range [start, start + count) of a source leaf and
+// the offset c_source_leaf - c_target_leaf rounded to FP32.
+struct NearEntry {
+    int32_t start, count;
+    float dx, dy, dz;
+    int32_t pad[3];
+};
+// Evaluation task: targets [t0, t0 + nt) (sorted slots) of leaf `leaf` (depth-first index).
+struct Task {
+    int32_t leaf, t0, nt, pad;
+};
+
+enum Phase { kPhBuild = 0, kPhSort, kPhLists, kPhPrep, kPhUpward, kPhEval, kPhDirect, kNumPhases };
+
+}  // namespace sts
+
+struct sts_ctx {
+    int device = 0;
+    int* d_status = nullptr;  // device status word
+    int64_t* h_pinned = nullptr;  // small pinned host staging buffer [64]
+
+    // ---- tree over the current positions -------------------------------------------
+    int64_t n = 0;
+    int leaf_size = 0, max_level = 0;
+    bool have_tree = false;
+    sts::DevBuf<double> pos;             // [n,3] copy of the positions (caller order)
+    sts::DevBuf<int32_t> nodeof;         // [n] original index -> deepest node so far
+    sts::DevBuf<uint8_t> digit;          // [n] child digit at the current level
+    sts::DevBuf<int32_t> perm, perm_tmp; // [n] sorted slot -> original index
+    sts::DevBuf<uint32_t> skey, skey_tmp;// [n] sort keys
+    sts::DevBuf<int64_t> scan_tmp;       // scan scratch
+    sts::DevBuf<uint32_t> hist;          // radix histograms
+    sts::DevBuf<int32_t> flags;          // [n + 1] scratch
+    sts::DevBuf<int64_t> offs;           // [n + 1] scratch
+    // node table (level by level, key order within a level)
+    int64_t nnodes = 0, nleaves = 0, deepest = 0;
+    std::vector<int64_t> level_begin;    // first node id of each level, plus the end
+    sts::DevBuf<int32_t> nd_level, nd_parent, nd_first_child, nd_nchild, nd_start, nd_count,
+        nd_leaf;
+    sts::DevBuf<uint64_t> nd_key;
+    sts::DevBuf<double> nd_geom;         // [nodes,13]: v1, v2, v3, c, r
+    sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
+    sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
+    sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)
+    sts::DevBuf<int32_t> counters;       // small device counters
+    sts::DevBuf<int32_t> leaves;         // leaf node ids in depth-first order
+    sts::DevBuf<int32_t> slot_leaf;      // [n] sorted slot -> depth-first leaf index
+
+    // ---- clusters, proxy weights ---------------------------------------------------
+    int64_t nclusters = 0;
+    int up_degree = -1, up_precision = -1;
+    sts::DevBuf<int32_t> cluster_slot;   // per node: cluster index or -1
+    sts::DevBuf<int32_t> cluster_node;   // per cluster: node id
+    sts::DevBuf<int64_t> up_toff;        // [C+1] first upward task of each cluster
+    sts::DevBuf<int2> up_tasks;          // (cluster, chunk start)
+    int64_t n_up_tasks = 0;
+    sts::DevBuf<double> up_part;         // [tasks, M] partial moments
+    sts::DevBuf<double4> prx64;          // [C,M] (proxy point, 2 W)
+    sts::DevBuf<float4> prx32;           // [C,M] (proxy point - c_cluster, 2 W)
+
+    // ---- sorted particle data --------------------------------------------------------
+    sts::DevBuf<double4> src64;          // [n] sorted (x, y, z, 2 w)
+    sts::DevBuf<float4> src32;           // [n] sorted (x - c_leaf, 2 w)
+
+    // ---- interaction lists (per leaf in depth-first order) --------------------------
+    bool have_lists = false;
+    double list_theta = 0.0;
+    int64_t nfar = 0, nnear = 0;
+    sts::DevBuf<int64_t> far_off, near_off;
+    sts::DevBuf<int32_t> far_idx, near_idx;
+    sts::DevBuf<sts::FarEntry> far_ent;
+    sts::DevBuf<sts::NearEntry> near_ent;
+    sts::DevBuf<int32_t> list_cnt;       // [2 * leaves] scratch
+    sts::DevBuf<sts::Task> tasks;
+    int64_t ntasks = 0;
+    int list_degree = -1;                // degree the far entries' slots refer to
+
+    // ---- direct sum scratch ------------------------------------------------------------
+    sts::DevBuf<double4> dsrc64;
+    sts::DevBuf<float4> dsrc32;          // [2n]: hi (x, y, z, 2w), lo (x, y, z, 0)
+    sts::DevBuf<double> dpart;           // [splits, nt, 3]
+
+    // ---- RK4 scratch -------------------------------------------------------------------
+    sts::DevBuf<double> rk_x0, rk_z0, rk_xs, rk_zs, rk_k, rk_ksum;
+
+    // ---- stats and phase timing -------------------------------------------------------
+    sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
+    bool timing = false;
+    cudaEvent_t ev[sts::kNumPhases][2] = {};
+    float phase_ms[sts::kNumPhases] = {};
+    int phase_count[sts::kNumPhases] = {};
+    bool phase_open[sts::kNumPhases] = {};
+
+    std::vector<sts::RefTable*> refs;    // by degree
+    ~sts_ctx();
+};
+
+namespace sts {
+
+// ---- host tables (sts_tables.cu) --------------------------------------------------
+void icosahedron(double V[12][3], int F[20][3], double C[20][3]);
+int build_ref_table(int d, RefTable* t);
+RefTable* get_ref(sts_ctx* ctx, int d);
+
+// ---- scans and sorting (sts_scan.cu) -----------------------------------------------
+// out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total.  scratch: >= scan_scratch(n)
+int64_t scan_scratch(int64_t n);
+void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch,
+                        cudaStream_t s);
+// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.  Result in
+// key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n).
+int64_t radix_hist_size(int64_t n);
+void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* val_tmp,
+                      int64_t n, int bits, uint32_t* hist, int64_t* scan_out,
+                      int64_t* scan_scratch_buf, cudaStream_t s);
+
+// ---- tree and lists (sts_tree.cu) ----------------------------------------------------
+int tree_build(sts_ctx* ctx, const double* pos, int64_t n, int leaf_size, int max_level,
+               cudaStream_t s);
+int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
+
+// ---- sorted sources, clusters, upward pass (sts_upward.cu) --------------------------
+int prepare_sources(sts_ctx* ctx, const double* zeta, const double* area, cudaStream_t s);
+int build_clusters(sts_ctx* ctx, cudaStream_t s);
+int upward_pass(sts_ctx* ctx, int degree, int precision, cudaStream_t s);
+int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
+
+// ---- evaluation (sts_eval.cu) ---------------------------------------------------------
+int evaluate(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
+int count_interactions(sts_ctx* ctx, int degree, cudaStream_t s);
+int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+               int64_t n, const int64_t* targets, int64_t nt, int precision, double* vel,
+               cudaStream_t s);
+
+// ---- RK4 (sts_rk4.cu) -----------------------------------------------------------------
+void rk4_stage(const double* x0, const double* z0, const double* k, double cdt, double Omega,
+               double* xs, double* zs, double* ksum, double b, int first, int64_t n,
+               cudaStream_t s);
+void rk4_final(double* x, double* z, const double* x0, const double* z0, const double* ksum,
+               const double* k4, double dt, double Omega, int64_t n, cudaStream_t s);
+
+// ---- phase timing (sts_api.cu) -----------------------------------------------------------
+void phase_begin(sts_ctx* ctx, int ph, cudaStream_t s);
+void phase_end(sts_ctx* ctx, int ph, cudaStream_t s);
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+inline int nbasis(int d) { return (d + 1) * (d + 2) / 2; }
+
+}  // namespace sts
+
+#define STS_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            sts::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                           __FILE__, __LINE__);                                           \
+            return STS_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define STS_LAUNCH_CHECK()                                                                \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) {                                                          \
+            sts::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),    \
+                           __FILE__, __LINE__);                                           \
+            return STS_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)

@@ -1,0 +1,229 @@
+// Host-side tables of the tree code: the icosahedron whose faces are the 20 root
+// triangles (Sec. 3, "Grids on a Sphere"), and per degree d the reference interpolation
+// data of Sec. 3.2 / 3.3.2: approximate Fekete points on the reference simplex and the
+// inverse of the SBB Vandermonde matrix at those points.
+//
+// Compiled without FMA contraction (-ffp-contract=off): the icosahedron values decide
+// which face owns each particle, so every operation below is a plain IEEE double op in
+// the order written.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sts_internal.cuh"
+
+namespace sts {
+
+namespace {
+
+struct h3 {
+    double x, y, z;
+};
+h3 hmk(double x, double y, double z) { return h3{x, y, z}; }
+h3 hadd(h3 a, h3 b) { return hmk(a.x + b.x, a.y + b.y, a.z + b.z); }
+h3 hsub(h3 a, h3 b) { return hmk(a.x - b.x, a.y - b.y, a.z - b.z); }
+double hdot(h3 a, h3 b) { return (a.x * b.x + a.y * b.y) + a.z * b.z; }
+h3 hcross(h3 a, h3 b)
+{
+    return hmk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+h3 hunit(h3 s)
+{
+    double n = sqrt(hdot(s, s));
+    return hmk(s.x / n, s.y / n, s.z / n);
+}
+
+}  // namespace
+
+// The icosahedron, in the orientation and numbering this library fixes (the paper gives
+// none): vertices are the cyclic families (0, +-1, +-g), (+-1, +-g, 0), (+-g, 0, +-1)
+// (g = golden ratio; families in that order, sign pairs (+,+), (+,-), (-,+), (-,-)) scaled
+// to unit length; faces are the vertex triples at unscaled pairwise squared distance 4,
+// in lexicographic order, each stored counter-clockwise seen from outside; the face
+// centre is the unit vector along the sum of its three vertices.
+void icosahedron(double V[12][3], int F[20][3], double C[20][3])
+{
+    const double g = (1.0 + sqrt(5.0)) / 2.0;
+    const double sgn[4][2] = {{1.0, 1.0}, {1.0, -1.0}, {-1.0, 1.0}, {-1.0, -1.0}};
+    h3 raw[12], u[12];
+    int n = 0;
+    for (int fam = 0; fam < 3; fam++)
+        for (int s = 0; s < 4; s++) {
+            const double a = sgn[s][0], b = sgn[s][1];
+            if (fam == 0)
+                raw[n] = hmk(0.0, a * 1.0, b * g);
+            else if (fam == 1)
+                raw[n] = hmk(a * 1.0, b * g, 0.0);
+            else
+                raw[n] = hmk(a * g, 0.0, b * 1.0);
+            n++;
+        }
+    for (int i = 0; i < 12; i++) {
+        u[i] = hunit(raw[i]);
+        V[i][0] = u[i].x;
+        V[i][1] = u[i].y;
+        V[i][2] = u[i].z;
+    }
+    int nf = 0;
+    for (int i = 0; i < 12; i++)
+        for (int j = i + 1; j < 12; j++)
+            for (int k = j + 1; k < 12; k++) {
+                h3 eij = hsub(raw[i], raw[j]), eik = hsub(raw[i], raw[k]), ejk = hsub(raw[j], raw[k]);
+                if (fabs(hdot(eij, eij) - 4.0) > 1e-9 || fabs(hdot(eik, eik) - 4.0) > 1e-9 ||
+                    fabs(hdot(ejk, ejk) - 4.0) > 1e-9)
+                    continue;
+                const bool ccw = hdot(u[i], hcross(u[j], u[k])) > 0.0;
+                F[nf][0] = i;
+                F[nf][1] = ccw ? j : k;
+                F[nf][2] = ccw ? k : j;
+                nf++;
+            }
+    for (int f = 0; f < 20; f++) {
+        h3 c = hunit(hadd(hadd(u[F[f][0]], u[F[f][1]]), u[F[f][2]]));
+        C[f][0] = c.x;
+        C[f][1] = c.y;
+        C[f][2] = c.z;
+    }
+}
+
+// Bernstein-monomial row of degree d at barycentric b (Sec. 3.2: B_ijk = b1^i b2^j b3^k,
+// i + j + k = d), in the order i = d..0, then j = d - i..0.
+static void sbb_row(int d, const double b[3], double* out)
+{
+    double p[3][kMaxDegree + 1];
+    for (int a = 0; a < 3; a++) {
+        p[a][0] = 1.0;
+        for (int e = 1; e <= d; e++) p[a][e] = p[a][e - 1] * b[a];
+    }
+    int k = 0;
+    for (int i = d; i >= 0; i--)
+        for (int j = d - i; j >= 0; j--) out[k++] = (p[0][i] * p[1][j]) * p[2][d - i - j];
+}
+
+// Approximate Fekete points: greedy column pivoting on the matrix whose columns are the
+// SBB rows of candidate points (the barycentric lattice of resolution 3d, enumerated
+// p = 3d..0, q = 3d - p..0).  At each step the candidate whose column has the largest
+// component orthogonal to the columns already chosen is taken (ties within a relative
+// 1e-9 go to the lowest candidate index).  Implemented with modified Gram-Schmidt on
+// the residual columns.  Then V_ref[m][k] = B_k(beta_m) is inverted by LU with partial
+// pivoting.
+int build_ref_table(int d, RefTable* t)
+{
+    if (d < 1 || d > kMaxDegree) return STS_ERR_ARG;
+    const int M = (d + 1) * (d + 2) / 2, R = 3 * d, K = (R + 1) * (R + 2) / 2;
+    std::vector<double> cand(3 * (size_t)K), res((size_t)K * M), q(M);
+    std::vector<char> taken(K, 0);
+    int c = 0;
+    for (int p = R; p >= 0; p--)
+        for (int qq = R - p; qq >= 0; qq--) {
+            double b[3] = {(double)p / (double)R, (double)qq / (double)R,
+                           (double)(R - p - qq) / (double)R};
+            memcpy(&cand[3 * (size_t)c], b, sizeof(b));
+            sbb_row(d, b, &res[(size_t)c * M]);
+            c++;
+        }
+    t->degree = d;
+    t->M = M;
+    t->beta.assign(3 * (size_t)M, 0.0);
+    for (int s = 0; s < M; s++) {
+        double best = -1.0;
+        std::vector<double> nrm(K, 0.0);
+        for (c = 0; c < K; c++) {
+            if (taken[c]) continue;
+            const double* r = &res[(size_t)c * M];
+            double a = 0.0;
+            for (int k = 0; k < M; k++) a += r[k] * r[k];
+            nrm[c] = a;
+            if (a > best) best = a;
+        }
+        int pick = -1;
+        for (c = 0; c < K; c++)
+            if (!taken[c] && nrm[c] >= best * (1.0 - 1e-9)) {
+                pick = c;
+                break;
+            }
+        if (pick < 0 || !(best > 0.0)) return STS_ERR_ARG;
+        taken[pick] = 1;
+        memcpy(&t->beta[3 * (size_t)s], &cand[3 * (size_t)pick], 3 * sizeof(double));
+        const double inv = 1.0 / sqrt(nrm[pick]);
+        for (int k = 0; k < M; k++) q[k] = res[(size_t)pick * M + k] * inv;
+        for (c = 0; c < K; c++) {
+            if (taken[c]) continue;
+            double* r = &res[(size_t)c * M];
+            double a = 0.0;
+            for (int k = 0; k < M; k++) a += q[k] * r[k];
+            for (int k = 0; k < M; k++) r[k] -= a * q[k];
+        }
+    }
+    // LU with partial pivoting of V, then V^{-1} column by column.
+    std::vector<double> lu((size_t)M * M);
+    std::vector<int> piv(M);
+    for (int m = 0; m < M; m++) sbb_row(d, &t->beta[3 * (size_t)m], &lu[(size_t)m * M]);
+    for (int k = 0; k < M; k++) {
+        int p = k;
+        for (int i = k + 1; i < M; i++)
+            if (fabs(lu[(size_t)i * M + k]) > fabs(lu[(size_t)p * M + k])) p = i;
+        if (lu[(size_t)p * M + k] == 0.0) return STS_ERR_ARG;
+        piv[k] = p;
+        if (p != k)
+            for (int j = 0; j < M; j++) {
+                double tmp = lu[(size_t)k * M + j];
+                lu[(size_t)k * M + j] = lu[(size_t)p * M + j];
+                lu[(size_t)p * M + j] = tmp;
+            }
+        for (int i = k + 1; i < M; i++) {
+            double f = lu[(size_t)i * M + k] / lu[(size_t)k * M + k];
+            lu[(size_t)i * M + k] = f;
+            for (int j = k + 1; j < M; j++) lu[(size_t)i * M + j] -= f * lu[(size_t)k * M + j];
+        }
+    }
+    t->vinv.assign((size_t)M * M, 0.0);
+    std::vector<double> x(M);
+    for (int col = 0; col < M; col++) {
+        for (int i = 0; i < M; i++) x[i] = (i == col) ? 1.0 : 0.0;
+        for (int k = 0; k < M; k++) {
+            double tmp = x[k];
+            x[k] = x[piv[k]];
+            x[piv[k]] = tmp;
+        }
+        for (int i = 0; i < M; i++)
+            for (int j = 0; j < i; j++) x[i] -= lu[(size_t)i * M + j] * x[j];
+        for (int i = M - 1; i >= 0; i--) {
+            for (int j = i + 1; j < M; j++) x[i] -= lu[(size_t)i * M + j] * x[j];
+            x[i] /= lu[(size_t)i * M + i];
+        }
+        for (int k = 0; k < M; k++) t->vinv[(size_t)k * M + col] = x[k];
+    }
+    return STS_OK;
+}
+
+RefTable* get_ref(sts_ctx* ctx, int d)
+{
+    if ((int)ctx->refs.size() <= d) ctx->refs.resize(d + 1, nullptr);
+    if (ctx->refs[d]) return ctx->refs[d];
+    RefTable* t = new RefTable();
+    if (build_ref_table(d, t) != STS_OK) {
+        delete t;
+        set_error("proxy reference table for degree %d failed", d);
+        return nullptr;
+    }
+    if (t->d_beta.reserve(t->beta.size()) != cudaSuccess ||
+        t->d_vinv.reserve(t->vinv.size()) != cudaSuccess ||
+        cudaMemcpy(t->d_beta.p, t->beta.data(), t->beta.size() * sizeof(double),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_vinv.p, t->vinv.data(), t->vinv.size() * sizeof(double),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        t->d_beta.release();
+        t->d_vinv.release();
+        delete t;
+        set_error("uploading the degree-%d proxy table failed", d);
+        return nullptr;
+    }
+    ctx->refs[d] = t;
+    return t;
+}
+
+}  // namespace sts

@@ -1,0 +1,641 @@
+// Icosahedral triangle tree (Sec. 3, "Grids on a Sphere": the 20 faces of an icosahedron,
+// each refined into four children) and the MAC-driven interaction lists of the tree
+// traversal (Sec. 3.4), built on the device.
+//
+// Every floating-point decision here (face of a particle, child digit, MAC) must come out
+// exactly as in an IEEE FP64 evaluation of the same expressions in the same order, so this
+// translation unit is compiled with --fmad=false and spells every FP64 operation on a
+// decision path with a round-to-nearest intrinsic (no contraction, no reassociation).
+//
+// Readings fixed here (the paper gives no orientation, numbering or tie rule):
+//   face      first face f maximising x . C_f over the 20 face centres C_f (the centres'
+//             spherical Voronoi cells are exactly the faces of the regular icosahedron);
+//   children  of (v1, v2, v3), with m_ab = unit(v_a + v_b): 0 = (v1, m12, m31),
+//             1 = (m12, v2, m23), 2 = (m31, m23, v3), 3 = (m12, m23, m31); digit of x is 0
+//             if (m12 x m31) . x >= 0, else 1 if (m23 x m12) . x >= 0, else 2 if
+//             (m31 x m23) . x >= 0, else 3;
+//   split     a triangle with more than N_T particles below the depth limit has children;
+//   geometry  circumcentre c = unit((v2 - v1) x (v3 - v1)), chord radius r = |c - v1|;
+//   MAC       (r_t + r_s) < theta |c_t - c_s| (strict; coincident centres never pass).
+//
+// Build, level by level, with the particles left in their original order:
+//   level 0   face of every particle (warp-aggregated counts); root nodes in face order.
+//   level l   split flags and child-digit normals per node; child digit per particle and
+//             child counts; child nodes numbered in key order (scan); particles move to
+//             their child.  The host reads the number of new nodes once per level.
+//   sort      a stable radix sort by the first slot of each particle's leaf gives the
+//             sorted order (leaves depth first, original order inside a leaf).
+#include <stdio.h>
+
+#include "sts_internal.cuh"
+
+namespace sts {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct g3 {
+    double x, y, z;
+};
+__device__ __forceinline__ g3 gmk(double x, double y, double z) { return g3{x, y, z}; }
+__device__ __forceinline__ g3 gadd(g3 a, g3 b)
+{
+    return gmk(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z));
+}
+__device__ __forceinline__ g3 gsub(g3 a, g3 b)
+{
+    return gmk(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z));
+}
+// (a.x b.x + a.y b.y) + a.z b.z
+__device__ __forceinline__ double gdot(g3 a, g3 b)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+__device__ __forceinline__ g3 gcross(g3 a, g3 b)
+{
+    return gmk(__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)),
+               __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+               __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+// s / |s|, |s| = sqrt of the dot above, three divisions
+__device__ __forceinline__ g3 gunit(g3 s)
+{
+    const double n = __dsqrt_rn(gdot(s, s));
+    return gmk(__ddiv_rn(s.x, n), __ddiv_rn(s.y, n), __ddiv_rn(s.z, n));
+}
+__device__ __forceinline__ g3 gld(const double* p) { return gmk(p[0], p[1], p[2]); }
+__device__ __forceinline__ void gst(double* p, g3 a)
+{
+    p[0] = a.x;
+    p[1] = a.y;
+    p[2] = a.z;
+}
+
+__constant__ double c_fc[20][3];     // face centres
+__constant__ double c_fv[20][3][3];  // face vertices (counter-clockwise seen from outside)
+
+__device__ void node_geometry(double* g, g3 v1, g3 v2, g3 v3)
+{
+    gst(g, v1);
+    gst(g + 3, v2);
+    gst(g + 6, v3);
+    const g3 c = gunit(gcross(gsub(v2, v1), gsub(v3, v1)));
+    gst(g + 9, c);
+    const g3 e = gsub(c, v1);
+    g[12] = __dsqrt_rn(gdot(e, e));
+}
+
+// Warp-aggregated atomicAdd of 1 to ctr[key] (keys may differ across lanes).
+__device__ __forceinline__ void agg_inc(int32_t* ctr, int key, bool active)
+{
+    const unsigned m = __ballot_sync(kFull, active);
+    if (!active) return;
+    const unsigned peers = __match_any_sync(m, key);
+    const int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&ctr[key], __popc(peers));
+}
+
+// ------------------------------------------------------------------------- level 0
+__global__ void k_faces(const double* __restrict__ pos, int64_t n, uint8_t* __restrict__ digit,
+                        int32_t* __restrict__ face_count, int* __restrict__ status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < n;
+    int best = 0;
+    if (active) {
+        const g3 x = gld(pos + 3 * i);
+        if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
+        double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
+#pragma unroll 4
+        for (int f = 1; f < 20; f++) {
+            const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
+            if (d > bd) {
+                bd = d;
+                best = f;
+            }
+        }
+        digit[i] = (uint8_t)best;
+    }
+    agg_inc(face_count, best, active);
+}
+
+// One thread: root nodes for the non-empty faces, in face order.  face_node[f] = node id
+// or -1; counters[0] = number of roots.
+__global__ void k_roots(const int32_t* __restrict__ face_count, int32_t* __restrict__ face_node,
+                        int32_t* level, uint64_t* key, int32_t* parent, int32_t* first_child,
+                        int32_t* nchild, int32_t* start, int32_t* count, int32_t* leaf,
+                        double* geom, int32_t* counters)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int id = 0, acc = 0;
+    for (int f = 0; f < 20; f++) {
+        const int c = face_count[f];
+        if (c == 0) {
+            face_node[f] = -1;
+            continue;
+        }
+        face_node[f] = id;
+        level[id] = 0;
+        key[id] = (uint64_t)f;
+        parent[id] = -1;
+        first_child[id] = -1;
+        nchild[id] = 0;
+        start[id] = acc;
+        count[id] = c;
+        leaf[id] = 0;
+        node_geometry(geom + 13 * (int64_t)id, gmk(c_fv[f][0][0], c_fv[f][0][1], c_fv[f][0][2]),
+                      gmk(c_fv[f][1][0], c_fv[f][1][1], c_fv[f][1][2]),
+                      gmk(c_fv[f][2][0], c_fv[f][2][1], c_fv[f][2][2]));
+        acc += c;
+        id++;
+    }
+    counters[0] = id;
+}
+
+__global__ void k_assign_roots(const uint8_t* __restrict__ digit, int64_t n,
+                               const int32_t* __restrict__ face_node, int32_t* __restrict__ nodeof)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) nodeof[i] = face_node[digit[i]];
+}
+
+// ------------------------------------------------------------------------- level l
+__global__ void k_level_nodes(int32_t lb, int32_t le, int leaf_size, int max_level,
+                              const int32_t* __restrict__ level, const int32_t* __restrict__ count,
+                              const double* __restrict__ geom, int32_t* __restrict__ leaf,
+                              double* __restrict__ norm, int32_t* __restrict__ cc)
+{
+    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= le) return;
+    const bool split = count[p] > leaf_size && level[p] < max_level;
+    leaf[p] = split ? 0 : 1;
+    if (!split) return;
+    const double* g = geom + 13 * (int64_t)p;
+    const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+    const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+    double* nn = norm + 9 * (int64_t)p;
+    gst(nn, gcross(m12, m31));
+    gst(nn + 3, gcross(m23, m12));
+    gst(nn + 6, gcross(m31, m23));
+    cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
+}
+
+__global__ void k_level_particles(int32_t lb, const double* __restrict__ pos, int64_t n,
+                                  const int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
+                                  const double* __restrict__ norm, uint8_t* __restrict__ digit,
+                                  int32_t* __restrict__ cc)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int p = -1, d = 0;
+    bool active = false;
+    if (i < n) {
+        p = nodeof[i];
+        active = p >= lb && leaf[p] == 0;
+    }
+    if (active) {
+        const g3 x = gld(pos + 3 * i);
+        const double* nn = norm + 9 * (int64_t)p;
+        if (gdot(gld(nn), x) >= 0.0)
+            d = 0;
+        else if (gdot(gld(nn + 3), x) >= 0.0)
+            d = 1;
+        else if (gdot(gld(nn + 6), x) >= 0.0)
+            d = 2;
+        else
+            d = 3;
+        digit[i] = (uint8_t)d;
+    }
+    agg_inc(cc, 4 * p + d, active);
+}
+
+__global__ void k_level_nch(int32_t lb, int32_t le, const int32_t* __restrict__ leaf,
+                            const int32_t* __restrict__ cc, int32_t* __restrict__ nch)
+{
+    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= le) return;
+    int c = 0;
+    if (!leaf[p])
+        for (int d = 0; d < 4; d++) c += cc[4 * p + d] > 0;
+    nch[p - lb] = c;
+}
+
+__global__ void k_level_children(int32_t lb, int32_t le, const int64_t* __restrict__ off,
+                                 const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
+                                 int32_t* parent, int32_t* first_child, int32_t* nchild,
+                                 int32_t* start, int32_t* count, int32_t* leaf, double* geom,
+                                 int32_t* __restrict__ child)
+{
+    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= le) return;
+    if (leaf[p]) {
+        first_child[p] = -1;
+        nchild[p] = 0;
+        return;
+    }
+    const double* g = geom + 13 * (int64_t)p;
+    const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+    const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+    const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
+    int32_t id = le + (int32_t)off[p - lb];
+    const int32_t first = id;
+    int32_t st = start[p];
+    const int32_t lv = level[p] + 1;
+    const uint64_t kp = key[p];
+    int nc = 0;
+    for (int d = 0; d < 4; d++) {
+        const int32_t c = cc[4 * p + d];
+        if (c == 0) {
+            child[4 * p + d] = -1;
+            continue;
+        }
+        child[4 * p + d] = id;
+        level[id] = lv;
+        key[id] = kp * 4u + (uint64_t)d;
+        parent[id] = p;
+        first_child[id] = -1;
+        nchild[id] = 0;
+        start[id] = st;
+        count[id] = c;
+        leaf[id] = 0;
+        node_geometry(geom + 13 * (int64_t)id, cv[d][0], cv[d][1], cv[d][2]);
+        st += c;
+        id++;
+        nc++;
+    }
+    first_child[p] = first;
+    nchild[p] = nc;
+}
+
+__global__ void k_level_assign(int32_t lb, int32_t le, int64_t n, const int32_t* __restrict__ leaf,
+                               const int32_t* __restrict__ child, const uint8_t* __restrict__ digit,
+                               int32_t* __restrict__ nodeof)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = nodeof[i];
+    if (p >= lb && p < le && leaf[p] == 0) nodeof[i] = child[4 * p + digit[i]];
+}
+
+// ------------------------------------------------------------------------- sorting
+__global__ void k_sort_keys(const int32_t* __restrict__ nodeof, int64_t n,
+                            const int32_t* __restrict__ start, uint32_t* __restrict__ skey,
+                            int32_t* __restrict__ perm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    skey[i] = (uint32_t)start[nodeof[i]];
+    perm[i] = (int32_t)i;
+}
+
+__global__ void k_leaf_flags(const int32_t* __restrict__ perm, const int32_t* __restrict__ nodeof,
+                             const int32_t* __restrict__ start, int64_t n, int32_t* __restrict__ flags)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    flags[k] = start[nodeof[perm[k]]] == (int32_t)k ? 1 : 0;
+}
+
+__global__ void k_leaf_list(const int32_t* __restrict__ perm, const int32_t* __restrict__ nodeof,
+                            const int32_t* __restrict__ flags, const int64_t* __restrict__ off,
+                            int64_t n, int32_t* __restrict__ leaves, int32_t* __restrict__ slot_leaf)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t li = off[k] + flags[k] - 1;
+    slot_leaf[k] = (int32_t)li;
+    if (flags[k]) leaves[li] = nodeof[perm[k]];
+}
+
+// ------------------------------------------------------------------------- lists
+constexpr int kStack = 128;
+
+__device__ __forceinline__ bool mac(const double* gt, const double* gs, double theta)
+{
+    const g3 e = gsub(gld(gt + 9), gld(gs + 9));
+    const double R = __dsqrt_rn(gdot(e, e));
+    return __dadd_rn(gt[12], gs[12]) < __dmul_rn(theta, R);
+}
+
+// Target-leaf traversal of Sec. 3.4 (PC + PP): from the roots in order; a source node that
+// passes the MAC is far (a cluster, more than N_T particles) or near; one that fails is
+// near if it is a leaf, else its children are visited in digit order.  fill = 0 counts,
+// fill = 1 writes the CSR rows.
+__global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ leaves,
+                        int32_t nroots, double theta, int leaf_size,
+                        const double* __restrict__ geom, const int32_t* __restrict__ leaf,
+                        const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
+                        const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+                        const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ cnt,
+                        const int64_t* __restrict__ far_off, const int64_t* __restrict__ near_off,
+                        int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
+                        FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
+                        int* __restrict__ status)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaves) return;
+    const int32_t t = leaves[L];
+    const double* gt = geom + 13 * (int64_t)t;
+    int32_t stk[kStack];
+    int sp = 0;
+    for (int r = nroots - 1; r >= 0; r--) stk[sp++] = r;
+    int64_t nf = 0, nn = 0;
+    int64_t fo = fill ? far_off[L] : 0, no = fill ? near_off[L] : 0;
+    while (sp > 0) {
+        const int32_t s = stk[--sp];
+        const double* gs = geom + 13 * (int64_t)s;
+        bool is_far = false, is_near = false;
+        if (mac(gt, gs, theta)) {
+            if (count[s] > leaf_size)
+                is_far = true;
+            else
+                is_near = true;
+        } else if (leaf[s]) {
+            is_near = true;
+        } else {
+            const int32_t fc = first_child[s], nc = nchild[s];
+            if (sp + nc > kStack) {
+                atomicOr(status, kStatusCapacity);
+                break;
+            }
+            for (int c = nc - 1; c >= 0; c--) stk[sp++] = fc + c;
+        }
+        if (is_far) {
+            if (fill) {
+                const int64_t q = fo + nf;
+                far_idx[q] = s;
+                FarEntry e;
+                e.slot = cluster_slot[s];
+                e.dx = (float)__dsub_rn(gs[9], gt[9]);
+                e.dy = (float)__dsub_rn(gs[10], gt[10]);
+                e.dz = (float)__dsub_rn(gs[11], gt[11]);
+                far_ent[q] = e;
+            }
+            nf++;
+        } else if (is_near) {
+            if (fill) {
+                const int64_t q = no + nn;
+                near_idx[q] = s;
+                NearEntry e;
+                e.start = start[s];
+                e.count = count[s];
+                e.dx = (float)__dsub_rn(gs[9], gt[9]);
+                e.dy = (float)__dsub_rn(gs[10], gt[10]);
+                e.dz = (float)__dsub_rn(gs[11], gt[11]);
+                e.pad[0] = e.pad[1] = e.pad[2] = 0;
+                near_ent[q] = e;
+            }
+            nn++;
+        }
+    }
+    if (!fill) {
+        cnt[L] = (int32_t)nf;
+        cnt[nleaves + L] = (int32_t)nn;
+    }
+}
+
+__global__ void k_task_count(int64_t nleaves, const int32_t* __restrict__ leaves,
+                             const int32_t* __restrict__ count, int32_t* __restrict__ ntask)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaves) return;
+    ntask[L] = (count[leaves[L]] + kTaskTargets - 1) / kTaskTargets;
+}
+
+__global__ void k_task_fill(int64_t nleaves, const int32_t* __restrict__ leaves,
+                            const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+                            const int64_t* __restrict__ toff, Task* __restrict__ tasks)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaves) return;
+    const int32_t id = leaves[L];
+    const int32_t st = start[id], c = count[id];
+    int64_t q = toff[L];
+    for (int32_t t0 = 0; t0 < c; t0 += kTaskTargets) {
+        Task tk;
+        tk.leaf = (int32_t)L;
+        tk.t0 = st + t0;
+        tk.nt = min(kTaskTargets, c - t0);
+        tk.pad = 0;
+        tasks[q++] = tk;
+    }
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int read_i64(sts_ctx* ctx, const int64_t* dptr, int64_t* out, cudaStream_t s)
+{
+    STS_CUDA(cudaMemcpyAsync(ctx->h_pinned, dptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    *out = ctx->h_pinned[0];
+    return STS_OK;
+}
+
+int read_status(sts_ctx* ctx, cudaStream_t s, int* st)
+{
+    STS_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    *st = (int)((int32_t*)ctx->h_pinned)[0];
+    return STS_OK;
+}
+
+int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
+{
+    STS_CUDA(c->nd_level.grow(need, keep, s));
+    STS_CUDA(c->nd_parent.grow(need, keep, s));
+    STS_CUDA(c->nd_first_child.grow(need, keep, s));
+    STS_CUDA(c->nd_nchild.grow(need, keep, s));
+    STS_CUDA(c->nd_start.grow(need, keep, s));
+    STS_CUDA(c->nd_count.grow(need, keep, s));
+    STS_CUDA(c->nd_leaf.grow(need, keep, s));
+    STS_CUDA(c->nd_key.grow(need, keep, s));
+    STS_CUDA(c->nd_geom.grow(13 * need, 13 * keep, s));
+    STS_CUDA(c->nd_norm.grow(9 * need, 9 * keep, s));
+    STS_CUDA(c->nd_cc.grow(4 * need, 4 * keep, s));
+    STS_CUDA(c->nd_child.grow(4 * need, 4 * keep, s));
+    return STS_OK;
+}
+
+}  // namespace
+
+int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_level, cudaStream_t s)
+{
+    c->have_tree = false;
+    c->have_lists = false;
+    c->up_degree = -1;
+    c->n = n;
+    c->leaf_size = leaf_size;
+    c->max_level = max_level;
+    c->level_begin.clear();
+    c->nnodes = c->nleaves = c->deepest = 0;
+    if (n == 0) {
+        c->level_begin.push_back(0);
+        c->have_tree = true;
+        return STS_OK;
+    }
+    {
+        double V[12][3], C[20][3], FV[20][3][3];
+        int F[20][3];
+        icosahedron(V, F, C);
+        for (int f = 0; f < 20; f++)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) FV[f][a][b] = V[F[f][a]][b];
+        STS_CUDA(cudaMemcpyToSymbolAsync(c_fc, C, sizeof(C), 0, cudaMemcpyHostToDevice, s));
+        STS_CUDA(cudaMemcpyToSymbolAsync(c_fv, FV, sizeof(FV), 0, cudaMemcpyHostToDevice, s));
+    }
+    STS_CUDA(c->pos.reserve(3 * n));
+    STS_CUDA(cudaMemcpyAsync(c->pos.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    STS_CUDA(c->nodeof.reserve(n));
+    STS_CUDA(c->digit.reserve(n));
+    STS_CUDA(c->perm.reserve(n));
+    STS_CUDA(c->perm_tmp.reserve(n));
+    STS_CUDA(c->skey.reserve(n));
+    STS_CUDA(c->skey_tmp.reserve(n));
+    STS_CUDA(c->flags.reserve(n + 1));
+    STS_CUDA(c->offs.reserve(n + 1));
+    STS_CUDA(c->slot_leaf.reserve(n));
+    const int64_t hs = radix_hist_size(n);
+    STS_CUDA(c->hist.reserve(hs));
+    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
+    STS_CUDA(c->counters.reserve(64));
+    if (grow_nodes(c, 20 + 80, 0, s)) return STS_ERR_CUDA;
+
+    const int T = 256;
+    int32_t* face_count = c->counters.p;      // [20]
+    int32_t* face_node = c->counters.p + 32;  // [20]
+    STS_CUDA(cudaMemsetAsync(face_count, 0, 20 * sizeof(int32_t), s));
+    (k_faces<<<blocks(n, T), T, 0, s>>>(c->pos.p, n, c->digit.p, face_count, c->d_status), note_launch());
+    (k_roots<<<1, 32, 0, s>>>(face_count, face_node, c->nd_level.p, c->nd_key.p, c->nd_parent.p,
+                             c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+                             c->nd_leaf.p, c->nd_geom.p, c->flags.p), note_launch());
+    STS_LAUNCH_CHECK();
+    (k_assign_roots<<<blocks(n, T), T, 0, s>>>(c->digit.p, n, face_node, c->nodeof.p), note_launch());
+    int64_t nroots = 0;
+    {
+        // k_roots wrote the root count into flags[0]
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        nroots = ((int32_t*)c->h_pinned)[0];
+        int st = 0;
+        if (read_status(c, s, &st)) return STS_ERR_CUDA;
+        if (st & kStatusNonfinite) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("sts_tree_build: non-finite position");
+            return STS_ERR_NONFINITE;
+        }
+    }
+    int64_t lb = 0, le = nroots;
+    c->level_begin.push_back(0);
+    int level = 0;
+    while (true) {
+        c->level_begin.push_back(le);
+        const int64_t nl = le - lb;
+        if (grow_nodes(c, le + 4 * nl, le, s)) return STS_ERR_CUDA;
+        (k_level_nodes<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, leaf_size, max_level,
+                                                   c->nd_level.p, c->nd_count.p, c->nd_geom.p,
+                                                   c->nd_leaf.p, c->nd_norm.p, c->nd_cc.p), note_launch());
+        (k_level_particles<<<blocks(n, T), T, 0, s>>>((int32_t)lb, c->pos.p, n, c->nodeof.p,
+                                                      c->nd_leaf.p, c->nd_norm.p, c->digit.p,
+                                                      c->nd_cc.p), note_launch());
+        (k_level_nch<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, c->nd_leaf.p, c->nd_cc.p,
+                                                c->flags.p), note_launch());
+        exclusive_scan_i32(c->flags.p, c->offs.p, nl, c->scan_tmp.p, s);
+        (k_level_children<<<blocks(nl, T), T, 0, s>>>(
+            (int32_t)lb, (int32_t)le, c->offs.p, c->nd_cc.p, c->nd_level.p, c->nd_key.p,
+            c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+            c->nd_leaf.p, c->nd_geom.p, c->nd_child.p), note_launch());
+        (k_level_assign<<<blocks(n, T), T, 0, s>>>((int32_t)lb, (int32_t)le, n, c->nd_leaf.p,
+                                                  c->nd_child.p, c->digit.p, c->nodeof.p), note_launch());
+        STS_LAUNCH_CHECK();
+        int64_t added = 0;
+        if (read_i64(c, c->offs.p + nl, &added, s)) return STS_ERR_CUDA;
+        if (added == 0) break;
+        lb = le;
+        le += added;
+        level++;
+    }
+    c->nnodes = le;
+    c->deepest = level;
+
+    phase_begin(c, kPhSort, s);
+    (k_sort_keys<<<blocks(n, T), T, 0, s>>>(c->nodeof.p, n, c->nd_start.p, c->skey.p, c->perm.p), note_launch());
+    int bits = 0;
+    while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
+    int64_t* scan_out = c->scan_tmp.p;
+    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
+    radix_sort_pairs(c->skey.p, c->perm.p, c->skey_tmp.p, c->perm_tmp.p, n, bits, c->hist.p,
+                     scan_out, scan_scr, s);
+    (k_leaf_flags<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->nd_start.p, n, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_tmp.p, s);
+    int64_t nleaves = 0;
+    if (read_i64(c, c->offs.p + n, &nleaves, s)) return STS_ERR_CUDA;
+    STS_CUDA(c->leaves.reserve(nleaves));
+    (k_leaf_list<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->flags.p, c->offs.p, n,
+                                           c->leaves.p, c->slot_leaf.p), note_launch());
+    STS_LAUNCH_CHECK();
+    phase_end(c, kPhSort, s);
+    c->nleaves = nleaves;
+    c->have_tree = true;
+    return STS_OK;
+}
+
+int build_lists(sts_ctx* c, double theta, cudaStream_t s)
+{
+    c->have_lists = false;
+    const int64_t L = c->nleaves;
+    const int T = 128;
+    STS_CUDA(c->list_cnt.reserve(2 * L + 2));
+    STS_CUDA(c->far_off.reserve(L + 1));
+    STS_CUDA(c->near_off.reserve(L + 1));
+    STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
+    const int32_t nroots = (int32_t)(c->level_begin.size() > 1 ? c->level_begin[1] : 0);
+    if (L > 0)
+        (k_lists<<<blocks(L, T), T, 0, s>>>(0, L, c->leaves.p, nroots, theta, c->leaf_size,
+                                           c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
+                                           c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
+                                           nullptr, nullptr, nullptr, nullptr, c->d_status), note_launch());
+    exclusive_scan_i32(c->list_cnt.p, c->far_off.p, L, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + L, c->near_off.p, L, c->scan_tmp.p, s);
+    STS_LAUNCH_CHECK();
+    int64_t nfar = 0, nnear = 0;
+    if (read_i64(c, c->far_off.p + L, &nfar, s)) return STS_ERR_CUDA;
+    if (read_i64(c, c->near_off.p + L, &nnear, s)) return STS_ERR_CUDA;
+    int st = 0;
+    if (read_status(c, s, &st)) return STS_ERR_CUDA;
+    if (st & kStatusCapacity) {
+        STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+        set_error("interaction lists: traversal stack overflow");
+        return STS_ERR_CAPACITY;
+    }
+    STS_CUDA(c->far_idx.reserve(nfar + 1));
+    STS_CUDA(c->near_idx.reserve(nnear + 1));
+    STS_CUDA(c->far_ent.reserve(nfar + 1));
+    STS_CUDA(c->near_ent.reserve(nnear + 1));
+    if (L > 0)
+        (k_lists<<<blocks(L, T), T, 0, s>>>(1, L, c->leaves.p, nroots, theta, c->leaf_size,
+                                           c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
+                                           c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+                                           c->cluster_slot.p, nullptr, c->far_off.p, c->near_off.p,
+                                           c->far_idx.p, c->near_idx.p, c->far_ent.p,
+                                           c->near_ent.p, c->d_status), note_launch());
+    // evaluation tasks: each leaf's targets in chunks of kTaskTargets
+    STS_CUDA(c->flags.reserve(L + 1));
+    STS_CUDA(c->offs.reserve(L + 1));
+    if (L > 0) (k_task_count<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s);
+    int64_t ntasks = 0;
+    if (read_i64(c, c->offs.p + L, &ntasks, s)) return STS_ERR_CUDA;
+    STS_CUDA(c->tasks.reserve(ntasks + 1));
+    if (L > 0)
+        (k_task_fill<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_start.p, c->nd_count.p,
+                                               c->offs.p, c->tasks.p), note_launch());
+    STS_LAUNCH_CHECK();
+    c->nfar = nfar;
+    c->nnear = nnear;
+    c->ntasks = ntasks;
+    c->list_theta = theta;
+    c->have_lists = true;
+    return STS_OK;
+}
+
+}  // namespace sts

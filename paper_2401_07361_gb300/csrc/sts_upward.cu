@@ -1,0 +1,274 @@
+// Sorted source data and the upward pass of the tree code (Sec. 3.3.2, PC interaction):
+// for every cluster (a triangle holding more than N_T particles) the SBB moments
+//     omega_k = sum_j B_k(b(y_j)) w_j,   B_k(b) = b1^a b2^b b3^c,  a + b + c = d,
+// with b(y) the spherical barycentric coordinates of y in the triangle (y = b1 v1 + b2 v2 +
+// b3 v3), are folded into proxy-point weights
+//     W_m = rho_m^d sum_k (V_ref^{-1})[k][m] omega_k,   y~_m = unit(sum_i beta_mi v_i),
+//     rho_m = |sum_i beta_mi v_i|,
+// so that the PC interaction sum_k alpha_k(x) omega_k of Sec. 3.3.2 equals
+// sum_m G(x, y~_m) W_m for every target x (V_s = diag(rho^-d) V_ref because B_k is
+// homogeneous of degree d and b(y~_m) = beta_m / rho_m).
+//
+// Moments: one CTA per (cluster, 128-particle chunk).  Each thread tabulates the powers
+// b^0..b^d of its particle in shared memory; thread k then sums w_j B_k(b_j) over the chunk.
+// The mixed path computes b = b(c) + T^{-1} (y - c) in FP32 from the FP64 offset y - c to
+// the cluster centre c, so b keeps FP32 relative accuracy however small the triangle.
+// Weights: one CTA per cluster sums the chunk partials in FP64 in a fixed order and applies
+// V_ref^{-1} in FP64.  The SBB monomial basis is badly conditioned (cond(V_ref) ~ 3.5e5 at
+// d = 8), so this contraction stays in FP64: rounding it to FP32 (or TF32) would put errors
+// of eps * |V_ref^{-1}| |omega| into W.  Rounding the moments themselves to FP32 is benign:
+// it perturbs W only along directions the interpolant maps back with norm ~1.
+#include "sts_internal.cuh"
+
+namespace sts {
+namespace {
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Sorted copies: src64[k] = (x, y, z, 2 zeta A) of particle perm[k]; src32[k] = the same
+// relative to the circumcentre of its leaf, rounded to FP32.
+__global__ void k_prepare(const double* __restrict__ pos, const double* __restrict__ zeta,
+                          const double* __restrict__ area, const int32_t* __restrict__ perm,
+                          const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
+                          const double* __restrict__ geom, int64_t n, double4* __restrict__ src64,
+                          float4* __restrict__ src32)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t i = perm[k];
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    const double w2 = 2.0 * (zeta[i] * area[i]);
+    src64[k] = make_double4(x, y, z, w2);
+    const double* c = geom + 13 * (int64_t)leaves[slot_leaf[k]] + 9;
+    src32[k] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)w2);
+}
+
+__global__ void k_cluster_flags(int64_t nnodes, const int32_t* __restrict__ count, int leaf_size,
+                                int32_t* __restrict__ flags)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnodes) flags[p] = count[p] > leaf_size ? 1 : 0;
+}
+
+__global__ void k_cluster_fill(int64_t nnodes, const int32_t* __restrict__ flags,
+                               const int64_t* __restrict__ off, const int32_t* __restrict__ count,
+                               int32_t* __restrict__ slot, int32_t* __restrict__ cnode,
+                               int32_t* __restrict__ nchunk)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnodes) return;
+    if (flags[p]) {
+        const int64_t c = off[p];
+        slot[p] = (int32_t)c;
+        cnode[c] = (int32_t)p;
+        nchunk[c] = (count[p] + kUpChunk - 1) / kUpChunk;
+    } else {
+        slot[p] = -1;
+    }
+}
+
+__global__ void k_up_tasks(int64_t nclu, const int64_t* __restrict__ toff, int2* __restrict__ tasks)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclu) return;
+    int32_t j = 0;
+    for (int64_t q = toff[c]; q < toff[c + 1]; q++, j += kUpChunk) tasks[q] = make_int2((int)c, j);
+}
+
+// Exponents (a, b, c) of SBB function k of degree d: a = d..0, then b = d - a..0.
+__device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int& c)
+{
+    int q = 0;
+    while ((q + 1) * (q + 2) / 2 <= k) q++;
+    const int r = k - q * (q + 1) / 2;
+    a = d - q;
+    b = q - r;
+    c = r;
+}
+
+// Moments of one (cluster, chunk) task.  T = float (mixed) or double (FP64).
+template <class T>
+__global__ void __launch_bounds__(kUpChunk)
+k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
+         const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+         const double* __restrict__ geom, const double4* __restrict__ src64, int d, int M,
+         double* __restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* P = reinterpret_cast<T*>(smem_raw);  // [3][d+1][kUpChunk + 1]
+    constexpr int LD = kUpChunk + 1;
+    T* Wt = P + 3 * (d + 1) * LD;           // [kUpChunk]
+    __shared__ double frame[12];            // rows n_i / D (9), b(c) (3)
+
+    const int2 tk = tasks[blockIdx.x];
+    const int32_t node = cnode[tk.x];
+    const double* g = geom + 13 * (int64_t)node;
+    if (threadIdx.x == 0) {
+        const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
+        const double v3x = g[6], v3y = g[7], v3z = g[8];
+        // n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2; D = v1 . n1 (Cramer's rule)
+        double n[9] = {v2y * v3z - v2z * v3y, v2z * v3x - v2x * v3z, v2x * v3y - v2y * v3x,
+                       v3y * v1z - v3z * v1y, v3z * v1x - v3x * v1z, v3x * v1y - v3y * v1x,
+                       v1y * v2z - v1z * v2y, v1z * v2x - v1x * v2z, v1x * v2y - v1y * v2x};
+        const double D = v1x * n[0] + v1y * n[1] + v1z * n[2];
+        for (int q = 0; q < 9; q++) frame[q] = n[q] / D;
+        const double cx = g[9], cy = g[10], cz = g[11];
+        for (int a = 0; a < 3; a++)
+            frame[9 + a] = frame[3 * a] * cx + frame[3 * a + 1] * cy + frame[3 * a + 2] * cz;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int64_t j = (int64_t)start[node] + tk.y + t;
+    const bool valid = tk.y + t < count[node];
+    T b[3] = {T(0), T(0), T(0)};
+    T w = T(0);
+    if (valid) {
+        const double4 y = src64[j];
+        w = T(0.5 * y.w);
+        if (sizeof(T) == sizeof(double)) {
+            for (int a = 0; a < 3; a++)
+                b[a] = T(frame[3 * a] * y.x + frame[3 * a + 1] * y.y + frame[3 * a + 2] * y.z);
+        } else {
+            const float dx = (float)(y.x - g[9]), dy = (float)(y.y - g[10]), dz = (float)(y.z - g[11]);
+            for (int a = 0; a < 3; a++)
+                b[a] = (float)frame[9 + a] + ((float)frame[3 * a] * dx + (float)frame[3 * a + 1] * dy +
+                                              (float)frame[3 * a + 2] * dz);
+        }
+    }
+    for (int a = 0; a < 3; a++) {
+        T p = T(1);
+        P[(a * (d + 1) + 0) * LD + t] = p;
+        for (int e = 1; e <= d; e++) {
+            p = p * b[a];
+            P[(a * (d + 1) + e) * LD + t] = p;
+        }
+    }
+    Wt[t] = w;
+    __syncthreads();
+    const int nv = min(kUpChunk, count[node] - tk.y);
+    for (int k = t; k < M; k += kUpChunk) {
+        int ea, eb, ec;
+        sbb_exponents(d, k, ea, eb, ec);
+        const T* p1 = P + (0 * (d + 1) + ea) * LD;
+        const T* p2 = P + (1 * (d + 1) + eb) * LD;
+        const T* p3 = P + (2 * (d + 1) + ec) * LD;
+        T acc = T(0);
+        for (int q = 0; q < nv; q++) acc += ((p1[q] * p2[q]) * p3[q]) * Wt[q];
+        part[(int64_t)blockIdx.x * M + k] = (double)acc;
+    }
+}
+
+// Proxy points and weights of one cluster (one CTA per cluster).
+__global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __restrict__ toff,
+                           const double* __restrict__ part, const double* __restrict__ geom,
+                           const double* __restrict__ beta, const double* __restrict__ vinv, int d,
+                           int M, double4* __restrict__ prx64, float4* __restrict__ prx32)
+{
+    __shared__ double om[kMaxM];
+    const int c = blockIdx.x;
+    const int64_t q0 = toff[c], q1 = toff[c + 1];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        double s = 0.0;
+        for (int64_t q = q0; q < q1; q++) s += part[q * M + k];
+        om[k] = s;
+    }
+    __syncthreads();
+    const double* g = geom + 13 * (int64_t)cnode[c];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < M; k++) acc += vinv[k * M + m] * om[k];
+        const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
+        const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+        const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+        const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+        const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
+        double rd = 1.0;
+        for (int e = 0; e < d; e++) rd *= rho;
+        const double W2 = 2.0 * (rd * acc);
+        const double yx = sx / rho, yy = sy / rho, yz = sz / rho;
+        prx64[(int64_t)c * M + m] = make_double4(yx, yy, yz, W2);
+        prx32[(int64_t)c * M + m] =
+            make_float4((float)(yx - g[9]), (float)(yy - g[10]), (float)(yz - g[11]), (float)W2);
+    }
+}
+
+}  // namespace
+
+int prepare_sources(sts_ctx* c, const double* zeta, const double* area, cudaStream_t s)
+{
+    const int64_t n = c->n;
+    STS_CUDA(c->src64.reserve(n + 1));
+    STS_CUDA(c->src32.reserve(n + 1));
+    if (n > 0)
+        (k_prepare<<<blocks(n, 256), 256, 0, s>>>(c->pos.p, zeta, area, c->perm.p, c->slot_leaf.p,
+                                                 c->leaves.p, c->nd_geom.p, n, c->src64.p, c->src32.p), note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int build_clusters(sts_ctx* c, cudaStream_t s)
+{
+    const int64_t nn = c->nnodes;
+    STS_CUDA(c->cluster_slot.reserve(nn + 1));
+    STS_CUDA(c->cluster_node.reserve(nn + 1));
+    STS_CUDA(c->flags.reserve(nn + 1));
+    STS_CUDA(c->offs.reserve(nn + 1));
+    STS_CUDA(c->up_toff.reserve(nn + 2));
+    STS_CUDA(c->list_cnt.reserve(nn + 1));
+    STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
+    if (nn > 0) (k_cluster_flags<<<blocks(nn, 256), 256, 0, s>>>(nn, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_tmp.p, s);
+    if (nn > 0)
+        (k_cluster_fill<<<blocks(nn, 256), 256, 0, s>>>(nn, c->flags.p, c->offs.p, c->nd_count.p,
+                                                       c->cluster_slot.p, c->cluster_node.p,
+                                                       c->list_cnt.p), note_launch());
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->offs.p + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    const int64_t nclu = c->h_pinned[0];
+    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nclu, c->scan_tmp.p, s);
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->up_toff.p + nclu, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    const int64_t ntask = c->h_pinned[0];
+    STS_CUDA(c->up_tasks.reserve(ntask + 1));
+    if (nclu > 0) (k_up_tasks<<<blocks(nclu, 256), 256, 0, s>>>(nclu, c->up_toff.p, c->up_tasks.p), note_launch());
+    STS_LAUNCH_CHECK();
+    c->nclusters = nclu;
+    c->n_up_tasks = ntask;
+    return STS_OK;
+}
+
+int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
+{
+    RefTable* ref = get_ref(c, degree);
+    if (!ref) return STS_ERR_CUDA;
+    const int M = ref->M;
+    const int64_t nclu = c->nclusters;
+    STS_CUDA(c->prx64.reserve(nclu * M + 1));
+    STS_CUDA(c->prx32.reserve(nclu * M + 1));
+    STS_CUDA(c->up_part.reserve(c->n_up_tasks * M + 1));
+    if (nclu == 0) return STS_OK;
+    const int LD = kUpChunk + 1;
+    if (precision == STS_FP64) {
+        const size_t sm = (3 * (degree + 1) * LD + kUpChunk) * sizeof(double);
+        STS_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        (k_upward<double><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
+            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->src64.p,
+            degree, M, c->up_part.p), note_launch());
+    } else {
+        const size_t sm = (3 * (degree + 1) * LD + kUpChunk) * sizeof(float);
+        STS_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        (k_upward<float><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
+            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->src64.p,
+            degree, M, c->up_part.p), note_launch());
+    }
+    (k_contract<<<(unsigned)nclu, 64, 0, s>>>(c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p,
+                                             ref->d_beta.p, ref->d_vinv.p, degree, M, c->prx64.p,
+                                             c->prx32.p), note_launch());
+    STS_LAUNCH_CHECK();
+    c->up_degree = degree;
+    c->up_precision = precision;
+    return STS_OK;
+}
+
+}  // namespace sts

@@ -1,0 +1,279 @@
+"""Python binding of the C ABI in ``include/sts.h`` (``libsts.so``), argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device arrays are torch CUDA
+tensors (float64 unless stated, contiguous); host arrays of the export calls are numpy.
+``stream`` is a ``torch.cuda.Stream`` or None for the current stream.  Every non-zero return
+code raises ``StsError`` with the library's message.  There is no fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STS_FP64 = 0
+STS_MIXED = 1
+PHASES = ("build", "sort", "lists", "prep", "upward", "eval", "direct")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class StsError(RuntimeError):
+    pass
+
+
+class sts_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("degree", C.c_int32), ("leaf_size", C.c_int32),
+                ("max_level", C.c_int32), ("precision", C.c_int32), ("near_fp64_tau", C.c_double)]
+
+
+def params(theta=0.7, degree=8, leaf_size=128, max_level=16, precision=STS_MIXED, near_fp64_tau=0.0):
+    return sts_params(float(theta), int(degree), int(leaf_size), int(max_level), int(precision),
+                      float(near_fp64_tau))
+
+
+def load(build_if_needed: bool = True):
+    """Loads ``libsts.so`` (building it first when sources are newer, if allowed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_needed and _build.needs_build():
+            _build.build()
+        if not os.path.exists(path):
+            raise StsError(f"libsts.so is missing ({path}); build it with paper_2401_07361_gb300.build")
+        lib = C.CDLL(path)
+        P, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        PP = C.POINTER(sts_params)
+        sig = {
+            "sts_create": (i32, [C.POINTER(P)]),
+            "sts_destroy": (None, [P]),
+            "sts_last_error": (C.c_char_p, []),
+            "sts_status": (i32, [P, P]),
+            "sts_direct": (i32, [P, P, P, P, i64, i32, P, P]),
+            "sts_direct_targets": (i32, [P, P, P, P, i64, P, i64, i32, P, P]),
+            "sts_tree_build": (i32, [P, P, i64, PP, P]),
+            "sts_velocity": (i32, [P, P, P, PP, P, P]),
+            "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
+            "sts_tree_info": (i32, [P, P, P]),
+            "sts_tree_export": (i32, [P] + [P] * 11 + [P]),
+            "sts_lists_export": (i32, [P, P, P, P, P, P]),
+            "sts_clusters_export": (i32, [P, P, P, P, P]),
+            "sts_proxy_reference": (i32, [i32, P, P]),
+            "sts_stats": (i32, [P, P, P]),
+            "sts_set_timing": (i32, [P, i32]),
+            "sts_phase_times": (i32, [P, P, P, i32]),
+            "sts_launch_count": (i32, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, fn):
+    if rc != 0:
+        msg = load().sts_last_error().decode(errors="replace")
+        raise StsError(f"{fn} returned {rc}: {msg}")
+
+
+def _dev(t, dtype=None, numel=None, name="array"):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise StsError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise StsError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise StsError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise StsError(f"{name} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _host(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ------------------------------------------------------------------------------- context
+def sts_create():
+    h = C.c_void_p()
+    _check(load().sts_create(C.byref(h)), "sts_create")
+    return h
+
+
+def sts_destroy(ctx):
+    if ctx is not None and _lib is not None:
+        _lib.sts_destroy(ctx)
+
+
+def sts_status(ctx, stream=None):
+    _check(load().sts_status(ctx, _stream(stream)), "sts_status")
+
+
+# ------------------------------------------------------------------------------- compute
+def sts_direct(ctx, pos, zeta, area, precision=STS_FP64, vel=None, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+    _check(load().sts_direct(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                             _dev(area, torch.float64, n, "area"), n, int(precision),
+                             _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)), "sts_direct")
+    return vel
+
+
+def sts_direct_targets(ctx, pos, zeta, area, targets, precision=STS_FP64, vel=None, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    nt = targets.numel()
+    if vel is None:
+        vel = torch.empty((nt, 3), dtype=torch.float64, device=pos.device)
+    _check(load().sts_direct_targets(ctx, _dev(pos, torch.float64, 3 * n, "pos"),
+                                     _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                     n, _dev(targets, torch.int64, nt, "targets"), nt, int(precision),
+                                     _dev(vel, torch.float64, 3 * nt, "vel"), _stream(stream)),
+           "sts_direct_targets")
+    return vel
+
+
+def sts_tree_build(ctx, pos, p, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    _check(load().sts_tree_build(ctx, _dev(pos, torch.float64, 3 * n, "pos"), n, C.byref(p), _stream(stream)),
+           "sts_tree_build")
+
+
+def sts_velocity(ctx, zeta, area, p, vel=None, stream=None):
+    import torch
+
+    n = zeta.numel()
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=zeta.device)
+    _check(load().sts_velocity(ctx, _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                               C.byref(p), _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
+           "sts_velocity")
+    return vel
+
+
+def bve_rk4_step(ctx, pos, zeta, area, dt, Omega, p, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    _check(load().bve_rk4_step(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                               _dev(area, torch.float64, n, "area"), n, float(dt), float(Omega), C.byref(p),
+                               _stream(stream)), "bve_rk4_step")
+
+
+# ---------------------------------------------------------------------------- inspection
+def sts_tree_info(ctx, stream=None):
+    a = np.zeros(8, np.int64)
+    _check(load().sts_tree_info(ctx, _host(a), _stream(stream)), "sts_tree_info")
+    keys = ("n", "nodes", "leaves", "depth", "nfar", "nnear", "clusters", "tasks")
+    return {k: int(v) for k, v in zip(keys, a)}
+
+
+def sts_tree_export(ctx, stream=None):
+    inf = sts_tree_info(ctx, stream)
+    n, nn, nl = inf["n"], inf["nodes"], inf["leaves"]
+    out = dict(perm=np.zeros(n, np.int64), level=np.zeros(nn, np.int32), key=np.zeros(nn, np.uint64),
+               parent=np.zeros(nn, np.int32), first_child=np.zeros(nn, np.int32), nchild=np.zeros(nn, np.int32),
+               start=np.zeros(nn, np.int64), count=np.zeros(nn, np.int64), leaf=np.zeros(nn, np.int32),
+               leaves=np.zeros(nl, np.int32), geom=np.zeros((nn, 13)))
+    _check(load().sts_tree_export(ctx, *[_host(out[k]) for k in ("perm", "level", "key", "parent", "first_child",
+                                                                  "nchild", "start", "count", "leaf", "leaves",
+                                                                  "geom")], _stream(stream)), "sts_tree_export")
+    return out
+
+
+def sts_lists_export(ctx, stream=None):
+    inf = sts_tree_info(ctx, stream)
+    nl = inf["leaves"]
+    out = dict(far_off=np.zeros(nl + 1, np.int64), far_idx=np.zeros(inf["nfar"], np.int32),
+               near_off=np.zeros(nl + 1, np.int64), near_idx=np.zeros(inf["nnear"], np.int32))
+    _check(load().sts_lists_export(ctx, _host(out["far_off"]), _host(out["far_idx"]), _host(out["near_off"]),
+                                   _host(out["near_idx"]), _stream(stream)), "sts_lists_export")
+    return out
+
+
+def sts_clusters_export(ctx, degree, stream=None):
+    inf = sts_tree_info(ctx, stream)
+    c = inf["clusters"]
+    M = (degree + 1) * (degree + 2) // 2
+    ids, yt, W = np.zeros(c, np.int32), np.zeros((c, M, 3)), np.zeros((c, M))
+    _check(load().sts_clusters_export(ctx, _host(ids), _host(yt), _host(W), _stream(stream)),
+           "sts_clusters_export")
+    return ids, yt, W
+
+
+def sts_proxy_reference(degree):
+    M = (degree + 1) * (degree + 2) // 2
+    beta, vinv = np.zeros((M, 3)), np.zeros((M, M))
+    _check(load().sts_proxy_reference(int(degree), _host(beta), _host(vinv)), "sts_proxy_reference")
+    return beta, vinv
+
+
+def sts_stats(ctx, stream=None):
+    a = np.zeros(2, np.int64)
+    _check(load().sts_stats(ctx, _host(a), _stream(stream)), "sts_stats")
+    return dict(pc=int(a[0]), pp=int(a[1]))
+
+
+def sts_set_timing(ctx, on=True):
+    _check(load().sts_set_timing(ctx, int(bool(on))), "sts_set_timing")
+
+
+def sts_phase_times(ctx):
+    ms = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), np.int32)
+    _check(load().sts_phase_times(ctx, _host(ms), _host(cnt), len(PHASES)), "sts_phase_times")
+    return {k: (float(m), int(c)) for k, m, c in zip(PHASES, ms, cnt)}
+
+
+def sts_launch_count():
+    a = np.zeros(1, np.int64)
+    _check(load().sts_launch_count(_host(a)), "sts_launch_count")
+    return int(a[0])
+
+
+class Context:
+    """Owns one ``sts_ctx`` (freed on close or garbage collection)."""
+
+    def __init__(self):
+        self.h = sts_create()
+
+    def close(self):
+        if self.h is not None:
+            sts_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

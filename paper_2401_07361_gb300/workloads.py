@@ -118,22 +118,21 @@ def rh_vorticity(pos: np.ndarray, w: float, K: float) -> np.ndarray:
     return 2.0 * w * z + 30.0 * K * z * (x**4 - 6.0 * x**2 * y**2 + y**4)
 
 
-def real_sh_table(pos: np.ndarray, lmax: int):
-    """Orthonormal real spherical harmonics Y_lm at ``pos`` for 0 <= l <= lmax.
-
-    Returns a dict {(l, m): values}, m in [-l, l]; m > 0 uses cos(m lambda), m < 0 uses
-    sin(|m| lambda).  Normalised associated Legendre functions by the standard three-term
-    recurrence in l (no Condon-Shortley phase).
-    """
+def _real_sh_iter(pos: np.ndarray, lmax: int):
+    """Yields ((l, m), values) of the orthonormal real spherical harmonics Y_lm at ``pos``
+    for 0 <= l <= lmax, m in [-l, l]; m > 0 uses cos(m lambda), m < 0 uses sin(|m| lambda).
+    Normalised associated Legendre functions by the standard three-term recurrence in l (no
+    Condon-Shortley phase).  Holds O(1) arrays at a time."""
     pos = np.asarray(pos, dtype=np.float64)
     z = np.clip(pos[:, 2], -1.0, 1.0)
     s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
     lam = np.arctan2(pos[:, 1], pos[:, 0])
-    out = {}
     pmm = np.full_like(z, 1.0 / math.sqrt(4.0 * math.pi))
     for m in range(lmax + 1):
         if m > 0:
             pmm = pmm * math.sqrt((2.0 * m + 1.0) / (2.0 * m)) * s
+        cm = np.cos(m * lam) if m > 0 else None
+        sm = np.sin(m * lam) if m > 0 else None
         plm2, plm1 = None, pmm
         for l in range(m, lmax + 1):
             if l == m:
@@ -147,11 +146,15 @@ def real_sh_table(pos: np.ndarray, lmax: int):
             if l > m:
                 plm2, plm1 = plm1, p
             if m == 0:
-                out[(l, 0)] = p.copy()
+                yield (l, 0), p
             else:
-                out[(l, m)] = math.sqrt(2.0) * p * np.cos(m * lam)
-                out[(l, -m)] = math.sqrt(2.0) * p * np.sin(m * lam)
-    return out
+                yield (l, m), math.sqrt(2.0) * p * cm
+                yield (l, -m), math.sqrt(2.0) * p * sm
+
+
+def real_sh_table(pos: np.ndarray, lmax: int):
+    """Orthonormal real spherical harmonics as a dict {(l, m): values} (small lmax only)."""
+    return {key: val.copy() for key, val in _real_sh_iter(pos, lmax)}
 
 
 def sh_coefficients(lmax: int, seed: int):
@@ -166,11 +169,11 @@ def sh_coefficients(lmax: int, seed: int):
 
 def sh_series_vorticity(pos: np.ndarray, lmax: int, seed: int = 0) -> np.ndarray:
     """Random zero-mean vorticity sum_{l=1..lmax} sum_m c_lm Y_lm with c_lm ~ N(0,1)/l."""
-    Y = real_sh_table(pos, lmax)
     coef = sh_coefficients(lmax, seed)
     zeta = np.zeros(np.asarray(pos).shape[0])
-    for key, c in coef.items():
-        zeta += c * Y[key]
+    for key, y in _real_sh_iter(pos, lmax):
+        if key[0] >= 1:
+            zeta += coef[key] * y
     return zeta
 
 

@@ -1,0 +1,223 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI (``paper_2401_07361_gb300.sts``).
+
+Bars (stated in the method's target): tree, keys, permutation and interaction lists are
+bit-exact; FP64 velocities within 1e-12 relative l2 of the oracle; mixed-precision
+velocities within 1e-6 relative l2 of the FP64 oracle at the same theta, degree and leaf
+size.  Relative l2 is the area-weighted E of Sec. 4.1; the max-norm is
+max_i |v_i - v_ref,i| / max_i |v_ref,i|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2401_07361_gb300 import sts
+from paper_2401_07361_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TREE_FIELDS = ("perm", "level", "key", "parent", "first_child", "nchild", "start", "count", "leaf", "leaves")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = sts.Context()
+    yield c.h
+    c.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t.to("cuda", dtype if dtype is not None else t.dtype)
+
+
+def _clustered(n_cap, n_uni, seed):
+    rng = np.random.default_rng(seed)
+    c = np.array([0.3, -0.5, 0.8])
+    c /= np.linalg.norm(c)
+    p = c + 0.01 * rng.standard_normal((n_cap, 3))
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    return np.vstack([p, W.uniform_points(n_uni, seed + 1)])
+
+
+def _case(name):
+    if name == "rand3000":
+        return W.uniform_points(3000, 21), 16, 16
+    if name == "ico4":
+        return W.icosahedral_points(4), 32, 16
+    if name == "rand20000":
+        return W.uniform_points(20000, 22), 64, 16
+    if name == "leaf1_depth6":
+        return W.uniform_points(5000, 23), 1, 6
+    if name == "clustered":
+        return _clustered(4000, 1000, 24), 24, 16
+    if name == "duplicates":
+        p = W.uniform_points(900, 25)
+        return np.vstack([p, p[:100]]), 8, 16
+    raise KeyError(name)
+
+
+CASES = ["rand3000", "ico4", "rand20000", "leaf1_depth6", "clustered", "duplicates"]
+
+
+def _fields(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n), rng.uniform(0.5, 1.5, n) * (4 * math.pi / n)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_tree_bit_exact(ctx, name):
+    pos, leaf, ml = _case(name)
+    p = sts.params(leaf_size=leaf, max_level=ml)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    g = sts.sts_tree_export(ctx)
+    o = O.Tree(pos, leaf, ml).export()
+    for k in TREE_FIELDS:
+        assert np.array_equal(g[k], o[k]), k
+    assert np.array_equal(g["geom"], o["geom"])  # the FP64 geometry itself, bit for bit
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("theta", [0.5, 0.7, 0.9])
+def test_lists_bit_exact(ctx, name, theta):
+    pos, leaf, ml = _case(name)
+    n = len(pos)
+    zeta, area = _fields(n, 1)
+    p = sts.params(theta=theta, degree=4, leaf_size=leaf, max_level=ml, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    sts.sts_velocity(ctx, dev(zeta), dev(area), p)
+    g = sts.sts_lists_export(ctx)
+    tr = O.Tree(pos, leaf, ml)
+    o = tr.lists(theta)
+    for k in ("far_off", "far_idx", "near_off", "near_idx"):
+        assert np.array_equal(g[k], o[k]), k
+    _, st = tr.velocity(zeta, area, theta, 4, return_stats=True)
+    assert sts.sts_stats(ctx) == st
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("degree", [3, 8])
+def test_velocity_fp64_matches_oracle(ctx, name, degree):
+    pos, leaf, ml = _case(name)
+    n = len(pos)
+    zeta, area = _fields(n, 2)
+    p = sts.params(theta=0.7, degree=degree, leaf_size=leaf, max_level=ml, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    ref = O.Tree(pos, leaf, ml).velocity(zeta, area, 0.7, degree)
+    assert O.rel_l2(v, ref, area) <= 1e-12
+    assert O.rel_max(v, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_velocity_mixed_within_1e6_of_fp64_oracle(ctx, name):
+    pos, leaf, ml = _case(name)
+    n = len(pos)
+    zeta, area = _fields(n, 3)
+    tau = 0.05 * 4 * math.pi / n
+    p = sts.params(theta=0.7, degree=8, leaf_size=leaf, max_level=ml, precision=sts.STS_MIXED, near_fp64_tau=tau)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    ref = O.Tree(pos, leaf, ml).velocity(zeta, area, 0.7, 8)
+    assert O.rel_l2(v, ref, area) <= 1e-6
+    assert O.rel_max(v, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["rand3000", "clustered"])
+def test_proxy_weights_match_oracle(ctx, name):
+    pos, leaf, ml = _case(name)
+    n = len(pos)
+    zeta, area = _fields(n, 4)
+    p = sts.params(theta=0.7, degree=6, leaf_size=leaf, max_level=ml, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    sts.sts_velocity(ctx, dev(zeta), dev(area), p)
+    ids, yt, Wg = sts.sts_clusters_export(ctx, 6)
+    oids, oyt, oW = O.Tree(pos, leaf, ml).clusters(zeta, area, 6)
+    assert np.array_equal(ids, oids)
+    assert np.max(np.abs(yt - oyt)) <= 4e-16
+    assert np.max(np.abs(Wg - oW)) <= 1e-11 * np.max(np.abs(oW))
+
+
+@pytest.mark.parametrize("n", [2, 3, 129, 1000, 4099])
+@pytest.mark.parametrize("prec", [sts.STS_FP64, sts.STS_MIXED])
+def test_direct_matches_oracle(ctx, n, prec):
+    pos = W.uniform_points(n, 30 + n)
+    zeta, area = _fields(n, 5)
+    v = sts.sts_direct(ctx, dev(pos), dev(zeta), dev(area), prec).cpu().numpy()
+    ref = O.direct(pos, zeta, area)
+    tol = 1e-12 if prec == sts.STS_FP64 else 1e-6
+    assert O.rel_l2(v, ref, area) <= tol
+    assert O.rel_max(v, ref) <= 10 * tol
+
+
+def test_direct_duplicates_and_targets(ctx):
+    pos = W.uniform_points(700, 40)
+    pos = np.vstack([pos, pos[:50]])
+    n = len(pos)
+    zeta, area = _fields(n, 6)
+    tg = np.array([0, 5, 749, 700, 3, 3], np.int64)
+    ref = O.direct(pos, zeta, area, targets=tg)
+    for prec, tol in ((sts.STS_FP64, 1e-12), (sts.STS_MIXED, 1e-6)):
+        v = sts.sts_direct_targets(ctx, dev(pos), dev(zeta), dev(area), dev(tg), prec).cpu().numpy()
+        assert np.max(np.abs(v - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_edge_cases(ctx):
+    p = sts.params(precision=sts.STS_FP64)
+    e = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    z0 = torch.zeros(0, dtype=torch.float64, device="cuda")
+    sts.sts_tree_build(ctx, e, p)
+    assert sts.sts_velocity(ctx, z0, z0, p).shape == (0, 3)
+    one = dev(W.uniform_points(1, 1))
+    o1 = torch.ones(1, dtype=torch.float64, device="cuda")
+    sts.sts_tree_build(ctx, one, p)
+    assert torch.all(sts.sts_velocity(ctx, o1, o1, p) == 0)
+    assert torch.all(sts.sts_direct(ctx, one, o1, o1) == 0)
+    two = W.uniform_points(2, 2)
+    z2, a2 = np.array([1.0, -2.0]), np.array([0.3, 0.4])
+    sts.sts_tree_build(ctx, dev(two), p)
+    v = sts.sts_velocity(ctx, dev(z2), dev(a2), p).cpu().numpy()
+    assert np.allclose(v, O.direct(two, z2, a2), rtol=1e-14, atol=0)
+    with pytest.raises(sts.StsError):
+        sts.sts_velocity(ctx, dev(z2), dev(a2), sts.params(theta=1.0))
+    with pytest.raises(sts.StsError):
+        sts.sts_tree_build(ctx, dev(two), sts.params(degree=17))
+    bad = two.copy()
+    bad[1, 0] = np.nan
+    with pytest.raises(sts.StsError):
+        sts.sts_tree_build(ctx, dev(bad), p)
+
+
+def test_velocity_requires_tree():
+    with sts.Context() as c:
+        z = torch.ones(4, dtype=torch.float64, device="cuda")
+        with pytest.raises(sts.StsError, match="no tree"):
+            sts.sts_velocity(c.h, z, z, sts.params())
+
+
+def test_rk4_step_matches_oracle(ctx):
+    pos = W.uniform_points(3000, 50)
+    area = W.equal_areas(3000)
+    zeta = W.rh_vorticity(pos, math.pi / 7, 1.0)
+    p = sts.params(theta=0.7, degree=6, leaf_size=32, precision=sts.STS_FP64)
+    x, z = dev(pos), dev(zeta)
+    sts.bve_rk4_step(ctx, x, z, dev(area), 0.01, 2 * math.pi, p)
+    vel = lambda xx, zz, aa: O.Tree(xx, 32, 16).velocity(zz, aa, 0.7, 6)
+    ox, oz = O.rk4_step(pos, zeta, area, 0.01, 2 * math.pi, vel)
+    assert np.max(np.abs(x.cpu().numpy() - ox)) <= 1e-13
+    assert np.max(np.abs(z.cpu().numpy() - oz)) <= 1e-12 * np.max(np.abs(oz))
+    assert np.max(np.abs(np.linalg.norm(x.cpu().numpy(), axis=1) - 1)) <= 4e-16
+
+
+def test_repeat_calls_are_deterministic(ctx):
+    pos = W.uniform_points(8000, 60)
+    zeta, area = _fields(8000, 7)
+    p = sts.params(theta=0.7, degree=8, leaf_size=64, precision=sts.STS_MIXED, near_fp64_tau=1e-4)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    a = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    sts.sts_tree_build(ctx, dev(pos), p)
+    b = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    assert np.array_equal(a, b)
