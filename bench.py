@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tau-c", type=float, default=0.05,
                     help="near FP64 threshold tau = c * 4 pi / N (half squared chord)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed device steps only (no e2e, FP64 or CPU legs): the command profiled by ncu")
     return ap.parse_args()
 
 
@@ -260,6 +262,15 @@ def main():
     ms_step = total_ms / max(1, args.steps)
     value = ws * n * args.steps / (total_ms / 1e3)
     v_mixed = vel.cpu().numpy().copy()
+    if args.profile:
+        clocks = sampler.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "targets/s", "ms_per_step": ms_step,
+                              "profile": True, "gpu_launches": int(launches), "clocks": clocks,
+                              "phases_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in phases.items() if v[1]},
+                              "interactions_per_step": stats, "tree": info}), flush=True)
+        ctx.close()
+        return 0
 
     # ---- end to end through host buffers ----------------------------------------------
     pos_p = torch.from_numpy(pos_h).pin_memory()
