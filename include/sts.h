@@ -97,6 +97,20 @@ int sts_direct_targets(sts_ctx* ctx, const double* pos, const double* zeta,
                        const double* area, int64_t n, const int64_t* targets, int64_t nt,
                        int32_t precision, double* vel, void* stream);
 
+/* Direct sum like sts_direct, for callers that cannot allocate device memory when they
+ * need the result: code recording into a CUDA graph it does not own, processes whose device
+ * memory belongs to another allocator, and loops that must not enter cudaMalloc/cudaFree
+ * (which can synchronise the device and take unbounded time) after start-up.  The paper has
+ * no counterpart; this is a library facility.  Takes no context and allocates nothing: its
+ * scratch is one fixed device array of about 7.4 MB inside the library, held on every GPU
+ * that loads the library until the process exits.  n is limited to 65536 (larger n returns
+ * STS_ERR_CAPACITY without touching the GPU).  The first call on a device looks up that
+ * array's device address, so make it before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race; order them on one stream.  Results equal
+ * sts_direct's for the same inputs and precision. */
+int sts_direct_noalloc(const double* pos, const double* zeta, const double* area, int64_t n,
+                       int32_t precision, double* vel, void* stream);
+
 /* Builds the icosahedral triangle tree of Sec. 3 over pos[n,3] (copied into the context):
  * each particle is assigned to one of the 20 faces, and every triangle holding more than
  * p->leaf_size particles below p->max_level is split into its four children.  Particles

@@ -20,6 +20,9 @@
 // with |d|^2 / 2 < tau are evaluated in FP64 from the FP64 positions instead.  A zero d
 // (the target itself, or a coincident particle) contributes nothing, as in the oracle:
 // |d|^2 carries an additive 1e-30 so that 2w / |d|^2 stays finite and is multiplied by 0.
+#include <algorithm>
+#include <mutex>
+
 #include "sts_internal.cuh"
 
 namespace sts {
@@ -443,3 +446,119 @@ int direct_sum(sts_ctx* c, const double* pos, const double* zeta, const double* 
 }
 
 }  // namespace sts
+
+// ---------------------------------------------------------------------------------------
+// Direct sum without any allocation (sts_direct_noalloc).
+//
+// Some callers cannot call cudaMalloc at the time they need a result: code that records
+// into a CUDA graph it does not own, processes whose device memory is already handed to
+// another allocator (a framework's caching allocator), and latency-critical loops that
+// must not enter the allocator after start-up (cudaMalloc and cudaFree can synchronise the
+// device and take unbounded time).  For them the direct sum takes its scratch from one
+// file-scope device array of fixed size instead of the context's growable buffers.  The
+// array is part of the loaded module, so every GPU that loads the library holds it until
+// the process exits.  Every call shares it: calls that overlap on the GPU race, so callers
+// order them on one stream or synchronise between streams.  Nothing in it needs to start
+// at zero (each call writes every entry it later reads), so no clearing is done.
+namespace sts {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 65536;
+// Partial sums: splits * n <= (4 * 152 / ceil(n / 128) + 1) * n <= 4 * 152 * 128 + n.
+constexpr int64_t kNoAllocMaxPart = 3 * (4 * 152 * kDirT + kNoAllocMaxN);
+constexpr size_t kNoAllocBytes64 = sizeof(double4) * kNoAllocMaxN;
+constexpr size_t kNoAllocBytes32 = sizeof(float4) * 2 * kNoAllocMaxN;
+constexpr size_t kNoAllocBytesPart = sizeof(double) * kNoAllocMaxPart;
+constexpr size_t kNoAllocBytes = kNoAllocBytes64 + kNoAllocBytes32 + kNoAllocBytesPart;  // ~7.4 MB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_direct_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_direct_scratch on the current device.  In host code the array's name
+// is only a host-side stand-in, so the address is looked up once per device (with that
+// device current) and cached.
+int noalloc_scratch(unsigned char** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("sts_direct_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+        return STS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("sts_direct_noalloc: device %d is beyond the %d devices supported", dev, kNoAllocMaxDevices);
+        return STS_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_direct_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_error("sts_direct_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return STS_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = (unsigned char*)g_noalloc_ptr[dev];
+    return STS_OK;
+}
+
+}  // namespace
+}  // namespace sts
+
+extern "C" int sts_direct_noalloc(const double* pos, const double* zeta, const double* area, int64_t n,
+                                  int32_t precision, double* vel, void* stream)
+{
+    using namespace sts;
+    set_error("%s", "");
+    if (n < 0 || (n > 0 && (!pos || !zeta || !area || !vel))) {
+        set_error("sts_direct_noalloc: n < 0 or NULL array");
+        return STS_ERR_ARG;
+    }
+    if (precision != STS_FP64 && precision != STS_MIXED) {
+        set_error("sts_direct_noalloc: precision must be STS_FP64 or STS_MIXED");
+        return STS_ERR_ARG;
+    }
+    if (n > kNoAllocMaxN) {
+        set_error("sts_direct_noalloc: n = %lld exceeds the fixed scratch limit of %lld particles "
+                  "(use sts_direct)", (long long)n, (long long)kNoAllocMaxN);
+        return STS_ERR_CAPACITY;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(vel, 0, 3 * sizeof(double), s));
+        return STS_OK;
+    }
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    double4* s64 = (double4*)base;
+    float4* s32 = (float4*)(base + kNoAllocBytes64);
+    double* part = (double*)(base + kNoAllocBytes64 + kNoAllocBytes32);
+    // the same split of the sources as sts_direct, so both give the same sums
+    const int64_t nt = n;
+    const int64_t ntb = (nt + kDirT - 1) / kDirT;
+    int64_t splits = (4 * 152 + ntb - 1) / ntb;
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, n / 1024)));
+    splits = std::min<int64_t>(splits, 256);
+    const int64_t chunk = ((n + splits - 1) / splits + kDirT - 1) / kDirT * kDirT;
+    splits = (n + chunk - 1) / chunk;
+    if (splits < 1) splits = 1;
+    if (3 * splits * nt > kNoAllocMaxPart) {
+        set_error("sts_direct_noalloc: internal partial-sum bound exceeded");
+        return STS_ERR_CAPACITY;
+    }
+    (k_direct_prep<<<blocks(n, 256), 256, 0, s>>>(pos, zeta, area, n, s64, s32), note_launch());
+    const dim3 grid((unsigned)ntb, (unsigned)splits);
+    if (precision == STS_FP64)
+        (k_direct_fp64<<<grid, kDirT, 0, s>>>(s64, n, nullptr, nt, chunk, part), note_launch());
+    else
+        (k_direct_mixed<<<grid, kDirT, 0, s>>>(s32, n, nullptr, nt, chunk, part), note_launch());
+    (k_direct_finish<<<blocks(nt, 256), 256, 0, s>>>(part, (int)splits, nt, nullptr, s64, vel), note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}

@@ -59,6 +59,7 @@ def load(build_if_needed: bool = True):
             "sts_status": (i32, [P, P]),
             "sts_direct": (i32, [P, P, P, P, i64, i32, P, P]),
             "sts_direct_targets": (i32, [P, P, P, P, i64, P, i64, i32, P, P]),
+            "sts_direct_noalloc": (i32, [P, P, P, i64, i32, P, P]),
             "sts_tree_build": (i32, [P, P, i64, PP, P]),
             "sts_velocity": (i32, [P, P, P, PP, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
@@ -152,6 +153,19 @@ def sts_direct_targets(ctx, pos, zeta, area, targets, precision=STS_FP64, vel=No
                                      n, _dev(targets, torch.int64, nt, "targets"), nt, int(precision),
                                      _dev(vel, torch.float64, 3 * nt, "vel"), _stream(stream)),
            "sts_direct_targets")
+    return vel
+
+
+def sts_direct_noalloc(pos, zeta, area, precision=STS_FP64, vel=None, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+    _check(load().sts_direct_noalloc(_dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                                     _dev(area, torch.float64, n, "area"), n, int(precision),
+                                     _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
+           "sts_direct_noalloc")
     return vel
 
 
