@@ -140,22 +140,30 @@ def test_proxy_weights_match_oracle(ctx, name):
     assert np.array_equal(ids, oids)
     assert np.max(np.abs(yt - oyt)) <= 4e-16
     # W_m = rho_m^d sum_k Vinv[k][m] omega_k with omega_k = sum_j w_j B_k(b_j).  The two sides
-    # order the sums differently, so each omega_k may differ by the recursive-summation bound
-    # (count + 2d + 16) eps sum_j |w_j B_k(b_j)|, which the contraction carries into W with
-    # weights rho_m^d |Vinv[k][m]| (cond(V_ref) ~ 8e3 at d = 6 makes this >> eps |W_m|).
+    # round omega_k differently in two ways: (1) the order of the sum, bounded by
+    # (count + 2d + 16) eps sum_j |w_j B_k(b_j)|; (2) the barycentric coordinates b = T^-1 y
+    # of Sec. 3.2, whose absolute rounding is ~3 eps |row_i of T^-1| (large for small
+    # triangles), moving B_k by at most d sum_i |db_i| since |dB_k/db_i| <= d inside the
+    # triangle.  The contraction carries both into W with weights rho_m^d |Vinv[k][m]|
+    # (cond(V_ref) ~ 8e3 at d = 6 makes this >> eps |W_m|).
+    d = 6
     ex = tr.export()
-    vinv = O.vref_inverse(6)
-    beta, _ = O.proxy_reference(6)
+    vinv = O.vref_inverse(d)
+    beta, _ = O.proxy_reference(d)
     aw = np.abs(zeta * area)
     eps = np.finfo(float).eps
     for q, node in enumerate(oids):
         v = ex["geom"][node, :9].reshape(3, 3)
         cnt = ex["count"][node]
         idx = ex["perm"][ex["start"][node]:ex["start"][node] + cnt]
-        _, _, om_abs = O.cluster(v.ravel(), 6, pos[idx], aw[idx])
+        _, _, om_abs = O.cluster(v.ravel(), d, pos[idx], aw[idx])
+        rows = np.array([np.cross(v[1], v[2]), np.cross(v[2], v[0]), np.cross(v[0], v[1])])
+        rows /= np.dot(v[0], rows[0])
+        db = 3 * eps * np.linalg.norm(rows, axis=1).sum()
+        dom = (cnt + 2 * d + 16) * eps * np.abs(om_abs) + 2 * d * db * aw[idx].sum()
         rho = np.linalg.norm(beta @ v, axis=1)
-        mag = rho ** 6 * (np.abs(vinv).T @ np.abs(om_abs))
-        assert np.all(np.abs(Wg[q] - oW[q]) <= (cnt + 2 * 6 + 16) * eps * mag), q
+        bound = rho ** d * (np.abs(vinv).T @ dom)
+        assert np.all(np.abs(Wg[q] - oW[q]) <= bound), q
 
 
 @pytest.mark.parametrize("n", [2, 3, 129, 1000, 4099])
