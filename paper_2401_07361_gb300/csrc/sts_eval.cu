@@ -29,8 +29,7 @@ namespace sts {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kEvalWarps = 4;
-constexpr int kPadStage = kStage + 16;
+
 constexpr float kEps = 1e-30f;
 constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
 
@@ -90,173 +89,285 @@ __device__ __forceinline__ void epilogue(double Sx, double Sy, double Sz, int G,
     }
 }
 
+// ------------------------------------------------------------------------ tree tasks
+// Task layout: targets t0 .. t0 + nt - 1 of one leaf; lane j < p = ceil(nt / 2) of phase s
+// (lane = s p + j, s < S) holds targets t0 + 2j and t0 + 2j + 1 and takes the sources
+// s, s + S, s + 2S, ... of every block; lanes beyond S p idle.  Blocks are the task leaf's
+// far entries (M proxy points of a cluster) followed by its near chunks (<= kStage particles
+// of a near leaf).
+constexpr int kEvalWarps = 8;
+constexpr int kEvalWarps64 = 4;
+
+struct BlockDesc {
+    int32_t idx;  // far: cluster slot; near: first sorted slot of the chunk
+    int32_t cnt;  // entries (0: no block)
+    float dx, dy, dz;
+    int32_t kind;  // 0 far, 1 near, 2 near that may hold pairs closer than tau
+};
+
+__device__ __forceinline__ BlockDesc load_desc(int b, int nf, int nbt, const FarEntry* __restrict__ fe,
+                                               const NearEntry* __restrict__ ne, int M, float tau_r)
+{
+    BlockDesc d;
+    d.idx = 0;
+    d.cnt = 0;
+    d.dx = d.dy = d.dz = 0.f;
+    d.kind = 0;
+    if (b >= nbt) return d;
+    if (b < nf) {
+        const FarEntry e = fe[b];
+        d.idx = e.slot;
+        d.cnt = M;
+        d.dx = e.dx;
+        d.dy = e.dy;
+        d.dz = e.dz;
+    } else {
+        const NearEntry e = ne[b - nf];
+        d.idx = e.start;
+        d.cnt = e.count;
+        d.dx = e.dx;
+        d.dy = e.dy;
+        d.dz = e.dz;
+        d.kind = e.gap < tau_r ? 2 : 1;
+    }
+    return d;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void issue_block(const BlockDesc& d, float4* sb, int lane, const float4* __restrict__ prx32,
+                                            const float4* __restrict__ src32, int M)
+{
+    const float4* src = d.kind == 0 ? prx32 + (int64_t)d.idx * M : src32 + d.idx;
+    for (int i = lane; i < d.cnt; i += 32) cp_async16(sb + i, src + i);
+}
+
+// FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
+// goes to corr (sorted order), read back by the owning lane in the epilogue.
+__device__ __noinline__ void close_pair(const double4* __restrict__ src64, int64_t j, int64_t tk,
+                                        double* __restrict__ corr)
+{
+    const double4 y = src64[j];
+    const double4 x = src64[tk];
+    const double dx = y.x - x.x, dy = y.y - x.y, dz = y.z - x.z;
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    if (r2 > 0.0) {
+        const double t = y.w / r2;
+        atomicAdd(corr + 3 * tk, t * dx);
+        atomicAdd(corr + 3 * tk + 1, t * dy);
+        atomicAdd(corr + 3 * tk + 2, t * dz);
+    }
+}
+
+template <bool TEST>
+__device__ __forceinline__ void block_pairs(const float4* sb, int cnt, int ph, int S, float ax, float ay, float az,
+                                            float bx, float by, float bz, float& p0x, float& p0y, float& p0z,
+                                            float& p1x, float& p1y, float& p1z, float tau2, int64_t base,
+                                            int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
+                                            double* __restrict__ corr)
+{
+#pragma unroll 4
+    for (int i = ph; i < cnt; i += S) {
+        const float4 s = sb[i];
+        const float d0x = s.x - ax, d0y = s.y - ay, d0z = s.z - az;
+        const float d1x = s.x - bx, d1y = s.y - by, d1z = s.z - bz;
+        const float r0 = fmaf(d0z, d0z, fmaf(d0y, d0y, fmaf(d0x, d0x, kEps)));
+        const float r1 = fmaf(d1z, d1z, fmaf(d1y, d1y, fmaf(d1x, d1x, kEps)));
+        float c0 = s.w * rcp_approx(r0);
+        float c1 = s.w * rcp_approx(r1);
+        if (TEST) {
+            if (r0 < tau2) {
+                c0 = 0.f;
+                close_pair(src64, base + i, tk0, corr);
+            }
+            if (r1 < tau2) {
+                c1 = 0.f;
+                close_pair(src64, base + i, tk1, corr);
+            }
+        }
+        p0x = fmaf(c0, d0x, p0x);
+        p0y = fmaf(c0, d0y, p0y);
+        p0z = fmaf(c0, d0z, p0z);
+        p1x = fmaf(c1, d1x, p1x);
+        p1y = fmaf(c1, d1y, p1y);
+        p1z = fmaf(c1, d1z, p1z);
+    }
+}
+
 // ------------------------------------------------------------------------ mixed tree
-__global__ void __launch_bounds__(kEvalWarps * 32)
+__global__ void __launch_bounds__(kEvalWarps * 32, 4)
 k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
-             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_off,
+             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
              const float4* __restrict__ src32, const double4* __restrict__ src64,
-             const int32_t* __restrict__ perm, float tau2, double* __restrict__ vel)
+             const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
+             double* __restrict__ vel)
 {
-    __shared__ float4 sbuf[kEvalWarps][kPadStage];
+    __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStage];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
     if (ti >= ntasks) return;
     const Task tk = tasks[ti];
-    const int S = tk.nt <= 8 ? 4 : (tk.nt <= 16 ? 2 : 1);
-    const int G = 32 / S;
-    const int tg = lane & (G - 1), ph = lane / G;
-    const bool valid = tg < tk.nt;
-    const int64_t k = tk.t0 + (valid ? tg : 0);
-    const float4 t4 = src32[k];
-    const double4 x64 = src64[k];
-    const float tx = valid ? t4.x : -1e3f, ty = valid ? t4.y : -1e3f, tz = valid ? t4.z : -1e3f;
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    double ex = 0.0, ey = 0.0, ez = 0.0;
-    float4* sb = sbuf[w];
-    const int step = 4 * S;
-    const float4 dummy = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+    const int p = (tk.nt + 1) >> 1, S = tk.S;
+    const int j = lane % p;
+    const int ph = lane < p * S ? lane / p : (1 << 20);
+    const int64_t tk0 = tk.t0 + 2 * j, tk1 = tk0 + 1;
+    const bool v0 = 2 * j < tk.nt, v1 = 2 * j + 1 < tk.nt;
+    float4 q = src32[v0 ? tk0 : tk.t0];
+    const float t0x = v0 ? q.x : -1e3f, t0y = v0 ? q.y : -1e3f, t0z = v0 ? q.z : -1e3f;
+    q = src32[v1 ? tk1 : tk.t0];
+    const float t1x = v1 ? q.x : -1e3f, t1y = v1 ? q.y : -1e3f, t1z = v1 ? q.z : -1e3f;
+    float h0x = 0.f, h0y = 0.f, h0z = 0.f, l0x = 0.f, l0y = 0.f, l0z = 0.f;
+    float h1x = 0.f, h1y = 0.f, h1z = 0.f, l1x = 0.f, l1y = 0.f, l1z = 0.f;
 
-    // far field: proxy points of well-separated clusters
-    for (int64_t q = far_off[tk.leaf], qe = far_off[tk.leaf + 1]; q < qe; q++) {
-        const FarEntry e = far_ent[q];
-        const float4* P = prx32 + (int64_t)e.slot * M;
-        for (int c0 = 0; c0 < M; c0 += kStage) {
-            const int nb = min(kStage, M - c0);
-            const int nbp = (nb + step - 1) / step * step;
-            __syncwarp();
-            for (int i = lane; i < nbp; i += 32) {
-                float4 v = i < nb ? P[c0 + i] : dummy;
-                v.x += e.dx;
-                v.y += e.dy;
-                v.z += e.dz;
-                sb[i] = v;
-            }
-            __syncwarp();
-            float px = 0.f, py = 0.f, pz = 0.f;
-            for (int i = ph; i < nbp; i += step) {
+    const int64_t fo = far_off[tk.leaf], co = near_coff[tk.leaf];
+    const int nf = (int)(far_off[tk.leaf + 1] - fo);
+    const int nbt = nf + (int)(near_coff[tk.leaf + 1] - co);
+    const FarEntry* fe = far_ent + fo;
+    const NearEntry* ne = near_ent + co;
+
+    BlockDesc cur = load_desc(0, nf, nbt, fe, ne, M, tau_r);
+    BlockDesc nxt = load_desc(1, nf, nbt, fe, ne, M, tau_r);
+    issue_block(cur, sbuf[w][0], lane, prx32, src32, M);
+    cp_commit();
+    for (int b = 0; b < nbt; b++) {
+        issue_block(nxt, sbuf[w][(b + 1) & 1], lane, prx32, src32, M);
+        cp_commit();
+        const BlockDesc nn = load_desc(b + 2, nf, nbt, fe, ne, M, tau_r);
+        cp_wait1();
+        __syncwarp();
+        const float4* sb = sbuf[w][b & 1];
+        // the source offset is folded into the targets: (y + delta) - x = y - (x - delta)
+        const float ax = t0x - cur.dx, ay = t0y - cur.dy, az = t0z - cur.dz;
+        const float bx = t1x - cur.dx, by = t1y - cur.dy, bz = t1z - cur.dz;
+        float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
+        if (cur.kind == 2)
+            block_pairs<true>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
+                              cur.idx, tk0, tk1, src64, corr);
+        else
+            block_pairs<false>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
+                               cur.idx, tk0, tk1, src64, corr);
+        two_sum_add(h0x, l0x, p0x);
+        two_sum_add(h0y, l0y, p0y);
+        two_sum_add(h0z, l0z, p0z);
+        two_sum_add(h1x, l1x, p1x);
+        two_sum_add(h1y, l1y, p1y);
+        two_sum_add(h1z, l1z, p1z);
+        __syncwarp();
+        cur = nxt;
+        nxt = nn;
+    }
+    double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
+                   (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};
+    for (int s2 = 1; s2 < S; s2++) {
+        const int src = (lane + s2 * p) & 31;
 #pragma unroll
-                for (int u = 0; u < 4; u++) pair32(sb[i + u * S], tx, ty, tz, px, py, pz);
-            }
-            two_sum_add(hx, lx, px);
-            two_sum_add(hy, ly, py);
-            two_sum_add(hz, lz, pz);
+        for (int c = 0; c < 6; c++) {
+            const double v = __shfl_sync(kFull, a[c], src);
+            if (lane < p) a[c] += v;
         }
     }
-    // near field: particles of the near leaves; pairs closer than tau in FP64
-    for (int64_t q = near_off[tk.leaf], qe = near_off[tk.leaf + 1]; q < qe; q++) {
-        const NearEntry e = near_ent[q];
-        for (int c0 = 0; c0 < e.count; c0 += kStage) {
-            const int nb = min(kStage, e.count - c0);
-            const int nbp = (nb + step - 1) / step * step;
-            const int64_t base = (int64_t)e.start + c0;
-            __syncwarp();
-            for (int i = lane; i < nbp; i += 32) {
-                float4 v = i < nb ? src32[base + i] : dummy;
-                v.x += e.dx;
-                v.y += e.dy;
-                v.z += e.dz;
-                sb[i] = v;
-            }
-            __syncwarp();
-            float px = 0.f, py = 0.f, pz = 0.f;
-            for (int i = ph; i < nbp; i += step) {
+    __syncwarp();
+    if (lane < p) {
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int ii = i + u * S;
-                    const float4 s = sb[ii];
-                    const float dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
-                    float c = s.w * rcp_approx(r2);
-                    if (r2 < tau2) {
-                        c = 0.f;  // padding slots (ii >= nb) carry w = 0 and are skipped
-                        const double4 y = src64[base + min(ii, nb - 1)];
-                        const double ddx = y.x - x64.x, ddy = y.y - x64.y, ddz = y.z - x64.z;
-                        const double s2 = fma(ddz, ddz, fma(ddy, ddy, ddx * ddx));
-                        if (s2 > 0.0 && ii < nb) {
-                            const double t = y.w / s2;
-                            ex = fma(t, ddx, ex);
-                            ey = fma(t, ddy, ey);
-                            ez = fma(t, ddz, ez);
-                        }
-                    }
-                    px = fmaf(c, dx, px);
-                    py = fmaf(c, dy, py);
-                    pz = fmaf(c, dz, pz);
-                }
+        for (int u = 0; u < 2; u++) {
+            const int64_t t = u == 0 ? tk0 : tk1;
+            if (!(u == 0 ? v0 : v1)) continue;
+            double Sx = a[3 * u], Sy = a[3 * u + 1], Sz = a[3 * u + 2];
+            if (corr) {
+                Sx += __ldcg(corr + 3 * t);
+                Sy += __ldcg(corr + 3 * t + 1);
+                Sz += __ldcg(corr + 3 * t + 2);
             }
-            two_sum_add(hx, lx, px);
-            two_sum_add(hy, ly, py);
-            two_sum_add(hz, lz, pz);
+            const double4 x = src64[t];
+            const int64_t i = perm[t];
+            vel[3 * i] = -kInv4Pi * (x.y * Sz - x.z * Sy);
+            vel[3 * i + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
+            vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
         }
     }
-    const double Sx = ((double)hx + (double)lx) + ex;
-    const double Sy = ((double)hy + (double)ly) + ey;
-    const double Sz = ((double)hz + (double)lz) + ez;
-    epilogue(Sx, Sy, Sz, G, valid && ph == 0, x64.x, x64.y, x64.z, perm[k], vel);
 }
 
 // ------------------------------------------------------------------------ FP64 tree
-__global__ void __launch_bounds__(kEvalWarps * 32)
+__global__ void __launch_bounds__(kEvalWarps64 * 32)
 k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
-            const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_off,
+            const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
             const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
-            const double4* __restrict__ src64, const int32_t* __restrict__ perm,
-            double* __restrict__ vel)
+            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel)
 {
-    __shared__ double4 sbuf[kEvalWarps][kPadStage];
+    __shared__ double4 sbuf[kEvalWarps64][kStage];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
+    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps64 + w;
     if (ti >= ntasks) return;
     const Task tk = tasks[ti];
-    const int S = tk.nt <= 8 ? 4 : (tk.nt <= 16 ? 2 : 1);
-    const int G = 32 / S;
-    const int tg = lane & (G - 1), ph = lane / G;
-    const bool valid = tg < tk.nt;
-    const int64_t k = tk.t0 + (valid ? tg : 0);
-    const double4 x64 = src64[k];
-    const double tx = valid ? x64.x : -1e3, ty = valid ? x64.y : -1e3, tz = valid ? x64.z : -1e3;
-    double ax = 0.0, ay = 0.0, az = 0.0;
+    const int p = (tk.nt + 1) >> 1, S = tk.S;
+    const int j = lane % p;
+    const int ph = lane < p * S ? lane / p : (1 << 20);
+    const int64_t tk0 = tk.t0 + 2 * j, tk1 = tk0 + 1;
+    const bool v0 = 2 * j < tk.nt, v1 = 2 * j + 1 < tk.nt;
+    const double4 x0 = src64[v0 ? tk0 : tk.t0], x1 = src64[v1 ? tk1 : tk.t0];
+    const double ax = v0 ? x0.x : -1e3, ay = v0 ? x0.y : -1e3, az = v0 ? x0.z : -1e3;
+    const double bx = v1 ? x1.x : -1e3, by = v1 ? x1.y : -1e3, bz = v1 ? x1.z : -1e3;
+    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double4* sb = sbuf[w];
-    const int step = 4 * S;
-    const double4 dummy = make_double4(1e3, 1e3, 1e3, 0.0);
-
-    for (int64_t q = far_off[tk.leaf], qe = far_off[tk.leaf + 1]; q < qe; q++) {
-        const double4* P = prx64 + (int64_t)far_ent[q].slot * M;
-        for (int c0 = 0; c0 < M; c0 += kStage) {
-            const int nb = min(kStage, M - c0);
-            const int nbp = (nb + step - 1) / step * step;
-            __syncwarp();
-            for (int i = lane; i < nbp; i += 32) sb[i] = i < nb ? P[c0 + i] : dummy;
-            __syncwarp();
-            for (int i = ph; i < nbp; i += step) {
-#pragma unroll
-                for (int u = 0; u < 4; u++) pair64(sb[i + u * S], tx, ty, tz, ax, ay, az);
-            }
+    const int64_t fo = far_off[tk.leaf], co = near_coff[tk.leaf];
+    const int nf = (int)(far_off[tk.leaf + 1] - fo);
+    const int nbt = nf + (int)(near_coff[tk.leaf + 1] - co);
+    for (int b = 0; b < nbt; b++) {
+        const double4* src;
+        int cnt;
+        if (b < nf) {
+            src = prx64 + (int64_t)far_ent[fo + b].slot * M;
+            cnt = M;
+        } else {
+            const NearEntry e = near_ent[co + b - nf];
+            src = src64 + e.start;
+            cnt = e.count;
+        }
+        __syncwarp();
+        for (int i = lane; i < cnt; i += 32) sb[i] = src[i];
+        __syncwarp();
+#pragma unroll 2
+        for (int i = ph; i < cnt; i += S) {
+            const double4 sv = sb[i];
+            pair64(sv, ax, ay, az, a[0], a[1], a[2]);
+            pair64(sv, bx, by, bz, a[3], a[4], a[5]);
         }
     }
-    for (int64_t q = near_off[tk.leaf], qe = near_off[tk.leaf + 1]; q < qe; q++) {
-        const NearEntry e = near_ent[q];
-        for (int c0 = 0; c0 < e.count; c0 += kStage) {
-            const int nb = min(kStage, e.count - c0);
-            const int nbp = (nb + step - 1) / step * step;
-            const int64_t base = (int64_t)e.start + c0;
-            __syncwarp();
-            for (int i = lane; i < nbp; i += 32) sb[i] = i < nb ? src64[base + i] : dummy;
-            __syncwarp();
-            for (int i = ph; i < nbp; i += step) {
+    for (int s2 = 1; s2 < S; s2++) {
+        const int src = (lane + s2 * p) & 31;
 #pragma unroll
-                for (int u = 0; u < 4; u++) pair64(sb[i + u * S], tx, ty, tz, ax, ay, az);
-            }
+        for (int c = 0; c < 6; c++) {
+            const double v = __shfl_sync(kFull, a[c], src);
+            if (lane < p) a[c] += v;
         }
     }
-    epilogue(ax, ay, az, G, valid && ph == 0, x64.x, x64.y, x64.z, perm[k], vel);
+    if (lane < p) {
+        if (v0) {
+            const int64_t i = perm[tk0];
+            vel[3 * i] = -kInv4Pi * (x0.y * a[2] - x0.z * a[1]);
+            vel[3 * i + 1] = -kInv4Pi * (x0.z * a[0] - x0.x * a[2]);
+            vel[3 * i + 2] = -kInv4Pi * (x0.x * a[1] - x0.y * a[0]);
+        }
+        if (v1) {
+            const int64_t i = perm[tk1];
+            vel[3 * i] = -kInv4Pi * (x1.y * a[5] - x1.z * a[4]);
+            vel[3 * i + 1] = -kInv4Pi * (x1.z * a[3] - x1.x * a[5]);
+            vel[3 * i + 2] = -kInv4Pi * (x1.x * a[4] - x1.y * a[3]);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------ counts
 __global__ void k_count(int64_t nleaves, const int32_t* __restrict__ leaves,
                         const int32_t* __restrict__ count, const int64_t* __restrict__ far_off,
-                        const int64_t* __restrict__ near_off, const NearEntry* __restrict__ near_ent,
+                        const int64_t* __restrict__ near_coff, const NearEntry* __restrict__ near_ent,
                         int M, unsigned long long* __restrict__ stats)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,7 +375,7 @@ __global__ void k_count(int64_t nleaves, const int32_t* __restrict__ leaves,
     const unsigned long long nl = (unsigned long long)count[leaves[L]];
     const unsigned long long pc = nl * (unsigned long long)M * (unsigned long long)(far_off[L + 1] - far_off[L]);
     unsigned long long ns = 0;
-    for (int64_t q = near_off[L]; q < near_off[L + 1]; q++) ns += (unsigned long long)near_ent[q].count;
+    for (int64_t q = near_coff[L]; q < near_coff[L + 1]; q++) ns += (unsigned long long)near_ent[q].count;
     atomicAdd(&stats[0], pc);
     atomicAdd(&stats[1], nl * (ns - 1ull));
 }
@@ -389,19 +500,31 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
 {
     const int M = nbasis(degree);
     if (c->ntasks == 0) return STS_OK;
-    const unsigned grid = blocks(c->ntasks, kEvalWarps);
-    phase_begin(c, kPhEval, s);
     if (precision == STS_FP64) {
-        (k_eval_fp64<<<grid, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p,
-                                                     c->near_off.p, c->near_ent.p, c->prx64.p, M,
-                                                     c->src64.p, c->perm.p, vel), note_launch());
+        phase_begin(c, kPhEval, s);
+        (k_eval_fp64<<<blocks(c->ntasks, kEvalWarps64), kEvalWarps64 * 32, 0, s>>>(
+             c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx64.p, M,
+             c->src64.p, c->perm.p, vel), note_launch());
+        phase_end(c, kPhEval, s);
     } else {
-        const float tau2 = (float)(2.0 * tau);
-        (k_eval_mixed<<<grid, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p,
-                                                      c->near_off.p, c->near_ent.p, c->prx32.p, M,
-                                                      c->src32.p, c->src64.p, c->perm.p, tau2, vel), note_launch());
+        double* corr = nullptr;
+        // |x - y|^2 / 2 <= 2 on the unit sphere: larger tau changes nothing, and the bound keeps
+        // the dummy targets of idle lanes (at distance ~1e3) out of the FP64 path
+        tau = std::min(tau, 2.0);
+        if (tau > 0.0) {
+            STS_CUDA(c->corr.reserve(3 * c->n + 3));
+            STS_CUDA(cudaMemsetAsync(c->corr.p, 0, 3 * c->n * sizeof(double), s));
+            corr = c->corr.p;
+        }
+        // FP32 threshold on |d|^2 and the distance bound below which a near block is tested
+        const float tau2 = corr ? (float)(2.0 * tau) : 0.f;
+        const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
+        phase_begin(c, kPhEval, s);
+        (k_eval_mixed<<<blocks(c->ntasks, kEvalWarps), kEvalWarps * 32, 0, s>>>(
+             c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx32.p, M,
+             c->src32.p, c->src64.p, c->perm.p, tau2, tau_r, corr, vel), note_launch());
+        phase_end(c, kPhEval, s);
     }
-    phase_end(c, kPhEval, s);
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
@@ -412,7 +535,7 @@ int count_interactions(sts_ctx* c, int degree, cudaStream_t s)
     STS_CUDA(cudaMemsetAsync(c->d_stats.p, 0, 2 * sizeof(unsigned long long), s));
     if (c->nleaves > 0)
         (k_count<<<blocks(c->nleaves, 128), 128, 0, s>>>(c->nleaves, c->leaves.p, c->nd_count.p,
-                                                       c->far_off.p, c->near_off.p, c->near_ent.p,
+                                                       c->far_off.p, c->near_coff.p, c->near_ent.p,
                                                        nbasis(degree), c->d_stats.p), note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;

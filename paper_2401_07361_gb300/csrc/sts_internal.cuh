@@ -19,10 +19,12 @@ constexpr int kMaxLevel = 24;
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusNonfinite = 2;
 
-// Evaluation tasks: one warp evaluates up to kTaskTargets consecutive targets of a leaf.
-constexpr int kTaskTargets = 32;
-// Source blocks are staged into shared memory kStage entries at a time.
-constexpr int kStage = 128;
+// Evaluation tasks: one warp evaluates up to kTaskTargets consecutive targets of a leaf, two
+// per lane.
+constexpr int kTaskTargets = 64;
+// Source blocks (a cluster's proxy points, a chunk of a near leaf) hold at most kStage
+// entries, so that one block fits the shared-memory stage; kStage >= the largest M.
+constexpr int kStage = 160;
 // Upward pass: one CTA folds kUpChunk particles of one cluster into SBB moments.
 constexpr int kUpChunk = 128;
 
@@ -93,16 +95,20 @@ struct FarEntry {
     int32_t slot;
     float dx, dy, dz;
 };
-// Near-field list entry: sorted source range [start, start + count) of a source leaf and
-// the offset c_source_leaf - c_target_leaf rounded to FP32.
+// Near-field list entry: a chunk of at most kStage particles [start, start + count) of a
+// source leaf, the offset c_source_leaf - c_target_leaf rounded to FP32, and a lower bound
+// on the chord distance between any point of the target leaf and any of the source leaf
+// (|c_t - c_s| - r_t - r_s, rounded down), which tells whether a pair can fall below tau.
 struct NearEntry {
     int32_t start, count;
     float dx, dy, dz;
-    int32_t pad[3];
+    float gap;
+    int32_t pad[2];
 };
-// Evaluation task: targets [t0, t0 + nt) (sorted slots) of leaf `leaf` (depth-first index).
+// Evaluation task: targets [t0, t0 + nt) (sorted slots) of leaf `leaf` (depth-first index);
+// S lanes share each pair of targets and split the sources between them.
 struct Task {
-    int32_t leaf, t0, nt, pad;
+    int32_t leaf, t0, nt, S;
 };
 
 enum Phase { kPhBuild = 0, kPhSort, kPhLists, kPhPrep, kPhUpward, kPhEval, kPhDirect, kNumPhases };
@@ -138,6 +144,7 @@ struct sts_ctx {
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)
     sts::DevBuf<int32_t> counters;       // small device counters
+    sts::DevBuf<int64_t> small;          // [16] values gathered for one host read
     sts::DevBuf<int32_t> leaves;         // leaf node ids in depth-first order
     sts::DevBuf<int32_t> slot_leaf;      // [n] sorted slot -> depth-first leaf index
 
@@ -161,7 +168,9 @@ struct sts_ctx {
     bool have_lists = false;
     double list_theta = 0.0;
     int64_t nfar = 0, nnear = 0;
-    sts::DevBuf<int64_t> far_off, near_off;
+    sts::DevBuf<int64_t> far_off, near_off, near_coff;  // near_coff: chunk offsets per leaf
+    int64_t nnear_chunks = 0;
+    sts::DevBuf<double> corr;            // [n,3] FP64 close-pair sums (sorted order)
     sts::DevBuf<int32_t> far_idx, near_idx;
     sts::DevBuf<sts::FarEntry> far_ent;
     sts::DevBuf<sts::NearEntry> near_ent;
@@ -213,6 +222,9 @@ void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* v
 int tree_build(sts_ctx* ctx, const double* pos, int64_t n, int leaf_size, int max_level,
                cudaStream_t s);
 int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
+// out[0..3] = *a, *b, *c, *d (0 for NULL), out[4] = status word: one host read for all.
+void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,
+                   const int* status, int64_t* out, cudaStream_t s);
 
 // ---- sorted sources, clusters, upward pass (sts_upward.cu) --------------------------
 int prepare_sources(sts_ctx* ctx, const double* zeta, const double* area, cudaStream_t s);

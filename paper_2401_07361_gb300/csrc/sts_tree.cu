@@ -327,6 +327,7 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
                         const int32_t* __restrict__ start, const int32_t* __restrict__ count,
                         const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ cnt,
                         const int64_t* __restrict__ far_off, const int64_t* __restrict__ near_off,
+                        const int64_t* __restrict__ near_coff,
                         int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
                         FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
                         int* __restrict__ status)
@@ -338,8 +339,8 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
     int32_t stk[kStack];
     int sp = 0;
     for (int r = nroots - 1; r >= 0; r--) stk[sp++] = r;
-    int64_t nf = 0, nn = 0;
-    int64_t fo = fill ? far_off[L] : 0, no = fill ? near_off[L] : 0;
+    int64_t nf = 0, nn = 0, nch = 0;
+    int64_t fo = fill ? far_off[L] : 0, no = fill ? near_off[L] : 0, co = fill ? near_coff[L] : 0;
     while (sp > 0) {
         const int32_t s = stk[--sp];
         const double* gs = geom + 13 * (int64_t)s;
@@ -372,17 +373,25 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
             }
             nf++;
         } else if (is_near) {
+            const int32_t st = start[s], ct = count[s];
             if (fill) {
-                const int64_t q = no + nn;
-                near_idx[q] = s;
+                near_idx[no + nn] = s;
+                const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
+                const double gap = __dsqrt_rn(gdot(e3, e3)) - gt[12] - gs[12];
                 NearEntry e;
-                e.start = start[s];
-                e.count = count[s];
                 e.dx = (float)__dsub_rn(gs[9], gt[9]);
                 e.dy = (float)__dsub_rn(gs[10], gt[10]);
                 e.dz = (float)__dsub_rn(gs[11], gt[11]);
-                e.pad[0] = e.pad[1] = e.pad[2] = 0;
-                near_ent[q] = e;
+                e.gap = __double2float_rd(gap);
+                e.pad[0] = e.pad[1] = 0;
+                for (int32_t c0 = 0; c0 < ct; c0 += kStage) {
+                    e.start = st + c0;
+                    e.count = min(kStage, ct - c0);
+                    near_ent[co + nch] = e;
+                    nch++;
+                }
+            } else {
+                nch += (ct + kStage - 1) / kStage;
             }
             nn++;
         }
@@ -390,7 +399,29 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
     if (!fill) {
         cnt[L] = (int32_t)nf;
         cnt[nleaves + L] = (int32_t)nn;
+        cnt[2 * nleaves + L] = (int32_t)nch;
     }
+}
+
+// Splits a leaf of nt targets into k warp tasks of nearly equal size, two targets per lane
+// and S = floor(32 / pairs) lanes per pair of targets.  k maximises the fraction of useful
+// interactions per warp step, nt S / (64 k) (ties go to the smaller k).
+__device__ int task_split(int nt)
+{
+    const int kmin = max(1, (nt + kTaskTargets - 1) / kTaskTargets);
+    int best = kmin;
+    float be = -1.f;
+    for (int k = kmin; k <= kmin + 3; k++) {
+        const int m = (nt + k - 1) / k;
+        const int p = (m + 1) / 2;
+        const int S = min(32 / p, 32);
+        const float e = (float)nt * (float)S / (64.f * (float)k);
+        if (e > be * (1.f + 1e-6f)) {
+            be = e;
+            best = k;
+        }
+    }
+    return best;
 }
 
 __global__ void k_task_count(int64_t nleaves, const int32_t* __restrict__ leaves,
@@ -398,7 +429,7 @@ __global__ void k_task_count(int64_t nleaves, const int32_t* __restrict__ leaves
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= nleaves) return;
-    ntask[L] = (count[leaves[L]] + kTaskTargets - 1) / kTaskTargets;
+    ntask[L] = task_split(count[leaves[L]]);
 }
 
 __global__ void k_task_fill(int64_t nleaves, const int32_t* __restrict__ leaves,
@@ -409,15 +440,32 @@ __global__ void k_task_fill(int64_t nleaves, const int32_t* __restrict__ leaves,
     if (L >= nleaves) return;
     const int32_t id = leaves[L];
     const int32_t st = start[id], c = count[id];
+    const int k = (int)(toff[L + 1] - toff[L]);
     int64_t q = toff[L];
-    for (int32_t t0 = 0; t0 < c; t0 += kTaskTargets) {
+    int32_t t0 = 0;
+    for (int i = 0; i < k; i++) {
+        const int32_t m = c / k + (i < c % k ? 1 : 0);
         Task tk;
         tk.leaf = (int32_t)L;
         tk.t0 = st + t0;
-        tk.nt = min(kTaskTargets, c - t0);
-        tk.pad = 0;
+        tk.nt = m;
+        tk.S = min(32 / ((m + 1) / 2), 32);
         tasks[q++] = tk;
+        t0 += m;
     }
+}
+
+// Copies up to four device int64 values and the status word into out[0..4] so that the host
+// reads them with one copy.
+__global__ void k_gather(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,
+                         const int* status, int64_t* out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    out[0] = a ? *a : 0;
+    out[1] = b ? *b : 0;
+    out[2] = c ? *c : 0;
+    out[3] = d ? *d : 0;
+    out[4] = *status;
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -456,6 +504,12 @@ int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
 }
 
 }  // namespace
+
+void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d, const int* status,
+                   int64_t* out, cudaStream_t s)
+{
+    (k_gather<<<1, 32, 0, s>>>(a, b, c, d, status, out), note_launch());
+}
 
 int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_level, cudaStream_t s)
 {
@@ -566,14 +620,15 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_
                      scan_out, scan_scr, s);
     (k_leaf_flags<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->nd_start.p, n, c->flags.p), note_launch());
     exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_tmp.p, s);
-    int64_t nleaves = 0;
-    if (read_i64(c, c->offs.p + n, &nleaves, s)) return STS_ERR_CUDA;
-    STS_CUDA(c->leaves.reserve(nleaves));
+    // the leaf count is read back together with the cluster counts (small[8])
+    STS_CUDA(c->small.reserve(16));
+    (k_gather<<<1, 32, 0, s>>>(c->offs.p + n, nullptr, nullptr, nullptr, c->d_status, c->small.p + 8), note_launch());
+    STS_CUDA(c->leaves.reserve(n + 1));
     (k_leaf_list<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->flags.p, c->offs.p, n,
                                            c->leaves.p, c->slot_leaf.p), note_launch());
     STS_LAUNCH_CHECK();
     phase_end(c, kPhSort, s);
-    c->nleaves = nleaves;
+    c->nleaves = -1;  // set by build_clusters
     c->have_tree = true;
     return STS_OK;
 }
@@ -583,26 +638,35 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     c->have_lists = false;
     const int64_t L = c->nleaves;
     const int T = 128;
-    STS_CUDA(c->list_cnt.reserve(2 * L + 2));
+    STS_CUDA(c->list_cnt.reserve(3 * L + 3));
     STS_CUDA(c->far_off.reserve(L + 1));
     STS_CUDA(c->near_off.reserve(L + 1));
+    STS_CUDA(c->near_coff.reserve(L + 1));
     STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
     const int32_t nroots = (int32_t)(c->level_begin.size() > 1 ? c->level_begin[1] : 0);
     if (L > 0)
         (k_lists<<<blocks(L, T), T, 0, s>>>(0, L, c->leaves.p, nroots, theta, c->leaf_size,
                                            c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
                                            c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
+                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr, nullptr,
                                            nullptr, nullptr, nullptr, nullptr, c->d_status), note_launch());
     exclusive_scan_i32(c->list_cnt.p, c->far_off.p, L, c->scan_tmp.p, s);
     exclusive_scan_i32(c->list_cnt.p + L, c->near_off.p, L, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + 2 * L, c->near_coff.p, L, c->scan_tmp.p, s);
+    // evaluation tasks: each leaf's targets in chunks of kTaskTargets
+    STS_CUDA(c->flags.reserve(L + 1));
+    STS_CUDA(c->offs.reserve(L + 1));
+    STS_CUDA(c->small.reserve(16));
+    if (L > 0) (k_task_count<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s);
+    (k_gather<<<1, 32, 0, s>>>(c->far_off.p + L, c->near_off.p + L, c->offs.p + L, c->near_coff.p + L,
+                               c->d_status, c->small.p), note_launch());
     STS_LAUNCH_CHECK();
-    int64_t nfar = 0, nnear = 0;
-    if (read_i64(c, c->far_off.p + L, &nfar, s)) return STS_ERR_CUDA;
-    if (read_i64(c, c->near_off.p + L, &nnear, s)) return STS_ERR_CUDA;
-    int st = 0;
-    if (read_status(c, s, &st)) return STS_ERR_CUDA;
-    if (st & kStatusCapacity) {
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    const int64_t nfar = c->h_pinned[0], nnear = c->h_pinned[1], ntasks = c->h_pinned[2];
+    const int64_t nchunks = c->h_pinned[3];
+    if (c->h_pinned[4] & kStatusCapacity) {
         STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
         set_error("interaction lists: traversal stack overflow");
         return STS_ERR_CAPACITY;
@@ -610,28 +674,22 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     STS_CUDA(c->far_idx.reserve(nfar + 1));
     STS_CUDA(c->near_idx.reserve(nnear + 1));
     STS_CUDA(c->far_ent.reserve(nfar + 1));
-    STS_CUDA(c->near_ent.reserve(nnear + 1));
-    if (L > 0)
+    STS_CUDA(c->near_ent.reserve(nchunks + 1));
+    STS_CUDA(c->tasks.reserve(ntasks + 1));
+    if (L > 0) {
         (k_lists<<<blocks(L, T), T, 0, s>>>(1, L, c->leaves.p, nroots, theta, c->leaf_size,
                                            c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
                                            c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
                                            c->cluster_slot.p, nullptr, c->far_off.p, c->near_off.p,
-                                           c->far_idx.p, c->near_idx.p, c->far_ent.p,
+                                           c->near_coff.p, c->far_idx.p, c->near_idx.p, c->far_ent.p,
                                            c->near_ent.p, c->d_status), note_launch());
-    // evaluation tasks: each leaf's targets in chunks of kTaskTargets
-    STS_CUDA(c->flags.reserve(L + 1));
-    STS_CUDA(c->offs.reserve(L + 1));
-    if (L > 0) (k_task_count<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s);
-    int64_t ntasks = 0;
-    if (read_i64(c, c->offs.p + L, &ntasks, s)) return STS_ERR_CUDA;
-    STS_CUDA(c->tasks.reserve(ntasks + 1));
-    if (L > 0)
         (k_task_fill<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_start.p, c->nd_count.p,
                                                c->offs.p, c->tasks.p), note_launch());
+    }
     STS_LAUNCH_CHECK();
     c->nfar = nfar;
     c->nnear = nnear;
+    c->nnear_chunks = nchunks;
     c->ntasks = ntasks;
     c->list_theta = theta;
     c->have_lists = true;

@@ -61,18 +61,22 @@ __global__ void k_cluster_fill(int64_t nnodes, const int32_t* __restrict__ flags
         const int64_t c = off[p];
         slot[p] = (int32_t)c;
         cnode[c] = (int32_t)p;
-        nchunk[c] = (count[p] + kUpChunk - 1) / kUpChunk;
+        nchunk[p] = (count[p] + kUpChunk - 1) / kUpChunk;
     } else {
         slot[p] = -1;
+        nchunk[p] = 0;
     }
 }
 
-__global__ void k_up_tasks(int64_t nclu, const int64_t* __restrict__ toff, int2* __restrict__ tasks)
+// toff is indexed by node: the tasks of node p are [toff[p], toff[p + 1]) (none unless p is a
+// cluster).
+__global__ void k_up_tasks(int64_t nnodes, const int32_t* __restrict__ slot, const int64_t* __restrict__ toff,
+                           int2* __restrict__ tasks)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nclu) return;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnodes || slot[p] < 0) return;
     int32_t j = 0;
-    for (int64_t q = toff[c]; q < toff[c + 1]; q++, j += kUpChunk) tasks[q] = make_int2((int)c, j);
+    for (int64_t q = toff[p]; q < toff[p + 1]; q++, j += kUpChunk) tasks[q] = make_int2(slot[p], j);
 }
 
 // Exponents (a, b, c) of SBB function k of degree d: a = d..0, then b = d - a..0.
@@ -166,7 +170,7 @@ __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __r
 {
     __shared__ double om[kMaxM];
     const int c = blockIdx.x;
-    const int64_t q0 = toff[c], q1 = toff[c + 1];
+    const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         double s = 0.0;
         for (int64_t q = q0; q < q1; q++) s += part[q * M + k];
@@ -222,16 +226,18 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
         (k_cluster_fill<<<blocks(nn, 256), 256, 0, s>>>(nn, c->flags.p, c->offs.p, c->nd_count.p,
                                                        c->cluster_slot.p, c->cluster_node.p,
                                                        c->list_cnt.p), note_launch());
+    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_tmp.p, s);
+    STS_CUDA(c->small.reserve(16));
+    gather_values(c->offs.p + nn, c->up_toff.p + nn, nullptr, nullptr, c->d_status, c->small.p, s);
     STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->offs.p + nn, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     STS_CUDA(cudaStreamSynchronize(s));
-    const int64_t nclu = c->h_pinned[0];
-    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nclu, c->scan_tmp.p, s);
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->up_toff.p + nclu, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    const int64_t ntask = c->h_pinned[0];
+    const int64_t nclu = c->h_pinned[0], ntask = c->h_pinned[1];
+    c->nleaves = c->h_pinned[8];
     STS_CUDA(c->up_tasks.reserve(ntask + 1));
-    if (nclu > 0) (k_up_tasks<<<blocks(nclu, 256), 256, 0, s>>>(nclu, c->up_toff.p, c->up_tasks.p), note_launch());
+    if (nn > 0)
+        (k_up_tasks<<<blocks(nn, 256), 256, 0, s>>>(nn, c->cluster_slot.p, c->up_toff.p, c->up_tasks.p),
+         note_launch());
     STS_LAUNCH_CHECK();
     c->nclusters = nclu;
     c->n_up_tasks = ntask;

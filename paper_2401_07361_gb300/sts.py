@@ -39,13 +39,14 @@ def params(theta=0.7, degree=8, leaf_size=128, max_level=16, precision=STS_MIXED
 
 
 def load(build_if_needed: bool = True):
-    """Loads ``libsts.so`` (building it first when sources are newer, if allowed)."""
+    """Loads ``libsts.so`` (building it first when sources are newer, if allowed).  The
+    environment variable STS_LIBRARY names another build of the same library to load."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_needed and _build.needs_build():
+        path = os.environ.get("STS_LIBRARY") or _build.LIB
+        if build_if_needed and path == _build.LIB and _build.needs_build():
             _build.build()
         if not os.path.exists(path):
             raise StsError(f"libsts.so is missing ({path}); build it with paper_2401_07361_gb300.build")
