@@ -59,12 +59,12 @@ sts_ctx::~sts_ctx()
     skey.release(); skey_tmp.release(); scan_tmp.release(); hist.release(); flags.release();
     offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
-    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_cc.release(); nd_child.release();
+    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
     counters.release(); small.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
-    cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release();
+    cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
-    near_ent.release(); list_cnt.release(); tasks.release(); dsrc64.release(); dsrc32.release();
+    near_ent.release(); list_cnt.release(); list_po.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
     rk_k.release(); rk_ksum.release(); d_stats.release();
     for (RefTable* t : refs)

@@ -141,6 +141,8 @@ struct sts_ctx {
     sts::DevBuf<uint64_t> nd_key;
     sts::DevBuf<double> nd_geom;         // [nodes,13]: v1, v2, v3, c, r
     sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
+    sts::DevBuf<float4> nd_norm32;       // [nodes,3]: the normals in FP32 + pre-filter margin
+    sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)
     sts::DevBuf<int32_t> counters;       // small device counters
@@ -157,6 +159,7 @@ struct sts_ctx {
     sts::DevBuf<int2> up_tasks;          // (cluster, chunk start)
     int64_t n_up_tasks = 0;
     sts::DevBuf<double> up_part;         // [tasks, M] partial moments
+    sts::DevBuf<double> up_frame;        // [C,12] barycentric frame of each cluster
     sts::DevBuf<double4> prx64;          // [C,M] (proxy point, 2 W)
     sts::DevBuf<float4> prx32;           // [C,M] (proxy point - c_cluster, 2 W)
 
@@ -174,7 +177,8 @@ struct sts_ctx {
     sts::DevBuf<int32_t> far_idx, near_idx;
     sts::DevBuf<sts::FarEntry> far_ent;
     sts::DevBuf<sts::NearEntry> near_ent;
-    sts::DevBuf<int32_t> list_cnt;       // [2 * leaves] scratch
+    sts::DevBuf<int32_t> list_cnt;       // [3 * leaves * roots] scratch
+    sts::DevBuf<int64_t> list_po;        // [3 * (leaves * roots + 1)] per-(leaf, root) offsets
     sts::DevBuf<sts::Task> tasks;
     int64_t ntasks = 0;
     int list_degree = -1;                // degree the far entries' slots refer to

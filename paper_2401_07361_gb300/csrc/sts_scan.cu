@@ -173,8 +173,34 @@ k_radix_scatter(const uint32_t* __restrict__ key, const int32_t* __restrict__ va
 
 int64_t scan_scratch(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
 
+// Whole scan in one block for n <= kScanTile (most per-level and per-leaf scans).
+__global__ void k_scan_single(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
+{
+    __shared__ int64_t sh[kScanThreads / 32];
+    const int64_t base = (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        sum += v[i];
+    }
+    int64_t tot;
+    int64_t run = block_excl_scan<kScanThreads>(sum, sh, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s)
 {
+    if (n <= kScanTile) {
+        (k_scan_single<<<1, kScanThreads, 0, s>>>(in, n, out), note_launch());
+        return;
+    }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb > 0) (k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch), note_launch());
     (k_scan_top<<<1, 1024, 0, s>>>(scratch, nb), note_launch());

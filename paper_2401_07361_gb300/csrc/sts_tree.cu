@@ -73,6 +73,17 @@ __device__ __forceinline__ void gst(double* p, g3 a)
 
 __constant__ double c_fc[20][3];     // face centres
 __constant__ double c_fv[20][3][3];  // face vertices (counter-clockwise seen from outside)
+__constant__ float c_fc32[20][3];    // face centres rounded to FP32 (pre-filter only)
+
+// FP32 pre-filters.  A decision is taken from FP32 values only when the FP32 result is
+// farther from the decision boundary than its worst-case rounding error (inputs rounded to
+// FP32, three products and two sums: below 3.1e-7 times the sum of |products| for points of
+// norm <= 1); otherwise the exact FP64 expression decides.  So every decision equals the
+// FP64 one bit for bit, and FP64 runs only for points within ~1e-6 of a boundary.
+__device__ __forceinline__ float fdot(float ax, float ay, float az, float bx, float by, float bz)
+{
+    return fmaf(az, bz, fmaf(ay, by, ax * bx));
+}
 
 __device__ void node_geometry(double* g, g3 v1, g3 v2, g3 v3)
 {
@@ -105,13 +116,31 @@ __global__ void k_faces(const double* __restrict__ pos, int64_t n, uint8_t* __re
     if (active) {
         const g3 x = gld(pos + 3 * i);
         if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
-        double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
+        const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
+        float b1 = fdot(fx, fy, fz, c_fc32[0][0], c_fc32[0][1], c_fc32[0][2]), b2 = -3.f;
+        int fb = 0;
 #pragma unroll 4
         for (int f = 1; f < 20; f++) {
-            const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
-            if (d > bd) {
-                bd = d;
-                best = f;
+            const float d = fdot(fx, fy, fz, c_fc32[f][0], c_fc32[f][1], c_fc32[f][2]);
+            if (d > b1) {
+                b2 = b1;
+                b1 = d;
+                fb = f;
+            } else if (d > b2) {
+                b2 = d;
+            }
+        }
+        const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+        if (b1 - b2 > 4e-6f * scale) {
+            best = fb;  // the FP32 winner leads by more than twice the FP32 error
+        } else {
+            double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
+            for (int f = 1; f < 20; f++) {
+                const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
+                if (d > bd) {
+                    bd = d;
+                    best = f;
+                }
             }
         }
         digit[i] = (uint8_t)best;
@@ -119,37 +148,38 @@ __global__ void k_faces(const double* __restrict__ pos, int64_t n, uint8_t* __re
     agg_inc(face_count, best, active);
 }
 
-// One thread: root nodes for the non-empty faces, in face order.  face_node[f] = node id
-// or -1; counters[0] = number of roots.
+// Root nodes for the non-empty faces, in face order, one thread per face.  face_node[f] =
+// node id or -1; counters[0] = number of roots.
 __global__ void k_roots(const int32_t* __restrict__ face_count, int32_t* __restrict__ face_node,
                         int32_t* level, uint64_t* key, int32_t* parent, int32_t* first_child,
                         int32_t* nchild, int32_t* start, int32_t* count, int32_t* leaf,
                         double* geom, int32_t* counters)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int f = threadIdx.x;
+    if (blockIdx.x != 0 || f >= 20) return;
     int id = 0, acc = 0;
-    for (int f = 0; f < 20; f++) {
-        const int c = face_count[f];
-        if (c == 0) {
-            face_node[f] = -1;
-            continue;
-        }
-        face_node[f] = id;
-        level[id] = 0;
-        key[id] = (uint64_t)f;
-        parent[id] = -1;
-        first_child[id] = -1;
-        nchild[id] = 0;
-        start[id] = acc;
-        count[id] = c;
-        leaf[id] = 0;
-        node_geometry(geom + 13 * (int64_t)id, gmk(c_fv[f][0][0], c_fv[f][0][1], c_fv[f][0][2]),
-                      gmk(c_fv[f][1][0], c_fv[f][1][1], c_fv[f][1][2]),
-                      gmk(c_fv[f][2][0], c_fv[f][2][1], c_fv[f][2][2]));
-        acc += c;
-        id++;
+    for (int g = 0; g < f; g++) {
+        id += face_count[g] > 0;
+        acc += face_count[g];
     }
-    counters[0] = id;
+    const int c = face_count[f];
+    if (f == 19) counters[0] = id + (c > 0);
+    if (c == 0) {
+        face_node[f] = -1;
+        return;
+    }
+    face_node[f] = id;
+    level[id] = 0;
+    key[id] = (uint64_t)f;
+    parent[id] = -1;
+    first_child[id] = -1;
+    nchild[id] = 0;
+    start[id] = acc;
+    count[id] = c;
+    leaf[id] = 0;
+    node_geometry(geom + 13 * (int64_t)id, gmk(c_fv[f][0][0], c_fv[f][0][1], c_fv[f][0][2]),
+                  gmk(c_fv[f][1][0], c_fv[f][1][1], c_fv[f][1][2]),
+                  gmk(c_fv[f][2][0], c_fv[f][2][1], c_fv[f][2][2]));
 }
 
 __global__ void k_assign_roots(const uint8_t* __restrict__ digit, int64_t n,
@@ -163,7 +193,7 @@ __global__ void k_assign_roots(const uint8_t* __restrict__ digit, int64_t n,
 __global__ void k_level_nodes(int32_t lb, int32_t le, int leaf_size, int max_level,
                               const int32_t* __restrict__ level, const int32_t* __restrict__ count,
                               const double* __restrict__ geom, int32_t* __restrict__ leaf,
-                              double* __restrict__ norm, int32_t* __restrict__ cc)
+                              double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc)
 {
     const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
     if (p >= le) return;
@@ -174,16 +204,19 @@ __global__ void k_level_nodes(int32_t lb, int32_t le, int leaf_size, int max_lev
     const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
     const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
     double* nn = norm + 9 * (int64_t)p;
-    gst(nn, gcross(m12, m31));
-    gst(nn + 3, gcross(m23, m12));
-    gst(nn + 6, gcross(m31, m23));
+    const g3 n3[3] = {gcross(m12, m31), gcross(m23, m12), gcross(m31, m23)};
+    for (int a = 0; a < 3; a++) {
+        gst(nn + 3 * a, n3[a]);
+        const float thr = 1e-6f * (float)(fabs(n3[a].x) + fabs(n3[a].y) + fabs(n3[a].z));
+        norm32[3 * (int64_t)p + a] = make_float4((float)n3[a].x, (float)n3[a].y, (float)n3[a].z, thr);
+    }
     cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
 }
 
 __global__ void k_level_particles(int32_t lb, const double* __restrict__ pos, int64_t n,
                                   const int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
-                                  const double* __restrict__ norm, uint8_t* __restrict__ digit,
-                                  int32_t* __restrict__ cc)
+                                  const double* __restrict__ norm, const float4* __restrict__ norm32,
+                                  uint8_t* __restrict__ digit, int32_t* __restrict__ cc)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int p = -1, d = 0;
@@ -194,15 +227,35 @@ __global__ void k_level_particles(int32_t lb, const double* __restrict__ pos, in
     }
     if (active) {
         const g3 x = gld(pos + 3 * i);
-        const double* nn = norm + 9 * (int64_t)p;
-        if (gdot(gld(nn), x) >= 0.0)
-            d = 0;
-        else if (gdot(gld(nn + 3), x) >= 0.0)
-            d = 1;
-        else if (gdot(gld(nn + 6), x) >= 0.0)
-            d = 2;
-        else
-            d = 3;
+        const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
+        const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+        // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
+        d = -1;
+        for (int a = 0; a < 3; a++) {
+            const float4 q = norm32[3 * (int64_t)p + a];
+            const float t = fdot(q.x, q.y, q.z, fx, fy, fz);
+            const float thr = q.w * scale;
+            if (t > thr) {
+                d = a;
+                break;
+            }
+            if (!(t < -thr)) {
+                d = -2;  // too close to this boundary for FP32
+                break;
+            }
+        }
+        if (d == -1) d = 3;
+        if (d == -2) {
+            const double* nn = norm + 9 * (int64_t)p;
+            if (gdot(gld(nn), x) >= 0.0)
+                d = 0;
+            else if (gdot(gld(nn + 3), x) >= 0.0)
+                d = 1;
+            else if (gdot(gld(nn + 6), x) >= 0.0)
+                d = 2;
+            else
+                d = 3;
+        }
         digit[i] = (uint8_t)d;
     }
     agg_inc(cc, 4 * p + d, active);
@@ -316,36 +369,59 @@ __device__ __forceinline__ bool mac(const double* gt, const double* gs, double t
     return __dadd_rn(gt[12], gs[12]) < __dmul_rn(theta, R);
 }
 
-// Target-leaf traversal of Sec. 3.4 (PC + PP): from the roots in order; a source node that
-// passes the MAC is far (a cluster, more than N_T particles) or near; one that fails is
-// near if it is a leaf, else its children are visited in digit order.  fill = 0 counts,
-// fill = 1 writes the CSR rows.
+// MAC with the FP32 pre-filter: |(r_t + r_s) - theta R| is decided in FP32 when it exceeds
+// the FP32 rounding bound (2.1e-7 + 5e-7 R + 2e-7 (r_t + r_s) for centres of norm 1),
+// otherwise by the exact FP64 expression above.
+__device__ __forceinline__ bool mac_filtered(float4 ct, float4 cs, float theta32, const double* gt,
+                                             const double* gs, double theta)
+{
+    const float ex = ct.x - cs.x, ey = ct.y - cs.y, ez = ct.z - cs.z;
+    const float R = sqrtf(fdot(ex, ey, ez, ex, ey, ez));
+    const float lhs = ct.w + cs.w, rhs = theta32 * R;
+    const float m = 1e-6f * (1.f + lhs + R);
+    if (lhs < rhs - m) return true;
+    if (lhs > rhs + m) return false;
+    return mac(gt, gs, theta);
+}
+
+// Target-leaf traversal of Sec. 3.4 (PC + PP), one thread per (target leaf, root): from the
+// root, a source node that passes the MAC is far (a cluster, more than N_T particles) or
+// near; one that fails is near if it is a leaf, else its children are visited in digit
+// order.  The rows of a leaf are the concatenation of its per-root rows in root order, which
+// is the depth-first order from the 20 roots.  fill = 0 counts far nodes, near nodes and
+// near chunks per (leaf, root); fill = 1 writes them at the scanned pair offsets.
 __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ leaves,
                         int32_t nroots, double theta, int leaf_size,
-                        const double* __restrict__ geom, const int32_t* __restrict__ leaf,
+                        const double* __restrict__ geom, const float4* __restrict__ c32,
+                        const int32_t* __restrict__ leaf,
                         const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
                         const int32_t* __restrict__ start, const int32_t* __restrict__ count,
                         const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ cnt,
-                        const int64_t* __restrict__ far_off, const int64_t* __restrict__ near_off,
-                        const int64_t* __restrict__ near_coff,
+                        const int64_t* __restrict__ far_po, const int64_t* __restrict__ near_po,
+                        const int64_t* __restrict__ chunk_po,
                         int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
                         FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
                         int* __restrict__ status)
 {
-    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaves) return;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t npairs = nleaves * nroots;
+    if (gid >= npairs) return;
+    const int64_t L = gid / nroots;
+    const int32_t root = (int32_t)(gid - L * nroots);
     const int32_t t = leaves[L];
     const double* gt = geom + 13 * (int64_t)t;
+    const float4 ct = c32[t];
+    const float theta32 = (float)theta;
     int32_t stk[kStack];
     int sp = 0;
-    for (int r = nroots - 1; r >= 0; r--) stk[sp++] = r;
+    stk[sp++] = root;
     int64_t nf = 0, nn = 0, nch = 0;
-    int64_t fo = fill ? far_off[L] : 0, no = fill ? near_off[L] : 0, co = fill ? near_coff[L] : 0;
+    const int64_t fo = fill ? far_po[gid] : 0, no = fill ? near_po[gid] : 0, co = fill ? chunk_po[gid] : 0;
     while (sp > 0) {
         const int32_t s = stk[--sp];
         const double* gs = geom + 13 * (int64_t)s;
         bool is_far = false, is_near = false;
-        if (mac(gt, gs, theta)) {
+        if (mac_filtered(ct, c32[s], theta32, gt, gs, theta)) {
             if (count[s] > leaf_size)
                 is_far = true;
             else
@@ -373,7 +449,7 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
             }
             nf++;
         } else if (is_near) {
-            const int32_t st = start[s], ct = count[s];
+            const int32_t st = start[s], ct2 = count[s];
             if (fill) {
                 near_idx[no + nn] = s;
                 const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
@@ -384,23 +460,40 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
                 e.dz = (float)__dsub_rn(gs[11], gt[11]);
                 e.gap = __double2float_rd(gap);
                 e.pad[0] = e.pad[1] = 0;
-                for (int32_t c0 = 0; c0 < ct; c0 += kStage) {
+                for (int32_t c0 = 0; c0 < ct2; c0 += kStage) {
                     e.start = st + c0;
-                    e.count = min(kStage, ct - c0);
+                    e.count = min(kStage, ct2 - c0);
                     near_ent[co + nch] = e;
                     nch++;
                 }
             } else {
-                nch += (ct + kStage - 1) / kStage;
+                nch += (ct2 + kStage - 1) / kStage;
             }
             nn++;
         }
     }
     if (!fill) {
-        cnt[L] = (int32_t)nf;
-        cnt[nleaves + L] = (int32_t)nn;
-        cnt[2 * nleaves + L] = (int32_t)nch;
+        cnt[gid] = (int32_t)nf;
+        cnt[npairs + gid] = (int32_t)nn;
+        cnt[2 * npairs + gid] = (int32_t)nch;
     }
+}
+
+// Per-leaf CSR offsets from the per-(leaf, root) offsets: off[L] = po[L * nroots].
+__global__ void k_leaf_offsets(int64_t nleaves, int32_t nroots, const int64_t* __restrict__ po,
+                               int64_t* __restrict__ off)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L <= nleaves) off[L] = po[L * nroots];
+}
+
+// FP32 copies of the node centres and radii for the pre-filtered MAC.
+__global__ void k_node_f32(int64_t nnodes, const double* __restrict__ geom, float4* __restrict__ c32)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nnodes) return;
+    const double* g = geom + 13 * p;
+    c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
 }
 
 // Splits a leaf of nt targets into k warp tasks of nearly equal size, two targets per lane
@@ -498,6 +591,7 @@ int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
     STS_CUDA(c->nd_key.grow(need, keep, s));
     STS_CUDA(c->nd_geom.grow(13 * need, 13 * keep, s));
     STS_CUDA(c->nd_norm.grow(9 * need, 9 * keep, s));
+    STS_CUDA(c->nd_norm32.grow(3 * need, 3 * keep, s));
     STS_CUDA(c->nd_cc.grow(4 * need, 4 * keep, s));
     STS_CUDA(c->nd_child.grow(4 * need, 4 * keep, s));
     return STS_OK;
@@ -535,6 +629,10 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_
                 for (int b = 0; b < 3; b++) FV[f][a][b] = V[F[f][a]][b];
         STS_CUDA(cudaMemcpyToSymbolAsync(c_fc, C, sizeof(C), 0, cudaMemcpyHostToDevice, s));
         STS_CUDA(cudaMemcpyToSymbolAsync(c_fv, FV, sizeof(FV), 0, cudaMemcpyHostToDevice, s));
+        float C32[20][3];
+        for (int f = 0; f < 20; f++)
+            for (int a = 0; a < 3; a++) C32[f][a] = (float)C[f][a];
+        STS_CUDA(cudaMemcpyToSymbolAsync(c_fc32, C32, sizeof(C32), 0, cudaMemcpyHostToDevice, s));
     }
     STS_CUDA(c->pos.reserve(3 * n));
     STS_CUDA(cudaMemcpyAsync(c->pos.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -586,9 +684,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_
         if (grow_nodes(c, le + 4 * nl, le, s)) return STS_ERR_CUDA;
         (k_level_nodes<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, leaf_size, max_level,
                                                    c->nd_level.p, c->nd_count.p, c->nd_geom.p,
-                                                   c->nd_leaf.p, c->nd_norm.p, c->nd_cc.p), note_launch());
+                                                   c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p), note_launch());
         (k_level_particles<<<blocks(n, T), T, 0, s>>>((int32_t)lb, c->pos.p, n, c->nodeof.p,
-                                                      c->nd_leaf.p, c->nd_norm.p, c->digit.p,
+                                                      c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->digit.p,
                                                       c->nd_cc.p), note_launch());
         (k_level_nch<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, c->nd_leaf.p, c->nd_cc.p,
                                                 c->flags.p), note_launch());
@@ -609,6 +707,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_
     }
     c->nnodes = le;
     c->deepest = level;
+    STS_CUDA(c->nd_c32.reserve(le + 1));
+    (k_node_f32<<<blocks(le, T), T, 0, s>>>(le, c->nd_geom.p, c->nd_c32.p), note_launch());
 
     phase_begin(c, kPhSort, s);
     (k_sort_keys<<<blocks(n, T), T, 0, s>>>(c->nodeof.p, n, c->nd_start.p, c->skey.p, c->perm.p), note_launch());
@@ -638,29 +738,37 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     c->have_lists = false;
     const int64_t L = c->nleaves;
     const int T = 128;
-    STS_CUDA(c->list_cnt.reserve(3 * L + 3));
+    const int32_t nroots = (int32_t)(c->level_begin.size() > 1 ? c->level_begin[1] : 0);
+    const int64_t np = L * nroots;
+    STS_CUDA(c->list_cnt.reserve(3 * np + 3));
+    STS_CUDA(c->list_po.reserve(3 * (np + 1)));
     STS_CUDA(c->far_off.reserve(L + 1));
     STS_CUDA(c->near_off.reserve(L + 1));
     STS_CUDA(c->near_coff.reserve(L + 1));
-    STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
-    const int32_t nroots = (int32_t)(c->level_begin.size() > 1 ? c->level_begin[1] : 0);
-    if (L > 0)
-        (k_lists<<<blocks(L, T), T, 0, s>>>(0, L, c->leaves.p, nroots, theta, c->leaf_size,
-                                           c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
-                                           c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr, nullptr,
-                                           nullptr, nullptr, nullptr, nullptr, c->d_status), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, c->far_off.p, L, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + L, c->near_off.p, L, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + 2 * L, c->near_coff.p, L, c->scan_tmp.p, s);
-    // evaluation tasks: each leaf's targets in chunks of kTaskTargets
+    STS_CUDA(c->scan_tmp.reserve(scan_scratch(np + 1) + scan_scratch(L + 1) + 8));
+    int64_t* far_po = c->list_po.p;
+    int64_t* near_po = c->list_po.p + (np + 1);
+    int64_t* chunk_po = c->list_po.p + 2 * (np + 1);
+    if (np > 0)
+        (k_lists<<<blocks(np, T), T, 0, s>>>(0, L, c->leaves.p, nroots, theta, c->leaf_size, c->nd_geom.p,
+                                            c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
+                                            c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p,
+                                            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                            c->d_status), note_launch());
+    exclusive_scan_i32(c->list_cnt.p, far_po, np, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + np, near_po, np, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + 2 * np, chunk_po, np, c->scan_tmp.p, s);
+    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, far_po, c->far_off.p), note_launch());
+    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, near_po, c->near_off.p), note_launch());
+    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, chunk_po, c->near_coff.p), note_launch());
+    // evaluation tasks: each leaf's targets split into warp tasks
     STS_CUDA(c->flags.reserve(L + 1));
     STS_CUDA(c->offs.reserve(L + 1));
     STS_CUDA(c->small.reserve(16));
     if (L > 0) (k_task_count<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
     exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s);
-    (k_gather<<<1, 32, 0, s>>>(c->far_off.p + L, c->near_off.p + L, c->offs.p + L, c->near_coff.p + L,
-                               c->d_status, c->small.p), note_launch());
+    (k_gather<<<1, 32, 0, s>>>(far_po + np, near_po + np, c->offs.p + L, chunk_po + np, c->d_status, c->small.p),
+     note_launch());
     STS_LAUNCH_CHECK();
     STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     STS_CUDA(cudaStreamSynchronize(s));
@@ -677,12 +785,11 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     STS_CUDA(c->near_ent.reserve(nchunks + 1));
     STS_CUDA(c->tasks.reserve(ntasks + 1));
     if (L > 0) {
-        (k_lists<<<blocks(L, T), T, 0, s>>>(1, L, c->leaves.p, nroots, theta, c->leaf_size,
-                                           c->nd_geom.p, c->nd_leaf.p, c->nd_first_child.p,
-                                           c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                                           c->cluster_slot.p, nullptr, c->far_off.p, c->near_off.p,
-                                           c->near_coff.p, c->far_idx.p, c->near_idx.p, c->far_ent.p,
-                                           c->near_ent.p, c->d_status), note_launch());
+        (k_lists<<<blocks(np, T), T, 0, s>>>(1, L, c->leaves.p, nroots, theta, c->leaf_size, c->nd_geom.p,
+                                            c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
+                                            c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po,
+                                            near_po, chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p,
+                                            c->near_ent.p, c->d_status), note_launch());
         (k_task_fill<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_start.p, c->nd_count.p,
                                                c->offs.p, c->tasks.p), note_launch());
     }

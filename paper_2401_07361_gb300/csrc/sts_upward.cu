@@ -90,75 +90,97 @@ __device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int&
     c = r;
 }
 
-// Moments of one (cluster, chunk) task.  T = float (mixed) or double (FP64).
+// Frame of each cluster for the spherical barycentric coordinates of Sec. 3.2 (y = b1 v1 +
+// b2 v2 + b3 v3, Cramer's rule): rows n_i / D with n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2,
+// D = v1 . n1, and b(c) = (n_i / D) . c at the circumcentre.  frame[c][12] in FP64.
+__global__ void k_cluster_frames(int64_t nclu, const int32_t* __restrict__ cnode,
+                                 const double* __restrict__ geom, double* __restrict__ frame)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclu) return;
+    const double* g = geom + 13 * (int64_t)cnode[c];
+    const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
+    const double v3x = g[6], v3y = g[7], v3z = g[8];
+    const double n[9] = {v2y * v3z - v2z * v3y, v2z * v3x - v2x * v3z, v2x * v3y - v2y * v3x,
+                         v3y * v1z - v3z * v1y, v3z * v1x - v3x * v1z, v3x * v1y - v3y * v1x,
+                         v1y * v2z - v1z * v2y, v1z * v2x - v1x * v2z, v1x * v2y - v1y * v2x};
+    const double D = v1x * n[0] + v1y * n[1] + v1z * n[2];
+    double* f = frame + 12 * c;
+    for (int q = 0; q < 9; q++) f[q] = n[q] / D;
+    for (int a = 0; a < 3; a++) f[9 + a] = f[3 * a] * g[9] + f[3 * a + 1] * g[10] + f[3 * a + 2] * g[11];
+}
+
+// Moments of one (cluster, chunk) task.  T = float (mixed) or double (FP64).  Each thread
+// tabulates the powers of its particle's barycentric coordinates; then G = 128 / M groups
+// of M threads (thread = basis function k) each sum a share of the chunk's particles, and
+// the group sums are added in a fixed order.
 template <class T>
 __global__ void __launch_bounds__(kUpChunk)
 k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
          const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-         const double* __restrict__ geom, const double4* __restrict__ src64, int d, int M,
-         double* __restrict__ part)
+         const double* __restrict__ geom, const double* __restrict__ frame,
+         const double4* __restrict__ src64, int d, int M, double* __restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* P = reinterpret_cast<T*>(smem_raw);  // [3][d+1][kUpChunk + 1]
     constexpr int LD = kUpChunk + 1;
     T* Wt = P + 3 * (d + 1) * LD;           // [kUpChunk]
-    __shared__ double frame[12];            // rows n_i / D (9), b(c) (3)
+    T* G2 = Wt + kUpChunk;                  // [kUpChunk] group partial sums
 
     const int2 tk = tasks[blockIdx.x];
     const int32_t node = cnode[tk.x];
     const double* g = geom + 13 * (int64_t)node;
-    if (threadIdx.x == 0) {
-        const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
-        const double v3x = g[6], v3y = g[7], v3z = g[8];
-        // n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2; D = v1 . n1 (Cramer's rule)
-        double n[9] = {v2y * v3z - v2z * v3y, v2z * v3x - v2x * v3z, v2x * v3y - v2y * v3x,
-                       v3y * v1z - v3z * v1y, v3z * v1x - v3x * v1z, v3x * v1y - v3y * v1x,
-                       v1y * v2z - v1z * v2y, v1z * v2x - v1x * v2z, v1x * v2y - v1y * v2x};
-        const double D = v1x * n[0] + v1y * n[1] + v1z * n[2];
-        for (int q = 0; q < 9; q++) frame[q] = n[q] / D;
-        const double cx = g[9], cy = g[10], cz = g[11];
-        for (int a = 0; a < 3; a++)
-            frame[9 + a] = frame[3 * a] * cx + frame[3 * a + 1] * cy + frame[3 * a + 2] * cz;
-    }
-    __syncthreads();
+    const double* f = frame + 12 * (int64_t)tk.x;
     const int t = threadIdx.x;
     const int64_t j = (int64_t)start[node] + tk.y + t;
-    const bool valid = tk.y + t < count[node];
+    const int nv = min(kUpChunk, count[node] - tk.y);
+    const bool valid = t < nv;
     T b[3] = {T(0), T(0), T(0)};
     T w = T(0);
     if (valid) {
         const double4 y = src64[j];
         w = T(0.5 * y.w);
         if (sizeof(T) == sizeof(double)) {
-            for (int a = 0; a < 3; a++)
-                b[a] = T(frame[3 * a] * y.x + frame[3 * a + 1] * y.y + frame[3 * a + 2] * y.z);
+            for (int a = 0; a < 3; a++) b[a] = T(f[3 * a] * y.x + f[3 * a + 1] * y.y + f[3 * a + 2] * y.z);
         } else {
             const float dx = (float)(y.x - g[9]), dy = (float)(y.y - g[10]), dz = (float)(y.z - g[11]);
             for (int a = 0; a < 3; a++)
-                b[a] = (float)frame[9 + a] + ((float)frame[3 * a] * dx + (float)frame[3 * a + 1] * dy +
-                                              (float)frame[3 * a + 2] * dz);
+                b[a] = (float)f[9 + a] + ((float)f[3 * a] * dx + (float)f[3 * a + 1] * dy + (float)f[3 * a + 2] * dz);
         }
     }
     for (int a = 0; a < 3; a++) {
-        T p = T(1);
-        P[(a * (d + 1) + 0) * LD + t] = p;
+        T pw = T(1);
+        P[(a * (d + 1) + 0) * LD + t] = pw;
         for (int e = 1; e <= d; e++) {
-            p = p * b[a];
-            P[(a * (d + 1) + e) * LD + t] = p;
+            pw = pw * b[a];
+            P[(a * (d + 1) + e) * LD + t] = pw;
         }
     }
     Wt[t] = w;
     __syncthreads();
-    const int nv = min(kUpChunk, count[node] - tk.y);
-    for (int k = t; k < M; k += kUpChunk) {
-        int ea, eb, ec;
-        sbb_exponents(d, k, ea, eb, ec);
-        const T* p1 = P + (0 * (d + 1) + ea) * LD;
-        const T* p2 = P + (1 * (d + 1) + eb) * LD;
-        const T* p3 = P + (2 * (d + 1) + ec) * LD;
+    const int G = max(1, kUpChunk / M);
+    for (int k0 = 0; k0 < M; k0 += kUpChunk / G) {
+        // thread t: basis k = k0 + t % (128 / G) ... in groups of M threads
+        const int per = M < kUpChunk ? M : kUpChunk;
+        const int grp = t / per, k = k0 + t % per;
         T acc = T(0);
-        for (int q = 0; q < nv; q++) acc += ((p1[q] * p2[q]) * p3[q]) * Wt[q];
-        part[(int64_t)blockIdx.x * M + k] = (double)acc;
+        if (grp < G && k < M) {
+            int ea, eb, ec;
+            sbb_exponents(d, k, ea, eb, ec);
+            const T* p1 = P + (0 * (d + 1) + ea) * LD;
+            const T* p2 = P + (1 * (d + 1) + eb) * LD;
+            const T* p3 = P + (2 * (d + 1) + ec) * LD;
+            for (int q = grp; q < nv; q += G) acc += ((p1[q] * p2[q]) * p3[q]) * Wt[q];
+        }
+        if (grp < G && k < M) G2[t] = acc;
+        __syncthreads();
+        if (t < per && k0 + t < M) {
+            double sum = 0.0;
+            for (int gg = 0; gg < G; gg++) sum += (double)G2[gg * per + t];
+            part[(int64_t)blockIdx.x * M + k0 + t] = sum;
+        }
+        __syncthreads();
+        if (G > 1) break;  // with G > 1 groups, M < 128 and one pass covers every k
     }
 }
 
@@ -235,6 +257,10 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
     const int64_t nclu = c->h_pinned[0], ntask = c->h_pinned[1];
     c->nleaves = c->h_pinned[8];
     STS_CUDA(c->up_tasks.reserve(ntask + 1));
+    STS_CUDA(c->up_frame.reserve(12 * nclu + 12));
+    if (nclu > 0)
+        (k_cluster_frames<<<blocks(nclu, 128), 128, 0, s>>>(nclu, c->cluster_node.p, c->nd_geom.p, c->up_frame.p),
+         note_launch());
     if (nn > 0)
         (k_up_tasks<<<blocks(nn, 256), 256, 0, s>>>(nn, c->cluster_slot.p, c->up_toff.p, c->up_tasks.p),
          note_launch());
@@ -256,17 +282,17 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
     if (nclu == 0) return STS_OK;
     const int LD = kUpChunk + 1;
     if (precision == STS_FP64) {
-        const size_t sm = (3 * (degree + 1) * LD + kUpChunk) * sizeof(double);
+        const size_t sm = (3 * (degree + 1) * LD + 2 * kUpChunk) * sizeof(double);
         STS_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         (k_upward<double><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
-            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->src64.p,
-            degree, M, c->up_part.p), note_launch());
+            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
+            c->src64.p, degree, M, c->up_part.p), note_launch());
     } else {
-        const size_t sm = (3 * (degree + 1) * LD + kUpChunk) * sizeof(float);
+        const size_t sm = (3 * (degree + 1) * LD + 2 * kUpChunk) * sizeof(float);
         STS_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         (k_upward<float><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
-            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->src64.p,
-            degree, M, c->up_part.p), note_launch());
+            c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
+            c->src64.p, degree, M, c->up_part.p), note_launch());
     }
     (k_contract<<<(unsigned)nclu, 64, 0, s>>>(c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p,
                                              ref->d_beta.p, ref->d_vinv.p, degree, M, c->prx64.p,
