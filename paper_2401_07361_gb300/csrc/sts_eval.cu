@@ -150,8 +150,8 @@ __device__ __forceinline__ void issue_block(const BlockDesc& d, float4* sb, int 
 
 // FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
 // goes to corr (sorted order), read back by the owning lane in the epilogue.
-__device__ __noinline__ void close_pair(const double4* __restrict__ src64, int64_t j, int64_t tk,
-                                        double* __restrict__ corr)
+__device__ __forceinline__ void close_pair(const double4* __restrict__ src64, int64_t j, int64_t tk,
+                                           double* __restrict__ corr)
 {
     const double4 y = src64[j];
     const double4 x = src64[tk];
@@ -165,12 +165,18 @@ __device__ __noinline__ void close_pair(const double4* __restrict__ src64, int64
     }
 }
 
+__device__ __forceinline__ float sqdist(const float4 s, float ax, float ay, float az)
+{
+    const float dx = s.x - ax, dy = s.y - ay, dz = s.z - az;
+    return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
+}
+
+// The FP32 pair loop of one block for a lane's two targets.  TEST: pairs with |d|^2 < 2 tau
+// contribute nothing here and set `hit`; the caller then evaluates them in FP64.
 template <bool TEST>
 __device__ __forceinline__ void block_pairs(const float4* sb, int cnt, int ph, int S, float ax, float ay, float az,
                                             float bx, float by, float bz, float& p0x, float& p0y, float& p0z,
-                                            float& p1x, float& p1y, float& p1z, float tau2, int64_t base,
-                                            int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
-                                            double* __restrict__ corr)
+                                            float& p1x, float& p1y, float& p1z, float tau2, bool& hit)
 {
 #pragma unroll 4
     for (int i = ph; i < cnt; i += S) {
@@ -182,14 +188,10 @@ __device__ __forceinline__ void block_pairs(const float4* sb, int cnt, int ph, i
         float c0 = s.w * rcp_approx(r0);
         float c1 = s.w * rcp_approx(r1);
         if (TEST) {
-            if (r0 < tau2) {
-                c0 = 0.f;
-                close_pair(src64, base + i, tk0, corr);
-            }
-            if (r1 < tau2) {
-                c1 = 0.f;
-                close_pair(src64, base + i, tk1, corr);
-            }
+            const bool z0 = r0 < tau2, z1 = r1 < tau2;
+            c0 = z0 ? 0.f : c0;
+            c1 = z1 ? 0.f : c1;
+            hit = hit || z0 || z1;
         }
         p0x = fmaf(c0, d0x, p0x);
         p0y = fmaf(c0, d0y, p0y);
@@ -200,8 +202,22 @@ __device__ __forceinline__ void block_pairs(const float4* sb, int cnt, int ph, i
     }
 }
 
+// Second pass over a tested block for a lane that hit: the same FP32 squared distances pick
+// the same pairs, which are evaluated in FP64 from the FP64 positions.
+__device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int ph, int S, float ax, float ay,
+                                               float az, float bx, float by, float bz, float tau2, int64_t base,
+                                               int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
+                                               double* __restrict__ corr)
+{
+    for (int i = ph; i < cnt; i += S) {
+        const float4 s = sb[i];
+        if (sqdist(s, ax, ay, az) < tau2) close_pair(src64, base + i, tk0, corr);
+        if (sqdist(s, bx, by, bz) < tau2) close_pair(src64, base + i, tk1, corr);
+    }
+}
+
 // ------------------------------------------------------------------------ mixed tree
-__global__ void __launch_bounds__(kEvalWarps * 32, 4)
+__global__ void __launch_bounds__(kEvalWarps * 32, 3)
 k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
              const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
@@ -239,7 +255,6 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
     for (int b = 0; b < nbt; b++) {
         issue_block(nxt, sbuf[w][(b + 1) & 1], lane, prx32, src32, M);
         cp_commit();
-        const BlockDesc nn = load_desc(b + 2, nf, nbt, fe, ne, M, tau_r);
         cp_wait1();
         __syncwarp();
         const float4* sb = sbuf[w][b & 1];
@@ -247,12 +262,13 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
         const float ax = t0x - cur.dx, ay = t0y - cur.dy, az = t0z - cur.dz;
         const float bx = t1x - cur.dx, by = t1y - cur.dy, bz = t1z - cur.dz;
         float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
-        if (cur.kind == 2)
-            block_pairs<true>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
-                              cur.idx, tk0, tk1, src64, corr);
-        else
-            block_pairs<false>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
-                               cur.idx, tk0, tk1, src64, corr);
+        bool hit = false;
+        if (cur.kind == 2) {
+            block_pairs<true>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+            if (hit) block_close_pairs(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, tau2, cur.idx, tk0, tk1, src64, corr);
+        } else {
+            block_pairs<false>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+        }
         two_sum_add(h0x, l0x, p0x);
         two_sum_add(h0y, l0y, p0y);
         two_sum_add(h0z, l0z, p0z);
@@ -261,7 +277,7 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
         two_sum_add(h1z, l1z, p1z);
         __syncwarp();
         cur = nxt;
-        nxt = nn;
+        nxt = load_desc(b + 2, nf, nbt, fe, ne, M, tau_r);
     }
     double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
                    (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};
