@@ -152,6 +152,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import numpy as np
+
     from oracle import oracle as O
 
     wl = load_workload(args.workload)
@@ -160,9 +162,13 @@ def run_reference(args):
     n = len(pos)
     cores = os.cpu_count() or 1
 
+    offs = wl.get("offsets", np.array([0, n], dtype=np.int64))
+
     def step():
-        tr = O.Tree(pos, leaf, 16)
-        return tr.velocity(zeta, area, args.theta, args.degree, nthreads=cores)
+        for b in range(len(offs) - 1):
+            lo, hi = int(offs[b]), int(offs[b + 1])
+            tr = O.Tree(pos[lo:hi], leaf, 16)
+            tr.velocity(zeta[lo:hi], area[lo:hi], args.theta, args.degree, nthreads=cores)
 
     for _ in range(args.warmup):
         step()
@@ -206,7 +212,9 @@ def main():
     pos_h, zeta_h, area_h = wl["pos"], wl["zeta"], wl["area"]
     n = len(pos_h)
     leaf = args.leaf or wl["leaf_size"]
-    tau = args.tau_c * 4.0 * math.pi / n
+    # one tau for the whole forest: that of the smallest instance (widest particle spacing)
+    n_tau = n if "offsets" not in wl else int(np.min(np.diff(wl["offsets"])[np.diff(wl["offsets"]) > 0]))
+    tau = args.tau_c * 4.0 * math.pi / n_tau
     pm = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16,
                     precision=sts.STS_MIXED, near_fp64_tau=tau)
     p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
@@ -218,8 +226,16 @@ def main():
     ctx = sts.Context()
     h = ctx.h
 
+    offsets = wl.get("offsets")
+
+    def build(x, p):
+        if offsets is None:
+            sts.sts_tree_build(h, x, p)
+        else:
+            sts.sts_tree_build_batched(h, x, offsets, p)
+
     def step(p=pm):
-        sts.sts_tree_build(h, pos, p)
+        build(pos, p)
         sts.sts_velocity(h, zeta, area, p, vel)
 
     def barrier():
@@ -291,7 +307,7 @@ def main():
         pos2.copy_(pos_p, non_blocking=True)
         zeta2.copy_(zeta_p, non_blocking=True)
         area2.copy_(area_p, non_blocking=True)
-        sts.sts_tree_build(h, pos2, pm)
+        build(pos2, pm)
         sts.sts_velocity(h, zeta2, area2, pm, vel2)
         vel_p.copy_(vel2, non_blocking=True)
         e1.record()
@@ -347,9 +363,13 @@ def main():
         from oracle import oracle as O
 
         cores = os.cpu_count() or 1
+        offs = offsets if offsets is not None else np.array([0, n], dtype=np.int64)
         t0 = time.perf_counter()
-        tr = O.Tree(pos_h, leaf, 16)
-        ref = tr.velocity(zeta_h, area_h, args.theta, args.degree, nthreads=cores)
+        ref = np.zeros((n, 3))
+        for b in range(len(offs) - 1):
+            lo, hi = int(offs[b]), int(offs[b + 1])
+            tr = O.Tree(pos_h[lo:hi], leaf, 16)
+            ref[lo:hi] = tr.velocity(zeta_h[lo:hi], area_h[lo:hi], args.theta, args.degree, nthreads=cores)
         dt = time.perf_counter() - t0
         cpu = {"value": n / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
                "sample": f"one full evaluation: oracle tree build + FP64 tree-code velocity of all {n} targets "

@@ -120,6 +120,18 @@ int sts_direct_noalloc(const double* pos, const double* zeta, const double* area
 int sts_tree_build(sts_ctx* ctx, const double* pos, int64_t n, const sts_params* p,
                    void* stream);
 
+/* Batched build: ninst independent instances (separate particle sets on the unit sphere,
+ * each with its own icosahedral tree of Sec. 3.1) concatenated in pos[n,3], instance b
+ * holding particles offsets[b] .. offsets[b+1] - 1 (offsets: HOST array of ninst + 1
+ * non-decreasing values, offsets[0] = 0, n = offsets[ninst]; empty instances allowed).  The
+ * trees form one forest whose roots are keyed (instance, face) = 20 b + f; every level of
+ * every instance is built by the same launches, and sts_velocity then evaluates all
+ * instances in one launch over their combined leaf tasks, each target interacting only with
+ * its own instance.  Each instance's velocities are those of sts_tree_build + sts_velocity
+ * on that instance alone.  Synchronises `stream`. */
+int sts_tree_build_batched(sts_ctx* ctx, const double* pos, const int64_t* offsets,
+                           int32_t ninst, const sts_params* p, void* stream);
+
 /* Tree-code velocity (Sec. 3.3 PC + PP interactions over MAC interaction lists, Sec. 3.4)
  * for the tree last built in ctx: zeta[n], area[n] in, vel[n,3] out in the caller's
  * order.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau; the tree's own
@@ -137,6 +149,13 @@ int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts
  * `stream`. */
 int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n,
                  double dt, double Omega, const sts_params* p, void* stream);
+
+/* One RK4 step of ninst independent instances (offsets as in sts_tree_build_batched), in
+ * place on pos[n,3] and zeta[n]; every stage builds the forest and evaluates all instances
+ * together.  Synchronises `stream`. */
+int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* area,
+                         const int64_t* offsets, int32_t ninst, double dt, double Omega,
+                         const sts_params* p, void* stream);
 
 /* ---- inspection (HOST output buffers; every call synchronises `stream`) -------------- */
 /* info[8] = {n, nodes, leaves, deepest level, far entries, near entries, clusters,

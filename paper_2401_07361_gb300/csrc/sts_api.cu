@@ -60,7 +60,8 @@ sts_ctx::~sts_ctx()
     offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
     nd_key.release(); nd_geom.release(); nd_norm.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
-    counters.release(); small.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
+    counters.release(); small.release(); inst_off.release(); root_cnt.release();
+    root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
@@ -169,13 +170,83 @@ int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_
     return STS_OK;
 }
 
-int build_impl(sts_ctx* c, const double* pos, int64_t n, const sts_params* p, cudaStream_t s)
+int build_impl(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off, int ninst, const sts_params* p,
+               cudaStream_t s)
 {
     phase_begin(c, kPhBuild, s);
-    int rc = tree_build(c, pos, n, p->leaf_size, p->max_level, s);
+    int rc = tree_build(c, pos, n, inst_off, ninst, p->leaf_size, p->max_level, s);
     if (rc == STS_OK && n > 0) rc = build_clusters(c, s);
     phase_end(c, kPhBuild, s);
     return rc;
+}
+
+int upload_offsets(sts_ctx* c, const int64_t* offsets, int32_t ninst, const int64_t** d_off, int64_t* n,
+                   const char* fn, cudaStream_t s)
+{
+    if (!offsets || ninst < 1 || ninst > (1 << 24)) {
+        set_error("%s: offsets must be a host array of ninst + 1 values, 1 <= ninst <= 2^24", fn);
+        return STS_ERR_ARG;
+    }
+    if (offsets[0] != 0) {
+        set_error("%s: offsets[0] must be 0", fn);
+        return STS_ERR_ARG;
+    }
+    for (int32_t b = 0; b < ninst; b++)
+        if (offsets[b + 1] < offsets[b]) {
+            set_error("%s: offsets must be non-decreasing (offsets[%d] > offsets[%d])", fn, b, b + 1);
+            return STS_ERR_ARG;
+        }
+    int rc = check_n(offsets[ninst], fn);
+    if (rc) return rc;
+    STS_CUDA(c->inst_off.reserve(ninst + 1));
+    STS_CUDA(cudaMemcpyAsync(c->inst_off.p, offsets, (ninst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    STS_CUDA(cudaStreamSynchronize(s));  // the host array may be pageable and reused by the caller
+    *d_off = c->inst_off.p;
+    *n = offsets[ninst];
+    return STS_OK;
+}
+
+// One RK4 step of the whole forest (one instance when inst_off is NULL).
+int rk4_impl(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, const int64_t* inst_off,
+             int ninst, double dt, double Omega, const sts_params* p, cudaStream_t s)
+{
+    int rc;
+    if (!isfinite(dt) || !isfinite(Omega)) {
+        set_error("bve_rk4_step: dt and Omega must be finite");
+        return STS_ERR_ARG;
+    }
+    if (n > 0 && (!pos || !zeta || !area)) {
+        set_error("bve_rk4_step: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (n == 0) return STS_OK;
+    sts_ctx* c = ctx;
+    STS_CUDA(c->rk_x0.reserve(3 * n));
+    STS_CUDA(c->rk_z0.reserve(n));
+    STS_CUDA(c->rk_xs.reserve(3 * n));
+    STS_CUDA(c->rk_zs.reserve(n));
+    STS_CUDA(c->rk_k.reserve(3 * n));
+    STS_CUDA(c->rk_ksum.reserve(3 * n));
+    STS_CUDA(cudaMemcpyAsync(c->rk_x0.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    STS_CUDA(cudaMemcpyAsync(c->rk_z0.p, zeta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double cst[3] = {0.5, 0.5, 1.0};
+    const double bst[3] = {1.0, 2.0, 2.0};
+    const double* xs = c->rk_x0.p;
+    const double* zs = c->rk_z0.p;
+    for (int st = 0; st < 4; st++) {
+        if ((rc = build_impl(c, xs, n, inst_off, ninst, p, s))) return rc;
+        if ((rc = velocity_impl(c, zs, area, p, c->rk_k.p, s))) return rc;
+        if (st < 3) {
+            rk4_stage(c->rk_x0.p, c->rk_z0.p, c->rk_k.p, cst[st] * dt, Omega, c->rk_xs.p, c->rk_zs.p,
+                      c->rk_ksum.p, bst[st], st == 0, n, s);
+            xs = c->rk_xs.p;
+            zs = c->rk_zs.p;
+        } else {
+            rk4_final(pos, zeta, c->rk_x0.p, c->rk_z0.p, c->rk_ksum.p, c->rk_k.p, dt, Omega, n, s);
+        }
+        STS_LAUNCH_CHECK();
+    }
+    return STS_OK;
 }
 
 }  // namespace
@@ -297,7 +368,7 @@ int sts_tree_build(sts_ctx* ctx, const double* pos, int64_t n, const sts_params*
         set_error("sts_tree_build: NULL pos");
         return STS_ERR_ARG;
     }
-    return build_impl(ctx, pos, n, p, S(stream));
+    return build_impl(ctx, pos, n, nullptr, 1, p, S(stream));
 }
 
 int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p, double* vel,
@@ -316,48 +387,38 @@ int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts
     return velocity_impl(ctx, zeta, area, p, vel, S(stream));
 }
 
+int sts_tree_build_batched(sts_ctx* ctx, const double* pos, const int64_t* offsets, int32_t ninst,
+                           const sts_params* p, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_tree_build_batched");
+    if (rc || (rc = check_params(p, "sts_tree_build_batched"))) return rc;
+    const int64_t* d_off = nullptr;
+    int64_t n = 0;
+    if ((rc = upload_offsets(ctx, offsets, ninst, &d_off, &n, "sts_tree_build_batched", S(stream)))) return rc;
+    if (n > 0 && !pos) {
+        set_error("sts_tree_build_batched: NULL pos");
+        return STS_ERR_ARG;
+    }
+    return build_impl(ctx, pos, n, d_off, ninst, p, S(stream));
+}
+
 int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, double dt,
                  double Omega, const sts_params* p, void* stream)
 {
     int rc = check_ctx(ctx, "bve_rk4_step");
     if (rc || (rc = check_n(n, "bve_rk4_step")) || (rc = check_params(p, "bve_rk4_step"))) return rc;
-    if (!isfinite(dt) || !isfinite(Omega)) {
-        set_error("bve_rk4_step: dt and Omega must be finite");
-        return STS_ERR_ARG;
-    }
-    if (n > 0 && (!pos || !zeta || !area)) {
-        set_error("bve_rk4_step: NULL array");
-        return STS_ERR_ARG;
-    }
-    if (n == 0) return STS_OK;
-    cudaStream_t s = S(stream);
-    sts_ctx* c = ctx;
-    STS_CUDA(c->rk_x0.reserve(3 * n));
-    STS_CUDA(c->rk_z0.reserve(n));
-    STS_CUDA(c->rk_xs.reserve(3 * n));
-    STS_CUDA(c->rk_zs.reserve(n));
-    STS_CUDA(c->rk_k.reserve(3 * n));
-    STS_CUDA(c->rk_ksum.reserve(3 * n));
-    STS_CUDA(cudaMemcpyAsync(c->rk_x0.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    STS_CUDA(cudaMemcpyAsync(c->rk_z0.p, zeta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    const double cst[3] = {0.5, 0.5, 1.0};
-    const double bst[3] = {1.0, 2.0, 2.0};
-    const double* xs = c->rk_x0.p;
-    const double* zs = c->rk_z0.p;
-    for (int st = 0; st < 4; st++) {
-        if ((rc = build_impl(c, xs, n, p, s))) return rc;
-        if ((rc = velocity_impl(c, zs, area, p, c->rk_k.p, s))) return rc;
-        if (st < 3) {
-            rk4_stage(c->rk_x0.p, c->rk_z0.p, c->rk_k.p, cst[st] * dt, Omega, c->rk_xs.p, c->rk_zs.p,
-                      c->rk_ksum.p, bst[st], st == 0, n, s);
-            xs = c->rk_xs.p;
-            zs = c->rk_zs.p;
-        } else {
-            rk4_final(pos, zeta, c->rk_x0.p, c->rk_z0.p, c->rk_ksum.p, c->rk_k.p, dt, Omega, n, s);
-        }
-        STS_LAUNCH_CHECK();
-    }
-    return STS_OK;
+    return rk4_impl(ctx, pos, zeta, area, n, nullptr, 1, dt, Omega, p, S(stream));
+}
+
+int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* area, const int64_t* offsets,
+                         int32_t ninst, double dt, double Omega, const sts_params* p, void* stream)
+{
+    int rc = check_ctx(ctx, "bve_rk4_step_batched");
+    if (rc || (rc = check_params(p, "bve_rk4_step_batched"))) return rc;
+    const int64_t* d_off = nullptr;
+    int64_t n = 0;
+    if ((rc = upload_offsets(ctx, offsets, ninst, &d_off, &n, "bve_rk4_step_batched", S(stream)))) return rc;
+    return rk4_impl(ctx, pos, zeta, area, n, d_off, ninst, dt, Omega, p, S(stream));
 }
 
 int sts_tree_info(sts_ctx* ctx, int64_t* info, void* stream)

@@ -146,6 +146,10 @@ struct sts_ctx {
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)
     sts::DevBuf<int32_t> counters;       // small device counters
+    int ninst = 1;                       // instances in the forest
+    sts::DevBuf<int64_t> inst_off;       // [ninst + 1] instance offsets (batched builds)
+    sts::DevBuf<int32_t> root_cnt, root_flag, face_node;  // [20 * ninst] per (instance, face)
+    sts::DevBuf<int64_t> root_id, root_start;             // [20 * ninst + 1] scans
     sts::DevBuf<int64_t> small;          // [16] values gathered for one host read
     sts::DevBuf<int32_t> leaves;         // leaf node ids in depth-first order
     sts::DevBuf<int32_t> slot_leaf;      // [n] sorted slot -> depth-first leaf index
@@ -223,8 +227,9 @@ void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* v
                       int64_t* scan_scratch_buf, cudaStream_t s);
 
 // ---- tree and lists (sts_tree.cu) ----------------------------------------------------
-int tree_build(sts_ctx* ctx, const double* pos, int64_t n, int leaf_size, int max_level,
-               cudaStream_t s);
+// inst_off: device offsets [ninst + 1] of the instances (NULL: one instance)
+int tree_build(sts_ctx* ctx, const double* pos, int64_t n, const int64_t* inst_off, int ninst,
+               int leaf_size, int max_level, cudaStream_t s);
 int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
 // out[0..3] = *a, *b, *c, *d (0 for NULL), out[4] = status word: one host read for all.
 void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,

@@ -107,12 +107,15 @@ __device__ __forceinline__ void agg_inc(int32_t* ctr, int key, bool active)
 }
 
 // ------------------------------------------------------------------------- level 0
-__global__ void k_faces(const double* __restrict__ pos, int64_t n, uint8_t* __restrict__ digit,
-                        int32_t* __restrict__ face_count, int* __restrict__ status)
+// Root key of every particle: instance b (from the instance offsets, b = 0 without them) times
+// 20 plus its face; counts per root key.  The key goes to rkey[i].
+__global__ void k_faces(const double* __restrict__ pos, int64_t n, const int64_t* __restrict__ inst_off,
+                        int32_t ninst, int32_t* __restrict__ rkey, int32_t* __restrict__ face_count,
+                        int* __restrict__ status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < n;
-    int best = 0;
+    int best = 0, rk = 0;
     if (active) {
         const g3 x = gld(pos + 3 * i);
         if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
@@ -143,38 +146,48 @@ __global__ void k_faces(const double* __restrict__ pos, int64_t n, uint8_t* __re
                 }
             }
         }
-        digit[i] = (uint8_t)best;
+        int b = 0;
+        if (inst_off) {  // largest b with inst_off[b] <= i
+            int lo = 0, hi = ninst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (inst_off[mid] <= i)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            b = lo;
+        }
+        rk = 20 * b + best;
+        rkey[i] = rk;
     }
-    agg_inc(face_count, best, active);
+    agg_inc(face_count, rk, active);
 }
 
-// Root nodes for the non-empty faces, in face order, one thread per face.  face_node[f] =
-// node id or -1; counters[0] = number of roots.
-__global__ void k_roots(const int32_t* __restrict__ face_count, int32_t* __restrict__ face_node,
-                        int32_t* level, uint64_t* key, int32_t* parent, int32_t* first_child,
-                        int32_t* nchild, int32_t* start, int32_t* count, int32_t* leaf,
-                        double* geom, int32_t* counters)
+// Root nodes for the non-empty (instance, face) keys in key order, one thread per key:
+// id = number of non-empty keys before it, start = number of particles before it.
+// face_node[key] = node id or -1.
+__global__ void k_roots(int32_t nkeys, const int32_t* __restrict__ face_count, const int64_t* __restrict__ rid,
+                        const int64_t* __restrict__ rstart, int32_t* __restrict__ face_node, int32_t* level,
+                        uint64_t* key, int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
+                        int32_t* count, int32_t* leaf, double* geom)
 {
-    const int f = threadIdx.x;
-    if (blockIdx.x != 0 || f >= 20) return;
-    int id = 0, acc = 0;
-    for (int g = 0; g < f; g++) {
-        id += face_count[g] > 0;
-        acc += face_count[g];
-    }
-    const int c = face_count[f];
-    if (f == 19) counters[0] = id + (c > 0);
+    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rk >= nkeys) return;
+    const int c = face_count[rk];
     if (c == 0) {
-        face_node[f] = -1;
+        face_node[rk] = -1;
         return;
     }
-    face_node[f] = id;
+    const int f = rk % 20;
+    const int32_t id = (int32_t)rid[rk];
+    face_node[rk] = id;
     level[id] = 0;
-    key[id] = (uint64_t)f;
+    key[id] = (uint64_t)rk;
     parent[id] = -1;
     first_child[id] = -1;
     nchild[id] = 0;
-    start[id] = acc;
+    start[id] = (int32_t)rstart[rk];
     count[id] = c;
     leaf[id] = 0;
     node_geometry(geom + 13 * (int64_t)id, gmk(c_fv[f][0][0], c_fv[f][0][1], c_fv[f][0][2]),
@@ -182,11 +195,16 @@ __global__ void k_roots(const int32_t* __restrict__ face_count, int32_t* __restr
                   gmk(c_fv[f][2][0], c_fv[f][2][1], c_fv[f][2][2]));
 }
 
-__global__ void k_assign_roots(const uint8_t* __restrict__ digit, int64_t n,
-                               const int32_t* __restrict__ face_node, int32_t* __restrict__ nodeof)
+__global__ void k_root_flags(int32_t nkeys, const int32_t* __restrict__ face_count, int32_t* __restrict__ flags)
+{
+    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rk < nkeys) flags[rk] = face_count[rk] > 0 ? 1 : 0;
+}
+
+__global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node, int32_t* __restrict__ nodeof)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) nodeof[i] = face_node[digit[i]];
+    if (i < n) nodeof[i] = face_node[nodeof[i]];
 }
 
 // ------------------------------------------------------------------------- level l
@@ -384,14 +402,14 @@ __device__ __forceinline__ bool mac_filtered(float4 ct, float4 cs, float theta32
     return mac(gt, gs, theta);
 }
 
-// Target-leaf traversal of Sec. 3.4 (PC + PP), one thread per (target leaf, root): from the
-// root, a source node that passes the MAC is far (a cluster, more than N_T particles) or
-// near; one that fails is near if it is a leaf, else its children are visited in digit
-// order.  The rows of a leaf are the concatenation of its per-root rows in root order, which
-// is the depth-first order from the 20 roots.  fill = 0 counts far nodes, near nodes and
-// near chunks per (leaf, root); fill = 1 writes them at the scanned pair offsets.
+// Target-leaf traversal of Sec. 3.4 (PC + PP), one thread per target leaf: from the roots of
+// the leaf's instance in face order, a source node that passes the MAC is far (a cluster,
+// more than N_T particles) or near; one that fails is near if it is a leaf, else its
+// children are visited in digit order.  fill = 0 counts far nodes, near nodes and near
+// chunks per leaf; fill = 1 writes them at the scanned offsets.
 __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ leaves,
-                        int32_t nroots, double theta, int leaf_size,
+                        const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
+                        const int32_t* __restrict__ level, double theta, int leaf_size,
                         const double* __restrict__ geom, const float4* __restrict__ c32,
                         const int32_t* __restrict__ leaf,
                         const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
@@ -403,20 +421,21 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
                         FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
                         int* __restrict__ status)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t npairs = nleaves * nroots;
-    if (gid >= npairs) return;
-    const int64_t L = gid / nroots;
-    const int32_t root = (int32_t)(gid - L * nroots);
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaves) return;
     const int32_t t = leaves[L];
+    // roots of the target leaf's own instance: root key (instance * 20 + face) of the leaf
+    const uint64_t rk = key[t] >> (2 * level[t]);
+    const int32_t* roots = face_node + (int64_t)(rk / 20) * 20;
     const double* gt = geom + 13 * (int64_t)t;
     const float4 ct = c32[t];
     const float theta32 = (float)theta;
     int32_t stk[kStack];
     int sp = 0;
-    stk[sp++] = root;
+    for (int f = 19; f >= 0; f--)
+        if (roots[f] >= 0) stk[sp++] = roots[f];
     int64_t nf = 0, nn = 0, nch = 0;
-    const int64_t fo = fill ? far_po[gid] : 0, no = fill ? near_po[gid] : 0, co = fill ? chunk_po[gid] : 0;
+    const int64_t fo = fill ? far_po[L] : 0, no = fill ? near_po[L] : 0, co = fill ? chunk_po[L] : 0;
     while (sp > 0) {
         const int32_t s = stk[--sp];
         const double* gs = geom + 13 * (int64_t)s;
@@ -473,18 +492,10 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
         }
     }
     if (!fill) {
-        cnt[gid] = (int32_t)nf;
-        cnt[npairs + gid] = (int32_t)nn;
-        cnt[2 * npairs + gid] = (int32_t)nch;
+        cnt[L] = (int32_t)nf;
+        cnt[nleaves + L] = (int32_t)nn;
+        cnt[2 * nleaves + L] = (int32_t)nch;
     }
-}
-
-// Per-leaf CSR offsets from the per-(leaf, root) offsets: off[L] = po[L * nroots].
-__global__ void k_leaf_offsets(int64_t nleaves, int32_t nroots, const int64_t* __restrict__ po,
-                               int64_t* __restrict__ off)
-{
-    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L <= nleaves) off[L] = po[L * nroots];
 }
 
 // FP32 copies of the node centres and radii for the pre-filtered MAC.
@@ -605,7 +616,8 @@ void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const i
     (k_gather<<<1, 32, 0, s>>>(a, b, c, d, status, out), note_launch());
 }
 
-int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_level, cudaStream_t s)
+int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off, int ninst, int leaf_size,
+               int max_level, cudaStream_t s)
 {
     c->have_tree = false;
     c->have_lists = false;
@@ -649,27 +661,39 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, int leaf_size, int max_
     STS_CUDA(c->hist.reserve(hs));
     STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
     STS_CUDA(c->counters.reserve(64));
-    if (grow_nodes(c, 20 + 80, 0, s)) return STS_ERR_CUDA;
+    const int32_t nkeys = 20 * ninst;
+    if (grow_nodes(c, nkeys + 80, 0, s)) return STS_ERR_CUDA;
+    STS_CUDA(c->root_cnt.reserve(nkeys + 1));
+    STS_CUDA(c->root_flag.reserve(nkeys + 1));
+    STS_CUDA(c->face_node.reserve(nkeys + 1));
+    STS_CUDA(c->root_id.reserve(nkeys + 1));
+    STS_CUDA(c->root_start.reserve(nkeys + 1));
+    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1) + scan_scratch(nkeys + 1)));
+    c->ninst = ninst;
 
     const int T = 256;
-    int32_t* face_count = c->counters.p;      // [20]
-    int32_t* face_node = c->counters.p + 32;  // [20]
-    STS_CUDA(cudaMemsetAsync(face_count, 0, 20 * sizeof(int32_t), s));
-    (k_faces<<<blocks(n, T), T, 0, s>>>(c->pos.p, n, c->digit.p, face_count, c->d_status), note_launch());
-    (k_roots<<<1, 32, 0, s>>>(face_count, face_node, c->nd_level.p, c->nd_key.p, c->nd_parent.p,
-                             c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                             c->nd_leaf.p, c->nd_geom.p, c->flags.p), note_launch());
+    int32_t* face_count = c->root_cnt.p;  // [20 * instances]
+    STS_CUDA(cudaMemsetAsync(face_count, 0, nkeys * sizeof(int32_t), s));
+    (k_faces<<<blocks(n, T), T, 0, s>>>(c->pos.p, n, inst_off, ninst, c->nodeof.p, face_count, c->d_status),
+     note_launch());
+    (k_root_flags<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_flag.p), note_launch());
+    exclusive_scan_i32(c->root_flag.p, c->root_id.p, nkeys, c->scan_tmp.p, s);
+    exclusive_scan_i32(face_count, c->root_start.p, nkeys, c->scan_tmp.p, s);
+    (k_roots<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_id.p, c->root_start.p, c->face_node.p,
+                                            c->nd_level.p, c->nd_key.p, c->nd_parent.p, c->nd_first_child.p,
+                                            c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->nd_leaf.p,
+                                            c->nd_geom.p), note_launch());
     STS_LAUNCH_CHECK();
-    (k_assign_roots<<<blocks(n, T), T, 0, s>>>(c->digit.p, n, face_node, c->nodeof.p), note_launch());
+    (k_assign_roots<<<blocks(n, T), T, 0, s>>>(n, c->face_node.p, c->nodeof.p), note_launch());
     int64_t nroots = 0;
     {
-        // k_roots wrote the root count into flags[0]
-        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(c->small.reserve(16));
+        (k_gather<<<1, 32, 0, s>>>(c->root_id.p + nkeys, nullptr, nullptr, nullptr, c->d_status, c->small.p),
+         note_launch());
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         STS_CUDA(cudaStreamSynchronize(s));
-        nroots = ((int32_t*)c->h_pinned)[0];
-        int st = 0;
-        if (read_status(c, s, &st)) return STS_ERR_CUDA;
-        if (st & kStatusNonfinite) {
+        nroots = c->h_pinned[0];
+        if (c->h_pinned[4] & kStatusNonfinite) {
             STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
             set_error("sts_tree_build: non-finite position");
             return STS_ERR_NONFINITE;
@@ -738,29 +762,24 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     c->have_lists = false;
     const int64_t L = c->nleaves;
     const int T = 128;
-    const int32_t nroots = (int32_t)(c->level_begin.size() > 1 ? c->level_begin[1] : 0);
-    const int64_t np = L * nroots;
-    STS_CUDA(c->list_cnt.reserve(3 * np + 3));
-    STS_CUDA(c->list_po.reserve(3 * (np + 1)));
+    STS_CUDA(c->list_cnt.reserve(3 * L + 3));
     STS_CUDA(c->far_off.reserve(L + 1));
     STS_CUDA(c->near_off.reserve(L + 1));
     STS_CUDA(c->near_coff.reserve(L + 1));
-    STS_CUDA(c->scan_tmp.reserve(scan_scratch(np + 1) + scan_scratch(L + 1) + 8));
-    int64_t* far_po = c->list_po.p;
-    int64_t* near_po = c->list_po.p + (np + 1);
-    int64_t* chunk_po = c->list_po.p + 2 * (np + 1);
-    if (np > 0)
-        (k_lists<<<blocks(np, T), T, 0, s>>>(0, L, c->leaves.p, nroots, theta, c->leaf_size, c->nd_geom.p,
-                                            c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
-                                            c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p,
-                                            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                            c->d_status), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, far_po, np, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + np, near_po, np, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + 2 * np, chunk_po, np, c->scan_tmp.p, s);
-    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, far_po, c->far_off.p), note_launch());
-    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, near_po, c->near_off.p), note_launch());
-    (k_leaf_offsets<<<blocks(L + 1, T), T, 0, s>>>(L, nroots, chunk_po, c->near_coff.p), note_launch());
+    STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
+    int64_t* far_po = c->far_off.p;
+    int64_t* near_po = c->near_off.p;
+    int64_t* chunk_po = c->near_coff.p;
+    if (L > 0)
+        (k_lists<<<blocks(L, T), T, 0, s>>>(0, L, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
+                                           c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p,
+                                           c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr, nullptr, nullptr,
+                                           nullptr, nullptr, nullptr, c->d_status), note_launch());
+    exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s);
+    const int64_t np = L;
     // evaluation tasks: each leaf's targets split into warp tasks
     STS_CUDA(c->flags.reserve(L + 1));
     STS_CUDA(c->offs.reserve(L + 1));
@@ -785,11 +804,11 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     STS_CUDA(c->near_ent.reserve(nchunks + 1));
     STS_CUDA(c->tasks.reserve(ntasks + 1));
     if (L > 0) {
-        (k_lists<<<blocks(np, T), T, 0, s>>>(1, L, c->leaves.p, nroots, theta, c->leaf_size, c->nd_geom.p,
-                                            c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
-                                            c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po,
-                                            near_po, chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p,
-                                            c->near_ent.p, c->d_status), note_launch());
+        (k_lists<<<blocks(L, T), T, 0, s>>>(1, L, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
+                                           c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p,
+                                           c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
+                                           c->cluster_slot.p, nullptr, far_po, near_po, chunk_po, c->far_idx.p,
+                                           c->near_idx.p, c->far_ent.p, c->near_ent.p, c->d_status), note_launch());
         (k_task_fill<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_start.p, c->nd_count.p,
                                                c->offs.p, c->tasks.p), note_launch());
     }

@@ -64,6 +64,8 @@ def load(build_if_needed: bool = True):
             "sts_tree_build": (i32, [P, P, i64, PP, P]),
             "sts_velocity": (i32, [P, P, P, PP, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
+            "sts_tree_build_batched": (i32, [P, P, P, i32, PP, P]),
+            "bve_rk4_step_batched": (i32, [P, P, P, P, P, i32, dbl, dbl, PP, P]),
             "sts_tree_info": (i32, [P, P, P]),
             "sts_tree_export": (i32, [P] + [P] * 11 + [P]),
             "sts_lists_export": (i32, [P, P, P, P, P, P]),
@@ -197,6 +199,35 @@ def bve_rk4_step(ctx, pos, zeta, area, dt, Omega, p, stream=None):
     _check(load().bve_rk4_step(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
                                _dev(area, torch.float64, n, "area"), n, float(dt), float(Omega), C.byref(p),
                                _stream(stream)), "bve_rk4_step")
+
+
+def _offsets(offsets):
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    return off, int(off.shape[0] - 1)
+
+
+def sts_tree_build_batched(ctx, pos, offsets, p, stream=None):
+    import torch
+
+    off, ninst = _offsets(offsets)
+    n = pos.shape[0]
+    if ninst < 1 or off[-1] != n:
+        raise StsError(f"offsets must end at the number of particles ({n}), got {off[-1] if ninst >= 0 else None}")
+    _check(load().sts_tree_build_batched(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _host(off), ninst,
+                                         C.byref(p), _stream(stream)), "sts_tree_build_batched")
+
+
+def bve_rk4_step_batched(ctx, pos, zeta, area, offsets, dt, Omega, p, stream=None):
+    import torch
+
+    off, ninst = _offsets(offsets)
+    n = pos.shape[0]
+    if ninst < 1 or off[-1] != n:
+        raise StsError(f"offsets must end at the number of particles ({n})")
+    _check(load().bve_rk4_step_batched(ctx, _dev(pos, torch.float64, 3 * n, "pos"),
+                                       _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                       _host(off), ninst, float(dt), float(Omega), C.byref(p), _stream(stream)),
+           "bve_rk4_step_batched")
 
 
 # ---------------------------------------------------------------------------- inspection

@@ -248,4 +248,21 @@ def workload(name: str, areas: str = "default"):
         zeta = sh_series_vorticity(pos, 32, seed=0)
         return dict(pos=pos, zeta=zeta, area=equal_areas(len(pos)), theta=0.7, degree=8,
                     leaf_size=256)
+    if name == "ensemble64":
+        # 64 independent instances, N_b log-uniform in [10242, 163842] (seed 0); uniform points
+        # (seed 100 + b); equal areas 4 pi / N_b; RH wave 4 plus 1e-2 x an RMS-normalised
+        # random harmonic series to degree 12 (seed 1000 + b).
+        sizes = ensemble_sizes(64, 10242, 163842, seed=0)
+        pos, zeta, area = [], [], []
+        for b, nb in enumerate(sizes):
+            p = uniform_points(nb, seed=100 + b)
+            z = rh_vorticity(p, RH_W_PER_S, RH_K_PER_S)
+            noise = sh_series_vorticity(p, 12, seed=1000 + b)
+            z = z + 1e-2 * np.sqrt(np.mean(z * z)) * noise / np.sqrt(np.mean(noise * noise))
+            pos.append(p)
+            zeta.append(z)
+            area.append(equal_areas(nb))
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        return dict(pos=np.vstack(pos), zeta=np.concatenate(zeta), area=np.concatenate(area), offsets=off,
+                    theta=0.7, degree=8, leaf_size=128)
     raise KeyError(name)
