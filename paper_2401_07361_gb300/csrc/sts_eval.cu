@@ -141,11 +141,15 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Copies a block into shared memory (cp.async, 16 bytes per entry) and pads it with
+// zero-weight entries far from every target up to a multiple of `pad`.
 __device__ __forceinline__ void issue_block(const BlockDesc& d, float4* sb, int lane, const float4* __restrict__ prx32,
-                                            const float4* __restrict__ src32, int M)
+                                            const float4* __restrict__ src32, int M, int pad)
 {
     const float4* src = d.kind == 0 ? prx32 + (int64_t)d.idx * M : src32 + d.idx;
     for (int i = lane; i < d.cnt; i += 32) cp_async16(sb + i, src + i);
+    const int cntp = (d.cnt + pad - 1) / pad * pad;
+    if (d.cnt + lane < cntp) sb[d.cnt + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
 }
 
 // FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
@@ -171,43 +175,48 @@ __device__ __forceinline__ float sqdist(const float4 s, float ax, float ay, floa
     return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
 }
 
-// The FP32 pair loop of one block for a lane's two targets.  TEST: pairs with |d|^2 < 2 tau
-// contribute nothing here and set `hit`; the caller then evaluates them in FP64.
-template <bool TEST>
-__device__ __forceinline__ void block_pairs(const float4* sb, int cnt, int ph, int S, float ax, float ay, float az,
+// The FP32 pair loop of one block for a lane's two targets: entries ph, ph + S, ... of a block
+// padded to a multiple of 4 S (padding entries carry w = 0 far away), four per trip.  TEST:
+// pairs with |d|^2 < 2 tau contribute nothing here and set `hit`; the caller then evaluates
+// them in FP64.
+template <bool TEST, int S>
+__device__ __forceinline__ void block_pairs(const float4* sb, int cntp, int ph, float ax, float ay, float az,
                                             float bx, float by, float bz, float& p0x, float& p0y, float& p0z,
                                             float& p1x, float& p1y, float& p1z, float tau2, bool& hit)
 {
-#pragma unroll 4
-    for (int i = ph; i < cnt; i += S) {
-        const float4 s = sb[i];
-        const float d0x = s.x - ax, d0y = s.y - ay, d0z = s.z - az;
-        const float d1x = s.x - bx, d1y = s.y - by, d1z = s.z - bz;
-        const float r0 = fmaf(d0z, d0z, fmaf(d0y, d0y, fmaf(d0x, d0x, kEps)));
-        const float r1 = fmaf(d1z, d1z, fmaf(d1y, d1y, fmaf(d1x, d1x, kEps)));
-        float c0 = s.w * rcp_approx(r0);
-        float c1 = s.w * rcp_approx(r1);
-        if (TEST) {
-            const bool z0 = r0 < tau2, z1 = r1 < tau2;
-            c0 = z0 ? 0.f : c0;
-            c1 = z1 ? 0.f : c1;
-            hit = hit || z0 || z1;
+    for (int i = ph; i < cntp; i += 4 * S) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float4 s = sb[i + u * S];
+            const float d0x = s.x - ax, d0y = s.y - ay, d0z = s.z - az;
+            const float d1x = s.x - bx, d1y = s.y - by, d1z = s.z - bz;
+            const float r0 = fmaf(d0z, d0z, fmaf(d0y, d0y, fmaf(d0x, d0x, kEps)));
+            const float r1 = fmaf(d1z, d1z, fmaf(d1y, d1y, fmaf(d1x, d1x, kEps)));
+            float c0 = s.w * rcp_approx(r0);
+            float c1 = s.w * rcp_approx(r1);
+            if (TEST) {
+                const bool z0 = r0 < tau2, z1 = r1 < tau2;
+                c0 = z0 ? 0.f : c0;
+                c1 = z1 ? 0.f : c1;
+                hit = hit || z0 || z1;
+            }
+            p0x = fmaf(c0, d0x, p0x);
+            p0y = fmaf(c0, d0y, p0y);
+            p0z = fmaf(c0, d0z, p0z);
+            p1x = fmaf(c1, d1x, p1x);
+            p1y = fmaf(c1, d1y, p1y);
+            p1z = fmaf(c1, d1z, p1z);
         }
-        p0x = fmaf(c0, d0x, p0x);
-        p0y = fmaf(c0, d0y, p0y);
-        p0z = fmaf(c0, d0z, p0z);
-        p1x = fmaf(c1, d1x, p1x);
-        p1y = fmaf(c1, d1y, p1y);
-        p1z = fmaf(c1, d1z, p1z);
     }
 }
 
 // Second pass over a tested block for a lane that hit: the same FP32 squared distances pick
 // the same pairs, which are evaluated in FP64 from the FP64 positions.
-__device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int ph, int S, float ax, float ay,
-                                               float az, float bx, float by, float bz, float tau2, int64_t base,
-                                               int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
-                                               double* __restrict__ corr)
+template <int S>
+__device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int ph, float ax, float ay, float az,
+                                                  float bx, float by, float bz, float tau2, int64_t base,
+                                                  int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
+                                                  double* __restrict__ corr)
 {
     for (int i = ph; i < cnt; i += S) {
         const float4 s = sb[i];
@@ -217,20 +226,20 @@ __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int
 }
 
 // ------------------------------------------------------------------------ mixed tree
-__global__ void __launch_bounds__(kEvalWarps * 32, 3)
-k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
-             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
-             const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
-             const float4* __restrict__ src32, const double4* __restrict__ src64,
-             const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
-             double* __restrict__ vel)
+constexpr int kStagePad = kStage + 32;  // room for padding a block to a multiple of 4 S (S <= 8)
+
+template <int S>
+__device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[kStagePad], int lane,
+                                                const int64_t* __restrict__ far_off,
+                                                const FarEntry* __restrict__ far_ent,
+                                                const int64_t* __restrict__ near_coff,
+                                                const NearEntry* __restrict__ near_ent,
+                                                const float4* __restrict__ prx32, int M,
+                                                const float4* __restrict__ src32, const double4* __restrict__ src64,
+                                                const int32_t* __restrict__ perm, float tau2, float tau_r,
+                                                double* __restrict__ corr, double* __restrict__ vel)
 {
-    __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStage];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
-    if (ti >= ntasks) return;
-    const Task tk = tasks[ti];
-    const int p = (tk.nt + 1) >> 1, S = tk.S;
+    const int p = (tk.nt + 1) >> 1;
     const int j = lane % p;
     const int ph = lane < p * S ? lane / p : (1 << 20);
     const int64_t tk0 = tk.t0 + 2 * j, tk1 = tk0 + 1;
@@ -250,24 +259,25 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
 
     BlockDesc cur = load_desc(0, nf, nbt, fe, ne, M, tau_r);
     BlockDesc nxt = load_desc(1, nf, nbt, fe, ne, M, tau_r);
-    issue_block(cur, sbuf[w][0], lane, prx32, src32, M);
+    issue_block(cur, sbuf[0], lane, prx32, src32, M, 4 * S);
     cp_commit();
     for (int b = 0; b < nbt; b++) {
-        issue_block(nxt, sbuf[w][(b + 1) & 1], lane, prx32, src32, M);
+        issue_block(nxt, sbuf[(b + 1) & 1], lane, prx32, src32, M, 4 * S);
         cp_commit();
         cp_wait1();
         __syncwarp();
-        const float4* sb = sbuf[w][b & 1];
+        const float4* sb = sbuf[b & 1];
+        const int cntp = (cur.cnt + 4 * S - 1) / (4 * S) * (4 * S);
         // the source offset is folded into the targets: (y + delta) - x = y - (x - delta)
         const float ax = t0x - cur.dx, ay = t0y - cur.dy, az = t0z - cur.dz;
         const float bx = t1x - cur.dx, by = t1y - cur.dy, bz = t1z - cur.dz;
         float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
         bool hit = false;
         if (cur.kind == 2) {
-            block_pairs<true>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
-            if (hit) block_close_pairs(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, tau2, cur.idx, tk0, tk1, src64, corr);
+            block_pairs<true, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+            if (hit) block_close_pairs<S>(sb, cur.cnt, ph, ax, ay, az, bx, by, bz, tau2, cur.idx, tk0, tk1, src64, corr);
         } else {
-            block_pairs<false>(sb, cur.cnt, ph, S, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+            block_pairs<false, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
         }
         two_sum_add(h0x, l0x, p0x);
         two_sum_add(h0y, l0y, p0y);
@@ -281,6 +291,7 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
     }
     double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
                    (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};
+#pragma unroll
     for (int s2 = 1; s2 < S; s2++) {
         const int src = (lane + s2 * p) & 31;
 #pragma unroll
@@ -307,6 +318,39 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
             vel[3 * i + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
             vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
         }
+    }
+}
+
+__global__ void __launch_bounds__(kEvalWarps * 32, 3)
+k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
+             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
+             const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
+             const float4* __restrict__ src32, const double4* __restrict__ src64,
+             const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
+             double* __restrict__ vel)
+{
+    __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStagePad];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
+    if (ti >= ntasks) return;
+    const Task tk = tasks[ti];
+    switch (tk.S) {
+        case 1:
+            eval_task_mixed<1>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                               perm, tau2, tau_r, corr, vel);
+            break;
+        case 2:
+            eval_task_mixed<2>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                               perm, tau2, tau_r, corr, vel);
+            break;
+        case 4:
+            eval_task_mixed<4>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                               perm, tau2, tau_r, corr, vel);
+            break;
+        default:
+            eval_task_mixed<8>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                               perm, tau2, tau_r, corr, vel);
+            break;
     }
 }
 

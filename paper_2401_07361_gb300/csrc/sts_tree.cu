@@ -507,9 +507,16 @@ __global__ void k_node_f32(int64_t nnodes, const double* __restrict__ geom, floa
     c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
 }
 
+// Lanes sharing a pair of targets: the largest power of two S <= 8 with S * pairs <= 32.
+__device__ __forceinline__ int lanes_per_pair(int pairs)
+{
+    const int q = 32 / pairs;
+    return q >= 8 ? 8 : (q >= 4 ? 4 : (q >= 2 ? 2 : 1));
+}
+
 // Splits a leaf of nt targets into k warp tasks of nearly equal size, two targets per lane
-// and S = floor(32 / pairs) lanes per pair of targets.  k maximises the fraction of useful
-// interactions per warp step, nt S / (64 k) (ties go to the smaller k).
+// and S lanes per pair of targets.  k maximises the fraction of useful interactions per warp
+// step, nt S / (64 k) (ties go to the smaller k).
 __device__ int task_split(int nt)
 {
     const int kmin = max(1, (nt + kTaskTargets - 1) / kTaskTargets);
@@ -518,7 +525,7 @@ __device__ int task_split(int nt)
     for (int k = kmin; k <= kmin + 3; k++) {
         const int m = (nt + k - 1) / k;
         const int p = (m + 1) / 2;
-        const int S = min(32 / p, 32);
+        const int S = lanes_per_pair(p);
         const float e = (float)nt * (float)S / (64.f * (float)k);
         if (e > be * (1.f + 1e-6f)) {
             be = e;
@@ -553,7 +560,7 @@ __global__ void k_task_fill(int64_t nleaves, const int32_t* __restrict__ leaves,
         tk.leaf = (int32_t)L;
         tk.t0 = st + t0;
         tk.nt = m;
-        tk.S = min(32 / ((m + 1) / 2), 32);
+        tk.S = lanes_per_pair((m + 1) / 2);
         tasks[q++] = tk;
         t0 += m;
     }

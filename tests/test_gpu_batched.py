@@ -111,3 +111,24 @@ def test_batched_offsets_are_checked(ctx):
     for bad in ([1, 10], [0, 5, 3, 10], [0, 9]):
         with pytest.raises(sts.StsError):
             sts.sts_tree_build_batched(ctx, pos, bad, p)
+
+
+def test_autotuner_picks_fastest_within_budget():
+    from paper_2401_07361_gb300.autotune import autotune
+
+    pos = W.uniform_points(40962, 90)
+    zeta = W.sh_series_vorticity(pos, 8, seed=3)
+    area = W.equal_areas(len(pos))
+    res = autotune(dev(pos), dev(zeta), dev(area), budget=1e-4, thetas=(0.5, 0.7), degrees=(4, 8),
+                   leaf_sizes=(32, 128), samples=1024, repeats=2)
+    ok = [t for t in res.table if t[4] <= 1e-4]
+    assert res.error <= 1e-4 and ok
+    assert res.ms == min(t[3] for t in ok)
+    # the chosen parameters reproduce the measured accuracy against the oracle direct sum
+    tg = np.random.default_rng(5).choice(len(pos), 256, replace=False)
+    ref = O.direct(pos, zeta, area, targets=tg)
+    with sts.Context() as c:
+        p = res.params(near_fp64_tau=0.05 * 4 * math.pi / len(pos))
+        sts.sts_tree_build(c.h, dev(pos), p)
+        v = sts.sts_velocity(c.h, dev(zeta), dev(area), p).cpu().numpy()
+    assert O.rel_l2(v[tg], ref, area[tg]) <= 3e-4
