@@ -157,6 +157,17 @@ int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* 
                          const int64_t* offsets, int32_t ninst, double dt, double Omega,
                          const sts_params* p, void* stream);
 
+/* on != 0: bve_rk4_step and bve_rk4_step_batched run each step as one recorded CUDA graph.
+ * The first step (and any step whose arguments -- array pointers, n, offsets, dt, Omega,
+ * parameters, stream -- differ from the recorded ones) runs eagerly, which sizes the
+ * buffers (the largest tree, lists and task counts of its four stages, plus 25%), and then
+ * records one step without running it; the next calls replay the recording with no host
+ * synchronisation inside the step.  After a replay the host reads one overflow word: if the
+ * tree needed more levels or any list outgrew its recorded capacity, the step is undone
+ * from its saved start state and redone eagerly, and a new recording is made.  Recording
+ * needs a non-default stream.  on = 0 drops the recording. */
+int sts_set_graph(sts_ctx* ctx, int32_t on);
+
 /* ---- inspection (HOST output buffers; every call synchronises `stream`) -------------- */
 /* info[8] = {n, nodes, leaves, deepest level, far entries, near entries, clusters,
  * evaluation tasks}; the list counts are 0 before the first sts_velocity. */

@@ -29,7 +29,7 @@ void set_error(const char* fmt, ...)
 
 void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     if (c->phase_open[ph]) {
         float ms = 0.f;
         if (cudaEventSynchronize(c->ev[ph][1]) == cudaSuccess &&
@@ -44,7 +44,7 @@ void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 
 void phase_end(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing) return;
+    if (!c->timing || c->capturing) return;
     cudaEventRecord(c->ev[ph][1], s);
     c->phase_open[ph] = true;
 }
@@ -60,7 +60,7 @@ sts_ctx::~sts_ctx()
     offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
     nd_key.release(); nd_geom.release(); nd_norm.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
-    counters.release(); small.release(); inst_off.release(); root_cnt.release();
+    counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
@@ -77,6 +77,7 @@ sts_ctx::~sts_ctx()
     for (int p = 0; p < kNumPhases; p++)
         for (int q = 0; q < 2; q++)
             if (ev[p][q]) cudaEventDestroy(ev[p][q]);
+    if (rk_exec) cudaGraphExecDestroy(rk_exec);
     if (d_status) cudaFree(d_status);
     if (h_pinned) cudaFreeHost(h_pinned);
 }
@@ -249,6 +250,143 @@ int rk4_impl(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_
     return STS_OK;
 }
 
+// Host copies of the device counters after a recorded step ran (they are not read while
+// recording).
+int refresh_counts(sts_ctx* c, cudaStream_t s)
+{
+    if (!c->have_tree || c->nnodes >= 0) return STS_OK;
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p, kDcSize * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    const int64_t* h = c->h_pinned;
+    c->nnodes = h[kDcNodes];
+    c->nleaves = h[kDcLeaves];
+    c->nclusters = h[kDcClusters];
+    c->n_up_tasks = h[kDcUpTasks];
+    c->nfar = h[kDcFar];
+    c->nnear = h[kDcNear];
+    c->nnear_chunks = h[kDcChunks];
+    c->ntasks = h[kDcTasks];
+    c->level_begin.assign(1, 0);
+    c->deepest = 0;
+    for (int l = 1; l <= kMaxLevel + 2 && h[kDcLevel + l] > h[kDcLevel + l - 1]; l++) {
+        c->level_begin.push_back(h[kDcLevel + l]);
+        c->deepest = l - 1;
+    }
+    return STS_OK;
+}
+
+// Buffers for recording a step: the plan's sizes (maxima over the eager step) with slack.
+int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t s)
+{
+    const int64_t n = c->n;
+    auto grow = [](int64_t v, int64_t add) { return v + v / 4 + add; };
+    const int64_t nodes = grow(c->plan.nodes, 64 + 20 * (int64_t)ninst);
+    const int M = nbasis(p->degree);
+    const int64_t upt = grow(c->plan.up_tasks, 64);
+    int rc = reserve_tree_nodes(c, nodes, s);
+    if (rc) return rc;
+    const int64_t big = std::max(n, nodes) + 2;
+    STS_CUDA(c->cluster_slot.reserve(nodes + 1));
+    STS_CUDA(c->cluster_node.reserve(nodes + 1));
+    STS_CUDA(c->flags.reserve(big));
+    STS_CUDA(c->offs.reserve(big));
+    STS_CUDA(c->up_toff.reserve(nodes + 2));
+    STS_CUDA(c->list_cnt.reserve(std::max(3 * n + 3, nodes + 1)));
+    STS_CUDA(c->up_frame.reserve(12 * nodes + 12));
+    STS_CUDA(c->up_tasks.reserve(upt));
+    STS_CUDA(c->prx64.reserve(nodes * M + 1));
+    STS_CUDA(c->prx32.reserve(nodes * M + 1));
+    STS_CUDA(c->up_part.reserve(upt * M + 1));
+    STS_CUDA(c->far_idx.reserve(grow(c->plan.far, 1024)));
+    STS_CUDA(c->far_ent.reserve(grow(c->plan.far, 1024)));
+    STS_CUDA(c->near_idx.reserve(grow(c->plan.near, 1024)));
+    STS_CUDA(c->near_ent.reserve(grow(c->plan.chunks, 1024)));
+    STS_CUDA(c->tasks.reserve(grow(c->plan.tasks, 1024)));
+    STS_CUDA(c->far_off.reserve(n + 1));
+    STS_CUDA(c->near_off.reserve(n + 1));
+    STS_CUDA(c->near_coff.reserve(n + 1));
+    STS_CUDA(c->leaves.reserve(n + 1));
+    STS_CUDA(c->corr.reserve(3 * n + 3));
+    STS_CUDA(c->scan_tmp.reserve(radix_hist_size(n) + 1 + scan_scratch(radix_hist_size(n)) + 2 * scan_scratch(big) + 64));
+    return STS_OK;
+}
+
+// One RK4 step through a recorded graph: the first call (or a call with other arguments)
+// runs the step eagerly, which plans the capacities, then records the step; later calls
+// replay it.  A replay that ran out of a recorded capacity or level count is undone from
+// the saved start state and redone eagerly (and recorded again).
+int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t n, const int64_t* inst_off,
+              const int64_t* off_host, int ninst, double dt, double Omega, const sts_params* p, cudaStream_t s)
+{
+    std::vector<double> key = {(double)n, (double)ninst, dt, Omega, p->theta, (double)p->degree,
+                               (double)p->leaf_size, (double)p->max_level, (double)p->precision, p->near_fp64_tau};
+    std::vector<int64_t> okey = {(int64_t)(uintptr_t)pos, (int64_t)(uintptr_t)zeta, (int64_t)(uintptr_t)area,
+                                 (int64_t)(uintptr_t)s};
+    if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
+    int rc;
+    if (c->rk_exec && key == c->rk_key && okey == c->rk_off_key) {
+        STS_CUDA(cudaGraphLaunch(c->rk_exec, s));
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p + kDcOver, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned + 1, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        const int64_t over = c->h_pinned[0];
+        const int st = ((int32_t*)(c->h_pinned + 1))[0];
+        if (st & kStatusNonfinite) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("bve_rk4_step: non-finite position");
+            return STS_ERR_NONFINITE;
+        }
+        c->have_tree = true;
+        c->have_lists = true;
+        c->nnodes = -1;  // host counts refreshed on demand
+        if (over == 0) return STS_OK;
+        // undo the step and redo it eagerly below
+        STS_CUDA(cudaMemcpyAsync(pos, c->rk_x0.p, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        STS_CUDA(cudaMemcpyAsync(zeta, c->rk_z0.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        STS_CUDA(cudaGraphExecDestroy(c->rk_exec));
+        c->rk_exec = nullptr;
+    }
+    c->plan = Plan();
+    if ((rc = rk4_impl(c, pos, zeta, area, n, inst_off, ninst, dt, Omega, p, s))) return rc;
+    if ((rc = reserve_for_capture(c, p, ninst, s))) return rc;
+    STS_CUDA(cudaStreamSynchronize(s));
+    c->have_tree = c->have_lists = false;  // buffers may have moved; the replay rebuilds them
+    if (c->rk_exec) {
+        cudaGraphExecDestroy(c->rk_exec);
+        c->rk_exec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        set_error("bve_rk4_step: cannot record on this stream (%s); use a non-default stream",
+                  cudaGetErrorString(e));
+        return STS_ERR_CUDA;
+    }
+    c->capturing = true;
+    e = cudaMemsetAsync(c->dc.p + kDcOver, 0, sizeof(int64_t), s);
+    rc = e == cudaSuccess ? rk4_impl(c, pos, zeta, area, n, inst_off, ninst, dt, Omega, p, s) : STS_ERR_CUDA;
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (rc == STS_OK && e2 != cudaSuccess) {
+        set_error("bve_rk4_step: recording failed: %s", cudaGetErrorString(e2));
+        rc = STS_ERR_CUDA;
+    }
+    if (rc == STS_OK) {
+        const cudaError_t e3 = cudaGraphInstantiate(&c->rk_exec, g, 0);
+        if (e3 != cudaSuccess) {
+            set_error("bve_rk4_step: graph instantiation failed: %s", cudaGetErrorString(e3));
+            c->rk_exec = nullptr;
+            rc = STS_ERR_CUDA;
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc == STS_OK) {
+        c->rk_key = key;
+        c->rk_off_key = okey;
+    }
+    return rc;
+}
+
 }  // namespace
 
 namespace {
@@ -283,6 +421,8 @@ int sts_create(sts_ctx** out)
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int64_t));
+    if (e == cudaSuccess) e = c->dc.reserve(sts::kDcSize);
+    if (e == cudaSuccess) e = cudaMemset(c->dc.p, 0, sts::kDcSize * sizeof(int64_t));
     if (e != cudaSuccess) {
         set_error("sts_create: %s", cudaGetErrorString(e));
         delete c;
@@ -407,6 +547,7 @@ int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, in
 {
     int rc = check_ctx(ctx, "bve_rk4_step");
     if (rc || (rc = check_n(n, "bve_rk4_step")) || (rc = check_params(p, "bve_rk4_step"))) return rc;
+    if (ctx->graph_on) return rk4_graph(ctx, pos, zeta, area, n, nullptr, nullptr, 1, dt, Omega, p, S(stream));
     return rk4_impl(ctx, pos, zeta, area, n, nullptr, 1, dt, Omega, p, S(stream));
 }
 
@@ -418,6 +559,7 @@ int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* 
     const int64_t* d_off = nullptr;
     int64_t n = 0;
     if ((rc = upload_offsets(ctx, offsets, ninst, &d_off, &n, "bve_rk4_step_batched", S(stream)))) return rc;
+    if (ctx->graph_on) return rk4_graph(ctx, pos, zeta, area, n, d_off, offsets, ninst, dt, Omega, p, S(stream));
     return rk4_impl(ctx, pos, zeta, area, n, d_off, ninst, dt, Omega, p, S(stream));
 }
 
@@ -425,6 +567,7 @@ int sts_tree_info(sts_ctx* ctx, int64_t* info, void* stream)
 {
     int rc = check_ctx(ctx, "sts_tree_info");
     if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     if (!info) {
         set_error("sts_tree_info: NULL info");
         return STS_ERR_ARG;
@@ -447,6 +590,7 @@ int sts_tree_export(sts_ctx* ctx, int64_t* perm, int32_t* level, uint64_t* key, 
 {
     int rc = check_ctx(ctx, "sts_tree_export");
     if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     if (!ctx->have_tree) {
         set_error("sts_tree_export: no tree");
         return STS_ERR_STATE;
@@ -469,6 +613,7 @@ int sts_lists_export(sts_ctx* ctx, int64_t* far_off, int32_t* far_idx, int64_t* 
 {
     int rc = check_ctx(ctx, "sts_lists_export");
     if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     if (!ctx->have_lists) {
         set_error("sts_lists_export: no lists (call sts_velocity first)");
         return STS_ERR_STATE;
@@ -486,6 +631,7 @@ int sts_clusters_export(sts_ctx* ctx, int32_t* node_ids, double* yt, double* W, 
 {
     int rc = check_ctx(ctx, "sts_clusters_export");
     if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     if (ctx->up_degree < 0) {
         set_error("sts_clusters_export: no proxy weights (call sts_velocity first)");
         return STS_ERR_STATE;
@@ -531,6 +677,7 @@ int sts_stats(sts_ctx* ctx, int64_t* stats, void* stream)
 {
     int rc = check_ctx(ctx, "sts_stats");
     if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     if (!stats) {
         set_error("sts_stats: NULL stats");
         return STS_ERR_ARG;
@@ -598,6 +745,18 @@ int sts_launch_count(int64_t* out)
         return STS_ERR_ARG;
     }
     *out = (int64_t)g_launches.load(std::memory_order_relaxed);
+    return STS_OK;
+}
+
+int sts_set_graph(sts_ctx* ctx, int32_t on)
+{
+    int rc = check_ctx(ctx, "sts_set_graph");
+    if (rc) return rc;
+    ctx->graph_on = on != 0;
+    if (!ctx->graph_on && ctx->rk_exec) {
+        cudaGraphExecDestroy(ctx->rk_exec);
+        ctx->rk_exec = nullptr;
+    }
     return STS_OK;
 }
 

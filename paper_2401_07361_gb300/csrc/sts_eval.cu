@@ -327,12 +327,12 @@ k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __re
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
              const float4* __restrict__ src32, const double4* __restrict__ src64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
-             double* __restrict__ vel)
+             double* __restrict__ vel, const int64_t* __restrict__ ntasks_d)
 {
     __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStagePad];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
-    if (ti >= ntasks) return;
+    if (ti >= *ntasks_d) return;
     const Task tk = tasks[ti];
     switch (tk.S) {
         case 1:
@@ -359,12 +359,13 @@ __global__ void __launch_bounds__(kEvalWarps64 * 32)
 k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
             const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
-            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel)
+            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel,
+            const int64_t* __restrict__ ntasks_d)
 {
     __shared__ double4 sbuf[kEvalWarps64][kStage];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t ti = (int64_t)blockIdx.x * kEvalWarps64 + w;
-    if (ti >= ntasks) return;
+    if (ti >= *ntasks_d) return;
     const Task tk = tasks[ti];
     const int p = (tk.nt + 1) >> 1, S = tk.S;
     const int j = lane % p;
@@ -425,13 +426,13 @@ k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __res
 }
 
 // ------------------------------------------------------------------------ counts
-__global__ void k_count(int64_t nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_count(const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
                         const int32_t* __restrict__ count, const int64_t* __restrict__ far_off,
                         const int64_t* __restrict__ near_coff, const NearEntry* __restrict__ near_ent,
                         int M, unsigned long long* __restrict__ stats)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaves) return;
+    if (L >= *nleaves_p) return;
     const unsigned long long nl = (unsigned long long)count[leaves[L]];
     const unsigned long long pc = nl * (unsigned long long)M * (unsigned long long)(far_off[L + 1] - far_off[L]);
     unsigned long long ns = 0;
@@ -559,12 +560,14 @@ __global__ void k_direct_finish(const double* __restrict__ part, int splits, int
 int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
 {
     const int M = nbasis(degree);
-    if (c->ntasks == 0) return STS_OK;
+    const int64_t ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
+    if (ntasks <= 0) return STS_OK;
+    const int64_t* nt_d = c->dc.p + kDcTasks;
     if (precision == STS_FP64) {
         phase_begin(c, kPhEval, s);
-        (k_eval_fp64<<<blocks(c->ntasks, kEvalWarps64), kEvalWarps64 * 32, 0, s>>>(
-             c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx64.p, M,
-             c->src64.p, c->perm.p, vel), note_launch());
+        (k_eval_fp64<<<blocks(ntasks, kEvalWarps64), kEvalWarps64 * 32, 0, s>>>(
+             c->tasks.p, ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx64.p, M,
+             c->src64.p, c->perm.p, vel, nt_d), note_launch());
         phase_end(c, kPhEval, s);
     } else {
         double* corr = nullptr;
@@ -572,7 +575,7 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         // the dummy targets of idle lanes (at distance ~1e3) out of the FP64 path
         tau = std::min(tau, 2.0);
         if (tau > 0.0) {
-            STS_CUDA(c->corr.reserve(3 * c->n + 3));
+            if (!c->capturing) STS_CUDA(c->corr.reserve(3 * c->n + 3));
             STS_CUDA(cudaMemsetAsync(c->corr.p, 0, 3 * c->n * sizeof(double), s));
             corr = c->corr.p;
         }
@@ -580,9 +583,9 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         const float tau2 = corr ? (float)(2.0 * tau) : 0.f;
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
         phase_begin(c, kPhEval, s);
-        (k_eval_mixed<<<blocks(c->ntasks, kEvalWarps), kEvalWarps * 32, 0, s>>>(
-             c->tasks.p, c->ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx32.p, M,
-             c->src32.p, c->src64.p, c->perm.p, tau2, tau_r, corr, vel), note_launch());
+        (k_eval_mixed<<<blocks(ntasks, kEvalWarps), kEvalWarps * 32, 0, s>>>(
+             c->tasks.p, ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx32.p, M,
+             c->src32.p, c->src64.p, c->perm.p, tau2, tau_r, corr, vel, nt_d), note_launch());
         phase_end(c, kPhEval, s);
     }
     STS_LAUNCH_CHECK();
@@ -593,10 +596,11 @@ int count_interactions(sts_ctx* c, int degree, cudaStream_t s)
 {
     STS_CUDA(c->d_stats.reserve(2));
     STS_CUDA(cudaMemsetAsync(c->d_stats.p, 0, 2 * sizeof(unsigned long long), s));
-    if (c->nleaves > 0)
-        (k_count<<<blocks(c->nleaves, 128), 128, 0, s>>>(c->nleaves, c->leaves.p, c->nd_count.p,
-                                                       c->far_off.p, c->near_coff.p, c->near_ent.p,
-                                                       nbasis(degree), c->d_stats.p), note_launch());
+    const int64_t L = c->nleaves > 0 ? c->nleaves : c->n;
+    if (L > 0)
+        (k_count<<<blocks(L, 128), 128, 0, s>>>(c->dc.p + kDcLeaves, c->leaves.p, c->nd_count.p, c->far_off.p,
+                                               c->near_coff.p, c->near_ent.p, nbasis(degree), c->d_stats.p),
+         note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }

@@ -113,6 +113,23 @@ struct Task {
 
 enum Phase { kPhBuild = 0, kPhSort, kPhLists, kPhPrep, kPhUpward, kPhEval, kPhDirect, kNumPhases };
 
+// Device counters (ctx->dc, int64): every kernel reads its element counts from here, so no
+// launch depends on a host-side count and a whole RK4 step can be recorded as a graph.
+enum DevCount {
+    kDcRoots = 0, kDcLeaves, kDcClusters, kDcUpTasks, kDcFar, kDcNear, kDcChunks, kDcTasks, kDcNodes,
+    kDcOver,   // overflow bits: 1 node capacity, 2 levels, 4 list or task capacity
+    kDcTmp,
+    kDcLevel = 16,  // level_begin[0 .. kMaxLevel + 3]
+    kDcSize = 64
+};
+
+// Sizes seen by the last eager build (maxima over a step), used as capacities when recording.
+struct Plan {
+    int64_t n = -1;
+    int ninst = 0, leaf_size = 0, max_level = 0, depth = 0;
+    int64_t nodes = 0, up_tasks = 0, far = 0, near = 0, chunks = 0, tasks = 0, clusters = 0;
+};
+
 }  // namespace sts
 
 struct sts_ctx {
@@ -151,6 +168,15 @@ struct sts_ctx {
     sts::DevBuf<int32_t> root_cnt, root_flag, face_node;  // [20 * ninst] per (instance, face)
     sts::DevBuf<int64_t> root_id, root_start;             // [20 * ninst + 1] scans
     sts::DevBuf<int64_t> small;          // [16] values gathered for one host read
+    sts::DevBuf<int64_t> dc;             // [kDcSize] device counters
+    bool capturing = false;              // recording a graph: no host reads or allocations
+    bool consts_ok = false;              // icosahedron tables uploaded
+    sts::Plan plan;
+    // RK4 step recorded as a CUDA graph (sts_set_graph) and the arguments it was recorded for
+    bool graph_on = false;
+    cudaGraphExec_t rk_exec = nullptr;
+    std::vector<double> rk_key;
+    std::vector<int64_t> rk_off_key;
     sts::DevBuf<int32_t> leaves;         // leaf node ids in depth-first order
     sts::DevBuf<int32_t> slot_leaf;      // [n] sorted slot -> depth-first leaf index
 
@@ -217,8 +243,9 @@ RefTable* get_ref(sts_ctx* ctx, int d);
 // ---- scans and sorting (sts_scan.cu) -----------------------------------------------
 // out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total.  scratch: >= scan_scratch(n)
 int64_t scan_scratch(int64_t n);
+// n_dev: optional device count (then n is its upper bound, used to size the grid).
 void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch,
-                        cudaStream_t s);
+                        cudaStream_t s, const int64_t* n_dev = nullptr);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.  Result in
 // key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n).
 int64_t radix_hist_size(int64_t n);
@@ -231,6 +258,8 @@ void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* v
 int tree_build(sts_ctx* ctx, const double* pos, int64_t n, const int64_t* inst_off, int ninst,
                int leaf_size, int max_level, cudaStream_t s);
 int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
+// node-table capacity (contents are not kept)
+int reserve_tree_nodes(sts_ctx* ctx, int64_t nodes, cudaStream_t s);
 // out[0..3] = *a, *b, *c, *d (0 for NULL), out[4] = status word: one host read for all.
 void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,
                    const int* status, int64_t* out, cudaStream_t s);

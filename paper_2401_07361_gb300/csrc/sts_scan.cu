@@ -44,9 +44,11 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t* sh, int64_t* total)
     return woff + x - v;
 }
 
-__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ part)
+__global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ nd,
+                              int64_t* __restrict__ part)
 {
     __shared__ int64_t sh[kScanThreads / 32];
+    if (nd) n = *nd;
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t s = 0;
 #pragma unroll
@@ -73,9 +75,10 @@ __global__ void k_scan_top(int64_t* part, int64_t nb)
     if (threadIdx.x == 0) part[nb] = carry;
 }
 
-__global__ void k_scan_down(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ part,
-                            int64_t nb, int64_t* __restrict__ out)
+__global__ void k_scan_down(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ nd,
+                            const int64_t* __restrict__ part, int64_t nb, int64_t* __restrict__ out)
 {
+    if (nd) n = *nd;
     __shared__ int64_t sh[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
@@ -174,8 +177,10 @@ k_radix_scatter(const uint32_t* __restrict__ key, const int32_t* __restrict__ va
 int64_t scan_scratch(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
 
 // Whole scan in one block for n <= kScanTile (most per-level and per-leaf scans).
-__global__ void k_scan_single(const int32_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
+__global__ void k_scan_single(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ nd,
+                              int64_t* __restrict__ out)
 {
+    if (nd) n = *nd;
     __shared__ int64_t sh[kScanThreads / 32];
     const int64_t base = (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
@@ -195,19 +200,18 @@ __global__ void k_scan_single(const int32_t* __restrict__ in, int64_t n, int64_t
     if (threadIdx.x == 0) out[n] = tot;
 }
 
-void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s)
+void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s,
+                        const int64_t* n_dev)
 {
+    // with n_dev, n is only a capacity: the kernels read the count from the device
     if (n <= kScanTile) {
-        (k_scan_single<<<1, kScanThreads, 0, s>>>(in, n, out), note_launch());
+        (k_scan_single<<<1, kScanThreads, 0, s>>>(in, n, n_dev, out), note_launch());
         return;
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > 0) (k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch), note_launch());
+    (k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, n_dev, scratch), note_launch());
     (k_scan_top<<<1, 1024, 0, s>>>(scratch, nb), note_launch());
-    if (nb > 0)
-        (k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, scratch, nb, out), note_launch());
-    else
-        cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    (k_scan_down<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, n_dev, scratch, nb, out), note_launch());
 }
 
 int64_t radix_hist_size(int64_t n) { return 256 * ((n + kRadixTile - 1) / kRadixTile) + 1; }

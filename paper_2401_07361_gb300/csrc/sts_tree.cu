@@ -208,34 +208,40 @@ __global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node,
 }
 
 // ------------------------------------------------------------------------- level l
-__global__ void k_level_nodes(int32_t lb, int32_t le, int leaf_size, int max_level,
+// The level kernels read the node range of level l from the device array lvl: level l holds
+// nodes [lvl[l], lvl[l + 1]).  Node kernels stride over that range, so any grid size works
+// and the launches need no host-side count (the whole build can be captured in a graph).
+__global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_size, int max_level,
                               const int32_t* __restrict__ level, const int32_t* __restrict__ count,
                               const double* __restrict__ geom, int32_t* __restrict__ leaf,
                               double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc)
 {
-    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (p >= le) return;
-    const bool split = count[p] > leaf_size && level[p] < max_level;
-    leaf[p] = split ? 0 : 1;
-    if (!split) return;
-    const double* g = geom + 13 * (int64_t)p;
-    const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
-    const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
-    double* nn = norm + 9 * (int64_t)p;
-    const g3 n3[3] = {gcross(m12, m31), gcross(m23, m12), gcross(m31, m23)};
-    for (int a = 0; a < 3; a++) {
-        gst(nn + 3 * a, n3[a]);
-        const float thr = 1e-6f * (float)(fabs(n3[a].x) + fabs(n3[a].y) + fabs(n3[a].z));
-        norm32[3 * (int64_t)p + a] = make_float4((float)n3[a].x, (float)n3[a].y, (float)n3[a].z, thr);
+    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
+    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
+         p += (int32_t)(gridDim.x * blockDim.x)) {
+        const bool split = count[p] > leaf_size && level[p] < max_level;
+        leaf[p] = split ? 0 : 1;
+        if (!split) continue;
+        const double* g = geom + 13 * (int64_t)p;
+        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+        const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+        double* nn = norm + 9 * (int64_t)p;
+        const g3 n3[3] = {gcross(m12, m31), gcross(m23, m12), gcross(m31, m23)};
+        for (int a = 0; a < 3; a++) {
+            gst(nn + 3 * a, n3[a]);
+            const float thr = 1e-6f * (float)(fabs(n3[a].x) + fabs(n3[a].y) + fabs(n3[a].z));
+            norm32[3 * (int64_t)p + a] = make_float4((float)n3[a].x, (float)n3[a].y, (float)n3[a].z, thr);
+        }
+        cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
     }
-    cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
 }
 
-__global__ void k_level_particles(int32_t lb, const double* __restrict__ pos, int64_t n,
-                                  const int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
+__global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const double* __restrict__ pos,
+                                  int64_t n, const int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
                                   const double* __restrict__ norm, const float4* __restrict__ norm32,
                                   uint8_t* __restrict__ digit, int32_t* __restrict__ cc)
 {
+    const int32_t lb = (int32_t)lvl[l];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int p = -1, d = 0;
     bool active = false;
@@ -279,72 +285,114 @@ __global__ void k_level_particles(int32_t lb, const double* __restrict__ pos, in
     agg_inc(cc, 4 * p + d, active);
 }
 
-__global__ void k_level_nch(int32_t lb, int32_t le, const int32_t* __restrict__ leaf,
-                            const int32_t* __restrict__ cc, int32_t* __restrict__ nch)
+// Number of children of every node of level l (0 for leaves) into nch[p - lb]; nl = nodes.
+__global__ void k_level_nch(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ leaf,
+                            const int32_t* __restrict__ cc, int32_t* __restrict__ nch, int64_t* __restrict__ nl)
 {
-    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (p >= le) return;
-    int c = 0;
-    if (!leaf[p])
-        for (int d = 0; d < 4; d++) c += cc[4 * p + d] > 0;
-    nch[p - lb] = c;
+    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nl = le - lb;
+    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
+         p += (int32_t)(gridDim.x * blockDim.x)) {
+        int c = 0;
+        if (!leaf[p])
+            for (int d = 0; d < 4; d++) c += cc[4 * p + d] > 0;
+        nch[p - lb] = c;
+    }
 }
 
-__global__ void k_level_children(int32_t lb, int32_t le, const int64_t* __restrict__ off,
-                                 const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
-                                 int32_t* parent, int32_t* first_child, int32_t* nchild,
-                                 int32_t* start, int32_t* count, int32_t* leaf, double* geom,
-                                 int32_t* __restrict__ child)
+// Children of level l numbered in key order from le = lvl[l + 1] on (off = scan of nch).
+// A child beyond the node capacity is not created: its particles stay with the parent and
+// the overflow bit is set, so a captured build reports it instead of writing out of range.
+__global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
+                                 int64_t cap, const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
+                                 int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
+                                 int32_t* count, int32_t* leaf, double* geom, int32_t* __restrict__ child,
+                                 int64_t* __restrict__ over)
 {
-    const int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (p >= le) return;
-    if (leaf[p]) {
-        first_child[p] = -1;
-        nchild[p] = 0;
-        return;
-    }
-    const double* g = geom + 13 * (int64_t)p;
-    const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
-    const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
-    const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
-    int32_t id = le + (int32_t)off[p - lb];
-    const int32_t first = id;
-    int32_t st = start[p];
-    const int32_t lv = level[p] + 1;
-    const uint64_t kp = key[p];
-    int nc = 0;
-    for (int d = 0; d < 4; d++) {
-        const int32_t c = cc[4 * p + d];
-        if (c == 0) {
-            child[4 * p + d] = -1;
+    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
+    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
+         p += (int32_t)(gridDim.x * blockDim.x)) {
+        if (leaf[p]) {
+            first_child[p] = -1;
+            nchild[p] = 0;
             continue;
         }
-        child[4 * p + d] = id;
-        level[id] = lv;
-        key[id] = kp * 4u + (uint64_t)d;
-        parent[id] = p;
-        first_child[id] = -1;
-        nchild[id] = 0;
-        start[id] = st;
-        count[id] = c;
-        leaf[id] = 0;
-        node_geometry(geom + 13 * (int64_t)id, cv[d][0], cv[d][1], cv[d][2]);
-        st += c;
-        id++;
-        nc++;
+        const double* g = geom + 13 * (int64_t)p;
+        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+        const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+        const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
+        int32_t id = le + (int32_t)off[p - lb];
+        const int32_t first = id;
+        int32_t st = start[p];
+        const int32_t lv = level[p] + 1;
+        const uint64_t kp = key[p];
+        int nc = 0;
+        for (int d = 0; d < 4; d++) {
+            const int32_t c = cc[4 * p + d];
+            if (c == 0) {
+                child[4 * p + d] = -1;
+                continue;
+            }
+            if (id >= cap) {
+                child[4 * p + d] = p;
+                atomicOr((unsigned long long*)over, 1ull);
+                st += c;
+                continue;
+            }
+            child[4 * p + d] = id;
+            level[id] = lv;
+            key[id] = kp * 4u + (uint64_t)d;
+            parent[id] = p;
+            first_child[id] = -1;
+            nchild[id] = 0;
+            start[id] = st;
+            count[id] = c;
+            leaf[id] = 0;
+            node_geometry(geom + 13 * (int64_t)id, cv[d][0], cv[d][1], cv[d][2]);
+            st += c;
+            id++;
+            nc++;
+        }
+        first_child[p] = nc ? first : -1;
+        nchild[p] = nc;
     }
-    first_child[p] = first;
-    nchild[p] = nc;
 }
 
-__global__ void k_level_assign(int32_t lb, int32_t le, int64_t n, const int32_t* __restrict__ leaf,
+// lvl[l + 2] = end of level l + 1 (capped at the node capacity).
+__global__ void k_level_end(int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
+                            const int64_t* __restrict__ nl, int64_t cap)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) lvl[l + 2] = min(lvl[l + 1] + off[*nl], cap);
+}
+
+__global__ void k_level_assign(const int64_t* __restrict__ lvl, int l, int64_t n, const int32_t* __restrict__ leaf,
                                const int32_t* __restrict__ child, const uint8_t* __restrict__ digit,
                                int32_t* __restrict__ nodeof)
 {
+    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = nodeof[i];
     if (p >= lb && p < le && leaf[p] == 0) nodeof[i] = child[4 * p + digit[i]];
+}
+
+// After the level loop: nodes = lvl[last]; a last level that still produced children means
+// the build ran out of planned levels (overflow).
+__global__ void k_levels_done(const int64_t* __restrict__ lvl, int last, int64_t* __restrict__ nnodes,
+                              int64_t* __restrict__ over)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *nnodes = lvl[last];
+    if (lvl[last + 1] > lvl[last]) atomicOr((unsigned long long*)over, 2ull);
+}
+
+// Level range of the roots: lvl[0] = 0, lvl[1] = number of roots.
+__global__ void k_level0(int64_t* __restrict__ lvl, const int64_t* __restrict__ nroots)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        lvl[0] = 0;
+        lvl[1] = *nroots;
+    }
 }
 
 // ------------------------------------------------------------------------- sorting
@@ -407,7 +455,7 @@ __device__ __forceinline__ bool mac_filtered(float4 ct, float4 cs, float theta32
 // more than N_T particles) or near; one that fails is near if it is a leaf, else its
 // children are visited in digit order.  fill = 0 counts far nodes, near nodes and near
 // chunks per leaf; fill = 1 writes them at the scanned offsets.
-__global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
                         const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
                         const int32_t* __restrict__ level, double theta, int leaf_size,
                         const double* __restrict__ geom, const float4* __restrict__ c32,
@@ -419,10 +467,16 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
                         const int64_t* __restrict__ chunk_po,
                         int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
                         FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
-                        int* __restrict__ status)
+                        int64_t far_cap, int64_t near_cap, int64_t chunk_cap, int64_t ldc,
+                        int* __restrict__ status, int64_t* __restrict__ over)
 {
+    const int64_t nleaves = *nleaves_p;
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= nleaves) return;
+    if (fill && (far_po[L + 1] > far_cap || near_po[L + 1] > near_cap || chunk_po[L + 1] > chunk_cap)) {
+        atomicOr((unsigned long long*)over, 4ull);  // recorded capacities too small
+        return;
+    }
     const int32_t t = leaves[L];
     // roots of the target leaf's own instance: root key (instance * 20 + face) of the leaf
     const uint64_t rk = key[t] >> (2 * level[t]);
@@ -493,16 +547,35 @@ __global__ void k_lists(int fill, int64_t nleaves, const int32_t* __restrict__ l
     }
     if (!fill) {
         cnt[L] = (int32_t)nf;
-        cnt[nleaves + L] = (int32_t)nn;
-        cnt[2 * nleaves + L] = (int32_t)nch;
+        cnt[ldc + L] = (int32_t)nn;
+        cnt[2 * ldc + L] = (int32_t)nch;
     }
 }
 
+// List and task totals (scanned offsets read at index nleaves) into the device counters.
+__global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restrict__ far_off,
+                              const int64_t* __restrict__ near_off, const int64_t* __restrict__ chunk_off,
+                              const int64_t* __restrict__ toff)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t L = dc[kDcLeaves];
+    dc[kDcFar] = far_off[L];
+    dc[kDcNear] = near_off[L];
+    dc[kDcChunks] = chunk_off[L];
+    dc[kDcTasks] = toff[L];
+}
+
+__global__ void k_copy_count(const int64_t* __restrict__ src, int64_t* __restrict__ dst)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
+}
+
 // FP32 copies of the node centres and radii for the pre-filtered MAC.
-__global__ void k_node_f32(int64_t nnodes, const double* __restrict__ geom, float4* __restrict__ c32)
+__global__ void k_node_f32(const int64_t* __restrict__ nnodes, const double* __restrict__ geom,
+                           float4* __restrict__ c32)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nnodes) return;
+    if (p >= *nnodes) return;
     const double* g = geom + 13 * p;
     c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
 }
@@ -535,20 +608,25 @@ __device__ int task_split(int nt)
     return best;
 }
 
-__global__ void k_task_count(int64_t nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
                              const int32_t* __restrict__ count, int32_t* __restrict__ ntask)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaves) return;
+    if (L >= *nleaves) return;
     ntask[L] = task_split(count[leaves[L]]);
 }
 
-__global__ void k_task_fill(int64_t nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
                             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-                            const int64_t* __restrict__ toff, Task* __restrict__ tasks)
+                            const int64_t* __restrict__ toff, int64_t cap, Task* __restrict__ tasks,
+                            int64_t* __restrict__ over)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaves) return;
+    if (L >= *nleaves) return;
+    if (toff[L + 1] > cap) {
+        atomicOr((unsigned long long*)over, 4ull);
+        return;
+    }
     const int32_t id = leaves[L];
     const int32_t st = start[id], c = count[id];
     const int k = (int)(toff[L + 1] - toff[L]);
@@ -610,12 +688,15 @@ int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
     STS_CUDA(c->nd_geom.grow(13 * need, 13 * keep, s));
     STS_CUDA(c->nd_norm.grow(9 * need, 9 * keep, s));
     STS_CUDA(c->nd_norm32.grow(3 * need, 3 * keep, s));
+    STS_CUDA(c->nd_c32.grow(need, keep, s));
     STS_CUDA(c->nd_cc.grow(4 * need, 4 * keep, s));
     STS_CUDA(c->nd_child.grow(4 * need, 4 * keep, s));
     return STS_OK;
 }
 
 }  // namespace
+
+int reserve_tree_nodes(sts_ctx* c, int64_t nodes, cudaStream_t s) { return grow_nodes(c, nodes, 0, s); }
 
 void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d, const int* status,
                    int64_t* out, cudaStream_t s)
@@ -639,7 +720,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         c->have_tree = true;
         return STS_OK;
     }
-    {
+    if (!c->consts_ok) {  // the icosahedron tables, uploaded once (never while recording)
+        c->consts_ok = true;
         double V[12][3], C[20][3], FV[20][3][3];
         int F[20][3];
         icosahedron(V, F, C);
@@ -668,6 +750,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_CUDA(c->hist.reserve(hs));
     STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
     STS_CUDA(c->counters.reserve(64));
+    STS_CUDA(c->small.reserve(16));
     const int32_t nkeys = 20 * ninst;
     if (grow_nodes(c, nkeys + 80, 0, s)) return STS_ERR_CUDA;
     STS_CUDA(c->root_cnt.reserve(nkeys + 1));
@@ -692,54 +775,84 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
                                             c->nd_geom.p), note_launch());
     STS_LAUNCH_CHECK();
     (k_assign_roots<<<blocks(n, T), T, 0, s>>>(n, c->face_node.p, c->nodeof.p), note_launch());
-    int64_t nroots = 0;
-    {
-        STS_CUDA(c->small.reserve(16));
+    int64_t* dc = c->dc.p;
+    int64_t* lvl = dc + kDcLevel;
+    const bool cap = c->capturing;  // recording a graph: no host reads, planned capacities
+    if (!cap) STS_CUDA(cudaMemsetAsync(dc + kDcOver, 0, sizeof(int64_t), s));
+    (k_level0<<<1, 32, 0, s>>>(lvl, c->root_id.p + nkeys), note_launch());
+    int64_t lb = 0, le = 0;
+    if (!cap) {
         (k_gather<<<1, 32, 0, s>>>(c->root_id.p + nkeys, nullptr, nullptr, nullptr, c->d_status, c->small.p),
          note_launch());
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         STS_CUDA(cudaStreamSynchronize(s));
-        nroots = c->h_pinned[0];
+        le = c->h_pinned[0];
         if (c->h_pinned[4] & kStatusNonfinite) {
             STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
             set_error("sts_tree_build: non-finite position");
             return STS_ERR_NONFINITE;
         }
     }
-    int64_t lb = 0, le = nroots;
-    c->level_begin.push_back(0);
-    int level = 0;
-    while (true) {
-        c->level_begin.push_back(le);
-        const int64_t nl = le - lb;
-        if (grow_nodes(c, le + 4 * nl, le, s)) return STS_ERR_CUDA;
-        (k_level_nodes<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, leaf_size, max_level,
-                                                   c->nd_level.p, c->nd_count.p, c->nd_geom.p,
-                                                   c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p), note_launch());
-        (k_level_particles<<<blocks(n, T), T, 0, s>>>((int32_t)lb, c->pos.p, n, c->nodeof.p,
-                                                      c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->digit.p,
-                                                      c->nd_cc.p), note_launch());
-        (k_level_nch<<<blocks(nl, T), T, 0, s>>>((int32_t)lb, (int32_t)le, c->nd_leaf.p, c->nd_cc.p,
-                                                c->flags.p), note_launch());
-        exclusive_scan_i32(c->flags.p, c->offs.p, nl, c->scan_tmp.p, s);
-        (k_level_children<<<blocks(nl, T), T, 0, s>>>(
-            (int32_t)lb, (int32_t)le, c->offs.p, c->nd_cc.p, c->nd_level.p, c->nd_key.p,
-            c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-            c->nd_leaf.p, c->nd_geom.p, c->nd_child.p), note_launch());
-        (k_level_assign<<<blocks(n, T), T, 0, s>>>((int32_t)lb, (int32_t)le, n, c->nd_leaf.p,
-                                                  c->nd_child.p, c->digit.p, c->nodeof.p), note_launch());
+    // levels: eagerly until a level adds no node (one host read per level), or, while
+    // recording, the planned number of levels plus one that must come out empty
+    const int nlev = cap ? std::min(c->plan.depth + 2, max_level + 1) : max_level + 1;
+    const int64_t node_cap = cap ? (int64_t)c->nd_level.cap : 0;
+    const unsigned gnode = cap ? (unsigned)std::min<int64_t>(4096, (node_cap + T - 1) / T) : 0;
+    int level = 0, last = 0;
+    c->level_begin.assign(1, 0);
+    for (level = 0; level < nlev; level++) {
+        int64_t capn;
+        unsigned g;
+        if (!cap) {
+            c->level_begin.push_back(le);
+            const int64_t nl = le - lb;
+            if (grow_nodes(c, le + 4 * nl, le, s)) return STS_ERR_CUDA;
+            capn = (int64_t)c->nd_level.cap;
+            g = blocks(std::max<int64_t>(nl, 1), T);
+        } else {
+            capn = node_cap;
+            g = gnode;
+        }
+        (k_level_nodes<<<g, T, 0, s>>>(lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p,
+                                       c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p),
+         note_launch());
+        (k_level_particles<<<blocks(n, T), T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_leaf.p,
+                                                      c->nd_norm.p, c->nd_norm32.p, c->digit.p, c->nd_cc.p),
+         note_launch());
+        (k_level_nch<<<g, T, 0, s>>>(lvl, level, c->nd_leaf.p, c->nd_cc.p, c->flags.p, dc + kDcTmp),
+         note_launch());
+        exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_tmp.p, s,
+                           dc + kDcTmp);
+        (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, capn, c->nd_cc.p, c->nd_level.p, c->nd_key.p,
+                                          c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
+                                          c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p, dc + kDcOver),
+         note_launch());
+        (k_level_end<<<1, 32, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn), note_launch());
+        (k_level_assign<<<blocks(n, T), T, 0, s>>>(lvl, level, n, c->nd_leaf.p, c->nd_child.p, c->digit.p,
+                                                  c->nodeof.p), note_launch());
         STS_LAUNCH_CHECK();
-        int64_t added = 0;
-        if (read_i64(c, c->offs.p + nl, &added, s)) return STS_ERR_CUDA;
-        if (added == 0) break;
-        lb = le;
-        le += added;
-        level++;
+        if (!cap) {
+            int64_t next = 0;
+            if (read_i64(c, lvl + level + 2, &next, s)) return STS_ERR_CUDA;
+            if (next == le) break;
+            lb = le;
+            le = next;
+        }
     }
-    c->nnodes = le;
-    c->deepest = level;
-    STS_CUDA(c->nd_c32.reserve(le + 1));
-    (k_node_f32<<<blocks(le, T), T, 0, s>>>(le, c->nd_geom.p, c->nd_c32.p), note_launch());
+    last = cap ? nlev : level + 1;
+    (k_levels_done<<<1, 32, 0, s>>>(lvl, last, dc + kDcNodes, dc + kDcOver), note_launch());
+    if (!cap) {
+        c->nnodes = le;
+        c->deepest = level;
+        c->plan.nodes = std::max(c->plan.nodes, le);
+        c->plan.depth = std::max(c->plan.depth, level);
+    } else {
+        c->nnodes = -1;  // known after the graph runs
+        c->deepest = -1;
+    }
+    const int64_t nodes_grid = cap ? node_cap : c->nnodes;
+    (k_node_f32<<<blocks(std::max<int64_t>(nodes_grid, 1), T), T, 0, s>>>(dc + kDcNodes, c->nd_geom.p, c->nd_c32.p),
+     note_launch());
 
     phase_begin(c, kPhSort, s);
     (k_sort_keys<<<blocks(n, T), T, 0, s>>>(c->nodeof.p, n, c->nd_start.p, c->skey.p, c->perm.p), note_launch());
@@ -751,9 +864,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
                      scan_out, scan_scr, s);
     (k_leaf_flags<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->nd_start.p, n, c->flags.p), note_launch());
     exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_tmp.p, s);
-    // the leaf count is read back together with the cluster counts (small[8])
-    STS_CUDA(c->small.reserve(16));
-    (k_gather<<<1, 32, 0, s>>>(c->offs.p + n, nullptr, nullptr, nullptr, c->d_status, c->small.p + 8), note_launch());
+    (k_copy_count<<<1, 32, 0, s>>>(c->offs.p + n, c->dc.p + kDcLeaves), note_launch());
     STS_CUDA(c->leaves.reserve(n + 1));
     (k_leaf_list<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->flags.p, c->offs.p, n,
                                            c->leaves.p, c->slot_leaf.p), note_launch());
@@ -767,63 +878,70 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
 int build_lists(sts_ctx* c, double theta, cudaStream_t s)
 {
     c->have_lists = false;
-    const int64_t L = c->nleaves;
+    const bool cap = c->capturing;
+    const int64_t L = cap ? c->n : c->nleaves;  // leaf count or its bound
     const int T = 128;
-    STS_CUDA(c->list_cnt.reserve(3 * L + 3));
-    STS_CUDA(c->far_off.reserve(L + 1));
-    STS_CUDA(c->near_off.reserve(L + 1));
-    STS_CUDA(c->near_coff.reserve(L + 1));
-    STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
+    int64_t* dc = c->dc.p;
+    if (!cap) {
+        STS_CUDA(c->list_cnt.reserve(3 * L + 3));
+        STS_CUDA(c->far_off.reserve(L + 1));
+        STS_CUDA(c->near_off.reserve(L + 1));
+        STS_CUDA(c->near_coff.reserve(L + 1));
+        STS_CUDA(c->flags.reserve(L + 1));
+        STS_CUDA(c->offs.reserve(L + 1));
+        STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
+    }
     int64_t* far_po = c->far_off.p;
     int64_t* near_po = c->near_off.p;
     int64_t* chunk_po = c->near_coff.p;
-    if (L > 0)
-        (k_lists<<<blocks(L, T), T, 0, s>>>(0, L, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
-                                           c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p,
-                                           c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                                           c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr, nullptr, nullptr,
-                                           nullptr, nullptr, nullptr, c->d_status), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s);
-    exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s);
-    const int64_t np = L;
+    const unsigned g = blocks(std::max<int64_t>(L, 1), T);
+    (k_lists<<<g, T, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
+                             c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
+                             c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->d_status,
+                             dc + kDcOver), note_launch());  // list_cnt: three rows of stride L
+    exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
+    exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
+    exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
-    STS_CUDA(c->flags.reserve(L + 1));
-    STS_CUDA(c->offs.reserve(L + 1));
-    STS_CUDA(c->small.reserve(16));
-    if (L > 0) (k_task_count<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s);
-    (k_gather<<<1, 32, 0, s>>>(far_po + np, near_po + np, c->offs.p + L, chunk_po + np, c->d_status, c->small.p),
-     note_launch());
+    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s, dc + kDcLeaves);
+    (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po, c->offs.p), note_launch());
     STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    const int64_t nfar = c->h_pinned[0], nnear = c->h_pinned[1], ntasks = c->h_pinned[2];
-    const int64_t nchunks = c->h_pinned[3];
-    if (c->h_pinned[4] & kStatusCapacity) {
-        STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
-        set_error("interaction lists: traversal stack overflow");
-        return STS_ERR_CAPACITY;
+    if (!cap) {
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned + 16, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        if (((int32_t*)(c->h_pinned + 16))[0] & kStatusCapacity) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("interaction lists: traversal stack overflow");
+            return STS_ERR_CAPACITY;
+        }
+        c->nfar = c->h_pinned[kDcFar];
+        c->nnear = c->h_pinned[kDcNear];
+        c->nnear_chunks = c->h_pinned[kDcChunks];
+        c->ntasks = c->h_pinned[kDcTasks];
+        c->plan.far = std::max(c->plan.far, c->nfar);
+        c->plan.near = std::max(c->plan.near, c->nnear);
+        c->plan.chunks = std::max(c->plan.chunks, c->nnear_chunks);
+        c->plan.tasks = std::max(c->plan.tasks, c->ntasks);
+        STS_CUDA(c->far_idx.reserve(c->nfar + 1));
+        STS_CUDA(c->near_idx.reserve(c->nnear + 1));
+        STS_CUDA(c->far_ent.reserve(c->nfar + 1));
+        STS_CUDA(c->near_ent.reserve(c->nnear_chunks + 1));
+        STS_CUDA(c->tasks.reserve(c->ntasks + 1));
+    } else {
+        c->nfar = c->nnear = c->nnear_chunks = c->ntasks = -1;
     }
-    STS_CUDA(c->far_idx.reserve(nfar + 1));
-    STS_CUDA(c->near_idx.reserve(nnear + 1));
-    STS_CUDA(c->far_ent.reserve(nfar + 1));
-    STS_CUDA(c->near_ent.reserve(nchunks + 1));
-    STS_CUDA(c->tasks.reserve(ntasks + 1));
-    if (L > 0) {
-        (k_lists<<<blocks(L, T), T, 0, s>>>(1, L, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
-                                           c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p,
-                                           c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p, c->nd_count.p,
-                                           c->cluster_slot.p, nullptr, far_po, near_po, chunk_po, c->far_idx.p,
-                                           c->near_idx.p, c->far_ent.p, c->near_ent.p, c->d_status), note_launch());
-        (k_task_fill<<<blocks(L, T), T, 0, s>>>(L, c->leaves.p, c->nd_start.p, c->nd_count.p,
-                                               c->offs.p, c->tasks.p), note_launch());
-    }
+    (k_lists<<<g, T, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
+                             c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
+                             c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po,
+                             chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
+                             (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L,
+                             c->d_status, dc + kDcOver), note_launch());
+    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_start.p, c->nd_count.p, c->offs.p,
+                                 (int64_t)c->tasks.cap, c->tasks.p, dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
-    c->nfar = nfar;
-    c->nnear = nnear;
-    c->nnear_chunks = nchunks;
-    c->ntasks = ntasks;
     c->list_theta = theta;
     c->have_lists = true;
     return STS_OK;

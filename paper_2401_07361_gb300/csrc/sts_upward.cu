@@ -18,6 +18,8 @@
 // d = 8), so this contraction stays in FP64: rounding it to FP32 (or TF32) would put errors
 // of eps * |V_ref^{-1}| |omega| into W.  Rounding the moments themselves to FP32 is benign:
 // it perturbs W only along directions the interpolant maps back with norm ~1.
+#include <algorithm>
+
 #include "sts_internal.cuh"
 
 namespace sts {
@@ -43,20 +45,30 @@ __global__ void k_prepare(const double* __restrict__ pos, const double* __restri
     src32[k] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)w2);
 }
 
-__global__ void k_cluster_flags(int64_t nnodes, const int32_t* __restrict__ count, int leaf_size,
+__global__ void k_cluster_flags(const int64_t* __restrict__ nnodes, const int32_t* __restrict__ count, int leaf_size,
                                 int32_t* __restrict__ flags)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < nnodes) flags[p] = count[p] > leaf_size ? 1 : 0;
+    if (p < *nnodes) flags[p] = count[p] > leaf_size ? 1 : 0;
 }
 
-__global__ void k_cluster_fill(int64_t nnodes, const int32_t* __restrict__ flags,
+// Cluster and upward-task totals: offsets scanned over the nodes, read at index nnodes.
+__global__ void k_cluster_totals(int64_t* __restrict__ dc, const int64_t* __restrict__ off,
+                                 const int64_t* __restrict__ toff)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t nn = dc[kDcNodes];
+    dc[kDcClusters] = off[nn];
+    dc[kDcUpTasks] = toff[nn];
+}
+
+__global__ void k_cluster_fill(const int64_t* __restrict__ nnodes_p, const int32_t* __restrict__ flags,
                                const int64_t* __restrict__ off, const int32_t* __restrict__ count,
                                int32_t* __restrict__ slot, int32_t* __restrict__ cnode,
                                int32_t* __restrict__ nchunk)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nnodes) return;
+    if (p >= *nnodes_p) return;
     if (flags[p]) {
         const int64_t c = off[p];
         slot[p] = (int32_t)c;
@@ -70,13 +82,20 @@ __global__ void k_cluster_fill(int64_t nnodes, const int32_t* __restrict__ flags
 
 // toff is indexed by node: the tasks of node p are [toff[p], toff[p + 1]) (none unless p is a
 // cluster).
-__global__ void k_up_tasks(int64_t nnodes, const int32_t* __restrict__ slot, const int64_t* __restrict__ toff,
-                           int2* __restrict__ tasks)
+__global__ void k_up_tasks(const int64_t* __restrict__ nnodes, const int32_t* __restrict__ slot,
+                           const int64_t* __restrict__ toff, int64_t cap, int2* __restrict__ tasks,
+                           int64_t* __restrict__ over)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nnodes || slot[p] < 0) return;
+    if (p >= *nnodes || slot[p] < 0) return;
     int32_t j = 0;
-    for (int64_t q = toff[p]; q < toff[p + 1]; q++, j += kUpChunk) tasks[q] = make_int2(slot[p], j);
+    for (int64_t q = toff[p]; q < toff[p + 1]; q++, j += kUpChunk) {
+        if (q >= cap) {
+            atomicOr((unsigned long long*)over, 4ull);
+            return;
+        }
+        tasks[q] = make_int2(slot[p], j);
+    }
 }
 
 // Exponents (a, b, c) of SBB function k of degree d: a = d..0, then b = d - a..0.
@@ -93,11 +112,11 @@ __device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int&
 // Frame of each cluster for the spherical barycentric coordinates of Sec. 3.2 (y = b1 v1 +
 // b2 v2 + b3 v3, Cramer's rule): rows n_i / D with n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2,
 // D = v1 . n1, and b(c) = (n_i / D) . c at the circumcentre.  frame[c][12] in FP64.
-__global__ void k_cluster_frames(int64_t nclu, const int32_t* __restrict__ cnode,
+__global__ void k_cluster_frames(const int64_t* __restrict__ nclu, const int32_t* __restrict__ cnode,
                                  const double* __restrict__ geom, double* __restrict__ frame)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nclu) return;
+    if (c >= *nclu) return;
     const double* g = geom + 13 * (int64_t)cnode[c];
     const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
     const double v3x = g[6], v3y = g[7], v3z = g[8];
@@ -119,8 +138,10 @@ __global__ void __launch_bounds__(kUpChunk)
 k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
          const int32_t* __restrict__ start, const int32_t* __restrict__ count,
          const double* __restrict__ geom, const double* __restrict__ frame,
-         const double4* __restrict__ src64, int d, int M, double* __restrict__ part)
+         const double4* __restrict__ src64, int d, int M, double* __restrict__ part,
+         const int64_t* __restrict__ ntasks)
 {
+    if (blockIdx.x >= *ntasks) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* P = reinterpret_cast<T*>(smem_raw);  // [3][d+1][kUpChunk + 1]
     constexpr int LD = kUpChunk + 1;
@@ -188,10 +209,12 @@ k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
 __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __restrict__ toff,
                            const double* __restrict__ part, const double* __restrict__ geom,
                            const double* __restrict__ beta, const double* __restrict__ vinv, int d,
-                           int M, double4* __restrict__ prx64, float4* __restrict__ prx32)
+                           int M, double4* __restrict__ prx64, float4* __restrict__ prx32,
+                           const int64_t* __restrict__ nclu)
 {
     __shared__ double om[kMaxM];
     const int c = blockIdx.x;
+    if (c >= *nclu) return;
     const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         double s = 0.0;
@@ -234,39 +257,44 @@ int prepare_sources(sts_ctx* c, const double* zeta, const double* area, cudaStre
 
 int build_clusters(sts_ctx* c, cudaStream_t s)
 {
-    const int64_t nn = c->nnodes;
-    STS_CUDA(c->cluster_slot.reserve(nn + 1));
-    STS_CUDA(c->cluster_node.reserve(nn + 1));
-    STS_CUDA(c->flags.reserve(nn + 1));
-    STS_CUDA(c->offs.reserve(nn + 1));
-    STS_CUDA(c->up_toff.reserve(nn + 2));
-    STS_CUDA(c->list_cnt.reserve(nn + 1));
-    STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
-    if (nn > 0) (k_cluster_flags<<<blocks(nn, 256), 256, 0, s>>>(nn, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_tmp.p, s);
-    if (nn > 0)
-        (k_cluster_fill<<<blocks(nn, 256), 256, 0, s>>>(nn, c->flags.p, c->offs.p, c->nd_count.p,
-                                                       c->cluster_slot.p, c->cluster_node.p,
-                                                       c->list_cnt.p), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_tmp.p, s);
-    STS_CUDA(c->small.reserve(16));
-    gather_values(c->offs.p + nn, c->up_toff.p + nn, nullptr, nullptr, c->d_status, c->small.p, s);
+    const bool cap = c->capturing;
+    const int64_t nn = cap ? (int64_t)c->nd_level.cap : c->nnodes;  // node count or its capacity
+    int64_t* dc = c->dc.p;
+    if (!cap) {
+        STS_CUDA(c->cluster_slot.reserve(nn + 1));
+        STS_CUDA(c->cluster_node.reserve(nn + 1));
+        STS_CUDA(c->flags.reserve(nn + 1));
+        STS_CUDA(c->offs.reserve(nn + 1));
+        STS_CUDA(c->up_toff.reserve(nn + 2));
+        STS_CUDA(c->list_cnt.reserve(nn + 1));
+        STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
+        STS_CUDA(c->up_frame.reserve(12 * nn + 12));
+    }
+    const unsigned g = blocks(std::max<int64_t>(nn, 1), 256);
+    (k_cluster_flags<<<g, 256, 0, s>>>(dc + kDcNodes, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
+    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_tmp.p, s, dc + kDcNodes);
+    (k_cluster_fill<<<g, 256, 0, s>>>(dc + kDcNodes, c->flags.p, c->offs.p, c->nd_count.p, c->cluster_slot.p,
+                                      c->cluster_node.p, c->list_cnt.p), note_launch());
+    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_tmp.p, s, dc + kDcNodes);
+    (k_cluster_totals<<<1, 32, 0, s>>>(dc, c->offs.p, c->up_toff.p), note_launch());
     STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    const int64_t nclu = c->h_pinned[0], ntask = c->h_pinned[1];
-    c->nleaves = c->h_pinned[8];
-    STS_CUDA(c->up_tasks.reserve(ntask + 1));
-    STS_CUDA(c->up_frame.reserve(12 * nclu + 12));
-    if (nclu > 0)
-        (k_cluster_frames<<<blocks(nclu, 128), 128, 0, s>>>(nclu, c->cluster_node.p, c->nd_geom.p, c->up_frame.p),
-         note_launch());
-    if (nn > 0)
-        (k_up_tasks<<<blocks(nn, 256), 256, 0, s>>>(nn, c->cluster_slot.p, c->up_toff.p, c->up_tasks.p),
-         note_launch());
+    if (!cap) {
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        c->nclusters = c->h_pinned[kDcClusters];
+        c->n_up_tasks = c->h_pinned[kDcUpTasks];
+        c->nleaves = c->h_pinned[kDcLeaves];
+        c->plan.clusters = std::max(c->plan.clusters, c->nclusters);
+        c->plan.up_tasks = std::max(c->plan.up_tasks, c->n_up_tasks);
+        STS_CUDA(c->up_tasks.reserve(c->n_up_tasks + 1));
+    } else {
+        c->nclusters = c->n_up_tasks = c->nleaves = -1;  // known after the graph runs
+    }
+    (k_cluster_frames<<<g, 256, 0, s>>>(dc + kDcClusters, c->cluster_node.p, c->nd_geom.p, c->up_frame.p),
+     note_launch());
+    (k_up_tasks<<<g, 256, 0, s>>>(dc + kDcNodes, c->cluster_slot.p, c->up_toff.p, (int64_t)c->up_tasks.cap,
+                                  c->up_tasks.p, dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
-    c->nclusters = nclu;
-    c->n_up_tasks = ntask;
     return STS_OK;
 }
 
@@ -275,28 +303,37 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
     RefTable* ref = get_ref(c, degree);
     if (!ref) return STS_ERR_CUDA;
     const int M = ref->M;
-    const int64_t nclu = c->nclusters;
-    STS_CUDA(c->prx64.reserve(nclu * M + 1));
-    STS_CUDA(c->prx32.reserve(nclu * M + 1));
-    STS_CUDA(c->up_part.reserve(c->n_up_tasks * M + 1));
-    if (nclu == 0) return STS_OK;
+    const bool cap = c->capturing;
+    const int64_t nclu = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    const int64_t nupt = cap ? (int64_t)c->up_tasks.cap : c->n_up_tasks;
+    if (!cap) {
+        STS_CUDA(c->prx64.reserve(nclu * M + 1));
+        STS_CUDA(c->prx32.reserve(nclu * M + 1));
+        STS_CUDA(c->up_part.reserve(nupt * M + 1));
+    }
+    if (nclu == 0 || nupt == 0) {
+        c->up_degree = degree;
+        c->up_precision = precision;
+        return STS_OK;
+    }
+    int64_t* dc = c->dc.p;
     const int LD = kUpChunk + 1;
     if (precision == STS_FP64) {
         const size_t sm = (3 * (degree + 1) * LD + 2 * kUpChunk) * sizeof(double);
-        STS_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        (k_upward<double><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
+        if (!cap) STS_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        (k_upward<double><<<(unsigned)nupt, kUpChunk, sm, s>>>(
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
-            c->src64.p, degree, M, c->up_part.p), note_launch());
+            c->src64.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     } else {
         const size_t sm = (3 * (degree + 1) * LD + 2 * kUpChunk) * sizeof(float);
-        STS_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        (k_upward<float><<<(unsigned)c->n_up_tasks, kUpChunk, sm, s>>>(
+        if (!cap) STS_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        (k_upward<float><<<(unsigned)nupt, kUpChunk, sm, s>>>(
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
-            c->src64.p, degree, M, c->up_part.p), note_launch());
+            c->src64.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     }
     (k_contract<<<(unsigned)nclu, 64, 0, s>>>(c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p,
-                                             ref->d_beta.p, ref->d_vinv.p, degree, M, c->prx64.p,
-                                             c->prx32.p), note_launch());
+                                             ref->d_beta.p, ref->d_vinv.p, degree, M, c->prx64.p, c->prx32.p,
+                                             dc + kDcClusters), note_launch());
     STS_LAUNCH_CHECK();
     c->up_degree = degree;
     c->up_precision = precision;

@@ -75,6 +75,7 @@ def load(build_if_needed: bool = True):
             "sts_set_timing": (i32, [P, i32]),
             "sts_phase_times": (i32, [P, P, P, i32]),
             "sts_launch_count": (i32, [P]),
+            "sts_set_graph": (i32, [P, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -293,6 +294,10 @@ def sts_phase_times(ctx):
     cnt = np.zeros(len(PHASES), np.int32)
     _check(load().sts_phase_times(ctx, _host(ms), _host(cnt), len(PHASES)), "sts_phase_times")
     return {k: (float(m), int(c)) for k, m, c in zip(PHASES, ms, cnt)}
+
+
+def sts_set_graph(ctx, on=True):
+    _check(load().sts_set_graph(ctx, int(bool(on))), "sts_set_graph")
 
 
 def sts_launch_count():
