@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--tau-c", type=float, default=0.05,
                     help="near FP64 threshold tau = c * 4 pi / N (half squared chord)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
                     help="timed device steps only (no e2e, FP64 or CPU legs): the command profiled by ncu")
     return ap.parse_args()
@@ -225,18 +227,16 @@ def main():
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = sts.Context()
     h = ctx.h
+    # the step is recorded once as a CUDA graph and replayed (recording needs its own stream)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    sts.sts_set_graph(h, not args.no_graph)
+    sts.sts_set_timing(h, True)
 
     offsets = wl.get("offsets")
 
-    def build(x, p):
-        if offsets is None:
-            sts.sts_tree_build(h, x, p)
-        else:
-            sts.sts_tree_build_batched(h, x, offsets, p)
-
     def step(p=pm):
-        build(pos, p)
-        sts.sts_velocity(h, zeta, area, p, vel)
+        sts.sts_tree_velocity(h, pos, zeta, area, p, vel, offsets=offsets)
 
     def barrier():
         if ws > 1:
@@ -251,7 +251,7 @@ def main():
     # ---- device-resident timed steps ------------------------------------------------
     sampler = ClockSampler(local)
     sampler.start()
-    sts.sts_set_timing(h, True)
+    sts.sts_set_timing(h, True)  # resets the totals; events recorded in the graph stay
     l0 = sts.sts_launch_count()
     barrier()
     torch.cuda.synchronize()
@@ -307,8 +307,7 @@ def main():
         pos2.copy_(pos_p, non_blocking=True)
         zeta2.copy_(zeta_p, non_blocking=True)
         area2.copy_(area_p, non_blocking=True)
-        build(pos2, pm)
-        sts.sts_velocity(h, zeta2, area2, pm, vel2)
+        sts.sts_tree_velocity(h, pos2, zeta2, area2, pm, vel2, offsets=offsets)
         vel_p.copy_(vel2, non_blocking=True)
         e1.record()
         e1.synchronize()
@@ -386,7 +385,8 @@ def main():
                        "leaf_size": leaf, "max_level": 16, "precision": "mixed (f32 pairs, f64 positions/"
                        "contraction/near pairs below tau)", "near_fp64_tau": tau,
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       "launch": "host launches" if args.no_graph else "recorded CUDA graph, replayed per step"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": ws * n / (e2e_ms / 1e3), "unit": "targets/s",

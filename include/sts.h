@@ -157,7 +157,17 @@ int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* 
                          const int64_t* offsets, int32_t ninst, double dt, double Omega,
                          const sts_params* p, void* stream);
 
-/* on != 0: bve_rk4_step and bve_rk4_step_batched run each step as one recorded CUDA graph.
+/* Tree build and tree-code velocity in one call (sts_tree_build_batched + sts_velocity):
+ * pos[n,3], zeta[n], area[n], HOST offsets[ninst + 1] of the instances (ninst = 1 and
+ * offsets = {0, n} for one instance), vel[n,3] out.  With sts_set_graph(ctx, 1) the call is
+ * recorded as one CUDA graph and replayed on later calls with the same arguments, with the
+ * same capacity planning and eager redo on overflow as the RK4 step. */
+int sts_tree_velocity(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+                      const int64_t* offsets, int32_t ninst, const sts_params* p, double* vel,
+                      void* stream);
+
+/* on != 0: bve_rk4_step, bve_rk4_step_batched and sts_tree_velocity run as recorded CUDA
+ * graphs.  For the RK4 step:
  * The first step (and any step whose arguments -- array pointers, n, offsets, dt, Omega,
  * parameters, stream -- differ from the recorded ones) runs eagerly, which sizes the
  * buffers (the largest tree, lists and task counts of its four stages, plus 25%), and then

@@ -29,7 +29,11 @@ void set_error(const char* fmt, ...)
 
 void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing || c->capturing) return;
+    if (!c->timing) return;
+    if (c->capturing) {  // recorded as an event node of the graph; read after each replay
+        cudaEventRecord(c->ev[ph][0], s);
+        return;
+    }
     if (c->phase_open[ph]) {
         float ms = 0.f;
         if (cudaEventSynchronize(c->ev[ph][1]) == cudaSuccess &&
@@ -44,9 +48,26 @@ void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 
 void phase_end(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing || c->capturing) return;
+    if (!c->timing) return;
     cudaEventRecord(c->ev[ph][1], s);
-    c->phase_open[ph] = true;
+    if (c->capturing)
+        c->phase_in_graph[ph] = true;
+    else
+        c->phase_open[ph] = true;
+}
+
+// After a replay has completed: add the phases recorded inside the graph.
+void phase_harvest_graph(sts_ctx* c)
+{
+    if (!c->timing) return;
+    for (int ph = 0; ph < kNumPhases; ph++) {
+        if (!c->phase_in_graph[ph]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[ph][0], c->ev[ph][1]) == cudaSuccess) {
+            c->phase_ms[ph] += ms;
+            c->phase_count[ph] += 1;
+        }
+    }
 }
 
 }  // namespace sts
@@ -78,6 +99,7 @@ sts_ctx::~sts_ctx()
         for (int q = 0; q < 2; q++)
             if (ev[p][q]) cudaEventDestroy(ev[p][q]);
     if (rk_exec) cudaGraphExecDestroy(rk_exec);
+    if (ev_exec) cudaGraphExecDestroy(ev_exec);
     if (d_status) cudaFree(d_status);
     if (h_pinned) cudaFreeHost(h_pinned);
 }
@@ -326,9 +348,11 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
     int rc;
     if (c->rk_exec && key == c->rk_key && okey == c->rk_off_key) {
         STS_CUDA(cudaGraphLaunch(c->rk_exec, s));
+        g_launches.fetch_add(c->rk_kernels, std::memory_order_relaxed);
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p + kDcOver, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         STS_CUDA(cudaMemcpyAsync(c->h_pinned + 1, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         STS_CUDA(cudaStreamSynchronize(s));
+        phase_harvest_graph(c);
         const int64_t over = c->h_pinned[0];
         const int st = ((int32_t*)(c->h_pinned + 1))[0];
         if (st & kStatusNonfinite) {
@@ -361,10 +385,14 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
                   cudaGetErrorString(e));
         return STS_ERR_CUDA;
     }
+    for (int ph = 0; ph < kNumPhases; ph++) c->phase_in_graph[ph] = false;
     c->capturing = true;
+    const long long l0 = g_launches.load();
     e = cudaMemsetAsync(c->dc.p + kDcOver, 0, sizeof(int64_t), s);
     rc = e == cudaSuccess ? rk4_impl(c, pos, zeta, area, n, inst_off, ninst, dt, Omega, p, s) : STS_ERR_CUDA;
     c->capturing = false;
+    c->rk_kernels = g_launches.load() - l0;  // recorded, not launched: counted per replay
+    g_launches.fetch_sub(c->rk_kernels);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s, &g);
     if (rc == STS_OK && e2 != cudaSuccess) {
@@ -383,6 +411,86 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
     if (rc == STS_OK) {
         c->rk_key = key;
         c->rk_off_key = okey;
+    }
+    return rc;
+}
+
+// Tree build + velocity through a recorded graph (same scheme as rk4_graph): record on the
+// first call or when the arguments change, replay afterwards, redo eagerly on overflow.
+int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
+               const int64_t* inst_off, const int64_t* off_host, int ninst, const sts_params* p, double* vel,
+               cudaStream_t s)
+{
+    std::vector<double> key = {-1.0, (double)n, (double)ninst, p->theta, (double)p->degree, (double)p->leaf_size,
+                               (double)p->max_level, (double)p->precision, p->near_fp64_tau};
+    std::vector<int64_t> okey = {(int64_t)(uintptr_t)pos, (int64_t)(uintptr_t)zeta, (int64_t)(uintptr_t)area,
+                                 (int64_t)(uintptr_t)vel, (int64_t)(uintptr_t)s};
+    if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
+    int rc;
+    if (c->ev_exec && key == c->ev_key && okey == c->ev_off_key) {
+        STS_CUDA(cudaGraphLaunch(c->ev_exec, s));
+        g_launches.fetch_add(c->ev_kernels, std::memory_order_relaxed);
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p + kDcOver, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned + 1, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        phase_harvest_graph(c);
+        const int64_t over = c->h_pinned[0];
+        const int st = ((int32_t*)(c->h_pinned + 1))[0];
+        if (st & kStatusNonfinite) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("sts_tree_velocity: non-finite position");
+            return STS_ERR_NONFINITE;
+        }
+        c->have_tree = c->have_lists = true;
+        c->nnodes = -1;
+        if (over == 0) return STS_OK;
+        STS_CUDA(cudaGraphExecDestroy(c->ev_exec));
+        c->ev_exec = nullptr;
+    }
+    c->plan = Plan();
+    if ((rc = build_impl(c, pos, n, inst_off, ninst, p, s))) return rc;
+    if ((rc = velocity_impl(c, zeta, area, p, vel, s))) return rc;
+    if (n < 2) return STS_OK;
+    if ((rc = reserve_for_capture(c, p, ninst, s))) return rc;
+    STS_CUDA(cudaStreamSynchronize(s));
+    // the eager result is in vel; the recording below is not run now
+    std::vector<double> keep;
+    if (c->ev_exec) {
+        cudaGraphExecDestroy(c->ev_exec);
+        c->ev_exec = nullptr;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        set_error("sts_tree_velocity: cannot record on this stream (%s); use a non-default stream",
+                  cudaGetErrorString(e));
+        c->have_tree = c->have_lists = false;
+        return STS_ERR_CUDA;
+    }
+    for (int ph = 0; ph < kNumPhases; ph++) c->phase_in_graph[ph] = false;
+    c->capturing = true;
+    const long long l0 = g_launches.load();
+    e = cudaMemsetAsync(c->dc.p + kDcOver, 0, sizeof(int64_t), s);
+    rc = e == cudaSuccess ? build_impl(c, pos, n, inst_off, ninst, p, s) : STS_ERR_CUDA;
+    if (rc == STS_OK) rc = velocity_impl(c, zeta, area, p, vel, s);
+    c->capturing = false;
+    c->ev_kernels = g_launches.load() - l0;  // recorded, not launched: counted per replay
+    g_launches.fetch_sub(c->ev_kernels);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (rc == STS_OK && e2 != cudaSuccess) {
+        set_error("sts_tree_velocity: recording failed: %s", cudaGetErrorString(e2));
+        rc = STS_ERR_CUDA;
+    }
+    if (rc == STS_OK && cudaGraphInstantiate(&c->ev_exec, g, 0) != cudaSuccess) {
+        set_error("sts_tree_velocity: graph instantiation failed");
+        c->ev_exec = nullptr;
+        rc = STS_ERR_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    c->have_tree = c->have_lists = false;  // the recording reused the buffers; the next call replays
+    if (rc == STS_OK) {
+        c->ev_key = key;
+        c->ev_off_key = okey;
     }
     return rc;
 }
@@ -757,7 +865,30 @@ int sts_set_graph(sts_ctx* ctx, int32_t on)
         cudaGraphExecDestroy(ctx->rk_exec);
         ctx->rk_exec = nullptr;
     }
+    if (!ctx->graph_on && ctx->ev_exec) {
+        cudaGraphExecDestroy(ctx->ev_exec);
+        ctx->ev_exec = nullptr;
+    }
     return STS_OK;
+}
+
+int sts_tree_velocity(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+                      const int64_t* offsets, int32_t ninst, const sts_params* p, double* vel, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_tree_velocity");
+    if (rc || (rc = check_params(p, "sts_tree_velocity"))) return rc;
+    const int64_t* d_off = nullptr;
+    int64_t n = 0;
+    if ((rc = upload_offsets(ctx, offsets, ninst, &d_off, &n, "sts_tree_velocity", S(stream)))) return rc;
+    if (n > 0 && (!pos || !zeta || !area || !vel)) {
+        set_error("sts_tree_velocity: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (ninst == 1) d_off = nullptr;
+    if (ctx->graph_on && n >= 2)
+        return eval_graph(ctx, pos, zeta, area, n, d_off, ninst > 1 ? offsets : nullptr, ninst, p, vel, S(stream));
+    if ((rc = build_impl(ctx, pos, n, d_off, ninst, p, S(stream)))) return rc;
+    return velocity_impl(ctx, zeta, area, p, vel, S(stream));
 }
 
 }  // extern "C"

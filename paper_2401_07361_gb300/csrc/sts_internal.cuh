@@ -177,6 +177,10 @@ struct sts_ctx {
     cudaGraphExec_t rk_exec = nullptr;
     std::vector<double> rk_key;
     std::vector<int64_t> rk_off_key;
+    cudaGraphExec_t ev_exec = nullptr;   // tree build + velocity recorded (sts_tree_velocity)
+    long long ev_kernels = 0, rk_kernels = 0;  // kernels per replay of each recording
+    std::vector<double> ev_key;
+    std::vector<int64_t> ev_off_key;
     sts::DevBuf<int32_t> leaves;         // leaf node ids in depth-first order
     sts::DevBuf<int32_t> slot_leaf;      // [n] sorted slot -> depth-first leaf index
 
@@ -228,6 +232,7 @@ struct sts_ctx {
     float phase_ms[sts::kNumPhases] = {};
     int phase_count[sts::kNumPhases] = {};
     bool phase_open[sts::kNumPhases] = {};
+    bool phase_in_graph[sts::kNumPhases] = {};  // phases recorded inside the current graphs
 
     std::vector<sts::RefTable*> refs;    // by degree
     ~sts_ctx();

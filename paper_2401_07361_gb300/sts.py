@@ -76,6 +76,7 @@ def load(build_if_needed: bool = True):
             "sts_phase_times": (i32, [P, P, P, i32]),
             "sts_launch_count": (i32, [P]),
             "sts_set_graph": (i32, [P, i32]),
+            "sts_tree_velocity": (i32, [P, P, P, P, P, i32, PP, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -294,6 +295,21 @@ def sts_phase_times(ctx):
     cnt = np.zeros(len(PHASES), np.int32)
     _check(load().sts_phase_times(ctx, _host(ms), _host(cnt), len(PHASES)), "sts_phase_times")
     return {k: (float(m), int(c)) for k, m, c in zip(PHASES, ms, cnt)}
+
+
+def sts_tree_velocity(ctx, pos, zeta, area, p, vel=None, offsets=None, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    off, ninst = _offsets(offsets if offsets is not None else [0, n])
+    if off[-1] != n:
+        raise StsError(f"offsets must end at the number of particles ({n})")
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
+    _check(load().sts_tree_velocity(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                                    _dev(area, torch.float64, n, "area"), _host(off), ninst, C.byref(p),
+                                    _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)), "sts_tree_velocity")
+    return vel
 
 
 def sts_set_graph(ctx, on=True):

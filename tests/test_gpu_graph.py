@@ -94,3 +94,28 @@ def test_graph_overflow_falls_back_to_eager():
         sts.bve_rk4_step(c.h, x, z0, a, 0.01, 2 * math.pi, p)
         torch.cuda.synchronize()
         assert np.array_equal(xg, x.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", [sts.STS_FP64, sts.STS_MIXED])
+def test_recorded_tree_velocity_equals_eager(prec):
+    pos, zeta, area = _state(20000, 8)
+    p = sts.params(theta=0.7, degree=8, leaf_size=64, precision=prec)
+    st = torch.cuda.Stream()
+    d = lambda a: torch.from_numpy(a).cuda()
+    x, z, a = d(pos), d(zeta), d(area)
+    torch.cuda.synchronize()
+    with sts.Context() as c:
+        sts.sts_tree_build(c.h, x, p)
+        ref = sts.sts_velocity(c.h, z, a, p).cpu().numpy()
+    with sts.Context() as c, torch.cuda.stream(st):
+        sts.sts_set_graph(c.h, True)
+        vel = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
+        outs = []
+        for _ in range(3):  # eager + record, then two replays
+            sts.sts_tree_velocity(c.h, x, z, a, p, vel, stream=st)
+            outs.append(vel.cpu().numpy())
+        info = sts.sts_tree_info(c.h, stream=st)
+        lists = sts.sts_lists_export(c.h, stream=st)
+    for o in outs:
+        assert np.array_equal(o, ref)
+    assert info["leaves"] + 1 == len(lists["far_off"]) and info["nfar"] == len(lists["far_idx"])
