@@ -30,8 +30,8 @@ void set_error(const char* fmt, ...)
 void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 {
     if (!c->timing) return;
-    if (c->capturing) {  // recorded as an event node of the graph; read after each replay
-        cudaEventRecord(c->ev[ph][0], s);
+    if (c->capturing) {  // an event record node of the graph (external: it records at replay)
+        cudaEventRecordWithFlags(c->ev[ph][0], s, cudaEventRecordExternal);
         return;
     }
     if (c->phase_open[ph]) {
@@ -49,11 +49,13 @@ void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 void phase_end(sts_ctx* c, int ph, cudaStream_t s)
 {
     if (!c->timing) return;
-    cudaEventRecord(c->ev[ph][1], s);
-    if (c->capturing)
+    if (c->capturing) {
+        cudaEventRecordWithFlags(c->ev[ph][1], s, cudaEventRecordExternal);
         c->phase_in_graph[ph] = true;
-    else
+    } else {
+        cudaEventRecord(c->ev[ph][1], s);
         c->phase_open[ph] = true;
+    }
 }
 
 // After a replay has completed: add the phases recorded inside the graph.
@@ -66,6 +68,8 @@ void phase_harvest_graph(sts_ctx* c)
         if (cudaEventElapsedTime(&ms, c->ev[ph][0], c->ev[ph][1]) == cudaSuccess) {
             c->phase_ms[ph] += ms;
             c->phase_count[ph] += 1;
+        } else {
+            (void)cudaGetLastError();  // timing is best effort; do not leave the error pending
         }
     }
 }
@@ -86,7 +90,7 @@ sts_ctx::~sts_ctx()
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
-    near_ent.release(); list_cnt.release(); list_po.release(); tasks.release(); dsrc64.release(); dsrc32.release();
+    near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
     rk_k.release(); rk_ksum.release(); d_stats.release();
     for (RefTable* t : refs)
@@ -328,6 +332,7 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->near_off.reserve(n + 1));
     STS_CUDA(c->near_coff.reserve(n + 1));
     STS_CUDA(c->leaves.reserve(n + 1));
+    STS_CUDA(c->wover.reserve(n + 1));
     STS_CUDA(c->corr.reserve(3 * n + 3));
     STS_CUDA(c->scan_tmp.reserve(radix_hist_size(n) + 1 + scan_scratch(radix_hist_size(n)) + 2 * scan_scratch(big) + 64));
     return STS_OK;

@@ -212,7 +212,7 @@ struct sts_ctx {
     sts::DevBuf<sts::FarEntry> far_ent;
     sts::DevBuf<sts::NearEntry> near_ent;
     sts::DevBuf<int32_t> list_cnt;       // [3 * leaves * roots] scratch
-    sts::DevBuf<int64_t> list_po;        // [3 * (leaves * roots + 1)] per-(leaf, root) offsets
+    sts::DevBuf<uint8_t> wover;          // [leaves] lists left to the per-thread traversal
     sts::DevBuf<sts::Task> tasks;
     int64_t ntasks = 0;
     int list_degree = -1;                // degree the far entries' slots refer to

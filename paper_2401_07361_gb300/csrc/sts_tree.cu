@@ -468,11 +468,12 @@ __global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const i
                         int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
                         FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent,
                         int64_t far_cap, int64_t near_cap, int64_t chunk_cap, int64_t ldc,
-                        int* __restrict__ status, int64_t* __restrict__ over)
+                        const uint8_t* __restrict__ only, int* __restrict__ status, int64_t* __restrict__ over)
 {
     const int64_t nleaves = *nleaves_p;
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= nleaves) return;
+    if (only && !only[L]) return;  // the warp traversal handled this leaf
     if (fill && (far_po[L + 1] > far_cap || near_po[L + 1] > near_cap || chunk_po[L + 1] > chunk_cap)) {
         atomicOr((unsigned long long*)over, 4ull);  // recorded capacities too small
         return;
@@ -546,6 +547,210 @@ __global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const i
         }
     }
     if (!fill) {
+        cnt[L] = (int32_t)nf;
+        cnt[ldc + L] = (int32_t)nn;
+        cnt[2 * ldc + L] = (int32_t)nch;
+    }
+}
+
+// ------------------------------------------------------------------------- lists, warp form
+// One warp per target leaf: the traversal of k_lists, expanded breadth first (32 source
+// nodes decided per round), then the terminal nodes (far and near entries) sorted into the
+// depth-first order of the roots by a left-aligned key, which is the order the per-thread
+// traversal emits.  Frontier and terminals live in shared memory; a leaf whose traversal
+// does not fit sets `wover` and is left to k_lists.
+constexpr int kLwWarps = 4;
+constexpr int kLwFront = 512;   // frontier nodes per level
+constexpr int kLwTerm = 512;    // far + near nodes per leaf
+
+__device__ __forceinline__ uint64_t dfs_key(uint64_t key, int lv)
+{
+    const uint64_t low = key & ((1ull << (2 * lv)) - 1ull);
+    const uint64_t face = (key >> (2 * lv)) % 20ull;
+    return ((face << (2 * lv)) | low) << (2 * (kMaxLevel - lv));
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total)
+{
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+__global__ void __launch_bounds__(kLwWarps * 32)
+k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
+             const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
+             const int32_t* __restrict__ level, double theta, int leaf_size, const double* __restrict__ geom,
+             const float4* __restrict__ c32, const int32_t* __restrict__ leaf,
+             const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
+             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+             const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ cnt,
+             const int64_t* __restrict__ far_po, const int64_t* __restrict__ near_po,
+             const int64_t* __restrict__ chunk_po, int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
+             FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent, int64_t far_cap,
+             int64_t near_cap, int64_t chunk_cap, int64_t ldc, uint8_t* __restrict__ wover,
+             int64_t* __restrict__ over)
+{
+    __shared__ int32_t front[kLwWarps][2][kLwFront];
+    __shared__ uint64_t tkey[kLwWarps][kLwTerm];
+    __shared__ int32_t tnode[kLwWarps][kLwTerm];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t L = (int64_t)blockIdx.x * kLwWarps + w;
+    if (L >= *nleaves_p) return;
+    if (fill) {
+        if (wover[L]) return;  // done by k_lists
+        if (far_po[L + 1] > far_cap || near_po[L + 1] > near_cap || chunk_po[L + 1] > chunk_cap) {
+            if (lane == 0) atomicOr((unsigned long long*)over, 4ull);
+            return;
+        }
+    }
+    const int32_t t = leaves[L];
+    const double* gt = geom + 13 * (int64_t)t;
+    const float4 ct = c32[t];
+    const float theta32 = (float)theta;
+    const uint64_t rk = key[t] >> (2 * level[t]);
+    const int32_t* roots = face_node + (int64_t)(rk / 20) * 20;
+    int32_t* fr[2] = {front[w][0], front[w][1]};
+    // roots of the leaf's instance, in face order
+    {
+        const int32_t r = lane < 20 ? roots[lane] : -1;
+        const unsigned m = __ballot_sync(kFull, r >= 0);
+        if (r >= 0) fr[0][__popc(m & ((1u << lane) - 1u))] = r;
+    }
+    int nfront = __popc(__ballot_sync(kFull, lane < 20 && roots[lane < 20 ? lane : 0] >= 0));
+    int cur = 0, nterm = 0;
+    bool bad = false;
+    __syncwarp();
+    while (nfront > 0 && !bad) {
+        int nnext = 0;
+        for (int b0 = 0; b0 < nfront; b0 += 32) {
+            const int i = b0 + lane;
+            int32_t s = -1;
+            int kind = 0;  // 1 far, 2 near, 3 expand
+            if (i < nfront) {
+                s = fr[cur][i];
+                const double* gs = geom + 13 * (int64_t)s;
+                if (mac_filtered(ct, c32[s], theta32, gt, gs, theta))
+                    kind = count[s] > leaf_size ? 1 : 2;
+                else
+                    kind = leaf[s] ? 2 : 3;
+            }
+            const int nc = kind == 3 ? nchild[s] : 0;
+            int ctot;
+            const int coff = warp_excl_scan(nc, lane, &ctot);
+            if (nnext + ctot > kLwFront) {
+                bad = true;
+                break;
+            }
+            for (int c = 0; c < nc; c++) fr[cur ^ 1][nnext + coff + c] = first_child[s] + c;
+            nnext += ctot;
+            const bool term = kind == 1 || kind == 2;
+            const unsigned tm = __ballot_sync(kFull, term);
+            if (nterm + __popc(tm) > kLwTerm) {
+                bad = true;
+                break;
+            }
+            if (term) {
+                const int pos = nterm + __popc(tm & ((1u << lane) - 1u));
+                tkey[w][pos] = dfs_key(key[s], level[s]);
+                tnode[w][pos] = s | (kind == 1 ? (int32_t)0x80000000 : 0);
+            }
+            nterm += __popc(tm);
+        }
+        __syncwarp();
+        cur ^= 1;
+        nfront = nnext;
+    }
+    if (bad) {
+        if (!fill && lane == 0) wover[L] = 1;
+        return;
+    }
+    if (!fill && lane == 0) wover[L] = 0;
+    // bitonic sort of the terminals by key (padding keys sort last)
+    int P = 1;
+    while (P < nterm) P <<= 1;
+    for (int i = nterm + lane; i < P; i += 32) tkey[w][i] = ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a = tkey[w][i], b = tkey[w][ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        tkey[w][i] = b;
+                        tkey[w][ixj] = a;
+                        const int32_t tn = tnode[w][i];
+                        tnode[w][i] = tnode[w][ixj];
+                        tnode[w][ixj] = tn;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    // emit in order: far, near and near chunks get their ranks by warp scans
+    int64_t nf = 0, nn = 0, nch = 0;
+    const int64_t fo = fill ? far_po[L] : 0, no = fill ? near_po[L] : 0, co = fill ? chunk_po[L] : 0;
+    for (int b0 = 0; b0 < nterm; b0 += 32) {
+        const int i = b0 + lane;
+        int32_t s = -1;
+        bool isfar = false;
+        int chunks = 0;
+        if (i < nterm) {
+            const int32_t tn = tnode[w][i];
+            isfar = tn < 0;
+            s = tn & 0x7fffffff;
+            if (!isfar) chunks = (count[s] + kStage - 1) / kStage;
+        }
+        const bool valid = i < nterm;
+        const unsigned fm = __ballot_sync(kFull, valid && isfar);
+        const unsigned nm = __ballot_sync(kFull, valid && !isfar);
+        int chtot;
+        const int choff = warp_excl_scan(chunks, lane, &chtot);
+        if (fill && valid) {
+            const double* gs = geom + 13 * (int64_t)s;
+            const float dx = (float)__dsub_rn(gs[9], gt[9]);
+            const float dy = (float)__dsub_rn(gs[10], gt[10]);
+            const float dz = (float)__dsub_rn(gs[11], gt[11]);
+            if (isfar) {
+                const int64_t q = fo + nf + __popc(fm & ((1u << lane) - 1u));
+                far_idx[q] = s;
+                FarEntry e;
+                e.slot = cluster_slot[s];
+                e.dx = dx;
+                e.dy = dy;
+                e.dz = dz;
+                far_ent[q] = e;
+            } else {
+                near_idx[no + nn + __popc(nm & ((1u << lane) - 1u))] = s;
+                const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
+                const double gap = __dsqrt_rn(gdot(e3, e3)) - gt[12] - gs[12];
+                NearEntry e;
+                e.dx = dx;
+                e.dy = dy;
+                e.dz = dz;
+                e.gap = __double2float_rd(gap);
+                e.pad[0] = e.pad[1] = 0;
+                const int32_t st = start[s], ct2 = count[s];
+                int64_t q = co + nch + choff;
+                for (int32_t c0 = 0; c0 < ct2; c0 += kStage) {
+                    e.start = st + c0;
+                    e.count = min(kStage, ct2 - c0);
+                    near_ent[q++] = e;
+                }
+            }
+        }
+        nf += __popc(fm);
+        nn += __popc(nm);
+        nch += chtot;
+    }
+    if (!fill && lane == 0) {
         cnt[L] = (int32_t)nf;
         cnt[ldc + L] = (int32_t)nn;
         cnt[2 * ldc + L] = (int32_t)nch;
@@ -894,12 +1099,22 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     int64_t* far_po = c->far_off.p;
     int64_t* near_po = c->near_off.p;
     int64_t* chunk_po = c->near_coff.p;
+    STS_CUDA(c->wover.reserve(L + 1));
     const unsigned g = blocks(std::max<int64_t>(L, 1), T);
+    const unsigned gw = blocks(std::max<int64_t>(L, 1), kLwWarps);
+    // counts: one warp per leaf; leaves whose traversal overflows the warp's shared memory are
+    // counted (and later filled) by the per-thread traversal
+    (k_lists_warp<<<gw, kLwWarps * 32, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
+                                               c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
+                                               c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
+                                               c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
+                                               dc + kDcOver), note_launch());
     (k_lists<<<g, T, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr,
-                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->d_status,
-                             dc + kDcOver), note_launch());  // list_cnt: three rows of stride L
+                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
+                             c->d_status, dc + kDcOver), note_launch());  // list_cnt: three rows of stride L
     exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
@@ -933,12 +1148,19 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     } else {
         c->nfar = c->nnear = c->nnear_chunks = c->ntasks = -1;
     }
+    (k_lists_warp<<<gw, kLwWarps * 32, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
+                                               c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
+                                               c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
+                                               c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po, chunk_po,
+                                               c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
+                                               (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap,
+                                               (int64_t)c->near_ent.cap, L, c->wover.p, dc + kDcOver), note_launch());
     (k_lists<<<g, T, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po,
                              chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
                              (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L,
-                             c->d_status, dc + kDcOver), note_launch());
+                             c->wover.p, c->d_status, dc + kDcOver), note_launch());
     (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_start.p, c->nd_count.p, c->offs.p,
                                  (int64_t)c->tasks.cap, c->tasks.p, dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
