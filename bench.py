@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--tau-c", type=float, default=0.05,
                     help="near FP64 threshold tau = c * 4 pi / N (half squared chord)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rk4", type=int, default=0,
+                    help="time this many RK4 steps of the workload instead of single evaluations "
+                         "(Omega = 2 pi per day, dt = 1/288 day) and report the invariants' drift")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
@@ -194,10 +197,99 @@ def run_reference(args):
     return 0
 
 
+def run_rk4(args):
+    """RK4 time stepping (the Sec. 4 integrator) of the workload, each step recorded once as a
+    CUDA graph and replayed: steps/s, particle-stages/s, and the drift of the energy
+    E = 1/2 sum |u|^2 A, the enstrophy Z = 1/2 sum zeta^2 A, the circulation sum zeta A and
+    the per-particle absolute vorticity zeta + 2 Omega z (carried exactly by the
+    unprojected scheme)."""
+    import numpy as np
+    import torch
+
+    from paper_2401_07361_gb300 import sts
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = load_workload(args.workload)
+    n = len(wl["pos"])
+    leaf = args.leaf or wl["leaf_size"]
+    offsets = wl.get("offsets")
+    n_tau = n if offsets is None else int(np.min(np.diff(offsets)[np.diff(offsets) > 0]))
+    tau = args.tau_c * 4.0 * math.pi / n_tau
+    pm = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16,
+                    precision=sts.STS_MIXED, near_fp64_tau=tau)
+    Omega, dt = 2.0 * math.pi, 1.0 / 288.0
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    pos = torch.from_numpy(wl["pos"]).to(dev)
+    zeta = torch.from_numpy(wl["zeta"]).to(dev)
+    area = torch.from_numpy(wl["area"]).to(dev)
+    vel = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    ctx = sts.Context()
+    h = ctx.h
+
+    def invariants():
+        sts.sts_set_graph(h, False)
+        sts.sts_tree_velocity(h, pos, zeta, area, pm, vel, offsets=offsets)
+        torch.cuda.synchronize()
+        u, z, a, x = vel.cpu().numpy(), zeta.cpu().numpy(), area.cpu().numpy(), pos.cpu().numpy()
+        return dict(E=0.5 * float(np.sum(np.sum(u * u, 1) * a)), Z=0.5 * float(np.sum(z * z * a)),
+                    C=float(np.sum(z * a)), q=z + 2 * Omega * x[:, 2], r=np.linalg.norm(x, axis=1))
+
+    def step():
+        if offsets is None:
+            sts.bve_rk4_step(h, pos, zeta, area, dt, Omega, pm)
+        else:
+            sts.bve_rk4_step_batched(h, pos, zeta, area, offsets, dt, Omega, pm)
+
+    inv0 = invariants()
+    sts.sts_set_graph(h, not args.no_graph)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = sts.sts_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.rk4):
+        step()
+    e1.record()
+    e1.synchronize()
+    clocks = sampler.stop()
+    launches = sts.sts_launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    inv1 = invariants()
+    nsteps = args.rk4 + max(3, args.warmup)
+    line = {
+        "metric": "BVE RK4 particle-steps/s (4 tree-code velocity evaluations per step)", "value": n * args.rk4 / (ms / 1e3),
+        "unit": "particle-steps/s", "n_gpus": ws, "steps": args.rk4, "warmup": max(3, args.warmup),
+        "ms_per_step": ms / args.rk4, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
+                   "dt_day": dt, "Omega_per_day": Omega, "near_fp64_tau": tau,
+                   "launch": "host launches" if args.no_graph else "recorded CUDA graph per step"},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "drift_after_steps": nsteps,
+        "drift": {"energy_rel": (inv1["E"] - inv0["E"]) / inv0["E"], "enstrophy_rel": (inv1["Z"] - inv0["Z"]) / inv0["Z"],
+                  "circulation_abs": inv1["C"] - inv0["C"],
+                  "abs_vorticity_max_change": float(np.max(np.abs(inv1["q"] - inv0["q"]))),
+                  "max_radius_error": float(np.max(np.abs(inv1["r"] - 1.0)))},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.rk4 > 0:
+        return run_rk4(args)
     import numpy as np
     import torch
 

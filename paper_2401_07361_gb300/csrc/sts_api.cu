@@ -84,7 +84,7 @@ sts_ctx::~sts_ctx()
     skey.release(); skey_tmp.release(); scan_tmp.release(); hist.release(); flags.release();
     offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
-    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
+    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_mid.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();

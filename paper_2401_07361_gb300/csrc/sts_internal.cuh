@@ -159,6 +159,7 @@ struct sts_ctx {
     sts::DevBuf<double> nd_geom;         // [nodes,13]: v1, v2, v3, c, r
     sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
     sts::DevBuf<float4> nd_norm32;       // [nodes,3]: the normals in FP32 + pre-filter margin
+    sts::DevBuf<double> nd_mid;          // [nodes,9]: edge midpoints m12, m23, m31 of split nodes
     sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)

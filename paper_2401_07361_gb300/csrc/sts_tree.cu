@@ -214,7 +214,8 @@ __global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node,
 __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_size, int max_level,
                               const int32_t* __restrict__ level, const int32_t* __restrict__ count,
                               const double* __restrict__ geom, int32_t* __restrict__ leaf,
-                              double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc)
+                              double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc,
+                              double* __restrict__ mid)
 {
     const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
     for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
@@ -225,6 +226,10 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
         const double* g = geom + 13 * (int64_t)p;
         const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
         const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+        double* mm = mid + 9 * (int64_t)p;
+        gst(mm, m12);
+        gst(mm + 3, m23);
+        gst(mm + 6, m31);
         double* nn = norm + 9 * (int64_t)p;
         const g3 n3[3] = {gcross(m12, m31), gcross(m23, m12), gcross(m31, m23)};
         for (int a = 0; a < 3; a++) {
@@ -307,7 +312,7 @@ __global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const i
                                  int64_t cap, const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
                                  int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
                                  int32_t* count, int32_t* leaf, double* geom, int32_t* __restrict__ child,
-                                 int64_t* __restrict__ over)
+                                 int64_t* __restrict__ over, const double* __restrict__ mid)
 {
     const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
     for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
@@ -319,7 +324,8 @@ __global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const i
         }
         const double* g = geom + 13 * (int64_t)p;
         const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
-        const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
+        const double* mm = mid + 9 * (int64_t)p;
+        const g3 m12 = gld(mm), m23 = gld(mm + 3), m31 = gld(mm + 6);
         const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
         int32_t id = le + (int32_t)off[p - lb];
         const int32_t first = id;
@@ -348,7 +354,10 @@ __global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const i
             start[id] = st;
             count[id] = c;
             leaf[id] = 0;
-            node_geometry(geom + 13 * (int64_t)id, cv[d][0], cv[d][1], cv[d][2]);
+            double* gc = geom + 13 * (int64_t)id;  // vertices; centre and radius in k_child_geometry
+            gst(gc, cv[d][0]);
+            gst(gc + 3, cv[d][1]);
+            gst(gc + 6, cv[d][2]);
             st += c;
             id++;
             nc++;
@@ -363,6 +372,17 @@ __global__ void k_level_end(int64_t* __restrict__ lvl, int l, const int64_t* __r
                             const int64_t* __restrict__ nl, int64_t cap)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) lvl[l + 2] = min(lvl[l + 1] + off[*nl], cap);
+}
+
+// Circumcentre and chord radius of the nodes of level l + 1 (vertices written by
+// k_level_children), one thread per node.
+__global__ void k_child_geometry(const int64_t* __restrict__ lvl, int l, double* __restrict__ geom)
+{
+    const int64_t lb = lvl[l + 1], le = lvl[l + 2];
+    for (int64_t q = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < le; q += (int64_t)gridDim.x * blockDim.x) {
+        double* g = geom + 13 * q;
+        node_geometry(g, gld(g), gld(g + 3), gld(g + 6));
+    }
 }
 
 __global__ void k_level_assign(const int64_t* __restrict__ lvl, int l, int64_t n, const int32_t* __restrict__ leaf,
@@ -894,6 +914,7 @@ int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
     STS_CUDA(c->nd_norm.grow(9 * need, 9 * keep, s));
     STS_CUDA(c->nd_norm32.grow(3 * need, 3 * keep, s));
     STS_CUDA(c->nd_c32.grow(need, keep, s));
+    STS_CUDA(c->nd_mid.grow(9 * need, 9 * keep, s));
     STS_CUDA(c->nd_cc.grow(4 * need, 4 * keep, s));
     STS_CUDA(c->nd_child.grow(4 * need, 4 * keep, s));
     return STS_OK;
@@ -1019,8 +1040,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
             g = gnode;
         }
         (k_level_nodes<<<g, T, 0, s>>>(lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p,
-                                       c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p),
-         note_launch());
+                                       c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p,
+                                       c->nd_mid.p), note_launch());
         (k_level_particles<<<blocks(n, T), T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_leaf.p,
                                                       c->nd_norm.p, c->nd_norm32.p, c->digit.p, c->nd_cc.p),
          note_launch());
@@ -1030,9 +1051,11 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
                            dc + kDcTmp);
         (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, capn, c->nd_cc.p, c->nd_level.p, c->nd_key.p,
                                           c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                          c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p, dc + kDcOver),
-         note_launch());
+                                          c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p, dc + kDcOver,
+                                          c->nd_mid.p), note_launch());
         (k_level_end<<<1, 32, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn), note_launch());
+        (k_child_geometry<<<cap ? gnode : blocks(std::max<int64_t>(4 * (le - lb), 1), T), T, 0, s>>>(
+             lvl, level, c->nd_geom.p), note_launch());
         (k_level_assign<<<blocks(n, T), T, 0, s>>>(lvl, level, n, c->nd_leaf.p, c->nd_child.p, c->digit.p,
                                                   c->nodeof.p), note_launch());
         STS_LAUNCH_CHECK();
