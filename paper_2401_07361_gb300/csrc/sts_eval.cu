@@ -322,51 +322,55 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[k
 }
 
 __global__ void __launch_bounds__(kEvalWarps * 32, 3)
-k_eval_mixed(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
+k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
              const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
              const float4* __restrict__ src32, const double4* __restrict__ src64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
-             double* __restrict__ vel, const int64_t* __restrict__ ntasks_d)
+             double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
+             unsigned long long* __restrict__ queue)
 {
     __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStagePad];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps + w;
-    if (ti >= *ntasks_d) return;
-    const Task tk = tasks[ti];
-    switch (tk.S) {
-        case 1:
-            eval_task_mixed<1>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                               perm, tau2, tau_r, corr, vel);
-            break;
-        case 2:
-            eval_task_mixed<2>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                               perm, tau2, tau_r, corr, vel);
-            break;
-        case 4:
-            eval_task_mixed<4>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                               perm, tau2, tau_r, corr, vel);
-            break;
-        default:
-            eval_task_mixed<8>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                               perm, tau2, tau_r, corr, vel);
-            break;
+    const int64_t nt = min(*ntasks_d, cap);  // a recorded step whose tasks overflowed is redone
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(queue, 1ull);
+        const int64_t ti = (int64_t)__shfl_sync(kFull, t, 0);
+        if (ti >= nt) break;
+        const Task tk = tasks[ti];
+        switch (tk.S) {
+            case 1:
+                eval_task_mixed<1>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            case 2:
+                eval_task_mixed<2>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            case 4:
+                eval_task_mixed<4>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            default:
+                eval_task_mixed<8>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+        }
+        __syncwarp();
     }
 }
 
 // ------------------------------------------------------------------------ FP64 tree
-__global__ void __launch_bounds__(kEvalWarps64 * 32)
-k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __restrict__ far_off,
-            const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
-            const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
-            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel,
-            const int64_t* __restrict__ ntasks_d)
+__device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int lane,
+                                               const int64_t* __restrict__ far_off,
+                                               const FarEntry* __restrict__ far_ent,
+                                               const int64_t* __restrict__ near_coff,
+                                               const NearEntry* __restrict__ near_ent,
+                                               const double4* __restrict__ prx64, int M,
+                                               const double4* __restrict__ src64, const int32_t* __restrict__ perm,
+                                               double* __restrict__ vel)
 {
-    __shared__ double4 sbuf[kEvalWarps64][kStage];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ti = (int64_t)blockIdx.x * kEvalWarps64 + w;
-    if (ti >= *ntasks_d) return;
-    const Task tk = tasks[ti];
     const int p = (tk.nt + 1) >> 1, S = tk.S;
     const int j = lane % p;
     const int ph = lane < p * S ? lane / p : (1 << 20);
@@ -376,7 +380,6 @@ k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __res
     const double ax = v0 ? x0.x : -1e3, ay = v0 ? x0.y : -1e3, az = v0 ? x0.z : -1e3;
     const double bx = v1 ? x1.x : -1e3, by = v1 ? x1.y : -1e3, bz = v1 ? x1.z : -1e3;
     double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    double4* sb = sbuf[w];
     const int64_t fo = far_off[tk.leaf], co = near_coff[tk.leaf];
     const int nf = (int)(far_off[tk.leaf + 1] - fo);
     const int nbt = nf + (int)(near_coff[tk.leaf + 1] - co);
@@ -423,6 +426,30 @@ k_eval_fp64(const Task* __restrict__ tasks, int64_t ntasks, const int64_t* __res
             vel[3 * i + 2] = -kInv4Pi * (x1.x * a[4] - x1.y * a[3]);
         }
     }
+    __syncwarp();
+}
+
+// Next task of a persistent warp: lane 0 takes the queue's next index, all lanes receive it.
+__device__ __forceinline__ int64_t next_task(unsigned long long* queue, int lane)
+{
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1ull);
+    return (int64_t)__shfl_sync(kFull, t, 0);
+}
+
+// Persistent warps: each warp takes tasks from the queue until it runs dry.
+__global__ void __launch_bounds__(kEvalWarps64 * 32)
+k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
+            const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
+            const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
+            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel,
+            const int64_t* __restrict__ ntasks_d, int64_t cap, unsigned long long* __restrict__ queue)
+{
+    __shared__ double4 sbuf[kEvalWarps64][kStage];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nt = min(*ntasks_d, cap);
+    for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane))
+        eval_task_fp64(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, perm, vel);
 }
 
 // ------------------------------------------------------------------------ counts
@@ -563,11 +590,24 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
     const int64_t ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
     if (ntasks <= 0) return STS_OK;
     const int64_t* nt_d = c->dc.p + kDcTasks;
+    unsigned long long* queue = (unsigned long long*)(c->dc.p + kDcQueue);
+    if (c->eval_blocks_mixed <= 0) {
+        // persistent grids: as many blocks as stay resident on all SMs at once
+        int dev = 0, sms = 0, b32 = 0, b64 = 0;
+        STS_CUDA(cudaGetDevice(&dev));
+        STS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32, 0));
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64, kEvalWarps64 * 32, 0));
+        c->eval_blocks_mixed = std::max(1, sms * b32);
+        c->eval_blocks_fp64 = std::max(1, sms * b64);
+    }
+    STS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     if (precision == STS_FP64) {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
         phase_begin(c, kPhEval, s);
-        (k_eval_fp64<<<blocks(ntasks, kEvalWarps64), kEvalWarps64 * 32, 0, s>>>(
-             c->tasks.p, ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx64.p, M,
-             c->src64.p, c->perm.p, vel, nt_d), note_launch());
+        (k_eval_fp64<<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+                                                     c->near_ent.p, c->prx64.p, M, c->src64.p, c->perm.p, vel,
+                                                     nt_d, ntasks, queue), note_launch());
         phase_end(c, kPhEval, s);
     } else {
         double* corr = nullptr;
@@ -582,10 +622,11 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         // FP32 threshold on |d|^2 and the distance bound below which a near block is tested
         const float tau2 = corr ? (float)(2.0 * tau) : 0.f;
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps), c->eval_blocks_mixed);
         phase_begin(c, kPhEval, s);
-        (k_eval_mixed<<<blocks(ntasks, kEvalWarps), kEvalWarps * 32, 0, s>>>(
-             c->tasks.p, ntasks, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx32.p, M,
-             c->src32.p, c->src64.p, c->perm.p, tau2, tau_r, corr, vel, nt_d), note_launch());
+        (k_eval_mixed<<<g, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+                                                    c->near_ent.p, c->prx32.p, M, c->src32.p, c->src64.p, c->perm.p,
+                                                    tau2, tau_r, corr, vel, nt_d, ntasks, queue), note_launch());
         phase_end(c, kPhEval, s);
     }
     STS_LAUNCH_CHECK();

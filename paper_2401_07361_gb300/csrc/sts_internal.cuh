@@ -120,6 +120,9 @@ enum DevCount {
     kDcOver,   // overflow bits: 1 node capacity, 2 levels, 4 list or task capacity
     kDcTmp,
     kDcLevel = 16,  // level_begin[0 .. kMaxLevel + 3]
+    kDcClass = 44,      // evaluation tasks per lane class S = 1, 2, 4, 8 (4 counters)
+    kDcClassFill = 48,  // tasks placed so far per class (4 counters)
+    kDcQueue = 52,      // next task of the persistent evaluation kernels
     kDcSize = 64
 };
 
@@ -160,6 +163,7 @@ struct sts_ctx {
     sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
     sts::DevBuf<float4> nd_norm32;       // [nodes,3]: the normals in FP32 + pre-filter margin
     sts::DevBuf<double> nd_mid;          // [nodes,9]: edge midpoints m12, m23, m31 of split nodes
+    int eval_blocks_mixed = 0, eval_blocks_fp64 = 0;  // resident blocks of the persistent eval kernels
     sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)

@@ -779,15 +779,14 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
 
 // List and task totals (scanned offsets read at index nleaves) into the device counters.
 __global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restrict__ far_off,
-                              const int64_t* __restrict__ near_off, const int64_t* __restrict__ chunk_off,
-                              const int64_t* __restrict__ toff)
+                              const int64_t* __restrict__ near_off, const int64_t* __restrict__ chunk_off)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int64_t L = dc[kDcLeaves];
     dc[kDcFar] = far_off[L];
     dc[kDcNear] = near_off[L];
     dc[kDcChunks] = chunk_off[L];
-    dc[kDcTasks] = toff[L];
+    dc[kDcTasks] = dc[kDcClass] + dc[kDcClass + 1] + dc[kDcClass + 2] + dc[kDcClass + 3];
 }
 
 __global__ void k_copy_count(const int64_t* __restrict__ src, int64_t* __restrict__ dst)
@@ -833,29 +832,38 @@ __device__ int task_split(int nt)
     return best;
 }
 
+__device__ __forceinline__ int lane_class(int S) { return S == 1 ? 0 : (S == 2 ? 1 : (S == 4 ? 2 : 3)); }
+
+// Counts the warp tasks of every leaf by lane class (S = 1, 2, 4, 8) into cls[0..3].
 __global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
-                             const int32_t* __restrict__ count, int32_t* __restrict__ ntask)
+                             const int32_t* __restrict__ count, unsigned long long* __restrict__ cls)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= *nleaves) return;
-    ntask[L] = task_split(count[leaves[L]]);
+    const int32_t c = count[leaves[L]];
+    const int k = task_split(c);
+    int per[4] = {0, 0, 0, 0};
+    for (int i = 0; i < k; i++) per[lane_class(lanes_per_pair((c / k + (i < c % k ? 1 : 0) + 1) / 2))]++;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (per[q]) atomicAdd(cls + q, (unsigned long long)per[q]);
 }
 
+// Writes the warp tasks grouped by lane class, S = 1 first: a task's run time grows with the
+// sources each lane visits (list length / S), so the task queue hands out the longest tasks
+// first and the persistent evaluation kernel ends with short ones.  The order within a class
+// is arbitrary; every task writes only its own targets, so the results do not depend on it.
 __global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
                             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-                            const int64_t* __restrict__ toff, int64_t cap, Task* __restrict__ tasks,
-                            int64_t* __restrict__ over)
+                            const int64_t* __restrict__ cls, unsigned long long* __restrict__ fill, int64_t cap,
+                            Task* __restrict__ tasks, int64_t* __restrict__ over)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= *nleaves) return;
-    if (toff[L + 1] > cap) {
-        atomicOr((unsigned long long*)over, 4ull);
-        return;
-    }
+    const int64_t base[4] = {0, cls[0], cls[0] + cls[1], cls[0] + cls[1] + cls[2]};
     const int32_t id = leaves[L];
     const int32_t st = start[id], c = count[id];
-    const int k = (int)(toff[L + 1] - toff[L]);
-    int64_t q = toff[L];
+    const int k = task_split(c);
     int32_t t0 = 0;
     for (int i = 0; i < k; i++) {
         const int32_t m = c / k + (i < c % k ? 1 : 0);
@@ -864,7 +872,12 @@ __global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* 
         tk.t0 = st + t0;
         tk.nt = m;
         tk.S = lanes_per_pair((m + 1) / 2);
-        tasks[q++] = tk;
+        const int q = lane_class(tk.S);
+        const int64_t pos = base[q] + (int64_t)atomicAdd(fill + q, 1ull);
+        if (pos < cap)
+            tasks[pos] = tk;
+        else
+            atomicOr((unsigned long long*)over, 4ull);
         t0 += m;
     }
 }
@@ -1142,9 +1155,10 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
-    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_count.p, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, L, c->scan_tmp.p, s, dc + kDcLeaves);
-    (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po, c->offs.p), note_launch());
+    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 8 * sizeof(int64_t), s));
+    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_count.p,
+                                  (unsigned long long*)(dc + kDcClass)), note_launch());
+    (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po), note_launch());
     STS_LAUNCH_CHECK();
     if (!cap) {
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1184,8 +1198,9 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
                              chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
                              (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L,
                              c->wover.p, c->d_status, dc + kDcOver), note_launch());
-    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_start.p, c->nd_count.p, c->offs.p,
-                                 (int64_t)c->tasks.cap, c->tasks.p, dc + kDcOver), note_launch());
+    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
+                                 (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
+                                 dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
     c->list_theta = theta;
     c->have_lists = true;
