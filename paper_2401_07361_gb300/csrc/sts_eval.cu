@@ -226,10 +226,108 @@ __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int
 }
 
 // ------------------------------------------------------------------------ mixed tree
-constexpr int kStagePad = kStage + 32;  // room for padding a block to a multiple of 4 S (S <= 8)
+constexpr int kStagePad = kStage + 32;  // one stage: a group of padded blocks
+#ifndef STS_EVAL_MIN_BLOCKS
+#define STS_EVAL_MIN_BLOCKS 3  // resident blocks per SM asked of the register allocator
+#endif
+constexpr int kRing = 64;               // block descriptors per warp: two windows of 32
+
+// Per-warp shared state of the mixed evaluation: two stages and a ring of block descriptors.
+struct EvalSmem {
+    float4 stage[2][kStagePad];
+    float4 off[kRing];  // source offset (dx, dy, dz) of the block
+    int4 info[kRing];   // first source (slot or cluster), count, kind, padded start in its window
+};
+
+// A group of consecutive blocks staged together: [e0, e1) of the task's list, whose padded
+// counts (multiples of 4 S) add up to at most one stage; base = padded start of e0.
+struct Group {
+    int e0, e1, base;
+};
+
+// Loads the descriptors of list blocks [wb, wb + 32) into the ring (lane j: block wb + j) and
+// returns the lane's inclusive prefix of padded counts within the window.
+template <int S>
+__device__ __forceinline__ int load_window(EvalSmem& sm, int wb, int lane, int nf, int nbt,
+                                           const FarEntry* __restrict__ fe, const NearEntry* __restrict__ ne,
+                                           int M, float tau_r)
+{
+    const int e = wb + lane;
+    int idx = 0, cnt = 0, kind = 0;
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    if (e < nbt) {
+        if (e < nf) {
+            const FarEntry f = fe[e];
+            idx = f.slot;
+            cnt = M;
+            dx = f.dx;
+            dy = f.dy;
+            dz = f.dz;
+        } else {
+            const NearEntry q = ne[e - nf];
+            idx = q.start;
+            cnt = q.count;
+            dx = q.dx;
+            dy = q.dy;
+            dz = q.dz;
+            kind = q.gap < tau_r ? 2 : 1;
+        }
+    }
+    const int pc = (cnt + 4 * S - 1) / (4 * S) * (4 * S);
+    int inc = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += v;
+    }
+    sm.off[e & (kRing - 1)] = make_float4(dx, dy, dz, 0.f);
+    sm.info[e & (kRing - 1)] = make_int4(idx, cnt, kind, inc - pc);
+    __syncwarp();
+    return inc;
+}
+
+// The largest group of consecutive blocks from e0 on that fits one stage; loads the next window
+// of descriptors when e0 starts it.  An empty group (e0 == e1) ends the task.
+template <int S>
+__device__ __forceinline__ Group form_group(EvalSmem& sm, int e0, int& wb, int& winc, int lane, int nf, int nbt,
+                                            const FarEntry* __restrict__ fe, const NearEntry* __restrict__ ne,
+                                            int M, float tau_r)
+{
+    Group g;
+    g.e0 = g.e1 = e0;
+    g.base = 0;
+    if (e0 >= nbt) return g;
+    if (e0 >= wb + 32) {
+        wb += 32;
+        winc = load_window<S>(sm, wb, lane, nf, nbt, fe, ne, M, tau_r);
+    }
+    const int r = e0 - wb;
+    const int prev = __shfl_sync(kFull, winc, (r + 31) & 31);
+    g.base = r > 0 ? prev : 0;
+    const bool in = lane >= r && wb + lane < nbt && winc - g.base <= kStagePad;
+    g.e1 = e0 + __popc(__ballot_sync(kFull, in));
+    return g;
+}
+
+// Copies the blocks of a group into a stage (cp.async, 16 bytes per entry), each at its padded
+// start and padded with zero-weight entries far from every target to a multiple of 4 S.
+template <int S>
+__device__ __forceinline__ void issue_group(const EvalSmem& sm, const Group& g, float4* st, int lane, int nf,
+                                            const float4* __restrict__ prx32, const float4* __restrict__ src32,
+                                            int M)
+{
+    for (int e = g.e0; e < g.e1; e++) {
+        const int4 in = sm.info[e & (kRing - 1)];
+        float4* dst = st + (in.w - g.base);
+        const float4* src = e < nf ? prx32 + (int64_t)in.x * M : src32 + in.x;
+        for (int i = lane; i < in.y; i += 32) cp_async16(dst + i, src + i);
+        const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
+        if (in.y + lane < cntp) dst[in.y + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+    }
+}
 
 template <int S>
-__device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[kStagePad], int lane,
+__device__ __forceinline__ void eval_task_mixed(const Task& tk, EvalSmem& sm, int lane,
                                                 const int64_t* __restrict__ far_off,
                                                 const FarEntry* __restrict__ far_ent,
                                                 const int64_t* __restrict__ near_coff,
@@ -257,27 +355,34 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[k
     const FarEntry* fe = far_ent + fo;
     const NearEntry* ne = near_ent + co;
 
-    BlockDesc cur = load_desc(0, nf, nbt, fe, ne, M, tau_r);
-    BlockDesc nxt = load_desc(1, nf, nbt, fe, ne, M, tau_r);
-    issue_block(cur, sbuf[0], lane, prx32, src32, M, 4 * S);
+    int wb = 0;
+    int winc = load_window<S>(sm, 0, lane, nf, nbt, fe, ne, M, tau_r);
+    Group cur = form_group<S>(sm, 0, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
+    issue_group<S>(sm, cur, sm.stage[0], lane, nf, prx32, src32, M);
     cp_commit();
-    for (int b = 0; b < nbt; b++) {
-        issue_block(nxt, sbuf[(b + 1) & 1], lane, prx32, src32, M, 4 * S);
+    Group nxt = form_group<S>(sm, cur.e1, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
+    for (int b = 0; cur.e1 > cur.e0; b++) {
+        issue_group<S>(sm, nxt, sm.stage[(b + 1) & 1], lane, nf, prx32, src32, M);
         cp_commit();
         cp_wait1();
         __syncwarp();
-        const float4* sb = sbuf[b & 1];
-        const int cntp = (cur.cnt + 4 * S - 1) / (4 * S) * (4 * S);
-        // the source offset is folded into the targets: (y + delta) - x = y - (x - delta)
-        const float ax = t0x - cur.dx, ay = t0y - cur.dy, az = t0z - cur.dz;
-        const float bx = t1x - cur.dx, by = t1y - cur.dy, bz = t1z - cur.dz;
+        const float4* st = sm.stage[b & 1];
         float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
-        bool hit = false;
-        if (cur.kind == 2) {
-            block_pairs<true, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
-            if (hit) block_close_pairs<S>(sb, cur.cnt, ph, ax, ay, az, bx, by, bz, tau2, cur.idx, tk0, tk1, src64, corr);
-        } else {
-            block_pairs<false, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+        for (int e = cur.e0; e < cur.e1; e++) {
+            const float4 o = sm.off[e & (kRing - 1)];
+            const int4 in = sm.info[e & (kRing - 1)];
+            const float4* sb = st + (in.w - cur.base);
+            const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
+            // the source offset is folded into the targets: (y + delta) - x = y - (x - delta)
+            const float ax = t0x - o.x, ay = t0y - o.y, az = t0z - o.z;
+            const float bx = t1x - o.x, by = t1y - o.y, bz = t1z - o.z;
+            bool hit = false;
+            if (in.z == 2) {
+                block_pairs<true, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+                if (hit) block_close_pairs<S>(sb, in.y, ph, ax, ay, az, bx, by, bz, tau2, in.x, tk0, tk1, src64, corr);
+            } else {
+                block_pairs<false, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+            }
         }
         two_sum_add(h0x, l0x, p0x);
         two_sum_add(h0y, l0y, p0y);
@@ -287,7 +392,7 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[k
         two_sum_add(h1z, l1z, p1z);
         __syncwarp();
         cur = nxt;
-        nxt = load_desc(b + 2, nf, nbt, fe, ne, M, tau_r);
+        nxt = form_group<S>(sm, cur.e1, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
     }
     double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
                    (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};
@@ -321,7 +426,7 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, float4 (*sbuf)[k
     }
 }
 
-__global__ void __launch_bounds__(kEvalWarps * 32, 3)
+__global__ void __launch_bounds__(kEvalWarps * 32, STS_EVAL_MIN_BLOCKS)
 k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
              const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
@@ -330,7 +435,7 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
              double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
              unsigned long long* __restrict__ queue)
 {
-    __shared__ __align__(16) float4 sbuf[kEvalWarps][2][kStagePad];
+    extern __shared__ __align__(16) EvalSmem sbuf[];  // kEvalWarps of them
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);  // a recorded step whose tasks overflowed is redone
     for (;;) {
@@ -596,7 +701,10 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         int dev = 0, sms = 0, b32 = 0, b64 = 0;
         STS_CUDA(cudaGetDevice(&dev));
         STS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32, 0));
+        STS_CUDA(cudaFuncSetAttribute(k_eval_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kEvalWarps * sizeof(EvalSmem))));
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32,
+                                                               kEvalWarps * sizeof(EvalSmem)));
         STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64, kEvalWarps64 * 32, 0));
         c->eval_blocks_mixed = std::max(1, sms * b32);
         c->eval_blocks_fp64 = std::max(1, sms * b64);
@@ -624,7 +732,7 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
         const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps), c->eval_blocks_mixed);
         phase_begin(c, kPhEval, s);
-        (k_eval_mixed<<<g, kEvalWarps * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+        (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
                                                     c->near_ent.p, c->prx32.p, M, c->src32.p, c->src64.p, c->perm.p,
                                                     tau2, tau_r, corr, vel, nt_d, ntasks, queue), note_launch());
         phase_end(c, kPhEval, s);
