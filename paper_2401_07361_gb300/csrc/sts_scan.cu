@@ -176,35 +176,42 @@ k_radix_scatter(const uint32_t* __restrict__ key, const int32_t* __restrict__ va
 
 int64_t scan_scratch(int64_t n) { return (n + kScanTile - 1) / kScanTile + 2; }
 
-// Whole scan in one block for n <= kScanTile (most per-level and per-leaf scans).
+// Whole scan in one block, tile by tile with a running carry, for n <= kSingleMax (the
+// per-level node scans and other small scans: one launch instead of three).
+constexpr int64_t kSingleMax = 16 * kScanTile;
+
 __global__ void k_scan_single(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ nd,
                               int64_t* __restrict__ out)
 {
-    if (nd) n = *nd;
+    if (nd) n = min(*nd, n);
     __shared__ int64_t sh[kScanThreads / 32];
-    const int64_t base = (int64_t)threadIdx.x * kScanItems;
-    int64_t v[kScanItems];
-    int64_t sum = 0;
+    int64_t carry = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += kScanTile) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * kScanItems;
+        int64_t v[kScanItems];
+        int64_t sum = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; i++) {
-        v[i] = base + i < n ? in[base + i] : 0;
-        sum += v[i];
-    }
-    int64_t tot;
-    int64_t run = block_excl_scan<kScanThreads>(sum, sh, &tot);
+        for (int i = 0; i < kScanItems; i++) {
+            v[i] = base + i < n ? in[base + i] : 0;
+            sum += v[i];
+        }
+        int64_t tot;
+        int64_t run = carry + block_excl_scan<kScanThreads>(sum, sh, &tot);
 #pragma unroll
-    for (int i = 0; i < kScanItems; i++) {
-        if (base + i < n) out[base + i] = run;
-        run += v[i];
+        for (int i = 0; i < kScanItems; i++) {
+            if (base + i < n) out[base + i] = run;
+            run += v[i];
+        }
+        carry += tot;
     }
-    if (threadIdx.x == 0) out[n] = tot;
+    if (threadIdx.x == 0) out[n] = carry;
 }
 
 void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s,
                         const int64_t* n_dev)
 {
     // with n_dev, n is only a capacity: the kernels read the count from the device
-    if (n <= kScanTile) {
+    if (n <= kSingleMax) {
         (k_scan_single<<<1, kScanThreads, 0, s>>>(in, n, n_dev, out), note_launch());
         return;
     }

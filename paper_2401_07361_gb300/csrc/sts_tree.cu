@@ -213,18 +213,19 @@ __global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node,
 // and the launches need no host-side count (the whole build can be captured in a graph).
 __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_size, int max_level,
                               const int32_t* __restrict__ level, const int32_t* __restrict__ count,
-                              const double* __restrict__ geom, int32_t* __restrict__ leaf,
+                              double* __restrict__ geom, int32_t* __restrict__ leaf,
                               double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc,
                               double* __restrict__ mid)
 {
     const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
     for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
          p += (int32_t)(gridDim.x * blockDim.x)) {
+        double* g = geom + 13 * (int64_t)p;
+        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+        if (l > 0) node_geometry(g, v1, v2, v3);  // circumcentre and radius (roots: k_roots)
         const bool split = count[p] > leaf_size && level[p] < max_level;
         leaf[p] = split ? 0 : 1;
         if (!split) continue;
-        const double* g = geom + 13 * (int64_t)p;
-        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
         const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
         double* mm = mid + 9 * (int64_t)p;
         gst(mm, m12);
@@ -241,17 +242,25 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
     }
 }
 
+// Per particle: first the move of level l - 1 (a particle of a split node of level l - 1 goes
+// to the child its digit names), then the digit of its node if that node of level l splits.
 __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const double* __restrict__ pos,
-                                  int64_t n, const int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
+                                  int64_t n, int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
                                   const double* __restrict__ norm, const float4* __restrict__ norm32,
-                                  uint8_t* __restrict__ digit, int32_t* __restrict__ cc)
+                                  const int32_t* __restrict__ child, uint8_t* __restrict__ digit,
+                                  int32_t* __restrict__ cc)
 {
     const int32_t lb = (int32_t)lvl[l];
+    const int32_t pb = l > 0 ? (int32_t)lvl[l - 1] : 0;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int p = -1, d = 0;
     bool active = false;
     if (i < n) {
         p = nodeof[i];
+        if (p >= pb && p < lb && leaf[p] == 0) {
+            p = child[4 * p + digit[i]];
+            nodeof[i] = p;
+        }
         active = p >= lb && leaf[p] == 0;
     }
     if (active) {
@@ -308,13 +317,14 @@ __global__ void k_level_nch(const int64_t* __restrict__ lvl, int l, const int32_
 // Children of level l numbered in key order from le = lvl[l + 1] on (off = scan of nch).
 // A child beyond the node capacity is not created: its particles stay with the parent and
 // the overflow bit is set, so a captured build reports it instead of writing out of range.
-__global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
-                                 int64_t cap, const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
+__global__ void k_level_children(int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
+                                 const int64_t* __restrict__ nl, int64_t cap, const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
                                  int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
                                  int32_t* count, int32_t* leaf, double* geom, int32_t* __restrict__ child,
                                  int64_t* __restrict__ over, const double* __restrict__ mid)
 {
     const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[l + 2] = min((int64_t)le + off[*nl], cap);  // end of level l + 1
     for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
          p += (int32_t)(gridDim.x * blockDim.x)) {
         if (leaf[p]) {
@@ -354,7 +364,7 @@ __global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const i
             start[id] = st;
             count[id] = c;
             leaf[id] = 0;
-            double* gc = geom + 13 * (int64_t)id;  // vertices; centre and radius in k_child_geometry
+            double* gc = geom + 13 * (int64_t)id;  // vertices; centre and radius in k_level_nodes
             gst(gc, cv[d][0]);
             gst(gc + 3, cv[d][1]);
             gst(gc + 6, cv[d][2]);
@@ -365,35 +375,6 @@ __global__ void k_level_children(const int64_t* __restrict__ lvl, int l, const i
         first_child[p] = nc ? first : -1;
         nchild[p] = nc;
     }
-}
-
-// lvl[l + 2] = end of level l + 1 (capped at the node capacity).
-__global__ void k_level_end(int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
-                            const int64_t* __restrict__ nl, int64_t cap)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) lvl[l + 2] = min(lvl[l + 1] + off[*nl], cap);
-}
-
-// Circumcentre and chord radius of the nodes of level l + 1 (vertices written by
-// k_level_children), one thread per node.
-__global__ void k_child_geometry(const int64_t* __restrict__ lvl, int l, double* __restrict__ geom)
-{
-    const int64_t lb = lvl[l + 1], le = lvl[l + 2];
-    for (int64_t q = lb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < le; q += (int64_t)gridDim.x * blockDim.x) {
-        double* g = geom + 13 * q;
-        node_geometry(g, gld(g), gld(g + 3), gld(g + 6));
-    }
-}
-
-__global__ void k_level_assign(const int64_t* __restrict__ lvl, int l, int64_t n, const int32_t* __restrict__ leaf,
-                               const int32_t* __restrict__ child, const uint8_t* __restrict__ digit,
-                               int32_t* __restrict__ nodeof)
-{
-    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int p = nodeof[i];
-    if (p >= lb && p < le && leaf[p] == 0) nodeof[i] = child[4 * p + digit[i]];
 }
 
 // After the level loop: nodes = lvl[last]; a last level that still produced children means
@@ -590,6 +571,13 @@ __device__ __forceinline__ uint64_t dfs_key(uint64_t key, int lv)
     return ((face << (2 * lv)) | low) << (2 * (kMaxLevel - lv));
 }
 
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total)
 {
     int x = v;
@@ -690,7 +678,29 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
         if (!fill && lane == 0) wover[L] = 1;
         return;
     }
-    if (!fill && lane == 0) wover[L] = 0;
+    if (!fill) {
+        // the counts need no order
+        int nf = 0, nn = 0, nch = 0;
+        for (int i = lane; i < nterm; i += 32) {
+            const int32_t tn = tnode[w][i];
+            if (tn < 0) {
+                nf++;
+            } else {
+                nn++;
+                nch += (count[tn] + kStage - 1) / kStage;
+            }
+        }
+        nf = warp_sum(nf);
+        nn = warp_sum(nn);
+        nch = warp_sum(nch);
+        if (lane == 0) {
+            wover[L] = 0;
+            cnt[L] = nf;
+            cnt[ldc + L] = nn;
+            cnt[2 * ldc + L] = nch;
+        }
+        return;
+    }
     // bitonic sort of the terminals by key (padding keys sort last)
     int P = 1;
     while (P < nterm) P <<= 1;
@@ -769,11 +779,6 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
         nf += __popc(fm);
         nn += __popc(nm);
         nch += chtot;
-    }
-    if (!fill && lane == 0) {
-        cnt[L] = (int32_t)nf;
-        cnt[ldc + L] = (int32_t)nn;
-        cnt[2 * ldc + L] = (int32_t)nch;
     }
 }
 
@@ -1056,21 +1061,16 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
                                        c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p,
                                        c->nd_mid.p), note_launch());
         (k_level_particles<<<blocks(n, T), T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_leaf.p,
-                                                      c->nd_norm.p, c->nd_norm32.p, c->digit.p, c->nd_cc.p),
-         note_launch());
+                                                      c->nd_norm.p, c->nd_norm32.p, c->nd_child.p, c->digit.p,
+                                                      c->nd_cc.p), note_launch());
         (k_level_nch<<<g, T, 0, s>>>(lvl, level, c->nd_leaf.p, c->nd_cc.p, c->flags.p, dc + kDcTmp),
          note_launch());
         exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_tmp.p, s,
                            dc + kDcTmp);
-        (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, capn, c->nd_cc.p, c->nd_level.p, c->nd_key.p,
-                                          c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                          c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p, dc + kDcOver,
-                                          c->nd_mid.p), note_launch());
-        (k_level_end<<<1, 32, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn), note_launch());
-        (k_child_geometry<<<cap ? gnode : blocks(std::max<int64_t>(4 * (le - lb), 1), T), T, 0, s>>>(
-             lvl, level, c->nd_geom.p), note_launch());
-        (k_level_assign<<<blocks(n, T), T, 0, s>>>(lvl, level, n, c->nd_leaf.p, c->nd_child.p, c->digit.p,
-                                                  c->nodeof.p), note_launch());
+        (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn, c->nd_cc.p, c->nd_level.p,
+                                          c->nd_key.p, c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p,
+                                          c->nd_start.p, c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p,
+                                          dc + kDcOver, c->nd_mid.p), note_launch());
         STS_LAUNCH_CHECK();
         if (!cap) {
             int64_t next = 0;
