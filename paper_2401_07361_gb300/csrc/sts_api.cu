@@ -88,6 +88,7 @@ sts_ctx::~sts_ctx()
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
+    up_frame32.release(); src_hl.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
@@ -319,6 +320,8 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->up_toff.reserve(nodes + 2));
     STS_CUDA(c->list_cnt.reserve(std::max(3 * n + 3, nodes + 1)));
     STS_CUDA(c->up_frame.reserve(12 * nodes + 12));
+    STS_CUDA(c->up_frame32.reserve(18 * nodes + 18));
+    STS_CUDA(c->src_hl.reserve(2 * n + 2));
     STS_CUDA(c->up_tasks.reserve(upt));
     STS_CUDA(c->prx64.reserve(nodes * M + 1));
     STS_CUDA(c->prx32.reserve(nodes * M + 1));

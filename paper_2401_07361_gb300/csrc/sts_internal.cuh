@@ -163,6 +163,7 @@ struct sts_ctx {
     sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
     sts::DevBuf<float4> nd_norm32;       // [nodes,3]: the normals in FP32 + pre-filter margin
     sts::DevBuf<double> nd_mid;          // [nodes,9]: edge midpoints m12, m23, m31 of split nodes
+    int num_sms = 0;                                  // SMs of the context's device
     int eval_blocks_mixed = 0, eval_blocks_fp64 = 0;  // resident blocks of the persistent eval kernels
     sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
@@ -199,12 +200,14 @@ struct sts_ctx {
     int64_t n_up_tasks = 0;
     sts::DevBuf<double> up_part;         // [tasks, M] partial moments
     sts::DevBuf<double> up_frame;        // [C,12] barycentric frame of each cluster
+    sts::DevBuf<float> up_frame32;       // [C,18] the frame in FP32 and the centre as FP32 hi, lo
     sts::DevBuf<double4> prx64;          // [C,M] (proxy point, 2 W)
     sts::DevBuf<float4> prx32;           // [C,M] (proxy point - c_cluster, 2 W)
 
     // ---- sorted particle data --------------------------------------------------------
     sts::DevBuf<double4> src64;          // [n] sorted (x, y, z, 2 w)
     sts::DevBuf<float4> src32;           // [n] sorted (x - c_leaf, 2 w)
+    sts::DevBuf<float4> src_hl;          // [2n] sorted: hi (x, y, z, w), lo (x, y, z, 0) with x = hi + lo
 
     // ---- interaction lists (per leaf in depth-first order) --------------------------
     bool have_lists = false;

@@ -225,7 +225,10 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
         if (l > 0) node_geometry(g, v1, v2, v3);  // circumcentre and radius (roots: k_roots)
         const bool split = count[p] > leaf_size && level[p] < max_level;
         leaf[p] = split ? 0 : 1;
-        if (!split) continue;
+        if (!split) {
+            norm32[3 * (int64_t)p] = make_float4(0.f, 0.f, 0.f, -1.f);  // w < 0: no digits (a leaf)
+            continue;
+        }
         const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
         double* mm = mid + 9 * (int64_t)p;
         gst(mm, m12);
@@ -242,61 +245,84 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
     }
 }
 
-// Per particle: first the move of level l - 1 (a particle of a split node of level l - 1 goes
-// to the child its digit names), then the digit of its node if that node of level l splits.
+// Per particle: first the move of level l - 1 (a particle of a node of level l - 1 goes to
+// the child its digit names; a leaf's child table points at itself), then the digit of its
+// node if that node of level l splits (norm32.w >= 0), counted per (node, digit) in cc.  The
+// loads of one particle form two dependent rounds (node, then child and normals).  Levels with
+// at most kPrivNodes nodes count in shared memory first (one global add per counter and
+// block): there every counter takes thousands of increments, which serialise in L2.
+constexpr int kPrivNodes = 256;
+
 __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const double* __restrict__ pos,
-                                  int64_t n, int32_t* __restrict__ nodeof, const int32_t* __restrict__ leaf,
-                                  const double* __restrict__ norm, const float4* __restrict__ norm32,
-                                  const int32_t* __restrict__ child, uint8_t* __restrict__ digit,
-                                  int32_t* __restrict__ cc)
+                                  int64_t n, int32_t* __restrict__ nodeof, const double* __restrict__ norm,
+                                  const float4* __restrict__ norm32, const int32_t* __restrict__ child,
+                                  uint8_t* __restrict__ digit, int32_t* __restrict__ cc)
 {
-    const int32_t lb = (int32_t)lvl[l];
+    __shared__ int32_t shc[4 * kPrivNodes];
+    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
     const int32_t pb = l > 0 ? (int32_t)lvl[l - 1] : 0;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int p = -1, d = 0;
-    bool active = false;
-    if (i < n) {
-        p = nodeof[i];
-        if (p >= pb && p < lb && leaf[p] == 0) {
-            p = child[4 * p + digit[i]];
-            nodeof[i] = p;
-        }
-        active = p >= lb && leaf[p] == 0;
+    const bool priv = le - lb <= kPrivNodes;
+    if (priv) {
+        for (int k = threadIdx.x; k < 4 * (le - lb); k += blockDim.x) shc[k] = 0;
+        __syncthreads();
     }
-    if (active) {
-        const g3 x = gld(pos + 3 * i);
-        const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
-        const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
-        // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
-        d = -1;
-        for (int a = 0; a < 3; a++) {
-            const float4 q = norm32[3 * (int64_t)p + a];
-            const float t = fdot(q.x, q.y, q.z, fx, fy, fz);
-            const float thr = q.w * scale;
-            if (t > thr) {
-                d = a;
-                break;
+    const int64_t nr = (n + 31) & ~(int64_t)31;  // whole warps run every trip (warp-wide counting)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x) {
+        int p = -1, d = 0;
+        bool active = false;
+        if (i < n) {
+            p = nodeof[i];
+            const int dg = digit[i];
+            const g3 x = gld(pos + 3 * i);
+            if (p >= pb && p < lb) {
+                p = child[4 * p + dg];
+                nodeof[i] = p;
             }
-            if (!(t < -thr)) {
-                d = -2;  // too close to this boundary for FP32
-                break;
+            if (p >= lb) {
+                const float4 q3[3] = {norm32[3 * (int64_t)p], norm32[3 * (int64_t)p + 1],
+                                      norm32[3 * (int64_t)p + 2]};
+                active = q3[0].w >= 0.f;
+                if (active) {
+                    const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
+                    const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+                    // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
+                    d = -1;
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        if (d != -1) continue;
+                        const float t = fdot(q3[a].x, q3[a].y, q3[a].z, fx, fy, fz);
+                        const float thr = q3[a].w * scale;
+                        if (t > thr)
+                            d = a;
+                        else if (!(t < -thr))
+                            d = -2;  // too close to this boundary for FP32
+                    }
+                    if (d == -1) d = 3;
+                    if (d == -2) {
+                        const double* nn = norm + 9 * (int64_t)p;
+                        if (gdot(gld(nn), x) >= 0.0)
+                            d = 0;
+                        else if (gdot(gld(nn + 3), x) >= 0.0)
+                            d = 1;
+                        else if (gdot(gld(nn + 6), x) >= 0.0)
+                            d = 2;
+                        else
+                            d = 3;
+                    }
+                    digit[i] = (uint8_t)d;
+                }
             }
         }
-        if (d == -1) d = 3;
-        if (d == -2) {
-            const double* nn = norm + 9 * (int64_t)p;
-            if (gdot(gld(nn), x) >= 0.0)
-                d = 0;
-            else if (gdot(gld(nn + 3), x) >= 0.0)
-                d = 1;
-            else if (gdot(gld(nn + 6), x) >= 0.0)
-                d = 2;
-            else
-                d = 3;
-        }
-        digit[i] = (uint8_t)d;
+        if (priv)
+            agg_inc(shc, 4 * (p - lb) + d, active);
+        else
+            agg_inc(cc, 4 * p + d, active);
     }
-    agg_inc(cc, 4 * p + d, active);
+    if (priv) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 4 * (le - lb); k += blockDim.x)
+            if (shc[k]) atomicAdd(&cc[4 * (int64_t)lb + k], shc[k]);
+    }
 }
 
 // Number of children of every node of level l (0 for leaves) into nch[p - lb]; nl = nodes.
@@ -330,6 +356,7 @@ __global__ void k_level_children(int64_t* __restrict__ lvl, int l, const int64_t
         if (leaf[p]) {
             first_child[p] = -1;
             nchild[p] = 0;
+            child[4 * p] = child[4 * p + 1] = child[4 * p + 2] = child[4 * p + 3] = p;
             continue;
         }
         const double* g = geom + 13 * (int64_t)p;
@@ -561,8 +588,9 @@ __global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const i
 // traversal emits.  Frontier and terminals live in shared memory; a leaf whose traversal
 // does not fit sets `wover` and is left to k_lists.
 constexpr int kLwWarps = 4;
-constexpr int kLwFront = 512;   // frontier nodes per level
-constexpr int kLwTerm = 512;    // far + near nodes per leaf
+// CAP: frontier nodes per level and far + near nodes per leaf that one warp holds in shared
+// memory (256 for theta >= 0.6, whose lists stay well below it; 512 below, at half the
+// occupancy).  A leaf that needs more goes to the per-thread traversal.
 
 __device__ __forceinline__ uint64_t dfs_key(uint64_t key, int lv)
 {
@@ -590,6 +618,7 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total)
     return x - v;
 }
 
+template <int CAP>
 __global__ void __launch_bounds__(kLwWarps * 32)
 k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
              const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
@@ -604,9 +633,9 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
              int64_t near_cap, int64_t chunk_cap, int64_t ldc, uint8_t* __restrict__ wover,
              int64_t* __restrict__ over)
 {
-    __shared__ int32_t front[kLwWarps][2][kLwFront];
-    __shared__ uint64_t tkey[kLwWarps][kLwTerm];
-    __shared__ int32_t tnode[kLwWarps][kLwTerm];
+    __shared__ int32_t front[kLwWarps][2][CAP];
+    __shared__ uint64_t tkey[kLwWarps][CAP];
+    __shared__ int32_t tnode[kLwWarps][CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t L = (int64_t)blockIdx.x * kLwWarps + w;
     if (L >= *nleaves_p) return;
@@ -651,7 +680,7 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
             const int nc = kind == 3 ? nchild[s] : 0;
             int ctot;
             const int coff = warp_excl_scan(nc, lane, &ctot);
-            if (nnext + ctot > kLwFront) {
+            if (nnext + ctot > CAP) {
                 bad = true;
                 break;
             }
@@ -659,7 +688,7 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
             nnext += ctot;
             const bool term = kind == 1 || kind == 2;
             const unsigned tm = __ballot_sync(kFull, term);
-            if (nterm + __popc(tm) > kLwTerm) {
+            if (nterm + __popc(tm) > CAP) {
                 bad = true;
                 break;
             }
@@ -1044,6 +1073,13 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     const unsigned gnode = cap ? (unsigned)std::min<int64_t>(4096, (node_cap + T - 1) / T) : 0;
     int level = 0, last = 0;
     c->level_begin.assign(1, 0);
+    if (c->num_sms <= 0) {
+        int dev = 0;
+        STS_CUDA(cudaGetDevice(&dev));
+        STS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // particle passes: a few resident blocks per SM, each striding over many particles
+    const unsigned gpart = (unsigned)std::min<int64_t>(blocks(n, T), 6 * (int64_t)c->num_sms);
     for (level = 0; level < nlev; level++) {
         int64_t capn;
         unsigned g;
@@ -1060,9 +1096,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         (k_level_nodes<<<g, T, 0, s>>>(lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p,
                                        c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p,
                                        c->nd_mid.p), note_launch());
-        (k_level_particles<<<blocks(n, T), T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_leaf.p,
-                                                      c->nd_norm.p, c->nd_norm32.p, c->nd_child.p, c->digit.p,
-                                                      c->nd_cc.p), note_launch());
+        (k_level_particles<<<gpart, T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_norm.p,
+                                                      c->nd_norm32.p, c->nd_child.p, c->digit.p, c->nd_cc.p),
+         note_launch());
         (k_level_nch<<<g, T, 0, s>>>(lvl, level, c->nd_leaf.p, c->nd_cc.p, c->flags.p, dc + kDcTmp),
          note_launch());
         exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_tmp.p, s,
@@ -1140,12 +1176,13 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     const unsigned gw = blocks(std::max<int64_t>(L, 1), kLwWarps);
     // counts: one warp per leaf; leaves whose traversal overflows the warp's shared memory are
     // counted (and later filled) by the per-thread traversal
-    (k_lists_warp<<<gw, kLwWarps * 32, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
-                                               c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
-                                               c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                               c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
-                                               nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
-                                               dc + kDcOver), note_launch());
+    auto klw = theta >= 0.6 ? k_lists_warp<256> : k_lists_warp<512>;
+    (klw<<<gw, kLwWarps * 32, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
+                                     c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
+                                     c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
+                                     c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
+                                     nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
+                                     dc + kDcOver), note_launch());
     (k_lists<<<g, T, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr,
@@ -1185,13 +1222,13 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     } else {
         c->nfar = c->nnear = c->nnear_chunks = c->ntasks = -1;
     }
-    (k_lists_warp<<<gw, kLwWarps * 32, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
-                                               c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
-                                               c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                               c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po, chunk_po,
-                                               c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
-                                               (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap,
-                                               (int64_t)c->near_ent.cap, L, c->wover.p, dc + kDcOver), note_launch());
+    (klw<<<gw, kLwWarps * 32, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
+                                     c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
+                                     c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
+                                     c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po, chunk_po,
+                                     c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
+                                     (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap,
+                                     (int64_t)c->near_ent.cap, L, c->wover.p, dc + kDcOver), note_launch());
     (k_lists<<<g, T, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po,

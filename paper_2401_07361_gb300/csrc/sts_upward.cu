@@ -33,14 +33,19 @@ __global__ void k_prepare(const double* __restrict__ pos, const double* __restri
                           const double* __restrict__ area, const int32_t* __restrict__ perm,
                           const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                           const double* __restrict__ geom, int64_t n, double4* __restrict__ src64,
-                          float4* __restrict__ src32)
+                          float4* __restrict__ src32, float4* __restrict__ src_hl)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t i = perm[k];
     const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-    const double w2 = 2.0 * (zeta[i] * area[i]);
+    const double zw = zeta[i] * area[i];
+    const double w2 = 2.0 * zw;
     src64[k] = make_double4(x, y, z, w2);
+    // x = hi + lo to about 2^-48 |x|: FP32 differences of these pairs keep FP32 relative accuracy
+    const float hx = (float)x, hy = (float)y, hz = (float)z;
+    src_hl[2 * k] = make_float4(hx, hy, hz, (float)zw);
+    src_hl[2 * k + 1] = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.f);
     const double* c = geom + 13 * (int64_t)leaves[slot_leaf[k]] + 9;
     src32[k] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)w2);
 }
@@ -112,8 +117,10 @@ __device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int&
 // Frame of each cluster for the spherical barycentric coordinates of Sec. 3.2 (y = b1 v1 +
 // b2 v2 + b3 v3, Cramer's rule): rows n_i / D with n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2,
 // D = v1 . n1, and b(c) = (n_i / D) . c at the circumcentre.  frame[c][12] in FP64.
+// frame32: the frame in FP32 plus the centre as an FP32 hi/lo pair (18 floats per cluster).
 __global__ void k_cluster_frames(const int64_t* __restrict__ nclu, const int32_t* __restrict__ cnode,
-                                 const double* __restrict__ geom, double* __restrict__ frame)
+                                 const double* __restrict__ geom, double* __restrict__ frame,
+                                 float* __restrict__ frame32)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= *nclu) return;
@@ -127,6 +134,13 @@ __global__ void k_cluster_frames(const int64_t* __restrict__ nclu, const int32_t
     double* f = frame + 12 * c;
     for (int q = 0; q < 9; q++) f[q] = n[q] / D;
     for (int a = 0; a < 3; a++) f[9 + a] = f[3 * a] * g[9] + f[3 * a + 1] * g[10] + f[3 * a + 2] * g[11];
+    float* h = frame32 + 18 * c;
+    for (int q = 0; q < 12; q++) h[q] = (float)f[q];
+    for (int a = 0; a < 3; a++) {
+        const float hi = (float)g[9 + a];
+        h[12 + a] = hi;
+        h[15 + a] = (float)(g[9 + a] - (double)hi);
+    }
 }
 
 // Moments of one (cluster, chunk) task.  T = float (mixed) or double (FP64).  Each thread
@@ -137,9 +151,9 @@ template <class T>
 __global__ void __launch_bounds__(kUpChunk)
 k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
          const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-         const double* __restrict__ geom, const double* __restrict__ frame,
-         const double4* __restrict__ src64, int d, int M, double* __restrict__ part,
-         const int64_t* __restrict__ ntasks)
+         const double* __restrict__ geom, const double* __restrict__ frame, const float* __restrict__ frame32,
+         const double4* __restrict__ src64, const float4* __restrict__ src_hl, int d, int M,
+         double* __restrict__ part, const int64_t* __restrict__ ntasks)
 {
     if (blockIdx.x >= *ntasks) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -159,14 +173,19 @@ k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
     T b[3] = {T(0), T(0), T(0)};
     T w = T(0);
     if (valid) {
-        const double4 y = src64[j];
-        w = T(0.5 * y.w);
         if (sizeof(T) == sizeof(double)) {
+            const double4 y = src64[j];
+            w = T(0.5 * y.w);
             for (int a = 0; a < 3; a++) b[a] = T(f[3 * a] * y.x + f[3 * a + 1] * y.y + f[3 * a + 2] * y.z);
         } else {
-            const float dx = (float)(y.x - g[9]), dy = (float)(y.y - g[10]), dz = (float)(y.z - g[11]);
-            for (int a = 0; a < 3; a++)
-                b[a] = (float)f[9 + a] + ((float)f[3 * a] * dx + (float)f[3 * a + 1] * dy + (float)f[3 * a + 2] * dz);
+            // all-FP32: y - c from the hi/lo pairs, then the frame about the centre
+            const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
+            const float* h = frame32 + 18 * (int64_t)tk.x;
+            const float dx = (hi.x - h[12]) + (lo.x - h[15]);
+            const float dy = (hi.y - h[13]) + (lo.y - h[16]);
+            const float dz = (hi.z - h[14]) + (lo.z - h[17]);
+            w = T(hi.w);
+            for (int a = 0; a < 3; a++) b[a] = h[9 + a] + (h[3 * a] * dx + h[3 * a + 1] * dy + h[3 * a + 2] * dz);
         }
     }
     for (int a = 0; a < 3; a++) {
@@ -248,9 +267,11 @@ int prepare_sources(sts_ctx* c, const double* zeta, const double* area, cudaStre
     const int64_t n = c->n;
     STS_CUDA(c->src64.reserve(n + 1));
     STS_CUDA(c->src32.reserve(n + 1));
+    STS_CUDA(c->src_hl.reserve(2 * n + 2));
     if (n > 0)
-        (k_prepare<<<blocks(n, 256), 256, 0, s>>>(c->pos.p, zeta, area, c->perm.p, c->slot_leaf.p,
-                                                 c->leaves.p, c->nd_geom.p, n, c->src64.p, c->src32.p), note_launch());
+        (k_prepare<<<blocks(n, 256), 256, 0, s>>>(c->pos.p, zeta, area, c->perm.p, c->slot_leaf.p, c->leaves.p,
+                                                 c->nd_geom.p, n, c->src64.p, c->src32.p, c->src_hl.p),
+         note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
@@ -269,6 +290,7 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
         STS_CUDA(c->list_cnt.reserve(nn + 1));
         STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
         STS_CUDA(c->up_frame.reserve(12 * nn + 12));
+        STS_CUDA(c->up_frame32.reserve(18 * nn + 18));
     }
     const unsigned g = blocks(std::max<int64_t>(nn, 1), 256);
     (k_cluster_flags<<<g, 256, 0, s>>>(dc + kDcNodes, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
@@ -290,7 +312,8 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
     } else {
         c->nclusters = c->n_up_tasks = c->nleaves = -1;  // known after the graph runs
     }
-    (k_cluster_frames<<<g, 256, 0, s>>>(dc + kDcClusters, c->cluster_node.p, c->nd_geom.p, c->up_frame.p),
+    (k_cluster_frames<<<g, 256, 0, s>>>(dc + kDcClusters, c->cluster_node.p, c->nd_geom.p, c->up_frame.p,
+                                        c->up_frame32.p),
      note_launch());
     (k_up_tasks<<<g, 256, 0, s>>>(dc + kDcNodes, c->cluster_slot.p, c->up_toff.p, (int64_t)c->up_tasks.cap,
                                   c->up_tasks.p, dc + kDcOver), note_launch());
@@ -323,13 +346,13 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
         if (!cap) STS_CUDA(cudaFuncSetAttribute(k_upward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         (k_upward<double><<<(unsigned)nupt, kUpChunk, sm, s>>>(
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
-            c->src64.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
+            c->up_frame32.p, c->src64.p, c->src_hl.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     } else {
         const size_t sm = (3 * (degree + 1) * LD + 2 * kUpChunk) * sizeof(float);
         if (!cap) STS_CUDA(cudaFuncSetAttribute(k_upward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         (k_upward<float><<<(unsigned)nupt, kUpChunk, sm, s>>>(
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
-            c->src64.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
+            c->up_frame32.p, c->src64.p, c->src_hl.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     }
     (k_contract<<<(unsigned)nclu, 64, 0, s>>>(c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p,
                                              ref->d_beta.p, ref->d_vinv.p, degree, M, c->prx64.p, c->prx32.p,
