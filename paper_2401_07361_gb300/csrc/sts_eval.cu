@@ -453,8 +453,24 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
                 eval_task_mixed<2>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
                                    perm, tau2, tau_r, corr, vel);
                 break;
+            case 3:
+                eval_task_mixed<3>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
             case 4:
                 eval_task_mixed<4>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            case 5:
+                eval_task_mixed<5>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            case 6:
+                eval_task_mixed<6>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
+                                   perm, tau2, tau_r, corr, vel);
+                break;
+            case 7:
+                eval_task_mixed<7>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
                                    perm, tau2, tau_r, corr, vel);
                 break;
             default:

@@ -120,9 +120,9 @@ enum DevCount {
     kDcOver,   // overflow bits: 1 node capacity, 2 levels, 4 list or task capacity
     kDcTmp,
     kDcLevel = 16,  // level_begin[0 .. kMaxLevel + 3]
-    kDcClass = 44,      // evaluation tasks per lane class S = 1, 2, 4, 8 (4 counters)
-    kDcClassFill = 48,  // tasks placed so far per class (4 counters)
-    kDcQueue = 52,      // next task of the persistent evaluation kernels
+    kDcClass = 44,      // evaluation tasks per lane class S = 1 .. 8 (8 counters)
+    kDcClassFill = 52,  // tasks placed so far per class (8 counters)
+    kDcQueue = 60,      // next task of the persistent evaluation kernels
     kDcSize = 64
 };
 

@@ -211,6 +211,11 @@ __global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node,
 // The level kernels read the node range of level l from the device array lvl: level l holds
 // nodes [lvl[l], lvl[l + 1]).  Node kernels stride over that range, so any grid size works
 // and the launches need no host-side count (the whole build can be captured in a graph).
+//
+// Level nodes, four lanes per node (the FP64 square roots and divisions are long dependent
+// chains, so the work of one node is spread): lane a < 3 forms the edge midpoint m_a and the
+// child-digit normal n_a = m_a x m_(a+2 mod 3); lane 3 the circumcentre and radius (levels
+// below the roots).  Leaves get norm32.w = -1 (no digits).
 __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_size, int max_level,
                               const int32_t* __restrict__ level, const int32_t* __restrict__ count,
                               double* __restrict__ geom, int32_t* __restrict__ leaf,
@@ -218,30 +223,40 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
                               double* __restrict__ mid)
 {
     const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
-         p += (int32_t)(gridDim.x * blockDim.x)) {
-        double* g = geom + 13 * (int64_t)p;
-        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
-        if (l > 0) node_geometry(g, v1, v2, v3);  // circumcentre and radius (roots: k_roots)
-        const bool split = count[p] > leaf_size && level[p] < max_level;
-        leaf[p] = split ? 0 : 1;
-        if (!split) {
-            norm32[3 * (int64_t)p] = make_float4(0.f, 0.f, 0.f, -1.f);  // w < 0: no digits (a leaf)
-            continue;
+    const int64_t nt = ((int64_t)4 * (le - lb) + 31) & ~(int64_t)31;  // whole warps (shuffles below)
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = lb + (int32_t)(t >> 2);
+        const int a = (int)(t & 3);
+        const bool valid = p < le;
+        bool split = false;
+        g3 m = gmk(0.0, 0.0, 0.0);
+        if (valid) {
+            double* g = geom + 13 * (int64_t)p;
+            split = count[p] > leaf_size && level[p] < max_level;
+            if (a == 3) {
+                if (l > 0) node_geometry(g, gld(g), gld(g + 3), gld(g + 6));  // roots: k_roots
+                leaf[p] = split ? 0 : 1;
+                if (split)
+                    cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
+                else
+                    norm32[3 * (int64_t)p] = make_float4(0.f, 0.f, 0.f, -1.f);  // w < 0: a leaf
+            } else if (split) {
+                // m_0 = unit(v1 + v2), m_1 = unit(v2 + v3), m_2 = unit(v3 + v1)
+                const g3 va = gld(g + 3 * a), vb = gld(g + 3 * (a == 2 ? 0 : a + 1));
+                m = gunit(gadd(va, vb));
+                gst(mid + 9 * (int64_t)p + 3 * a, m);
+            }
         }
-        const g3 m12 = gunit(gadd(v1, v2)), m23 = gunit(gadd(v2, v3)), m31 = gunit(gadd(v3, v1));
-        double* mm = mid + 9 * (int64_t)p;
-        gst(mm, m12);
-        gst(mm + 3, m23);
-        gst(mm + 6, m31);
-        double* nn = norm + 9 * (int64_t)p;
-        const g3 n3[3] = {gcross(m12, m31), gcross(m23, m12), gcross(m31, m23)};
-        for (int a = 0; a < 3; a++) {
-            gst(nn + 3 * a, n3[a]);
-            const float thr = 1e-6f * (float)(fabs(n3[a].x) + fabs(n3[a].y) + fabs(n3[a].z));
-            norm32[3 * (int64_t)p + a] = make_float4((float)n3[a].x, (float)n3[a].y, (float)n3[a].z, thr);
+        // m_(a+2 mod 3) from lane a + 2 (a = 0) or a - 1 (a = 1, 2) of the same node
+        const int src = (lane & ~3) + (a == 0 ? 2 : a - 1);
+        const g3 mp = gmk(__shfl_sync(kFull, m.x, src), __shfl_sync(kFull, m.y, src), __shfl_sync(kFull, m.z, src));
+        if (valid && split && a < 3) {
+            const g3 nv = gcross(m, mp);
+            gst(norm + 9 * (int64_t)p + 3 * a, nv);
+            const float thr = 1e-6f * (float)(fabs(nv.x) + fabs(nv.y) + fabs(nv.z));
+            norm32[3 * (int64_t)p + a] = make_float4((float)nv.x, (float)nv.y, (float)nv.z, thr);
         }
-        cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
     }
 }
 
@@ -820,7 +835,9 @@ __global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restric
     dc[kDcFar] = far_off[L];
     dc[kDcNear] = near_off[L];
     dc[kDcChunks] = chunk_off[L];
-    dc[kDcTasks] = dc[kDcClass] + dc[kDcClass + 1] + dc[kDcClass + 2] + dc[kDcClass + 3];
+    int64_t t = 0;
+    for (int q = 0; q < 8; q++) t += dc[kDcClass + q];
+    dc[kDcTasks] = t;
 }
 
 __global__ void k_copy_count(const int64_t* __restrict__ src, int64_t* __restrict__ dst)
@@ -838,12 +855,8 @@ __global__ void k_node_f32(const int64_t* __restrict__ nnodes, const double* __r
     c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
 }
 
-// Lanes sharing a pair of targets: the largest power of two S <= 8 with S * pairs <= 32.
-__device__ __forceinline__ int lanes_per_pair(int pairs)
-{
-    const int q = 32 / pairs;
-    return q >= 8 ? 8 : (q >= 4 ? 4 : (q >= 2 ? 2 : 1));
-}
+// Lanes sharing a pair of targets: the largest S <= 8 with S * pairs <= 32.
+__device__ __forceinline__ int lanes_per_pair(int pairs) { return min(8, 32 / pairs); }
 
 // Splits a leaf of nt targets into k warp tasks of nearly equal size, two targets per lane
 // and S lanes per pair of targets.  k maximises the fraction of useful interactions per warp
@@ -866,9 +879,7 @@ __device__ int task_split(int nt)
     return best;
 }
 
-__device__ __forceinline__ int lane_class(int S) { return S == 1 ? 0 : (S == 2 ? 1 : (S == 4 ? 2 : 3)); }
-
-// Counts the warp tasks of every leaf by lane class (S = 1, 2, 4, 8) into cls[0..3].
+// Counts the warp tasks of every leaf by lane class (S = 1 .. 8) into cls[0..7].
 __global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
                              const int32_t* __restrict__ count, unsigned long long* __restrict__ cls)
 {
@@ -876,11 +887,7 @@ __global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t*
     if (L >= *nleaves) return;
     const int32_t c = count[leaves[L]];
     const int k = task_split(c);
-    int per[4] = {0, 0, 0, 0};
-    for (int i = 0; i < k; i++) per[lane_class(lanes_per_pair((c / k + (i < c % k ? 1 : 0) + 1) / 2))]++;
-#pragma unroll
-    for (int q = 0; q < 4; q++)
-        if (per[q]) atomicAdd(cls + q, (unsigned long long)per[q]);
+    for (int i = 0; i < k; i++) atomicAdd(cls + lanes_per_pair((c / k + (i < c % k ? 1 : 0) + 1) / 2) - 1, 1ull);
 }
 
 // Writes the warp tasks grouped by lane class, S = 1 first: a task's run time grows with the
@@ -894,7 +901,10 @@ __global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* 
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= *nleaves) return;
-    const int64_t base[4] = {0, cls[0], cls[0] + cls[1], cls[0] + cls[1] + cls[2]};
+    int64_t base[8];
+    base[0] = 0;
+#pragma unroll
+    for (int q = 1; q < 8; q++) base[q] = base[q - 1] + cls[q - 1];
     const int32_t id = leaves[L];
     const int32_t st = start[id], c = count[id];
     const int k = task_split(c);
@@ -906,7 +916,7 @@ __global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* 
         tk.t0 = st + t0;
         tk.nt = m;
         tk.S = lanes_per_pair((m + 1) / 2);
-        const int q = lane_class(tk.S);
+        const int q = tk.S - 1;
         const int64_t pos = base[q] + (int64_t)atomicAdd(fill + q, 1ull);
         if (pos < cap)
             tasks[pos] = tk;
@@ -1093,9 +1103,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
             capn = node_cap;
             g = gnode;
         }
-        (k_level_nodes<<<g, T, 0, s>>>(lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p,
-                                       c->nd_geom.p, c->nd_leaf.p, c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p,
-                                       c->nd_mid.p), note_launch());
+        (k_level_nodes<<<cap ? gnode : blocks(4 * std::max<int64_t>(le - lb, 1), T), T, 0, s>>>(
+             lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p, c->nd_geom.p, c->nd_leaf.p,
+             c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p, c->nd_mid.p), note_launch());
         (k_level_particles<<<gpart, T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_norm.p,
                                                       c->nd_norm32.p, c->nd_child.p, c->digit.p, c->nd_cc.p),
          note_launch());
@@ -1192,7 +1202,7 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
-    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 8 * sizeof(int64_t), s));
+    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
     (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_count.p,
                                   (unsigned long long*)(dc + kDcClass)), note_launch());
     (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po), note_launch());
