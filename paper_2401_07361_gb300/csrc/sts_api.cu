@@ -88,7 +88,7 @@ sts_ctx::~sts_ctx()
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
-    up_frame32.release(); src_hl.release();
+    up_frame32.release(); src_hl.release(); lw_terms.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
@@ -331,6 +331,8 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->near_idx.reserve(grow(c->plan.near, 1024)));
     STS_CUDA(c->near_ent.reserve(grow(c->plan.chunks, 1024)));
     STS_CUDA(c->tasks.reserve(grow(c->plan.tasks, 1024)));
+    // the leaf bound of build_lists while recording, times the larger traversal capacity
+    STS_CUDA(c->lw_terms.reserve(std::min<int64_t>(n, grow(c->plan.leaves, 64)) * 512 + 1));
     STS_CUDA(c->far_off.reserve(n + 1));
     STS_CUDA(c->near_off.reserve(n + 1));
     STS_CUDA(c->near_coff.reserve(n + 1));

@@ -130,7 +130,7 @@ enum DevCount {
 struct Plan {
     int64_t n = -1;
     int ninst = 0, leaf_size = 0, max_level = 0, depth = 0;
-    int64_t nodes = 0, up_tasks = 0, far = 0, near = 0, chunks = 0, tasks = 0, clusters = 0;
+    int64_t nodes = 0, up_tasks = 0, far = 0, near = 0, chunks = 0, tasks = 0, clusters = 0, leaves = 0;
 };
 
 }  // namespace sts
@@ -207,6 +207,7 @@ struct sts_ctx {
     // ---- sorted particle data --------------------------------------------------------
     sts::DevBuf<double4> src64;          // [n] sorted (x, y, z, 2 w)
     sts::DevBuf<float4> src32;           // [n] sorted (x - c_leaf, 2 w)
+    sts::DevBuf<int32_t> lw_terms;       // [leaves, 256 or 512] unsorted terminals of the warp traversal
     sts::DevBuf<float4> src_hl;          // [2n] sorted: hi (x, y, z, w), lo (x, y, z, 0) with x = hi + lo
 
     // ---- interaction lists (per leaf in depth-first order) --------------------------

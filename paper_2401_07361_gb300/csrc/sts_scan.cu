@@ -48,7 +48,7 @@ __global__ void k_scan_reduce(const int32_t* __restrict__ in, int64_t n, const i
                               int64_t* __restrict__ part)
 {
     __shared__ int64_t sh[kScanThreads / 32];
-    if (nd) n = *nd;
+    if (nd) n = min(*nd, n);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t s = 0;
 #pragma unroll
@@ -78,7 +78,7 @@ __global__ void k_scan_top(int64_t* part, int64_t nb)
 __global__ void k_scan_down(const int32_t* __restrict__ in, int64_t n, const int64_t* __restrict__ nd,
                             const int64_t* __restrict__ part, int64_t nb, int64_t* __restrict__ out)
 {
-    if (nd) n = *nd;
+    if (nd) n = min(*nd, n);
     __shared__ int64_t sh[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];

@@ -513,7 +513,7 @@ __global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const i
                         int64_t far_cap, int64_t near_cap, int64_t chunk_cap, int64_t ldc,
                         const uint8_t* __restrict__ only, int* __restrict__ status, int64_t* __restrict__ over)
 {
-    const int64_t nleaves = *nleaves_p;
+    const int64_t nleaves = min(*nleaves_p, ldc);
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= nleaves) return;
     if (only && !only[L]) return;  // the warp traversal handled this leaf
@@ -633,34 +633,26 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int* total)
     return x - v;
 }
 
+// Count pass of the warp traversal, one warp per target leaf: breadth-first from the roots of
+// the leaf's instance (frontier in shared memory), MAC as in k_lists; the terminals (far
+// nodes flagged by the sign bit) go unsorted to terms[L * CAP ...] for the fill pass, the
+// counts to cnt.  A leaf whose frontier or terminal list exceeds CAP is marked in wover and
+// left to the per-thread traversal.
 template <int CAP>
 __global__ void __launch_bounds__(kLwWarps * 32)
-k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
-             const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
-             const int32_t* __restrict__ level, double theta, int leaf_size, const double* __restrict__ geom,
-             const float4* __restrict__ c32, const int32_t* __restrict__ leaf,
-             const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
-             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-             const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ cnt,
-             const int64_t* __restrict__ far_po, const int64_t* __restrict__ near_po,
-             const int64_t* __restrict__ chunk_po, int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
-             FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent, int64_t far_cap,
-             int64_t near_cap, int64_t chunk_cap, int64_t ldc, uint8_t* __restrict__ wover,
-             int64_t* __restrict__ over)
+k_lists_count(const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
+              const int32_t* __restrict__ face_node, const uint64_t* __restrict__ key,
+              const int32_t* __restrict__ level, double theta, int leaf_size, const double* __restrict__ geom,
+              const float4* __restrict__ c32, const int32_t* __restrict__ leaf,
+              const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
+              const int32_t* __restrict__ count, int32_t* __restrict__ cnt, int32_t* __restrict__ terms,
+              int64_t ldc, uint8_t* __restrict__ wover)
 {
     __shared__ int32_t front[kLwWarps][2][CAP];
-    __shared__ uint64_t tkey[kLwWarps][CAP];
     __shared__ int32_t tnode[kLwWarps][CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t L = (int64_t)blockIdx.x * kLwWarps + w;
-    if (L >= *nleaves_p) return;
-    if (fill) {
-        if (wover[L]) return;  // done by k_lists
-        if (far_po[L + 1] > far_cap || near_po[L + 1] > near_cap || chunk_po[L + 1] > chunk_cap) {
-            if (lane == 0) atomicOr((unsigned long long*)over, 4ull);
-            return;
-        }
-    }
+    if (L >= min(*nleaves_p, ldc)) return;
     const int32_t t = leaves[L];
     const double* gt = geom + 13 * (int64_t)t;
     const float4 ct = c32[t];
@@ -707,11 +699,7 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
                 bad = true;
                 break;
             }
-            if (term) {
-                const int pos = nterm + __popc(tm & ((1u << lane) - 1u));
-                tkey[w][pos] = dfs_key(key[s], level[s]);
-                tnode[w][pos] = s | (kind == 1 ? (int32_t)0x80000000 : 0);
-            }
+            if (term) tnode[w][nterm + __popc(tm & ((1u << lane) - 1u))] = s | (kind == 1 ? (int32_t)0x80000000 : 0);
             nterm += __popc(tm);
         }
         __syncwarp();
@@ -719,36 +707,73 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
         nfront = nnext;
     }
     if (bad) {
-        if (!fill && lane == 0) wover[L] = 1;
+        if (lane == 0) wover[L] = 1;
         return;
     }
-    if (!fill) {
-        // the counts need no order
-        int nf = 0, nn = 0, nch = 0;
-        for (int i = lane; i < nterm; i += 32) {
-            const int32_t tn = tnode[w][i];
-            if (tn < 0) {
-                nf++;
-            } else {
-                nn++;
-                nch += (count[tn] + kStage - 1) / kStage;
-            }
+    int nf = 0, nn = 0, nch = 0;
+    int32_t* out = terms + L * CAP;
+    for (int i = lane; i < nterm; i += 32) {
+        const int32_t tn = tnode[w][i];
+        out[i] = tn;
+        if (tn < 0) {
+            nf++;
+        } else {
+            nn++;
+            nch += (count[tn] + kStage - 1) / kStage;
         }
-        nf = warp_sum(nf);
-        nn = warp_sum(nn);
-        nch = warp_sum(nch);
-        if (lane == 0) {
-            wover[L] = 0;
-            cnt[L] = nf;
-            cnt[ldc + L] = nn;
-            cnt[2 * ldc + L] = nch;
-        }
+    }
+    nf = warp_sum(nf);
+    nn = warp_sum(nn);
+    nch = warp_sum(nch);
+    if (lane == 0) {
+        wover[L] = 0;
+        cnt[L] = nf;
+        cnt[ldc + L] = nn;
+        cnt[2 * ldc + L] = nch;
+    }
+}
+
+// Fill pass of the warp traversal: the leaf's terminals from terms, sorted by depth-first key
+// (bitonic sort in shared memory), written at the scanned offsets: far clusters with their
+// FP32 centre offsets, near leaves split into chunks of at most kStage particles.
+template <int CAP>
+__global__ void __launch_bounds__(kLwWarps * 32)
+k_lists_fill(const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
+             const uint64_t* __restrict__ key, const int32_t* __restrict__ level, const double* __restrict__ geom,
+             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+             const int32_t* __restrict__ cluster_slot, const int32_t* __restrict__ terms,
+             const int64_t* __restrict__ far_po, const int64_t* __restrict__ near_po,
+             const int64_t* __restrict__ chunk_po, int32_t* __restrict__ far_idx, int32_t* __restrict__ near_idx,
+             FarEntry* __restrict__ far_ent, NearEntry* __restrict__ near_ent, int64_t far_cap,
+             int64_t near_cap, int64_t chunk_cap, int64_t ldc, const uint8_t* __restrict__ wover,
+             int64_t* __restrict__ over)
+{
+    __shared__ uint64_t tkey[kLwWarps][CAP];
+    __shared__ int32_t tnode[kLwWarps][CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t L = (int64_t)blockIdx.x * kLwWarps + w;
+    if (L >= min(*nleaves_p, ldc)) return;
+    if (wover[L]) return;  // done by k_lists
+    if (far_po[L + 1] > far_cap || near_po[L + 1] > near_cap || chunk_po[L + 1] > chunk_cap) {
+        if (lane == 0) atomicOr((unsigned long long*)over, 4ull);
         return;
     }
-    // bitonic sort of the terminals by key (padding keys sort last)
+    const int32_t t = leaves[L];
+    const double* gt = geom + 13 * (int64_t)t;
+    const int nterm = (int)((far_po[L + 1] - far_po[L]) + (near_po[L + 1] - near_po[L]));
+    const int32_t* in = terms + L * CAP;
     int P = 1;
     while (P < nterm) P <<= 1;
-    for (int i = nterm + lane; i < P; i += 32) tkey[w][i] = ~0ull;
+    for (int i = lane; i < P; i += 32) {
+        uint64_t k = ~0ull;  // padding keys sort last
+        if (i < nterm) {
+            const int32_t tn = in[i];
+            const int32_t s = tn & 0x7fffffff;
+            tnode[w][i] = tn;
+            k = dfs_key(key[s], level[s]);
+        }
+        tkey[w][i] = k;
+    }
     __syncwarp();
     for (int k = 2; k <= P; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -770,7 +795,7 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
         }
     // emit in order: far, near and near chunks get their ranks by warp scans
     int64_t nf = 0, nn = 0, nch = 0;
-    const int64_t fo = fill ? far_po[L] : 0, no = fill ? near_po[L] : 0, co = fill ? chunk_po[L] : 0;
+    const int64_t fo = far_po[L], no = near_po[L], co = chunk_po[L];
     for (int b0 = 0; b0 < nterm; b0 += 32) {
         const int i = b0 + lane;
         int32_t s = -1;
@@ -787,7 +812,7 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
         const unsigned nm = __ballot_sync(kFull, valid && !isfar);
         int chtot;
         const int choff = warp_excl_scan(chunks, lane, &chtot);
-        if (fill && valid) {
+        if (valid) {
             const double* gs = geom + 13 * (int64_t)s;
             const float dx = (float)__dsub_rn(gs[9], gt[9]);
             const float dy = (float)__dsub_rn(gs[10], gt[10]);
@@ -828,10 +853,12 @@ k_lists_warp(int fill, const int64_t* __restrict__ nleaves_p, const int32_t* __r
 
 // List and task totals (scanned offsets read at index nleaves) into the device counters.
 __global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restrict__ far_off,
-                              const int64_t* __restrict__ near_off, const int64_t* __restrict__ chunk_off)
+                              const int64_t* __restrict__ near_off, const int64_t* __restrict__ chunk_off,
+                              int64_t ldc)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int64_t L = dc[kDcLeaves];
+    if (dc[kDcLeaves] > ldc) atomicOr((unsigned long long*)(dc + kDcOver), 4ull);  // recorded leaf bound
+    const int64_t L = min(dc[kDcLeaves], ldc);
     dc[kDcFar] = far_off[L];
     dc[kDcNear] = near_off[L];
     dc[kDcChunks] = chunk_off[L];
@@ -880,11 +907,11 @@ __device__ int task_split(int nt)
 }
 
 // Counts the warp tasks of every leaf by lane class (S = 1 .. 8) into cls[0..7].
-__global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_task_count(const int64_t* __restrict__ nleaves, int64_t ldc, const int32_t* __restrict__ leaves,
                              const int32_t* __restrict__ count, unsigned long long* __restrict__ cls)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= *nleaves) return;
+    if (L >= min(*nleaves, ldc)) return;
     const int32_t c = count[leaves[L]];
     const int k = task_split(c);
     for (int i = 0; i < k; i++) atomicAdd(cls + lanes_per_pair((c / k + (i < c % k ? 1 : 0) + 1) / 2) - 1, 1ull);
@@ -894,13 +921,13 @@ __global__ void k_task_count(const int64_t* __restrict__ nleaves, const int32_t*
 // sources each lane visits (list length / S), so the task queue hands out the longest tasks
 // first and the persistent evaluation kernel ends with short ones.  The order within a class
 // is arbitrary; every task writes only its own targets, so the results do not depend on it.
-__global__ void k_task_fill(const int64_t* __restrict__ nleaves, const int32_t* __restrict__ leaves,
+__global__ void k_task_fill(const int64_t* __restrict__ nleaves, int64_t ldc, const int32_t* __restrict__ leaves,
                             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
                             const int64_t* __restrict__ cls, unsigned long long* __restrict__ fill, int64_t cap,
                             Task* __restrict__ tasks, int64_t* __restrict__ over)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= *nleaves) return;
+    if (L >= min(*nleaves, ldc)) return;
     int64_t base[8];
     base[0] = 0;
 #pragma unroll
@@ -1166,7 +1193,10 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
 {
     c->have_lists = false;
     const bool cap = c->capturing;
-    const int64_t L = cap ? c->n : c->nleaves;  // leaf count or its bound
+    // leaf count, or while recording its planned bound (a replay with more leaves sets the
+    // overflow bit in k_list_totals and is redone)
+    const int64_t L = cap ? std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64) : c->nleaves;
+    const int lcap = theta >= 0.6 ? 256 : 512;  // terminals per leaf held by the warp traversal
     const int T = 128;
     int64_t* dc = c->dc.p;
     if (!cap) {
@@ -1182,17 +1212,16 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     int64_t* near_po = c->near_off.p;
     int64_t* chunk_po = c->near_coff.p;
     STS_CUDA(c->wover.reserve(L + 1));
+    STS_CUDA(c->lw_terms.reserve(L * lcap + 1));
     const unsigned g = blocks(std::max<int64_t>(L, 1), T);
     const unsigned gw = blocks(std::max<int64_t>(L, 1), kLwWarps);
     // counts: one warp per leaf; leaves whose traversal overflows the warp's shared memory are
     // counted (and later filled) by the per-thread traversal
-    auto klw = theta >= 0.6 ? k_lists_warp<256> : k_lists_warp<512>;
-    (klw<<<gw, kLwWarps * 32, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
-                                     c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
-                                     c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                     c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr, nullptr,
-                                     nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
-                                     dc + kDcOver), note_launch());
+    (lcap == 256 ? k_lists_count<256> : k_lists_count<512>)<<<gw, kLwWarps * 32, 0, s>>>(
+        dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta, c->leaf_size, c->nd_geom.p,
+        c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_count.p, c->list_cnt.p,
+        c->lw_terms.p, L, c->wover.p);
+    note_launch();
     (k_lists<<<g, T, 0, s>>>(0, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr,
@@ -1203,9 +1232,9 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
     STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
-    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_count.p,
+    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
                                   (unsigned long long*)(dc + kDcClass)), note_launch());
-    (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po), note_launch());
+    (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po, L), note_launch());
     STS_LAUNCH_CHECK();
     if (!cap) {
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -1232,20 +1261,19 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     } else {
         c->nfar = c->nnear = c->nnear_chunks = c->ntasks = -1;
     }
-    (klw<<<gw, kLwWarps * 32, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p,
-                                     c->nd_level.p, theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p,
-                                     c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p, c->nd_start.p,
-                                     c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po, chunk_po,
-                                     c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
-                                     (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap,
-                                     (int64_t)c->near_ent.cap, L, c->wover.p, dc + kDcOver), note_launch());
+    (lcap == 256 ? k_lists_fill<256> : k_lists_fill<512>)<<<gw, kLwWarps * 32, 0, s>>>(
+        dc + kDcLeaves, c->leaves.p, c->nd_key.p, c->nd_level.p, c->nd_geom.p, c->nd_start.p, c->nd_count.p,
+        c->cluster_slot.p, c->lw_terms.p, far_po, near_po, chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p,
+        c->near_ent.p, (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L, c->wover.p,
+        dc + kDcOver);
+    note_launch();
     (k_lists<<<g, T, 0, s>>>(1, dc + kDcLeaves, c->leaves.p, c->face_node.p, c->nd_key.p, c->nd_level.p, theta,
                              c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p,
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, far_po, near_po,
                              chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
                              (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L,
                              c->wover.p, c->d_status, dc + kDcOver), note_launch());
-    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
+    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
                                  (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
                                  dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();

@@ -328,6 +328,7 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
         c->n_up_tasks = c->h_pinned[kDcUpTasks];
         c->nleaves = c->h_pinned[kDcLeaves];
         c->plan.clusters = std::max(c->plan.clusters, c->nclusters);
+        c->plan.leaves = std::max(c->plan.leaves, c->nleaves);
         c->plan.up_tasks = std::max(c->plan.up_tasks, c->n_up_tasks);
         STS_CUDA(c->up_tasks.reserve(c->n_up_tasks + 1));
     } else {
