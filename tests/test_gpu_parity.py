@@ -98,6 +98,34 @@ def test_lists_bit_exact(ctx, name, theta):
     assert sts.sts_stats(ctx) == st
 
 
+@pytest.mark.parametrize("case", ["clustered_leaf4_theta0.6", "rand20000_leaf16_theta0.3"])
+def test_lists_bit_exact_past_warp_capacity(ctx, case):
+    """Leaves whose lists exceed the warp traversal's shared-memory capacity (256 terminals
+    for theta >= 0.6, 512 below) go to the per-thread traversal; both must give the oracle's
+    lists, and the velocities built on them must match the oracle."""
+    if case.startswith("clustered"):
+        # leaves of 4 particles inside the 0.01-radius cap are triangles of edge ~1e-3: their
+        # FP64 barycentric coordinates carry rounding ~eps / edge, which the two sides take
+        # differently (Cramer's rule on one side, a pre-divided frame on the other), and the
+        # proxy contraction amplifies it; a dropped or doubled interaction would be O(1e-3)
+        pos, leaf, theta, tol = _clustered(4000, 1000, 24), 4, 0.6, 1e-10
+    else:
+        pos, leaf, theta, tol = W.uniform_points(20000, 22), 16, 0.3, 1e-12
+    tr = O.Tree(pos, leaf, 16)
+    o = tr.lists(theta)
+    terms = np.diff(o["far_off"]) + np.diff(o["near_off"])
+    assert terms.max() > (256 if theta >= 0.6 else 512)  # the fallback really runs
+    n = len(pos)
+    zeta, area = _fields(n, 8)
+    p = sts.params(theta=theta, degree=4, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    g = sts.sts_lists_export(ctx)
+    for k in ("far_off", "far_idx", "near_off", "near_idx"):
+        assert np.array_equal(g[k], o[k]), k
+    assert O.rel_l2(v, tr.velocity(zeta, area, theta, 4), area) <= tol
+
+
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("degree", [3, 8])
 def test_velocity_fp64_matches_oracle(ctx, name, degree):
