@@ -78,7 +78,9 @@ void sts_destroy(sts_ctx* ctx);
 /* Message of the calling thread's last error ("" if none).  Never NULL. */
 const char* sts_last_error(void);
 /* Synchronises `stream`, returns STS_OK or the error recorded in the context's device
- * status word (STS_ERR_CAPACITY, STS_ERR_NONFINITE), and clears the word. */
+ * status word (STS_ERR_CAPACITY, STS_ERR_NONFINITE, STS_ERR_TIMEOUT: the mixed evaluation
+ * gave up waiting for a staged source block, so that launch's velocities are incomplete),
+ * and clears the word. */
 int sts_status(sts_ctx* ctx, void* stream);
 
 /* Direct summation of the Sec. 2 system (the O(N^2) sum of Sec. 4.1).

@@ -370,6 +370,11 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
             set_error("bve_rk4_step: non-finite position");
             return STS_ERR_NONFINITE;
         }
+        if (st & kStatusTimeout) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("bve_rk4_step: a device-side wait for staged sources gave up");
+            return STS_ERR_TIMEOUT;
+        }
         c->have_tree = true;
         c->have_lists = true;
         c->nnodes = -1;  // host counts refreshed on demand
@@ -450,6 +455,11 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
             STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
             set_error("sts_tree_velocity: non-finite position");
             return STS_ERR_NONFINITE;
+        }
+        if (st & kStatusTimeout) {
+            STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+            set_error("sts_tree_velocity: a device-side wait for staged sources gave up");
+            return STS_ERR_TIMEOUT;
         }
         c->have_tree = c->have_lists = true;
         c->nnodes = -1;
@@ -575,6 +585,10 @@ int sts_status(sts_ctx* ctx, void* stream)
     if (st & kStatusNonfinite) {
         set_error("non-finite position");
         return STS_ERR_NONFINITE;
+    }
+    if (st & kStatusTimeout) {
+        set_error("a device-side wait for staged sources gave up; results of that launch are incomplete");
+        return STS_ERR_TIMEOUT;
     }
     return STS_OK;
 }

@@ -98,58 +98,46 @@ __device__ __forceinline__ void epilogue(double Sx, double Sy, double Sz, int G,
 constexpr int kEvalWarps = 8;
 constexpr int kEvalWarps64 = 4;
 
-struct BlockDesc {
-    int32_t idx;  // far: cluster slot; near: first sorted slot of the chunk
-    int32_t cnt;  // entries (0: no block)
-    float dx, dy, dz;
-    int32_t kind;  // 0 far, 1 near, 2 near that may hold pairs closer than tau
-};
-
-__device__ __forceinline__ BlockDesc load_desc(int b, int nf, int nbt, const FarEntry* __restrict__ fe,
-                                               const NearEntry* __restrict__ ne, int M, float tau_r)
+// Bulk copies (the TMA engine's 1-D form) into shared memory, completed on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
 {
-    BlockDesc d;
-    d.idx = 0;
-    d.cnt = 0;
-    d.dx = d.dy = d.dz = 0.f;
-    d.kind = 0;
-    if (b >= nbt) return d;
-    if (b < nf) {
-        const FarEntry e = fe[b];
-        d.idx = e.slot;
-        d.cnt = M;
-        d.dx = e.dx;
-        d.dy = e.dy;
-        d.dz = e.dz;
-    } else {
-        const NearEntry e = ne[b - nf];
-        d.idx = e.start;
-        d.cnt = e.count;
-        d.dx = e.dx;
-        d.dy = e.dy;
-        d.dz = e.dz;
-        d.kind = e.gap < tau_r ? 2 : 1;
-    }
-    return d;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
 {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Copies a block into shared memory (cp.async, 16 bytes per entry) and pads it with
-// zero-weight entries far from every target up to a multiple of `pad`.
-__device__ __forceinline__ void issue_block(const BlockDesc& d, float4* sb, int lane, const float4* __restrict__ prx32,
-                                            const float4* __restrict__ src32, int M, int pad)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity)
 {
-    const float4* src = d.kind == 0 ? prx32 + (int64_t)d.idx * M : src32 + d.idx;
-    for (int i = lane; i < d.cnt; i += 32) cp_async16(sb + i, src + i);
-    const int cntp = (d.cnt + pad - 1) / pad * pad;
-    if (d.cnt + lane < cntp) sb[d.cnt + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// dst, src and bytes are multiples of 16 bytes
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// A bounded wait for the phase `parity` of an mbarrier (all lanes of the warp): false after
+// kWaitSpins polls, which no copy of a few KB ever needs; the caller then reports
+// STS_ERR_TIMEOUT instead of hanging.
+constexpr int kWaitSpins = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+{
+    for (int k = 0; k < kWaitSpins; k++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
@@ -237,6 +225,7 @@ struct EvalSmem {
     float4 stage[2][kStagePad];
     float4 off[kRing];  // source offset (dx, dy, dz) of the block
     int4 info[kRing];   // first source (slot or cluster), count, kind, padded start in its window
+    uint64_t bar[2];    // mbarriers of the two stages
 };
 
 // A group of consecutive blocks staged together: [e0, e1) of the task's list, whose padded
@@ -309,25 +298,44 @@ __device__ __forceinline__ Group form_group(EvalSmem& sm, int e0, int& wb, int& 
     return g;
 }
 
-// Copies the blocks of a group into a stage (cp.async, 16 bytes per entry), each at its padded
-// start and padded with zero-weight entries far from every target to a multiple of 4 S.
+// Copies the blocks of a group into a stage: one bulk copy per block (each at its padded start,
+// issued by its own lane) against the stage's mbarrier, and pads each block with zero-weight
+// entries far from every target up to a multiple of 4 S.
 template <int S>
-__device__ __forceinline__ void issue_group(const EvalSmem& sm, const Group& g, float4* st, int lane, int nf,
+__device__ __forceinline__ void issue_group(EvalSmem& sm, const Group& g, int stg, int lane, int nf,
                                             const float4* __restrict__ prx32, const float4* __restrict__ src32,
                                             int M)
 {
-    for (int e = g.e0; e < g.e1; e++) {
+    if (g.e1 == g.e0) return;
+    float4* st = sm.stage[stg];
+    // lane k copies block e0 + k; lane 0 arms the barrier with the group's byte count (a copy
+    // that lands first leaves the count transiently negative, which the barrier allows)
+    const int e = g.e0 + lane;
+    int cnt = 0;
+    if (e < g.e1) {
         const int4 in = sm.info[e & (kRing - 1)];
-        float4* dst = st + (in.w - g.base);
+        cnt = in.y;
         const float4* src = e < nf ? prx32 + (int64_t)in.x * M : src32 + in.x;
-        for (int i = lane; i < in.y; i += 32) cp_async16(dst + i, src + i);
-        const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
-        if (in.y + lane < cntp) dst[in.y + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+        fence_proxy_async();  // the stage's earlier reads and writes come before the copies
+        if (cnt > 0) bulk_g2s(st + (in.w - g.base), src, 16u * (unsigned)cnt, &sm.bar[stg]);
     }
+    for (int f = g.e0; f < g.e1; f++) {
+        const int4 in = sm.info[f & (kRing - 1)];
+        const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
+        if (in.y + lane < cntp) st[in.w - g.base + in.y + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
+    }
+    int bytes = 16 * cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(kFull, bytes, o);
+    if (lane == 0) mbar_arrive_expect_tx(&sm.bar[stg], (unsigned)bytes);
 }
 
+// One warp task of the mixed tree code.  Returns false if a staging wait gave up (status
+// flagged STS_ERR_TIMEOUT after the copies in flight were given a bounded time to land).
+// par: the parity bits of the two stage barriers, carried from task to task.
 template <int S>
-__device__ __forceinline__ void eval_task_mixed(const Task& tk, EvalSmem& sm, int lane,
+__device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, int lane, unsigned& par,
+                                                int* __restrict__ status,
                                                 const int64_t* __restrict__ far_off,
                                                 const FarEntry* __restrict__ far_ent,
                                                 const int64_t* __restrict__ near_coff,
@@ -358,15 +366,20 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, EvalSmem& sm, in
     int wb = 0;
     int winc = load_window<S>(sm, 0, lane, nf, nbt, fe, ne, M, tau_r);
     Group cur = form_group<S>(sm, 0, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
-    issue_group<S>(sm, cur, sm.stage[0], lane, nf, prx32, src32, M);
-    cp_commit();
+    issue_group<S>(sm, cur, 0, lane, nf, prx32, src32, M);
     Group nxt = form_group<S>(sm, cur.e1, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
     for (int b = 0; cur.e1 > cur.e0; b++) {
-        issue_group<S>(sm, nxt, sm.stage[(b + 1) & 1], lane, nf, prx32, src32, M);
-        cp_commit();
-        cp_wait1();
-        __syncwarp();
-        const float4* st = sm.stage[b & 1];
+        const int stg = b & 1;
+        issue_group<S>(sm, nxt, stg ^ 1, lane, nf, prx32, src32, M);
+        if (!mbar_wait(&sm.bar[stg], (par >> stg) & 1u)) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            if (nxt.e1 > nxt.e0) mbar_wait(&sm.bar[stg ^ 1], (par >> (stg ^ 1)) & 1u);
+            mbar_wait(&sm.bar[stg], (par >> stg) & 1u);
+            return false;
+        }
+        par ^= 1u << stg;
+        __syncwarp();  // the padding written by the other lanes
+        const float4* st = sm.stage[stg];
         float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
         for (int e = cur.e0; e < cur.e1; e++) {
             const float4 o = sm.off[e & (kRing - 1)];
@@ -424,6 +437,7 @@ __device__ __forceinline__ void eval_task_mixed(const Task& tk, EvalSmem& sm, in
             vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
         }
     }
+    return true;
 }
 
 __global__ void __launch_bounds__(kEvalWarps * 32, STS_EVAL_MIN_BLOCKS)
@@ -433,51 +447,60 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
              const float4* __restrict__ src32, const double4* __restrict__ src64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
              double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
-             unsigned long long* __restrict__ queue)
+             unsigned long long* __restrict__ queue, int* __restrict__ status)
 {
     extern __shared__ __align__(16) EvalSmem sbuf[];  // kEvalWarps of them
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);  // a recorded step whose tasks overflowed is redone
+    if (lane == 0) {
+        mbar_init(&sbuf[w].bar[0], 1);
+        mbar_init(&sbuf[w].bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    unsigned par = 0;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(queue, 1ull);
         const int64_t ti = (int64_t)__shfl_sync(kFull, t, 0);
         if (ti >= nt) break;
         const Task tk = tasks[ti];
+        bool ok;
         switch (tk.S) {
             case 1:
-                eval_task_mixed<1>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<1>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 2:
-                eval_task_mixed<2>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<2>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 3:
-                eval_task_mixed<3>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<3>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 4:
-                eval_task_mixed<4>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<4>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 5:
-                eval_task_mixed<5>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<5>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 6:
-                eval_task_mixed<6>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<6>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             case 7:
-                eval_task_mixed<7>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<7>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
             default:
-                eval_task_mixed<8>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx32, M, src32, src64,
-                                   perm, tau2, tau_r, corr, vel);
+                ok = eval_task_mixed<8>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
                 break;
         }
+        if (!ok) break;
         __syncwarp();
     }
 }
@@ -750,7 +773,8 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         phase_begin(c, kPhEval, s);
         (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
                                                     c->near_ent.p, c->prx32.p, M, c->src32.p, c->src64.p, c->perm.p,
-                                                    tau2, tau_r, corr, vel, nt_d, ntasks, queue), note_launch());
+                                                    tau2, tau_r, corr, vel, nt_d, ntasks, queue, c->d_status),
+         note_launch());
         phase_end(c, kPhEval, s);
     }
     STS_LAUNCH_CHECK();

@@ -18,6 +18,7 @@ constexpr int kMaxLevel = 24;
 // Device status word bits (ORed by kernels, read and cleared by sts_status).
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusNonfinite = 2;
+constexpr int kStatusTimeout = 4;  // a bounded device-side wait gave up
 
 // Evaluation tasks: one warp evaluates up to kTaskTargets consecutive targets of a leaf, two
 // per lane.
