@@ -546,6 +546,7 @@ int sts_create(sts_ctx** out)
         return STS_ERR_ARG;
     }
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int64_t));

@@ -164,7 +164,7 @@ struct sts_ctx {
     sts::DevBuf<double> nd_norm;         // [nodes,9]: child-digit normals of split nodes
     sts::DevBuf<float4> nd_norm32;       // [nodes,3]: the normals in FP32 + pre-filter margin
     sts::DevBuf<double> nd_mid;          // [nodes,9]: edge midpoints m12, m23, m31 of split nodes
-    int num_sms = 0;                                  // SMs of the context's device
+    int num_sms = 1;                                  // SMs of the context's device (sts_create)
     int eval_blocks_mixed = 0, eval_blocks_fp64 = 0;  // resident blocks of the persistent eval kernels
     sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)

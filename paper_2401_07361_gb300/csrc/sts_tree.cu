@@ -281,57 +281,80 @@ __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const 
         for (int k = threadIdx.x; k < 4 * (le - lb); k += blockDim.x) shc[k] = 0;
         __syncthreads();
     }
+    // kPU particles per thread and trip, their loads issued together round by round
+    constexpr int kPU = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t nr = (n + 31) & ~(int64_t)31;  // whole warps run every trip (warp-wide counting)
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x) {
-        int p = -1, d = 0;
-        bool active = false;
-        if (i < n) {
-            p = nodeof[i];
-            const int dg = digit[i];
-            const g3 x = gld(pos + 3 * i);
-            if (p >= pb && p < lb) {
-                p = child[4 * p + dg];
-                nodeof[i] = p;
-            }
-            if (p >= lb) {
-                const float4 q3[3] = {norm32[3 * (int64_t)p], norm32[3 * (int64_t)p + 1],
-                                      norm32[3 * (int64_t)p + 2]};
-                active = q3[0].w >= 0.f;
-                if (active) {
-                    const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
-                    const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
-                    // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
-                    d = -1;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nr; i0 += kPU * stride) {
+        int p[kPU], dg[kPU];
+        float fx[kPU], fy[kPU], fz[kPU];
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        if (d != -1) continue;
-                        const float t = fdot(q3[a].x, q3[a].y, q3[a].z, fx, fy, fz);
-                        const float thr = q3[a].w * scale;
-                        if (t > thr)
-                            d = a;
-                        else if (!(t < -thr))
-                            d = -2;  // too close to this boundary for FP32
-                    }
-                    if (d == -1) d = 3;
-                    if (d == -2) {
-                        const double* nn = norm + 9 * (int64_t)p;
-                        if (gdot(gld(nn), x) >= 0.0)
-                            d = 0;
-                        else if (gdot(gld(nn + 3), x) >= 0.0)
-                            d = 1;
-                        else if (gdot(gld(nn + 6), x) >= 0.0)
-                            d = 2;
-                        else
-                            d = 3;
-                    }
-                    digit[i] = (uint8_t)d;
-                }
+        for (int u = 0; u < kPU; u++) {
+            const int64_t i = i0 + u * stride;
+            p[u] = -1;
+            dg[u] = 0;
+            fx[u] = fy[u] = fz[u] = 0.f;
+            if (i < n) {
+                p[u] = nodeof[i];
+                dg[u] = digit[i];
+                fx[u] = (float)pos[3 * i];
+                fy[u] = (float)pos[3 * i + 1];
+                fz[u] = (float)pos[3 * i + 2];
             }
         }
-        if (priv)
-            agg_inc(shc, 4 * (p - lb) + d, active);
-        else
-            agg_inc(cc, 4 * p + d, active);
+#pragma unroll
+        for (int u = 0; u < kPU; u++) {
+            if (p[u] >= pb && p[u] < lb) {
+                p[u] = child[4 * p[u] + dg[u]];
+                nodeof[i0 + u * stride] = p[u];
+            }
+        }
+        float4 q3[kPU][3];
+#pragma unroll
+        for (int u = 0; u < kPU; u++) {
+            const int64_t pp = p[u] >= lb ? p[u] : 0;
+#pragma unroll
+            for (int a = 0; a < 3; a++) q3[u][a] = norm32[3 * pp + a];
+        }
+#pragma unroll
+        for (int u = 0; u < kPU; u++) {
+            const int64_t i = i0 + u * stride;
+            const bool active = p[u] >= lb && q3[u][0].w >= 0.f;
+            int d = 0;
+            if (active) {
+                const float scale = fmaxf(1.f, fmaxf(fabsf(fx[u]), fmaxf(fabsf(fy[u]), fabsf(fz[u]))));
+                // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
+                d = -1;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (d != -1) continue;
+                    const float t = fdot(q3[u][a].x, q3[u][a].y, q3[u][a].z, fx[u], fy[u], fz[u]);
+                    const float thr = q3[u][a].w * scale;
+                    if (t > thr)
+                        d = a;
+                    else if (!(t < -thr))
+                        d = -2;  // too close to this boundary for FP32
+                }
+                if (d == -1) d = 3;
+                if (d == -2) {
+                    const g3 x = gld(pos + 3 * i);
+                    const double* nn = norm + 9 * (int64_t)p[u];
+                    if (gdot(gld(nn), x) >= 0.0)
+                        d = 0;
+                    else if (gdot(gld(nn + 3), x) >= 0.0)
+                        d = 1;
+                    else if (gdot(gld(nn + 6), x) >= 0.0)
+                        d = 2;
+                    else
+                        d = 3;
+                }
+                digit[i] = (uint8_t)d;
+            }
+            if (priv)
+                agg_inc(shc, 4 * (p[u] - lb) + d, active);
+            else
+                agg_inc(cc, 4 * p[u] + d, active);
+        }
     }
     if (priv) {
         __syncthreads();
@@ -493,6 +516,20 @@ __device__ __forceinline__ bool mac_filtered(float4 ct, float4 cs, float theta32
     return mac(gt, gs, theta);
 }
 
+// A lower bound on the distance between any point of leaf t and any point of leaf s (their
+// circumcircles' gap), in FP32: the centre difference and its squared length are FP64, the
+// square root and the radii FP32, and a margin of 1e-6 of the sum covers every FP32 rounding
+// (about 6 units of 2^-24 of it).  The evaluator only compares it with the close-pair radius to
+// decide whether a near block needs the close-pair test, so a bound that is a little low costs
+// a test and never changes a result.
+__device__ __forceinline__ float near_gap(const double* gt, const double* gs)
+{
+    const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
+    const float dist = sqrtf((float)gdot(e3, e3));
+    const float rt = (float)gt[12], rs = (float)gs[12];
+    return dist - rt - rs - 1e-6f * (dist + rt + rs);
+}
+
 // Target-leaf traversal of Sec. 3.4 (PC + PP), one thread per target leaf: from the roots of
 // the leaf's instance in face order, a source node that passes the MAC is far (a cluster,
 // more than N_T particles) or near; one that fails is near if it is a leaf, else its
@@ -569,13 +606,12 @@ __global__ void k_lists(int fill, const int64_t* __restrict__ nleaves_p, const i
             const int32_t st = start[s], ct2 = count[s];
             if (fill) {
                 near_idx[no + nn] = s;
-                const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
-                const double gap = __dsqrt_rn(gdot(e3, e3)) - gt[12] - gs[12];
+                const float gap = near_gap(gt, gs);
                 NearEntry e;
                 e.dx = (float)__dsub_rn(gs[9], gt[9]);
                 e.dy = (float)__dsub_rn(gs[10], gt[10]);
                 e.dz = (float)__dsub_rn(gs[11], gt[11]);
-                e.gap = __double2float_rd(gap);
+                e.gap = gap;
                 e.pad[0] = e.pad[1] = 0;
                 for (int32_t c0 = 0; c0 < ct2; c0 += kStage) {
                     e.start = st + c0;
@@ -828,13 +864,12 @@ k_lists_fill(const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ 
                 far_ent[q] = e;
             } else {
                 near_idx[no + nn + __popc(nm & ((1u << lane) - 1u))] = s;
-                const g3 e3 = gsub(gld(gt + 9), gld(gs + 9));
-                const double gap = __dsqrt_rn(gdot(e3, e3)) - gt[12] - gs[12];
+                const float gap = near_gap(gt, gs);
                 NearEntry e;
                 e.dx = dx;
                 e.dy = dy;
                 e.dz = dz;
-                e.gap = __double2float_rd(gap);
+                e.gap = gap;
                 e.pad[0] = e.pad[1] = 0;
                 const int32_t st = start[s], ct2 = count[s];
                 int64_t q = co + nch + choff;
@@ -1110,13 +1145,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     const unsigned gnode = cap ? (unsigned)std::min<int64_t>(4096, (node_cap + T - 1) / T) : 0;
     int level = 0, last = 0;
     c->level_begin.assign(1, 0);
-    if (c->num_sms <= 0) {
-        int dev = 0;
-        STS_CUDA(cudaGetDevice(&dev));
-        STS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
     // particle passes: a few resident blocks per SM, each striding over many particles
-    const unsigned gpart = (unsigned)std::min<int64_t>(blocks(n, T), 6 * (int64_t)c->num_sms);
+    const unsigned gpart = (unsigned)std::min<int64_t>(blocks(n, 4 * T), 4 * (int64_t)c->num_sms);
     for (level = 0; level < nlev; level++) {
         int64_t capn;
         unsigned g;

@@ -228,7 +228,8 @@ k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
 // V_ref^-T stays FP64 in both precisions: its entries alternate in sign and reach ~1e5 at
 // d = 8, so FP32 rounding of the products would put errors ~1e-5 into the far field.  Four
 // interleaved partial sums shorten the dependent FP64 chain.  MIXED: the proxy points are
-// normalised with one reciprocal (FP32 copies only need the FP64 point to an ulp or so).
+// normalised with a reciprocal square root (FP32 copies only need the FP64 point to an ulp or
+// so).  A fixed grid strides over the clusters (their count is on the device).
 template <bool MIXED>
 __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __restrict__ toff,
                            const double* __restrict__ part, const double* __restrict__ geom,
@@ -237,47 +238,50 @@ __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __r
                            const int64_t* __restrict__ nclu)
 {
     __shared__ double om[kMaxM + 3];
-    const int c = blockIdx.x;
-    if (c >= *nclu) return;
-    const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
-    for (int k = threadIdx.x; k < M + 3; k += blockDim.x) {
-        double s = 0.0;
-        if (k < M)
-            for (int64_t q = q0; q < q1; q++) s += part[q * M + k];
-        om[k] = s;  // om[M .. M + 2] = 0 pads the four-way split below
-    }
-    __syncthreads();
-    const double* g = geom + 13 * (int64_t)cnode[c];
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        double a4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = 0; k < M; k += 4) {
+    const int64_t ncl = *nclu;
+    for (int64_t c = blockIdx.x; c < ncl; c += gridDim.x) {
+        const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
+        __syncthreads();  // om of the previous cluster is no longer read
+        for (int k = threadIdx.x; k < M + 3; k += blockDim.x) {
+            double s = 0.0;
+            if (k < M)
+                for (int64_t q = q0; q < q1; q++) s += part[q * M + k];
+            om[k] = s;  // om[M .. M + 2] = 0 pads the four-way split below
+        }
+        __syncthreads();
+        const double* g = geom + 13 * (int64_t)cnode[c];
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            double a4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < M; k += 4) {
 #pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (k + u < M) a4[u] += vinv[(k + u) * M + m] * om[k + u];
+                for (int u = 0; u < 4; u++)
+                    if (k + u < M) a4[u] += vinv[(k + u) * M + m] * om[k + u];
+            }
+            const double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
+            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+            const double ss = (sx * sx + sy * sy) + sz * sz;
+            double yx, yy, yz, rho;
+            if (MIXED) {
+                const double ri = rsqrt(ss);
+                yx = sx * ri;
+                yy = sy * ri;
+                yz = sz * ri;
+                rho = ss * ri;
+            } else {
+                rho = sqrt(ss);
+                yx = sx / rho;
+                yy = sy / rho;
+                yz = sz / rho;
+            }
+            double rd = 1.0;
+            for (int e = 0; e < d; e++) rd *= rho;
+            const double W2 = 2.0 * (rd * acc);
+            prx64[c * M + m] = make_double4(yx, yy, yz, W2);
+            prx32[c * M + m] = make_float4((float)(yx - g[9]), (float)(yy - g[10]), (float)(yz - g[11]), (float)W2);
         }
-        const double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-        const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
-        const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
-        const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
-        const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
-        const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
-        double rd = 1.0;
-        for (int e = 0; e < d; e++) rd *= rho;
-        const double W2 = 2.0 * (rd * acc);
-        double yx, yy, yz;
-        if (MIXED) {
-            const double ri = 1.0 / rho;
-            yx = sx * ri;
-            yy = sy * ri;
-            yz = sz * ri;
-        } else {
-            yx = sx / rho;
-            yy = sy / rho;
-            yz = sz / rho;
-        }
-        prx64[(int64_t)c * M + m] = make_double4(yx, yy, yz, W2);
-        prx32[(int64_t)c * M + m] =
-            make_float4((float)(yx - g[9]), (float)(yy - g[10]), (float)(yz - g[11]), (float)W2);
     }
 }
 
@@ -376,7 +380,8 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
             c->up_frame32.p, c->src64.p, c->src_hl.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     }
-    (precision == STS_FP64 ? k_contract<false> : k_contract<true>)<<<(unsigned)nclu, 64, 0, s>>>(
+    (precision == STS_FP64 ? k_contract<false> : k_contract<true>)<<<(unsigned)std::min<int64_t>(nclu, 16 * (int64_t)c->num_sms),
+                                                                   64, 0, s>>>(
         c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M,
         c->prx64.p, c->prx32.p, dc + kDcClusters);
     note_launch();
