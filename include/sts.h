@@ -82,6 +82,13 @@ const char* sts_last_error(void);
  * gave up waiting for a staged source block, so that launch's velocities are incomplete),
  * and clears the word. */
 int sts_status(sts_ctx* ctx, void* stream);
+/* Self-test of the bounded device-side wait that the mixed evaluation uses while its sources
+ * are staged: one warp waits on a shared-memory mbarrier that nothing arrives on, polling it
+ * `spins` times (1 <= spins <= 2^20; the evaluation polls 2^20 times), then flags a timeout.
+ * Returns STS_ERR_TIMEOUT (the expected result, from sts_status on `stream`) and leaves the
+ * context usable; STS_ERR_ARG for spins out of range.  The paper has no counterpart: this
+ * exists so that the timeout path can be exercised without faulting or hanging the GPU. */
+int sts_selftest_wait(sts_ctx* ctx, int32_t spins, void* stream);
 
 /* Direct summation of the Sec. 2 system (the O(N^2) sum of Sec. 4.1).
  * pos[n,3], zeta[n], area[n] in; vel[n,3] out (u_i at every particle; j = i and any other

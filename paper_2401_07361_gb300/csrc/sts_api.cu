@@ -594,6 +594,18 @@ int sts_status(sts_ctx* ctx, void* stream)
     return STS_OK;
 }
 
+int sts_selftest_wait(sts_ctx* ctx, int32_t spins, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_selftest_wait");
+    if (rc) return rc;
+    if (spins < 1 || spins > (1 << 20)) {
+        set_error("sts_selftest_wait: spins must be in [1, 2^20]");
+        return STS_ERR_ARG;
+    }
+    if ((rc = wait_selftest(ctx, spins, S(stream)))) return rc;
+    return sts_status(ctx, stream);
+}
+
 int sts_direct(sts_ctx* ctx, const double* pos, const double* zeta, const double* area, int64_t n,
                int32_t precision, double* vel, void* stream)
 {

@@ -133,11 +133,25 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 // kWaitSpins polls, which no copy of a few KB ever needs; the caller then reports
 // STS_ERR_TIMEOUT instead of hanging.
 constexpr int kWaitSpins = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int spins = kWaitSpins)
 {
-    for (int k = 0; k < kWaitSpins; k++)
+    for (int k = 0; k < spins; k++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+
+// The bounded wait on a barrier that nothing arrives on: it must give up after `spins` polls
+// and flag the timeout in the status word, leaving the context usable.
+__global__ void k_wait_selftest(int spins, int* __restrict__ status)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const bool done = mbar_wait(&bar, 0, spins);
+    if (!done && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
 }
 
 // FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
@@ -777,6 +791,13 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
          note_launch());
         phase_end(c, kPhEval, s);
     }
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int wait_selftest(sts_ctx* c, int spins, cudaStream_t s)
+{
+    (k_wait_selftest<<<1, 32, 0, s>>>(spins, c->d_status), note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }

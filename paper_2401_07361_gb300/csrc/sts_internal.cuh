@@ -287,6 +287,7 @@ int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
 
 // ---- evaluation (sts_eval.cu) ---------------------------------------------------------
 int evaluate(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
+int wait_selftest(sts_ctx* c, int spins, cudaStream_t s);
 int count_interactions(sts_ctx* ctx, int degree, cudaStream_t s);
 int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
                int64_t n, const int64_t* targets, int64_t nt, int precision, double* vel,

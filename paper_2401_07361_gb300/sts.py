@@ -18,6 +18,8 @@ from . import build as _build
 
 STS_FP64 = 0
 STS_MIXED = 1
+STS_OK, STS_ERR_ARG, STS_ERR_CUDA, STS_ERR_CAPACITY, STS_ERR_TIMEOUT, STS_ERR_NONFINITE, STS_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
 PHASES = ("build", "sort", "lists", "prep", "upward", "eval", "direct")
 
 _lock = threading.Lock()
@@ -58,6 +60,7 @@ def load(build_if_needed: bool = True):
             "sts_destroy": (None, [P]),
             "sts_last_error": (C.c_char_p, []),
             "sts_status": (i32, [P, P]),
+            "sts_selftest_wait": (i32, [P, i32, P]),
             "sts_direct": (i32, [P, P, P, P, i64, i32, P, P]),
             "sts_direct_targets": (i32, [P, P, P, P, i64, P, i64, i32, P, P]),
             "sts_direct_noalloc": (i32, [P, P, P, i64, i32, P, P]),
@@ -131,6 +134,12 @@ def sts_destroy(ctx):
 
 def sts_status(ctx, stream=None):
     _check(load().sts_status(ctx, _stream(stream)), "sts_status")
+
+
+def sts_selftest_wait(ctx, spins, stream=None):
+    """Runs the bounded-wait self-test; returns the library's return code (STS_ERR_TIMEOUT
+    expected) instead of raising."""
+    return int(load().sts_selftest_wait(ctx, int(spins), _stream(stream)))
 
 
 # ------------------------------------------------------------------------------- compute
