@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.7)
     ap.add_argument("--degree", type=int, default=8)
     ap.add_argument("--leaf", type=int, default=None)
-    ap.add_argument("--tau-c", type=float, default=0.05,
+    ap.add_argument("--tau-c", type=float, default=0.01,
                     help="near FP64 threshold tau = c * 4 pi / N (half squared chord)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rk4", type=int, default=0,

@@ -39,7 +39,7 @@ def _rel_l2(v, ref, w):
 
 
 def autotune(pos, zeta, area, budget=1e-4, thetas=(0.5, 0.6, 0.7, 0.8), degrees=(4, 6, 8, 10),
-             leaf_sizes=(64, 128, 256), precision=sts.STS_MIXED, tau_c=0.05, offsets=None,
+             leaf_sizes=(64, 128, 256), precision=sts.STS_MIXED, tau_c=0.01, offsets=None,
              samples=2048, repeats=3, seed=0, ctx=None, stream=None) -> TuneResult:
     """Fastest (theta, degree, leaf_size) with rel l2 error <= budget vs the FP64 direct sum.
 

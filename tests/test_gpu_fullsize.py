@@ -1,6 +1,6 @@
 """Parity at the benchmark's full size and launch configuration: N = 655362 uniform points,
 Voronoi areas, degree-16 harmonic vorticity, theta = 0.7, degree 8, N_T = 128, mixed
-precision with tau = 0.05 * 4 pi / N (the configuration ``bench.py`` times).
+precision with tau = 0.01 * 4 pi / N (the configuration ``bench.py`` times).
 
 The oracle finishes the FP64 tree code at this size in seconds, so the mixed GPU result is
 compared with it at every target; the tree and lists are compared bit for bit; the direct
@@ -32,7 +32,7 @@ def test_fullsize_tree_lists_and_mixed_velocity(setup):
     wl, h = setup
     pos, zeta, area = wl["pos"], wl["zeta"], wl["area"]
     n = len(pos)
-    tau = 0.05 * 4 * math.pi / n
+    tau = 0.01 * 4 * math.pi / n
     p = sts.params(theta=0.7, degree=8, leaf_size=128, max_level=16, precision=sts.STS_MIXED, near_fp64_tau=tau)
     d = lambda a: torch.from_numpy(a).to("cuda")
     sts.sts_tree_build(h, d(pos), p)
