@@ -36,7 +36,7 @@ FP32_LANES = 128
 L2_BYTES = 129 * 2**20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -56,7 +56,7 @@ def parse():
                     help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
                     help="timed device steps only (no e2e, FP64 or CPU legs): the command profiled by ncu")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -64,6 +64,19 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, ws, device):
+    """The largest value of x over the ranks of the job (x itself on one rank): every timed
+    quantity is taken from the slowest rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def load_workload(name):
@@ -362,11 +375,7 @@ def main():
     launches = sts.sts_launch_count() - l0
     phases = sts.sts_phase_times(h)
     sts.sts_set_timing(h, False)
-    total_ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), ws, dev)
     ms_step = total_ms / max(1, args.steps)
     value = ws * n * args.steps / (total_ms / 1e3)
     v_mixed = vel.cpu().numpy().copy()
@@ -391,6 +400,7 @@ def main():
     vel2 = torch.empty_like(vel)
     e2e_times = []
     e2e_steps = max(3, min(args.steps, 10))
+    barrier()
     for it in range(e2e_steps + 1):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -406,7 +416,7 @@ def main():
         if it > 0:
             e2e_times.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
-    e2e_ms = sum(e2e_times) / len(e2e_times)
+    e2e_ms = max_over_ranks(sum(e2e_times) / len(e2e_times), ws, dev)
     assert np.array_equal(vel_p.numpy(), v_mixed), "end-to-end result differs from the device-resident one"
 
     # ---- FP64 GPU tree code (same tree), error of the mixed result ------------------
