@@ -52,17 +52,6 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float p)
     lo += e;
 }
 
-__device__ __forceinline__ void pair32(const float4 s, float tx, float ty, float tz, float& ax,
-                                       float& ay, float& az)
-{
-    const float dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
-    const float c = s.w * rcp_approx(r2);
-    ax = fmaf(c, dx, ax);
-    ay = fmaf(c, dy, ay);
-    az = fmaf(c, dz, az);
-}
-
 __device__ __forceinline__ void pair64(const double4 s, double tx, double ty, double tz, double& ax,
                                        double& ay, double& az)
 {
@@ -72,21 +61,6 @@ __device__ __forceinline__ void pair64(const double4 s, double tx, double ty, do
     ax = fma(c, dx, ax);
     ay = fma(c, dy, ay);
     az = fma(c, dz, az);
-}
-
-__device__ __forceinline__ void epilogue(double Sx, double Sy, double Sz, int G, bool write,
-                                         double xx, double xy, double xz, int64_t i, double* vel)
-{
-    for (int o = G; o < 32; o <<= 1) {
-        Sx += __shfl_xor_sync(kFull, Sx, o);
-        Sy += __shfl_xor_sync(kFull, Sy, o);
-        Sz += __shfl_xor_sync(kFull, Sz, o);
-    }
-    if (write) {
-        vel[3 * i] = -kInv4Pi * (xy * Sz - xz * Sy);
-        vel[3 * i + 1] = -kInv4Pi * (xz * Sx - xx * Sz);
-        vel[3 * i + 2] = -kInv4Pi * (xx * Sy - xy * Sx);
-    }
 }
 
 // ------------------------------------------------------------------------ tree tasks

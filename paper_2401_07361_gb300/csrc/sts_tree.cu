@@ -1011,14 +1011,6 @@ int read_i64(sts_ctx* ctx, const int64_t* dptr, int64_t* out, cudaStream_t s)
     return STS_OK;
 }
 
-int read_status(sts_ctx* ctx, cudaStream_t s, int* st)
-{
-    STS_CUDA(cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    *st = (int)((int32_t*)ctx->h_pinned)[0];
-    return STS_OK;
-}
-
 int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
 {
     STS_CUDA(c->nd_level.grow(need, keep, s));

@@ -164,7 +164,6 @@ k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
 
     const int2 tk = tasks[blockIdx.x];
     const int32_t node = cnode[tk.x];
-    const double* g = geom + 13 * (int64_t)node;
     const double* f = frame + 12 * (int64_t)tk.x;
     const int t = threadIdx.x;
     const int64_t j = (int64_t)start[node] + tk.y + t;
