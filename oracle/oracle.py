@@ -61,6 +61,9 @@ def _L():
             lib.or_vref_inverse.argtypes = [i32, P]
             lib.or_cluster.argtypes = [P, i32, i64, P, P, P, P, P]
             lib.or_pc_pair.argtypes = [P, i32, i64, P, P, P, P, P]
+            lib.or_direct_potential.argtypes = [i64, P, P, P, i64, P, P, i32]
+            lib.or_tree_potential.argtypes = [P, P, P, dbl, i32, i32, P, P, i32]
+            lib.or_pc_pair_potential.argtypes = [P, i32, i64, P, P, P, P, P]
             lib.or_icosahedron.argtypes = [P, P]
             _lib = lib
     return _lib
@@ -100,6 +103,21 @@ def direct(pos, zeta, area, targets=None, nthreads: int = 0):
     vel = np.zeros((nt, 3))
     _check(_L().or_direct(n, _p(pos), _p(zeta), _p(area), nt, _p(tg), _p(vel), nthreads), "direct")
     return vel
+
+
+def direct_potential(pos, zeta, area, targets=None, nthreads: int = 0):
+    """Direct sum of the stream function psi_i = -(1/4pi) sum_{j != i} log(|x_i - x_j|^2 / 2)
+    zeta_j A_j (the Green's function of Sec. 2 as the kernel).  ``targets`` as for direct."""
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    zeta = _f64(zeta, (n,))
+    area = _f64(area, (n,))
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else tg.shape[0]
+    psi = np.zeros(nt)
+    _check(_L().or_direct_potential(n, _p(pos), _p(zeta), _p(area), nt, _p(tg), _p(psi), nthreads),
+           "direct potential")
+    return psi
 
 
 class Tree:
@@ -163,6 +181,20 @@ class Tree:
             return vel, dict(pc=int(st[0]), pp=int(st[1]))
         return vel
 
+    def potential(self, zeta, area, theta: float = 0.7, degree: int = 8, literal: bool = False,
+                  nthreads: int = 0, return_stats: bool = False):
+        """Tree-code stream function (same lists and proxies as ``velocity``)."""
+        n = self.pos.shape[0]
+        zeta = _f64(zeta, (n,))
+        area = _f64(area, (n,))
+        psi = np.zeros(n)
+        st = np.zeros(2, np.int64)
+        _check(_L().or_tree_potential(self._h, _p(zeta), _p(area), float(theta), int(degree),
+                                      int(bool(literal)), _p(psi), _p(st), nthreads), "tree potential")
+        if return_stats:
+            return psi, dict(pc=int(st[0]), pp=int(st[1]))
+        return psi
+
     def clusters(self, zeta, area, degree: int):
         n = self.pos.shape[0]
         zeta = _f64(zeta, (n,))
@@ -222,6 +254,19 @@ def pc_pair(verts, d, ys, ws, x):
     _check(_L().or_pc_pair(_p(verts), d, ys.shape[0], _p(ys), _p(ws), _p(x), _p(lit), _p(prx)),
            "pc pair")
     return lit, prx
+
+
+def pc_pair_potential(verts, d, ys, ws, x):
+    """The potential's PC interaction of target x with one triangle: (literal alpha-solve,
+    proxy form), both without the -1/4pi."""
+    verts = _f64(verts, (3, 3))
+    ys = _f64(ys, (-1, 3))
+    ws = _f64(ws, (ys.shape[0],))
+    x = _f64(x, (3,))
+    lit, prx = np.zeros(1), np.zeros(1)
+    _check(_L().or_pc_pair_potential(_p(verts), d, ys.shape[0], _p(ys), _p(ws), _p(x), _p(lit), _p(prx)),
+           "pc pair potential")
+    return float(lit[0]), float(prx[0])
 
 
 def icosahedron():

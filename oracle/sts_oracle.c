@@ -29,6 +29,10 @@
  *                         interaction (Sec. 3.3.2): W = V_s^{-T} omega.
  *   pc_literal            the PC interaction exactly as printed: solve V alpha = G(x, y~),
  *                         then sum_k alpha_k omega_k (Sec. 3.3.2).
+ *   pot_term / or_direct_potential / or_tree_potential
+ *                         the stream function: the same sums with the Green's function
+ *                         G = -(1/4pi) log(1 - x.y) of Sec. 2 as the kernel (the convolution
+ *                         of Sec. 3 with that G); pc_literal_pot is its printed PC form.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +82,20 @@ static void bs_term(v3 x, v3 y, double w, v3* acc)
     acc->z += c.z * t;
 }
 
+/* The potential kernel: G(x, y) = -(1/4pi) log(1 - x.y) (Sec. 2), the Green's function of
+ * the spherical Laplacian, so that psi_i = sum_{j != i} G(x_i, x_j) zeta_j A_j is the stream
+ * function of the particle system (Delta psi = zeta).  With Eq. altkernel 1 - x.y =
+ * |x - y|^2 / 2.  pot_term adds w log(|d|^2 / 2) to *acc; a distinct particle at the same
+ * position adds nothing, as in bs_term (the kernel is singular there; the paper defines no
+ * value).                                                                                  */
+static void pot_term(v3 x, v3 y, double w, double* acc)
+{
+    v3 d = vsub(y, x);
+    double h = 0.5 * vdot(d, d);
+    if (h == 0.0) return;
+    *acc += w * log(h);
+}
+
 static int set_threads(int nthreads)
 {
 #ifdef _OPENMP
@@ -117,6 +135,36 @@ int or_direct(int64_t n, const double* pos, const double* zeta, const double* ar
         vel[3 * k] = f * acc.x;
         vel[3 * k + 1] = f * acc.y;
         vel[3 * k + 2] = f * acc.z;
+    }
+    free(w);
+    return OR_OK;
+}
+
+/* Direct summation of the stream function psi_i = -(1/4pi) sum_{j != i} log(1 - x_i.x_j)
+ * zeta_j A_j (Sec. 2 Green's function, Sec. 3 convolution sum).  Arguments as or_direct;
+ * psi[nt] receives psi at each target.                                                    */
+int or_direct_potential(int64_t n, const double* pos, const double* zeta, const double* area,
+                        int64_t nt, const int64_t* targets, double* psi, int nthreads)
+{
+    if (n < 0 || nt < 0 || (n > 0 && (!pos || !zeta || !area)) || (nt > 0 && !psi))
+        return OR_ERR_ARG;
+    if (!targets) nt = n;
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!w) return OR_ERR_MEM;
+    for (int64_t j = 0; j < n; j++) w[j] = zeta[j] * area[j];
+    const double f = -1.0 / (4.0 * OR_PI);
+    int nth = set_threads(nthreads);
+    (void)nth;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nth)
+    for (int64_t k = 0; k < nt; k++) {
+        int64_t i = targets ? targets[k] : k;
+        v3 x = ld3(pos, i);
+        double acc = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            pot_term(x, ld3(pos, j), w[j], &acc);
+        }
+        psi[k] = f * acc;
     }
     free(w);
     return OR_OK;
@@ -910,16 +958,76 @@ int or_pc_pair(const double* verts, int d, int64_t ns, const double* ys, const d
     return rc;
 }
 
+/* The PC interaction of the potential as printed (Sec. 3.3.2): solve V_s alpha =
+ * (log h(x, y~_1), ..., log h(x, y~_M)), h = |x - y|^2 / 2, and return sum_k alpha_k omega_k
+ * (the kernel without the -1/4pi).                                                        */
+static int pc_literal_pot(const refdata* r, const v3* v, const v3* yt, const double* omega, v3 x, double* out)
+{
+    const int M = r->M, d = r->d;
+    double* Vs = (double*)malloc(sizeof(double) * (size_t)M * M);
+    double* g = (double*)malloc(sizeof(double) * (size_t)M);
+    if (!Vs || !g) {
+        free(Vs);
+        free(g);
+        return OR_ERR_MEM;
+    }
+    for (int m = 0; m < M; m++) {
+        double b[3];
+        sph_bary(yt[m], v[0], v[1], v[2], b);
+        sbb(d, b[0], b[1], b[2], Vs + (size_t)m * M);
+        g[m] = 0.0;
+        pot_term(x, yt[m], 1.0, &g[m]);
+    }
+    int rc = solve(M, Vs, g, 1);
+    if (rc == OR_OK) {
+        double acc = 0.0;
+        for (int k = 0; k < M; k++) acc += g[k] * omega[k];
+        *out = acc;
+    }
+    free(Vs);
+    free(g);
+    return rc;
+}
+
+/* The potential's PC interaction of one target with one source triangle, both ways (the
+ * literal alpha-solve *lit, the proxy-point form *prx), without the -1/4pi.              */
+int or_pc_pair_potential(const double* verts, int d, int64_t ns, const double* ys, const double* ws,
+                         const double* x, double* lit, double* prx)
+{
+    if (!verts || d < 1 || d > 16 || ns < 0 || !x || !lit || !prx) return OR_ERR_ARG;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    v3 v[3] = {ld3(verts, 0), ld3(verts, 1), ld3(verts, 2)};
+    v3* y = (v3*)malloc(sizeof(v3) * (size_t)(ns > 0 ? ns : 1));
+    for (int64_t j = 0; j < ns; j++) y[j] = ld3(ys, j);
+    v3 yt[153];
+    double W[153], om[153];
+    cluster_weights(&r, v, ns, y, ws, yt, W, om);
+    v3 xx = ld3(x, 0);
+    double a = 0.0, b = 0.0;
+    for (int m = 0; m < r.M; m++) pot_term(xx, yt[m], W[m], &a);
+    rc = pc_literal_pot(&r, v, yt, om, xx, &b);
+    *prx = a;
+    *lit = b;
+    free(y);
+    ref_free(&r);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------------------- */
 /* Tree-code velocity (Sec. 3): PC interactions with the far triangles of each target
  * leaf's list, PP interactions with its near triangles, j = i excluded.  literal != 0 uses
  * the alpha-solve for every PC interaction (tiny n only).  vel[n,3] in original order.
  * stats[0] = PC interactions (targets x proxy points), stats[1] = PP interactions
  * (target, source) pairs with j != i.                                                    */
-int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double theta, int d,
-                     int literal, double* vel, int64_t* stats, int nthreads)
+static int tree_sum(or_tree* tr, const double* zeta, const double* area, double theta, int d, int literal,
+                    int pot, double* out, int64_t* stats, int nthreads)
 {
-    if (!tr || d < 1 || d > 16 || !(theta > 0.0) || !(theta < 1.0) || !vel) return OR_ERR_ARG;
+    if (!tr || d < 1 || d > 16 || !(theta > 0.0) || !(theta < 1.0) || !out) return OR_ERR_ARG;
     if (tr->n > 0 && (!zeta || !area)) return OR_ERR_ARG;
     if (!tr->has_lists || tr->theta != theta) {
         int rc = or_tree_lists(tr, theta);
@@ -972,17 +1080,26 @@ int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double
         const onode* t = &tr->nodes[tr->leaves[L]];
         for (int64_t k = t->start; k < t->start + t->count; k++) {
             v3 x = ys[k];
-            v3 acc = mk(0.0, 0.0, 0.0);
+            v3 acc = mk(0.0, 0.0, 0.0);  /* velocity */
+            double ph = 0.0;             /* potential */
             for (int64_t q = tr->far_off[L]; q < tr->far_off[L + 1]; q++) {
                 int32_t s = tr->far_idx[q];
                 const v3* y = yt + (size_t)slot[s] * M;
                 const double* Wm = W + (size_t)slot[s] * M;
                 if (literal) {
-                    v3 b;
-                    if (pc_literal(&r, tr->nodes[s].v, y, om + (size_t)slot[s] * M, x, &b)) err = 1;
-                    acc.x += b.x;
-                    acc.y += b.y;
-                    acc.z += b.z;
+                    if (pot) {
+                        double b;
+                        if (pc_literal_pot(&r, tr->nodes[s].v, y, om + (size_t)slot[s] * M, x, &b)) err = 1;
+                        ph += b;
+                    } else {
+                        v3 b;
+                        if (pc_literal(&r, tr->nodes[s].v, y, om + (size_t)slot[s] * M, x, &b)) err = 1;
+                        acc.x += b.x;
+                        acc.y += b.y;
+                        acc.z += b.z;
+                    }
+                } else if (pot) {
+                    for (int m = 0; m < M; m++) pot_term(x, y[m], Wm[m], &ph);
                 } else {
                     for (int m = 0; m < M; m++) bs_term(x, y[m], Wm[m], &acc);
                 }
@@ -992,14 +1109,21 @@ int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double
                 const onode* s = &tr->nodes[tr->near_idx[q]];
                 for (int64_t j = s->start; j < s->start + s->count; j++) {
                     if (j == k) continue;
-                    bs_term(x, ys[j], ws[j], &acc);
+                    if (pot)
+                        pot_term(x, ys[j], ws[j], &ph);
+                    else
+                        bs_term(x, ys[j], ws[j], &acc);
                     npp++;
                 }
             }
             int64_t i = tr->perm[k];
-            vel[3 * i] = f * acc.x;
-            vel[3 * i + 1] = f * acc.y;
-            vel[3 * i + 2] = f * acc.z;
+            if (pot) {
+                out[i] = f * ph;
+            } else {
+                out[3 * i] = f * acc.x;
+                out[3 * i + 1] = f * acc.y;
+                out[3 * i + 2] = f * acc.z;
+            }
         }
     }
     if (stats) {
@@ -1009,6 +1133,22 @@ int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double
     free(ys); free(ws); free(slot); free(yt); free(W); free(om);
     ref_free(&r);
     return err ? OR_ERR_ARG : OR_OK;
+}
+
+int or_tree_velocity(or_tree* tr, const double* zeta, const double* area, double theta, int d,
+                     int literal, double* vel, int64_t* stats, int nthreads)
+{
+    return tree_sum(tr, zeta, area, theta, d, literal, 0, vel, stats, nthreads);
+}
+
+/* Tree-code stream function (Sec. 3 applied to the potential kernel G of Sec. 2): the same
+ * lists, proxy points and proxy weights as or_tree_velocity (the weights do not depend on
+ * the kernel), PC as sum_m G(x, y~_m) W_m and PP as sum_j G(x, y_j) zeta_j A_j, j = i
+ * excluded.  psi[n] in original order; literal and stats as for the velocity.             */
+int or_tree_potential(or_tree* tr, const double* zeta, const double* area, double theta, int d,
+                      int literal, double* psi, int64_t* stats, int nthreads)
+{
+    return tree_sum(tr, zeta, area, theta, d, literal, 1, psi, stats, nthreads);
 }
 
 /* Proxy points and weights of every node with more than N_T particles (the clusters), in

@@ -387,3 +387,103 @@ def test_rk4_rh_wave_stationary():
     z0 = W.rh_vorticity(x, w, 1.0)
     EN = math.sqrt(np.sum((z - z0) ** 2 * area) / np.sum(z0**2 * area))
     assert EN < 2e-3, EN
+
+
+# -------------------------------------------------------------------- stream function
+# The potential kernel is the Green's function of Sec. 2, G(x, y) = -(1/4pi) log(1 - x.y),
+# and psi_i = sum_{j != i} G(x_i, x_j) zeta_j A_j.  With this G, u = grad psi x x is the
+# velocity of Sec. 2 (its gradient is the Biot-Savart kernel), so psi = -psi' for the psi'
+# with Lap psi' = zeta used by the velocity pins above.
+def _psi_exact(pos, field):
+    x, y, z = pos[:, 0], pos[:, 1], pos[:, 2]
+    if field == "solid":  # zeta = 2 (0.3) z
+        return 0.3 * z
+    if field == "rh":  # zeta = rh_vorticity(0.4, 0.2)
+        return 0.4 * z + 0.2 * z * (x**4 - 6 * x**2 * y**2 + y**4)
+    return x * z / 6.0  # zeta = x z (degree 2: Lap = -6)
+
+
+@pytest.mark.parametrize("field", ["solid", "rh", "y21"])
+def test_potential_converges_to_closed_forms(field):
+    errs = []
+    for L in (3, 4, 5):
+        pos = W.icosahedral_points(L)
+        area = W.voronoi_areas(pos)
+        if field == "solid":
+            zeta = 2 * 0.3 * pos[:, 2]
+        elif field == "rh":
+            zeta = W.rh_vorticity(pos, 0.4, 0.2)
+        else:
+            zeta = pos[:, 0] * pos[:, 2]
+        pe = _psi_exact(pos, field)
+        psi = O.direct_potential(pos, zeta, area)
+        errs.append(math.sqrt(np.sum((psi - pe) ** 2 * area) / np.sum(pe**2 * area)))
+    # observed 2e-2..7e-2 at level 3, then about h^1.7 (a factor 0.3 per level)
+    assert errs[0] < 0.1, errs
+    assert errs[1] < 0.4 * errs[0] and errs[2] < 0.4 * errs[1], errs
+
+
+def test_potential_energy_matches_velocity_energy():
+    # the kinetic energy 1/2 int |u|^2 = 1/2 int psi zeta (Lap psi = -zeta, integration by
+    # parts): the two quadratures, from the two independent oracle sums, converge together
+    gaps = []
+    for L in (3, 4, 5):
+        pos = W.icosahedral_points(L)
+        area = W.voronoi_areas(pos)
+        zeta = W.rh_vorticity(pos, 0.4, 0.2)
+        ep = 0.5 * np.sum(O.direct_potential(pos, zeta, area) * zeta * area)
+        u = O.direct(pos, zeta, area)
+        eu = 0.5 * np.sum(np.sum(u * u, axis=1) * area)
+        gaps.append(abs(ep - eu) / eu)
+    assert gaps[1] < 0.4 * gaps[0] and gaps[2] < 0.4 * gaps[1] and gaps[2] < 1e-2, gaps
+
+
+def test_potential_antipodal_pair_and_duplicates():
+    # two antipodal points: 1 - x.y = 2, so psi_0 = -(1/4pi) log(2) zeta_1 A_1
+    e = np.array([0.6, 0.0, 0.8])
+    pos = np.vstack([e, -e])
+    zeta, area = np.array([1.5, -2.0]), np.array([0.3, 0.7])
+    psi = O.direct_potential(pos, zeta, area)
+    assert psi[0] == pytest.approx(-math.log(2.0) / (4 * math.pi) * (-2.0 * 0.7), rel=1e-15)
+    assert psi[1] == pytest.approx(-math.log(2.0) / (4 * math.pi) * (1.5 * 0.3), rel=1e-15)
+    # a distinct particle at the same position as particle 3 adds nothing to psi_3
+    p20 = W.uniform_points(20, seed=9)
+    pos2 = np.vstack([p20, p20[3:4]])
+    z2, a2 = np.arange(21, dtype=float), np.ones(21)
+    assert O.direct_potential(pos2, z2, a2)[3] == O.direct_potential(p20, z2[:20], a2[:20])[3]
+
+
+def test_potential_rotation_invariance():
+    pos = W.uniform_points(500, seed=7)
+    rng = np.random.default_rng(8)
+    zeta, area = rng.standard_normal(500), W.equal_areas(500)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    psi = O.direct_potential(pos, zeta, area)
+    assert np.max(np.abs(O.direct_potential(pos @ Q.T, zeta, area) - psi)) <= 1e-12 * np.max(np.abs(psi))
+
+
+def test_potential_literal_alpha_solve_equals_proxy_form_and_tiny_theta():
+    pos = W.uniform_points(1200, seed=14)
+    rng = np.random.default_rng(15)
+    zeta, area = rng.standard_normal(1200), W.equal_areas(1200)
+    tr = O.Tree(pos, leaf_size=24)
+    for d in (3, 6):
+        a = tr.potential(zeta, area, theta=0.8, degree=d, literal=True)
+        b = tr.potential(zeta, area, theta=0.8, degree=d)
+        assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(b))
+    pd = O.direct_potential(pos, zeta, area)
+    pt, st = tr.potential(zeta, area, theta=1e-6, degree=4, return_stats=True)
+    assert st["pc"] == 0 and st["pp"] == 1200 * 1199
+    assert np.max(np.abs(pt - pd)) <= 1e-13 * np.max(np.abs(pd))
+
+
+def test_potential_tree_error_falls_with_degree():
+    pos = W.icosahedral_points(5)
+    area = W.equal_areas(len(pos))
+    zeta = W.sh_series_vorticity(pos, 16, seed=0)
+    pd = O.direct_potential(pos, zeta, area)
+    tr = O.Tree(pos, leaf_size=64)
+    errs = [math.sqrt(np.sum((tr.potential(zeta, area, 0.7, d) - pd) ** 2 * area) / np.sum(pd**2 * area))
+            for d in (2, 4, 6, 8, 10)]
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[2] < 1e-3, errs  # theta 0.7, d = 6: well inside the paper's 3-4 digits
