@@ -98,6 +98,13 @@ int sts_selftest_wait(sts_ctx* ctx, int32_t spins, void* stream);
 int sts_direct(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
                int64_t n, int32_t precision, double* vel, void* stream);
 
+/* Direct summation of the stream function psi_i = -(1/4 pi) sum_{j != i} log(|x_i - x_j|^2
+ * / 2) zeta_j A_j (Sec. 2 Green's function, Sec. 3 convolution sum): pos[n,3], zeta[n],
+ * area[n] in, psi[n] out; a distinct particle at the same position adds nothing.  Only
+ * precision = STS_FP64 is implemented (STS_ERR_ARG otherwise).  Asynchronous on `stream`. */
+int sts_direct_potential(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
+                         int64_t n, int32_t precision, double* psi, void* stream);
+
 /* Direct summation at nt targets: targets[nt] (device, int64 original indices in [0, n)),
  * vel[nt,3] out (row t = velocity of particle targets[t]).  Same arithmetic as
  * sts_direct.  Target indices are not range-checked on the device: the caller keeps them
@@ -149,6 +156,17 @@ int sts_tree_build_batched(sts_ctx* ctx, const double* pos, const int64_t* offse
  * case (list sizes are read back).  STS_ERR_STATE without a tree. */
 int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
                  double* vel, void* stream);
+
+/* Tree-code stream function (the convolution of Sec. 3 with the Green's function of Sec. 2,
+ * G(x, y) = -(1/4 pi) log(1 - x.y), written as -(1/4 pi) log(|x - y|^2 / 2)):
+ * psi_i = sum_{j != i} G(x_i, x_j) zeta_j A_j over the same PC + PP lists and proxy weights as
+ * sts_velocity (the weights do not depend on the kernel).  zeta[n], area[n] in, psi[n] out in
+ * the caller's order; a distinct particle at a target's position adds nothing.  With this G,
+ * u = grad psi x x is the velocity of sts_velocity and Lap psi = -zeta for zero-mean zeta.
+ * Only p->precision = STS_FP64 is implemented (STS_ERR_ARG otherwise).  STS_ERR_STATE
+ * without a tree.  Synchronises `stream` when the lists are (re)built. */
+int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
+                  double* psi, void* stream);
 
 /* One classical RK4 step (Sec. 4) of the Sec. 2 system dx_i/dt = u_i,
  * dzeta_i/dt = -2 Omega u_z,i, in place on pos[n,3] and zeta[n]; area[n] is constant.

@@ -198,6 +198,34 @@ int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_
     return STS_OK;
 }
 
+// The stream function on the current tree: the FP64 sources, lists, FP64 proxy weights (the
+// upward pass does not depend on the kernel) and the potential evaluation.
+int potential_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p, double* psi,
+                   cudaStream_t s)
+{
+    const int64_t n = c->n;
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(psi, 0, sizeof(double), s));
+        return STS_OK;
+    }
+    int rc;
+    phase_begin(c, kPhPrep, s);
+    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
+    phase_end(c, kPhPrep, s);
+    if (!c->have_lists || c->list_theta != p->theta) {
+        phase_begin(c, kPhLists, s);
+        if ((rc = build_lists(c, p->theta, s))) return rc;
+        phase_end(c, kPhLists, s);
+    }
+    phase_begin(c, kPhUpward, s);
+    if ((rc = upward_pass(c, p->degree, STS_FP64, s))) return rc;
+    phase_end(c, kPhUpward, s);
+    if ((rc = evaluate_potential(c, p->degree, psi, s))) return rc;
+    c->list_degree = p->degree;
+    return STS_OK;
+}
+
 int build_impl(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off, int ninst, const sts_params* p,
                cudaStream_t s)
 {
@@ -604,6 +632,47 @@ int sts_selftest_wait(sts_ctx* ctx, int32_t spins, void* stream)
     }
     if ((rc = wait_selftest(ctx, spins, S(stream)))) return rc;
     return sts_status(ctx, stream);
+}
+
+int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p, double* psi,
+                  void* stream)
+{
+    int rc = check_ctx(ctx, "sts_potential");
+    if (rc || (rc = check_params(p, "sts_potential"))) return rc;
+    if (p->precision != STS_FP64) {
+        set_error("sts_potential: only precision STS_FP64 is implemented");
+        return STS_ERR_ARG;
+    }
+    if (!ctx->have_tree) {
+        set_error("sts_potential: no tree (call sts_tree_build first)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->n > 0 && (!zeta || !area || !psi)) {
+        set_error("sts_potential: NULL array");
+        return STS_ERR_ARG;
+    }
+    return potential_impl(ctx, zeta, area, p, psi, S(stream));
+}
+
+int sts_direct_potential(sts_ctx* ctx, const double* pos, const double* zeta, const double* area, int64_t n,
+                         int32_t precision, double* psi, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_direct_potential");
+    if (rc || (rc = check_n(n, "sts_direct_potential"))) return rc;
+    if (precision != STS_FP64) {
+        set_error("sts_direct_potential: only precision STS_FP64 is implemented");
+        return STS_ERR_ARG;
+    }
+    if (n > 0 && (!pos || !zeta || !area || !psi)) {
+        set_error("sts_direct_potential: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(psi, 0, sizeof(double), S(stream)));
+        return STS_OK;
+    }
+    return direct_potential(ctx, pos, zeta, area, n, psi, S(stream));
 }
 
 int sts_direct(sts_ctx* ctx, const double* pos, const double* zeta, const double* area, int64_t n,

@@ -63,6 +63,16 @@ __device__ __forceinline__ void pair64(const double4 s, double tx, double ty, do
     az = fma(c, dz, az);
 }
 
+// The potential kernel's pair term (Sec. 2 Green's function, Eq. altkernel): acc += (2 w)
+// log(|d|^2 / 2); the caller scales by -1/(8 pi).  A source at the target's position (the
+// target itself, or a distinct particle at the same point) adds nothing.
+__device__ __forceinline__ void pot64(const double4 s, double tx, double ty, double tz, double& acc)
+{
+    const double dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    if (r2 > 0.0) acc = fma(s.w, log(0.5 * r2), acc);
+}
+
 // ------------------------------------------------------------------------ tree tasks
 // Task layout: targets t0 .. t0 + nt - 1 of one leaf; lane j < p = ceil(nt / 2) of phase s
 // (lane = s p + j, s < S) holds targets t0 + 2j and t0 + 2j + 1 and takes the sources
@@ -494,6 +504,7 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
 }
 
 // ------------------------------------------------------------------------ FP64 tree
+template <bool POT>
 __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int lane,
                                                const int64_t* __restrict__ far_off,
                                                const FarEntry* __restrict__ far_ent,
@@ -532,8 +543,13 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
 #pragma unroll 2
         for (int i = ph; i < cnt; i += S) {
             const double4 sv = sb[i];
-            pair64(sv, ax, ay, az, a[0], a[1], a[2]);
-            pair64(sv, bx, by, bz, a[3], a[4], a[5]);
+            if (POT) {
+                pot64(sv, ax, ay, az, a[0]);
+                pot64(sv, bx, by, bz, a[3]);
+            } else {
+                pair64(sv, ax, ay, az, a[0], a[1], a[2]);
+                pair64(sv, bx, by, bz, a[3], a[4], a[5]);
+            }
         }
     }
     for (int s2 = 1; s2 < S; s2++) {
@@ -544,7 +560,11 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
             if (lane < p) a[c] += v;
         }
     }
-    if (lane < p) {
+    if (POT) {
+        // psi = -(1/4 pi) sum w log(|d|^2 / 2), accumulated with 2 w
+        if (lane < p && v0) vel[perm[tk0]] = -0.5 * kInv4Pi * a[0];
+        if (lane < p && v1) vel[perm[tk1]] = -0.5 * kInv4Pi * a[3];
+    } else if (lane < p) {
         if (v0) {
             const int64_t i = perm[tk0];
             vel[3 * i] = -kInv4Pi * (x0.y * a[2] - x0.z * a[1]);
@@ -569,7 +589,9 @@ __device__ __forceinline__ int64_t next_task(unsigned long long* queue, int lane
     return (int64_t)__shfl_sync(kFull, t, 0);
 }
 
-// Persistent warps: each warp takes tasks from the queue until it runs dry.
+// Persistent warps: each warp takes tasks from the queue until it runs dry.  POT: the
+// potential kernel (vel then receives psi[n]).
+template <bool POT>
 __global__ void __launch_bounds__(kEvalWarps64 * 32)
 k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
@@ -581,7 +603,8 @@ k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);
     for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane))
-        eval_task_fp64(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, perm, vel);
+        eval_task_fp64<POT>(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, perm,
+                            vel);
 }
 
 // ------------------------------------------------------------------------ counts
@@ -714,7 +737,88 @@ __global__ void k_direct_finish(const double* __restrict__ part, int splits, int
     vel[3 * t + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
 }
 
+// Direct sum of the potential (FP64), same tiling as k_direct_fp64: partial sums of 2 w
+// log(|d|^2 / 2) per (target, source chunk).
+__global__ void __launch_bounds__(kDirT)
+k_direct_pot_fp64(const double4* __restrict__ s64, int64_t n, const int64_t* __restrict__ targets,
+                  int64_t nt, int64_t chunk, double* __restrict__ part)
+{
+    __shared__ double4 sb[kDirT];
+    const int64_t t = (int64_t)blockIdx.x * kDirT + threadIdx.x;
+    const bool valid = t < nt;
+    const int64_t i = valid ? (targets ? targets[t] : t) : 0;
+    const double4 x = s64[i];
+    const double tx = valid ? x.x : -1e3, ty = valid ? x.y : -1e3, tz = valid ? x.z : -1e3;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk, j1 = min(n, j0 + chunk);
+    double acc = 0.0;
+    for (int64_t b = j0; b < j1; b += kDirT) {
+        __syncthreads();
+        const int64_t j = b + threadIdx.x;
+        sb[threadIdx.x] = j < j1 ? s64[j] : make_double4(1e3, 1e3, 1e3, 0.0);
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < kDirT; q++) pot64(sb[q], tx, ty, tz, acc);
+    }
+    if (valid) part[(int64_t)blockIdx.y * nt + t] = acc;
+}
+
+__global__ void k_direct_pot_finish(const double* __restrict__ part, int splits, int64_t nt,
+                                    double* __restrict__ psi)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    double S = 0.0;
+    for (int s = 0; s < splits; s++) S += part[(int64_t)s * nt + t];
+    psi[t] = -0.5 * kInv4Pi * S;
+}
+
 }  // namespace
+
+int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
+                     double* psi, cudaStream_t s)
+{
+    const int64_t nt = n;
+    if (nt == 0) return STS_OK;
+    STS_CUDA(c->dsrc64.reserve(n + 1));
+    STS_CUDA(c->dsrc32.reserve(2 * n + 2));
+    const int64_t ntb = (nt + kDirT - 1) / kDirT;
+    int64_t splits = (4 * (int64_t)c->num_sms + ntb - 1) / ntb;
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, n / 1024)));
+    splits = std::min<int64_t>(splits, 256);
+    const int64_t chunk = ((n + splits - 1) / splits + kDirT - 1) / kDirT * kDirT;
+    splits = std::max<int64_t>(1, (n + chunk - 1) / chunk);
+    STS_CUDA(c->dpart.reserve(splits * nt + 1));
+    phase_begin(c, kPhDirect, s);
+    (k_direct_prep<<<blocks(n, 256), 256, 0, s>>>(pos, zeta, area, n, c->dsrc64.p, c->dsrc32.p), note_launch());
+    (k_direct_pot_fp64<<<dim3((unsigned)ntb, (unsigned)splits), kDirT, 0, s>>>(c->dsrc64.p, n, nullptr, nt, chunk,
+                                                                                c->dpart.p), note_launch());
+    (k_direct_pot_finish<<<blocks(nt, 256), 256, 0, s>>>(c->dpart.p, (int)splits, nt, psi), note_launch());
+    phase_end(c, kPhDirect, s);
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
+{
+    const int M = nbasis(degree);
+    const int64_t ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
+    if (ntasks <= 0) return STS_OK;
+    if (c->eval_blocks_fp64 <= 0) {
+        int b64 = 0;
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<true>, kEvalWarps64 * 32, 0));
+        c->eval_blocks_fp64 = std::max(1, c->num_sms * b64);
+    }
+    unsigned long long* queue = (unsigned long long*)(c->dc.p + kDcQueue);
+    STS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
+    const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
+    phase_begin(c, kPhEval, s);
+    (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+                                                       c->near_ent.p, c->prx64.p, M, c->src64.p, c->perm.p, psi,
+                                                       c->dc.p + kDcTasks, ntasks, queue), note_launch());
+    phase_end(c, kPhEval, s);
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
 
 int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
 {
@@ -732,7 +836,7 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
                                       (int)(kEvalWarps * sizeof(EvalSmem))));
         STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32,
                                                                kEvalWarps * sizeof(EvalSmem)));
-        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64, kEvalWarps64 * 32, 0));
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<false>, kEvalWarps64 * 32, 0));
         c->eval_blocks_mixed = std::max(1, sms * b32);
         c->eval_blocks_fp64 = std::max(1, sms * b64);
     }
@@ -740,7 +844,7 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
     if (precision == STS_FP64) {
         const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
         phase_begin(c, kPhEval, s);
-        (k_eval_fp64<<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+        (k_eval_fp64<false><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
                                                      c->near_ent.p, c->prx64.p, M, c->src64.p, c->perm.p, vel,
                                                      nt_d, ntasks, queue), note_launch());
         phase_end(c, kPhEval, s);

@@ -287,6 +287,9 @@ int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
 
 // ---- evaluation (sts_eval.cu) ---------------------------------------------------------
 int evaluate(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
+int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
+                     double* psi, cudaStream_t s);
+int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s);
 int wait_selftest(sts_ctx* c, int spins, cudaStream_t s);
 int count_interactions(sts_ctx* ctx, int degree, cudaStream_t s);
 int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,

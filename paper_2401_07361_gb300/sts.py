@@ -66,6 +66,8 @@ def load(build_if_needed: bool = True):
             "sts_direct_noalloc": (i32, [P, P, P, i64, i32, P, P]),
             "sts_tree_build": (i32, [P, P, i64, PP, P]),
             "sts_velocity": (i32, [P, P, P, PP, P, P]),
+            "sts_potential": (i32, [P, P, P, PP, P, P]),
+            "sts_direct_potential": (i32, [P, P, P, P, i64, i32, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
             "sts_tree_build_batched": (i32, [P, P, P, i32, PP, P]),
             "bve_rk4_step_batched": (i32, [P, P, P, P, P, i32, dbl, dbl, PP, P]),
@@ -201,6 +203,33 @@ def sts_velocity(ctx, zeta, area, p, vel=None, stream=None):
                                C.byref(p), _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
            "sts_velocity")
     return vel
+
+
+def sts_potential(ctx, zeta, area, p, psi=None, stream=None):
+    """Tree-code stream function psi[n] (FP64) for the tree last built in ctx."""
+    import torch
+
+    n = zeta.numel()
+    if psi is None:
+        psi = torch.empty(n, dtype=torch.float64, device=zeta.device)
+    _check(load().sts_potential(ctx, _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                C.byref(p), _dev(psi, torch.float64, n, "psi"), _stream(stream)),
+           "sts_potential")
+    return psi
+
+
+def sts_direct_potential(ctx, pos, zeta, area, precision=STS_FP64, psi=None, stream=None):
+    """Direct-sum stream function psi[n] (FP64)."""
+    import torch
+
+    n = pos.shape[0]
+    if psi is None:
+        psi = torch.empty(n, dtype=torch.float64, device=pos.device)
+    _check(load().sts_direct_potential(ctx, _dev(pos, torch.float64, 3 * n, "pos"),
+                                       _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                       n, int(precision), _dev(psi, torch.float64, n, "psi"), _stream(stream)),
+           "sts_direct_potential")
+    return psi
 
 
 def bve_rk4_step(ctx, pos, zeta, area, dt, Omega, p, stream=None):

@@ -1,0 +1,103 @@
+"""GPU stream function (the Green's function of Sec. 2 as the kernel) against the FP64
+oracle: direct sum and tree code (same lists and proxy weights as the velocity) within
+1e-12, interaction counts identical, and psi consistent with the velocity (u = grad psi x x)
+through the kinetic-energy identity."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2401_07361_gb300 import sts
+from paper_2401_07361_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = sts.Context()
+    yield c.h
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _clustered(seed):
+    rng = np.random.default_rng(seed)
+    c = np.array([0.3, -0.5, 0.8])
+    c /= np.linalg.norm(c)
+    p = c + 0.01 * rng.standard_normal((2000, 3))
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    return np.vstack([p, W.uniform_points(1000, seed + 1)])
+
+
+def _rel(a, b, w):
+    return math.sqrt(np.sum((a - b) ** 2 * w) / np.sum(b**2 * w))
+
+
+@pytest.mark.parametrize("n", [2, 3, 129, 1000, 4099])
+def test_direct_potential_matches_oracle(ctx, n):
+    pos = W.uniform_points(n, 60 + n)
+    rng = np.random.default_rng(n)
+    zeta, area = rng.standard_normal(n), rng.uniform(0.5, 1.5, n) * (4 * math.pi / n)
+    psi = sts.sts_direct_potential(ctx, dev(pos), dev(zeta), dev(area)).cpu().numpy()
+    ref = O.direct_potential(pos, zeta, area)
+    assert _rel(psi, ref, area) <= 1e-12
+    assert np.max(np.abs(psi - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", ["rand3000", "ico4", "clustered", "duplicates"])
+@pytest.mark.parametrize("degree", [4, 8])
+def test_tree_potential_matches_oracle(ctx, case, degree):
+    if case == "rand3000":
+        pos, leaf = W.uniform_points(3000, 61), 16
+    elif case == "ico4":
+        pos, leaf = W.icosahedral_points(4), 32
+    elif case == "clustered":
+        pos, leaf = _clustered(62), 24
+    else:
+        p = W.uniform_points(900, 63)
+        pos, leaf = np.vstack([p, p[:100]]), 8
+    n = len(pos)
+    rng = np.random.default_rng(64)
+    zeta, area = rng.standard_normal(n), rng.uniform(0.5, 1.5, n) * (4 * math.pi / n)
+    p = sts.params(theta=0.7, degree=degree, leaf_size=leaf, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    psi = sts.sts_potential(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    st = sts.sts_stats(ctx)
+    tr = O.Tree(pos, leaf)
+    ref, ost = tr.potential(zeta, area, 0.7, degree, return_stats=True)
+    assert st == ost
+    assert _rel(psi, ref, area) <= 1e-12
+
+
+def test_potential_and_velocity_share_the_tree_and_energy(ctx):
+    pos = W.icosahedral_points(5)
+    area = W.voronoi_areas(pos)
+    zeta = W.rh_vorticity(pos, 0.4, 0.2)
+    p = sts.params(theta=0.7, degree=8, leaf_size=64, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    u = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    psi = sts.sts_potential(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    u2 = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    assert np.array_equal(u, u2)  # the potential call leaves the velocity path unchanged
+    ep = 0.5 * np.sum(psi * zeta * area)
+    eu = 0.5 * np.sum(np.sum(u * u, axis=1) * area)
+    assert abs(ep - eu) <= 1e-2 * eu  # both quadratures of the same energy (level 5: 5.4e-3)
+
+
+def test_potential_arguments(ctx):
+    pos = W.uniform_points(100, 65)
+    z, a = np.ones(100), np.ones(100)
+    with pytest.raises(sts.StsError):
+        sts.sts_direct_potential(ctx, dev(pos), dev(z), dev(a), precision=sts.STS_MIXED)
+    sts.sts_tree_build(ctx, dev(pos), sts.params(leaf_size=16))
+    with pytest.raises(sts.StsError):
+        sts.sts_potential(ctx, dev(z), dev(a), sts.params(precision=sts.STS_MIXED))
+    one = sts.sts_direct_potential(ctx, dev(pos[:1]), dev(z[:1]), dev(a[:1])).cpu().numpy()
+    assert one[0] == 0.0
