@@ -52,6 +52,8 @@ def parse(argv=None):
     ap.add_argument("--rk4", type=int, default=0,
                     help="time this many RK4 steps of the workload instead of single evaluations "
                          "(Omega = 2 pi per day, dt = 1/288 day) and report the invariants' drift")
+    ap.add_argument("--potential", action="store_true",
+                    help="time the FP64 tree-code stream function (build + potential) instead")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
@@ -213,7 +215,8 @@ def run_reference(args):
 def run_rk4(args):
     """RK4 time stepping (the Sec. 4 integrator) of the workload, each step recorded once as a
     CUDA graph and replayed: steps/s, particle-stages/s, and the drift of the energy
-    E = 1/2 sum |u|^2 A, the enstrophy Z = 1/2 sum zeta^2 A, the circulation sum zeta A and
+    E = 1/2 sum |u|^2 A (and its second quadrature 1/2 sum psi zeta A from the FP64 tree-code
+    stream function), the enstrophy Z = 1/2 sum zeta^2 A, the circulation sum zeta A and
     the per-particle absolute vorticity zeta + 2 Omega z (carried exactly by the
     unprojected scheme)."""
     import numpy as np
@@ -242,13 +245,18 @@ def run_rk4(args):
     ctx = sts.Context()
     h = ctx.h
 
+    p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
+    psi = torch.empty(n, dtype=torch.float64, device=dev)
+
     def invariants():
         sts.sts_set_graph(h, False)
         sts.sts_tree_velocity(h, pos, zeta, area, pm, vel, offsets=offsets)
+        sts.sts_potential(h, zeta, area, p64, psi)  # on the tree just built (a forest for offsets)
         torch.cuda.synchronize()
         u, z, a, x = vel.cpu().numpy(), zeta.cpu().numpy(), area.cpu().numpy(), pos.cpu().numpy()
-        return dict(E=0.5 * float(np.sum(np.sum(u * u, 1) * a)), Z=0.5 * float(np.sum(z * z * a)),
-                    C=float(np.sum(z * a)), q=z + 2 * Omega * x[:, 2], r=np.linalg.norm(x, axis=1))
+        return dict(E=0.5 * float(np.sum(np.sum(u * u, 1) * a)), Epsi=0.5 * float(np.sum(psi.cpu().numpy() * z * a)),
+                    Z=0.5 * float(np.sum(z * z * a)), C=float(np.sum(z * a)), q=z + 2 * Omega * x[:, 2],
+                    r=np.linalg.norm(x, axis=1))
 
     def step():
         if offsets is None:
@@ -286,11 +294,116 @@ def run_rk4(args):
                    "launch": "host launches" if args.no_graph else "recorded CUDA graph per step"},
         "gpu_launches": int(launches), "clocks": clocks,
         "drift_after_steps": nsteps,
-        "drift": {"energy_rel": (inv1["E"] - inv0["E"]) / inv0["E"], "enstrophy_rel": (inv1["Z"] - inv0["Z"]) / inv0["Z"],
+        "drift": {"energy_rel": (inv1["E"] - inv0["E"]) / inv0["E"],
+                  "energy_psi_rel": (inv1["Epsi"] - inv0["Epsi"]) / inv0["Epsi"],
+                  "enstrophy_rel": (inv1["Z"] - inv0["Z"]) / inv0["Z"],
                   "circulation_abs": inv1["C"] - inv0["C"],
                   "abs_vorticity_max_change": float(np.max(np.abs(inv1["q"] - inv0["q"]))),
                   "max_radius_error": float(np.max(np.abs(inv1["r"] - 1.0)))},
     }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_potential(args):
+    """The stream function psi_i = -(1/4pi) sum_{j != i} log(1 - x_i.x_j) zeta_j A_j by the
+    FP64 tree code (tree build + potential per step, same lists and proxies as the velocity),
+    timed like the velocity bench; roofline against the FP64 peak with 10 flop per interaction
+    (3 FSUB, 3 FMA for |d|^2 = 5, 1/2, log counted as 1, FMA = 2), the oracle tree code beside."""
+    import numpy as np
+    import torch
+
+    from paper_2401_07361_gb300 import sts
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = load_workload(args.workload)
+    n = len(wl["pos"])
+    leaf = args.leaf or wl["leaf_size"]
+    offsets = wl.get("offsets")
+    p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    pos = torch.from_numpy(wl["pos"]).to(dev)
+    zeta = torch.from_numpy(wl["zeta"]).to(dev)
+    area = torch.from_numpy(wl["area"]).to(dev)
+    psi = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = sts.Context()
+    h = ctx.h
+
+    def step():
+        if offsets is None:
+            sts.sts_tree_build(h, pos, p64)
+        else:
+            sts.sts_tree_build_batched(h, pos, offsets, p64)
+        sts.sts_potential(h, zeta, area, p64, psi)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    stats = sts.sts_stats(h)
+    sampler = ClockSampler(local)
+    sampler.start()
+    sts.sts_set_timing(h, True)
+    l0 = sts.sts_launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    launches = sts.sts_launch_count() - l0
+    phases = sts.sts_phase_times(h)
+    sts.sts_set_timing(h, False)
+    total_ms = max_over_ranks(sum(times), ws, dev)
+    ms = total_ms / max(1, args.steps)
+    eval_ms = phases["eval"][0] / max(1, phases["eval"][1])
+    inter = stats["pc"] + stats["pp"]
+    peaks = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0)) if isinstance(peaks, dict) else 2070.0
+    peak_fp64 = 152 * 2 * 2 * mhz * 1e6 / 1e12  # TFLOP/s: 2 FP64 FMA lanes per SM per clock
+    achieved = 10.0 * inter / (eval_ms / 1e3) / 1e12
+    line = {
+        "metric": "stream function targets/s, FP64 tree code", "value": ws * n / (ms / 1e3), "unit": "targets/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
+                   "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": "host launches (build + potential)"},
+        "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp64, "traffic": None, "kernel": "k_eval_fp64<true>",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x sm_max_mhz (nominal 1.25 TFLOP/s); "
+                                    "10 flop per interaction", "kernel_ms": eval_ms},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "phases_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in phases.items() if v[1]},
+        "interactions_per_step": stats,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and n <= 3_000_000:
+        from oracle import oracle as O
+
+        t0 = time.perf_counter()
+        if offsets is None:
+            ref = O.Tree(wl["pos"], leaf).potential(wl["zeta"], wl["area"], args.theta, args.degree)
+        else:
+            ref = np.concatenate([O.Tree(wl["pos"][a:b], leaf).potential(wl["zeta"][a:b], wl["area"][a:b], args.theta,
+                                                                         args.degree)
+                                  for a, b in zip(offsets[:-1], offsets[1:]) if b > a])
+        cpu_s = time.perf_counter() - t0
+        got = psi.cpu().numpy()
+        a = wl["area"]
+        line["error"] = {"vs_fp64_oracle_tree_rel_l2": float(np.sqrt(np.sum((got - ref) ** 2 * a) / np.sum(ref**2 * a)))}
+        line["cpu_baseline"] = {"value": n / cpu_s, "unit": "targets/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"full workload: oracle tree build + FP64 tree-code stream function of all "
+                                          f"{n} targets, OpenMP over target leaves"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -303,6 +416,8 @@ def main():
         return run_reference(args)
     if args.rk4 > 0:
         return run_rk4(args)
+    if args.potential:
+        return run_potential(args)
     import numpy as np
     import torch
 
