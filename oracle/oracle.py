@@ -19,6 +19,8 @@ import os
 import subprocess
 import threading
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -280,20 +282,64 @@ def _project(x):
     return x / np.sqrt(np.sum(x * x, axis=1, keepdims=True))
 
 
-def rk4_step(pos, zeta, area, dt, Omega, velocity, project=True):
+def forcing_ramp(t, Tp=4.0, Tf=15.0):
+    """A(t) of the polar-vortex forcing (Sec. 4.4): a half-cosine ramp up over [0, Tp), 1 until
+    Tf - Tp, a half-cosine ramp down until Tf, 0 after (and before 0)."""
+    t = float(t)
+    if t < 0.0 or t >= Tf:
+        return 0.0
+    if t < Tp:
+        return (1.0 - math.cos(t / Tp * math.pi)) / 2.0
+    if t < Tf - Tp:
+        return 1.0
+    return (1.0 - math.cos(math.pi + (t - Tf + Tp) / Tp * math.pi)) / 2.0
+
+
+def forcing_profile(pos, theta1=math.pi / 3):
+    """B(theta) of the forcing (Sec. 4.4), theta the latitude: with r = tan^2 theta1 / tan^2
+    theta, B = r exp(1 - r) in the northern hemisphere, 0 in the southern."""
+    pos = _f64(pos, (-1, 3))
+    lat = np.arcsin(np.clip(pos[:, 2], -1.0, 1.0))
+    out = np.zeros(len(pos))
+    north = lat > 0.0
+    r = math.tan(theta1) ** 2 / np.tan(lat[north]) ** 2
+    out[north] = r * np.exp(1.0 - r)
+    return out
+
+
+def forcing(pos, t, k, amplitude, Tp=4.0, Tf=15.0, theta1=math.pi / 3):
+    """F_R(x, t) = amplitude k^2 A(t) B(theta) cos(k phi) (Sec. 4.4; the paper's amplitude is
+    (3/5) Omega), phi the longitude."""
+    pos = _f64(pos, (-1, 3))
+    lon = np.arctan2(pos[:, 1], pos[:, 0])
+    return amplitude * k * k * forcing_ramp(t, Tp, Tf) * forcing_profile(pos, theta1) * np.cos(k * lon)
+
+
+def polar_vortex_vorticity(pos, beta=1.5, theta0=15 * math.pi / 32):
+    """Initial polar vortex of Sec. 4.4: zeta_0 = pi exp(-2 beta^2 (1 - cos(theta0 - theta)))
+    (2 beta^2 cos(theta) sin(theta0 - theta) + sin(theta)), theta the latitude."""
+    pos = _f64(pos, (-1, 3))
+    lat = np.arcsin(np.clip(pos[:, 2], -1.0, 1.0))
+    e = np.exp(-2.0 * beta**2 * (1.0 - np.cos(theta0 - lat)))
+    return math.pi * e * (2.0 * beta**2 * np.cos(lat) * np.sin(theta0 - lat) + np.sin(lat))
+
+
+def rk4_step(pos, zeta, area, dt, Omega, velocity, project=True, t=0.0, forcing=None):
     """One classical RK4 step of the Sec. 2 system (x, zeta), dzeta/dt = -2 Omega u_z.
 
     ``velocity(x, zeta, area)`` evaluates u at the stage positions with the stage
     vorticities.  Stage points and the new positions are projected to the sphere
-    (x / |x|) when ``project`` is set.
+    (x / |x|) when ``project`` is set.  ``forcing(x, t)``: the forced system of Sec. 4.4,
+    whose Biot-Savart source strength is (zeta - F_R(x, t)) A at every stage (stage times t,
+    t + dt/2, t + dt/2, t + dt); the particle vorticity still follows dzeta/dt = -2 Omega u_z.
     """
     pos = _f64(pos, (-1, 3))
     zeta = _f64(zeta)
     proj = _project if project else (lambda v: v)
     k = []
     xs, zs = pos, zeta
-    for c in (0.5, 0.5, 1.0, None):
-        u = velocity(xs, zs, area)
+    for c, ts in zip((0.5, 0.5, 1.0, None), (t, t + 0.5 * dt, t + 0.5 * dt, t + dt)):
+        u = velocity(xs, zs if forcing is None else zs - forcing(xs, ts), area)
         k.append(u)
         if c is None:
             break

@@ -487,3 +487,59 @@ def test_potential_tree_error_falls_with_degree():
             for d in (2, 4, 6, 8, 10)]
     assert all(a > b for a, b in zip(errs, errs[1:])), errs
     assert errs[2] < 1e-3, errs  # theta 0.7, d = 6: well inside the paper's 3-4 digits
+
+
+# ---------------------------------------------------------------- forced BVE (Sec. 4.4)
+def test_forcing_ramp_joints_and_range():
+    # A(t) as defined in Sec. 4.4 with T_p = 4, T_f = 15: 0 before and after, continuous
+    # with zero slope at every joint, 1 on the plateau, inside [0, 1]
+    A = O.forcing_ramp
+    h = 1e-7
+    for tj, v in ((0.0, 0.0), (4.0, 1.0), (11.0, 1.0), (15.0, 0.0)):
+        assert A(tj - h) == pytest.approx(v, abs=1e-12) and A(tj + h) == pytest.approx(v, abs=1e-12)
+    assert A(2.0) == pytest.approx(0.5) and A(13.0) == pytest.approx(0.5)
+    ts = np.linspace(-1, 16, 1701)
+    vals = np.array([A(t) for t in ts])
+    assert vals.min() >= 0.0 and vals.max() <= 1.0
+    assert np.all(np.diff(vals[(ts >= 0) & (ts <= 4)]) >= 0) and np.all(np.diff(vals[(ts >= 11) & (ts <= 15)]) <= 0)
+
+
+def test_forcing_profile_peak_and_hemispheres():
+    # B = r exp(1 - r), r = tan^2 theta1 / tan^2 theta: its maximum 1 sits at theta = theta1,
+    # it vanishes at the pole, towards the equator and in the southern hemisphere
+    lat = np.linspace(-1.5, 1.5707963, 3001)
+    pos = np.stack([np.cos(lat), np.zeros_like(lat), np.sin(lat)], axis=1)
+    B = O.forcing_profile(pos, math.pi / 3)
+    assert np.all(B[lat <= 0] == 0.0)
+    assert lat[np.argmax(B)] == pytest.approx(math.pi / 3, abs=2e-3) and B.max() <= 1.0 + 1e-15
+    t1 = math.pi / 3
+    assert O.forcing_profile(np.array([[math.cos(t1), 0.0, math.sin(t1)]]), t1)[0] == pytest.approx(1.0, abs=1e-15)
+    assert B[-1] < 1e-6 and O.forcing_profile(np.array([[1.0, 0.0, 1e-3]]))[0] < 1e-12
+
+
+def test_forcing_zonal_mean_vanishes():
+    # cos(k phi) sums to zero over equally spaced longitudes: the forcing adds no circulation
+    # on any latitude ring
+    for k in (1, 2, 3):
+        for lat in (0.3, 1.0, 1.4):
+            lon = np.arange(64) * (2 * math.pi / 64)
+            pos = np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.full(64, np.sin(lat))], axis=1)
+            F = O.forcing(pos, 7.0, k, 0.6 * 2 * math.pi)
+            assert abs(F.sum()) <= 1e-12 * np.abs(F).sum()
+
+
+def test_forced_rk4_reduces_to_unforced_after_tf_and_keeps_absolute_vorticity():
+    pos = W.icosahedral_points(3)
+    area = W.equal_areas(len(pos))
+    zeta = O.polar_vortex_vorticity(pos)
+    Om = 2 * math.pi
+    vel = lambda x, z, a: O.direct(x, z, a)
+    f = lambda x, t: O.forcing(x, t, 2, 0.6 * Om)
+    x0, z0 = O.rk4_step(pos, zeta, area, 0.01, Om, vel)
+    x1, z1 = O.rk4_step(pos, zeta, area, 0.01, Om, vel, t=20.0, forcing=f)  # A = 0 after T_f
+    assert np.array_equal(x0, x1) and np.array_equal(z0, z1)
+    x2, z2 = O.rk4_step(pos, zeta, area, 0.01, Om, vel, project=False, t=6.0, forcing=f)
+    assert not np.allclose(x2, O.rk4_step(pos, zeta, area, 0.01, Om, vel, project=False)[0])
+    # the forcing enters only the Biot-Savart source: zeta + 2 Omega z is still carried
+    # exactly by the unprojected scheme
+    assert np.max(np.abs((z2 + 2 * Om * x2[:, 2]) - (zeta + 2 * Om * pos[:, 2]))) <= 1e-13
