@@ -69,6 +69,22 @@ typedef struct sts_params {
     double near_fp64_tau;
 } sts_params;
 
+/* Vorticity forcing of Sec. 4.4 (the polar-vortex experiment): the Biot-Savart source of
+ * every RK4 stage becomes (zeta - F_R(x, t)) A with
+ *   F_R = amplitude k^2 A(t) B(theta) cos(k phi),
+ *   A(t) = half-cosine ramp up over [0, Tp), 1 until Tf - Tp, ramp down until Tf, 0 after,
+ *   B(theta) = r exp(1 - r), r = tan^2 theta1 / tan^2 theta for latitude theta > 0, else 0,
+ * phi the longitude.  The paper's values: amplitude = (3/5) Omega, Tp = 4, Tf = 15 (days),
+ * theta1 = pi / 3, k = 1 or 2.  The particle vorticity itself still follows
+ * dzeta/dt = -2 Omega dz/dt. */
+typedef struct {
+    int32_t k;        /* zonal wavenumber, >= 1 */
+    int32_t reserved; /* 0 */
+    double amplitude; /* factor in front of k^2 A(t) B cos(k phi) */
+    double Tp, Tf;    /* ramp length and end of the forcing, in the time unit of dt */
+    double theta1;    /* latitude of maximum forcing (radians, in (0, pi/2)) */
+} sts_forcing;
+
 typedef struct sts_ctx sts_ctx;
 
 /* Creates an empty context on the current device.  *out is set only on success. */
@@ -176,6 +192,14 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
  * `stream`. */
 int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n,
                  double dt, double Omega, const sts_params* p, void* stream);
+
+/* bve_rk4_step of the forced system of Sec. 4.4: the step starts at time t; stage k of the
+ * step sees the forcing at t, t + dt/2, t + dt/2, t + dt.  The step runs eagerly (it is not
+ * recorded as a graph: its stage times change from step to step).  STS_ERR_ARG for a NULL
+ * forcing, k < 1, Tp <= 0, Tf < 2 Tp, theta1 outside (0, pi/2) or non-finite values. */
+int bve_rk4_step_forced(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, double t,
+                        double dt, double Omega, const sts_forcing* forcing, const sts_params* p,
+                        void* stream);
 
 /* One RK4 step of ninst independent instances (offsets as in sts_tree_build_batched), in
  * place on pos[n,3] and zeta[n]; every stage builds the forest and evaluates all instances

@@ -88,7 +88,7 @@ sts_ctx::~sts_ctx()
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
-    up_frame32.release(); src_hl.release(); lw_terms.release();
+    up_frame32.release(); src_hl.release(); lw_terms.release(); rk_zf.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
@@ -264,7 +264,8 @@ int upload_offsets(sts_ctx* c, const int64_t* offsets, int32_t ninst, const int6
 
 // One RK4 step of the whole forest (one instance when inst_off is NULL).
 int rk4_impl(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, const int64_t* inst_off,
-             int ninst, double dt, double Omega, const sts_params* p, cudaStream_t s)
+             int ninst, double dt, double Omega, const sts_params* p, cudaStream_t s,
+             const sts_forcing* forcing = nullptr, double t = 0.0)
 {
     int rc;
     if (!isfinite(dt) || !isfinite(Omega)) {
@@ -287,11 +288,18 @@ int rk4_impl(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_
     STS_CUDA(cudaMemcpyAsync(c->rk_z0.p, zeta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     const double cst[3] = {0.5, 0.5, 1.0};
     const double bst[3] = {1.0, 2.0, 2.0};
+    const double tst[4] = {0.0, 0.5, 0.5, 1.0};  // stage times t + tst dt (forced system)
+    if (forcing) STS_CUDA(c->rk_zf.reserve(n));
     const double* xs = c->rk_x0.p;
     const double* zs = c->rk_z0.p;
     for (int st = 0; st < 4; st++) {
         if ((rc = build_impl(c, xs, n, inst_off, ninst, p, s))) return rc;
-        if ((rc = velocity_impl(c, zs, area, p, c->rk_k.p, s))) return rc;
+        const double* src = zs;
+        if (forcing) {
+            forced_source(xs, zs, n, forcing, t + tst[st] * dt, c->rk_zf.p, s);
+            src = c->rk_zf.p;
+        }
+        if ((rc = velocity_impl(c, src, area, p, c->rk_k.p, s))) return rc;
         if (st < 3) {
             rk4_stage(c->rk_x0.p, c->rk_z0.p, c->rk_k.p, cst[st] * dt, Omega, c->rk_xs.p, c->rk_zs.p,
                       c->rk_ksum.p, bst[st], st == 0, n, s);
@@ -763,6 +771,19 @@ int bve_rk4_step(sts_ctx* ctx, double* pos, double* zeta, const double* area, in
     if (rc || (rc = check_n(n, "bve_rk4_step")) || (rc = check_params(p, "bve_rk4_step"))) return rc;
     if (ctx->graph_on) return rk4_graph(ctx, pos, zeta, area, n, nullptr, nullptr, 1, dt, Omega, p, S(stream));
     return rk4_impl(ctx, pos, zeta, area, n, nullptr, 1, dt, Omega, p, S(stream));
+}
+
+int bve_rk4_step_forced(sts_ctx* ctx, double* pos, double* zeta, const double* area, int64_t n, double t,
+                        double dt, double Omega, const sts_forcing* f, const sts_params* p, void* stream)
+{
+    int rc = check_ctx(ctx, "bve_rk4_step_forced");
+    if (rc || (rc = check_params(p, "bve_rk4_step_forced")) || (rc = check_n(n, "bve_rk4_step_forced"))) return rc;
+    if (!f || f->k < 1 || !(f->Tp > 0.0) || !(f->Tf >= 2.0 * f->Tp) || !(f->theta1 > 0.0) ||
+        !(f->theta1 < 1.5707963267948966) || !isfinite(f->amplitude) || !isfinite(f->Tf) || !isfinite(t)) {
+        set_error("bve_rk4_step_forced: forcing needs k >= 1, Tp > 0, Tf >= 2 Tp, 0 < theta1 < pi/2, finite values");
+        return STS_ERR_ARG;
+    }
+    return rk4_impl(ctx, pos, zeta, area, n, nullptr, 1, dt, Omega, p, S(stream), f, t);
 }
 
 int bve_rk4_step_batched(sts_ctx* ctx, double* pos, double* zeta, const double* area, const int64_t* offsets,

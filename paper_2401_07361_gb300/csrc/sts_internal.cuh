@@ -234,6 +234,7 @@ struct sts_ctx {
 
     // ---- RK4 scratch -------------------------------------------------------------------
     sts::DevBuf<double> rk_x0, rk_z0, rk_xs, rk_zs, rk_k, rk_ksum;
+    sts::DevBuf<double> rk_zf;           // [n] forced source vorticity zeta - F_R (Sec. 4.4)
 
     // ---- stats and phase timing -------------------------------------------------------
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
@@ -297,6 +298,9 @@ int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double
                cudaStream_t s);
 
 // ---- RK4 (sts_rk4.cu) -----------------------------------------------------------------
+double forcing_ramp(double t, double Tp, double Tf);
+void forced_source(const double* xs, const double* zs, int64_t n, const sts_forcing* f, double t, double* zf,
+                   cudaStream_t s);
 void rk4_stage(const double* x0, const double* z0, const double* k, double cdt, double Omega,
                double* xs, double* zs, double* ksum, double b, int first, int64_t n,
                cudaStream_t s);

@@ -62,7 +62,45 @@ __global__ void k_final(double* __restrict__ x, double* __restrict__ z, const do
     z[i] = z0[i] + h * (-2.0 * Omega * sz);
 }
 
+// Source vorticity of the forced system (Sec. 4.4): zf = zs - c B(theta) cos(k phi), with
+// c = amplitude k^2 A(t) from the host, theta the latitude, phi the longitude of the stage
+// point, B = r exp(1 - r), r = tan^2 theta1 / tan^2 theta north of the equator, 0 south.
+__global__ void k_forced_source(const double* __restrict__ xs, const double* __restrict__ zs, int64_t n,
+                                double c, int k, double tan2t1, double* __restrict__ zf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = xs[3 * i], y = xs[3 * i + 1], z = xs[3 * i + 2];
+    const double lat = asin(fmin(1.0, fmax(-1.0, z)));
+    double F = 0.0;
+    if (lat > 0.0 && c != 0.0) {
+        const double t = tan(lat);
+        const double r = tan2t1 / (t * t);
+        F = c * (r * exp(1.0 - r)) * cos(k * atan2(y, x));
+    }
+    zf[i] = zs[i] - F;
+}
+
 }  // namespace
+
+// A(t) of Sec. 4.4: half-cosine ramps of length Tp at both ends of [0, Tf], 1 between.
+double forcing_ramp(double t, double Tp, double Tf)
+{
+    const double pi = 3.14159265358979323846;
+    if (t < 0.0 || t >= Tf) return 0.0;
+    if (t < Tp) return (1.0 - cos(t / Tp * pi)) / 2.0;
+    if (t < Tf - Tp) return 1.0;
+    return (1.0 - cos(pi + (t - Tf + Tp) / Tp * pi)) / 2.0;
+}
+
+void forced_source(const double* xs, const double* zs, int64_t n, const sts_forcing* f, double t, double* zf,
+                   cudaStream_t s)
+{
+    const double c = f->amplitude * (double)f->k * (double)f->k * forcing_ramp(t, f->Tp, f->Tf);
+    const double t1 = tan(f->theta1);
+    if (n > 0)
+        (k_forced_source<<<blocks(n, 256), 256, 0, s>>>(xs, zs, n, c, f->k, t1 * t1, zf), note_launch());
+}
 
 void rk4_stage(const double* x0, const double* z0, const double* k, double cdt, double Omega,
                double* xs, double* zs, double* ksum, double b, int first, int64_t n, cudaStream_t s)

@@ -9,6 +9,7 @@ cannot be loaded, every call raises.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -33,6 +34,17 @@ class StsError(RuntimeError):
 class sts_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("degree", C.c_int32), ("leaf_size", C.c_int32),
                 ("max_level", C.c_int32), ("precision", C.c_int32), ("near_fp64_tau", C.c_double)]
+
+
+class sts_forcing(C.Structure):
+    """The vorticity forcing of Sec. 4.4 (see include/sts.h)."""
+    _fields_ = [("k", C.c_int32), ("reserved", C.c_int32), ("amplitude", C.c_double), ("Tp", C.c_double),
+                ("Tf", C.c_double), ("theta1", C.c_double)]
+
+
+def forcing(k, amplitude, Tp=4.0, Tf=15.0, theta1=math.pi / 3):
+    """sts_forcing for zonal wavenumber k; the paper's amplitude is (3/5) Omega."""
+    return sts_forcing(int(k), 0, float(amplitude), float(Tp), float(Tf), float(theta1))
 
 
 def params(theta=0.7, degree=8, leaf_size=128, max_level=16, precision=STS_MIXED, near_fp64_tau=0.0):
@@ -69,6 +81,7 @@ def load(build_if_needed: bool = True):
             "sts_potential": (i32, [P, P, P, PP, P, P]),
             "sts_direct_potential": (i32, [P, P, P, P, i64, i32, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
+            "bve_rk4_step_forced": (i32, [P, P, P, P, i64, dbl, dbl, dbl, C.POINTER(sts_forcing), PP, P]),
             "sts_tree_build_batched": (i32, [P, P, P, i32, PP, P]),
             "bve_rk4_step_batched": (i32, [P, P, P, P, P, i32, dbl, dbl, PP, P]),
             "sts_tree_info": (i32, [P, P, P]),
@@ -239,6 +252,17 @@ def bve_rk4_step(ctx, pos, zeta, area, dt, Omega, p, stream=None):
     _check(load().bve_rk4_step(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
                                _dev(area, torch.float64, n, "area"), n, float(dt), float(Omega), C.byref(p),
                                _stream(stream)), "bve_rk4_step")
+
+
+def bve_rk4_step_forced(ctx, pos, zeta, area, t, dt, Omega, forcing, p, stream=None):
+    """One RK4 step of the forced system of Sec. 4.4 starting at time t (in place)."""
+    import torch
+
+    n = pos.shape[0]
+    _check(load().bve_rk4_step_forced(ctx, _dev(pos, torch.float64, 3 * n, "pos"),
+                                      _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                      n, float(t), float(dt), float(Omega), C.byref(forcing), C.byref(p),
+                                      _stream(stream)), "bve_rk4_step_forced")
 
 
 def _offsets(offsets):
