@@ -52,6 +52,9 @@ def parse(argv=None):
     ap.add_argument("--rk4", type=int, default=0,
                     help="time this many RK4 steps of the workload instead of single evaluations "
                          "(Omega = 2 pi per day, dt = 1/288 day) and report the invariants' drift")
+    ap.add_argument("--forcing", type=int, default=0,
+                    help="with --rk4: the forced system of Sec. 4.4 with this zonal wavenumber (0: none)")
+    ap.add_argument("--t0", type=float, default=0.0, help="with --forcing: start time of the run (days)")
     ap.add_argument("--potential", action="store_true",
                     help="time the FP64 tree-code stream function (build + potential) instead")
     ap.add_argument("--no-graph", action="store_true",
@@ -258,8 +261,14 @@ def run_rk4(args):
                     Z=0.5 * float(np.sum(z * z * a)), C=float(np.sum(z * a)), q=z + 2 * Omega * x[:, 2],
                     r=np.linalg.norm(x, axis=1))
 
+    forcing = sts.forcing(args.forcing, 0.6 * Omega) if args.forcing > 0 else None
+    clock = [args.t0]
+
     def step():
-        if offsets is None:
+        if forcing is not None:
+            sts.bve_rk4_step_forced(h, pos, zeta, area, clock[0], dt, Omega, forcing, pm)
+            clock[0] += dt
+        elif offsets is None:
             sts.bve_rk4_step(h, pos, zeta, area, dt, Omega, pm)
         else:
             sts.bve_rk4_step_batched(h, pos, zeta, area, offsets, dt, Omega, pm)
@@ -291,7 +300,10 @@ def run_rk4(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
                    "dt_day": dt, "Omega_per_day": Omega, "near_fp64_tau": tau,
-                   "launch": "host launches" if args.no_graph else "recorded CUDA graph per step"},
+                   "forcing": ({"k": args.forcing, "amplitude": "3/5 Omega", "Tp": 4.0, "Tf": 15.0,
+                                "theta1": "pi/3", "t0": args.t0} if forcing is not None else None),
+                   "launch": ("host launches (forced steps are not recorded)" if forcing is not None or args.no_graph
+                              else "recorded CUDA graph per step")},
         "gpu_launches": int(launches), "clocks": clocks,
         "drift_after_steps": nsteps,
         "drift": {"energy_rel": (inv1["E"] - inv0["E"]) / inv0["E"],

@@ -315,15 +315,6 @@ def forcing(pos, t, k, amplitude, Tp=4.0, Tf=15.0, theta1=math.pi / 3):
     return amplitude * k * k * forcing_ramp(t, Tp, Tf) * forcing_profile(pos, theta1) * np.cos(k * lon)
 
 
-def polar_vortex_vorticity(pos, beta=1.5, theta0=15 * math.pi / 32):
-    """Initial polar vortex of Sec. 4.4: zeta_0 = pi exp(-2 beta^2 (1 - cos(theta0 - theta)))
-    (2 beta^2 cos(theta) sin(theta0 - theta) + sin(theta)), theta the latitude."""
-    pos = _f64(pos, (-1, 3))
-    lat = np.arcsin(np.clip(pos[:, 2], -1.0, 1.0))
-    e = np.exp(-2.0 * beta**2 * (1.0 - np.cos(theta0 - lat)))
-    return math.pi * e * (2.0 * beta**2 * np.cos(lat) * np.sin(theta0 - lat) + np.sin(lat))
-
-
 def rk4_step(pos, zeta, area, dt, Omega, velocity, project=True, t=0.0, forcing=None):
     """One classical RK4 step of the Sec. 2 system (x, zeta), dzeta/dt = -2 Omega u_z.
 

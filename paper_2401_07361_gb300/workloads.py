@@ -118,6 +118,14 @@ def rh_vorticity(pos: np.ndarray, w: float, K: float) -> np.ndarray:
     return 2.0 * w * z + 30.0 * K * z * (x**4 - 6.0 * x**2 * y**2 + y**4)
 
 
+def polar_vortex_vorticity(pos: np.ndarray, beta: float = 1.5, theta0: float = 15 * math.pi / 32) -> np.ndarray:
+    """Initial polar vortex of Sec. 4.4: pi exp(-2 beta^2 (1 - cos(theta0 - theta)))
+    (2 beta^2 cos(theta) sin(theta0 - theta) + sin(theta)), theta the latitude."""
+    lat, _ = lat_lon(pos)
+    e = np.exp(-2.0 * beta**2 * (1.0 - np.cos(theta0 - lat)))
+    return math.pi * e * (2.0 * beta**2 * np.cos(lat) * np.sin(theta0 - lat) + np.sin(lat))
+
+
 def _real_sh_iter(pos: np.ndarray, lmax: int):
     """Yields ((l, m), values) of the orthonormal real spherical harmonics Y_lm at ``pos``
     for 0 <= l <= lmax, m in [-l, l]; m > 0 uses cos(m lambda), m < 0 uses sin(|m| lambda).
@@ -227,6 +235,8 @@ def workload(name: str, areas: str = "default"):
                   the coefficients would change nothing structural, the recipe is stated).
     ico9_jet      N = 2621442 icosahedral level-9 vertices, jet + bump, equal areas.
     rand10m_sh32  N = 10485762 uniform points (seed 0), SH series l <= 32, equal areas.
+    polar163k     N = 163842 icosahedral level-7 vertices, the polar vortex of Sec. 4.4, equal
+                  areas (degree 6 as in that experiment).
     """
     if name == "ico5_rh":
         pos = icosahedral_points(5)
@@ -248,6 +258,11 @@ def workload(name: str, areas: str = "default"):
         zeta = sh_series_vorticity(pos, 32, seed=0)
         return dict(pos=pos, zeta=zeta, area=equal_areas(len(pos)), theta=0.7, degree=8,
                     leaf_size=256)
+    if name == "polar163k":
+        pos = icosahedral_points(7)
+        zeta = polar_vortex_vorticity(pos)
+        area = voronoi_areas(pos) if areas == "voronoi" else equal_areas(len(pos))
+        return dict(pos=pos, zeta=zeta, area=area, leaf_size=128, degree=6)
     if name == "ensemble64":
         # 64 independent instances, N_b log-uniform in [10242, 163842] (seed 0); uniform points
         # (seed 100 + b); equal areas 4 pi / N_b; RH wave 4 plus 1e-2 x an RMS-normalised

@@ -38,7 +38,7 @@ def _step(ctx, pos, zeta, area, t, dt, k, p):
 def test_forced_step_matches_oracle(ctx, k, t):
     pos = W.icosahedral_points(4)
     area = W.equal_areas(len(pos))
-    zeta = O.polar_vortex_vorticity(pos)
+    zeta = W.polar_vortex_vorticity(pos)
     dt = 1.0 / 48.0
     tr_vel = lambda x, z, a: O.Tree(x, 32).velocity(z, a, 0.7, 6)
     f = lambda x, ts: O.forcing(x, ts, k, 0.6 * OMEGA)
@@ -60,7 +60,7 @@ def test_forced_step_matches_oracle(ctx, k, t):
 def test_forced_step_after_tf_equals_unforced(ctx):
     pos = W.icosahedral_points(3)
     area = W.equal_areas(len(pos))
-    zeta = O.polar_vortex_vorticity(pos)
+    zeta = W.polar_vortex_vorticity(pos)
     p = sts.params(theta=0.7, degree=6, leaf_size=32, precision=sts.STS_FP64)
     x1, z1 = _step(ctx, pos, zeta, area, 20.0, 0.01, 2, p)
     x2, z2 = dev(pos), dev(zeta)

@@ -531,7 +531,7 @@ def test_forcing_zonal_mean_vanishes():
 def test_forced_rk4_reduces_to_unforced_after_tf_and_keeps_absolute_vorticity():
     pos = W.icosahedral_points(3)
     area = W.equal_areas(len(pos))
-    zeta = O.polar_vortex_vorticity(pos)
+    zeta = W.polar_vortex_vorticity(pos)
     Om = 2 * math.pi
     vel = lambda x, z, a: O.direct(x, z, a)
     f = lambda x, t: O.forcing(x, t, 2, 0.6 * Om)
