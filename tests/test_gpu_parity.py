@@ -154,6 +154,42 @@ def test_velocity_mixed_within_1e6_of_fp64_oracle(ctx, name):
     assert O.rel_max(v, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("n,leaf", [(2, 1), (3, 1), (5, 2), (17, 4), (64, 64), (65, 64), (129, 16), (700, 128),
+                                    (700, 8), (1500, 3)])
+def test_small_and_ragged_mixed_and_fp64(ctx, n, leaf):
+    """Tiny trees, leaves of one particle, leaves just over a task's 64 targets, odd counts:
+    every lane class S = 1..8 and ragged block and task tails, FP64 and mixed against the
+    oracle."""
+    pos = W.uniform_points(n, 80 + n)
+    zeta, area = _fields(n, 81)
+    ref = O.Tree(pos, leaf).velocity(zeta, area, 0.6, 6)
+    for prec, tol in ((sts.STS_FP64, 1e-12), (sts.STS_MIXED, 1e-6)):
+        p = sts.params(theta=0.6, degree=6, leaf_size=leaf, precision=prec, near_fp64_tau=0.01 * 4 * math.pi / n)
+        sts.sts_tree_build(ctx, dev(pos), p)
+        v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+        assert O.rel_l2(v, ref, area) <= tol, (prec, O.rel_l2(v, ref, area))
+
+
+@pytest.mark.parametrize("degree", [1, 2, 10, 14, 16])
+def test_extreme_degrees(ctx, degree):
+    """Degrees 1 to 16 (M = 3 to 153 proxy points, the largest the tables hold) with far
+    clusters present, FP64 and mixed against the oracle.  At degree 16 the FP64 tolerance is
+    1e-11: cond(V_ref) grows by orders of magnitude per degree, and the contraction carries
+    the moments' summation-order rounding (which differs between the two sides) into W."""
+    pos = W.uniform_points(3000, 90)
+    zeta, area = _fields(3000, 91)
+    ref = O.Tree(pos, 16).velocity(zeta, area, 0.7, degree)
+    p = sts.params(theta=0.7, degree=degree, leaf_size=16, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    assert sts.sts_stats(ctx)["pc"] > 0
+    assert O.rel_l2(v, ref, area) <= (1e-12 if degree <= 14 else 1e-11)
+    p = sts.params(theta=0.7, degree=degree, leaf_size=16, precision=sts.STS_MIXED,
+                   near_fp64_tau=0.01 * 4 * math.pi / 3000)
+    v = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    assert O.rel_l2(v, ref, area) <= 1e-6
+
+
 @pytest.mark.parametrize("name", ["rand3000", "clustered"])
 def test_proxy_weights_match_oracle(ctx, name):
     pos, leaf, ml = _case(name)
