@@ -66,6 +66,9 @@ def _L():
             lib.or_direct_potential.argtypes = [i64, P, P, P, i64, P, P, i32]
             lib.or_tree_potential.argtypes = [P, P, P, dbl, i32, i32, P, P, i32]
             lib.or_pc_pair_potential.argtypes = [P, i32, i64, P, P, P, P, P]
+            lib.or_dual_lists.argtypes = [P, dbl, P]
+            lib.or_dual_export.argtypes = [P, i32, P, P]
+            lib.or_tree_velocity_dual.argtypes = [P, P, P, dbl, i32, P, P, i32]
             lib.or_icosahedron.argtypes = [P, P]
             _lib = lib
     return _lib
@@ -196,6 +199,33 @@ class Tree:
         if return_stats:
             return psi, dict(pc=int(st[0]), pp=int(st[1]))
         return psi
+
+    def dual_lists(self, theta: float):
+        """Pairs of the dual traversal (Sec. 3.4): {"PP"|"PC"|"CP"|"CC": (target nodes,
+        source nodes)} in traversal order."""
+        cnt = np.zeros(4, np.int64)
+        _check(_L().or_dual_lists(self._h, float(theta), _p(cnt)), "dual lists")
+        out = {}
+        for k, name in enumerate(("PP", "PC", "CP", "CC")):
+            t = np.zeros(int(cnt[k]), np.int32)
+            s = np.zeros(int(cnt[k]), np.int32)
+            _check(_L().or_dual_export(self._h, k, _p(t), _p(s)), "dual export")
+            out[name] = (t, s)
+        return out
+
+    def velocity_dual(self, zeta, area, theta: float = 0.7, degree: int = 8, nthreads: int = 0,
+                      return_stats: bool = False):
+        """Tree-code velocity with all four interactions of the dual traversal."""
+        n = self.pos.shape[0]
+        zeta = _f64(zeta, (n,))
+        area = _f64(area, (n,))
+        vel = np.zeros((n, 3))
+        st = np.zeros(5, np.int64)
+        _check(_L().or_tree_velocity_dual(self._h, _p(zeta), _p(area), float(theta), int(degree), _p(vel),
+                                          _p(st), nthreads), "dual velocity")
+        if return_stats:
+            return vel, dict(pp=int(st[0]), pc=int(st[1]), cp=int(st[2]), cc=int(st[3]), down=int(st[4]))
+        return vel
 
     def clusters(self, zeta, area, degree: int):
         n = self.pos.shape[0]

@@ -29,6 +29,10 @@
  *                         interaction (Sec. 3.3.2): W = V_s^{-T} omega.
  *   pc_literal            the PC interaction exactly as printed: solve V alpha = G(x, y~),
  *                         then sum_k alpha_k omega_k (Sec. 3.3.2).
+ *   dual / or_dual_lists / or_tree_velocity_dual
+ *                         the dual tree traversal of Sec. 3.4 with all four interactions
+ *                         (PP, PC, CP, CC of Sec. 3.3); CP and CC give the velocity at the
+ *                         target cluster's proxy points, interpolated to its particles.
  *   pot_term / or_direct_potential / or_tree_potential
  *                         the stream function: the same sums with the Green's function
  *                         G = -(1/4pi) log(1 - x.y) of Sec. 2 as the kernel (the convolution
@@ -238,6 +242,13 @@ typedef struct or_tree {
     int has_lists;
     int64_t *far_off, *near_off;
     int32_t *far_idx, *near_idx;
+    /* dual-traversal pairs (target node, source node) for one theta, per kind PP, PC, CP, CC,
+     * in traversal order */
+    double dual_theta;
+    int has_dual;
+    int32_t* dual_t[4];
+    int32_t* dual_s[4];
+    int64_t dual_n[4];
 } or_tree;
 
 static int push_node(or_tree* t, const onode* nd)
@@ -299,6 +310,10 @@ void or_tree_free(or_tree* t)
     free(t->near_off);
     free(t->far_idx);
     free(t->near_idx);
+    for (int k = 0; k < 4; k++) {
+        free(t->dual_t[k]);
+        free(t->dual_s[k]);
+    }
     free(t);
 }
 
@@ -599,6 +614,77 @@ int or_lists_export(const or_tree* tr, int64_t* far_off, int32_t* far_idx, int64
     if (near_off) memcpy(near_off, tr->near_off, sizeof(int64_t) * (size_t)(L + 1));
     if (far_idx) memcpy(far_idx, tr->far_idx, sizeof(int32_t) * (size_t)tr->far_off[L]);
     if (near_idx) memcpy(near_idx, tr->near_idx, sizeof(int32_t) * (size_t)tr->near_off[L]);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Dual tree traversal (Sec. 3.4) with the four interactions of Sec. 3.3.  From the 20 x 20
+ * pairs of roots, a pair (T_t, T_s) that passes the MAC interacts by its particle counts
+ * against N_T: PP when both hold at most N_T, PC when only the source holds more, CP when
+ * only the target does, CC when both do.  A pair that fails the MAC interacts directly (PP)
+ * when both triangles are leaves; otherwise the triangle with more particles is refined (its
+ * children paired with the other, in digit order).  Reading (the paper's sentence is garbled
+ * there): a leaf is never refined, so a failing pair with one leaf refines the other; on equal
+ * counts the target is refined.  A node "holds more than N_T" exactly when it is a cluster
+ * (count > N_T), so the targets of PC and PP are leaves and the targets of CP and CC are
+ * clusters, possibly leaves at the depth limit.                                           */
+enum { KPP = 0, KPC = 1, KCP = 2, KCC = 3 };
+
+static int dual(const or_tree* tr, int32_t t, int32_t s, double theta, ivec* pt, ivec* ps)
+{
+    const onode *tn = &tr->nodes[t], *sn = &tr->nodes[s];
+    const int tc = tn->count > tr->leaf_size, sc = sn->count > tr->leaf_size;
+    int kind = -1;
+    if (mac(tn, sn, theta))
+        kind = tc ? (sc ? KCC : KCP) : (sc ? KPC : KPP);
+    else if (tn->leaf && sn->leaf)
+        kind = KPP;
+    if (kind >= 0) {
+        if (ivec_push(&pt[kind], t) || ivec_push(&ps[kind], s)) return OR_ERR_MEM;
+        return OR_OK;
+    }
+    if (!tn->leaf && (sn->leaf || tn->count >= sn->count)) {
+        for (int c = 0; c < tn->nchild; c++)
+            if (dual(tr, tn->first_child + c, s, theta, pt, ps)) return OR_ERR_MEM;
+    } else {
+        for (int c = 0; c < sn->nchild; c++)
+            if (dual(tr, t, sn->first_child + c, theta, pt, ps)) return OR_ERR_MEM;
+    }
+    return OR_OK;
+}
+
+int or_dual_lists(or_tree* tr, double theta, int64_t* counts)
+{
+    if (!tr || !(theta > 0.0) || !(theta < 1.0)) return OR_ERR_ARG;
+    for (int k = 0; k < 4; k++) {
+        free(tr->dual_t[k]);
+        free(tr->dual_s[k]);
+        tr->dual_t[k] = tr->dual_s[k] = NULL;
+        tr->dual_n[k] = 0;
+    }
+    tr->has_dual = 0;
+    ivec pt[4] = {{0}}, ps[4] = {{0}};
+    int rc = OR_OK;
+    for (int64_t a = 0; a < tr->nnodes && tr->nodes[a].level == 0 && rc == OR_OK; a++)
+        for (int64_t b = 0; b < tr->nnodes && tr->nodes[b].level == 0 && rc == OR_OK; b++)
+            rc = dual(tr, (int32_t)a, (int32_t)b, theta, pt, ps);
+    for (int k = 0; k < 4; k++) {
+        tr->dual_t[k] = pt[k].p;
+        tr->dual_s[k] = ps[k].p;
+        tr->dual_n[k] = pt[k].n;
+        if (counts) counts[k] = pt[k].n;
+    }
+    if (rc != OR_OK) return rc;
+    tr->dual_theta = theta;
+    tr->has_dual = 1;
+    return OR_OK;
+}
+
+int or_dual_export(const or_tree* tr, int kind, int32_t* tgt, int32_t* src)
+{
+    if (!tr || !tr->has_dual || kind < 0 || kind > 3) return OR_ERR_ARG;
+    if (tgt && tr->dual_n[kind]) memcpy(tgt, tr->dual_t[kind], sizeof(int32_t) * (size_t)tr->dual_n[kind]);
+    if (src && tr->dual_n[kind]) memcpy(src, tr->dual_s[kind], sizeof(int32_t) * (size_t)tr->dual_n[kind]);
     return OR_OK;
 }
 
@@ -1149,6 +1235,212 @@ int or_tree_potential(or_tree* tr, const double* zeta, const double* area, doubl
                       int literal, double* psi, int64_t* stats, int nthreads)
 {
     return tree_sum(tr, zeta, area, theta, d, literal, 1, psi, stats, nthreads);
+}
+
+/* Tree-code velocity by the dual traversal (Sec. 3.3, 3.4): PP and PC at the target leaves as
+ * in tree_sum; CP and CC accumulate the velocity U_T at the proxy points of each target
+ * cluster T (from the source particles, resp. the source proxies with their weights W); then
+ * the interpolating polynomial of U_T over T (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m)), the
+ * SBB basis in T's barycentric coordinates) is evaluated at every particle below T.  A
+ * particle's velocity sums its leaf's PP and PC pairs in traversal order, then the
+ * interpolants of its cluster ancestors from the root down (its own leaf last when that is a
+ * cluster at the depth limit).  stats[0..4]: PP (target, source) particle pairs with j != i,
+ * PC target x proxy, CP proxy x source, CC proxy x proxy, downward particle x M.            */
+static int64_t* group_by(const int32_t* key, int64_t n, int64_t nkeys, int64_t** order)
+{
+    int64_t* off = (int64_t*)calloc((size_t)nkeys + 1, sizeof(int64_t));
+    int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!off || !ord) {
+        free(off);
+        free(ord);
+        return NULL;
+    }
+    for (int64_t q = 0; q < n; q++) off[key[q] + 1]++;
+    for (int64_t k = 0; k < nkeys; k++) off[k + 1] += off[k];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nkeys > 0 ? nkeys : 1));
+    if (!fill) {
+        free(off);
+        free(ord);
+        return NULL;
+    }
+    memcpy(fill, off, sizeof(int64_t) * (size_t)nkeys);
+    for (int64_t q = 0; q < n; q++) ord[fill[key[q]]++] = q;  /* stable: traversal order kept */
+    free(fill);
+    *order = ord;
+    return off;
+}
+
+int or_tree_velocity_dual(or_tree* tr, const double* zeta, const double* area, double theta, int d,
+                          double* vel, int64_t* stats, int nthreads)
+{
+    if (!tr || d < 1 || d > 16 || !(theta > 0.0) || !(theta < 1.0) || !vel) return OR_ERR_ARG;
+    if (tr->n > 0 && (!zeta || !area)) return OR_ERR_ARG;
+    if (!tr->has_dual || tr->dual_theta != theta) {
+        int rc = or_dual_lists(tr, theta, NULL);
+        if (rc) return rc;
+    }
+    const int64_t n = tr->n, nn = tr->nnodes;
+    refdata r;
+    int rc = ref_make(d, &r);
+    if (rc != OR_OK) {
+        ref_free(&r);
+        return rc;
+    }
+    const int M = r.M;
+    size_t n1 = (size_t)(n > 0 ? n : 1);
+    v3* ys = (v3*)malloc(sizeof(v3) * n1);
+    double* ws = (double*)malloc(sizeof(double) * n1);
+    int32_t* slot = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nn > 0 ? nn : 1));
+    if (!ys || !ws || !slot) {
+        free(ys); free(ws); free(slot); ref_free(&r);
+        return OR_ERR_MEM;
+    }
+    for (int64_t k = 0; k < n; k++) {
+        int64_t i = tr->perm[k];
+        ys[k] = ld3(tr->pos, i);
+        ws[k] = zeta[i] * area[i];
+    }
+    int64_t nclu = 0;
+    for (int64_t id = 0; id < nn; id++) slot[id] = tr->nodes[id].count > tr->leaf_size ? (int32_t)nclu++ : -1;
+    size_t c1 = (size_t)(nclu > 0 ? nclu : 1) * M;
+    v3* yt = (v3*)malloc(sizeof(v3) * c1);
+    double* W = (double*)malloc(sizeof(double) * c1);
+    double* om = (double*)malloc(sizeof(double) * c1);
+    v3* U = (v3*)calloc(c1, sizeof(v3));
+    v3* cf = (v3*)calloc(c1, sizeof(v3));
+    char* has = (char*)calloc((size_t)(nclu > 0 ? nclu : 1), 1);
+    int64_t *offs[4] = {NULL, NULL, NULL, NULL}, *ords[4] = {NULL, NULL, NULL, NULL};
+    int err = !yt || !W || !om || !U || !cf || !has;
+    for (int k = 0; k < 4 && !err; k++)
+        if (!(offs[k] = group_by(tr->dual_t[k], tr->dual_n[k], nn, &ords[k]))) err = 1;
+    if (!err) {
+        for (int64_t id = 0; id < nn; id++) {
+            if (slot[id] < 0) continue;
+            const onode* nd = &tr->nodes[id];
+            cluster_weights(&r, nd->v, nd->count, ys + nd->start, ws + nd->start, yt + (size_t)slot[id] * M,
+                            W + (size_t)slot[id] * M, om + (size_t)slot[id] * M);
+        }
+    }
+    int64_t nst[5] = {0, 0, 0, 0, 0};
+    int nth = set_threads(nthreads);
+    (void)nth;
+    /* CP and CC: velocity at the proxy points of every target cluster */
+    if (!err) {
+        int64_t ncp = 0, ncc = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth) reduction(+ : ncp, ncc) reduction(| : err)
+        for (int64_t T = 0; T < nn; T++) {
+            if (slot[T] < 0) continue;
+            const int64_t b0 = offs[KCP][T], b1 = offs[KCP][T + 1], c0 = offs[KCC][T], c1e = offs[KCC][T + 1];
+            if (b0 == b1 && c0 == c1e) continue;
+            has[slot[T]] = 1;
+            const v3* xt = yt + (size_t)slot[T] * M;
+            v3* Ut = U + (size_t)slot[T] * M;
+            for (int m = 0; m < M; m++) {
+                v3 acc = mk(0.0, 0.0, 0.0);
+                for (int64_t q = b0; q < b1; q++) {
+                    const onode* sn = &tr->nodes[tr->dual_s[KCP][ords[KCP][q]]];
+                    for (int64_t j = sn->start; j < sn->start + sn->count; j++) bs_term(xt[m], ys[j], ws[j], &acc);
+                    ncp += sn->count;
+                }
+                for (int64_t q = c0; q < c1e; q++) {
+                    const int32_t sid = tr->dual_s[KCC][ords[KCC][q]];
+                    const v3* y = yt + (size_t)slot[sid] * M;
+                    const double* Wm = W + (size_t)slot[sid] * M;
+                    for (int mm = 0; mm < M; mm++) bs_term(xt[m], y[mm], Wm[mm], &acc);
+                    ncc += M;
+                }
+                Ut[m] = acc;
+            }
+            /* interpolating polynomial over T: V_T c = U_T, three right-hand sides */
+            double* V = (double*)malloc(sizeof(double) * (size_t)M * M);
+            double* rhs = (double*)malloc(sizeof(double) * (size_t)M * 3);
+            if (!V || !rhs) {
+                free(V);
+                free(rhs);
+                err = 1;
+                continue;
+            }
+            const onode* tn = &tr->nodes[T];
+            for (int m = 0; m < M; m++) {
+                double b[3];
+                sph_bary(xt[m], tn->v[0], tn->v[1], tn->v[2], b);
+                sbb(d, b[0], b[1], b[2], V + (size_t)m * M);
+                rhs[3 * m] = Ut[m].x;
+                rhs[3 * m + 1] = Ut[m].y;
+                rhs[3 * m + 2] = Ut[m].z;
+            }
+            if (solve(M, V, rhs, 3) != OR_OK) err = 1;
+            v3* ct = cf + (size_t)slot[T] * M;
+            for (int k = 0; k < M; k++) ct[k] = mk(rhs[3 * k], rhs[3 * k + 1], rhs[3 * k + 2]);
+            free(V);
+            free(rhs);
+        }
+        nst[2] = ncp;
+        nst[3] = ncc;
+    }
+    /* PP and PC at the target leaves, then the interpolants of the cluster ancestors */
+    if (!err) {
+        const double f = -1.0 / (4.0 * OR_PI);
+        int64_t npp = 0, npc = 0, ndn = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth) reduction(+ : npp, npc, ndn)
+        for (int64_t L = 0; L < tr->nleaves; L++) {
+            const int32_t lid = tr->leaves[L];
+            const onode* t = &tr->nodes[lid];
+            int32_t chain[64];
+            int nch = 0;
+            for (int32_t a = lid; a >= 0 && nch < 64; a = tr->nodes[a].parent)
+                if (slot[a] >= 0 && has[slot[a]]) chain[nch++] = a;
+            double B[153];
+            for (int64_t k = t->start; k < t->start + t->count; k++) {
+                v3 x = ys[k];
+                v3 acc = mk(0.0, 0.0, 0.0);
+                for (int64_t q = offs[KPP][lid]; q < offs[KPP][lid + 1]; q++) {
+                    const onode* sn = &tr->nodes[tr->dual_s[KPP][ords[KPP][q]]];
+                    for (int64_t j = sn->start; j < sn->start + sn->count; j++) {
+                        if (j == k) continue;
+                        bs_term(x, ys[j], ws[j], &acc);
+                        npp++;
+                    }
+                }
+                for (int64_t q = offs[KPC][lid]; q < offs[KPC][lid + 1]; q++) {
+                    const int32_t sid = tr->dual_s[KPC][ords[KPC][q]];
+                    const v3* y = yt + (size_t)slot[sid] * M;
+                    const double* Wm = W + (size_t)slot[sid] * M;
+                    for (int m = 0; m < M; m++) bs_term(x, y[m], Wm[m], &acc);
+                    npc += M;
+                }
+                for (int c = nch - 1; c >= 0; c--) {  /* root down */
+                    const onode* an = &tr->nodes[chain[c]];
+                    double b[3];
+                    sph_bary(x, an->v[0], an->v[1], an->v[2], b);
+                    sbb(d, b[0], b[1], b[2], B);
+                    const v3* ct = cf + (size_t)slot[chain[c]] * M;
+                    for (int kk = 0; kk < M; kk++) {
+                        acc.x += B[kk] * ct[kk].x;
+                        acc.y += B[kk] * ct[kk].y;
+                        acc.z += B[kk] * ct[kk].z;
+                    }
+                    ndn += M;
+                }
+                int64_t i = tr->perm[k];
+                vel[3 * i] = f * acc.x;
+                vel[3 * i + 1] = f * acc.y;
+                vel[3 * i + 2] = f * acc.z;
+            }
+        }
+        nst[0] = npp;
+        nst[1] = npc;
+        nst[4] = ndn;
+    }
+    if (stats)
+        for (int k = 0; k < 5; k++) stats[k] = nst[k];
+    for (int k = 0; k < 4; k++) {
+        free(offs[k]);
+        free(ords[k]);
+    }
+    free(ys); free(ws); free(slot); free(yt); free(W); free(om); free(U); free(cf); free(has);
+    ref_free(&r);
+    return err ? OR_ERR_MEM : OR_OK;
 }
 
 /* Proxy points and weights of every node with more than N_T particles (the clusters), in

@@ -543,3 +543,65 @@ def test_forced_rk4_reduces_to_unforced_after_tf_and_keeps_absolute_vorticity():
     # the forcing enters only the Biot-Savart source: zeta + 2 Omega z is still carried
     # exactly by the unprojected scheme
     assert np.max(np.abs((z2 + 2 * Om * x2[:, 2]) - (zeta + 2 * Om * pos[:, 2]))) <= 1e-13
+
+
+# ------------------------------------------------------------- dual traversal (Sec. 3.4)
+@pytest.mark.parametrize("theta,leaf", [(0.5, 16), (0.7, 8), (0.9, 32)])
+def test_dual_pairs_cover_every_source_once_and_obey_the_mac(theta, leaf):
+    # every target particle sees every source particle exactly once: through the PP and PC
+    # pairs of its leaf and the CP and CC pairs of the clusters above it (Sec. 3.3, 3.4)
+    pos = np.vstack([W.uniform_points(2500, 40), _clustered_pins(500, 41)])
+    n = len(pos)
+    tr = O.Tree(pos, leaf)
+    ex = tr.export()
+    L = tr.dual_lists(theta)
+    g, cnt, st, par = ex["geom"], ex["count"], ex["start"], ex["parent"]
+    by_target = {}
+    for kind, (t, s) in L.items():
+        for a, b in zip(t, s):
+            by_target.setdefault(int(a), []).append((kind, int(b)))
+            if kind != "PP":  # the MAC holds for every approximated pair
+                R = np.linalg.norm(g[a, 9:12] - g[b, 9:12])
+                assert (g[a, 12] + g[b, 12]) / R < theta
+            small_t, small_s = cnt[a] <= leaf, cnt[b] <= leaf
+            assert (kind in ("PP", "PC")) == small_t and (kind in ("PP", "CP")) == small_s or \
+                (kind == "PP" and ex["leaf"][a] and ex["leaf"][b])
+    for lid in ex["leaves"]:
+        seen = np.zeros(n, np.int64)
+        a = int(lid)
+        while a >= 0:
+            for kind, b in by_target.get(a, []):
+                if (a == lid) == (kind in ("PP", "PC")) or (a == lid and cnt[a] > leaf):
+                    seen[st[b]:st[b] + cnt[b]] += 1
+            a = int(par[a])
+        assert np.all(seen == 1), int(lid)
+
+
+def _clustered_pins(n, seed):
+    rng = np.random.default_rng(seed)
+    c = np.array([0.2, 0.4, -0.9])
+    c /= np.linalg.norm(c)
+    p = c + 0.02 * rng.standard_normal((n, 3))
+    return p / np.linalg.norm(p, axis=1, keepdims=True)
+
+
+def test_dual_tiny_theta_is_direct_and_error_falls_with_degree():
+    pos = W.uniform_points(1500, seed=12)
+    rng = np.random.default_rng(13)
+    zeta, area = rng.standard_normal(1500), W.equal_areas(1500)
+    ud = O.direct(pos, zeta, area)
+    ut, st = O.Tree(pos, leaf_size=16).velocity_dual(zeta, area, theta=1e-6, degree=4, return_stats=True)
+    assert st["pc"] == st["cp"] == st["cc"] == st["down"] == 0 and st["pp"] == 1500 * 1499
+    assert np.max(np.abs(ut - ud)) <= 1e-13 * np.max(np.abs(ud))
+    pos = W.icosahedral_points(5)
+    area = W.equal_areas(len(pos))
+    zeta = W.sh_series_vorticity(pos, 16, seed=0)
+    ud = O.direct(pos, zeta, area)
+    tr = O.Tree(pos, leaf_size=64)
+    errs = {d: O.rel_l2(tr.velocity_dual(zeta, area, 0.7, d), ud, area) for d in (2, 4, 6, 8, 10)}
+    ds = sorted(errs)
+    assert all(errs[a] > errs[b] for a, b in zip(ds, ds[1:])), errs
+    with open(os.path.join(GOLDEN, "paper_values.json")) as f:
+        band = json.load(f)["tree_accuracy_theta0.7_d6"]
+    # Sec. 4.1's "between 3 and 4 digits" at theta 0.7, d 6 is printed for this (dual) method
+    assert band["E_min"] / 10 <= errs[6] <= band["E_max"], errs
