@@ -184,6 +184,25 @@ int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts
 int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
                   double* psi, void* stream);
 
+/* Tree-code velocity by the dual tree traversal of Sec. 3.4 with all four interactions of
+ * Sec. 3.3, for the tree last built in ctx: zeta[n], area[n] in, vel[n,3] out in the caller's
+ * order.  From every pair of roots of an instance, a pair of triangles (T_t, T_s) that passes
+ * the MAC interacts by its particle counts against N_T = leaf_size: PP (both at most N_T, the
+ * particle sum), PC (only the source above: the target particles against the source's proxy
+ * points and weights), CP (only the target above: the source particles summed at the target's
+ * proxy points), CC (both above: proxy points against proxy points).  A pair that fails the
+ * MAC is PP when both are leaves; otherwise the triangle holding more particles (the target
+ * on a tie; a leaf never) is replaced by its children.  CP and CC give the velocity at the
+ * target cluster's proxy points; the polynomial of degree d interpolating it over the cluster
+ * (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m))) is evaluated at every particle below it and
+ * added.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau (mixed precision: the
+ * pair sums in FP32 as in sts_velocity, the interpolation in FP64).  Runs eagerly; builds the
+ * pair lists when theta or the tree changed (synchronises `stream`), which replaces the lists
+ * of sts_velocity (the next sts_velocity rebuilds them).  STS_ERR_STATE without a tree or
+ * while a graph is being recorded. */
+int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
+                      double* vel, void* stream);
+
 /* One classical RK4 step (Sec. 4) of the Sec. 2 system dx_i/dt = u_i,
  * dzeta_i/dt = -2 Omega u_z,i, in place on pos[n,3] and zeta[n]; area[n] is constant.
  * Every stage evaluates the tree-code velocity (parameters p, tree rebuilt) at the stage
@@ -250,6 +269,16 @@ int sts_lists_export(sts_ctx* ctx, int64_t* far_off, int32_t* far_idx, int64_t* 
 /* Clusters of the last sts_velocity in node order: node_ids[C], proxy points yt[C,M,3] and
  * proxy weights W[C,M] (FP64 values as the evaluation uses them).  Any pointer may be NULL. */
 int sts_clusters_export(sts_ctx* ctx, int32_t* node_ids, double* yt, double* W, void* stream);
+/* Pairs of the last dual traversal (sts_velocity_dual) of one kind: 0 PP, 1 PC, 2 CP, 3 CC.
+ * *npairs (HOST) receives the count; tgt[npairs] and src[npairs] (HOST, may be NULL) the
+ * target and source node ids, sorted by target (depth-first leaf order for PP and PC, cluster
+ * order for CP and CC), then source node id.  STS_ERR_STATE without dual lists. */
+int sts_dual_export(sts_ctx* ctx, int32_t kind, int64_t* npairs, int32_t* tgt, int32_t* src,
+                    void* stream);
+/* Interaction counts of the dual lists at degree d (M = (d+1)(d+2)/2): stats[0] PP particle
+ * pairs (j != i), stats[1] PC target x proxy, stats[2] CP proxy x source, stats[3] CC
+ * proxy x proxy, stats[4] downward particle x M (clusters that are CP or CC targets). */
+int sts_dual_stats(sts_ctx* ctx, int32_t degree, int64_t* stats, void* stream);
 /* Proxy reference data of degree d, computed on the host: beta[M,3] (barycentric proxy
  * points on the reference simplex, in selection order) and vinv[M,M] (inverse of
  * V_ref[m][k] = B_k(beta_m), row k, column m).  Either pointer may be NULL.  Needs no GPU. */

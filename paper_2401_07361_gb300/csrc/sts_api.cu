@@ -226,6 +226,35 @@ int potential_impl(sts_ctx* c, const double* zeta, const double* area, const sts
     return STS_OK;
 }
 
+// Dual-traversal velocity on the current tree: sources, the four pair lists (rebuilt when theta
+// or the tree changed, or after the target-leaf lists replaced them), proxy weights and the
+// evaluation with the downward interpolation.
+int velocity_dual_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p, double* vel,
+                       cudaStream_t s)
+{
+    const int64_t n = c->n;
+    if (n == 0) return STS_OK;
+    if (n == 1) {
+        STS_CUDA(cudaMemsetAsync(vel, 0, 3 * sizeof(double), s));
+        return STS_OK;
+    }
+    int rc;
+    phase_begin(c, kPhPrep, s);
+    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
+    phase_end(c, kPhPrep, s);
+    if (!c->have_dual || c->dual_theta != p->theta) {
+        phase_begin(c, kPhLists, s);
+        if ((rc = build_dual(c, p->theta, s))) return rc;
+        phase_end(c, kPhLists, s);
+    }
+    phase_begin(c, kPhUpward, s);
+    if ((rc = upward_pass(c, p->degree, p->precision, s))) return rc;
+    phase_end(c, kPhUpward, s);
+    if ((rc = evaluate_dual(c, p->degree, p->precision, p->near_fp64_tau, vel, s))) return rc;
+    c->list_degree = p->degree;
+    return STS_OK;
+}
+
 int build_impl(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off, int ninst, const sts_params* p,
                cudaStream_t s)
 {
@@ -392,7 +421,7 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
                                  (int64_t)(uintptr_t)s};
     if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
     int rc;
-    if (c->rk_exec && key == c->rk_key && okey == c->rk_off_key) {
+    if (c->rk_exec && key == c->rk_key && okey == c->rk_off_key && c->rk_epoch == g_alloc_epoch.load()) {
         STS_CUDA(cudaGraphLaunch(c->rk_exec, s));
         g_launches.fetch_add(c->rk_kernels, std::memory_order_relaxed);
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p + kDcOver, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -413,6 +442,7 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
         }
         c->have_tree = true;
         c->have_lists = true;
+        c->have_dual = false;
         c->nnodes = -1;  // host counts refreshed on demand
         if (over == 0) return STS_OK;
         // undo the step and redo it eagerly below
@@ -426,6 +456,7 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
     if ((rc = reserve_for_capture(c, p, ninst, s))) return rc;
     STS_CUDA(cudaStreamSynchronize(s));
     c->have_tree = c->have_lists = false;  // buffers may have moved; the replay rebuilds them
+    c->have_dual = false;
     if (c->rk_exec) {
         cudaGraphExecDestroy(c->rk_exec);
         c->rk_exec = nullptr;
@@ -462,6 +493,7 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
     if (rc == STS_OK) {
         c->rk_key = key;
         c->rk_off_key = okey;
+        c->rk_epoch = g_alloc_epoch.load();
     }
     return rc;
 }
@@ -478,7 +510,7 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
                                  (int64_t)(uintptr_t)vel, (int64_t)(uintptr_t)s};
     if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
     int rc;
-    if (c->ev_exec && key == c->ev_key && okey == c->ev_off_key) {
+    if (c->ev_exec && key == c->ev_key && okey == c->ev_off_key && c->ev_epoch == g_alloc_epoch.load()) {
         STS_CUDA(cudaGraphLaunch(c->ev_exec, s));
         g_launches.fetch_add(c->ev_kernels, std::memory_order_relaxed);
         STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dc.p + kDcOver, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -498,6 +530,7 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
             return STS_ERR_TIMEOUT;
         }
         c->have_tree = c->have_lists = true;
+        c->have_dual = false;
         c->nnodes = -1;
         if (over == 0) return STS_OK;
         STS_CUDA(cudaGraphExecDestroy(c->ev_exec));
@@ -520,6 +553,7 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
         set_error("sts_tree_velocity: cannot record on this stream (%s); use a non-default stream",
                   cudaGetErrorString(e));
         c->have_tree = c->have_lists = false;
+        c->have_dual = false;
         return STS_ERR_CUDA;
     }
     for (int ph = 0; ph < kNumPhases; ph++) c->phase_in_graph[ph] = false;
@@ -544,9 +578,11 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
     }
     if (g) cudaGraphDestroy(g);
     c->have_tree = c->have_lists = false;  // the recording reused the buffers; the next call replays
+    c->have_dual = false;
     if (rc == STS_OK) {
         c->ev_key = key;
         c->ev_off_key = okey;
+        c->ev_epoch = g_alloc_epoch.load();
     }
     return rc;
 }
@@ -747,6 +783,62 @@ int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts
         return STS_ERR_ARG;
     }
     return velocity_impl(ctx, zeta, area, p, vel, S(stream));
+}
+
+int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p, double* vel,
+                      void* stream)
+{
+    int rc = check_ctx(ctx, "sts_velocity_dual");
+    if (rc || (rc = check_params(p, "sts_velocity_dual"))) return rc;
+    if (!ctx->have_tree) {
+        set_error("sts_velocity_dual: no tree (call sts_tree_build first)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->capturing) {
+        set_error("sts_velocity_dual: not available while recording");
+        return STS_ERR_STATE;
+    }
+    if (ctx->n > 0 && (!zeta || !area || !vel)) {
+        set_error("sts_velocity_dual: NULL array");
+        return STS_ERR_ARG;
+    }
+    return velocity_dual_impl(ctx, zeta, area, p, vel, S(stream));
+}
+
+int sts_dual_export(sts_ctx* ctx, int32_t kind, int64_t* npairs, int32_t* tgt, int32_t* src, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_dual_export");
+    if (rc) return rc;
+    if (kind < 0 || kind > 3) {
+        set_error("sts_dual_export: kind must be 0 (PP), 1 (PC), 2 (CP) or 3 (CC), got %d", kind);
+        return STS_ERR_ARG;
+    }
+    if (!ctx->have_dual) {
+        set_error("sts_dual_export: no dual lists (call sts_velocity_dual first)");
+        return STS_ERR_STATE;
+    }
+    const int64_t P = ctx->dual_n[kind];
+    if (npairs) *npairs = P;
+    cudaStream_t s = S(stream);
+    if (tgt && P) STS_CUDA(cudaMemcpyAsync(tgt, ctx->dual_t[kind].p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (src && P) STS_CUDA(cudaMemcpyAsync(src, ctx->dual_s[kind].p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    return STS_OK;
+}
+
+int sts_dual_stats(sts_ctx* ctx, int32_t degree, int64_t* stats, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_dual_stats");
+    if (rc) return rc;
+    if (!stats || degree < 1 || degree > kMaxDegree) {
+        set_error("sts_dual_stats: stats must be non-NULL and 1 <= degree <= %d", kMaxDegree);
+        return STS_ERR_ARG;
+    }
+    if (!ctx->have_dual) {
+        set_error("sts_dual_stats: no dual lists (call sts_velocity_dual first)");
+        return STS_ERR_STATE;
+    }
+    return dual_stats(ctx, degree, stats, S(stream));
 }
 
 int sts_tree_build_batched(sts_ctx* ctx, const double* pos, const int64_t* offsets, int32_t ninst,

@@ -140,11 +140,11 @@ __global__ void k_wait_selftest(int spins, int* __restrict__ status)
 
 // FP64 evaluation of one near pair whose FP32 squared distance fell below 2 tau; the sum
 // goes to corr (sorted order), read back by the owning lane in the epilogue.
-__device__ __forceinline__ void close_pair(const double4* __restrict__ src64, int64_t j, int64_t tk,
-                                           double* __restrict__ corr)
+__device__ __forceinline__ void close_pair(const double4* __restrict__ src64, const double4* __restrict__ tgt64,
+                                           int64_t j, int64_t tk, double* __restrict__ corr)
 {
     const double4 y = src64[j];
-    const double4 x = src64[tk];
+    const double4 x = tgt64[tk];
     const double dx = y.x - x.x, dy = y.y - x.y, dz = y.z - x.z;
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     if (r2 > 0.0) {
@@ -202,12 +202,12 @@ template <int S>
 __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int ph, float ax, float ay, float az,
                                                   float bx, float by, float bz, float tau2, int64_t base,
                                                   int64_t tk0, int64_t tk1, const double4* __restrict__ src64,
-                                                  double* __restrict__ corr)
+                                                  const double4* __restrict__ tgt64, double* __restrict__ corr)
 {
     for (int i = ph; i < cnt; i += S) {
         const float4 s = sb[i];
-        if (sqdist(s, ax, ay, az) < tau2) close_pair(src64, base + i, tk0, corr);
-        if (sqdist(s, bx, by, bz) < tau2) close_pair(src64, base + i, tk1, corr);
+        if (sqdist(s, ax, ay, az) < tau2) close_pair(src64, tgt64, base + i, tk0, corr);
+        if (sqdist(s, bx, by, bz) < tau2) close_pair(src64, tgt64, base + i, tk1, corr);
     }
 }
 
@@ -340,6 +340,7 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
                                                 const NearEntry* __restrict__ near_ent,
                                                 const float4* __restrict__ prx32, int M,
                                                 const float4* __restrict__ src32, const double4* __restrict__ src64,
+                                                const float4* __restrict__ tgt32, const double4* __restrict__ tgt64,
                                                 const int32_t* __restrict__ perm, float tau2, float tau_r,
                                                 double* __restrict__ corr, double* __restrict__ vel)
 {
@@ -348,9 +349,9 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
     const int ph = lane < p * S ? lane / p : (1 << 20);
     const int64_t tk0 = tk.t0 + 2 * j, tk1 = tk0 + 1;
     const bool v0 = 2 * j < tk.nt, v1 = 2 * j + 1 < tk.nt;
-    float4 q = src32[v0 ? tk0 : tk.t0];
+    float4 q = tgt32[v0 ? tk0 : tk.t0];
     const float t0x = v0 ? q.x : -1e3f, t0y = v0 ? q.y : -1e3f, t0z = v0 ? q.z : -1e3f;
-    q = src32[v1 ? tk1 : tk.t0];
+    q = tgt32[v1 ? tk1 : tk.t0];
     const float t1x = v1 ? q.x : -1e3f, t1y = v1 ? q.y : -1e3f, t1z = v1 ? q.z : -1e3f;
     float h0x = 0.f, h0y = 0.f, h0z = 0.f, l0x = 0.f, l0y = 0.f, l0z = 0.f;
     float h1x = 0.f, h1y = 0.f, h1z = 0.f, l1x = 0.f, l1y = 0.f, l1z = 0.f;
@@ -390,7 +391,9 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
             bool hit = false;
             if (in.z == 2) {
                 block_pairs<true, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
-                if (hit) block_close_pairs<S>(sb, in.y, ph, ax, ay, az, bx, by, bz, tau2, in.x, tk0, tk1, src64, corr);
+                if (hit)
+                    block_close_pairs<S>(sb, in.y, ph, ax, ay, az, bx, by, bz, tau2, in.x, tk0, tk1, src64, tgt64,
+                                         corr);
             } else {
                 block_pairs<false, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
             }
@@ -428,8 +431,8 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
                 Sy += __ldcg(corr + 3 * t + 1);
                 Sz += __ldcg(corr + 3 * t + 2);
             }
-            const double4 x = src64[t];
-            const int64_t i = perm[t];
+            const double4 x = tgt64[t];
+            const int64_t i = perm ? perm[t] : t;
             vel[3 * i] = -kInv4Pi * (x.y * Sz - x.z * Sy);
             vel[3 * i + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
             vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
@@ -443,6 +446,7 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
              const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
              const NearEntry* __restrict__ near_ent, const float4* __restrict__ prx32, int M,
              const float4* __restrict__ src32, const double4* __restrict__ src64,
+             const float4* __restrict__ tgt32, const double4* __restrict__ tgt64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
              double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
              unsigned long long* __restrict__ queue, int* __restrict__ status)
@@ -467,35 +471,35 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
         switch (tk.S) {
             case 1:
                 ok = eval_task_mixed<1>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 2:
                 ok = eval_task_mixed<2>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 3:
                 ok = eval_task_mixed<3>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 4:
                 ok = eval_task_mixed<4>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 5:
                 ok = eval_task_mixed<5>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 6:
                 ok = eval_task_mixed<6>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             case 7:
                 ok = eval_task_mixed<7>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
             default:
                 ok = eval_task_mixed<8>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
                 break;
         }
         if (!ok) break;
@@ -511,15 +515,15 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
                                                const int64_t* __restrict__ near_coff,
                                                const NearEntry* __restrict__ near_ent,
                                                const double4* __restrict__ prx64, int M,
-                                               const double4* __restrict__ src64, const int32_t* __restrict__ perm,
-                                               double* __restrict__ vel)
+                                               const double4* __restrict__ src64, const double4* __restrict__ tgt64,
+                                               const int32_t* __restrict__ perm, double* __restrict__ vel)
 {
     const int p = (tk.nt + 1) >> 1, S = tk.S;
     const int j = lane % p;
     const int ph = lane < p * S ? lane / p : (1 << 20);
     const int64_t tk0 = tk.t0 + 2 * j, tk1 = tk0 + 1;
     const bool v0 = 2 * j < tk.nt, v1 = 2 * j + 1 < tk.nt;
-    const double4 x0 = src64[v0 ? tk0 : tk.t0], x1 = src64[v1 ? tk1 : tk.t0];
+    const double4 x0 = tgt64[v0 ? tk0 : tk.t0], x1 = tgt64[v1 ? tk1 : tk.t0];
     const double ax = v0 ? x0.x : -1e3, ay = v0 ? x0.y : -1e3, az = v0 ? x0.z : -1e3;
     const double bx = v1 ? x1.x : -1e3, by = v1 ? x1.y : -1e3, bz = v1 ? x1.z : -1e3;
     double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -566,13 +570,13 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
         if (lane < p && v1) vel[perm[tk1]] = -0.5 * kInv4Pi * a[3];
     } else if (lane < p) {
         if (v0) {
-            const int64_t i = perm[tk0];
+            const int64_t i = perm ? perm[tk0] : tk0;
             vel[3 * i] = -kInv4Pi * (x0.y * a[2] - x0.z * a[1]);
             vel[3 * i + 1] = -kInv4Pi * (x0.z * a[0] - x0.x * a[2]);
             vel[3 * i + 2] = -kInv4Pi * (x0.x * a[1] - x0.y * a[0]);
         }
         if (v1) {
-            const int64_t i = perm[tk1];
+            const int64_t i = perm ? perm[tk1] : tk1;
             vel[3 * i] = -kInv4Pi * (x1.y * a[5] - x1.z * a[4]);
             vel[3 * i + 1] = -kInv4Pi * (x1.z * a[3] - x1.x * a[5]);
             vel[3 * i + 2] = -kInv4Pi * (x1.x * a[4] - x1.y * a[3]);
@@ -596,15 +600,16 @@ __global__ void __launch_bounds__(kEvalWarps64 * 32)
 k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
             const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
             const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
-            const double4* __restrict__ src64, const int32_t* __restrict__ perm, double* __restrict__ vel,
-            const int64_t* __restrict__ ntasks_d, int64_t cap, unsigned long long* __restrict__ queue)
+            const double4* __restrict__ src64, const double4* __restrict__ tgt64, const int32_t* __restrict__ perm,
+            double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
+            unsigned long long* __restrict__ queue)
 {
     __shared__ double4 sbuf[kEvalWarps64][kStage];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);
     for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane))
-        eval_task_fp64<POT>(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, perm,
-                            vel);
+        eval_task_fp64<POT>(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, tgt64,
+                            perm, vel);
 }
 
 // ------------------------------------------------------------------------ counts
@@ -813,40 +818,64 @@ int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
     const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
     phase_begin(c, kPhEval, s);
     (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
-                                                       c->near_ent.p, c->prx64.p, M, c->src64.p, c->perm.p, psi,
-                                                       c->dc.p + kDcTasks, ntasks, queue), note_launch());
+                                                       c->near_ent.p, c->prx64.p, M, c->src64.p, c->src64.p,
+                                                       c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue),
+     note_launch());
     phase_end(c, kPhEval, s);
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
 
-int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
+namespace {
+
+// One list set for the evaluation kernels: the leaf lists (targets: the sorted particles,
+// results to vel in the caller's order) or the cluster lists of the dual traversal (targets:
+// the proxy points of the target clusters, results in proxy order).
+struct ListSet {
+    const Task* tasks;
+    const int64_t* ntasks_d;
+    int64_t ntasks;
+    const int64_t *far_off, *near_coff;
+    const FarEntry* far_ent;
+    const NearEntry* near_ent;
+    const float4* tgt32;
+    const double4* tgt64;
+    const int32_t* perm;  // target slot -> output row, or nullptr for the identity
+    int64_t ntargets;     // rows of corr
+};
+
+int eval_blocks(sts_ctx* c)
+{
+    if (c->eval_blocks_mixed > 0) return STS_OK;
+    // persistent grids: as many blocks as stay resident on all SMs at once
+    int b32 = 0, b64 = 0;
+    STS_CUDA(cudaFuncSetAttribute(k_eval_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(kEvalWarps * sizeof(EvalSmem))));
+    STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32,
+                                                           kEvalWarps * sizeof(EvalSmem)));
+    STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<false>, kEvalWarps64 * 32, 0));
+    c->eval_blocks_mixed = std::max(1, c->num_sms * b32);
+    c->eval_blocks_fp64 = std::max(1, c->num_sms * b64);
+    return STS_OK;
+}
+
+// corr: FP64 close-pair scratch of at least 3 * ls.ntargets doubles (mixed precision).
+int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, double tau, DevBuf<double>& corrbuf,
+                   double* vel, cudaStream_t s)
 {
     const int M = nbasis(degree);
-    const int64_t ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
-    if (ntasks <= 0) return STS_OK;
-    const int64_t* nt_d = c->dc.p + kDcTasks;
+    if (ls.ntasks <= 0) return STS_OK;
     unsigned long long* queue = (unsigned long long*)(c->dc.p + kDcQueue);
-    if (c->eval_blocks_mixed <= 0) {
-        // persistent grids: as many blocks as stay resident on all SMs at once
-        int dev = 0, sms = 0, b32 = 0, b64 = 0;
-        STS_CUDA(cudaGetDevice(&dev));
-        STS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        STS_CUDA(cudaFuncSetAttribute(k_eval_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kEvalWarps * sizeof(EvalSmem))));
-        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32,
-                                                               kEvalWarps * sizeof(EvalSmem)));
-        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<false>, kEvalWarps64 * 32, 0));
-        c->eval_blocks_mixed = std::max(1, sms * b32);
-        c->eval_blocks_fp64 = std::max(1, sms * b64);
-    }
+    int rc = eval_blocks(c);
+    if (rc) return rc;
     STS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     if (precision == STS_FP64) {
-        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ls.ntasks, kEvalWarps64), c->eval_blocks_fp64);
         phase_begin(c, kPhEval, s);
-        (k_eval_fp64<false><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
-                                                     c->near_ent.p, c->prx64.p, M, c->src64.p, c->perm.p, vel,
-                                                     nt_d, ntasks, queue), note_launch());
+        (k_eval_fp64<false><<<g, kEvalWarps64 * 32, 0, s>>>(ls.tasks, ls.far_off, ls.far_ent, ls.near_coff,
+                                                            ls.near_ent, c->prx64.p, M, c->src64.p, ls.tgt64,
+                                                            ls.perm, vel, ls.ntasks_d, ls.ntasks, queue),
+         note_launch());
         phase_end(c, kPhEval, s);
     } else {
         double* corr = nullptr;
@@ -854,21 +883,194 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
         // the dummy targets of idle lanes (at distance ~1e3) out of the FP64 path
         tau = std::min(tau, 2.0);
         if (tau > 0.0) {
-            if (!c->capturing) STS_CUDA(c->corr.reserve(3 * c->n + 3));
-            STS_CUDA(cudaMemsetAsync(c->corr.p, 0, 3 * c->n * sizeof(double), s));
-            corr = c->corr.p;
+            if (!c->capturing) STS_CUDA(corrbuf.reserve(3 * ls.ntargets + 3));
+            STS_CUDA(cudaMemsetAsync(corrbuf.p, 0, 3 * ls.ntargets * sizeof(double), s));
+            corr = corrbuf.p;
         }
         // FP32 threshold on |d|^2 and the distance bound below which a near block is tested
         const float tau2 = corr ? (float)(2.0 * tau) : 0.f;
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
-        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps), c->eval_blocks_mixed);
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ls.ntasks, kEvalWarps), c->eval_blocks_mixed);
         phase_begin(c, kPhEval, s);
-        (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
-                                                    c->near_ent.p, c->prx32.p, M, c->src32.p, c->src64.p, c->perm.p,
-                                                    tau2, tau_r, corr, vel, nt_d, ntasks, queue, c->d_status),
+        (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
+             ls.tasks, ls.far_off, ls.far_ent, ls.near_coff, ls.near_ent, c->prx32.p, M, c->src32.p, c->src64.p,
+             ls.tgt32, ls.tgt64, ls.perm, tau2, tau_r, corr, vel, ls.ntasks_d, ls.ntasks, queue, c->d_status),
          note_launch());
         phase_end(c, kPhEval, s);
     }
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+}  // namespace
+
+int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
+{
+    ListSet ls;
+    ls.tasks = c->tasks.p;
+    ls.ntasks_d = c->dc.p + kDcTasks;
+    ls.ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
+    ls.far_off = c->far_off.p;
+    ls.near_coff = c->near_coff.p;
+    ls.far_ent = c->far_ent.p;
+    ls.near_ent = c->near_ent.p;
+    ls.tgt32 = c->src32.p;
+    ls.tgt64 = c->src64.p;
+    ls.perm = c->perm.p;
+    ls.ntargets = c->n;
+    return evaluate_lists(c, ls, degree, precision, tau, c->corr, vel, s);
+}
+
+// ------------------------------------------------------------------------ dual: downward
+namespace {
+
+// Coefficients of the interpolating polynomial of every target cluster (Sec. 3.2 applied to
+// the velocity): with proxy points x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|,
+// the spherical barycentric coordinates of x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref
+// (the basis is homogeneous of degree d) and V_T c = U gives c = V_ref^-1 diag(rho^d) U.
+// U: the velocity at the proxy points (cvel).  One CTA per cluster, a fixed grid striding.
+__global__ void k_down_coef(int64_t nclu, const uint8_t* __restrict__ has, const int32_t* __restrict__ cnode,
+                            const double* __restrict__ geom, const double* __restrict__ beta,
+                            const double* __restrict__ vinv, int d, int M, const double* __restrict__ cvel,
+                            double* __restrict__ coef)
+{
+    __shared__ double u[3 * kMaxM];
+    for (int64_t c = blockIdx.x; c < nclu; c += gridDim.x) {
+        if (!has[c]) continue;
+        const double* g = geom + 13 * (int64_t)cnode[c];
+        __syncthreads();  // u of the previous cluster is no longer read
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
+            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
+            double rd = 1.0;
+            for (int e = 0; e < d; e++) rd *= rho;
+            const double* v = cvel + 3 * (c * M + m);
+            u[3 * m] = rd * v[0];
+            u[3 * m + 1] = rd * v[1];
+            u[3 * m + 2] = rd * v[2];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            for (int m = 0; m < M; m++) {
+                const double w = vinv[k * M + m];
+                ax += w * u[3 * m];
+                ay += w * u[3 * m + 1];
+                az += w * u[3 * m + 2];
+            }
+            double* o = coef + 3 * (c * M + k);
+            o[0] = ax;
+            o[1] = ay;
+            o[2] = az;
+        }
+    }
+}
+
+// Plain FP64 products and sums in a fixed order (no contraction): the barycentric coordinates
+// below come out exactly as a plain IEEE evaluation of the same formula.
+__device__ __forceinline__ double dot3_rn(double ax, double ay, double az, double bx, double by, double bz)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by)), __dmul_rn(az, bz));
+}
+__device__ __forceinline__ void cross3_rn(const double* a, const double* b, double* c)
+{
+    c[0] = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
+    c[1] = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
+    c[2] = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
+}
+
+// Adds to every particle the interpolants of its cluster ancestors that are CP / CC targets
+// (its own leaf included when that is a cluster): b = the particle's spherical barycentric
+// coordinates in the ancestor (Sec. 3.2, y = b1 v1 + b2 v2 + b3 v3 by Cramer's rule:
+// b_i = (y . n_i) / D, n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1), B_k(b) =
+// b1^a b2^b b3^c in the order a = d..0, b = d - a..0, sum_k B_k(b) c_k.  One thread per
+// particle (sorted slot).
+__global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
+                           const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
+                           const uint8_t* __restrict__ has, const double* __restrict__ geom,
+                           const double4* __restrict__ src64, const int32_t* __restrict__ perm, int d, int M,
+                           const double* __restrict__ coef, double* __restrict__ vel)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double4 x = src64[j];
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    double p1[kMaxDegree + 1], p2[kMaxDegree + 1], p3[kMaxDegree + 1];
+    for (int32_t a = leaves[slot_leaf[j]]; a >= 0; a = parent[a]) {
+        const int32_t cs = cluster_slot[a];
+        if (cs < 0 || !has[cs]) continue;
+        const double* g = geom + 13 * (int64_t)a;
+        double n1[3], n2[3], n3[3];
+        cross3_rn(g + 3, g + 6, n1);
+        cross3_rn(g + 6, g, n2);
+        cross3_rn(g, g + 3, n3);
+        const double D = dot3_rn(g[0], g[1], g[2], n1[0], n1[1], n1[2]);
+        const double b1 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n1[0], n1[1], n1[2]), D);
+        const double b2 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n2[0], n2[1], n2[2]), D);
+        const double b3 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n3[0], n3[1], n3[2]), D);
+        p1[0] = p2[0] = p3[0] = 1.0;
+        for (int e = 1; e <= d; e++) {
+            p1[e] = p1[e - 1] * b1;
+            p2[e] = p2[e - 1] * b2;
+            p3[e] = p3[e - 1] * b3;
+        }
+        const double* cf = coef + 3 * ((int64_t)cs * M);
+        int k = 0;
+        for (int ea = d; ea >= 0; ea--)
+            for (int eb = d - ea; eb >= 0; eb--, k++) {
+                const double B = (p1[ea] * p2[eb]) * p3[d - ea - eb];
+                ax += B * cf[3 * k];
+                ay += B * cf[3 * k + 1];
+                az += B * cf[3 * k + 2];
+            }
+    }
+    const int64_t i = perm[j];
+    vel[3 * i] += ax;
+    vel[3 * i + 1] += ay;
+    vel[3 * i + 2] += az;
+}
+
+}  // namespace
+
+int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
+{
+    // PP and PC: the leaf lists hold the dual traversal's pairs of the target leaves
+    int rc = evaluate(c, degree, precision, tau, vel, s);
+    if (rc) return rc;
+    const int64_t C = c->nclusters;
+    if (C == 0 || (c->dual_n[2] == 0 && c->dual_n[3] == 0)) return STS_OK;
+    RefTable* ref = get_ref(c, degree);
+    if (!ref) return STS_ERR_CUDA;
+    const int M = ref->M;
+    if ((rc = cluster_tasks(c, M, s))) return rc;
+    STS_CUDA(c->cvel.reserve(3 * C * M + 3));
+    STS_CUDA(c->cdown.reserve(3 * C * M + 3));
+    // CP and CC: the velocity at the proxy points of the target clusters
+    ListSet ls;
+    ls.tasks = c->ctasks.p;
+    ls.ntasks_d = c->dual_cnt.p + 5;
+    ls.ntasks = c->nctasks;
+    ls.far_off = c->cfar_off.p;
+    ls.near_coff = c->cnear_coff.p;
+    ls.far_ent = c->cfar_ent.p;
+    ls.near_ent = c->cnear_ent.p;
+    ls.tgt32 = c->prx32.p;
+    ls.tgt64 = c->prx64.p;
+    ls.perm = nullptr;
+    ls.ntargets = C * M;
+    if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s))) return rc;
+    // interpolation down to the particles
+    (k_down_coef<<<(unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms), 64, 0, s>>>(
+         C, c->chas.p, c->cluster_node.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M, c->cvel.p,
+         c->cdown.p),
+     note_launch());
+    (k_downward<<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
+                                                   c->cluster_slot.p, c->chas.p, c->nd_geom.p, c->src64.p, c->perm.p,
+                                                   degree, M, c->cdown.p, vel),
+     note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }

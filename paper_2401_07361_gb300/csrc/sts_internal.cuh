@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <vector>
 
 #include "../../include/sts.h"
@@ -33,6 +34,10 @@ void set_error(const char* fmt, ...);
 // Counts kernel launches of the library (reported by sts_launch_count).
 void note_launch();
 
+// Count of device (re)allocations made by any DevBuf.  A recorded graph holds buffer addresses,
+// so it is replayed only while this count equals the one seen when it was recorded.
+inline std::atomic<unsigned long long> g_alloc_epoch{0};
+
 // A device buffer that only grows.  reserve() drops the old contents; grow() keeps them.
 // cudaMalloc / cudaFree happen outside any stream capture.
 template <class T>
@@ -46,6 +51,7 @@ struct DevBuf {
         p = nullptr;
         cap = 0;
         size_t want = n + n / 8 + 16;
+        g_alloc_epoch.fetch_add(1);
         cudaError_t e = cudaMalloc((void**)&p, want * sizeof(T));
         if (e == cudaSuccess) cap = want;
         return e;
@@ -72,10 +78,12 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = q;
         cap = want;
+        g_alloc_epoch.fetch_add(1);
         return cudaSuccess;
     }
     void release()
     {
+        if (p) g_alloc_epoch.fetch_add(1);
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -185,6 +193,7 @@ struct sts_ctx {
     std::vector<double> rk_key;
     std::vector<int64_t> rk_off_key;
     cudaGraphExec_t ev_exec = nullptr;   // tree build + velocity recorded (sts_tree_velocity)
+    unsigned long long rk_epoch = 0, ev_epoch = 0;  // g_alloc_epoch when each was recorded
     long long ev_kernels = 0, rk_kernels = 0;  // kernels per replay of each recording
     std::vector<double> ev_key;
     std::vector<int64_t> ev_off_key;
@@ -226,6 +235,30 @@ struct sts_ctx {
     sts::DevBuf<sts::Task> tasks;
     int64_t ntasks = 0;
     int list_degree = -1;                // degree the far entries' slots refer to
+
+    // ---- dual traversal (Sec. 3.4) ---------------------------------------------------
+    // Pairs (target node, source node) of the four kinds PP, PC, CP, CC, each sorted by target
+    // then source.  While have_dual holds, the leaf lists above hold the PP (near) and PC (far)
+    // pairs of the target leaves; the cluster lists below hold the CP (near) and CC (far) pairs
+    // of the target clusters, whose targets are the clusters' proxy points.
+    bool have_dual = false;
+    double dual_theta = 0.0;
+    sts::DevBuf<int32_t> dual_t[4], dual_s[4];
+    int64_t dual_n[4] = {0, 0, 0, 0};
+    sts::DevBuf<int32_t> dual_ft, dual_fs, dual_gt, dual_gs;  // pair frontiers (current, next)
+    sts::DevBuf<uint32_t> dual_key, dual_ktmp;
+    sts::DevBuf<int32_t> dual_vtmp;
+    sts::DevBuf<int64_t> dual_cnt;       // [8] terminal counts per kind, next frontier size
+    sts::DevBuf<int64_t> dual_scan;      // chunk scan of the near pairs
+    sts::DevBuf<int64_t> cfar_off, cnear_off, cnear_coff;  // [C + 1] per target cluster slot
+    sts::DevBuf<sts::FarEntry> cfar_ent;
+    sts::DevBuf<sts::NearEntry> cnear_ent;
+    sts::DevBuf<sts::Task> ctasks;
+    int64_t nctasks = 0, ncnear_chunks = 0;
+    sts::DevBuf<double> cvel;            // [C, M, 3] velocity at the proxy points of target clusters
+    sts::DevBuf<double> ccorr;           // [C, M, 3] FP64 close-pair sums of the proxy targets
+    sts::DevBuf<double> cdown;           // [C, M, 3] coefficients of the interpolating polynomials
+    sts::DevBuf<uint8_t> chas;           // [C] the cluster is the target of CP or CC pairs
 
     // ---- direct sum scratch ------------------------------------------------------------
     sts::DevBuf<double4> dsrc64;
@@ -274,6 +307,13 @@ void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* v
 int tree_build(sts_ctx* ctx, const double* pos, int64_t n, const int64_t* inst_off, int ninst,
                int leaf_size, int max_level, cudaStream_t s);
 int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
+// Dual traversal (Sec. 3.4): the four pair lists, the leaf lists of PP and PC pairs and the
+// cluster lists of CP and CC pairs with their evaluation tasks.  Synchronises `s`.
+int build_dual(sts_ctx* ctx, double theta, cudaStream_t s);
+// Pair counts of the dual lists: stats[0..3] = PP pairs (j != i), PC, CP, CC interactions.
+int dual_stats(sts_ctx* ctx, int degree, int64_t* stats, cudaStream_t s);
+// Evaluation tasks of the clusters that are targets of CP or CC pairs, and their has flags.
+int cluster_tasks(sts_ctx* ctx, int M, cudaStream_t s);
 // node-table capacity (contents are not kept)
 int reserve_tree_nodes(sts_ctx* ctx, int64_t nodes, cudaStream_t s);
 // out[0..3] = *a, *b, *c, *d (0 for NULL), out[4] = status word: one host read for all.
@@ -288,6 +328,10 @@ int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
 
 // ---- evaluation (sts_eval.cu) ---------------------------------------------------------
 int evaluate(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
+// Dual-traversal velocity: PP and PC at the particles of the target leaves, CP and CC at the
+// proxy points of the target clusters, then the interpolating polynomial of every target
+// cluster evaluated at its particles and added (Sec. 3.3, 3.4).
+int evaluate_dual(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
 int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
                      double* psi, cudaStream_t s);
 int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s);

@@ -27,6 +27,9 @@
 //             sorted order (leaves depth first, original order inside a leaf).
 #include <stdio.h>
 
+#include <algorithm>
+#include <utility>
+
 #include "sts_internal.cuh"
 
 namespace sts {
@@ -1001,6 +1004,239 @@ __global__ void k_gather(const int64_t* a, const int64_t* b, const int64_t* c, c
     out[4] = *status;
 }
 
+// ------------------------------------------------------------------------- dual traversal
+// Dual tree traversal of Sec. 3.4 over pairs (target node, source node), level-synchronous:
+// every pair of the current frontier is decided at once.  A pair that passes the MAC is a
+// terminal of its kind by the two particle counts against N_T (PP both at most N_T, PC only
+// the source above, CP only the target above, CC both above); a failing pair of two leaves
+// is PP; otherwise the triangle with more particles (the target on a tie; never a leaf) is
+// replaced by its children, which form the next frontier's pairs.  The terminals are
+// appended in any order and sorted afterwards, so the lists do not depend on the schedule.
+enum { kPP = 0, kPC = 1, kCP = 2, kCC = 3 };
+
+struct DualOut {
+    int32_t* t[4];
+    int32_t* s[4];
+    int64_t cap[4];
+};
+
+// The 20 x 20 root pairs of every instance (a target interacts with its own instance only).
+__global__ void k_dual_roots(const int32_t* __restrict__ face_node, int ninst, int32_t* __restrict__ ft,
+                             int32_t* __restrict__ fs, unsigned long long* __restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ninst * 400) return;
+    const int64_t b = i / 400;
+    const int f1 = (int)(i % 400) / 20, f2 = (int)(i % 20);
+    const int32_t t = face_node[20 * b + f1], s = face_node[20 * b + f2];
+    if (t < 0 || s < 0) return;
+    const unsigned long long q = atomicAdd(cnt + 4, 1ull);
+    ft[q] = t;
+    fs[q] = s;
+}
+
+// One level of the traversal: cnt[0..3] count the terminals per kind, cnt[4] the next
+// frontier.  Writes past a capacity are dropped; the host sees the counts, grows the buffers
+// and runs the level again from the same frontier.
+__global__ void k_dual_step(const int32_t* __restrict__ ft, const int32_t* __restrict__ fs, int64_t nf,
+                            double theta, int leaf_size, const double* __restrict__ geom,
+                            const float4* __restrict__ c32, const int32_t* __restrict__ leaf,
+                            const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
+                            const int32_t* __restrict__ count, int32_t* __restrict__ gt, int32_t* __restrict__ gs,
+                            int64_t gcap, DualOut out, unsigned long long* __restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const int32_t t = ft[i], s = fs[i];
+    const int32_t ct = count[t], cs = count[s];
+    const bool lt = leaf[t] != 0, ls = leaf[s] != 0;
+    int kind = -1;
+    if (mac_filtered(c32[t], c32[s], (float)theta, geom + 13 * (int64_t)t, geom + 13 * (int64_t)s, theta)) {
+        const bool tc = ct > leaf_size, sc = cs > leaf_size;
+        kind = tc ? (sc ? kCC : kCP) : (sc ? kPC : kPP);
+    } else if (lt && ls) {
+        kind = kPP;
+    }
+    if (kind >= 0) {
+        const unsigned long long q = atomicAdd(cnt + kind, 1ull);
+        if ((int64_t)q < out.cap[kind]) {
+            out.t[kind][q] = t;
+            out.s[kind][q] = s;
+        }
+        return;
+    }
+    const bool split_t = !lt && (ls || ct >= cs);
+    const int32_t p = split_t ? t : s;
+    const int32_t fc = first_child[p], nc = nchild[p];
+    const int64_t q = (int64_t)atomicAdd(cnt + 4, (unsigned long long)nc);
+    if (q + nc > gcap) return;
+    for (int32_t c = 0; c < nc; c++) {
+        gt[q + c] = split_t ? fc + c : t;
+        gs[q + c] = split_t ? s : fc + c;
+    }
+}
+
+// Sorting a kind's pairs by (target key, source): key = source, then (after a stable sort)
+// the target's key with the sources as values.  Target key: the depth-first leaf index for
+// leaf targets (PP, PC), the cluster slot for cluster targets (CP, CC).
+__global__ void k_dual_key_src(const int32_t* __restrict__ src, int64_t n, uint32_t* __restrict__ key)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) key[i] = (uint32_t)src[i];
+}
+
+__global__ void k_dual_key_tgt(uint32_t* __restrict__ key, const int32_t* __restrict__ tgt, int64_t n,
+                               const int32_t* __restrict__ start, const int32_t* __restrict__ slot_leaf,
+                               const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ src)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    src[i] = (int32_t)key[i];
+    const int32_t t = tgt[i];
+    key[i] = (uint32_t)(cluster_slot ? cluster_slot[t] : slot_leaf[start[t]]);
+}
+
+__global__ void k_dual_key_back(const uint32_t* __restrict__ key, int64_t n, const int32_t* __restrict__ node_of,
+                                int32_t* __restrict__ tgt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tgt[i] = node_of[key[i]];
+}
+
+// off[k] = first pair whose key is >= k, for k in [0, K] (binary search in the sorted keys).
+__global__ void k_dual_offsets(const uint32_t* __restrict__ key, int64_t n, int64_t K, int64_t* __restrict__ off)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > K) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)key[mid] < k)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[k] = lo;
+}
+
+__global__ void k_dual_chunks(const int32_t* __restrict__ src, int64_t n, const int32_t* __restrict__ count,
+                              int32_t* __restrict__ chunks)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) chunks[i] = (count[src[i]] + kStage - 1) / kStage;
+}
+
+__global__ void k_dual_coff(const int64_t* __restrict__ off, int64_t K, const int64_t* __restrict__ scan,
+                            int64_t* __restrict__ coff)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= K) coff[k] = scan[off[k]];
+}
+
+// List entries of sorted pairs: far (a source cluster's proxy block) or near (a source leaf in
+// chunks of at most kStage particles), with the FP32 centre offset c_s - c_t and, for near
+// entries, the lower bound on the distance between the two triangles' points.
+__global__ void k_dual_fill(bool is_far, const uint32_t* __restrict__ key, const int32_t* __restrict__ src,
+                            int64_t n, const int32_t* __restrict__ node_of, const double* __restrict__ geom,
+                            const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+                            const int32_t* __restrict__ cluster_slot, const int64_t* __restrict__ chunk_scan,
+                            int32_t* __restrict__ idx, FarEntry* __restrict__ far_ent,
+                            NearEntry* __restrict__ near_ent)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t t = node_of[key[i]], s = src[i];
+    const double* gt = geom + 13 * (int64_t)t;
+    const double* gs = geom + 13 * (int64_t)s;
+    const float dx = (float)__dsub_rn(gs[9], gt[9]);
+    const float dy = (float)__dsub_rn(gs[10], gt[10]);
+    const float dz = (float)__dsub_rn(gs[11], gt[11]);
+    if (idx) idx[i] = s;
+    if (is_far) {
+        FarEntry e;
+        e.slot = cluster_slot[s];
+        e.dx = dx;
+        e.dy = dy;
+        e.dz = dz;
+        far_ent[i] = e;
+        return;
+    }
+    NearEntry e;
+    e.dx = dx;
+    e.dy = dy;
+    e.dz = dz;
+    e.gap = near_gap(gt, gs);
+    e.pad[0] = e.pad[1] = 0;
+    const int32_t st = start[s], ct = count[s];
+    int64_t q = chunk_scan[i];
+    for (int32_t c0 = 0; c0 < ct; c0 += kStage) {
+        e.start = st + c0;
+        e.count = min(kStage, ct - c0);
+        near_ent[q++] = e;
+    }
+}
+
+// Evaluation tasks of the target clusters (targets: the M proxy points of cluster slot c,
+// rows c M .. c M + M - 1); has[c] = the cluster is the target of a CP or CC pair.
+__global__ void k_cluster_tasks(int64_t nclu, const int64_t* __restrict__ cfar_off,
+                                const int64_t* __restrict__ cnear_off, int M, uint8_t* __restrict__ has,
+                                Task* __restrict__ tasks, int64_t cap, unsigned long long* __restrict__ ntask,
+                                int* __restrict__ status)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclu) return;
+    const bool h = cfar_off[c + 1] > cfar_off[c] || cnear_off[c + 1] > cnear_off[c];
+    has[c] = h ? 1 : 0;
+    if (!h) return;
+    const int k = task_split(M);
+    const int64_t base = (int64_t)atomicAdd(ntask, (unsigned long long)k);
+    int32_t t0 = 0;
+    for (int i = 0; i < k; i++) {
+        const int32_t m = M / k + (i < M % k ? 1 : 0);
+        Task tk;
+        tk.leaf = (int32_t)c;
+        tk.t0 = (int32_t)(c * M) + t0;
+        tk.nt = m;
+        tk.S = lanes_per_pair((m + 1) / 2);
+        if (base + i < cap)
+            tasks[base + i] = tk;
+        else
+            atomicOr(status, kStatusCapacity);
+        t0 += m;
+    }
+}
+
+// Interaction counts of the dual lists: st[0] PP pairs (j != i), st[1] PC target x proxy,
+// st[2] CP proxy x source, st[3] CC proxy x proxy; st[4] downward particle x M over the
+// clusters in has (launched over clusters with kind = 4).
+__global__ void k_dual_count(int kind, const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
+                             const int32_t* __restrict__ count, const uint8_t* __restrict__ has, int M,
+                             unsigned long long* __restrict__ st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) {
+        const unsigned long long mm = (unsigned long long)M;
+        if (kind == 4) {
+            v = has[i] ? (unsigned long long)count[tgt[i]] * mm : 0ull;  // tgt: cluster nodes
+        } else {
+            const int32_t t = tgt[i], s = src[i];
+            const unsigned long long ct = (unsigned long long)count[t], cs = (unsigned long long)count[s];
+            if (kind == kPP)
+                v = ct * cs - (t == s ? ct : 0ull);
+            else if (kind == kPC)
+                v = ct * mm;
+            else if (kind == kCP)
+                v = mm * cs;
+            else
+                v = mm * mm;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(st + kind, v);
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int read_i64(sts_ctx* ctx, const int64_t* dptr, int64_t* out, cudaStream_t s)
@@ -1046,6 +1282,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
 {
     c->have_tree = false;
     c->have_lists = false;
+    c->have_dual = false;
     c->up_degree = -1;
     c->n = n;
     c->leaf_size = leaf_size;
@@ -1214,6 +1451,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
 int build_lists(sts_ctx* c, double theta, cudaStream_t s)
 {
     c->have_lists = false;
+    c->have_dual = false;  // the leaf lists no longer hold the dual traversal's PP / PC pairs
     const bool cap = c->capturing;
     // leaf count, or while recording its planned bound (a replay with more leaves sets the
     // overflow bit in k_list_totals and is redone)
@@ -1301,6 +1539,259 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     STS_LAUNCH_CHECK();
     c->list_theta = theta;
     c->have_lists = true;
+    return STS_OK;
+}
+
+// Sorts the pairs of one kind by (target key, source); afterwards c->dual_key holds the sorted
+// target keys and dual_t / dual_s the pairs.  leaf_targets: key = depth-first leaf index,
+// else the cluster slot.
+static int sort_dual_kind(sts_ctx* c, int kind, bool leaf_targets, cudaStream_t s)
+{
+    const int64_t P = c->dual_n[kind];
+    if (P == 0) return STS_OK;
+    const int T = 256;
+    const int64_t hs = radix_hist_size(P);
+    int64_t* scan_out = c->scan_tmp.p;
+    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
+    int bits_node = 0, bits_key = 0;
+    while (bits_node < 32 && ((int64_t)1 << bits_node) < c->nnodes) bits_node++;
+    const int64_t K = leaf_targets ? c->nleaves : c->nclusters;
+    while (bits_key < 32 && ((int64_t)1 << bits_key) < K) bits_key++;
+    (k_dual_key_src<<<blocks(P, T), T, 0, s>>>(c->dual_s[kind].p, P, c->dual_key.p), note_launch());
+    radix_sort_pairs(c->dual_key.p, c->dual_t[kind].p, c->dual_ktmp.p, c->dual_vtmp.p, P, bits_node, c->hist.p,
+                     scan_out, scan_scr, s);
+    (k_dual_key_tgt<<<blocks(P, T), T, 0, s>>>(c->dual_key.p, c->dual_t[kind].p, P, c->nd_start.p, c->slot_leaf.p,
+                                               leaf_targets ? nullptr : c->cluster_slot.p, c->dual_s[kind].p),
+     note_launch());
+    radix_sort_pairs(c->dual_key.p, c->dual_s[kind].p, c->dual_ktmp.p, c->dual_vtmp.p, P, bits_key, c->hist.p,
+                     scan_out, scan_scr, s);
+    (k_dual_key_back<<<blocks(P, T), T, 0, s>>>(c->dual_key.p, P,
+                                                leaf_targets ? c->leaves.p : c->cluster_node.p, c->dual_t[kind].p),
+     note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+// CSR of one sorted kind over K target keys: off[K + 1] (pairs); for near kinds also the chunk
+// offsets coff[K + 1] and the chunked entries.  Reads the chunk total back (synchronises s).
+static int fill_dual_kind(sts_ctx* c, int kind, int64_t K, bool is_far, int64_t* off, int64_t* coff,
+                          int32_t* idx, DevBuf<FarEntry>* far_ent, DevBuf<NearEntry>* near_ent, int64_t* chunks,
+                          cudaStream_t s)
+{
+    const int64_t P = c->dual_n[kind];
+    const int T = 256;
+    const int32_t* node_of = (kind == kPP || kind == kPC) ? c->leaves.p : c->cluster_node.p;
+    (k_dual_offsets<<<blocks(K + 1, T), T, 0, s>>>(c->dual_key.p, P, K, off), note_launch());
+    if (is_far) {
+        STS_CUDA(far_ent->reserve(P + 1));
+        if (P > 0)
+            (k_dual_fill<<<blocks(P, T), T, 0, s>>>(true, c->dual_key.p, c->dual_s[kind].p, P, node_of, c->nd_geom.p,
+                                                    c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, idx,
+                                                    far_ent->p, nullptr),
+             note_launch());
+        STS_LAUNCH_CHECK();
+        return STS_OK;
+    }
+    // chunk counts per pair (in the radix scratch, free after the sort), their scan, and the
+    // chunk offset of every key
+    if (P > 0)
+        (k_dual_chunks<<<blocks(P, T), T, 0, s>>>(c->dual_s[kind].p, P, c->nd_count.p, c->dual_vtmp.p),
+         note_launch());
+    exclusive_scan_i32(c->dual_vtmp.p, c->dual_scan.p, P, c->scan_tmp.p, s);
+    (k_dual_coff<<<blocks(K + 1, T), T, 0, s>>>(off, K, c->dual_scan.p, coff), note_launch());
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_scan.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    *chunks = c->h_pinned[0];
+    STS_CUDA(near_ent->reserve(*chunks + 1));
+    if (P > 0)
+        (k_dual_fill<<<blocks(P, T), T, 0, s>>>(false, c->dual_key.p, c->dual_s[kind].p, P, node_of, c->nd_geom.p,
+                                                c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->dual_scan.p, idx,
+                                                nullptr, near_ent->p),
+         note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+int build_dual(sts_ctx* c, double theta, cudaStream_t s)
+{
+    c->have_dual = false;
+    c->have_lists = false;  // the leaf lists are replaced by the PP / PC pairs
+    if (c->capturing) {
+        set_error("dual traversal: not available while recording a graph");
+        return STS_ERR_STATE;
+    }
+    const int T = 256;
+    const int64_t nn = c->nnodes, L = c->nleaves, C = c->nclusters;
+    STS_CUDA(c->dual_cnt.reserve(8));
+    unsigned long long* cnt = (unsigned long long*)c->dual_cnt.p;
+    int64_t fcap = std::max<int64_t>(400 * (int64_t)c->ninst, 8 * nn + 64);
+    STS_CUDA(c->dual_ft.reserve(fcap));
+    STS_CUDA(c->dual_fs.reserve(fcap));
+    STS_CUDA(c->dual_gt.reserve(fcap));
+    STS_CUDA(c->dual_gs.reserve(fcap));
+    const int64_t init_cap[4] = {48 * L + 64, 48 * L + 64, 16 * C + 64, 16 * C + 64};
+    for (int k = 0; k < 4; k++) {
+        STS_CUDA(c->dual_t[k].reserve(init_cap[k]));
+        STS_CUDA(c->dual_s[k].reserve(init_cap[k]));
+    }
+    STS_CUDA(cudaMemsetAsync(c->dual_cnt.p, 0, 8 * sizeof(int64_t), s));
+    (k_dual_roots<<<blocks(400 * (int64_t)c->ninst, T), T, 0, s>>>(c->face_node.p, c->ninst, c->dual_ft.p,
+                                                                  c->dual_fs.p, cnt), note_launch());
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    int64_t nf = c->h_pinned[4];
+    int64_t done[4] = {0, 0, 0, 0};
+    // each level refines one side of a pair, so the traversal ends within 2 (depth + 1) levels;
+    // every retry grows a buffer
+    for (int it = 0; nf > 0; it++) {
+        if (it > 4 * (kMaxLevel + 2) + 64) {
+            set_error("dual traversal: no progress");
+            return STS_ERR_CAPACITY;
+        }
+        for (int k = 0; k < 4; k++) c->h_pinned[k] = done[k];
+        c->h_pinned[4] = 0;
+        STS_CUDA(cudaMemcpyAsync(c->dual_cnt.p, c->h_pinned, 5 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        DualOut out;
+        for (int k = 0; k < 4; k++) {
+            out.t[k] = c->dual_t[k].p;
+            out.s[k] = c->dual_s[k].p;
+            out.cap[k] = (int64_t)std::min(c->dual_t[k].cap, c->dual_s[k].cap);
+        }
+        const int64_t gcap = (int64_t)std::min(c->dual_gt.cap, c->dual_gs.cap);
+        (k_dual_step<<<blocks(nf, T), T, 0, s>>>(c->dual_ft.p, c->dual_fs.p, nf, theta, c->leaf_size, c->nd_geom.p,
+                                                 c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
+                                                 c->nd_count.p, c->dual_gt.p, c->dual_gs.p, gcap, out, cnt),
+         note_launch());
+        STS_LAUNCH_CHECK();
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        bool redo = false;
+        for (int k = 0; k < 4; k++)
+            if (c->h_pinned[k] > out.cap[k]) {
+                const int64_t need = c->h_pinned[k];
+                STS_CUDA(c->dual_t[k].grow(need, done[k], s));
+                STS_CUDA(c->dual_s[k].grow(need, done[k], s));
+                redo = true;
+            }
+        const int64_t ng = c->h_pinned[4];
+        if (ng > gcap) {
+            STS_CUDA(c->dual_gt.reserve(ng));
+            STS_CUDA(c->dual_gs.reserve(ng));
+            redo = true;
+        }
+        if (redo) continue;  // the same frontier again, with room for every write
+        for (int k = 0; k < 4; k++) done[k] = c->h_pinned[k];
+        nf = ng;
+        std::swap(c->dual_ft, c->dual_gt);
+        std::swap(c->dual_fs, c->dual_gs);
+    }
+    int64_t pmax = 1;
+    for (int k = 0; k < 4; k++) {
+        c->dual_n[k] = done[k];
+        pmax = std::max(pmax, done[k]);
+    }
+    // sort every kind by (target, source)
+    const int64_t hs = radix_hist_size(pmax);
+    STS_CUDA(c->dual_key.reserve(pmax + 1));
+    STS_CUDA(c->dual_ktmp.reserve(pmax + 1));
+    STS_CUDA(c->dual_vtmp.reserve(pmax + 1));
+    STS_CUDA(c->dual_scan.reserve(pmax + 1));
+    STS_CUDA(c->hist.reserve(hs));
+    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(pmax + 1) + scan_scratch(nn + 1) + 64));
+    // leaf lists: PC far, PP near (per depth-first leaf); cluster lists: CC far, CP near
+    STS_CUDA(c->far_off.reserve(L + 1));
+    STS_CUDA(c->near_off.reserve(L + 1));
+    STS_CUDA(c->near_coff.reserve(L + 1));
+    STS_CUDA(c->far_idx.reserve(c->dual_n[kPC] + 1));
+    STS_CUDA(c->near_idx.reserve(c->dual_n[kPP] + 1));
+    STS_CUDA(c->cfar_off.reserve(C + 1));
+    STS_CUDA(c->cnear_off.reserve(C + 1));
+    STS_CUDA(c->cnear_coff.reserve(C + 1));
+    int rc;
+    int64_t chunks = 0, cchunks = 0;
+    if ((rc = sort_dual_kind(c, kPC, true, s))) return rc;
+    if ((rc = fill_dual_kind(c, kPC, L, true, c->far_off.p, nullptr, c->far_idx.p, &c->far_ent, nullptr, nullptr, s)))
+        return rc;
+    if ((rc = sort_dual_kind(c, kPP, true, s))) return rc;
+    if ((rc = fill_dual_kind(c, kPP, L, false, c->near_off.p, c->near_coff.p, c->near_idx.p, nullptr, &c->near_ent,
+                             &chunks, s)))
+        return rc;
+    if ((rc = sort_dual_kind(c, kCC, false, s))) return rc;
+    if ((rc = fill_dual_kind(c, kCC, C, true, c->cfar_off.p, nullptr, nullptr, &c->cfar_ent, nullptr, nullptr, s)))
+        return rc;
+    if ((rc = sort_dual_kind(c, kCP, false, s))) return rc;
+    if ((rc = fill_dual_kind(c, kCP, C, false, c->cnear_off.p, c->cnear_coff.p, nullptr, nullptr, &c->cnear_ent,
+                             &cchunks, s)))
+        return rc;
+    // the sorted target keys are no longer needed; the pairs stay for export (targets: node ids)
+    int64_t* dc = c->dc.p;
+    const unsigned g = blocks(std::max<int64_t>(L, 1), 128);
+    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
+    (k_task_count<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
+                                    (unsigned long long*)(dc + kDcClass)), note_launch());
+    (k_list_totals<<<1, 32, 0, s>>>(dc, c->far_off.p, c->near_off.p, c->near_coff.p, L), note_launch());
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    c->nfar = c->h_pinned[kDcFar];
+    c->nnear = c->h_pinned[kDcNear];
+    c->nnear_chunks = c->h_pinned[kDcChunks];
+    c->ntasks = c->h_pinned[kDcTasks];
+    c->ncnear_chunks = cchunks;
+    STS_CUDA(c->tasks.reserve(c->ntasks + 1));
+    (k_task_fill<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
+                                   (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
+                                   dc + kDcOver), note_launch());
+    STS_LAUNCH_CHECK();
+    c->dual_theta = theta;
+    c->have_dual = true;
+    return STS_OK;
+}
+
+int cluster_tasks(sts_ctx* c, int M, cudaStream_t s)
+{
+    const int64_t C = c->nclusters;
+    c->nctasks = 0;
+    STS_CUDA(c->chas.reserve(C + 1));
+    if (C == 0) return STS_OK;
+    const int64_t cap = C * ((M + kTaskTargets - 1) / kTaskTargets + 3);
+    STS_CUDA(c->ctasks.reserve(cap + 1));
+    STS_CUDA(cudaMemsetAsync(c->dual_cnt.p + 5, 0, sizeof(int64_t), s));
+    (k_cluster_tasks<<<blocks(C, 128), 128, 0, s>>>(C, c->cfar_off.p, c->cnear_off.p, M, c->chas.p, c->ctasks.p, cap,
+                                                    (unsigned long long*)(c->dual_cnt.p + 5), c->d_status),
+     note_launch());
+    STS_LAUNCH_CHECK();
+    c->nctasks = cap;  // a bound: the kernels read the count from dual_cnt[5]
+    return STS_OK;
+}
+
+int dual_stats(sts_ctx* c, int degree, int64_t* stats, cudaStream_t s)
+{
+    for (int k = 0; k < 5; k++) stats[k] = 0;
+    if (!c->have_dual) return STS_OK;
+    const int M = (degree + 1) * (degree + 2) / 2;
+    STS_CUDA(c->d_stats.reserve(8));
+    STS_CUDA(cudaMemsetAsync(c->d_stats.p, 0, 8 * sizeof(unsigned long long), s));
+    const int T = 256;
+    for (int k = 0; k < 4; k++)
+        if (c->dual_n[k] > 0)
+            (k_dual_count<<<blocks(c->dual_n[k], T), T, 0, s>>>(k, c->dual_t[k].p, c->dual_s[k].p, c->dual_n[k],
+                                                                c->nd_count.p, nullptr, M, c->d_stats.p),
+             note_launch());
+    if (c->nclusters > 0) {
+        // the clusters that are targets of CP or CC pairs (as the dual evaluation marks them)
+        int rc = cluster_tasks(c, M, s);
+        if (rc) return rc;
+        (k_dual_count<<<blocks(c->nclusters, T), T, 0, s>>>(4, c->cluster_node.p, nullptr, c->nclusters,
+                                                            c->nd_count.p, c->chas.p, M, c->d_stats.p),
+         note_launch());
+    }
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->d_stats.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 5; k++) stats[k] = c->h_pinned[k];
     return STS_OK;
 }
 

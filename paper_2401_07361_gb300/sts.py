@@ -79,6 +79,9 @@ def load(build_if_needed: bool = True):
             "sts_tree_build": (i32, [P, P, i64, PP, P]),
             "sts_velocity": (i32, [P, P, P, PP, P, P]),
             "sts_potential": (i32, [P, P, P, PP, P, P]),
+            "sts_velocity_dual": (i32, [P, P, P, PP, P, P]),
+            "sts_dual_export": (i32, [P, i32, P, P, P, P]),
+            "sts_dual_stats": (i32, [P, i32, P, P]),
             "sts_direct_potential": (i32, [P, P, P, P, i64, i32, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
             "bve_rk4_step_forced": (i32, [P, P, P, P, i64, dbl, dbl, dbl, C.POINTER(sts_forcing), PP, P]),
@@ -216,6 +219,43 @@ def sts_velocity(ctx, zeta, area, p, vel=None, stream=None):
                                C.byref(p), _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
            "sts_velocity")
     return vel
+
+
+def sts_velocity_dual(ctx, zeta, area, p, vel=None, stream=None):
+    """Tree-code velocity vel[n,3] by the dual traversal (PP, PC, CP, CC) for the tree last
+    built in ctx."""
+    import torch
+
+    n = zeta.numel()
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=zeta.device)
+    _check(load().sts_velocity_dual(ctx, _dev(zeta, torch.float64, n, "zeta"),
+                                    _dev(area, torch.float64, n, "area"), C.byref(p),
+                                    _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
+           "sts_velocity_dual")
+    return vel
+
+
+DUAL_KINDS = ("PP", "PC", "CP", "CC")
+
+
+def sts_dual_export(ctx, stream=None):
+    """Pairs of the last dual traversal: {"PP"|"PC"|"CP"|"CC": (target nodes, source nodes)},
+    sorted by target (leaf or cluster order), then source."""
+    out = {}
+    for k, name in enumerate(DUAL_KINDS):
+        cnt = np.zeros(1, np.int64)
+        _check(load().sts_dual_export(ctx, k, _host(cnt), None, None, _stream(stream)), "sts_dual_export")
+        t, s = np.zeros(int(cnt[0]), np.int32), np.zeros(int(cnt[0]), np.int32)
+        _check(load().sts_dual_export(ctx, k, _host(cnt), _host(t), _host(s), _stream(stream)), "sts_dual_export")
+        out[name] = (t, s)
+    return out
+
+
+def sts_dual_stats(ctx, degree, stream=None):
+    a = np.zeros(5, np.int64)
+    _check(load().sts_dual_stats(ctx, int(degree), _host(a), _stream(stream)), "sts_dual_stats")
+    return dict(pp=int(a[0]), pc=int(a[1]), cp=int(a[2]), cc=int(a[3]), down=int(a[4]))
 
 
 def sts_potential(ctx, zeta, area, p, psi=None, stream=None):

@@ -64,3 +64,28 @@ def test_fullsize_direct_sampled_targets(setup):
     for prec, tol in ((sts.STS_FP64, 1e-12), (sts.STS_MIXED, 1e-6)):
         v = sts.sts_direct_targets(h, d(pos), d(zeta), d(area), d(tg), prec).cpu().numpy()
         assert O.rel_l2(v, ref, area[tg]) <= tol
+
+
+def test_fullsize_dual_lists_and_mixed_velocity(setup):
+    """The dual traversal (PP, PC, CP, CC) at the full size in the launch configuration of
+    ``bench.py --dual``: the four pair lists bit for bit, the mixed velocity within 1e-6 of the
+    oracle's FP64 dual tree code at every target."""
+    wl, h = setup
+    pos, zeta, area = wl["pos"], wl["zeta"], wl["area"]
+    n = len(pos)
+    p = sts.params(theta=0.7, degree=8, leaf_size=128, max_level=16, precision=sts.STS_MIXED,
+                   near_fp64_tau=0.01 * 4 * math.pi / n)
+    d = lambda a: torch.from_numpy(a).to("cuda")
+    sts.sts_tree_build(h, d(pos), p)
+    v = sts.sts_velocity_dual(h, d(zeta), d(area), p).cpu().numpy()
+    tr = O.Tree(pos, 128, 16)
+    o, g = tr.dual_lists(0.7), sts.sts_dual_export(h)
+    for k in sts.DUAL_KINDS:
+        oo, go = np.lexsort((o[k][1], o[k][0])), np.lexsort((g[k][1], g[k][0]))
+        assert np.array_equal(o[k][0][oo], g[k][0][go]) and np.array_equal(o[k][1][oo], g[k][1][go]), k
+    ref, st = tr.velocity_dual(zeta, area, 0.7, 8, return_stats=True)
+    assert sts.sts_dual_stats(h, 8) == st
+    e2, em = O.rel_l2(v, ref, area), O.rel_max(v, ref)
+    print(f"dual mixed vs FP64 oracle dual: rel_l2 {e2:.3e} rel_max {em:.3e}")
+    assert e2 <= 1e-6
+    assert em <= 1e-5
