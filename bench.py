@@ -58,7 +58,8 @@ def parse(argv=None):
     ap.add_argument("--potential", action="store_true",
                     help="time the FP64 tree-code stream function (build + potential) instead")
     ap.add_argument("--dual", action="store_true",
-                    help="time the dual-traversal tree code (PP, PC, CP, CC of Sec. 3.4) instead")
+                    help="the tree code by the dual traversal of Sec. 3.4 (PP, PC, CP, CC) instead of the "
+                         "target-leaf lists (PC, PP)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
@@ -424,113 +425,6 @@ def run_potential(args):
     return 0
 
 
-def run_dual(args):
-    """The dual-traversal tree code (Sec. 3.4 with all four interactions), mixed precision:
-    tree build + dual lists + upward pass + PP/PC evaluation at the particles + CP/CC at the
-    target proxies + downward interpolation per step, host launches.  Roofline of the
-    evaluation kernel against the FP32 peak (16 flop per interaction, as the velocity bench),
-    the oracle's dual tree code beside it."""
-    import numpy as np
-    import torch
-
-    from paper_2401_07361_gb300 import sts
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    wl = load_workload(args.workload)
-    n = len(wl["pos"])
-    leaf = args.leaf or wl["leaf_size"]
-    offsets = wl.get("offsets")
-    tau = args.tau_c * 4 * math.pi / max(1, n if offsets is None else max(np.diff(offsets)))
-    p = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_MIXED,
-                   near_fp64_tau=tau)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
-    pos = torch.from_numpy(wl["pos"]).to(dev)
-    zeta = torch.from_numpy(wl["zeta"]).to(dev)
-    area = torch.from_numpy(wl["area"]).to(dev)
-    vel = torch.empty((n, 3), dtype=torch.float64, device=dev)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    ctx = sts.Context()
-    h = ctx.h
-
-    def step():
-        if offsets is None:
-            sts.sts_tree_build(h, pos, p)
-        else:
-            sts.sts_tree_build_batched(h, pos, offsets, p)
-        sts.sts_velocity_dual(h, zeta, area, p, vel)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    stats = sts.sts_dual_stats(h, args.degree)
-    sampler = ClockSampler(local)
-    sampler.start()
-    sts.sts_set_timing(h, True)
-    l0 = sts.sts_launch_count()
-    times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step()
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-    clocks = sampler.stop()
-    launches = sts.sts_launch_count() - l0
-    phases = sts.sts_phase_times(h)
-    sts.sts_set_timing(h, False)
-    total_ms = max_over_ranks(sum(times), ws, dev)
-    ms = total_ms / max(1, args.steps)
-    # two evaluation launches per step (leaf targets, then cluster proxy targets)
-    eval_ms = phases["eval"][0] / max(1, args.steps)
-    inter = stats["pp"] + stats["pc"] + stats["cp"] + stats["cc"]
-    peaks = measured_peaks()
-    mhz = float(peaks.get("sm_max_mhz", 2070.0)) if isinstance(peaks, dict) else 2070.0
-    peak32 = 152 * 128 * 2 * mhz * 1e6 / 1e12
-    achieved = 16.0 * inter / (eval_ms / 1e3) / 1e12
-    line = {
-        "metric": "velocity targets/s, dual-traversal tree code", "value": ws * n / (ms / 1e3), "unit": "targets/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
-                   "precision": "mixed", "tau_c": args.tau_c, "l2": "flushed between timed steps (256 MiB write)",
-                   "launch": "host launches (build + dual lists + upward + evaluation + downward)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                     "frac": achieved / peak32, "traffic": None, "kernel": "k_eval_mixed (both launches)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz; 16 flop per interaction",
-                     "kernel_ms": eval_ms},
-        "gpu_launches": int(launches), "clocks": clocks,
-        "phases_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in phases.items() if v[1]},
-        "interactions_per_step": stats,
-    }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and n <= 3_000_000:
-        from oracle import oracle as O
-
-        t0 = time.perf_counter()
-        if offsets is None:
-            ref = O.Tree(wl["pos"], leaf).velocity_dual(wl["zeta"], wl["area"], args.theta, args.degree)
-        else:
-            ref = np.concatenate([O.Tree(wl["pos"][a:b], leaf).velocity_dual(wl["zeta"][a:b], wl["area"][a:b],
-                                                                            args.theta, args.degree)
-                                  for a, b in zip(offsets[:-1], offsets[1:]) if b > a])
-        cpu_s = time.perf_counter() - t0
-        got = vel.cpu().numpy()
-        a = wl["area"][:, None]
-        line["error"] = {"vs_fp64_oracle_dual_rel_l2": float(np.sqrt(np.sum((got - ref) ** 2 * a) / np.sum(ref**2 * a)))}
-        line["cpu_baseline"] = {"value": n / cpu_s, "unit": "targets/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"full workload: oracle tree build + FP64 dual-traversal tree code of all "
-                                          f"{n} targets, OpenMP over target clusters and leaves"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    return 0
-
-
 def main():
     args = parse()
     if args.impl == "reference":
@@ -539,8 +433,6 @@ def main():
         return run_rk4(args)
     if args.potential:
         return run_potential(args)
-    if args.dual:
-        return run_dual(args)
     import numpy as np
     import torch
 
@@ -574,6 +466,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     sts.sts_set_graph(h, not args.no_graph)
+    sts.sts_set_traversal(h, args.dual)
     sts.sts_set_timing(h, True)
 
     offsets = wl.get("offsets")
@@ -588,7 +481,7 @@ def main():
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
-    stats = sts.sts_stats(h)
+    stats = sts.sts_dual_stats(h, args.degree) if args.dual else sts.sts_stats(h)
     info = sts.sts_tree_info(h)
 
     # ---- device-resident timed steps ------------------------------------------------
@@ -680,6 +573,7 @@ def main():
     err_vs_gpu64 = rel_l2(v_mixed, v64, area_h)
 
     # ---- roofline of the evaluation kernel ----------------------------------------------
+    # (the launch over the leaf lists: PC + PP, which the dual traversal's PP and PC pairs fill)
     eval_ms, eval_cnt = phases["eval"]
     eval_avg_ms = eval_ms / max(1, eval_cnt)
     inter = stats["pc"] + stats["pp"]
@@ -690,7 +584,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": profile_traffic(os.path.join(ROOT, "paper_2401_07361_gb300", "csrc", "sts_eval.cu")),
-                "kernel": "k_eval_mixed", "flops_per_launch": flops,
+                "kernel": "k_eval_mixed (leaf lists)" if args.dual else "k_eval_mixed", "flops_per_launch": flops,
                 "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                f"(MEASURED_PEAKS sm_max_mhz); 16 flop per interaction",
                 "kernel_ms": eval_avg_ms}
@@ -708,11 +602,14 @@ def main():
         for b in range(len(offs) - 1):
             lo, hi = int(offs[b]), int(offs[b + 1])
             tr = O.Tree(pos_h[lo:hi], leaf, 16)
-            ref[lo:hi] = tr.velocity(zeta_h[lo:hi], area_h[lo:hi], args.theta, args.degree, nthreads=cores)
+            vfun = tr.velocity_dual if args.dual else tr.velocity
+            ref[lo:hi] = vfun(zeta_h[lo:hi], area_h[lo:hi], args.theta, args.degree, nthreads=cores)
         dt = time.perf_counter() - t0
+        how = ("dual traversal (PP, PC, CP, CC), OpenMP over target clusters and leaves" if args.dual
+               else "OpenMP over target leaves")
         cpu = {"value": n / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
                "sample": f"one full evaluation: oracle tree build + FP64 tree-code velocity of all {n} targets "
-                         f"(theta {args.theta}, degree {args.degree}, N_T {leaf}), OpenMP over target leaves"}
+                         f"(theta {args.theta}, degree {args.degree}, N_T {leaf}), {how}"}
         err_vs_oracle = {"rel_l2": rel_l2(v_mixed, ref, area_h), "rel_max": rel_max(v_mixed, ref),
                          "fp64_gpu_rel_l2": rel_l2(v64, ref, area_h)}
 
@@ -724,6 +621,7 @@ def main():
             "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree,
                        "leaf_size": leaf, "max_level": 16, "precision": "mixed (f32 pairs, f64 positions/"
                        "contraction/near pairs below tau)", "near_fp64_tau": tau,
+                       "traversal": "dual (PP, PC, CP, CC)" if args.dual else "target-leaf lists (PC, PP)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "launch": "host launches" if args.no_graph else "recorded CUDA graph, replayed per step"},
@@ -737,7 +635,7 @@ def main():
             "error": {"mixed_vs_fp64_gpu_tree_rel_l2": err_vs_gpu64, "vs_fp64_oracle_tree": err_vs_oracle},
             "fp64_tree": {"value": n / (fp64_ms / 1e3), "unit": "targets/s", "ms": fp64_ms},
             "phases_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in phases.items() if v[1]},
-            "interactions_per_step": {"pc": stats["pc"], "pp": stats["pp"]},
+            "interactions_per_step": stats,
             "tree": info,
         }
         print(json.dumps(line), flush=True)

@@ -196,10 +196,9 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
  * target cluster's proxy points; the polynomial of degree d interpolating it over the cluster
  * (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m))) is evaluated at every particle below it and
  * added.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau (mixed precision: the
- * pair sums in FP32 as in sts_velocity, the interpolation in FP64).  Runs eagerly; builds the
- * pair lists when theta or the tree changed (synchronises `stream`), which replaces the lists
- * of sts_velocity (the next sts_velocity rebuilds them).  STS_ERR_STATE without a tree or
- * while a graph is being recorded. */
+ * pair sums in FP32 as in sts_velocity, the interpolation in FP64).  Builds the pair lists when
+ * theta or the tree changed (synchronises `stream` once), which replaces the lists of
+ * sts_velocity (the next sts_velocity rebuilds them).  STS_ERR_STATE without a tree. */
 int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
                       double* vel, void* stream);
 
@@ -269,6 +268,11 @@ int sts_lists_export(sts_ctx* ctx, int64_t* far_off, int32_t* far_idx, int64_t* 
 /* Clusters of the last sts_velocity in node order: node_ids[C], proxy points yt[C,M,3] and
  * proxy weights W[C,M] (FP64 values as the evaluation uses them).  Any pointer may be NULL. */
 int sts_clusters_export(sts_ctx* ctx, int32_t* node_ids, double* yt, double* W, void* stream);
+/* dual != 0: sts_velocity, sts_tree_velocity and the RK4 steps compute the tree-code
+ * velocity by the dual traversal of sts_velocity_dual (all four interactions); 0 (the default):
+ * by the target-leaf lists (PC + PP).  Graph recordings are keyed by this choice.  sts_potential
+ * always uses the target-leaf lists. */
+int sts_set_traversal(sts_ctx* ctx, int32_t dual);
 /* Pairs of the last dual traversal (sts_velocity_dual) of one kind: 0 PP, 1 PC, 2 CP, 3 CC.
  * *npairs (HOST) receives the count; tgt[npairs] and src[npairs] (HOST, may be NULL) the
  * target and source node ids, sorted by target (depth-first leaf order for PP and PC, cluster
@@ -293,9 +297,10 @@ int sts_stats(sts_ctx* ctx, int64_t* stats, void* stream);
 #define STS_PHASE_LISTS 2  /* interaction lists and evaluation tasks                    */
 #define STS_PHASE_PREP 3   /* sorted source copies                                      */
 #define STS_PHASE_UPWARD 4 /* SBB moments and proxy weights                             */
-#define STS_PHASE_EVAL 5   /* the far + near evaluation kernel                          */
+#define STS_PHASE_EVAL 5   /* the far + near evaluation kernel (PP + PC of the dual too)  */
 #define STS_PHASE_DIRECT 6 /* direct sum (all its kernels)                              */
-#define STS_NUM_PHASES 7
+#define STS_PHASE_CLUSTER 7 /* dual traversal: CP + CC at the target proxies, downward  */
+#define STS_NUM_PHASES 8
 /* on != 0 starts recording per-phase events and resets the totals; 0 stops. */
 int sts_set_timing(sts_ctx* ctx, int32_t on);
 /* Total milliseconds and number of timed occurrences per phase since sts_set_timing(1);

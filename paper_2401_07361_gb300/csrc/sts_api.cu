@@ -29,7 +29,7 @@ void set_error(const char* fmt, ...)
 
 void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing) return;
+    if (!c->timing || ph < 0) return;  // ph < 0: inside a phase the caller times
     if (c->capturing) {  // an event record node of the graph (external: it records at replay)
         cudaEventRecordWithFlags(c->ev[ph][0], s, cudaEventRecordExternal);
         return;
@@ -48,7 +48,7 @@ void phase_begin(sts_ctx* c, int ph, cudaStream_t s)
 
 void phase_end(sts_ctx* c, int ph, cudaStream_t s)
 {
-    if (!c->timing) return;
+    if (!c->timing || ph < 0) return;
     if (c->capturing) {
         cudaEventRecordWithFlags(c->ev[ph][1], s, cudaEventRecordExternal);
         c->phase_in_graph[ph] = true;
@@ -172,9 +172,13 @@ int check_n(int64_t n, const char* fn)
     return STS_OK;
 }
 
+int velocity_dual_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p, double* vel,
+                       cudaStream_t s);
+
 int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p,
                   double* vel, cudaStream_t s)
 {
+    if (c->use_dual) return velocity_dual_impl(c, zeta, area, p, vel, s);
     const int64_t n = c->n;
     if (n == 0) return STS_OK;
     if (n == 1) {
@@ -405,7 +409,18 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->wover.reserve(n + 1));
     STS_CUDA(c->corr.reserve(3 * n + 3));
     STS_CUDA(c->scan_tmp.reserve(radix_hist_size(n) + 1 + scan_scratch(radix_hist_size(n)) + 2 * scan_scratch(big) + 64));
+    if (c->use_dual && (rc = reserve_dual_for_capture(c, p->degree, s))) return rc;
     return STS_OK;
+}
+
+// After a replay the lists of the recorded traversal are in place (host counts refreshed on
+// demand).
+void mark_replayed_lists(sts_ctx* c, double theta)
+{
+    c->have_lists = !c->use_dual;
+    c->have_dual = c->use_dual;
+    c->list_theta = c->dual_theta = theta;
+    for (int k = 0; k < 4; k++) c->dual_n[k] = -1;
 }
 
 // One RK4 step through a recorded graph: the first call (or a call with other arguments)
@@ -416,7 +431,8 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
               const int64_t* off_host, int ninst, double dt, double Omega, const sts_params* p, cudaStream_t s)
 {
     std::vector<double> key = {(double)n, (double)ninst, dt, Omega, p->theta, (double)p->degree,
-                               (double)p->leaf_size, (double)p->max_level, (double)p->precision, p->near_fp64_tau};
+                               (double)p->leaf_size, (double)p->max_level, (double)p->precision, p->near_fp64_tau,
+                               (double)c->use_dual};
     std::vector<int64_t> okey = {(int64_t)(uintptr_t)pos, (int64_t)(uintptr_t)zeta, (int64_t)(uintptr_t)area,
                                  (int64_t)(uintptr_t)s};
     if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
@@ -441,8 +457,7 @@ int rk4_graph(sts_ctx* c, double* pos, double* zeta, const double* area, int64_t
             return STS_ERR_TIMEOUT;
         }
         c->have_tree = true;
-        c->have_lists = true;
-        c->have_dual = false;
+        mark_replayed_lists(c, p->theta);
         c->nnodes = -1;  // host counts refreshed on demand
         if (over == 0) return STS_OK;
         // undo the step and redo it eagerly below
@@ -505,7 +520,7 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
                cudaStream_t s)
 {
     std::vector<double> key = {-1.0, (double)n, (double)ninst, p->theta, (double)p->degree, (double)p->leaf_size,
-                               (double)p->max_level, (double)p->precision, p->near_fp64_tau};
+                               (double)p->max_level, (double)p->precision, p->near_fp64_tau, (double)c->use_dual};
     std::vector<int64_t> okey = {(int64_t)(uintptr_t)pos, (int64_t)(uintptr_t)zeta, (int64_t)(uintptr_t)area,
                                  (int64_t)(uintptr_t)vel, (int64_t)(uintptr_t)s};
     if (off_host) okey.insert(okey.end(), off_host, off_host + ninst + 1);
@@ -529,8 +544,8 @@ int eval_graph(sts_ctx* c, const double* pos, const double* zeta, const double* 
             set_error("sts_tree_velocity: a device-side wait for staged sources gave up");
             return STS_ERR_TIMEOUT;
         }
-        c->have_tree = c->have_lists = true;
-        c->have_dual = false;
+        c->have_tree = true;
+        mark_replayed_lists(c, p->theta);
         c->nnodes = -1;
         if (over == 0) return STS_OK;
         STS_CUDA(cudaGraphExecDestroy(c->ev_exec));
@@ -624,6 +639,10 @@ int sts_create(sts_ctx** out)
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int64_t));
     if (e == cudaSuccess) e = c->dc.reserve(sts::kDcSize);
     if (e == cudaSuccess) e = cudaMemset(c->dc.p, 0, sts::kDcSize * sizeof(int64_t));
+    // inspection counters and the dual traversal's counters: allocated once here, so that
+    // inspecting a context between graph replays moves no buffer the recordings use
+    if (e == cudaSuccess) e = c->d_stats.reserve(8);
+    if (e == cudaSuccess) e = c->dual_cnt.reserve(128);
     if (e != cudaSuccess) {
         set_error("sts_create: %s", cudaGetErrorString(e));
         delete c;
@@ -817,12 +836,19 @@ int sts_dual_export(sts_ctx* ctx, int32_t kind, int64_t* npairs, int32_t* tgt, i
         set_error("sts_dual_export: no dual lists (call sts_velocity_dual first)");
         return STS_ERR_STATE;
     }
-    const int64_t P = ctx->dual_n[kind];
-    if (npairs) *npairs = P;
-    cudaStream_t s = S(stream);
-    if (tgt && P) STS_CUDA(cudaMemcpyAsync(tgt, ctx->dual_t[kind].p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    if (src && P) STS_CUDA(cudaMemcpyAsync(src, ctx->dual_s[kind].p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
+    return dual_export(ctx, kind, npairs, tgt, src, S(stream));
+}
+
+int sts_set_traversal(sts_ctx* ctx, int32_t dual)
+{
+    int rc = check_ctx(ctx, "sts_set_traversal");
+    if (rc) return rc;
+    if (dual != 0 && dual != 1) {
+        set_error("sts_set_traversal: dual must be 0 (target-leaf lists) or 1 (dual traversal), got %d", dual);
+        return STS_ERR_ARG;
+    }
+    ctx->use_dual = dual != 0;
     return STS_OK;
 }
 
@@ -838,6 +864,7 @@ int sts_dual_stats(sts_ctx* ctx, int32_t degree, int64_t* stats, void* stream)
         set_error("sts_dual_stats: no dual lists (call sts_velocity_dual first)");
         return STS_ERR_STATE;
     }
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     return dual_stats(ctx, degree, stats, S(stream));
 }
 
@@ -904,10 +931,11 @@ int sts_tree_info(sts_ctx* ctx, int64_t* info, void* stream)
     info[1] = ctx->nnodes;
     info[2] = ctx->nleaves;
     info[3] = ctx->deepest;
-    info[4] = ctx->have_lists ? ctx->nfar : 0;
-    info[5] = ctx->have_lists ? ctx->nnear : 0;
+    const bool lists = ctx->have_lists || ctx->have_dual;  // leaf lists (the dual's PP / PC)
+    info[4] = lists ? ctx->nfar : 0;
+    info[5] = lists ? ctx->nnear : 0;
     info[6] = ctx->nclusters;
-    info[7] = ctx->have_lists ? ctx->ntasks : 0;
+    info[7] = lists ? ctx->ntasks : 0;
     return STS_OK;
 }
 

@@ -449,9 +449,11 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
              const float4* __restrict__ tgt32, const double4* __restrict__ tgt64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
              double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
-             unsigned long long* __restrict__ queue, int* __restrict__ status)
+             unsigned long long* __restrict__ queue, int* __restrict__ status, const int64_t* __restrict__ over)
 {
     extern __shared__ __align__(16) EvalSmem sbuf[];  // kEvalWarps of them
+    // a recorded step whose lists outgrew their capacities evaluates nothing (the host redoes it)
+    if (*over) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);  // a recorded step whose tasks overflowed is redone
     if (lane == 0) {
@@ -602,9 +604,10 @@ k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
             const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
             const double4* __restrict__ src64, const double4* __restrict__ tgt64, const int32_t* __restrict__ perm,
             double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
-            unsigned long long* __restrict__ queue)
+            unsigned long long* __restrict__ queue, const int64_t* __restrict__ over)
 {
     __shared__ double4 sbuf[kEvalWarps64][kStage];
+    if (*over) return;  // lists past their recorded capacities: the host redoes the step
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);
     for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane))
@@ -819,7 +822,8 @@ int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
     phase_begin(c, kPhEval, s);
     (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
                                                        c->near_ent.p, c->prx64.p, M, c->src64.p, c->src64.p,
-                                                       c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue),
+                                                       c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue,
+                                                       c->dc.p + kDcOver),
      note_launch());
     phase_end(c, kPhEval, s);
     STS_LAUNCH_CHECK();
@@ -861,7 +865,7 @@ int eval_blocks(sts_ctx* c)
 
 // corr: FP64 close-pair scratch of at least 3 * ls.ntargets doubles (mixed precision).
 int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, double tau, DevBuf<double>& corrbuf,
-                   double* vel, cudaStream_t s)
+                   double* vel, cudaStream_t s, int phase = kPhEval)
 {
     const int M = nbasis(degree);
     if (ls.ntasks <= 0) return STS_OK;
@@ -871,12 +875,13 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
     STS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
     if (precision == STS_FP64) {
         const unsigned g = (unsigned)std::min<int64_t>(blocks(ls.ntasks, kEvalWarps64), c->eval_blocks_fp64);
-        phase_begin(c, kPhEval, s);
+        phase_begin(c, phase, s);
         (k_eval_fp64<false><<<g, kEvalWarps64 * 32, 0, s>>>(ls.tasks, ls.far_off, ls.far_ent, ls.near_coff,
                                                             ls.near_ent, c->prx64.p, M, c->src64.p, ls.tgt64,
-                                                            ls.perm, vel, ls.ntasks_d, ls.ntasks, queue),
+                                                            ls.perm, vel, ls.ntasks_d, ls.ntasks, queue,
+                                                            c->dc.p + kDcOver),
          note_launch());
-        phase_end(c, kPhEval, s);
+        phase_end(c, phase, s);
     } else {
         double* corr = nullptr;
         // |x - y|^2 / 2 <= 2 on the unit sphere: larger tau changes nothing, and the bound keeps
@@ -891,12 +896,13 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
         const float tau2 = corr ? (float)(2.0 * tau) : 0.f;
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
         const unsigned g = (unsigned)std::min<int64_t>(blocks(ls.ntasks, kEvalWarps), c->eval_blocks_mixed);
-        phase_begin(c, kPhEval, s);
+        phase_begin(c, phase, s);
         (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
              ls.tasks, ls.far_off, ls.far_ent, ls.near_coff, ls.near_ent, c->prx32.p, M, c->src32.p, c->src64.p,
-             ls.tgt32, ls.tgt64, ls.perm, tau2, tau_r, corr, vel, ls.ntasks_d, ls.ntasks, queue, c->d_status),
+             ls.tgt32, ls.tgt64, ls.perm, tau2, tau_r, corr, vel, ls.ntasks_d, ls.ntasks, queue, c->d_status,
+             c->dc.p + kDcOver),
          note_launch());
-        phase_end(c, kPhEval, s);
+        phase_end(c, phase, s);
     }
     STS_LAUNCH_CHECK();
     return STS_OK;
@@ -924,51 +930,6 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
 // ------------------------------------------------------------------------ dual: downward
 namespace {
 
-// Coefficients of the interpolating polynomial of every target cluster (Sec. 3.2 applied to
-// the velocity): with proxy points x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|,
-// the spherical barycentric coordinates of x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref
-// (the basis is homogeneous of degree d) and V_T c = U gives c = V_ref^-1 diag(rho^d) U.
-// U: the velocity at the proxy points (cvel).  One CTA per cluster, a fixed grid striding.
-__global__ void k_down_coef(int64_t nclu, const uint8_t* __restrict__ has, const int32_t* __restrict__ cnode,
-                            const double* __restrict__ geom, const double* __restrict__ beta,
-                            const double* __restrict__ vinv, int d, int M, const double* __restrict__ cvel,
-                            double* __restrict__ coef)
-{
-    __shared__ double u[3 * kMaxM];
-    for (int64_t c = blockIdx.x; c < nclu; c += gridDim.x) {
-        if (!has[c]) continue;
-        const double* g = geom + 13 * (int64_t)cnode[c];
-        __syncthreads();  // u of the previous cluster is no longer read
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
-            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
-            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
-            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
-            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
-            double rd = 1.0;
-            for (int e = 0; e < d; e++) rd *= rho;
-            const double* v = cvel + 3 * (c * M + m);
-            u[3 * m] = rd * v[0];
-            u[3 * m + 1] = rd * v[1];
-            u[3 * m + 2] = rd * v[2];
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int m = 0; m < M; m++) {
-                const double w = vinv[k * M + m];
-                ax += w * u[3 * m];
-                ay += w * u[3 * m + 1];
-                az += w * u[3 * m + 2];
-            }
-            double* o = coef + 3 * (c * M + k);
-            o[0] = ax;
-            o[1] = ay;
-            o[2] = az;
-        }
-    }
-}
-
 // Plain FP64 products and sums in a fixed order (no contraction): the barycentric coordinates
 // below come out exactly as a plain IEEE evaluation of the same formula.
 __device__ __forceinline__ double dot3_rn(double ax, double ay, double az, double bx, double by, double bz)
@@ -982,51 +943,127 @@ __device__ __forceinline__ void cross3_rn(const double* a, const double* b, doub
     c[2] = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
 }
 
-// Adds to every particle the interpolants of its cluster ancestors that are CP / CC targets
-// (its own leaf included when that is a cluster): b = the particle's spherical barycentric
-// coordinates in the ancestor (Sec. 3.2, y = b1 v1 + b2 v2 + b3 v3 by Cramer's rule:
-// b_i = (y . n_i) / D, n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1), B_k(b) =
-// b1^a b2^b b3^c in the order a = d..0, b = d - a..0, sum_k B_k(b) c_k.  One thread per
-// particle (sorted slot).
+// The interpolating polynomial of triangle g (vertices g[0..8]) with coefficients cf[M][3] at x:
+// b = the spherical barycentric coordinates of x (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3 by
+// Cramer's rule: b_i = (x . n_i) / D, n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1),
+// sum_k B_k(b) c_k with B_k(b) = b1^a b2^b b3^c in the order a = d..0, b = d - a..0.
+__device__ __forceinline__ void eval_interp(const double* __restrict__ g, const double* __restrict__ cf, int d,
+                                            double xx, double xy, double xz, double& ax, double& ay, double& az)
+{
+    double n1[3], n2[3], n3[3];
+    cross3_rn(g + 3, g + 6, n1);
+    cross3_rn(g + 6, g, n2);
+    cross3_rn(g, g + 3, n3);
+    const double D = dot3_rn(g[0], g[1], g[2], n1[0], n1[1], n1[2]);
+    const double b1 = __ddiv_rn(dot3_rn(xx, xy, xz, n1[0], n1[1], n1[2]), D);
+    const double b2 = __ddiv_rn(dot3_rn(xx, xy, xz, n2[0], n2[1], n2[2]), D);
+    const double b3 = __ddiv_rn(dot3_rn(xx, xy, xz, n3[0], n3[1], n3[2]), D);
+    double p1[kMaxDegree + 1], p2[kMaxDegree + 1], p3[kMaxDegree + 1];
+    p1[0] = p2[0] = p3[0] = 1.0;
+    for (int e = 1; e <= d; e++) {
+        p1[e] = p1[e - 1] * b1;
+        p2[e] = p2[e - 1] * b2;
+        p3[e] = p3[e - 1] * b3;
+    }
+    int k = 0;
+    for (int ea = d; ea >= 0; ea--)
+        for (int eb = d - ea; eb >= 0; eb--, k++) {
+            const double B = (p1[ea] * p2[eb]) * p3[d - ea - eb];
+            ax += B * cf[3 * k];
+            ay += B * cf[3 * k + 1];
+            az += B * cf[3 * k + 2];
+        }
+}
+
+// Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the velocity at the target
+// cluster's proxy points, interpolated over the cluster), passed down the tree.  U_T = the
+// velocity of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs) plus
+// the interpolant of its parent, which already holds every ancestor's, evaluated there.  A
+// degree-d polynomial in one triangle's barycentric coordinates is one in any other's (both are
+// the homogeneous degree-d polynomials in x), so interpolating the parent's at T's M proxy
+// points reproduces it exactly: a particle then evaluates its lowest cluster's interpolant only,
+// which equals the sum of all its ancestors' interpolants.  Coefficients: with proxy points
+// x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|, the barycentric coordinates of
+// x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref and c = V_ref^-1 diag(rho^d) U.
+// acc[c]: cluster c holds an interpolant.  One CTA per cluster of the level.
+__global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ parent,
+                             const int32_t* __restrict__ cluster_slot, const uint8_t* __restrict__ has,
+                             uint8_t* __restrict__ acc, const double* __restrict__ geom,
+                             const double4* __restrict__ prx64, const double* __restrict__ beta,
+                             const double* __restrict__ vinv, int d, int M, const double* __restrict__ cvel,
+                             double* __restrict__ coef)
+{
+    __shared__ double u[3 * kMaxM];
+    const int64_t lb = lvl[l], le = lvl[l + 1];
+    for (int64_t p = lb + blockIdx.x; p < le; p += gridDim.x) {
+        const int32_t cs = cluster_slot[p];
+        if (cs < 0) continue;
+        const int32_t par = parent[p];
+        const int32_t ps = par >= 0 ? cluster_slot[par] : -1;
+        const bool from_parent = ps >= 0 && acc[ps];
+        const bool own = has[cs] != 0;
+        if (threadIdx.x == 0) acc[cs] = (own || from_parent) ? 1 : 0;
+        if (!own && !from_parent) continue;
+        const double* g = geom + 13 * p;
+        __syncthreads();  // u of the previous cluster is no longer read
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            double vx = 0.0, vy = 0.0, vz = 0.0;
+            if (own) {
+                const double* v = cvel + 3 * ((int64_t)cs * M + m);
+                vx = v[0];
+                vy = v[1];
+                vz = v[2];
+            }
+            if (from_parent) {
+                const double4 x = prx64[(int64_t)cs * M + m];
+                eval_interp(geom + 13 * (int64_t)par, coef + 3 * (int64_t)ps * M, d, x.x, x.y, x.z, vx, vy, vz);
+            }
+            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
+            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
+            double rd = 1.0;
+            for (int e = 0; e < d; e++) rd *= rho;
+            u[3 * m] = rd * vx;
+            u[3 * m + 1] = rd * vy;
+            u[3 * m + 2] = rd * vz;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            for (int m = 0; m < M; m++) {
+                const double w = vinv[k * M + m];
+                ax += w * u[3 * m];
+                ay += w * u[3 * m + 1];
+                az += w * u[3 * m + 2];
+            }
+            double* o = coef + 3 * ((int64_t)cs * M + k);
+            o[0] = ax;
+            o[1] = ay;
+            o[2] = az;
+        }
+    }
+}
+
+// Adds to every particle (sorted slot) the interpolant of its lowest cluster: its leaf when
+// that is a cluster (at the depth limit), else the leaf's parent.
 __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
-                           const uint8_t* __restrict__ has, const double* __restrict__ geom,
+                           const uint8_t* __restrict__ acc, const double* __restrict__ geom,
                            const double4* __restrict__ src64, const int32_t* __restrict__ perm, int d, int M,
                            const double* __restrict__ coef, double* __restrict__ vel)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    int32_t a = leaves[slot_leaf[j]];
+    if (cluster_slot[a] < 0) a = parent[a];
+    if (a < 0) return;  // a root leaf: no cluster above it
+    const int32_t cs = cluster_slot[a];
+    if (cs < 0 || !acc[cs]) return;
     const double4 x = src64[j];
     double ax = 0.0, ay = 0.0, az = 0.0;
-    double p1[kMaxDegree + 1], p2[kMaxDegree + 1], p3[kMaxDegree + 1];
-    for (int32_t a = leaves[slot_leaf[j]]; a >= 0; a = parent[a]) {
-        const int32_t cs = cluster_slot[a];
-        if (cs < 0 || !has[cs]) continue;
-        const double* g = geom + 13 * (int64_t)a;
-        double n1[3], n2[3], n3[3];
-        cross3_rn(g + 3, g + 6, n1);
-        cross3_rn(g + 6, g, n2);
-        cross3_rn(g, g + 3, n3);
-        const double D = dot3_rn(g[0], g[1], g[2], n1[0], n1[1], n1[2]);
-        const double b1 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n1[0], n1[1], n1[2]), D);
-        const double b2 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n2[0], n2[1], n2[2]), D);
-        const double b3 = __ddiv_rn(dot3_rn(x.x, x.y, x.z, n3[0], n3[1], n3[2]), D);
-        p1[0] = p2[0] = p3[0] = 1.0;
-        for (int e = 1; e <= d; e++) {
-            p1[e] = p1[e - 1] * b1;
-            p2[e] = p2[e - 1] * b2;
-            p3[e] = p3[e - 1] * b3;
-        }
-        const double* cf = coef + 3 * ((int64_t)cs * M);
-        int k = 0;
-        for (int ea = d; ea >= 0; ea--)
-            for (int eb = d - ea; eb >= 0; eb--, k++) {
-                const double B = (p1[ea] * p2[eb]) * p3[d - ea - eb];
-                ax += B * cf[3 * k];
-                ay += B * cf[3 * k + 1];
-                az += B * cf[3 * k + 2];
-            }
-    }
+    eval_interp(geom + 13 * (int64_t)a, coef + 3 * (int64_t)cs * M, d, x.x, x.y, x.z, ax, ay, az);
     const int64_t i = perm[j];
     vel[3 * i] += ax;
     vel[3 * i + 1] += ay;
@@ -1040,18 +1077,23 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     // PP and PC: the leaf lists hold the dual traversal's pairs of the target leaves
     int rc = evaluate(c, degree, precision, tau, vel, s);
     if (rc) return rc;
-    const int64_t C = c->nclusters;
-    if (C == 0 || (c->dual_n[2] == 0 && c->dual_n[3] == 0)) return STS_OK;
+    const bool cap = c->capturing;
+    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    if (C == 0 || c->n < 2) return STS_OK;
+    if (!cap && c->dual_n[2] == 0 && c->dual_n[3] == 0) return STS_OK;  // no CP or CC pairs
     RefTable* ref = get_ref(c, degree);
     if (!ref) return STS_ERR_CUDA;
     const int M = ref->M;
     if ((rc = cluster_tasks(c, M, s))) return rc;
-    STS_CUDA(c->cvel.reserve(3 * C * M + 3));
-    STS_CUDA(c->cdown.reserve(3 * C * M + 3));
+    if (!cap) {
+        STS_CUDA(c->cvel.reserve(3 * C * M + 3));
+        STS_CUDA(c->cdown.reserve(3 * C * M + 3));
+        STS_CUDA(c->cacc.reserve(C + 1));
+    }
     // CP and CC: the velocity at the proxy points of the target clusters
     ListSet ls;
     ls.tasks = c->ctasks.p;
-    ls.ntasks_d = c->dual_cnt.p + 5;
+    ls.ntasks_d = cluster_task_count(c);
     ls.ntasks = c->nctasks;
     ls.far_off = c->cfar_off.p;
     ls.near_coff = c->cnear_coff.p;
@@ -1061,16 +1103,21 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     ls.tgt64 = c->prx64.p;
     ls.perm = nullptr;
     ls.ntargets = C * M;
-    if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s))) return rc;
-    // interpolation down to the particles
-    (k_down_coef<<<(unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms), 64, 0, s>>>(
-         C, c->chas.p, c->cluster_node.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M, c->cvel.p,
-         c->cdown.p),
-     note_launch());
+    phase_begin(c, kPhCluster, s);
+    if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s, -1))) return rc;
+    // interpolants passed down level by level, then evaluated at the particles
+    const int levels = (cap ? c->plan.depth : (int)c->deepest) + 1;
+    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
+    for (int l = 0; l < levels; l++)
+        (k_down_level<<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
+                                        c->cacc.p, c->nd_geom.p, c->prx64.p, ref->d_beta.p, ref->d_vinv.p, degree,
+                                        M, c->cvel.p, c->cdown.p),
+         note_launch());
     (k_downward<<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                   c->cluster_slot.p, c->chas.p, c->nd_geom.p, c->src64.p, c->perm.p,
+                                                   c->cluster_slot.p, c->cacc.p, c->nd_geom.p, c->src64.p, c->perm.p,
                                                    degree, M, c->cdown.p, vel),
      note_launch());
+    phase_end(c, kPhCluster, s);
     STS_LAUNCH_CHECK();
     return STS_OK;
 }

@@ -120,7 +120,7 @@ struct Task {
     int32_t leaf, t0, nt, S;
 };
 
-enum Phase { kPhBuild = 0, kPhSort, kPhLists, kPhPrep, kPhUpward, kPhEval, kPhDirect, kNumPhases };
+enum Phase { kPhBuild = 0, kPhSort, kPhLists, kPhPrep, kPhUpward, kPhEval, kPhDirect, kPhCluster, kNumPhases };
 
 // Device counters (ctx->dc, int64): every kernel reads its element counts from here, so no
 // launch depends on a host-side count and a whole RK4 step can be recorded as a graph.
@@ -140,6 +140,8 @@ struct Plan {
     int64_t n = -1;
     int ninst = 0, leaf_size = 0, max_level = 0, depth = 0;
     int64_t nodes = 0, up_tasks = 0, far = 0, near = 0, chunks = 0, tasks = 0, clusters = 0, leaves = 0;
+    // dual traversal: largest frontier, terminal pairs, and per kind pairs and near chunks
+    int64_t dual_front = 0, dual_terms = 0, dual_pairs[4] = {0, 0, 0, 0}, dual_chunks[2] = {0, 0};
 };
 
 }  // namespace sts
@@ -237,28 +239,34 @@ struct sts_ctx {
     int list_degree = -1;                // degree the far entries' slots refer to
 
     // ---- dual traversal (Sec. 3.4) ---------------------------------------------------
-    // Pairs (target node, source node) of the four kinds PP, PC, CP, CC, each sorted by target
-    // then source.  While have_dual holds, the leaf lists above hold the PP (near) and PC (far)
-    // pairs of the target leaves; the cluster lists below hold the CP (near) and CC (far) pairs
-    // of the target clusters, whose targets are the clusters' proxy points.
+    // Pairs (target node, source node) of the four kinds PP, PC, CP, CC, sorted by kind, target
+    // key (depth-first leaf index for PP / PC, cluster slot for CP / CC), then source.  While
+    // have_dual holds, the leaf lists above hold the PP (near) and PC (far) pairs of the target
+    // leaves; the cluster lists below hold the CP (near) and CC (far) pairs of the target
+    // clusters, whose targets are the clusters' proxy points.  Every count lives on the device
+    // (dual_cnt), so the whole traversal can be recorded in a graph.
     bool have_dual = false;
+    bool use_dual = false;               // sts_set_traversal: tree-code velocities by the dual traversal
     double dual_theta = 0.0;
-    sts::DevBuf<int32_t> dual_t[4], dual_s[4];
-    int64_t dual_n[4] = {0, 0, 0, 0};
-    sts::DevBuf<int32_t> dual_ft, dual_fs, dual_gt, dual_gs;  // pair frontiers (current, next)
+    int64_t dual_n[4] = {-1, -1, -1, -1};  // host copies of the pair counts (-1: on the device only)
+    sts::DevBuf<int32_t> dual_ft, dual_fs, dual_gt, dual_gs;  // pair frontiers (ping-pong)
+    sts::DevBuf<int32_t> dual_tt, dual_ts;  // terminal pairs as found
+    sts::DevBuf<uint8_t> dual_tk;           // their kinds
+    sts::DevBuf<int32_t> dual_t, dual_s;    // terminal pairs sorted
     sts::DevBuf<uint32_t> dual_key, dual_ktmp;
-    sts::DevBuf<int32_t> dual_vtmp;
-    sts::DevBuf<int64_t> dual_cnt;       // [8] terminal counts per kind, next frontier size
-    sts::DevBuf<int64_t> dual_scan;      // chunk scan of the near pairs
+    sts::DevBuf<int32_t> dual_perm, dual_ptmp, dual_chunk;
+    sts::DevBuf<int64_t> dual_cnt;       // counters of the traversal (layout in sts_tree.cu)
+    sts::DevBuf<int64_t> dual_scan;      // chunk offsets of the sorted pairs
     sts::DevBuf<int64_t> cfar_off, cnear_off, cnear_coff;  // [C + 1] per target cluster slot
     sts::DevBuf<sts::FarEntry> cfar_ent;
     sts::DevBuf<sts::NearEntry> cnear_ent;
     sts::DevBuf<sts::Task> ctasks;
-    int64_t nctasks = 0, ncnear_chunks = 0;
+    int64_t nctasks = 0;
     sts::DevBuf<double> cvel;            // [C, M, 3] velocity at the proxy points of target clusters
     sts::DevBuf<double> ccorr;           // [C, M, 3] FP64 close-pair sums of the proxy targets
     sts::DevBuf<double> cdown;           // [C, M, 3] coefficients of the interpolating polynomials
     sts::DevBuf<uint8_t> chas;           // [C] the cluster is the target of CP or CC pairs
+    sts::DevBuf<uint8_t> cacc;           // [C] the cluster holds an interpolant (its own or an ancestor's)
 
     // ---- direct sum scratch ------------------------------------------------------------
     sts::DevBuf<double4> dsrc64;
@@ -297,23 +305,34 @@ void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scr
                         cudaStream_t s, const int64_t* n_dev = nullptr);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.  Result in
 // key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n).
+// n_dev: optional device count (n is then its upper bound and sizes the grids).
 int64_t radix_hist_size(int64_t n);
 void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* val_tmp,
                       int64_t n, int bits, uint32_t* hist, int64_t* scan_out,
-                      int64_t* scan_scratch_buf, cudaStream_t s);
+                      int64_t* scan_scratch_buf, cudaStream_t s, const int64_t* n_dev = nullptr);
 
 // ---- tree and lists (sts_tree.cu) ----------------------------------------------------
 // inst_off: device offsets [ninst + 1] of the instances (NULL: one instance)
 int tree_build(sts_ctx* ctx, const double* pos, int64_t n, const int64_t* inst_off, int ninst,
                int leaf_size, int max_level, cudaStream_t s);
 int build_lists(sts_ctx* ctx, double theta, cudaStream_t s);
-// Dual traversal (Sec. 3.4): the four pair lists, the leaf lists of PP and PC pairs and the
-// cluster lists of CP and CC pairs with their evaluation tasks.  Synchronises `s`.
+// Dual traversal (Sec. 3.4): the four pair lists, the leaf lists of PP and PC pairs with the
+// leaves' evaluation tasks, and the cluster lists of CP and CC pairs.  Eager: synchronises `s`
+// once (counts and overflow; buffers grown and the traversal redone on overflow).  Recording:
+// no host access; an overflow sets bit 4 of the device overflow word.
 int build_dual(sts_ctx* ctx, double theta, cudaStream_t s);
+// Buffers of the dual traversal for recording it (the plan's sizes with slack).
+int reserve_dual_for_capture(sts_ctx* ctx, int degree, cudaStream_t s);
+// Host copies of the dual pair counts after a recorded step ran.
+int refresh_dual_counts(sts_ctx* ctx, cudaStream_t s);
 // Pair counts of the dual lists: stats[0..3] = PP pairs (j != i), PC, CP, CC interactions.
 int dual_stats(sts_ctx* ctx, int degree, int64_t* stats, cudaStream_t s);
-// Evaluation tasks of the clusters that are targets of CP or CC pairs, and their has flags.
+// Evaluation tasks of the clusters that are targets of CP or CC pairs, and their has flags;
+// cluster_task_count: the device count of those tasks.
 int cluster_tasks(sts_ctx* ctx, int M, cudaStream_t s);
+const int64_t* cluster_task_count(sts_ctx* ctx);
+// Sorted pairs of one kind (0 PP, 1 PC, 2 CP, 3 CC) to host arrays (either may be NULL).
+int dual_export(sts_ctx* ctx, int kind, int64_t* npairs, int32_t* tgt, int32_t* src, cudaStream_t s);
 // node-table capacity (contents are not kept)
 int reserve_tree_nodes(sts_ctx* ctx, int64_t nodes, cudaStream_t s);
 // out[0..3] = *a, *b, *c, *d (0 for NULL), out[4] = status word: one host read for all.

@@ -103,9 +103,10 @@ constexpr int kRadixWarps = 8;
 constexpr int kRadixRounds = 8;
 constexpr int kRadixTile = kRadixWarps * kRadixRounds * 32;  // 2048 items per block
 
-__global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int shift,
-                             int64_t nb, int32_t* __restrict__ hist)
+__global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, const int64_t* __restrict__ n_dev,
+                             int shift, int64_t nb, int32_t* __restrict__ hist)
 {
+    if (n_dev) n = min(*n_dev, n);
     __shared__ int32_t h[256];
     for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
     __syncthreads();
@@ -122,9 +123,10 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ key, int64_t n, int sh
 // [w * 256, (w + 1) * 256) of the tile and walks them in rounds of 32 consecutive items.
 __global__ void __launch_bounds__(kRadixWarps * 32)
 k_radix_scatter(const uint32_t* __restrict__ key, const int32_t* __restrict__ val, int64_t n,
-                int shift, int64_t nb, const int64_t* __restrict__ scanned,
+                const int64_t* __restrict__ n_dev, int shift, int64_t nb, const int64_t* __restrict__ scanned,
                 uint32_t* __restrict__ key_out, int32_t* __restrict__ val_out)
 {
+    if (n_dev) n = min(*n_dev, n);
     __shared__ int32_t wcount[kRadixWarps][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
@@ -225,7 +227,7 @@ int64_t radix_hist_size(int64_t n) { return 256 * ((n + kRadixTile - 1) / kRadix
 
 void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* val_tmp, int64_t n,
                       int bits, uint32_t* hist, int64_t* scan_out, int64_t* scan_scratch_buf,
-                      cudaStream_t s)
+                      cudaStream_t s, const int64_t* n_dev)
 {
     if (n <= 1) return;
     const int64_t nb = (n + kRadixTile - 1) / kRadixTile;
@@ -234,9 +236,10 @@ void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* v
     int32_t *va = val, *vb = val_tmp;
     for (int p = 0; p < passes; p++) {
         const int shift = 8 * p;
-        (k_radix_hist<<<(unsigned)nb, 256, 0, s>>>(ka, n, shift, nb, (int32_t*)hist), note_launch());
+        (k_radix_hist<<<(unsigned)nb, 256, 0, s>>>(ka, n, n_dev, shift, nb, (int32_t*)hist), note_launch());
         exclusive_scan_i32((const int32_t*)hist, scan_out, 256 * nb, scan_scratch_buf, s);
-        (k_radix_scatter<<<(unsigned)nb, kRadixWarps * 32, 0, s>>>(ka, va, n, shift, nb, scan_out, kb, vb), note_launch());
+        (k_radix_scatter<<<(unsigned)nb, kRadixWarps * 32, 0, s>>>(ka, va, n, n_dev, shift, nb, scan_out, kb, vb),
+         note_launch());
         uint32_t* tk = ka;
         ka = kb;
         kb = tk;

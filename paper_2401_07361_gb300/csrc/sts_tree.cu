@@ -1010,19 +1010,32 @@ __global__ void k_gather(const int64_t* a, const int64_t* b, const int64_t* c, c
 // terminal of its kind by the two particle counts against N_T (PP both at most N_T, PC only
 // the source above, CP only the target above, CC both above); a failing pair of two leaves
 // is PP; otherwise the triangle with more particles (the target on a tie; never a leaf) is
-// replaced by its children, which form the next frontier's pairs.  The terminals are
-// appended in any order and sorted afterwards, so the lists do not depend on the schedule.
+// replaced by its children, which form the next frontier's pairs.  Terminals are appended in
+// any order and sorted afterwards (by kind, target, source), so nothing depends on the
+// schedule.  Every count stays on the device: a fixed number of level launches (enough for
+// the tree's depth) reads its frontier size from the counters, and a write past a capacity
+// is dropped and flagged, after which the host grows the buffers and runs the traversal again.
 enum { kPP = 0, kPC = 1, kCP = 2, kCC = 3 };
 
-struct DualOut {
-    int32_t* t[4];
-    int32_t* s[4];
-    int64_t cap[4];
-};
+// dual_cnt layout (int64)
+constexpr int kDuTerms = 0;      // terminal pairs found (every attempt counted)
+constexpr int kDuP = 1;          // terminal pairs kept: min(found, capacity)
+constexpr int kDuStart = 2;      // [2 .. 6]: first sorted pair of each kind, then the end
+constexpr int kDuChunks = 8;     // [8] near chunks of PP, [9] of CP
+constexpr int kDuFrontMax = 10;  // largest frontier asked for
+constexpr int kDuOver = 11;      // overflow bits (eager runs)
+constexpr int kDuCTasks = 12;    // evaluation tasks of the target clusters
+constexpr int kDuFront = 16;     // [16 + l]: pairs entering level l
+constexpr int kDuMaxLevels = 2 * kMaxLevel + 8;
+constexpr int kDuSize = kDuFront + kDuMaxLevels + 1;
+
+__device__ __forceinline__ bool near_kind(int k) { return k == kPP || k == kCP; }
+__device__ __forceinline__ bool leaf_kind(int k) { return k == kPP || k == kPC; }
 
 // The 20 x 20 root pairs of every instance (a target interacts with its own instance only).
 __global__ void k_dual_roots(const int32_t* __restrict__ face_node, int ninst, int32_t* __restrict__ ft,
-                             int32_t* __restrict__ fs, unsigned long long* __restrict__ cnt)
+                             int32_t* __restrict__ fs, int64_t fcap, int64_t* __restrict__ du,
+                             unsigned long long* __restrict__ over)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)ninst * 400) return;
@@ -1030,21 +1043,26 @@ __global__ void k_dual_roots(const int32_t* __restrict__ face_node, int ninst, i
     const int f1 = (int)(i % 400) / 20, f2 = (int)(i % 20);
     const int32_t t = face_node[20 * b + f1], s = face_node[20 * b + f2];
     if (t < 0 || s < 0) return;
-    const unsigned long long q = atomicAdd(cnt + 4, 1ull);
-    ft[q] = t;
-    fs[q] = s;
+    const int64_t q = (int64_t)atomicAdd((unsigned long long*)(du + kDuFront), 1ull);
+    if (q < fcap) {
+        ft[q] = t;
+        fs[q] = s;
+    } else {
+        atomicOr(over, 4ull);
+    }
 }
 
-// One level of the traversal: cnt[0..3] count the terminals per kind, cnt[4] the next
-// frontier.  Writes past a capacity are dropped; the host sees the counts, grows the buffers
-// and runs the level again from the same frontier.
-__global__ void k_dual_step(const int32_t* __restrict__ ft, const int32_t* __restrict__ fs, int64_t nf,
-                            double theta, int leaf_size, const double* __restrict__ geom,
-                            const float4* __restrict__ c32, const int32_t* __restrict__ leaf,
-                            const int32_t* __restrict__ first_child, const int32_t* __restrict__ nchild,
-                            const int32_t* __restrict__ count, int32_t* __restrict__ gt, int32_t* __restrict__ gs,
-                            int64_t gcap, DualOut out, unsigned long long* __restrict__ cnt)
+// Level l of the traversal: the pairs of frontier l (ft, fs) decided; terminals appended to
+// (tt, ts, tk), refined pairs to frontier l + 1 (gt, gs).
+__global__ void k_dual_level(int l, const int32_t* __restrict__ ft, const int32_t* __restrict__ fs,
+                             int32_t* __restrict__ gt, int32_t* __restrict__ gs, int64_t fcap, double theta,
+                             int leaf_size, const double* __restrict__ geom, const float4* __restrict__ c32,
+                             const int32_t* __restrict__ leaf, const int32_t* __restrict__ first_child,
+                             const int32_t* __restrict__ nchild, const int32_t* __restrict__ count,
+                             int32_t* __restrict__ tt, int32_t* __restrict__ ts, uint8_t* __restrict__ tk,
+                             int64_t tcap, int64_t* __restrict__ du, unsigned long long* __restrict__ over)
 {
+    const int64_t nf = min(du[kDuFront + l], fcap);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     const int32_t t = ft[i], s = fs[i];
@@ -1058,138 +1076,205 @@ __global__ void k_dual_step(const int32_t* __restrict__ ft, const int32_t* __res
         kind = kPP;
     }
     if (kind >= 0) {
-        const unsigned long long q = atomicAdd(cnt + kind, 1ull);
-        if ((int64_t)q < out.cap[kind]) {
-            out.t[kind][q] = t;
-            out.s[kind][q] = s;
+        const int64_t q = (int64_t)atomicAdd((unsigned long long*)(du + kDuTerms), 1ull);
+        if (q < tcap) {
+            tt[q] = t;
+            ts[q] = s;
+            tk[q] = (uint8_t)kind;
+        } else {
+            atomicOr(over, 4ull);
         }
         return;
     }
     const bool split_t = !lt && (ls || ct >= cs);
     const int32_t p = split_t ? t : s;
     const int32_t fc = first_child[p], nc = nchild[p];
-    const int64_t q = (int64_t)atomicAdd(cnt + 4, (unsigned long long)nc);
-    if (q + nc > gcap) return;
-    for (int32_t c = 0; c < nc; c++) {
+    const int64_t q = (int64_t)atomicAdd((unsigned long long*)(du + kDuFront + l + 1), (unsigned long long)nc);
+    atomicMax((unsigned long long*)(du + kDuFrontMax), (unsigned long long)(q + nc));
+    if (q + nc > fcap) atomicOr(over, 4ull);
+    // every slot below the capacity is written (the next level reads min(count, fcap) pairs),
+    // also those of a refinement that does not fit whole
+    for (int32_t c = 0; c < nc && q + c < fcap; c++) {
         gt[q + c] = split_t ? fc + c : t;
         gs[q + c] = split_t ? s : fc + c;
     }
 }
 
-// Sorting a kind's pairs by (target key, source): key = source, then (after a stable sort)
-// the target's key with the sources as values.  Target key: the depth-first leaf index for
-// leaf targets (PP, PC), the cluster slot for cluster targets (CP, CC).
-__global__ void k_dual_key_src(const int32_t* __restrict__ src, int64_t n, uint32_t* __restrict__ key)
+// After the last level: the traversal must have ended (an empty frontier), and the pairs kept
+// are the found ones up to the capacity.  Sort keys of the first pass: the source node.
+__global__ void k_dual_close(int levels, int64_t tcap, int64_t* __restrict__ du, unsigned long long* __restrict__ over)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) key[i] = (uint32_t)src[i];
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (du[kDuFront + levels] > 0) atomicOr(over, 4ull);  // deeper than the levels launched
+    du[kDuP] = min(du[kDuTerms], tcap);
 }
 
-__global__ void k_dual_key_tgt(uint32_t* __restrict__ key, const int32_t* __restrict__ tgt, int64_t n,
-                               const int32_t* __restrict__ start, const int32_t* __restrict__ slot_leaf,
-                               const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ src)
+__global__ void k_dual_keys_src(const int32_t* __restrict__ ts, const int64_t* __restrict__ du, int64_t cap,
+                                uint32_t* __restrict__ key, int32_t* __restrict__ perm)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    src[i] = (int32_t)key[i];
-    const int32_t t = tgt[i];
-    key[i] = (uint32_t)(cluster_slot ? cluster_slot[t] : slot_leaf[start[t]]);
+    if (i >= min(du[kDuP], cap)) return;
+    key[i] = (uint32_t)ts[i];
+    perm[i] = (int32_t)i;
 }
 
-__global__ void k_dual_key_back(const uint32_t* __restrict__ key, int64_t n, const int32_t* __restrict__ node_of,
-                                int32_t* __restrict__ tgt)
+// Second pass keys: kind << bits_t | target key (depth-first leaf index of a leaf target,
+// cluster slot of a cluster target).
+__global__ void k_dual_keys_tgt(const int32_t* __restrict__ tt, const uint8_t* __restrict__ tk,
+                                const int32_t* __restrict__ perm, const int64_t* __restrict__ du, int64_t cap,
+                                int bits_t, const int32_t* __restrict__ start, const int32_t* __restrict__ slot_leaf,
+                                const int32_t* __restrict__ cluster_slot, uint32_t* __restrict__ key)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tgt[i] = node_of[key[i]];
+    if (i >= min(du[kDuP], cap)) return;
+    const int32_t q = perm[i], t = tt[q];
+    const int k = tk[q];
+    const uint32_t tkey = (uint32_t)(leaf_kind(k) ? slot_leaf[start[t]] : cluster_slot[t]);
+    key[i] = ((uint32_t)k << bits_t) | tkey;
 }
 
-// off[k] = first pair whose key is >= k, for k in [0, K] (binary search in the sorted keys).
-__global__ void k_dual_offsets(const uint32_t* __restrict__ key, int64_t n, int64_t K, int64_t* __restrict__ off)
+// Sorted pairs, and the near chunks of every pair (0 for far kinds).
+__global__ void k_dual_gather(const int32_t* __restrict__ tt, const int32_t* __restrict__ ts,
+                              const int32_t* __restrict__ perm, const uint32_t* __restrict__ key, int bits_t,
+                              const int64_t* __restrict__ du, int64_t cap, const int32_t* __restrict__ count,
+                              int32_t* __restrict__ st, int32_t* __restrict__ ss, int32_t* __restrict__ chunks)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > K) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(du[kDuP], cap)) return;
+    const int32_t q = perm[i], s = ts[q];
+    st[i] = tt[q];
+    ss[i] = s;
+    chunks[i] = near_kind((int)(key[i] >> bits_t)) ? (count[s] + kStage - 1) / kStage : 0;
+}
+
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* __restrict__ key, int64_t n, uint32_t v)
+{
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if ((int64_t)key[mid] < k)
+        if (key[mid] < v)
             lo = mid + 1;
         else
             hi = mid;
     }
-    off[k] = lo;
+    return lo;
 }
 
-__global__ void k_dual_chunks(const int32_t* __restrict__ src, int64_t n, const int32_t* __restrict__ count,
-                              int32_t* __restrict__ chunks)
+// CSR offsets of the four kinds (blockIdx.y = kind): off[j] = first pair of target key j
+// within its kind, j = 0 .. K (leaves for PP / PC, clusters for CP / CC); near kinds also the
+// chunk offsets.  Thread 0 of each kind records the kind's first pair and its chunk total.
+struct DualCsr {
+    int64_t* off[4];
+    int64_t* coff[4];
+};
+
+__global__ void k_dual_csr(const uint32_t* __restrict__ key, const int64_t* __restrict__ scan, int bits_t,
+                           const int64_t* __restrict__ dc, int64_t lcap, int64_t ccap, DualCsr out,
+                           int64_t* __restrict__ du)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) chunks[i] = (count[src[i]] + kStage - 1) / kStage;
+    const int k = blockIdx.y;
+    const int64_t K = leaf_kind(k) ? min(dc[kDcLeaves], lcap) : min(dc[kDcClusters], ccap);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > K) return;
+    const int64_t P = du[kDuP];
+    const uint32_t base = (uint32_t)k << bits_t;
+    const int64_t ks = lower_bound_u32(key, P, base);
+    const int64_t o = lower_bound_u32(key, P, base + (uint32_t)j);
+    out.off[k][j] = o - ks;
+    if (near_kind(k)) out.coff[k][j] = scan[o] - scan[ks];
+    if (j == 0) {
+        du[kDuStart + k] = ks;
+        if (k == kCC) du[kDuStart + 4] = P;
+        if (near_kind(k)) {
+            const int64_t ke = lower_bound_u32(key, P, (uint32_t)(k + 1) << bits_t);  // k + 1 <= kCC
+            du[kDuChunks + (k == kPP ? 0 : 1)] = scan[ke] - scan[ks];
+        }
+    }
 }
 
-__global__ void k_dual_coff(const int64_t* __restrict__ off, int64_t K, const int64_t* __restrict__ scan,
-                            int64_t* __restrict__ coff)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k <= K) coff[k] = scan[off[k]];
-}
+// List entries of the sorted pairs: far (a source cluster's proxy block) or near (a source leaf
+// in chunks of at most kStage particles), with the FP32 centre offset c_s - c_t and, for near
+// entries, the lower bound on the distance between the two triangles' points.  Entries of kind
+// k go to its arrays at (pair index - the kind's first pair), chunks at their scanned offsets.
+struct DualFill {
+    FarEntry* far[2];     // PC, CC
+    NearEntry* near[2];   // PP, CP
+    int32_t* idx[2];      // source node ids: PP (near_idx), PC (far_idx)
+    int64_t far_cap[2], near_cap[2], idx_cap[2];
+};
 
-// List entries of sorted pairs: far (a source cluster's proxy block) or near (a source leaf in
-// chunks of at most kStage particles), with the FP32 centre offset c_s - c_t and, for near
-// entries, the lower bound on the distance between the two triangles' points.
-__global__ void k_dual_fill(bool is_far, const uint32_t* __restrict__ key, const int32_t* __restrict__ src,
-                            int64_t n, const int32_t* __restrict__ node_of, const double* __restrict__ geom,
+__global__ void k_dual_fill(const uint32_t* __restrict__ key, const int32_t* __restrict__ st,
+                            const int32_t* __restrict__ ss, const int64_t* __restrict__ scan, int bits_t,
+                            const int64_t* __restrict__ du, int64_t cap, const double* __restrict__ geom,
                             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-                            const int32_t* __restrict__ cluster_slot, const int64_t* __restrict__ chunk_scan,
-                            int32_t* __restrict__ idx, FarEntry* __restrict__ far_ent,
-                            NearEntry* __restrict__ near_ent)
+                            const int32_t* __restrict__ cluster_slot, DualFill out,
+                            unsigned long long* __restrict__ over)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t t = node_of[key[i]], s = src[i];
+    if (i >= min(du[kDuP], cap)) return;
+    const int k = (int)(key[i] >> bits_t);
+    const int64_t ks = du[kDuStart + k], local = i - ks;
+    const int32_t t = st[i], s = ss[i];
     const double* gt = geom + 13 * (int64_t)t;
     const double* gs = geom + 13 * (int64_t)s;
     const float dx = (float)__dsub_rn(gs[9], gt[9]);
     const float dy = (float)__dsub_rn(gs[10], gt[10]);
     const float dz = (float)__dsub_rn(gs[11], gt[11]);
-    if (idx) idx[i] = s;
-    if (is_far) {
+    if (leaf_kind(k)) {
+        const int a = k == kPP ? 0 : 1;
+        if (local < out.idx_cap[a])
+            out.idx[a][local] = s;
+        else
+            atomicOr(over, 4ull);
+    }
+    if (!near_kind(k)) {
+        const int a = k == kPC ? 0 : 1;
+        if (local >= out.far_cap[a]) {
+            atomicOr(over, 4ull);
+            return;
+        }
         FarEntry e;
         e.slot = cluster_slot[s];
         e.dx = dx;
         e.dy = dy;
         e.dz = dz;
-        far_ent[i] = e;
+        out.far[a][local] = e;
         return;
     }
+    const int a = k == kPP ? 0 : 1;
     NearEntry e;
     e.dx = dx;
     e.dy = dy;
     e.dz = dz;
     e.gap = near_gap(gt, gs);
     e.pad[0] = e.pad[1] = 0;
-    const int32_t st = start[s], ct = count[s];
-    int64_t q = chunk_scan[i];
+    const int32_t s0 = start[s], ct = count[s];
+    int64_t q = scan[i] - scan[ks];
+    if (q + (ct + kStage - 1) / kStage > out.near_cap[a]) {
+        atomicOr(over, 4ull);
+        return;
+    }
     for (int32_t c0 = 0; c0 < ct; c0 += kStage) {
-        e.start = st + c0;
+        e.start = s0 + c0;
         e.count = min(kStage, ct - c0);
-        near_ent[q++] = e;
+        out.near[a][q++] = e;
     }
 }
 
 // Evaluation tasks of the target clusters (targets: the M proxy points of cluster slot c,
 // rows c M .. c M + M - 1); has[c] = the cluster is the target of a CP or CC pair.
-__global__ void k_cluster_tasks(int64_t nclu, const int64_t* __restrict__ cfar_off,
+__global__ void k_cluster_tasks(const int64_t* __restrict__ dc, int64_t ccap, const int64_t* __restrict__ cfar_off,
                                 const int64_t* __restrict__ cnear_off, int M, uint8_t* __restrict__ has,
-                                Task* __restrict__ tasks, int64_t cap, unsigned long long* __restrict__ ntask,
-                                int* __restrict__ status)
+                                Task* __restrict__ tasks, int64_t cap, int64_t* __restrict__ du,
+                                unsigned long long* __restrict__ over)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nclu) return;
+    if (c >= min(dc[kDcClusters], ccap)) return;
     const bool h = cfar_off[c + 1] > cfar_off[c] || cnear_off[c + 1] > cnear_off[c];
     has[c] = h ? 1 : 0;
     if (!h) return;
     const int k = task_split(M);
-    const int64_t base = (int64_t)atomicAdd(ntask, (unsigned long long)k);
+    const int64_t base = (int64_t)atomicAdd((unsigned long long*)(du + kDuCTasks), (unsigned long long)k);
     int32_t t0 = 0;
     for (int i = 0; i < k; i++) {
         const int32_t m = M / k + (i < M % k ? 1 : 0);
@@ -1201,17 +1286,17 @@ __global__ void k_cluster_tasks(int64_t nclu, const int64_t* __restrict__ cfar_o
         if (base + i < cap)
             tasks[base + i] = tk;
         else
-            atomicOr(status, kStatusCapacity);
+            atomicOr(over, 4ull);
         t0 += m;
     }
 }
 
-// Interaction counts of the dual lists: st[0] PP pairs (j != i), st[1] PC target x proxy,
-// st[2] CP proxy x source, st[3] CC proxy x proxy; st[4] downward particle x M over the
-// clusters in has (launched over clusters with kind = 4).
-__global__ void k_dual_count(int kind, const int32_t* __restrict__ tgt, const int32_t* __restrict__ src, int64_t n,
-                             const int32_t* __restrict__ count, const uint8_t* __restrict__ has, int M,
-                             unsigned long long* __restrict__ st)
+// Interaction counts of the sorted dual pairs: st[kind] += PP pairs (j != i), PC target x
+// proxy, CP proxy x source, CC proxy x proxy; launched over clusters with kind = 4: downward
+// particle x M over the clusters in has.
+__global__ void k_dual_count(int kind, const int32_t* __restrict__ tgt, const int32_t* __restrict__ src,
+                             int64_t first, int64_t n, const int32_t* __restrict__ count,
+                             const uint8_t* __restrict__ has, int M, unsigned long long* __restrict__ st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long v = 0;
@@ -1220,7 +1305,7 @@ __global__ void k_dual_count(int kind, const int32_t* __restrict__ tgt, const in
         if (kind == 4) {
             v = has[i] ? (unsigned long long)count[tgt[i]] * mm : 0ull;  // tgt: cluster nodes
         } else {
-            const int32_t t = tgt[i], s = src[i];
+            const int32_t t = tgt[first + i], s = src[first + i];
             const unsigned long long ct = (unsigned long long)count[t], cs = (unsigned long long)count[s];
             if (kind == kPP)
                 v = ct * cs - (t == s ? ct : 0ull);
@@ -1313,6 +1398,10 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_CUDA(cudaMemcpyAsync(c->pos.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     STS_CUDA(c->nodeof.reserve(n));
     STS_CUDA(c->digit.reserve(n));
+    // the particle pass moves every particle of a node of the previous level to child[4 p +
+    // digit]; a particle whose root is a leaf never gets a digit written, so it must read a
+    // valid one (0: a leaf's child table points at the leaf itself)
+    if (n > 0) STS_CUDA(cudaMemsetAsync(c->digit.p, 0, n * sizeof(uint8_t), s));
     STS_CUDA(c->perm.reserve(n));
     STS_CUDA(c->perm_tmp.reserve(n));
     STS_CUDA(c->skey.reserve(n));
@@ -1542,73 +1631,154 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     return STS_OK;
 }
 
-// Sorts the pairs of one kind by (target key, source); afterwards c->dual_key holds the sorted
-// target keys and dual_t / dual_s the pairs.  leaf_targets: key = depth-first leaf index,
-// else the cluster slot.
-static int sort_dual_kind(sts_ctx* c, int kind, bool leaf_targets, cudaStream_t s)
+// Capacities of the dual traversal's buffers.
+struct DualCaps {
+    int64_t front, terms, pc, pp, pp_chunks, cc, cp, cp_chunks;
+    int levels;
+};
+
+static int bits_for(int64_t n)
 {
-    const int64_t P = c->dual_n[kind];
-    if (P == 0) return STS_OK;
-    const int T = 256;
-    const int64_t hs = radix_hist_size(P);
-    int64_t* scan_out = c->scan_tmp.p;
-    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
-    int bits_node = 0, bits_key = 0;
-    while (bits_node < 32 && ((int64_t)1 << bits_node) < c->nnodes) bits_node++;
-    const int64_t K = leaf_targets ? c->nleaves : c->nclusters;
-    while (bits_key < 32 && ((int64_t)1 << bits_key) < K) bits_key++;
-    (k_dual_key_src<<<blocks(P, T), T, 0, s>>>(c->dual_s[kind].p, P, c->dual_key.p), note_launch());
-    radix_sort_pairs(c->dual_key.p, c->dual_t[kind].p, c->dual_ktmp.p, c->dual_vtmp.p, P, bits_node, c->hist.p,
-                     scan_out, scan_scr, s);
-    (k_dual_key_tgt<<<blocks(P, T), T, 0, s>>>(c->dual_key.p, c->dual_t[kind].p, P, c->nd_start.p, c->slot_leaf.p,
-                                               leaf_targets ? nullptr : c->cluster_slot.p, c->dual_s[kind].p),
-     note_launch());
-    radix_sort_pairs(c->dual_key.p, c->dual_s[kind].p, c->dual_ktmp.p, c->dual_vtmp.p, P, bits_key, c->hist.p,
-                     scan_out, scan_scr, s);
-    (k_dual_key_back<<<blocks(P, T), T, 0, s>>>(c->dual_key.p, P,
-                                                leaf_targets ? c->leaves.p : c->cluster_node.p, c->dual_t[kind].p),
-     note_launch());
-    STS_LAUNCH_CHECK();
+    int b = 0;
+    while (b < 31 && ((int64_t)1 << b) < n) b++;
+    return b;
+}
+
+// Capacities from the plan (the largest sizes seen by eager runs), with slack; eager runs
+// start from estimates and grow on overflow.
+static DualCaps dual_caps(const sts_ctx* c, int64_t L, int64_t C, int64_t nodes)
+{
+    auto g = [](int64_t v, int64_t add) { return v + v / 4 + add; };
+    const Plan& pl = c->plan;
+    DualCaps k;
+    k.front = std::max(g(pl.dual_front, 1024), 400 * (int64_t)c->ninst + 4 * nodes);
+    k.terms = std::max(g(pl.dual_terms, 1024), 40 * L + 16 * C + 1024);
+    k.pp = std::max(g(pl.dual_pairs[kPP], 256), k.terms / 2);
+    k.pc = std::max(g(pl.dual_pairs[kPC], 256), 8 * L + 256);
+    k.cp = std::max(g(pl.dual_pairs[kCP], 256), 16 * C + 256);
+    k.cc = std::max(g(pl.dual_pairs[kCC], 256), 16 * C + 256);
+    k.pp_chunks = std::max(g(pl.dual_chunks[0], 256), k.pp);
+    k.cp_chunks = std::max(g(pl.dual_chunks[1], 256), k.cp);
+    k.levels = 0;
+    return k;
+}
+
+static int reserve_dual(sts_ctx* c, const DualCaps& k, int64_t L, int64_t C, int64_t nodes)
+{
+    STS_CUDA(c->dual_cnt.reserve(kDuSize + 8));
+    STS_CUDA(c->dual_ft.reserve(k.front));
+    STS_CUDA(c->dual_fs.reserve(k.front));
+    STS_CUDA(c->dual_gt.reserve(k.front));
+    STS_CUDA(c->dual_gs.reserve(k.front));
+    STS_CUDA(c->dual_tt.reserve(k.terms));
+    STS_CUDA(c->dual_ts.reserve(k.terms));
+    STS_CUDA(c->dual_tk.reserve(k.terms));
+    STS_CUDA(c->dual_t.reserve(k.terms));
+    STS_CUDA(c->dual_s.reserve(k.terms));
+    STS_CUDA(c->dual_key.reserve(k.terms));
+    STS_CUDA(c->dual_ktmp.reserve(k.terms));
+    STS_CUDA(c->dual_perm.reserve(k.terms));
+    STS_CUDA(c->dual_ptmp.reserve(k.terms));
+    STS_CUDA(c->dual_chunk.reserve(k.terms));
+    STS_CUDA(c->dual_scan.reserve(k.terms + 1));
+    const int64_t hs = radix_hist_size(k.terms);
+    STS_CUDA(c->hist.reserve(hs));
+    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(k.terms + 1) + scan_scratch(nodes + 1) +
+                                 64));
+    STS_CUDA(c->far_off.reserve(L + 1));
+    STS_CUDA(c->near_off.reserve(L + 1));
+    STS_CUDA(c->near_coff.reserve(L + 1));
+    STS_CUDA(c->far_idx.reserve(k.pc));
+    STS_CUDA(c->far_ent.reserve(k.pc));
+    STS_CUDA(c->near_idx.reserve(k.pp));
+    STS_CUDA(c->near_ent.reserve(k.pp_chunks));
+    STS_CUDA(c->cfar_off.reserve(C + 1));
+    STS_CUDA(c->cnear_off.reserve(C + 1));
+    STS_CUDA(c->cnear_coff.reserve(C + 1));
+    STS_CUDA(c->cfar_ent.reserve(k.cc));
+    STS_CUDA(c->cnear_ent.reserve(k.cp_chunks));
+    STS_CUDA(c->tasks.reserve(c->n / kTaskTargets + 4 * L + 64));  // task_split's bound per leaf
+    STS_CUDA(c->chas.reserve(C + 1));
     return STS_OK;
 }
 
-// CSR of one sorted kind over K target keys: off[K + 1] (pairs); for near kinds also the chunk
-// offsets coff[K + 1] and the chunked entries.  Reads the chunk total back (synchronises s).
-static int fill_dual_kind(sts_ctx* c, int kind, int64_t K, bool is_far, int64_t* off, int64_t* coff,
-                          int32_t* idx, DevBuf<FarEntry>* far_ent, DevBuf<NearEntry>* near_ent, int64_t* chunks,
-                          cudaStream_t s)
+// Every launch of the traversal, sort and list construction; no host access.
+// k: the capacities reserve_dual sized the buffers for (every buffer holds at least that many).
+static int launch_dual(sts_ctx* c, double theta, int levels, int64_t L, int64_t C, int64_t nodes,
+                       const DualCaps& k, unsigned long long* over, cudaStream_t s)
 {
-    const int64_t P = c->dual_n[kind];
     const int T = 256;
-    const int32_t* node_of = (kind == kPP || kind == kPC) ? c->leaves.p : c->cluster_node.p;
-    (k_dual_offsets<<<blocks(K + 1, T), T, 0, s>>>(c->dual_key.p, P, K, off), note_launch());
-    if (is_far) {
-        STS_CUDA(far_ent->reserve(P + 1));
-        if (P > 0)
-            (k_dual_fill<<<blocks(P, T), T, 0, s>>>(true, c->dual_key.p, c->dual_s[kind].p, P, node_of, c->nd_geom.p,
-                                                    c->nd_start.p, c->nd_count.p, c->cluster_slot.p, nullptr, idx,
-                                                    far_ent->p, nullptr),
-             note_launch());
-        STS_LAUNCH_CHECK();
-        return STS_OK;
+    int64_t* du = c->dual_cnt.p;
+    int64_t* dc = c->dc.p;
+    const int64_t fcap = k.front, tcap = k.terms;
+    STS_CUDA(cudaMemsetAsync(du, 0, kDuSize * sizeof(int64_t), s));
+    (k_dual_roots<<<blocks(400 * (int64_t)c->ninst, T), T, 0, s>>>(c->face_node.p, c->ninst, c->dual_ft.p,
+                                                                  c->dual_fs.p, fcap, du, over), note_launch());
+    const unsigned gf = blocks(fcap, T);
+    for (int l = 0; l < levels; l++) {
+        const bool even = (l & 1) == 0;
+        (k_dual_level<<<gf, T, 0, s>>>(l, even ? c->dual_ft.p : c->dual_gt.p, even ? c->dual_fs.p : c->dual_gs.p,
+                                       even ? c->dual_gt.p : c->dual_ft.p, even ? c->dual_gs.p : c->dual_fs.p, fcap,
+                                       theta, c->leaf_size, c->nd_geom.p, c->nd_c32.p, c->nd_leaf.p,
+                                       c->nd_first_child.p, c->nd_nchild.p, c->nd_count.p, c->dual_tt.p, c->dual_ts.p,
+                                       c->dual_tk.p, tcap, du, over),
+         note_launch());
     }
-    // chunk counts per pair (in the radix scratch, free after the sort), their scan, and the
-    // chunk offset of every key
-    if (P > 0)
-        (k_dual_chunks<<<blocks(P, T), T, 0, s>>>(c->dual_s[kind].p, P, c->nd_count.p, c->dual_vtmp.p),
-         note_launch());
-    exclusive_scan_i32(c->dual_vtmp.p, c->dual_scan.p, P, c->scan_tmp.p, s);
-    (k_dual_coff<<<blocks(K + 1, T), T, 0, s>>>(off, K, c->dual_scan.p, coff), note_launch());
-    STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_scan.p + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    *chunks = c->h_pinned[0];
-    STS_CUDA(near_ent->reserve(*chunks + 1));
-    if (P > 0)
-        (k_dual_fill<<<blocks(P, T), T, 0, s>>>(false, c->dual_key.p, c->dual_s[kind].p, P, node_of, c->nd_geom.p,
-                                                c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->dual_scan.p, idx,
-                                                nullptr, near_ent->p),
-         note_launch());
+    (k_dual_close<<<1, 32, 0, s>>>(levels, tcap, du, over), note_launch());
+    // sort by (kind, target key, source): stable passes on the source, then on kind | target
+    const int bits_t = bits_for(std::max<int64_t>(std::max(L, C), 1));
+    const int bits_n = bits_for(std::max<int64_t>(nodes, 1));
+    const int64_t hs = radix_hist_size(tcap);
+    int64_t* scan_out = c->scan_tmp.p;
+    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
+    const unsigned gt = blocks(tcap, T);
+    (k_dual_keys_src<<<gt, T, 0, s>>>(c->dual_ts.p, du, tcap, c->dual_key.p, c->dual_perm.p), note_launch());
+    radix_sort_pairs(c->dual_key.p, c->dual_perm.p, c->dual_ktmp.p, c->dual_ptmp.p, tcap, bits_n, c->hist.p, scan_out,
+                     scan_scr, s, du + kDuP);
+    (k_dual_keys_tgt<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_tk.p, c->dual_perm.p, du, tcap, bits_t, c->nd_start.p,
+                                      c->slot_leaf.p, c->cluster_slot.p, c->dual_key.p), note_launch());
+    radix_sort_pairs(c->dual_key.p, c->dual_perm.p, c->dual_ktmp.p, c->dual_ptmp.p, tcap, bits_t + 2, c->hist.p,
+                     scan_out, scan_scr, s, du + kDuP);
+    (k_dual_gather<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_ts.p, c->dual_perm.p, c->dual_key.p, bits_t, du, tcap,
+                                    c->nd_count.p, c->dual_t.p, c->dual_s.p, c->dual_chunk.p), note_launch());
+    exclusive_scan_i32(c->dual_chunk.p, c->dual_scan.p, tcap, c->scan_tmp.p, s, du + kDuP);
+    // CSR per kind, then the entries
+    DualCsr csr;
+    csr.off[kPP] = c->near_off.p;
+    csr.coff[kPP] = c->near_coff.p;
+    csr.off[kPC] = c->far_off.p;
+    csr.coff[kPC] = nullptr;
+    csr.off[kCP] = c->cnear_off.p;
+    csr.coff[kCP] = c->cnear_coff.p;
+    csr.off[kCC] = c->cfar_off.p;
+    csr.coff[kCC] = nullptr;
+    const dim3 gc(blocks(std::max(L, C) + 1, T), 4);
+    (k_dual_csr<<<gc, T, 0, s>>>(c->dual_key.p, c->dual_scan.p, bits_t, dc, L, C, csr, du), note_launch());
+    DualFill fo;
+    fo.far[0] = c->far_ent.p;
+    fo.far[1] = c->cfar_ent.p;
+    fo.near[0] = c->near_ent.p;
+    fo.near[1] = c->cnear_ent.p;
+    fo.idx[0] = c->near_idx.p;
+    fo.idx[1] = c->far_idx.p;
+    fo.far_cap[0] = (int64_t)c->far_ent.cap;
+    fo.far_cap[1] = (int64_t)c->cfar_ent.cap;
+    fo.near_cap[0] = (int64_t)c->near_ent.cap;
+    fo.near_cap[1] = (int64_t)c->cnear_ent.cap;
+    fo.idx_cap[0] = (int64_t)c->near_idx.cap;
+    fo.idx_cap[1] = (int64_t)c->far_idx.cap;
+    (k_dual_fill<<<gt, T, 0, s>>>(c->dual_key.p, c->dual_t.p, c->dual_s.p, c->dual_scan.p, bits_t, du, tcap,
+                                  c->nd_geom.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, fo, over),
+     note_launch());
+    // evaluation tasks of the target leaves (as for the leaf lists) and the list totals
+    const unsigned g = blocks(std::max<int64_t>(L, 1), 128);
+    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
+    (k_task_count<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
+                                    (unsigned long long*)(dc + kDcClass)), note_launch());
+    (k_list_totals<<<1, 32, 0, s>>>(dc, c->far_off.p, c->near_off.p, c->near_coff.p, L), note_launch());
+    (k_task_fill<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
+                                   (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
+                                   dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
@@ -1617,174 +1787,151 @@ int build_dual(sts_ctx* c, double theta, cudaStream_t s)
 {
     c->have_dual = false;
     c->have_lists = false;  // the leaf lists are replaced by the PP / PC pairs
-    if (c->capturing) {
-        set_error("dual traversal: not available while recording a graph");
-        return STS_ERR_STATE;
+    for (int k = 0; k < 4; k++) c->dual_n[k] = -1;
+    const bool cap = c->capturing;
+    // leaf, cluster and node counts, or while recording their planned bounds (a replay that
+    // exceeds them sets the overflow bit and is redone)
+    const int64_t L = cap ? std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64) : c->nleaves;
+    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    const int64_t nodes = cap ? (int64_t)c->nd_level.cap : c->nnodes;
+    const int depth = cap ? c->plan.depth : (int)c->deepest;
+    // a pair's two levels each grow by one per refinement, up to the deepest level: at most
+    // 2 depth + 1 levels, the last of which only has terminals
+    const int levels = std::min(2 * depth + 2, kDuMaxLevels);
+    if (cap) {
+        const int rc = launch_dual(c, theta, levels, L, C, nodes, dual_caps(c, L, C, nodes),
+                                   (unsigned long long*)(c->dc.p + kDcOver), s);
+        if (rc) return rc;
+        c->nfar = c->nnear = c->nnear_chunks = c->ntasks = -1;
+        c->dual_theta = theta;
+        c->have_dual = true;
+        return STS_OK;
     }
-    const int T = 256;
-    const int64_t nn = c->nnodes, L = c->nleaves, C = c->nclusters;
-    STS_CUDA(c->dual_cnt.reserve(8));
-    unsigned long long* cnt = (unsigned long long*)c->dual_cnt.p;
-    int64_t fcap = std::max<int64_t>(400 * (int64_t)c->ninst, 8 * nn + 64);
-    STS_CUDA(c->dual_ft.reserve(fcap));
-    STS_CUDA(c->dual_fs.reserve(fcap));
-    STS_CUDA(c->dual_gt.reserve(fcap));
-    STS_CUDA(c->dual_gs.reserve(fcap));
-    const int64_t init_cap[4] = {48 * L + 64, 48 * L + 64, 16 * C + 64, 16 * C + 64};
-    for (int k = 0; k < 4; k++) {
-        STS_CUDA(c->dual_t[k].reserve(init_cap[k]));
-        STS_CUDA(c->dual_s[k].reserve(init_cap[k]));
-    }
-    STS_CUDA(cudaMemsetAsync(c->dual_cnt.p, 0, 8 * sizeof(int64_t), s));
-    (k_dual_roots<<<blocks(400 * (int64_t)c->ninst, T), T, 0, s>>>(c->face_node.p, c->ninst, c->dual_ft.p,
-                                                                  c->dual_fs.p, cnt), note_launch());
-    STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 8 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    int64_t nf = c->h_pinned[4];
-    int64_t done[4] = {0, 0, 0, 0};
-    // each level refines one side of a pair, so the traversal ends within 2 (depth + 1) levels;
-    // every retry grows a buffer
-    for (int it = 0; nf > 0; it++) {
-        if (it > 4 * (kMaxLevel + 2) + 64) {
-            set_error("dual traversal: no progress");
+    DualCaps k = dual_caps(c, L, C, nodes);
+    for (int attempt = 0;; attempt++) {
+        int rc = reserve_dual(c, k, L, C, nodes);
+        if (rc) return rc;
+        unsigned long long* over = (unsigned long long*)(c->dual_cnt.p + kDuOver);
+        if ((rc = launch_dual(c, theta, levels, L, C, nodes, k, over, s))) return rc;
+        int64_t* h = c->h_pinned;
+        STS_CUDA(cudaMemcpyAsync(h, c->dual_cnt.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaMemcpyAsync(h + 16, c->dc.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaStreamSynchronize(s));
+        const int64_t P = h[kDuP];
+        int64_t n4[4];
+        for (int q = 0; q < 4; q++) n4[q] = h[kDuStart + q + 1] - h[kDuStart + q];
+        const bool over_hit = h[kDuOver] != 0 || (h[16 + kDcOver] & 4) != 0;
+        if (!over_hit) {
+            for (int q = 0; q < 4; q++) c->dual_n[q] = n4[q];
+            Plan& pl = c->plan;
+            pl.dual_front = std::max(pl.dual_front, h[kDuFrontMax]);
+            pl.dual_terms = std::max(pl.dual_terms, P);
+            for (int q = 0; q < 4; q++) pl.dual_pairs[q] = std::max(pl.dual_pairs[q], n4[q]);
+            pl.dual_chunks[0] = std::max(pl.dual_chunks[0], h[kDuChunks]);
+            pl.dual_chunks[1] = std::max(pl.dual_chunks[1], h[kDuChunks + 1]);
+            c->nfar = h[16 + kDcFar];
+            c->nnear = h[16 + kDcNear];
+            c->nnear_chunks = h[16 + kDcChunks];
+            c->ntasks = h[16 + kDcTasks];
+            pl.far = std::max(pl.far, c->nfar);
+            pl.near = std::max(pl.near, c->nnear);
+            pl.chunks = std::max(pl.chunks, c->nnear_chunks);
+            pl.tasks = std::max(pl.tasks, c->ntasks);
+            break;
+        }
+        if (attempt >= 8) {
+            set_error("dual traversal: buffers keep overflowing");
             return STS_ERR_CAPACITY;
         }
-        for (int k = 0; k < 4; k++) c->h_pinned[k] = done[k];
-        c->h_pinned[4] = 0;
-        STS_CUDA(cudaMemcpyAsync(c->dual_cnt.p, c->h_pinned, 5 * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        DualOut out;
-        for (int k = 0; k < 4; k++) {
-            out.t[k] = c->dual_t[k].p;
-            out.s[k] = c->dual_s[k].p;
-            out.cap[k] = (int64_t)std::min(c->dual_t[k].cap, c->dual_s[k].cap);
+        // grow what overflowed (the counters saw every attempted write) and run it again
+        STS_CUDA(cudaMemsetAsync(c->dc.p + kDcOver, 0, sizeof(int64_t), s));
+        auto g = [](int64_t v) { return v + v / 2 + 1024; };
+        k.front = std::max(k.front, g(h[kDuFrontMax]));
+        k.terms = std::max(k.terms, g(h[kDuTerms]));
+        if (P == h[kDuTerms]) {  // the sort ran on every pair: the kind counts are exact
+            k.pp = std::max(k.pp, g(n4[kPP]));
+            k.pc = std::max(k.pc, g(n4[kPC]));
+            k.cp = std::max(k.cp, g(n4[kCP]));
+            k.cc = std::max(k.cc, g(n4[kCC]));
+            k.pp_chunks = std::max(k.pp_chunks, g(h[kDuChunks]));
+            k.cp_chunks = std::max(k.cp_chunks, g(h[kDuChunks + 1]));
         }
-        const int64_t gcap = (int64_t)std::min(c->dual_gt.cap, c->dual_gs.cap);
-        (k_dual_step<<<blocks(nf, T), T, 0, s>>>(c->dual_ft.p, c->dual_fs.p, nf, theta, c->leaf_size, c->nd_geom.p,
-                                                 c->nd_c32.p, c->nd_leaf.p, c->nd_first_child.p, c->nd_nchild.p,
-                                                 c->nd_count.p, c->dual_gt.p, c->dual_gs.p, gcap, out, cnt),
-         note_launch());
-        STS_LAUNCH_CHECK();
-        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        STS_CUDA(cudaStreamSynchronize(s));
-        bool redo = false;
-        for (int k = 0; k < 4; k++)
-            if (c->h_pinned[k] > out.cap[k]) {
-                const int64_t need = c->h_pinned[k];
-                STS_CUDA(c->dual_t[k].grow(need, done[k], s));
-                STS_CUDA(c->dual_s[k].grow(need, done[k], s));
-                redo = true;
-            }
-        const int64_t ng = c->h_pinned[4];
-        if (ng > gcap) {
-            STS_CUDA(c->dual_gt.reserve(ng));
-            STS_CUDA(c->dual_gs.reserve(ng));
-            redo = true;
-        }
-        if (redo) continue;  // the same frontier again, with room for every write
-        for (int k = 0; k < 4; k++) done[k] = c->h_pinned[k];
-        nf = ng;
-        std::swap(c->dual_ft, c->dual_gt);
-        std::swap(c->dual_fs, c->dual_gs);
     }
-    int64_t pmax = 1;
-    for (int k = 0; k < 4; k++) {
-        c->dual_n[k] = done[k];
-        pmax = std::max(pmax, done[k]);
-    }
-    // sort every kind by (target, source)
-    const int64_t hs = radix_hist_size(pmax);
-    STS_CUDA(c->dual_key.reserve(pmax + 1));
-    STS_CUDA(c->dual_ktmp.reserve(pmax + 1));
-    STS_CUDA(c->dual_vtmp.reserve(pmax + 1));
-    STS_CUDA(c->dual_scan.reserve(pmax + 1));
-    STS_CUDA(c->hist.reserve(hs));
-    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(pmax + 1) + scan_scratch(nn + 1) + 64));
-    // leaf lists: PC far, PP near (per depth-first leaf); cluster lists: CC far, CP near
-    STS_CUDA(c->far_off.reserve(L + 1));
-    STS_CUDA(c->near_off.reserve(L + 1));
-    STS_CUDA(c->near_coff.reserve(L + 1));
-    STS_CUDA(c->far_idx.reserve(c->dual_n[kPC] + 1));
-    STS_CUDA(c->near_idx.reserve(c->dual_n[kPP] + 1));
-    STS_CUDA(c->cfar_off.reserve(C + 1));
-    STS_CUDA(c->cnear_off.reserve(C + 1));
-    STS_CUDA(c->cnear_coff.reserve(C + 1));
-    int rc;
-    int64_t chunks = 0, cchunks = 0;
-    if ((rc = sort_dual_kind(c, kPC, true, s))) return rc;
-    if ((rc = fill_dual_kind(c, kPC, L, true, c->far_off.p, nullptr, c->far_idx.p, &c->far_ent, nullptr, nullptr, s)))
-        return rc;
-    if ((rc = sort_dual_kind(c, kPP, true, s))) return rc;
-    if ((rc = fill_dual_kind(c, kPP, L, false, c->near_off.p, c->near_coff.p, c->near_idx.p, nullptr, &c->near_ent,
-                             &chunks, s)))
-        return rc;
-    if ((rc = sort_dual_kind(c, kCC, false, s))) return rc;
-    if ((rc = fill_dual_kind(c, kCC, C, true, c->cfar_off.p, nullptr, nullptr, &c->cfar_ent, nullptr, nullptr, s)))
-        return rc;
-    if ((rc = sort_dual_kind(c, kCP, false, s))) return rc;
-    if ((rc = fill_dual_kind(c, kCP, C, false, c->cnear_off.p, c->cnear_coff.p, nullptr, nullptr, &c->cnear_ent,
-                             &cchunks, s)))
-        return rc;
-    // the sorted target keys are no longer needed; the pairs stay for export (targets: node ids)
-    int64_t* dc = c->dc.p;
-    const unsigned g = blocks(std::max<int64_t>(L, 1), 128);
-    STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
-    (k_task_count<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
-                                    (unsigned long long*)(dc + kDcClass)), note_launch());
-    (k_list_totals<<<1, 32, 0, s>>>(dc, c->far_off.p, c->near_off.p, c->near_coff.p, L), note_launch());
-    STS_LAUNCH_CHECK();
-    STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    STS_CUDA(cudaStreamSynchronize(s));
-    c->nfar = c->h_pinned[kDcFar];
-    c->nnear = c->h_pinned[kDcNear];
-    c->nnear_chunks = c->h_pinned[kDcChunks];
-    c->ntasks = c->h_pinned[kDcTasks];
-    c->ncnear_chunks = cchunks;
-    STS_CUDA(c->tasks.reserve(c->ntasks + 1));
-    (k_task_fill<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
-                                   (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
-                                   dc + kDcOver), note_launch());
-    STS_LAUNCH_CHECK();
     c->dual_theta = theta;
     c->have_dual = true;
     return STS_OK;
 }
 
-int cluster_tasks(sts_ctx* c, int M, cudaStream_t s)
+int reserve_dual_for_capture(sts_ctx* c, int degree, cudaStream_t s)
 {
-    const int64_t C = c->nclusters;
-    c->nctasks = 0;
-    STS_CUDA(c->chas.reserve(C + 1));
-    if (C == 0) return STS_OK;
-    const int64_t cap = C * ((M + kTaskTargets - 1) / kTaskTargets + 3);
-    STS_CUDA(c->ctasks.reserve(cap + 1));
-    STS_CUDA(cudaMemsetAsync(c->dual_cnt.p + 5, 0, sizeof(int64_t), s));
-    (k_cluster_tasks<<<blocks(C, 128), 128, 0, s>>>(C, c->cfar_off.p, c->cnear_off.p, M, c->chas.p, c->ctasks.p, cap,
-                                                    (unsigned long long*)(c->dual_cnt.p + 5), c->d_status),
-     note_launch());
-    STS_LAUNCH_CHECK();
-    c->nctasks = cap;  // a bound: the kernels read the count from dual_cnt[5]
+    (void)s;
+    const int64_t L = std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64);
+    const int64_t C = (int64_t)c->nd_level.cap, nodes = (int64_t)c->nd_level.cap;
+    int rc = reserve_dual(c, dual_caps(c, L, C, nodes), L, C, nodes);
+    if (rc) return rc;
+    const int M = (degree + 1) * (degree + 2) / 2;
+    STS_CUDA(c->ctasks.reserve(C * ((M + kTaskTargets - 1) / kTaskTargets + 3) + 1));
+    STS_CUDA(c->cvel.reserve(3 * C * M + 3));
+    STS_CUDA(c->cdown.reserve(3 * C * M + 3));
+    STS_CUDA(c->ccorr.reserve(3 * C * M + 3));
+    STS_CUDA(c->cacc.reserve(C + 1));
     return STS_OK;
 }
+
+int refresh_dual_counts(sts_ctx* c, cudaStream_t s)
+{
+    if (!c->have_dual || c->dual_n[0] >= 0) return STS_OK;
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < 4; q++) c->dual_n[q] = c->h_pinned[kDuStart + q + 1] - c->h_pinned[kDuStart + q];
+    return STS_OK;
+}
+
+int cluster_tasks(sts_ctx* c, int M, cudaStream_t s)
+{
+    const bool cap = c->capturing;
+    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    if (!cap) {
+        STS_CUDA(c->chas.reserve(C + 1));
+        STS_CUDA(c->ctasks.reserve(C * ((M + kTaskTargets - 1) / kTaskTargets + 3) + 1));
+    }
+    // task_split's bound: at most ceil(M / 64) + 3 tasks per cluster
+    c->nctasks = std::min<int64_t>((int64_t)c->ctasks.cap, C * ((M + kTaskTargets - 1) / kTaskTargets + 3));
+    STS_CUDA(cudaMemsetAsync(c->dual_cnt.p + kDuCTasks, 0, sizeof(int64_t), s));
+    if (C > 0)
+        (k_cluster_tasks<<<blocks(C, 128), 128, 0, s>>>(c->dc.p, C, c->cfar_off.p, c->cnear_off.p, M, c->chas.p,
+                                                        c->ctasks.p, c->nctasks, c->dual_cnt.p,
+                                                        (unsigned long long*)(c->dc.p + kDcOver)),
+         note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
+}
+
+const int64_t* cluster_task_count(sts_ctx* c) { return c->dual_cnt.p + kDuCTasks; }
 
 int dual_stats(sts_ctx* c, int degree, int64_t* stats, cudaStream_t s)
 {
     for (int k = 0; k < 5; k++) stats[k] = 0;
     if (!c->have_dual) return STS_OK;
+    int rc = refresh_dual_counts(c, s);
+    if (rc) return rc;
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    int64_t first[4];
+    for (int q = 0; q < 4; q++) first[q] = c->h_pinned[kDuStart + q];
     const int M = (degree + 1) * (degree + 2) / 2;
     STS_CUDA(c->d_stats.reserve(8));
     STS_CUDA(cudaMemsetAsync(c->d_stats.p, 0, 8 * sizeof(unsigned long long), s));
     const int T = 256;
     for (int k = 0; k < 4; k++)
         if (c->dual_n[k] > 0)
-            (k_dual_count<<<blocks(c->dual_n[k], T), T, 0, s>>>(k, c->dual_t[k].p, c->dual_s[k].p, c->dual_n[k],
+            (k_dual_count<<<blocks(c->dual_n[k], T), T, 0, s>>>(k, c->dual_t.p, c->dual_s.p, first[k], c->dual_n[k],
                                                                 c->nd_count.p, nullptr, M, c->d_stats.p),
              note_launch());
     if (c->nclusters > 0) {
         // the clusters that are targets of CP or CC pairs (as the dual evaluation marks them)
-        int rc = cluster_tasks(c, M, s);
-        if (rc) return rc;
-        (k_dual_count<<<blocks(c->nclusters, T), T, 0, s>>>(4, c->cluster_node.p, nullptr, c->nclusters,
+        if ((rc = cluster_tasks(c, M, s))) return rc;
+        (k_dual_count<<<blocks(c->nclusters, T), T, 0, s>>>(4, c->cluster_node.p, nullptr, 0, c->nclusters,
                                                             c->nd_count.p, c->chas.p, M, c->d_stats.p),
          note_launch());
     }
@@ -1792,6 +1939,22 @@ int dual_stats(sts_ctx* c, int degree, int64_t* stats, cudaStream_t s)
     STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->d_stats.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     STS_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < 5; k++) stats[k] = c->h_pinned[k];
+    return STS_OK;
+}
+
+int dual_export(sts_ctx* c, int kind, int64_t* npairs, int32_t* tgt, int32_t* src, cudaStream_t s)
+{
+    int rc = refresh_dual_counts(c, s);
+    if (rc) return rc;
+    STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->dual_cnt.p, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    const int64_t first = c->h_pinned[kDuStart + kind], P = c->dual_n[kind];
+    if (npairs) *npairs = P;
+    if (tgt && P)
+        STS_CUDA(cudaMemcpyAsync(tgt, c->dual_t.p + first, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (src && P)
+        STS_CUDA(cudaMemcpyAsync(src, c->dual_s.p + first, P * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
     return STS_OK;
 }
 

@@ -21,7 +21,7 @@ STS_FP64 = 0
 STS_MIXED = 1
 STS_OK, STS_ERR_ARG, STS_ERR_CUDA, STS_ERR_CAPACITY, STS_ERR_TIMEOUT, STS_ERR_NONFINITE, STS_ERR_STATE = (
     0, -1, -2, -3, -4, -5, -6)
-PHASES = ("build", "sort", "lists", "prep", "upward", "eval", "direct")
+PHASES = ("build", "sort", "lists", "prep", "upward", "eval", "direct", "cluster")
 
 _lock = threading.Lock()
 _lib = None
@@ -82,6 +82,7 @@ def load(build_if_needed: bool = True):
             "sts_velocity_dual": (i32, [P, P, P, PP, P, P]),
             "sts_dual_export": (i32, [P, i32, P, P, P, P]),
             "sts_dual_stats": (i32, [P, i32, P, P]),
+            "sts_set_traversal": (i32, [P, i32]),
             "sts_direct_potential": (i32, [P, P, P, P, i64, i32, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
             "bve_rk4_step_forced": (i32, [P, P, P, P, i64, dbl, dbl, dbl, C.POINTER(sts_forcing), PP, P]),
@@ -250,6 +251,12 @@ def sts_dual_export(ctx, stream=None):
         _check(load().sts_dual_export(ctx, k, _host(cnt), _host(t), _host(s), _stream(stream)), "sts_dual_export")
         out[name] = (t, s)
     return out
+
+
+def sts_set_traversal(ctx, dual=True):
+    """Selects the dual traversal (True) or the target-leaf lists (False) for sts_velocity,
+    sts_tree_velocity and the RK4 steps."""
+    _check(load().sts_set_traversal(ctx, int(bool(dual))), "sts_set_traversal")
 
 
 def sts_dual_stats(ctx, degree, stream=None):

@@ -310,3 +310,23 @@ def test_repeat_calls_are_deterministic(ctx):
     sts.sts_tree_build(ctx, dev(pos), p)
     b = sts.sts_velocity(ctx, dev(zeta), dev(area), p).cpu().numpy()
     assert np.array_equal(a, b)
+
+
+def test_tree_bit_exact_on_reused_device_memory():
+    """Buffers from cudaMalloc hold whatever the process left there: fill the device memory
+    with 0xFF bytes, hand it back, then build in a new context a forest whose sparse faces are
+    leaves at the root (their particles never get a child digit written) next to faces that
+    split.  The tree must still be the oracle's, bit for bit."""
+    junk = torch.full((2**28,), -1, dtype=torch.int64, device="cuda")  # 2 GiB of 0xFF
+    torch.cuda.synchronize()
+    del junk
+    torch.cuda.empty_cache()
+    pos = _clustered(3000, 150, 31)  # one dense cap, most faces with a few points
+    with sts.Context() as c:
+        p = sts.params(leaf_size=32, max_level=16)
+        sts.sts_tree_build(c.h, dev(pos), p)
+        g = sts.sts_tree_export(c.h)
+    o = O.Tree(pos, 32, 16).export()
+    assert (o["count"][o["level"] == 0] <= 32).any() and (o["level"] > 0).any()
+    for k in TREE_FIELDS:
+        assert np.array_equal(g[k], o[k]), k
