@@ -930,49 +930,42 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
 // ------------------------------------------------------------------------ dual: downward
 namespace {
 
-// Plain FP64 products and sums in a fixed order (no contraction): the barycentric coordinates
-// below come out exactly as a plain IEEE evaluation of the same formula.
-__device__ __forceinline__ double dot3_rn(double ax, double ay, double az, double bx, double by, double bz)
+// The interpolating polynomial of cluster slot cs at x (degree D, M = (D+1)(D+2)/2
+// coefficients cf[M][3]): b = the spherical barycentric coordinates of x in the cluster's
+// triangle (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3; frame rows n_i / D from Cramer's rule:
+// n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1), then sum_k B_k(b) c_k with
+// B_k(b) = b1^a b2^b b3^c in the order a = D..0, b = D - a..0, summed per a and then over a.
+// D is a template parameter so that the powers stay in registers.
+template <int D>
+__device__ __forceinline__ void eval_interp(const double* __restrict__ f, const double* __restrict__ cf, double xx,
+                                            double xy, double xz, double& ax, double& ay, double& az)
 {
-    return __dadd_rn(__dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by)), __dmul_rn(az, bz));
-}
-__device__ __forceinline__ void cross3_rn(const double* a, const double* b, double* c)
-{
-    c[0] = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
-    c[1] = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
-    c[2] = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
-}
-
-// The interpolating polynomial of triangle g (vertices g[0..8]) with coefficients cf[M][3] at x:
-// b = the spherical barycentric coordinates of x (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3 by
-// Cramer's rule: b_i = (x . n_i) / D, n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1),
-// sum_k B_k(b) c_k with B_k(b) = b1^a b2^b b3^c in the order a = d..0, b = d - a..0.
-__device__ __forceinline__ void eval_interp(const double* __restrict__ g, const double* __restrict__ cf, int d,
-                                            double xx, double xy, double xz, double& ax, double& ay, double& az)
-{
-    double n1[3], n2[3], n3[3];
-    cross3_rn(g + 3, g + 6, n1);
-    cross3_rn(g + 6, g, n2);
-    cross3_rn(g, g + 3, n3);
-    const double D = dot3_rn(g[0], g[1], g[2], n1[0], n1[1], n1[2]);
-    const double b1 = __ddiv_rn(dot3_rn(xx, xy, xz, n1[0], n1[1], n1[2]), D);
-    const double b2 = __ddiv_rn(dot3_rn(xx, xy, xz, n2[0], n2[1], n2[2]), D);
-    const double b3 = __ddiv_rn(dot3_rn(xx, xy, xz, n3[0], n3[1], n3[2]), D);
-    double p1[kMaxDegree + 1], p2[kMaxDegree + 1], p3[kMaxDegree + 1];
+    const double b1 = f[0] * xx + f[1] * xy + f[2] * xz;
+    const double b2 = f[3] * xx + f[4] * xy + f[5] * xz;
+    const double b3 = f[6] * xx + f[7] * xy + f[8] * xz;
+    double p1[D + 1], p2[D + 1], p3[D + 1];
     p1[0] = p2[0] = p3[0] = 1.0;
-    for (int e = 1; e <= d; e++) {
+#pragma unroll
+    for (int e = 1; e <= D; e++) {
         p1[e] = p1[e - 1] * b1;
         p2[e] = p2[e - 1] * b2;
         p3[e] = p3[e - 1] * b3;
     }
     int k = 0;
-    for (int ea = d; ea >= 0; ea--)
-        for (int eb = d - ea; eb >= 0; eb--, k++) {
-            const double B = (p1[ea] * p2[eb]) * p3[d - ea - eb];
-            ax += B * cf[3 * k];
-            ay += B * cf[3 * k + 1];
-            az += B * cf[3 * k + 2];
+#pragma unroll
+    for (int ea = D; ea >= 0; ea--) {
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+        for (int eb = D - ea; eb >= 0; eb--, k++) {
+            const double B = p2[eb] * p3[D - ea - eb];
+            sx += B * cf[3 * k];
+            sy += B * cf[3 * k + 1];
+            sz += B * cf[3 * k + 2];
         }
+        ax += p1[ea] * sx;
+        ay += p1[ea] * sy;
+        az += p1[ea] * sz;
+    }
 }
 
 // Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the velocity at the target
@@ -986,13 +979,15 @@ __device__ __forceinline__ void eval_interp(const double* __restrict__ g, const 
 // x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|, the barycentric coordinates of
 // x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref and c = V_ref^-1 diag(rho^d) U.
 // acc[c]: cluster c holds an interpolant.  One CTA per cluster of the level.
+template <int D>
 __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ parent,
                              const int32_t* __restrict__ cluster_slot, const uint8_t* __restrict__ has,
                              uint8_t* __restrict__ acc, const double* __restrict__ geom,
-                             const double4* __restrict__ prx64, const double* __restrict__ beta,
-                             const double* __restrict__ vinv, int d, int M, const double* __restrict__ cvel,
-                             double* __restrict__ coef)
+                             const double* __restrict__ frame, const double4* __restrict__ prx64,
+                             const double* __restrict__ beta, const double* __restrict__ vinv,
+                             const double* __restrict__ cvel, double* __restrict__ coef)
 {
+    constexpr int d = D, M = (D + 1) * (D + 2) / 2;
     __shared__ double u[3 * kMaxM];
     const int64_t lb = lvl[l], le = lvl[l + 1];
     for (int64_t p = lb + blockIdx.x; p < le; p += gridDim.x) {
@@ -1016,7 +1011,7 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
             }
             if (from_parent) {
                 const double4 x = prx64[(int64_t)cs * M + m];
-                eval_interp(geom + 13 * (int64_t)par, coef + 3 * (int64_t)ps * M, d, x.x, x.y, x.z, vx, vy, vz);
+                eval_interp<D>(frame + 12 * (int64_t)ps, coef + 3 * (int64_t)ps * M, x.x, x.y, x.z, vx, vy, vz);
             }
             const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
             const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
@@ -1048,12 +1043,14 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
 
 // Adds to every particle (sorted slot) the interpolant of its lowest cluster: its leaf when
 // that is a cluster (at the depth limit), else the leaf's parent.
+template <int D>
 __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
-                           const uint8_t* __restrict__ acc, const double* __restrict__ geom,
-                           const double4* __restrict__ src64, const int32_t* __restrict__ perm, int d, int M,
+                           const uint8_t* __restrict__ acc, const double* __restrict__ frame,
+                           const double4* __restrict__ src64, const int32_t* __restrict__ perm,
                            const double* __restrict__ coef, double* __restrict__ vel)
 {
+    constexpr int M = (D + 1) * (D + 2) / 2;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int32_t a = leaves[slot_leaf[j]];
@@ -1063,11 +1060,30 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
     if (cs < 0 || !acc[cs]) return;
     const double4 x = src64[j];
     double ax = 0.0, ay = 0.0, az = 0.0;
-    eval_interp(geom + 13 * (int64_t)a, coef + 3 * (int64_t)cs * M, d, x.x, x.y, x.z, ax, ay, az);
+    eval_interp<D>(frame + 12 * (int64_t)cs, coef + 3 * (int64_t)cs * M, x.x, x.y, x.z, ax, ay, az);
     const int64_t i = perm[j];
     vel[3 * i] += ax;
     vel[3 * i + 1] += ay;
     vel[3 * i + 2] += az;
+}
+
+}  // namespace
+
+namespace {
+
+template <int D>
+void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, cudaStream_t s)
+{
+    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
+    for (int l = 0; l < levels; l++)
+        (k_down_level<D><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
+                                           c->cacc.p, c->nd_geom.p, c->up_frame.p, c->prx64.p, ref->d_beta.p,
+                                           ref->d_vinv.p, c->cvel.p, c->cdown.p),
+         note_launch());
+    (k_downward<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
+                                                      c->cluster_slot.p, c->cacc.p, c->up_frame.p, c->src64.p,
+                                                      c->perm.p, c->cdown.p, vel),
+     note_launch());
 }
 
 }  // namespace
@@ -1107,16 +1123,24 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s, -1))) return rc;
     // interpolants passed down level by level, then evaluated at the particles
     const int levels = (cap ? c->plan.depth : (int)c->deepest) + 1;
-    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
-    for (int l = 0; l < levels; l++)
-        (k_down_level<<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
-                                        c->cacc.p, c->nd_geom.p, c->prx64.p, ref->d_beta.p, ref->d_vinv.p, degree,
-                                        M, c->cvel.p, c->cdown.p),
-         note_launch());
-    (k_downward<<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                   c->cluster_slot.p, c->cacc.p, c->nd_geom.p, c->src64.p, c->perm.p,
-                                                   degree, M, c->cdown.p, vel),
-     note_launch());
+    switch (degree) {
+        case 1: launch_down<1>(c, ref, levels, C, vel, s); break;
+        case 2: launch_down<2>(c, ref, levels, C, vel, s); break;
+        case 3: launch_down<3>(c, ref, levels, C, vel, s); break;
+        case 4: launch_down<4>(c, ref, levels, C, vel, s); break;
+        case 5: launch_down<5>(c, ref, levels, C, vel, s); break;
+        case 6: launch_down<6>(c, ref, levels, C, vel, s); break;
+        case 7: launch_down<7>(c, ref, levels, C, vel, s); break;
+        case 8: launch_down<8>(c, ref, levels, C, vel, s); break;
+        case 9: launch_down<9>(c, ref, levels, C, vel, s); break;
+        case 10: launch_down<10>(c, ref, levels, C, vel, s); break;
+        case 11: launch_down<11>(c, ref, levels, C, vel, s); break;
+        case 12: launch_down<12>(c, ref, levels, C, vel, s); break;
+        case 13: launch_down<13>(c, ref, levels, C, vel, s); break;
+        case 14: launch_down<14>(c, ref, levels, C, vel, s); break;
+        case 15: launch_down<15>(c, ref, levels, C, vel, s); break;
+        default: launch_down<16>(c, ref, levels, C, vel, s); break;
+    }
     phase_end(c, kPhCluster, s);
     STS_LAUNCH_CHECK();
     return STS_OK;

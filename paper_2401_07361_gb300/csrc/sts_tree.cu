@@ -1053,7 +1053,8 @@ __global__ void k_dual_roots(const int32_t* __restrict__ face_node, int ninst, i
 }
 
 // Level l of the traversal: the pairs of frontier l (ft, fs) decided; terminals appended to
-// (tt, ts, tk), refined pairs to frontier l + 1 (gt, gs).
+// (tt, ts, tk), refined pairs to frontier l + 1 (gt, gs).  Appends are warp-aggregated: one
+// atomic per warp reserves the warp's terminals, one its refined pairs.
 __global__ void k_dual_level(int l, const int32_t* __restrict__ ft, const int32_t* __restrict__ fs,
                              int32_t* __restrict__ gt, int32_t* __restrict__ gs, int64_t fcap, double theta,
                              int leaf_size, const double* __restrict__ geom, const float4* __restrict__ c32,
@@ -1063,40 +1064,65 @@ __global__ void k_dual_level(int l, const int32_t* __restrict__ ft, const int32_
                              int64_t tcap, int64_t* __restrict__ du, unsigned long long* __restrict__ over)
 {
     const int64_t nf = min(du[kDuFront + l], fcap);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    const int32_t t = ft[i], s = fs[i];
-    const int32_t ct = count[t], cs = count[s];
-    const bool lt = leaf[t] != 0, ls = leaf[s] != 0;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+    if (i0 >= nf) return;  // whole warps below (the warp scans need every lane)
+    const int64_t i = i0 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int32_t t = -1, s = -1, fc = 0, nc = 0;
     int kind = -1;
-    if (mac_filtered(c32[t], c32[s], (float)theta, geom + 13 * (int64_t)t, geom + 13 * (int64_t)s, theta)) {
-        const bool tc = ct > leaf_size, sc = cs > leaf_size;
-        kind = tc ? (sc ? kCC : kCP) : (sc ? kPC : kPP);
-    } else if (lt && ls) {
-        kind = kPP;
-    }
-    if (kind >= 0) {
-        const int64_t q = (int64_t)atomicAdd((unsigned long long*)(du + kDuTerms), 1ull);
-        if (q < tcap) {
-            tt[q] = t;
-            ts[q] = s;
-            tk[q] = (uint8_t)kind;
+    bool split_t = false;
+    if (i < nf) {
+        t = ft[i];
+        s = fs[i];
+        const int32_t ct = count[t], cs = count[s];
+        const bool lt = leaf[t] != 0, ls = leaf[s] != 0;
+        if (mac_filtered(c32[t], c32[s], (float)theta, geom + 13 * (int64_t)t, geom + 13 * (int64_t)s, theta)) {
+            const bool tc = ct > leaf_size, sc = cs > leaf_size;
+            kind = tc ? (sc ? kCC : kCP) : (sc ? kPC : kPP);
+        } else if (lt && ls) {
+            kind = kPP;
         } else {
-            atomicOr(over, 4ull);
+            split_t = !lt && (ls || ct >= cs);
+            const int32_t p = split_t ? t : s;
+            fc = first_child[p];
+            nc = nchild[p];
         }
-        return;
     }
-    const bool split_t = !lt && (ls || ct >= cs);
-    const int32_t p = split_t ? t : s;
-    const int32_t fc = first_child[p], nc = nchild[p];
-    const int64_t q = (int64_t)atomicAdd((unsigned long long*)(du + kDuFront + l + 1), (unsigned long long)nc);
-    atomicMax((unsigned long long*)(du + kDuFrontMax), (unsigned long long)(q + nc));
-    if (q + nc > fcap) atomicOr(over, 4ull);
-    // every slot below the capacity is written (the next level reads min(count, fcap) pairs),
-    // also those of a refinement that does not fit whole
-    for (int32_t c = 0; c < nc && q + c < fcap; c++) {
-        gt[q + c] = split_t ? fc + c : t;
-        gs[q + c] = split_t ? s : fc + c;
+    // terminals: one reservation per warp
+    const unsigned tm = __ballot_sync(kFull, kind >= 0);
+    if (tm) {
+        unsigned long long base = 0;
+        if (lane == __ffs(tm) - 1) base = atomicAdd((unsigned long long*)(du + kDuTerms), (unsigned long long)__popc(tm));
+        base = __shfl_sync(kFull, base, __ffs(tm) - 1);
+        if (kind >= 0) {
+            const int64_t q = (int64_t)base + __popc(tm & ((1u << lane) - 1u));
+            if (q < tcap) {
+                tt[q] = t;
+                ts[q] = s;
+                tk[q] = (uint8_t)kind;
+            } else {
+                atomicOr(over, 4ull);
+            }
+        }
+    }
+    // refined pairs: a warp scan of the child counts, one reservation per warp
+    int tot;
+    const int off = warp_excl_scan(nc, lane, &tot);
+    if (tot > 0) {
+        unsigned long long base = 0;
+        if (lane == 0) {
+            base = atomicAdd((unsigned long long*)(du + kDuFront + l + 1), (unsigned long long)tot);
+            atomicMax((unsigned long long*)(du + kDuFrontMax), base + (unsigned long long)tot);
+        }
+        base = __shfl_sync(kFull, base, 0);
+        const int64_t q = (int64_t)base + off;
+        if (nc > 0 && q + nc > fcap) atomicOr(over, 4ull);
+        // every slot below the capacity is written (the next level reads min(count, fcap) pairs),
+        // also those of a refinement that does not fit whole
+        for (int32_t c = 0; c < nc && q + c < fcap; c++) {
+            gt[q + c] = split_t ? fc + c : t;
+            gs[q + c] = split_t ? s : fc + c;
+        }
     }
 }
 
