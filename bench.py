@@ -60,6 +60,9 @@ def parse(argv=None):
     ap.add_argument("--dual", action="store_true",
                     help="the tree code by the dual traversal of Sec. 3.4 (PP, PC, CP, CC) instead of the "
                          "target-leaf lists (PC, PP)")
+    ap.add_argument("--amr", type=int, default=0,
+                    help="time this many RK4 steps of the Gaussian vortex with an AMR pass after each "
+                         "(Appendix A; level-5 icosahedral mesh, eps1 0.0025, eps2 0.2, dt 0.01 day)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying the recorded step")
     ap.add_argument("--profile", action="store_true",
@@ -322,6 +325,114 @@ def run_rk4(args):
     return 0
 
 
+def run_amr(args):
+    """RK4 steps of the Gaussian vortex (Sec. 4.3) with the adaptive mesh refinement of
+    Appendix A after every step: per step, the particles are gathered from the mesh, advanced by
+    one RK4 step of the tree code (eager: the particle count changes between steps), written
+    back, and one AMR pass splits and merges triangles.  Reports particle-steps/s and the AMR
+    pass time; the oracle's AMR pass on the same final state is the CPU baseline."""
+    import numpy as np
+    import torch
+
+    from paper_2401_07361_gb300 import sts
+    from paper_2401_07361_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    level, levels, eps1, eps2, dt, Omega = 5, 3, 0.0025, 0.2, 0.01, 2.0 * math.pi
+    pos0, faces = W.icosahedral_mesh(level)
+    n0 = len(pos0)
+    zeta0 = W.gaussian_vortex_vorticity(pos0, W.equal_areas(n0))
+    leaf = args.leaf or 64
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    mesh, tree = sts.Context(), sts.Context()
+    sts.sts_amr_init(mesh.h, faces, torch.from_numpy(pos0).to(dev), torch.from_numpy(zeta0).to(dev), levels)
+
+    def params(n):
+        return sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16,
+                          precision=sts.STS_MIXED, near_fp64_tau=args.tau_c * 4.0 * math.pi / n)
+
+    t_rk = [0.0]
+    t_amr = [0.0]
+    particle_steps = [0]
+
+    def step():
+        x, z, a, _ = sts.sts_amr_gather(mesh.h)
+        n = x.shape[0]
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        sts.bve_rk4_step(tree.h, x, z, a, dt, Omega, params(n))
+        sts.sts_amr_scatter(mesh.h, x, z)
+        e1.record()
+        counts = sts.sts_amr_step(mesh.h, eps1, eps2)
+        e2.record()
+        e2.synchronize()
+        t_rk[0] += e0.elapsed_time(e1)
+        t_amr[0] += e1.elapsed_time(e2)
+        particle_steps[0] += n
+        return counts
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t_rk[0] = t_amr[0] = 0.0
+    particle_steps[0] = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = sts.sts_launch_count()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record()
+    last = None
+    for _ in range(args.amr):
+        last = step()
+    c1.record()
+    c1.synchronize()
+    clocks = sampler.stop()
+    launches = sts.sts_launch_count() - l0
+    ms = c0.elapsed_time(c1)
+    nfinal = sts.sts_amr_info(mesh.h)["particles"]
+    line = {
+        "metric": "BVE RK4 + AMR particle-steps/s (Gaussian vortex, one AMR pass per step)",
+        "value": particle_steps[0] / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": ws, "steps": args.amr,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.amr, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "gaussian_vortex_ico5_amr", "N_start": n0, "levels": levels, "eps1": eps1,
+                   "eps2": eps2, "dt_day": dt, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
+                   "precision": "mixed", "launch": "host launches (the particle count changes every step)"},
+        "phases_ms_per_step": {"rk4": t_rk[0] / args.amr, "amr_pass": t_amr[0] / args.amr},
+        "particles_end": nfinal, "last_pass": {"splits": last[0], "merges": last[1], "particles": last[2],
+                                               "leaf_triangles": last[3]},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+
+        # a pass visits every possible triangle on both sides, so its cost hardly depends on
+        # the state: the oracle's passes from the initial vortex on the same mesh are timed
+        m = O.Amr(faces, n0, levels)
+        m.set(pos0, zeta0)
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 3 or time.perf_counter() - t0 < 2.0:
+            m.step(eps1, eps2)
+            reps += 1
+        cpu_ms = (time.perf_counter() - t0) * 1e3 / reps
+        line["cpu_baseline"] = {"value": n0 / (cpu_ms / 1e3), "unit": "vertices/s (AMR pass)", "cores": 1,
+                                "kind": "oracle", "sample": f"{reps} oracle AMR passes from the initial vortex "
+                                                            f"on the base mesh ({n0} particles, "
+                                                            f"{m.nt} possible triangles), single thread"}
+        line["amr_pass_gpu_ms"] = t_amr[0] / args.amr
+        line["amr_pass_cpu_ms"] = cpu_ms
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mesh.close()
+    tree.close()
+    return 0
+
+
 def run_potential(args):
     """The stream function psi_i = -(1/4pi) sum_{j != i} log(1 - x_i.x_j) zeta_j A_j by the
     FP64 tree code (tree build + potential per step, same lists and proxies as the velocity),
@@ -429,6 +540,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.amr > 0:
+        return run_amr(args)
     if args.rk4 > 0:
         return run_rk4(args)
     if args.potential:

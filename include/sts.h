@@ -219,6 +219,43 @@ int bve_rk4_step_forced(sts_ctx* ctx, double* pos, double* zeta, const double* a
                         double dt, double Omega, const sts_forcing* forcing, const sts_params* p,
                         void* stream);
 
+/* ---- adaptive mesh refinement (Appendix A) -------------------------------------------- */
+/* The particles are the vertices of a triangulation of the sphere (the refined icosahedron):
+ * faces[nfaces,3] (HOST, vertex indices in [0, n0)) over the base particles pos0[n0,3],
+ * zeta0[n0] (device).  A leaf triangle splits into four (v1, m12, m31), (m12, v2, m23),
+ * (m31, m23, v3), (m12, m23, m31) when the magnitude of its circulation |A (z1 + z2 + z3) / 3|
+ * >= eps1 or its vorticity variation max z - min z >= eps2, at most `levels` (<= 6) times
+ * below the base mesh; four leaf children merge back when neither criterion holds on their
+ * parent's corners and none of them splits.  A is the spherical area of the triangle of the
+ * current corner positions.  Every triangle and vertex the refinement can create is numbered
+ * once here: level by level, each triangle of the previous level in order gives the midpoints
+ * of its edges (v1 v2), (v2 v3), (v3 v1), numbered when first met.  Vertex v < n0 is base
+ * particle v.  A new midpoint is placed at unit(p_a + p_b) of its edge ends' current positions
+ * with vorticity (z_a + z_b) / 2.  The particles are the corners of leaf triangles, weighted by
+ * the sum of A / 3 over them.  Synchronises `stream`.  The mesh lives in ctx until the next
+ * sts_amr_init or sts_destroy. */
+int sts_amr_init(sts_ctx* ctx, const int32_t* faces, int64_t nfaces, int64_t n0, const double* pos0,
+                 const double* zeta0, int32_t levels, void* stream);
+/* One refinement pass (every decision on the state at the start of the pass).  counts (HOST,
+ * may be NULL) [4] = {splits, merges, particles, leaf triangles}.  Synchronises `stream`. */
+int sts_amr_step(sts_ctx* ctx, double eps1, double eps2, int64_t* counts, void* stream);
+/* info (HOST) [5] = {base vertices, possible vertices, base triangles, possible triangles,
+ * particles}. */
+int sts_amr_info(sts_ctx* ctx, int64_t* info);
+/* The particles in vertex order (device outputs, any may be NULL): pos[np,3], zeta[np],
+ * area[np] (the weights) and ids[np] (their vertex numbers), np = info[4]. */
+int sts_amr_gather(sts_ctx* ctx, double* pos, double* zeta, double* area, int64_t* ids, void* stream);
+/* Writes back the particles' positions and vorticities (device, in the order of
+ * sts_amr_gather) and recomputes the weights.  Synchronises `stream`. */
+int sts_amr_scatter(sts_ctx* ctx, const double* pos, const double* zeta, void* stream);
+/* The whole mesh (HOST outputs, any may be NULL): per possible triangle corners tv[nt,3],
+ * parent, first child (-1 at the deepest level), level (0 = base), state (0 absent, 1 leaf,
+ * 2 split); per possible vertex the edge ends vparent[nv,2] (-1 for base vertices), alive
+ * flag, pos[nv,3], zeta[nv], area[nv] (zeros where not alive). */
+int sts_amr_export(sts_ctx* ctx, int32_t* tv, int32_t* tparent, int32_t* tchild, int8_t* tlevel,
+                   int32_t* vparent, uint8_t* tstate, uint8_t* valive, double* pos, double* zeta,
+                   double* area, void* stream);
+
 /* One RK4 step of ninst independent instances (offsets as in sts_tree_build_batched), in
  * place on pos[n,3] and zeta[n]; every stage builds the forest and evaluates all instances
  * together.  Synchronises `stream`. */

@@ -70,6 +70,13 @@ def _L():
             lib.or_dual_export.argtypes = [P, i32, P, P]
             lib.or_tree_velocity_dual.argtypes = [P, P, P, dbl, i32, P, P, i32]
             lib.or_icosahedron.argtypes = [P, P]
+            lib.or_amr_create.argtypes = [P, i64, i64, i32, C.POINTER(P)]
+            lib.or_amr_free.argtypes = [P]
+            lib.or_amr_set.argtypes = [P, P, P]
+            lib.or_amr_step.argtypes = [P, dbl, dbl, P]
+            lib.or_amr_info.argtypes = [P, P]
+            lib.or_amr_export.argtypes = [P] + [P] * 10
+            lib.or_amr_update.argtypes = [P, P, P]
             _lib = lib
     return _lib
 
@@ -242,6 +249,47 @@ class Tree:
         _check(_L().or_tree_clusters(self._h, _p(zeta), _p(area), degree, _p(nc), _p(ids), _p(yt),
                                      _p(W)), "clusters")
         return ids, yt, W
+
+
+class Amr:
+    """Adaptive mesh refinement of Appendix A over a particle triangulation (base faces
+    ``faces[t0, 3]`` over ``n0`` base particles, at most ``levels`` levels of splitting)."""
+
+    def __init__(self, faces, n0: int, levels: int = 3):
+        faces = np.ascontiguousarray(faces, dtype=np.int32)
+        self._h = C.c_void_p()
+        _check(_L().or_amr_create(_p(faces), faces.shape[0], int(n0), int(levels), C.byref(self._h)), "amr create")
+        info = np.zeros(4, np.int64)
+        _check(_L().or_amr_info(self._h, _p(info)), "amr info")
+        self.n0, self.nv, self.t0, self.nt = (int(x) for x in info)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _L().or_amr_free(self._h)
+            self._h = None
+
+    def set(self, pos0, zeta0):
+        _check(_L().or_amr_set(self._h, _p(_f64(pos0, (self.n0, 3))), _p(_f64(zeta0, (self.n0,)))), "amr set")
+
+    def update(self, pos, zeta):
+        """Positions and vorticities of the alive vertices (arrays over all vertices)."""
+        _check(_L().or_amr_update(self._h, _p(_f64(pos, (self.nv, 3))), _p(_f64(zeta, (self.nv,)))), "amr update")
+
+    def step(self, eps1: float, eps2: float):
+        """One refinement pass; returns (splits, merges, alive vertices, leaf triangles)."""
+        c = np.zeros(4, np.int64)
+        _check(_L().or_amr_step(self._h, float(eps1), float(eps2), _p(c)), "amr step")
+        return tuple(int(x) for x in c)
+
+    def export(self):
+        nt, nv = self.nt, self.nv
+        o = dict(tv=np.zeros((nt, 3), np.int32), tparent=np.zeros(nt, np.int32), tchild=np.zeros(nt, np.int32),
+                 tlevel=np.zeros(nt, np.int8), vparent=np.zeros((nv, 2), np.int32), tstate=np.zeros(nt, np.uint8),
+                 valive=np.zeros(nv, np.uint8), pos=np.zeros((nv, 3)), zeta=np.zeros(nv), area=np.zeros(nv))
+        _check(_L().or_amr_export(self._h, *(_p(o[k]) for k in ("tv", "tparent", "tchild", "tlevel", "vparent",
+                                                                 "tstate", "valive", "pos", "zeta", "area"))),
+               "amr export")
+        return o
 
 
 def tree_velocity(pos, zeta, area, theta=0.7, degree=8, leaf_size=128, max_level=16, nthreads=0):

@@ -37,6 +37,9 @@
  *                         the stream function: the same sums with the Green's function
  *                         G = -(1/4pi) log(1 - x.y) of Sec. 2 as the kernel (the convolution
  *                         of Sec. 3 with that G); pc_literal_pot is its printed PC form.
+ *   or_amr_*              the adaptive mesh refinement of Appendix A (split and merge of the
+ *                         particle triangulation by the circulation and vorticity-variation
+ *                         criteria, at most `levels` levels below the base mesh).
  */
 #include <math.h>
 #include <stdint.h>
@@ -1506,5 +1509,302 @@ int or_icosahedron(double* V, int32_t* F)
     }
     for (int i = 0; i < 20; i++)
         for (int a = 0; a < 3; a++) F[3 * i + a] = f[i][a];
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------- */
+/* Adaptive mesh refinement of Appendix A.  The particles are the vertices of a triangulation
+ * of the sphere (the refined icosahedron) with a tree structure: each leaf triangle may be
+ * split into four, up to `levels` times below the base mesh, and merged back.
+ *
+ * Readings (the appendix gives the criteria and the limits, not the bookkeeping):
+ *   mesh      the base triangles come from the caller (faces of the base particles); the
+ *             possible refinements are numbered once: level by level, every triangle of the
+ *             previous level in order gives the midpoint vertices of its edges (v1 v2),
+ *             (v2 v3), (v3 v1), each numbered when first met (shared edges share it), and the
+ *             children (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
+ *   area      A = the spherical excess 2 atan2(|a . (b x c)|, 1 + a.b + b.c + c.a) of the
+ *             triangle of the three current corner positions.
+ *   criteria  refine a leaf when |A (z1 + z2 + z3) / 3| >= eps1 (the magnitude of its
+ *             circulation) or max z - min z >= eps2, below the level limit; merge the four
+ *             leaf children of a triangle when neither criterion holds on the parent's corners
+ *             and no child is to be refined.  One pass per call: every decision is taken on
+ *             the state at the start of the pass, then merges and splits are applied.
+ *   new vertex  at a split, a midpoint not alive yet is placed at unit(p_a + p_b) of the
+ *             current positions of its edge's ends, with vorticity (z_a + z_b) / 2.
+ *   alive     a vertex is a particle when it is a corner of a leaf triangle; its weight is the
+ *             sum of A / 3 over the leaf triangles it is a corner of.                       */
+typedef struct or_amr {
+    int64_t n0, nv;      /* base vertices, all possible vertices */
+    int64_t t0, nt;      /* base triangles, all possible triangles */
+    int levels;
+    int32_t* tv;         /* [nt][3] corners */
+    int32_t* tparent;    /* [nt] parent or -1 */
+    int32_t* tchild;     /* [nt] first of the four children or -1 (deepest level) */
+    int8_t* tlevel;      /* [nt] 0 = base */
+    int32_t* vparent;    /* [nv][2] edge ends of a midpoint vertex (-1 for base vertices) */
+    uint8_t* tstate;     /* [nt] 0 absent, 1 leaf, 2 split */
+    uint8_t* valive;     /* [nv] */
+    double *pos, *zeta, *area; /* [nv][3], [nv], [nv] */
+} or_amr;
+
+void or_amr_free(or_amr* m)
+{
+    if (!m) return;
+    free(m->tv); free(m->tparent); free(m->tchild); free(m->tlevel); free(m->vparent);
+    free(m->tstate); free(m->valive); free(m->pos); free(m->zeta); free(m->area);
+    free(m);
+}
+
+int or_amr_create(const int32_t* faces, int64_t t0, int64_t n0, int levels, or_amr** out)
+{
+    if (!faces || !out || t0 < 1 || n0 < 3 || levels < 0 || levels > 6) return OR_ERR_ARG;
+    int64_t nt = 0, per = t0;
+    for (int l = 0; l <= levels; l++, per *= 4) nt += per;
+    /* vertices: at most 3 new ones per triangle that has children (all but the deepest
+     * level, t0 4^levels = per / 4 triangles) */
+    const int64_t nvmax = n0 + 3 * (nt - per / 4);
+    or_amr* m = (or_amr*)calloc(1, sizeof(or_amr));
+    if (!m) return OR_ERR_MEM;
+    m->n0 = n0; m->t0 = t0; m->nt = nt; m->levels = levels;
+    m->tv = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)nt);
+    m->tparent = (int32_t*)malloc(sizeof(int32_t) * (size_t)nt);
+    m->tchild = (int32_t*)malloc(sizeof(int32_t) * (size_t)nt);
+    m->tlevel = (int8_t*)malloc((size_t)nt);
+    m->vparent = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)nvmax);
+    if (!m->tv || !m->tparent || !m->tchild || !m->tlevel || !m->vparent) {
+        or_amr_free(m);
+        return OR_ERR_MEM;
+    }
+    for (int64_t t = 0; t < t0; t++) {
+        for (int a = 0; a < 3; a++) {
+            if (faces[3 * t + a] < 0 || faces[3 * t + a] >= n0) {
+                or_amr_free(m);
+                return OR_ERR_ARG;
+            }
+            m->tv[3 * t + a] = faces[3 * t + a];
+        }
+        m->tparent[t] = -1;
+        m->tlevel[t] = 0;
+    }
+    for (int64_t v = 0; v < n0; v++) m->vparent[2 * v] = m->vparent[2 * v + 1] = -1;
+    int64_t nv = n0, lb = 0, le = t0;
+    /* edge -> midpoint map of one level: open addressing on the key lo * nvmax + hi */
+    for (int l = 1; l <= levels; l++) {
+        const int64_t ntl = le - lb, cap = 8 * ntl + 16;
+        int64_t* hk = (int64_t*)malloc(sizeof(int64_t) * (size_t)cap);
+        int32_t* hv = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+        if (!hk || !hv) {
+            free(hk); free(hv); or_amr_free(m);
+            return OR_ERR_MEM;
+        }
+        for (int64_t q = 0; q < cap; q++) hk[q] = -1;
+        int64_t nc = le;
+        for (int64_t t = lb; t < le; t++) {
+            int32_t mid[3];
+            for (int e = 0; e < 3; e++) {
+                const int32_t a = m->tv[3 * t + e], b = m->tv[3 * t + (e + 1) % 3];
+                const int64_t lo = a < b ? a : b, hi = a < b ? b : a, key = lo * nvmax + hi;
+                int64_t q = (int64_t)((uint64_t)key * 0x9E3779B97F4A7C15ull % (uint64_t)cap);
+                while (hk[q] != -1 && hk[q] != key) q = (q + 1) % cap;
+                if (hk[q] == -1) {
+                    hk[q] = key;
+                    hv[q] = (int32_t)nv;
+                    m->vparent[2 * nv] = a;
+                    m->vparent[2 * nv + 1] = b;
+                    nv++;
+                }
+                mid[e] = hv[q];
+            }
+            const int32_t v1 = m->tv[3 * t], v2 = m->tv[3 * t + 1], v3 = m->tv[3 * t + 2];
+            const int32_t m12 = mid[0], m23 = mid[1], m31 = mid[2];
+            const int32_t ch[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
+            m->tchild[t] = (int32_t)nc;
+            for (int c = 0; c < 4; c++, nc++) {
+                for (int a = 0; a < 3; a++) m->tv[3 * nc + a] = ch[c][a];
+                m->tparent[nc] = (int32_t)t;
+                m->tlevel[nc] = (int8_t)l;
+            }
+        }
+        free(hk);
+        free(hv);
+        lb = le;
+        le = nc;
+    }
+    for (int64_t t = lb; t < le; t++) m->tchild[t] = -1;
+    m->nv = nv;
+    m->tstate = (uint8_t*)calloc((size_t)nt, 1);
+    m->valive = (uint8_t*)calloc((size_t)nv, 1);
+    m->pos = (double*)calloc(3 * (size_t)nv, sizeof(double));
+    m->zeta = (double*)calloc((size_t)nv, sizeof(double));
+    m->area = (double*)calloc((size_t)nv, sizeof(double));
+    if (!m->tstate || !m->valive || !m->pos || !m->zeta || !m->area) {
+        or_amr_free(m);
+        return OR_ERR_MEM;
+    }
+    for (int64_t t = 0; t < t0; t++) m->tstate[t] = 1;
+    for (int64_t v = 0; v < n0; v++) m->valive[v] = 1;
+    *out = m;
+    return OR_OK;
+}
+
+static double amr_area(const double* pos, const int32_t* tv)
+{
+    const v3 a = ld3(pos, tv[0]), b = ld3(pos, tv[1]), c = ld3(pos, tv[2]);
+    const double det = vdot(a, vcross(b, c));
+    const double den = ((1.0 + vdot(a, b)) + vdot(b, c)) + vdot(c, a);
+    return 2.0 * atan2(fabs(det), den);
+}
+
+static int amr_crit(const or_amr* m, int64_t t, double eps1, double eps2)
+{
+    const int32_t* tv = m->tv + 3 * t;
+    const double z1 = m->zeta[tv[0]], z2 = m->zeta[tv[1]], z3 = m->zeta[tv[2]];
+    const double A = amr_area(m->pos, tv);
+    const double circ = A * (((z1 + z2) + z3) / 3.0);
+    double zmax = z1, zmin = z1;
+    if (z2 > zmax) zmax = z2;
+    if (z3 > zmax) zmax = z3;
+    if (z2 < zmin) zmin = z2;
+    if (z3 < zmin) zmin = z3;
+    return fabs(circ) >= eps1 || zmax - zmin >= eps2;
+}
+
+/* Particle weights: sum of A / 3 over the leaf triangles of each alive vertex (triangles in
+ * index order). */
+static void amr_areas(or_amr* m)
+{
+    for (int64_t v = 0; v < m->nv; v++) m->area[v] = 0.0;
+    for (int64_t t = 0; t < m->nt; t++) {
+        if (m->tstate[t] != 1) continue;
+        const double w = amr_area(m->pos, m->tv + 3 * t) / 3.0;
+        for (int a = 0; a < 3; a++) m->area[m->tv[3 * t + a]] += w;
+    }
+}
+
+int or_amr_set(or_amr* m, const double* pos0, const double* zeta0)
+{
+    if (!m || !pos0 || !zeta0) return OR_ERR_ARG;
+    for (int64_t v = 0; v < m->n0; v++) {
+        for (int a = 0; a < 3; a++) m->pos[3 * v + a] = pos0[3 * v + a];
+        m->zeta[v] = zeta0[v];
+    }
+    amr_areas(m);
+    return OR_OK;
+}
+
+int or_amr_step(or_amr* m, double eps1, double eps2, int64_t* counts)
+{
+    if (!m) return OR_ERR_ARG;
+    uint8_t* refine = (uint8_t*)calloc((size_t)m->nt, 1);
+    uint8_t* merge = (uint8_t*)calloc((size_t)m->nt, 1);
+    uint8_t* alive0 = (uint8_t*)malloc((size_t)m->nv);
+    if (!refine || !merge || !alive0) {
+        free(refine); free(merge); free(alive0);
+        return OR_ERR_MEM;
+    }
+    memcpy(alive0, m->valive, (size_t)m->nv);
+    int64_t nref = 0, nmerge = 0;
+    for (int64_t t = 0; t < m->nt; t++)
+        if (m->tstate[t] == 1 && m->tlevel[t] < m->levels && amr_crit(m, t, eps1, eps2)) refine[t] = 1;
+    for (int64_t t = 0; t < m->nt; t++) {
+        if (m->tstate[t] != 2) continue;
+        const int32_t c0 = m->tchild[t];
+        int ok = 1;
+        for (int c = 0; c < 4; c++) ok = ok && m->tstate[c0 + c] == 1 && !refine[c0 + c];
+        if (ok && !amr_crit(m, t, eps1, eps2)) merge[t] = 1;
+    }
+    for (int64_t t = 0; t < m->nt; t++) {
+        if (merge[t]) {
+            m->tstate[t] = 1;
+            for (int c = 0; c < 4; c++) m->tstate[m->tchild[t] + c] = 0;
+            nmerge++;
+        }
+        if (refine[t]) {
+            m->tstate[t] = 2;
+            const int32_t c0 = m->tchild[t];
+            for (int c = 0; c < 4; c++) m->tstate[c0 + c] = 1;
+            /* midpoints: the corners of the centre child (m12, m23, m31) */
+            for (int a = 0; a < 3; a++) {
+                const int32_t v = m->tv[3 * (c0 + 3) + a];
+                if (alive0[v]) continue;
+                const int32_t pa = m->vparent[2 * v], pb = m->vparent[2 * v + 1];
+                const double sx = m->pos[3 * pa] + m->pos[3 * pb];
+                const double sy = m->pos[3 * pa + 1] + m->pos[3 * pb + 1];
+                const double sz = m->pos[3 * pa + 2] + m->pos[3 * pb + 2];
+                const double r = sqrt((sx * sx + sy * sy) + sz * sz);
+                m->pos[3 * v] = sx / r;
+                m->pos[3 * v + 1] = sy / r;
+                m->pos[3 * v + 2] = sz / r;
+                m->zeta[v] = (m->zeta[pa] + m->zeta[pb]) * 0.5;
+            }
+            nref++;
+        }
+    }
+    /* alive vertices: the corners of leaf triangles; a removed vertex's state is cleared */
+    memset(m->valive, 0, (size_t)m->nv);
+    for (int64_t t = 0; t < m->nt; t++)
+        if (m->tstate[t] == 1)
+            for (int a = 0; a < 3; a++) m->valive[m->tv[3 * t + a]] = 1;
+    for (int64_t v = 0; v < m->nv; v++)
+        if (!m->valive[v]) {
+            m->pos[3 * v] = m->pos[3 * v + 1] = m->pos[3 * v + 2] = 0.0;
+            m->zeta[v] = 0.0;
+        }
+    amr_areas(m);
+    if (counts) {
+        int64_t na = 0, nl = 0;
+        for (int64_t v = 0; v < m->nv; v++) na += m->valive[v];
+        for (int64_t t = 0; t < m->nt; t++) nl += m->tstate[t] == 1;
+        counts[0] = nref;
+        counts[1] = nmerge;
+        counts[2] = na;
+        counts[3] = nl;
+    }
+    free(refine);
+    free(merge);
+    free(alive0);
+    return OR_OK;
+}
+
+int or_amr_info(const or_amr* m, int64_t* info)
+{
+    if (!m || !info) return OR_ERR_ARG;
+    info[0] = m->n0;
+    info[1] = m->nv;
+    info[2] = m->t0;
+    info[3] = m->nt;
+    return OR_OK;
+}
+
+/* Full state: tables (any pointer may be NULL) and per-vertex / per-triangle state. */
+int or_amr_export(const or_amr* m, int32_t* tv, int32_t* tparent, int32_t* tchild, int8_t* tlevel,
+                  int32_t* vparent, uint8_t* tstate, uint8_t* valive, double* pos, double* zeta, double* area)
+{
+    if (!m) return OR_ERR_ARG;
+    if (tv) memcpy(tv, m->tv, sizeof(int32_t) * 3 * (size_t)m->nt);
+    if (tparent) memcpy(tparent, m->tparent, sizeof(int32_t) * (size_t)m->nt);
+    if (tchild) memcpy(tchild, m->tchild, sizeof(int32_t) * (size_t)m->nt);
+    if (tlevel) memcpy(tlevel, m->tlevel, (size_t)m->nt);
+    if (vparent) memcpy(vparent, m->vparent, sizeof(int32_t) * 2 * (size_t)m->nv);
+    if (tstate) memcpy(tstate, m->tstate, (size_t)m->nt);
+    if (valive) memcpy(valive, m->valive, (size_t)m->nv);
+    if (pos) memcpy(pos, m->pos, sizeof(double) * 3 * (size_t)m->nv);
+    if (zeta) memcpy(zeta, m->zeta, sizeof(double) * (size_t)m->nv);
+    if (area) memcpy(area, m->area, sizeof(double) * (size_t)m->nv);
+    return OR_OK;
+}
+
+/* Writes positions and vorticities of the alive vertices (e.g. after a time step): pos[nv,3],
+ * zeta[nv] indexed by vertex; entries of vertices that are not alive are ignored. */
+int or_amr_update(or_amr* m, const double* pos, const double* zeta)
+{
+    if (!m || !pos || !zeta) return OR_ERR_ARG;
+    for (int64_t v = 0; v < m->nv; v++)
+        if (m->valive[v]) {
+            for (int a = 0; a < 3; a++) m->pos[3 * v + a] = pos[3 * v + a];
+            m->zeta[v] = zeta[v];
+        }
+    amr_areas(m);
     return OR_OK;
 }

@@ -19,11 +19,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsts.so")
 
 SOURCES = ["sts_api.cu", "sts_tables.cu", "sts_scan.cu", "sts_tree.cu", "sts_upward.cu",
-           "sts_eval.cu", "sts_rk4.cu"]
+           "sts_eval.cu", "sts_rk4.cu", "sts_amr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-Xptxas", "-v"]
-PER_FILE = {"sts_tree.cu": ["--fmad=false"]}
+PER_FILE = {"sts_tree.cu": ["--fmad=false"], "sts_amr.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

@@ -94,6 +94,13 @@ sts_ctx::~sts_ctx()
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
     rk_k.release(); rk_ksum.release(); d_stats.release();
+    dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
+    dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
+    dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
+    dual_scan.release(); cfar_off.release(); cnear_off.release(); cnear_coff.release(); cfar_ent.release();
+    cnear_ent.release(); ctasks.release(); cvel.release(); ccorr.release(); cdown.release(); chas.release();
+    cacc.release();
+    if (amr) amr_free(amr);
     for (RefTable* t : refs)
         if (t) {
             t->d_beta.release();
@@ -838,6 +845,80 @@ int sts_dual_export(sts_ctx* ctx, int32_t kind, int64_t* npairs, int32_t* tgt, i
     }
     if ((rc = refresh_counts(ctx, S(stream)))) return rc;
     return dual_export(ctx, kind, npairs, tgt, src, S(stream));
+}
+
+int sts_amr_init(sts_ctx* ctx, const int32_t* faces, int64_t nfaces, int64_t n0, const double* pos0,
+                 const double* zeta0, int32_t levels, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_amr_init");
+    if (rc) return rc;
+    if (!faces || !pos0 || !zeta0 || nfaces < 1 || n0 < 3 || levels < 0 || levels > 6) {
+        set_error("sts_amr_init: need faces, pos0, zeta0, nfaces >= 1, n0 >= 3 and 0 <= levels <= 6");
+        return STS_ERR_ARG;
+    }
+    if ((rc = check_n(n0, "sts_amr_init"))) return rc;
+    return amr_init(ctx, faces, nfaces, n0, pos0, zeta0, levels, S(stream));
+}
+
+int sts_amr_step(sts_ctx* ctx, double eps1, double eps2, int64_t* counts, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_amr_step");
+    if (rc) return rc;
+    if (!ctx->amr) {
+        set_error("sts_amr_step: no mesh (call sts_amr_init first)");
+        return STS_ERR_STATE;
+    }
+    if (std::isnan(eps1) || std::isnan(eps2)) {
+        set_error("sts_amr_step: eps1 and eps2 must not be NaN");
+        return STS_ERR_ARG;
+    }
+    return amr_step(ctx, eps1, eps2, counts, S(stream));
+}
+
+int sts_amr_info(sts_ctx* ctx, int64_t* info)
+{
+    int rc = check_ctx(ctx, "sts_amr_info");
+    if (rc) return rc;
+    if (!ctx->amr || !info) {
+        set_error("sts_amr_info: no mesh or NULL info");
+        return ctx->amr ? STS_ERR_ARG : STS_ERR_STATE;
+    }
+    return amr_info(ctx, info);
+}
+
+int sts_amr_gather(sts_ctx* ctx, double* pos, double* zeta, double* area, int64_t* ids, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_amr_gather");
+    if (rc) return rc;
+    if (!ctx->amr) {
+        set_error("sts_amr_gather: no mesh (call sts_amr_init first)");
+        return STS_ERR_STATE;
+    }
+    return amr_gather(ctx, pos, zeta, area, ids, S(stream));
+}
+
+int sts_amr_scatter(sts_ctx* ctx, const double* pos, const double* zeta, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_amr_scatter");
+    if (rc) return rc;
+    if (!ctx->amr || !pos || !zeta) {
+        set_error("sts_amr_scatter: no mesh or NULL array");
+        return ctx->amr ? STS_ERR_ARG : STS_ERR_STATE;
+    }
+    return amr_scatter(ctx, pos, zeta, S(stream));
+}
+
+int sts_amr_export(sts_ctx* ctx, int32_t* tv, int32_t* tparent, int32_t* tchild, int8_t* tlevel,
+                   int32_t* vparent, uint8_t* tstate, uint8_t* valive, double* pos, double* zeta, double* area,
+                   void* stream)
+{
+    int rc = check_ctx(ctx, "sts_amr_export");
+    if (rc) return rc;
+    if (!ctx->amr) {
+        set_error("sts_amr_export: no mesh (call sts_amr_init first)");
+        return STS_ERR_STATE;
+    }
+    return amr_export(ctx, tv, tparent, tchild, tlevel, vparent, tstate, valive, pos, zeta, area, S(stream));
 }
 
 int sts_set_traversal(sts_ctx* ctx, int32_t dual)

@@ -144,6 +144,8 @@ struct Plan {
     int64_t dual_front = 0, dual_terms = 0, dual_pairs[4] = {0, 0, 0, 0}, dual_chunks[2] = {0, 0};
 };
 
+struct AmrState;  // adaptive mesh refinement of the particle triangulation (sts_amr.cu)
+
 }  // namespace sts
 
 struct sts_ctx {
@@ -268,6 +270,9 @@ struct sts_ctx {
     sts::DevBuf<uint8_t> chas;           // [C] the cluster is the target of CP or CC pairs
     sts::DevBuf<uint8_t> cacc;           // [C] the cluster holds an interpolant (its own or an ancestor's)
 
+    // ---- adaptive mesh refinement (Appendix A) -----------------------------------------
+    sts::AmrState* amr = nullptr;
+
     // ---- direct sum scratch ------------------------------------------------------------
     sts::DevBuf<double4> dsrc64;
     sts::DevBuf<float4> dsrc32;          // [2n]: hi (x, y, z, 2w), lo (x, y, z, 0)
@@ -325,6 +330,17 @@ int build_dual(sts_ctx* ctx, double theta, cudaStream_t s);
 int reserve_dual_for_capture(sts_ctx* ctx, int degree, cudaStream_t s);
 // Host copies of the dual pair counts after a recorded step ran.
 int refresh_dual_counts(sts_ctx* ctx, cudaStream_t s);
+
+// ---- adaptive mesh refinement (sts_amr.cu) -------------------------------------------------
+void amr_free(AmrState* m);
+int amr_init(sts_ctx* c, const int32_t* faces, int64_t t0, int64_t n0, const double* pos0, const double* zeta0,
+             int levels, cudaStream_t s);
+int amr_step(sts_ctx* c, double eps1, double eps2, int64_t* counts, cudaStream_t s);
+int amr_gather(sts_ctx* c, double* pos, double* zeta, double* area, int64_t* ids, cudaStream_t s);
+int amr_scatter(sts_ctx* c, const double* pos, const double* zeta, cudaStream_t s);
+int amr_info(sts_ctx* c, int64_t* info);
+int amr_export(sts_ctx* c, int32_t* tv, int32_t* tparent, int32_t* tchild, int8_t* tlevel, int32_t* vparent,
+               uint8_t* tstate, uint8_t* valive, double* pos, double* zeta, double* area, cudaStream_t s);
 // Pair counts of the dual lists: stats[0..3] = PP pairs (j != i), PC, CP, CC interactions.
 int dual_stats(sts_ctx* ctx, int degree, int64_t* stats, cudaStream_t s);
 // Evaluation tasks of the clusters that are targets of CP or CC pairs, and their has flags;

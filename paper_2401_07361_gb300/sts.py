@@ -83,6 +83,12 @@ def load(build_if_needed: bool = True):
             "sts_dual_export": (i32, [P, i32, P, P, P, P]),
             "sts_dual_stats": (i32, [P, i32, P, P]),
             "sts_set_traversal": (i32, [P, i32]),
+            "sts_amr_init": (i32, [P, P, i64, i64, P, P, i32, P]),
+            "sts_amr_step": (i32, [P, dbl, dbl, P, P]),
+            "sts_amr_info": (i32, [P, P]),
+            "sts_amr_gather": (i32, [P, P, P, P, P, P]),
+            "sts_amr_scatter": (i32, [P, P, P, P]),
+            "sts_amr_export": (i32, [P] + [P] * 10 + [P]),
             "sts_direct_potential": (i32, [P, P, P, P, i64, i32, P, P]),
             "bve_rk4_step": (i32, [P, P, P, P, i64, dbl, dbl, PP, P]),
             "bve_rk4_step_forced": (i32, [P, P, P, P, i64, dbl, dbl, dbl, C.POINTER(sts_forcing), PP, P]),
@@ -251,6 +257,67 @@ def sts_dual_export(ctx, stream=None):
         _check(load().sts_dual_export(ctx, k, _host(cnt), _host(t), _host(s), _stream(stream)), "sts_dual_export")
         out[name] = (t, s)
     return out
+
+
+# ---------------------------------------------------------------------------- adaptive mesh
+def sts_amr_init(ctx, faces, pos0, zeta0, levels=3, stream=None):
+    """Adaptive mesh over the base triangulation faces[t0, 3] (host) of the particles pos0[n0, 3],
+    zeta0[n0] (device)."""
+    import torch
+
+    faces = np.ascontiguousarray(faces, dtype=np.int32)
+    n0 = pos0.shape[0]
+    _check(load().sts_amr_init(ctx, _host(faces), faces.shape[0], n0, _dev(pos0, torch.float64, 3 * n0, "pos0"),
+                               _dev(zeta0, torch.float64, n0, "zeta0"), int(levels), _stream(stream)), "sts_amr_init")
+
+
+def sts_amr_step(ctx, eps1, eps2, stream=None):
+    """One refinement pass; returns (splits, merges, particles, leaf triangles)."""
+    c = np.zeros(4, np.int64)
+    _check(load().sts_amr_step(ctx, float(eps1), float(eps2), _host(c), _stream(stream)), "sts_amr_step")
+    return tuple(int(x) for x in c)
+
+
+def sts_amr_info(ctx):
+    a = np.zeros(5, np.int64)
+    _check(load().sts_amr_info(ctx, _host(a)), "sts_amr_info")
+    return dict(n0=int(a[0]), nv=int(a[1]), t0=int(a[2]), nt=int(a[3]), particles=int(a[4]))
+
+
+def sts_amr_gather(ctx, stream=None):
+    """The particles (device tensors): pos[np, 3], zeta[np], area[np], ids[np]."""
+    import torch
+
+    n = sts_amr_info(ctx)["particles"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pos = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    zeta = torch.empty(n, dtype=torch.float64, device=dev)
+    area = torch.empty(n, dtype=torch.float64, device=dev)
+    ids = torch.empty(n, dtype=torch.int64, device=dev)
+    _check(load().sts_amr_gather(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                                 _dev(area, torch.float64, n, "area"), _dev(ids, torch.int64, n, "ids"),
+                                 _stream(stream)), "sts_amr_gather")
+    return pos, zeta, area, ids
+
+
+def sts_amr_scatter(ctx, pos, zeta, stream=None):
+    import torch
+
+    n = pos.shape[0]
+    _check(load().sts_amr_scatter(ctx, _dev(pos, torch.float64, 3 * n, "pos"), _dev(zeta, torch.float64, n, "zeta"),
+                                  _stream(stream)), "sts_amr_scatter")
+
+
+def sts_amr_export(ctx, stream=None):
+    i = sts_amr_info(ctx)
+    nt, nv = i["nt"], i["nv"]
+    o = dict(tv=np.zeros((nt, 3), np.int32), tparent=np.zeros(nt, np.int32), tchild=np.zeros(nt, np.int32),
+             tlevel=np.zeros(nt, np.int8), vparent=np.zeros((nv, 2), np.int32), tstate=np.zeros(nt, np.uint8),
+             valive=np.zeros(nv, np.uint8), pos=np.zeros((nv, 3)), zeta=np.zeros(nv), area=np.zeros(nv))
+    _check(load().sts_amr_export(ctx, *(_host(o[k]) for k in ("tv", "tparent", "tchild", "tlevel", "vparent",
+                                                               "tstate", "valive", "pos", "zeta", "area")),
+                                 _stream(stream)), "sts_amr_export")
+    return o
 
 
 def sts_set_traversal(ctx, dual=True):

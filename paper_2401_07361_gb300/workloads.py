@@ -83,6 +83,42 @@ def icosahedral_points(level: int) -> np.ndarray:
     return out
 
 
+def icosahedral_mesh(level: int):
+    """The refined icosahedron as a triangulation: vertices ``[10 * 4**level + 2, 3]`` (those
+    of ``icosahedral_points(level)``, same order) and faces ``int32 [20 * 4**level, 3]`` (the
+    children of each face in the order (a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca))."""
+    v = [tuple(p) for p in _icosahedron_vertices()]
+    pts = list(v)
+    faces = [tuple(int(x) for x in f) for f in _icosahedron_faces(np.array(v))]
+    for _ in range(level):
+        mid = {}
+        new_faces = []
+
+        def midpoint(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in mid:
+                p = np.add(pts[a], pts[b])
+                p = p / np.linalg.norm(p)
+                mid[key] = len(pts)
+                pts.append(tuple(p))
+            return mid[key]
+
+        for a, b, c in faces:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            new_faces += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        faces = new_faces
+    return np.array(pts, dtype=np.float64), np.array(faces, dtype=np.int32)
+
+
+def gaussian_vortex_vorticity(pos, area, lat_c=math.pi / 20, lon_c=0.0):
+    """Initial vorticity of the Gaussian vortex test (Sec. 4.3): 4 pi exp(-16 |x - x_c|^2) + C
+    (per day), x_c at latitude lat_c and longitude lon_c, C such that sum zeta A = 0."""
+    xc = np.array([math.cos(lat_c) * math.cos(lon_c), math.cos(lat_c) * math.sin(lon_c), math.sin(lat_c)])
+    d2 = np.sum((pos - xc) ** 2, axis=1)
+    z = 4.0 * math.pi * np.exp(-16.0 * d2)
+    return z - np.sum(z * area) / np.sum(area)
+
+
 def uniform_points(n: int, seed: int = 0) -> np.ndarray:
     """``n`` points uniform on the unit sphere, float64 ``[n, 3]``."""
     rng = np.random.default_rng(seed)

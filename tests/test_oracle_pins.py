@@ -605,3 +605,68 @@ def test_dual_tiny_theta_is_direct_and_error_falls_with_degree():
         band = json.load(f)["tree_accuracy_theta0.7_d6"]
     # Sec. 4.1's "between 3 and 4 digits" at theta 0.7, d 6 is printed for this (dual) method
     assert band["E_min"] / 10 <= errs[6] <= band["E_max"], errs
+
+
+# ---------------------------------------------------------------- adaptive mesh refinement (F4)
+def _amr_mesh(level, levels=3):
+    pos, faces = W.icosahedral_mesh(level)
+    return pos, faces, O.Amr(faces, len(pos), levels)
+
+
+def test_amr_full_refinement_is_the_refined_icosahedron():
+    """Splitting every triangle `levels` times reproduces the icosahedron refined that many
+    more times (vertex numbering, order and positions), and stops at the level limit."""
+    pos, faces, m = _amr_mesh(1, 2)
+    m.set(pos, np.zeros(len(pos)))
+    for _ in range(4):  # two passes more than the limit allows
+        m.step(0.0, 0.0)
+    e = m.export()
+    ref = W.icosahedral_points(3)
+    alive = e["valive"].astype(bool)
+    assert alive.sum() == len(ref) == 10 * 4**3 + 2
+    assert np.array_equal(np.flatnonzero(alive), np.arange(len(ref)))
+    assert np.max(np.abs(e["pos"][alive] - ref)) <= 4e-16
+    leaves = e["tstate"] == 1
+    assert leaves.sum() == 20 * 4**3 and (e["tlevel"][leaves] == 2).all()
+
+
+def test_amr_merge_restores_the_base_mesh():
+    pos, faces, m = _amr_mesh(1, 3)
+    z = np.random.default_rng(3).standard_normal(len(pos))
+    m.set(pos, z)
+    for _ in range(3):
+        m.step(0.0, 0.0)
+    for _ in range(3):
+        m.step(np.inf, np.inf)
+    e = m.export()
+    assert (e["tstate"][: m.t0] == 1).all() and (e["tstate"][m.t0:] == 0).all()
+    assert np.flatnonzero(e["valive"]).tolist() == list(range(len(pos)))
+    assert np.array_equal(e["zeta"][: len(pos)], z) and np.array_equal(e["pos"][: len(pos)], pos)
+
+
+def test_amr_spike_splits_exactly_the_triangles_around_it_and_weights_tile_the_sphere():
+    """A vorticity spike at one particle trips the variation criterion on exactly the base
+    triangles around it (5 at an icosahedron corner); their midpoints get the mean vorticity of
+    their edge ends and lie on the sphere; the neighbours keep their corners (hanging
+    vertices), and the weights still sum to 4 pi."""
+    pos, faces, m = _amr_mesh(1, 3)
+    z = np.zeros(len(pos))
+    z[0] = 1.0
+    m.set(pos, z)
+    splits, merges, nalive, nleaf = m.step(np.inf, 0.5)
+    around = np.flatnonzero((faces == 0).any(axis=1))
+    assert splits == len(around) == 5 and merges == 0
+    e = m.export()
+    assert (e["tstate"][around] == 2).all() and (np.delete(e["tstate"][: m.t0], around) == 1).all()
+    new = np.flatnonzero(e["valive"][len(pos):]) + len(pos)
+    assert nalive == len(pos) + len(new) and len(new) == 10  # 5 spokes + 5 rim edges
+    for v in new:
+        a, b = e["vparent"][v]
+        assert e["zeta"][v] == 0.5 * (z[a] + z[b])
+        assert abs(np.linalg.norm(e["pos"][v]) - 1.0) <= 2e-16
+    assert abs(e["area"].sum() - 4 * math.pi) <= 1e-12
+    assert (e["area"][e["valive"].astype(bool)] > 0).all() and (e["area"][~e["valive"].astype(bool)] == 0).all()
+    # the next pass splits the children that still see the spike, one level deeper only
+    m.step(np.inf, 0.5)
+    e2 = m.export()
+    assert e2["tlevel"][e2["tstate"] == 1].max() == 2
