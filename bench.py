@@ -330,7 +330,8 @@ def run_amr(args):
     Appendix A after every step: per step, the particles are gathered from the mesh, advanced by
     one RK4 step of the tree code (eager: the particle count changes between steps), written
     back, and one AMR pass splits and merges triangles.  Reports particle-steps/s and the AMR
-    pass time; the oracle's AMR pass on the same final state is the CPU baseline."""
+    pass time; the CPU baseline is the oracle's AMR pass on the same mesh (its cost depends on
+    the number of possible triangles, not on the state)."""
     import numpy as np
     import torch
 
