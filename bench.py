@@ -157,12 +157,14 @@ class ClockSampler:
         return out
 
 
-def profile_traffic(kernel_file):
-    """DRAM bytes per launch of the evaluation kernel from the committed ncu summary, or None
-    when the summary is missing or was taken on a different kernel source."""
+def profile_traffic(kernel_file, workload, dual=False):
+    """DRAM bytes per launch of the evaluation kernel from the committed ncu summary of this
+    workload and traversal, or None when there is none or it was taken on a different kernel
+    source."""
     import hashlib
 
-    prof = os.path.join(ROOT, "profiles", "k_eval_mixed_rand655k_sh16.md")
+    name = f"k_eval_mixed_{workload}{'_dual_leaves' if dual else ''}.md"
+    prof = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(prof):
         return None
     with open(kernel_file, "rb") as f:
@@ -253,6 +255,7 @@ def run_rk4(args):
     vel = torch.empty((n, 3), dtype=torch.float64, device=dev)
     ctx = sts.Context()
     h = ctx.h
+    sts.sts_set_traversal(h, args.dual)
 
     p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
     psi = torch.empty(n, dtype=torch.float64, device=dev)
@@ -306,6 +309,7 @@ def run_rk4(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
                    "dt_day": dt, "Omega_per_day": Omega, "near_fp64_tau": tau,
+                   "traversal": "dual (PP, PC, CP, CC)" if args.dual else "target-leaf lists (PC, PP)",
                    "forcing": ({"k": args.forcing, "amplitude": "3/5 Omega", "Tp": 4.0, "Tf": 15.0,
                                 "theta1": "pi/3", "t0": args.t0} if forcing is not None else None),
                    "launch": ("host launches (forced steps are not recorded)" if forcing is not None or args.no_graph
@@ -697,7 +701,8 @@ def main():
     achieved = flops / (eval_avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
-                "traffic": profile_traffic(os.path.join(ROOT, "paper_2401_07361_gb300", "csrc", "sts_eval.cu")),
+                "traffic": profile_traffic(os.path.join(ROOT, "paper_2401_07361_gb300", "csrc", "sts_eval.cu"),
+                                           args.workload, args.dual),
                 "kernel": "k_eval_mixed (leaf lists)" if args.dual else "k_eval_mixed", "flops_per_launch": flops,
                 "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {sm_max:.0f} MHz "
                                f"(MEASURED_PEAKS sm_max_mhz); 16 flop per interaction",

@@ -192,10 +192,11 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
  * points and weights), CP (only the target above: the source particles summed at the target's
  * proxy points), CC (both above: proxy points against proxy points).  A pair that fails the
  * MAC is PP when both are leaves; otherwise the triangle holding more particles (the target
- * on a tie; a leaf never) is replaced by its children.  CP and CC give the velocity at the
- * target cluster's proxy points; the polynomial of degree d interpolating it over the cluster
- * (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m))) is evaluated at every particle below it and
- * added.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau (mixed precision: the
+ * on a tie; a leaf never) is replaced by its children.  CP and CC give the kernel sum S (the
+ * velocity is -(1/4 pi) x x S) at the target cluster's proxy points; the polynomial of degree
+ * d interpolating it over the cluster (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m))) is
+ * evaluated at every particle x below it, and -(1/4 pi) x x (that value) is added, so the
+ * velocity stays tangent to the sphere.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau (mixed precision: the
  * pair sums in FP32 as in sts_velocity, the interpolation in FP64).  Builds the pair lists when
  * theta or the tree changed (synchronises `stream` once), which replaces the lists of
  * sts_velocity (the next sts_velocity rebuilds them).  STS_ERR_STATE without a tree. */

@@ -89,6 +89,19 @@ static void bs_term(v3 x, v3 y, double w, v3* acc)
     acc->z += c.z * t;
 }
 
+/* The vector sum S of the velocity kernel: acc += w (y - x) / (|y - x|^2 / 2), so that the
+ * velocity is -(1/4pi) x x S (the x x factor taken out of bs_term; x x (y - x) = x x y).     */
+static void bs_sum(v3 x, v3 y, double w, v3* acc)
+{
+    v3 d = vsub(y, x);
+    double h = 0.5 * vdot(d, d);
+    if (h == 0.0) return;
+    double t = w / h;
+    acc->x += d.x * t;
+    acc->y += d.y * t;
+    acc->z += d.z * t;
+}
+
 /* The potential kernel: G(x, y) = -(1/4pi) log(1 - x.y) (Sec. 2), the Green's function of
  * the spherical Laplacian, so that psi_i = sum_{j != i} G(x_i, x_j) zeta_j A_j is the stream
  * function of the particle system (Delta psi = zeta).  With Eq. altkernel 1 - x.y =
@@ -1241,13 +1254,14 @@ int or_tree_potential(or_tree* tr, const double* zeta, const double* area, doubl
 }
 
 /* Tree-code velocity by the dual traversal (Sec. 3.3, 3.4): PP and PC at the target leaves as
- * in tree_sum; CP and CC accumulate the velocity U_T at the proxy points of each target
- * cluster T (from the source particles, resp. the source proxies with their weights W); then
- * the interpolating polynomial of U_T over T (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m)), the
- * SBB basis in T's barycentric coordinates) is evaluated at every particle below T.  A
- * particle's velocity sums its leaf's PP and PC pairs in traversal order, then the
- * interpolants of its cluster ancestors from the root down (its own leaf last when that is a
- * cluster at the depth limit).  stats[0..4]: PP (target, source) particle pairs with j != i,
+ * in tree_sum; CP and CC accumulate the kernel sum U_T = S at the proxy points of each target
+ * cluster T (bs_sum: the velocity is -(1/4pi) x x S, so the interpolated field keeps the
+ * velocity tangent to the sphere), from the source particles, resp. the source proxies with
+ * their weights W; then the interpolating polynomial of U_T over T (solve V_T c = U_T,
+ * V_T[m][k] = B_k(b(x~_m)), the SBB basis in T's barycentric coordinates) is evaluated at every
+ * particle below T.  A particle's velocity sums its leaf's PP and PC pairs in traversal order,
+ * plus x crossed with the sum of the interpolants of its cluster ancestors from the root down
+ * (its own leaf last when that is a cluster at the depth limit).  stats[0..4]: PP (target, source) particle pairs with j != i,
  * PC target x proxy, CP proxy x source, CC proxy x proxy, downward particle x M.            */
 static int64_t* group_by(const int32_t* key, int64_t n, int64_t nkeys, int64_t** order)
 {
@@ -1342,14 +1356,14 @@ int or_tree_velocity_dual(or_tree* tr, const double* zeta, const double* area, d
                 v3 acc = mk(0.0, 0.0, 0.0);
                 for (int64_t q = b0; q < b1; q++) {
                     const onode* sn = &tr->nodes[tr->dual_s[KCP][ords[KCP][q]]];
-                    for (int64_t j = sn->start; j < sn->start + sn->count; j++) bs_term(xt[m], ys[j], ws[j], &acc);
+                    for (int64_t j = sn->start; j < sn->start + sn->count; j++) bs_sum(xt[m], ys[j], ws[j], &acc);
                     ncp += sn->count;
                 }
                 for (int64_t q = c0; q < c1e; q++) {
                     const int32_t sid = tr->dual_s[KCC][ords[KCC][q]];
                     const v3* y = yt + (size_t)slot[sid] * M;
                     const double* Wm = W + (size_t)slot[sid] * M;
-                    for (int mm = 0; mm < M; mm++) bs_term(xt[m], y[mm], Wm[mm], &acc);
+                    for (int mm = 0; mm < M; mm++) bs_sum(xt[m], y[mm], Wm[mm], &acc);
                     ncc += M;
                 }
                 Ut[m] = acc;
@@ -1412,23 +1426,25 @@ int or_tree_velocity_dual(or_tree* tr, const double* zeta, const double* area, d
                     for (int m = 0; m < M; m++) bs_term(x, y[m], Wm[m], &acc);
                     npc += M;
                 }
-                for (int c = nch - 1; c >= 0; c--) {  /* root down */
+                v3 sacc = mk(0.0, 0.0, 0.0);  /* interpolated kernel sums, root down */
+                for (int c = nch - 1; c >= 0; c--) {
                     const onode* an = &tr->nodes[chain[c]];
                     double b[3];
                     sph_bary(x, an->v[0], an->v[1], an->v[2], b);
                     sbb(d, b[0], b[1], b[2], B);
                     const v3* ct = cf + (size_t)slot[chain[c]] * M;
                     for (int kk = 0; kk < M; kk++) {
-                        acc.x += B[kk] * ct[kk].x;
-                        acc.y += B[kk] * ct[kk].y;
-                        acc.z += B[kk] * ct[kk].z;
+                        sacc.x += B[kk] * ct[kk].x;
+                        sacc.y += B[kk] * ct[kk].y;
+                        sacc.z += B[kk] * ct[kk].z;
                     }
                     ndn += M;
                 }
+                const v3 xs = vcross(x, sacc);
                 int64_t i = tr->perm[k];
-                vel[3 * i] = f * acc.x;
-                vel[3 * i + 1] = f * acc.y;
-                vel[3 * i + 2] = f * acc.z;
+                vel[3 * i] = f * (acc.x + xs.x);
+                vel[3 * i + 1] = f * (acc.y + xs.y);
+                vel[3 * i + 2] = f * (acc.z + xs.z);
             }
         }
         nst[0] = npp;

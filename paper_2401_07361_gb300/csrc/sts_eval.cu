@@ -431,8 +431,14 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
                 Sy += __ldcg(corr + 3 * t + 1);
                 Sz += __ldcg(corr + 3 * t + 2);
             }
+            if (!perm) {  // proxy targets of the dual traversal: the kernel sum, -(1/4 pi) S
+                vel[3 * t] = -kInv4Pi * Sx;
+                vel[3 * t + 1] = -kInv4Pi * Sy;
+                vel[3 * t + 2] = -kInv4Pi * Sz;
+                continue;
+            }
             const double4 x = tgt64[t];
-            const int64_t i = perm ? perm[t] : t;
+            const int64_t i = perm[t];
             vel[3 * i] = -kInv4Pi * (x.y * Sz - x.z * Sy);
             vel[3 * i + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
             vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
@@ -570,15 +576,20 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
         // psi = -(1/4 pi) sum w log(|d|^2 / 2), accumulated with 2 w
         if (lane < p && v0) vel[perm[tk0]] = -0.5 * kInv4Pi * a[0];
         if (lane < p && v1) vel[perm[tk1]] = -0.5 * kInv4Pi * a[3];
+    } else if (lane < p && !perm) {  // proxy targets of the dual traversal: -(1/4 pi) S
+        if (v0)
+            for (int c = 0; c < 3; c++) vel[3 * tk0 + c] = -kInv4Pi * a[c];
+        if (v1)
+            for (int c = 0; c < 3; c++) vel[3 * tk1 + c] = -kInv4Pi * a[3 + c];
     } else if (lane < p) {
         if (v0) {
-            const int64_t i = perm ? perm[tk0] : tk0;
+            const int64_t i = perm[tk0];
             vel[3 * i] = -kInv4Pi * (x0.y * a[2] - x0.z * a[1]);
             vel[3 * i + 1] = -kInv4Pi * (x0.z * a[0] - x0.x * a[2]);
             vel[3 * i + 2] = -kInv4Pi * (x0.x * a[1] - x0.y * a[0]);
         }
         if (v1) {
-            const int64_t i = perm ? perm[tk1] : tk1;
+            const int64_t i = perm[tk1];
             vel[3 * i] = -kInv4Pi * (x1.y * a[5] - x1.z * a[4]);
             vel[3 * i + 1] = -kInv4Pi * (x1.z * a[3] - x1.x * a[5]);
             vel[3 * i + 2] = -kInv4Pi * (x1.x * a[4] - x1.y * a[3]);
@@ -968,9 +979,10 @@ __device__ __forceinline__ void eval_interp(const double* __restrict__ f, const 
     }
 }
 
-// Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the velocity at the target
-// cluster's proxy points, interpolated over the cluster), passed down the tree.  U_T = the
-// velocity of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs) plus
+// Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the kernel sum -(1/4 pi) S at
+// the target cluster's proxy points, interpolated over the cluster; the velocity at a particle
+// x is then x x the interpolant, tangent to the sphere), passed down the tree.  U_T = the sum
+// of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs) plus
 // the interpolant of its parent, which already holds every ancestor's, evaluated there.  A
 // degree-d polynomial in one triangle's barycentric coordinates is one in any other's (both are
 // the homogeneous degree-d polynomials in x), so interpolating the parent's at T's M proxy
@@ -1041,8 +1053,8 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
     }
 }
 
-// Adds to every particle (sorted slot) the interpolant of its lowest cluster: its leaf when
-// that is a cluster (at the depth limit), else the leaf's parent.
+// Adds to every particle x (sorted slot) x crossed with the interpolant of its lowest cluster:
+// its leaf when that is a cluster (at the depth limit), else the leaf's parent.
 template <int D>
 __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
@@ -1059,12 +1071,12 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
     const int32_t cs = cluster_slot[a];
     if (cs < 0 || !acc[cs]) return;
     const double4 x = src64[j];
-    double ax = 0.0, ay = 0.0, az = 0.0;
+    double ax = 0.0, ay = 0.0, az = 0.0;  // the interpolated -(1/4 pi) S
     eval_interp<D>(frame + 12 * (int64_t)cs, coef + 3 * (int64_t)cs * M, x.x, x.y, x.z, ax, ay, az);
     const int64_t i = perm[j];
-    vel[3 * i] += ax;
-    vel[3 * i + 1] += ay;
-    vel[3 * i + 2] += az;
+    vel[3 * i] += x.y * az - x.z * ay;
+    vel[3 * i + 1] += x.z * ax - x.x * az;
+    vel[3 * i + 2] += x.x * ay - x.y * ax;
 }
 
 }  // namespace

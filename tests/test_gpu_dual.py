@@ -213,3 +213,15 @@ def test_dual_clustered_close_pairs(ctx):
     sts.sts_tree_build(ctx, dev(pos), p)
     v = sts.sts_velocity_dual(ctx, dev(zeta), dev(area), p).cpu().numpy()
     assert O.rel_l2(v, ref, area) <= 1e-6, O.rel_l2(v, ref, area)
+
+
+@pytest.mark.parametrize("prec", [sts.STS_FP64, sts.STS_MIXED])
+def test_dual_velocity_tangent(ctx, prec):
+    """The interpolated CP / CC part enters as x x (the interpolated kernel sum), so the dual
+    velocity is tangent to the sphere to rounding, in both precisions."""
+    pos, leaf, ml = _case("rand20000")
+    zeta, area = _fields(len(pos), 7)
+    p = sts.params(theta=0.7, degree=8, leaf_size=leaf, max_level=ml, precision=prec, near_fp64_tau=_tau(len(pos)))
+    sts.sts_tree_build(ctx, dev(pos), p)
+    v = sts.sts_velocity_dual(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    assert np.max(np.abs(np.sum(pos * v, axis=1))) <= 1e-14 * np.max(np.linalg.norm(v, axis=1))

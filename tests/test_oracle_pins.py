@@ -670,3 +670,17 @@ def test_amr_spike_splits_exactly_the_triangles_around_it_and_weights_tile_the_s
     m.step(np.inf, 0.5)
     e2 = m.export()
     assert e2["tlevel"][e2["tstate"] == 1].max() == 2
+
+
+def test_dual_velocity_is_tangent():
+    """The dual traversal interpolates the kernel sum S over each target cluster and takes the
+    velocity as -(1/4 pi) x x S at the particle, so x . u = 0 holds to rounding for every
+    particle, as for the direct sum (interpolating u itself would leave x . u of the size of
+    the interpolation error)."""
+    pos = W.uniform_points(4000, 61)
+    zeta = W.sh_series_vorticity(pos, 8, seed=62)
+    area = W.equal_areas(len(pos))
+    tr = O.Tree(pos, 16)
+    v, st = tr.velocity_dual(zeta, area, 0.7, 6, return_stats=True)
+    assert st["cp"] > 0 and st["cc"] > 0
+    assert np.max(np.abs(np.sum(pos * v, axis=1))) <= 1e-14 * np.max(np.linalg.norm(v, axis=1))
