@@ -1,12 +1,13 @@
 """Autotuner for the tree-code parameters under a fixed error budget.
 
 The tree code trades accuracy for speed through the MAC parameter theta (Sec. 3.4), the
-interpolation degree d (Sec. 3.2) and the leaf size N_T (Sec. 3).  For one particle set,
+interpolation degree d (Sec. 3.2), the leaf size N_T (Sec. 3) and the traversal (target-leaf
+lists with PC + PP, or the dual traversal with PP, PC, CP and CC).  For one particle set,
 ``autotune`` times the whole path (tree build + velocity, through the C ABI, CUDA events on
-the caller's stream) for every candidate (theta, d, N_T) and measures its error against the
-FP64 direct sum on sampled targets (relative l2, area weighted as in Sec. 4.1).  It returns
-the fastest candidate whose error is within the budget.  Every evaluation runs in the CUDA
-library; this module only chooses parameters.
+the caller's stream) for every candidate and measures its error against the FP64 direct sum
+on sampled targets (relative l2, area weighted as in Sec. 4.1).  It returns the fastest
+candidate whose error is within the budget.  Every evaluation runs in the CUDA library; this
+module only chooses parameters.
 """
 from __future__ import annotations
 
@@ -26,7 +27,8 @@ class TuneResult:
     leaf_size: int
     ms: float
     error: float
-    table: list = field(default_factory=list)  # (theta, degree, leaf, ms, error) per candidate
+    table: list = field(default_factory=list)  # (theta, degree, leaf, ms, error, dual) per candidate
+    dual: bool = False  # the dual traversal (apply with sts.sts_set_traversal)
 
     def params(self, precision=sts.STS_MIXED, near_fp64_tau=0.0, max_level=16):
         return sts.params(self.theta, self.degree, self.leaf_size, max_level, precision, near_fp64_tau)
@@ -40,8 +42,9 @@ def _rel_l2(v, ref, w):
 
 def autotune(pos, zeta, area, budget=1e-4, thetas=(0.5, 0.6, 0.7, 0.8), degrees=(4, 6, 8, 10),
              leaf_sizes=(64, 128, 256), precision=sts.STS_MIXED, tau_c=0.01, offsets=None,
-             samples=2048, repeats=3, seed=0, ctx=None, stream=None) -> TuneResult:
-    """Fastest (theta, degree, leaf_size) with rel l2 error <= budget vs the FP64 direct sum.
+             samples=2048, repeats=3, seed=0, ctx=None, stream=None, traversals=(False, True)) -> TuneResult:
+    """Fastest (theta, degree, leaf_size, traversal) with rel l2 error <= budget vs the FP64
+    direct sum (traversals: False = target-leaf lists, True = dual traversal).
 
     pos, zeta, area: CUDA float64 tensors ([n,3], [n], [n]).  offsets: instance offsets of a
     batched (forest) set, or None.  The error is measured at ``samples`` random targets (all
@@ -79,8 +82,9 @@ def autotune(pos, zeta, area, budget=1e-4, thetas=(0.5, 0.6, 0.7, 0.8), degrees=
     vel = torch.empty((n, 3), dtype=torch.float64, device=pos.device)
     table = []
     best = None
-    for theta, d, leaf in itertools.product(thetas, degrees, leaf_sizes):
+    for theta, d, leaf, dual in itertools.product(thetas, degrees, leaf_sizes, traversals):
         p = sts.params(theta, d, leaf, 16, precision, tau)
+        sts.sts_set_traversal(ctx, dual)
 
         def run():
             if offsets is None:
@@ -102,12 +106,13 @@ def autotune(pos, zeta, area, budget=1e-4, thetas=(0.5, 0.6, 0.7, 0.8), degrees=
             times.append(e0.elapsed_time(e1))
         ms = float(np.median(times))
         err = _rel_l2(vel.cpu().numpy()[tg], ref, w)
-        table.append((theta, d, leaf, ms, err))
+        table.append((theta, d, leaf, ms, err, bool(dual)))
         if err <= budget and (best is None or ms < best[3]):
-            best = (theta, d, leaf, ms, err)
+            best = (theta, d, leaf, ms, err, bool(dual))
+    sts.sts_set_traversal(ctx, False)
     if own:
         ctx_obj.close()
     if best is None:
         raise ValueError(f"no candidate meets the error budget {budget:g}; smallest error "
                          f"{min(t[4] for t in table):.3e}")
-    return TuneResult(best[0], best[1], best[2], best[3], best[4], table)
+    return TuneResult(best[0], best[1], best[2], best[3], best[4], table, best[5])

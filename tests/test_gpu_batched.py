@@ -129,6 +129,9 @@ def test_autotuner_picks_fastest_within_budget():
     ref = O.direct(pos, zeta, area, targets=tg)
     with sts.Context() as c:
         p = res.params(near_fp64_tau=0.05 * 4 * math.pi / len(pos))
+        sts.sts_set_traversal(c.h, res.dual)
         sts.sts_tree_build(c.h, dev(pos), p)
         v = sts.sts_velocity(c.h, dev(zeta), dev(area), p).cpu().numpy()
     assert O.rel_l2(v[tg], ref, area[tg]) <= 3e-4
+    # both traversals were tried for every (theta, degree, leaf size)
+    assert {t[5] for t in res.table} == {False, True} and len(res.table) == 16

@@ -198,3 +198,20 @@ def test_graph_dual_overflow_falls_back_to_eager():
         sts.bve_rk4_step(c.h, x, z0, a, 0.01, 2 * math.pi, p)
         torch.cuda.synchronize()
         assert np.array_equal(xg, x.cpu().numpy())
+
+
+def test_graph_batched_dual_mixed_matches_eager():
+    """A forest of instances stepped with the dual traversal, recorded and replayed, equals the
+    eager steps (mixed precision: the FP64 close-pair sums are atomics, so to rounding)."""
+    sizes = [3000, 1200, 4500]
+    parts = [_state(nb, 20 + b) for b, nb in enumerate(sizes)]
+    pos = np.vstack([q[0] for q in parts])
+    zeta = np.concatenate([q[1] for q in parts])
+    area = np.concatenate([q[2] for q in parts])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    p = sts.params(theta=0.7, degree=8, leaf_size=64, precision=sts.STS_MIXED, near_fp64_tau=1e-6)
+    st = torch.cuda.Stream()
+    xe, ze, _ = _run(pos, zeta, area, p, 3, False, st, off, dual=True)
+    xg, zg, _ = _run(pos, zeta, area, p, 3, True, st, off, dual=True)
+    assert np.max(np.abs(xe - xg)) <= 1e-15
+    assert np.max(np.abs(ze - zg)) <= 1e-14 * np.max(np.abs(ze))
