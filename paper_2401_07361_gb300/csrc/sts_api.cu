@@ -98,7 +98,8 @@ sts_ctx::~sts_ctx()
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
     dual_scan.release(); cfar_off.release(); cnear_off.release(); cnear_coff.release(); cfar_ent.release();
-    cnear_ent.release(); ctasks.release(); cvel.release(); ccorr.release(); cdown.release(); chas.release();
+    cnear_ent.release(); ctasks.release(); cvel.release(); ccorr.release(); cdown.release(); cdown32.release();
+    chas.release();
     cacc.release();
     if (amr) amr_free(amr);
     for (RefTable* t : refs)

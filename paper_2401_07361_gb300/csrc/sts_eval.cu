@@ -941,21 +941,19 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
 // ------------------------------------------------------------------------ dual: downward
 namespace {
 
-// The interpolating polynomial of cluster slot cs at x (degree D, M = (D+1)(D+2)/2
-// coefficients cf[M][3]): b = the spherical barycentric coordinates of x in the cluster's
-// triangle (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3; frame rows n_i / D from Cramer's rule:
-// n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1), then sum_k B_k(b) c_k with
-// B_k(b) = b1^a b2^b b3^c in the order a = D..0, b = D - a..0, summed per a and then over a.
-// D is a template parameter so that the powers stay in registers.
-template <int D>
-__device__ __forceinline__ void eval_interp(const double* __restrict__ f, const double* __restrict__ cf, double xx,
-                                            double xy, double xz, double& ax, double& ay, double& az)
+// The interpolating polynomial of a cluster (degree D, M = (D+1)(D+2)/2 coefficients
+// cf[M][3]) at a point with spherical barycentric coordinates b in the cluster's triangle
+// (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3): sum_k B_k(b) c_k with B_k(b) = b1^a b2^b b3^c in the
+// order a = D..0, b = D - a..0, summed per a and then over a.  D is a template parameter so
+// that the powers stay in registers.  T = double, or float for the particles of the mixed path:
+// the coefficients come from the FP64 contraction and describe a smooth interpolant, so the
+// evaluation carries none of the contraction's cancellation (its error is eps32 times the
+// Bernstein coefficients, which track the interpolated values).
+template <int D, class T>
+__device__ __forceinline__ void eval_poly(T b1, T b2, T b3, const T* __restrict__ cf, T& ax, T& ay, T& az)
 {
-    const double b1 = f[0] * xx + f[1] * xy + f[2] * xz;
-    const double b2 = f[3] * xx + f[4] * xy + f[5] * xz;
-    const double b3 = f[6] * xx + f[7] * xy + f[8] * xz;
-    double p1[D + 1], p2[D + 1], p3[D + 1];
-    p1[0] = p2[0] = p3[0] = 1.0;
+    T p1[D + 1], p2[D + 1], p3[D + 1];
+    p1[0] = p2[0] = p3[0] = T(1);
 #pragma unroll
     for (int e = 1; e <= D; e++) {
         p1[e] = p1[e - 1] * b1;
@@ -965,10 +963,10 @@ __device__ __forceinline__ void eval_interp(const double* __restrict__ f, const 
     int k = 0;
 #pragma unroll
     for (int ea = D; ea >= 0; ea--) {
-        double sx = 0.0, sy = 0.0, sz = 0.0;
+        T sx = T(0), sy = T(0), sz = T(0);
 #pragma unroll
         for (int eb = D - ea; eb >= 0; eb--, k++) {
-            const double B = p2[eb] * p3[D - ea - eb];
+            const T B = p2[eb] * p3[D - ea - eb];
             sx += B * cf[3 * k];
             sy += B * cf[3 * k + 1];
             sz += B * cf[3 * k + 2];
@@ -977,6 +975,26 @@ __device__ __forceinline__ void eval_interp(const double* __restrict__ f, const 
         ay += p1[ea] * sy;
         az += p1[ea] * sz;
     }
+}
+
+// Barycentric coordinates from the FP64 frame (rows n_i / D of Cramer's rule: n1 = v2 x v3,
+// n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1) ...
+__device__ __forceinline__ void bary64(const double* __restrict__ f, double x, double y, double z, double& b1,
+                                       double& b2, double& b3)
+{
+    b1 = f[0] * x + f[1] * y + f[2] * z;
+    b2 = f[3] * x + f[4] * y + f[5] * z;
+    b3 = f[6] * x + f[7] * y + f[8] * z;
+}
+
+// ... and from the FP32 frame about the centre: b = b(c) + (n_i / D) . (x - c), with x - c
+// already formed accurately (hi/lo pairs or an FP64 difference).
+__device__ __forceinline__ void bary32(const float* __restrict__ h, float dx, float dy, float dz, float& b1,
+                                       float& b2, float& b3)
+{
+    b1 = h[9] + (h[0] * dx + h[1] * dy + h[2] * dz);
+    b2 = h[10] + (h[3] * dx + h[4] * dy + h[5] * dz);
+    b3 = h[11] + (h[6] * dx + h[7] * dy + h[8] * dz);
 }
 
 // Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the kernel sum -(1/4 pi) S at
@@ -991,13 +1009,14 @@ __device__ __forceinline__ void eval_interp(const double* __restrict__ f, const 
 // x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|, the barycentric coordinates of
 // x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref and c = V_ref^-1 diag(rho^d) U.
 // acc[c]: cluster c holds an interpolant.  One CTA per cluster of the level.
-template <int D>
+template <int D, bool MIXED>
 __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ parent,
                              const int32_t* __restrict__ cluster_slot, const uint8_t* __restrict__ has,
                              uint8_t* __restrict__ acc, const double* __restrict__ geom,
                              const double* __restrict__ frame, const double4* __restrict__ prx64,
-                             const double* __restrict__ beta, const double* __restrict__ vinv,
-                             const double* __restrict__ cvel, double* __restrict__ coef)
+                             const double* __restrict__ beta,
+                             const double* __restrict__ vinv, const double* __restrict__ cvel,
+                             double* __restrict__ coef, float* __restrict__ coef32)
 {
     constexpr int d = D, M = (D + 1) * (D + 2) / 2;
     __shared__ double u[3 * kMaxM];
@@ -1021,9 +1040,11 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
                 vy = v[1];
                 vz = v[2];
             }
-            if (from_parent) {
+            if (from_parent) {  // FP64 in both precisions: the error would compound level by level
                 const double4 x = prx64[(int64_t)cs * M + m];
-                eval_interp<D>(frame + 12 * (int64_t)ps, coef + 3 * (int64_t)ps * M, x.x, x.y, x.z, vx, vy, vz);
+                double b1, b2, b3;
+                bary64(frame + 12 * (int64_t)ps, x.x, x.y, x.z, b1, b2, b3);
+                eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)ps * M, vx, vy, vz);
             }
             const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
             const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
@@ -1049,18 +1070,25 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
             o[0] = ax;
             o[1] = ay;
             o[2] = az;
+            if (MIXED) {  // the copy the particles evaluate in FP32
+                float* o32 = coef32 + 3 * ((int64_t)cs * M + k);
+                o32[0] = (float)ax;
+                o32[1] = (float)ay;
+                o32[2] = (float)az;
+            }
         }
     }
 }
 
 // Adds to every particle x (sorted slot) x crossed with the interpolant of its lowest cluster:
 // its leaf when that is a cluster (at the depth limit), else the leaf's parent.
-template <int D>
+template <int D, bool MIXED>
 __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
                            const uint8_t* __restrict__ acc, const double* __restrict__ frame,
-                           const double4* __restrict__ src64, const int32_t* __restrict__ perm,
-                           const double* __restrict__ coef, double* __restrict__ vel)
+                           const float* __restrict__ frame32, const double4* __restrict__ src64,
+                           const float4* __restrict__ src_hl, const int32_t* __restrict__ perm,
+                           const double* __restrict__ coef, const float* __restrict__ coef32, double* __restrict__ vel)
 {
     constexpr int M = (D + 1) * (D + 2) / 2;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1072,7 +1100,22 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
     if (cs < 0 || !acc[cs]) return;
     const double4 x = src64[j];
     double ax = 0.0, ay = 0.0, az = 0.0;  // the interpolated -(1/4 pi) S
-    eval_interp<D>(frame + 12 * (int64_t)cs, coef + 3 * (int64_t)cs * M, x.x, x.y, x.z, ax, ay, az);
+    if (MIXED) {
+        // x - c from the FP32 hi/lo pairs of the particle and of the cluster centre
+        const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
+        const float* h = frame32 + 18 * (int64_t)cs;
+        float b1, b2, b3, fx = 0.f, fy = 0.f, fz = 0.f;
+        bary32(h, (hi.x - h[12]) + (lo.x - h[15]), (hi.y - h[13]) + (lo.y - h[16]), (hi.z - h[14]) + (lo.z - h[17]),
+               b1, b2, b3);
+        eval_poly<D, float>(b1, b2, b3, coef32 + 3 * (int64_t)cs * M, fx, fy, fz);
+        ax = fx;
+        ay = fy;
+        az = fz;
+    } else {
+        double b1, b2, b3;
+        bary64(frame + 12 * (int64_t)cs, x.x, x.y, x.z, b1, b2, b3);
+        eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)cs * M, ax, ay, az);
+    }
     const int64_t i = perm[j];
     vel[3 * i] += x.y * az - x.z * ay;
     vel[3 * i + 1] += x.z * ax - x.x * az;
@@ -1083,19 +1126,30 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
 
 namespace {
 
-template <int D>
-void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, cudaStream_t s)
+template <int D, bool MIXED>
+void launch_down_p(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, cudaStream_t s)
 {
     const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
     for (int l = 0; l < levels; l++)
-        (k_down_level<D><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
-                                           c->cacc.p, c->nd_geom.p, c->up_frame.p, c->prx64.p, ref->d_beta.p,
-                                           ref->d_vinv.p, c->cvel.p, c->cdown.p),
+        (k_down_level<D, MIXED><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p,
+                                                  c->chas.p, c->cacc.p, c->nd_geom.p, c->up_frame.p,
+                                                  c->prx64.p, ref->d_beta.p, ref->d_vinv.p,
+                                                  c->cvel.p, c->cdown.p, c->cdown32.p),
          note_launch());
-    (k_downward<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                      c->cluster_slot.p, c->cacc.p, c->up_frame.p, c->src64.p,
-                                                      c->perm.p, c->cdown.p, vel),
+    (k_downward<D, MIXED><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
+                                                             c->cluster_slot.p, c->cacc.p, c->up_frame.p,
+                                                             c->up_frame32.p, c->src64.p, c->src_hl.p, c->perm.p,
+                                                             c->cdown.p, c->cdown32.p, vel),
      note_launch());
+}
+
+template <int D>
+void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, bool mixed, cudaStream_t s)
+{
+    if (mixed)
+        launch_down_p<D, true>(c, ref, levels, C, vel, s);
+    else
+        launch_down_p<D, false>(c, ref, levels, C, vel, s);
 }
 
 }  // namespace
@@ -1116,6 +1170,7 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     if (!cap) {
         STS_CUDA(c->cvel.reserve(3 * C * M + 3));
         STS_CUDA(c->cdown.reserve(3 * C * M + 3));
+        STS_CUDA(c->cdown32.reserve(3 * C * M + 3));
         STS_CUDA(c->cacc.reserve(C + 1));
     }
     // CP and CC: the velocity at the proxy points of the target clusters
@@ -1135,23 +1190,24 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s, -1))) return rc;
     // interpolants passed down level by level, then evaluated at the particles
     const int levels = (cap ? c->plan.depth : (int)c->deepest) + 1;
+    const bool mixed = precision != STS_FP64;
     switch (degree) {
-        case 1: launch_down<1>(c, ref, levels, C, vel, s); break;
-        case 2: launch_down<2>(c, ref, levels, C, vel, s); break;
-        case 3: launch_down<3>(c, ref, levels, C, vel, s); break;
-        case 4: launch_down<4>(c, ref, levels, C, vel, s); break;
-        case 5: launch_down<5>(c, ref, levels, C, vel, s); break;
-        case 6: launch_down<6>(c, ref, levels, C, vel, s); break;
-        case 7: launch_down<7>(c, ref, levels, C, vel, s); break;
-        case 8: launch_down<8>(c, ref, levels, C, vel, s); break;
-        case 9: launch_down<9>(c, ref, levels, C, vel, s); break;
-        case 10: launch_down<10>(c, ref, levels, C, vel, s); break;
-        case 11: launch_down<11>(c, ref, levels, C, vel, s); break;
-        case 12: launch_down<12>(c, ref, levels, C, vel, s); break;
-        case 13: launch_down<13>(c, ref, levels, C, vel, s); break;
-        case 14: launch_down<14>(c, ref, levels, C, vel, s); break;
-        case 15: launch_down<15>(c, ref, levels, C, vel, s); break;
-        default: launch_down<16>(c, ref, levels, C, vel, s); break;
+        case 1: launch_down<1>(c, ref, levels, C, vel, mixed, s); break;
+        case 2: launch_down<2>(c, ref, levels, C, vel, mixed, s); break;
+        case 3: launch_down<3>(c, ref, levels, C, vel, mixed, s); break;
+        case 4: launch_down<4>(c, ref, levels, C, vel, mixed, s); break;
+        case 5: launch_down<5>(c, ref, levels, C, vel, mixed, s); break;
+        case 6: launch_down<6>(c, ref, levels, C, vel, mixed, s); break;
+        case 7: launch_down<7>(c, ref, levels, C, vel, mixed, s); break;
+        case 8: launch_down<8>(c, ref, levels, C, vel, mixed, s); break;
+        case 9: launch_down<9>(c, ref, levels, C, vel, mixed, s); break;
+        case 10: launch_down<10>(c, ref, levels, C, vel, mixed, s); break;
+        case 11: launch_down<11>(c, ref, levels, C, vel, mixed, s); break;
+        case 12: launch_down<12>(c, ref, levels, C, vel, mixed, s); break;
+        case 13: launch_down<13>(c, ref, levels, C, vel, mixed, s); break;
+        case 14: launch_down<14>(c, ref, levels, C, vel, mixed, s); break;
+        case 15: launch_down<15>(c, ref, levels, C, vel, mixed, s); break;
+        default: launch_down<16>(c, ref, levels, C, vel, mixed, s); break;
     }
     phase_end(c, kPhCluster, s);
     STS_LAUNCH_CHECK();

@@ -267,6 +267,7 @@ struct sts_ctx {
     sts::DevBuf<double> cvel;            // [C, M, 3] velocity at the proxy points of target clusters
     sts::DevBuf<double> ccorr;           // [C, M, 3] FP64 close-pair sums of the proxy targets
     sts::DevBuf<double> cdown;           // [C, M, 3] coefficients of the interpolating polynomials
+    sts::DevBuf<float> cdown32;          // [C, M, 3] the same rounded to FP32 (mixed precision)
     sts::DevBuf<uint8_t> chas;           // [C] the cluster is the target of CP or CC pairs
     sts::DevBuf<uint8_t> cacc;           // [C] the cluster holds an interpolant (its own or an ancestor's)
 
