@@ -106,6 +106,7 @@ sts_ctx::~sts_ctx()
         if (t) {
             t->d_beta.release();
             t->d_vinv.release();
+            t->d_vinvT.release();
             delete t;
         }
     for (int p = 0; p < kNumPhases; p++)

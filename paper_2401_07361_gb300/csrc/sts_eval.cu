@@ -997,11 +997,11 @@ __device__ __forceinline__ void bary32(const float* __restrict__ h, float dx, fl
     b3 = h[11] + (h[6] * dx + h[7] * dy + h[8] * dz);
 }
 
-// Interpolants of the clusters of level l (Sec. 3.3, CP and CC: the kernel sum -(1/4 pi) S at
-// the target cluster's proxy points, interpolated over the cluster; the velocity at a particle
-// x is then x x the interpolant, tangent to the sphere), passed down the tree.  U_T = the sum
-// of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs) plus
-// the interpolant of its parent, which already holds every ancestor's, evaluated there.  A
+// FP64 precision: interpolants of the clusters of level l (Sec. 3.3, CP and CC: the kernel sum
+// -(1/4 pi) S at the target cluster's proxy points, interpolated over the cluster; the velocity
+// at a particle x is then x x the interpolant, tangent to the sphere), passed down the tree.
+// U_T = the sum of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs)
+// plus the interpolant of its parent, which already holds every ancestor's, evaluated there.  A
 // degree-d polynomial in one triangle's barycentric coordinates is one in any other's (both are
 // the homogeneous degree-d polynomials in x), so interpolating the parent's at T's M proxy
 // points reproduces it exactly: a particle then evaluates its lowest cluster's interpolant only,
@@ -1009,14 +1009,13 @@ __device__ __forceinline__ void bary32(const float* __restrict__ h, float dx, fl
 // x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|, the barycentric coordinates of
 // x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref and c = V_ref^-1 diag(rho^d) U.
 // acc[c]: cluster c holds an interpolant.  One CTA per cluster of the level.
-template <int D, bool MIXED>
+template <int D>
 __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ parent,
                              const int32_t* __restrict__ cluster_slot, const uint8_t* __restrict__ has,
                              uint8_t* __restrict__ acc, const double* __restrict__ geom,
                              const double* __restrict__ frame, const double4* __restrict__ prx64,
-                             const double* __restrict__ beta,
-                             const double* __restrict__ vinv, const double* __restrict__ cvel,
-                             double* __restrict__ coef, float* __restrict__ coef32)
+                             const double* __restrict__ beta, const double* __restrict__ vinvT,
+                             const double* __restrict__ cvel, double* __restrict__ coef)
 {
     constexpr int d = D, M = (D + 1) * (D + 2) / 2;
     __shared__ double u[3 * kMaxM];
@@ -1040,7 +1039,7 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
                 vy = v[1];
                 vz = v[2];
             }
-            if (from_parent) {  // FP64 in both precisions: the error would compound level by level
+            if (from_parent) {
                 const double4 x = prx64[(int64_t)cs * M + m];
                 double b1, b2, b3;
                 bary64(frame + 12 * (int64_t)ps, x.x, x.y, x.z, b1, b2, b3);
@@ -1061,7 +1060,7 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
         for (int k = threadIdx.x; k < M; k += blockDim.x) {
             double ax = 0.0, ay = 0.0, az = 0.0;
             for (int m = 0; m < M; m++) {
-                const double w = vinv[k * M + m];
+                const double w = vinvT[m * M + k];
                 ax += w * u[3 * m];
                 ay += w * u[3 * m + 1];
                 az += w * u[3 * m + 2];
@@ -1070,25 +1069,18 @@ __global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32
             o[0] = ax;
             o[1] = ay;
             o[2] = az;
-            if (MIXED) {  // the copy the particles evaluate in FP32
-                float* o32 = coef32 + 3 * ((int64_t)cs * M + k);
-                o32[0] = (float)ax;
-                o32[1] = (float)ay;
-                o32[2] = (float)az;
-            }
         }
     }
 }
 
-// Adds to every particle x (sorted slot) x crossed with the interpolant of its lowest cluster:
-// its leaf when that is a cluster (at the depth limit), else the leaf's parent.
-template <int D, bool MIXED>
+// FP64 precision: adds to every particle x (sorted slot) x crossed with the interpolant of its
+// lowest cluster: its leaf when that is a cluster (at the depth limit), else the leaf's parent.
+template <int D>
 __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
                            const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
                            const uint8_t* __restrict__ acc, const double* __restrict__ frame,
-                           const float* __restrict__ frame32, const double4* __restrict__ src64,
-                           const float4* __restrict__ src_hl, const int32_t* __restrict__ perm,
-                           const double* __restrict__ coef, const float* __restrict__ coef32, double* __restrict__ vel)
+                           const double4* __restrict__ src64, const int32_t* __restrict__ perm,
+                           const double* __restrict__ coef, double* __restrict__ vel)
 {
     constexpr int M = (D + 1) * (D + 2) / 2;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1100,22 +1092,97 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
     if (cs < 0 || !acc[cs]) return;
     const double4 x = src64[j];
     double ax = 0.0, ay = 0.0, az = 0.0;  // the interpolated -(1/4 pi) S
-    if (MIXED) {
-        // x - c from the FP32 hi/lo pairs of the particle and of the cluster centre
-        const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
+    double b1, b2, b3;
+    bary64(frame + 12 * (int64_t)cs, x.x, x.y, x.z, b1, b2, b3);
+    eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)cs * M, ax, ay, az);
+    const int64_t i = perm[j];
+    vel[3 * i] += x.y * az - x.z * ay;
+    vel[3 * i + 1] += x.z * ax - x.x * az;
+    vel[3 * i + 2] += x.x * ay - x.y * ax;
+}
+
+// Mixed precision: the interpolant of every cluster with CP or CC pairs (Sec. 3.3), each from
+// its own U_T only: c = V_ref^-1 diag(rho^d) U_T in FP64 (V_ref^-1 carries cond(V_ref), so
+// FP32 would lose the coefficients), rounded to FP32 once for the particles.  The clusters are
+// independent (no parent's interpolant is carried down), so one launch takes all of them: a
+// fixed grid strides over the clusters, whose count is on the device.
+template <int D>
+__global__ void k_cluster_coef(const int64_t* __restrict__ nclu, const int32_t* __restrict__ cnode,
+                               const uint8_t* __restrict__ has, const double* __restrict__ geom,
+                               const double* __restrict__ beta, const double* __restrict__ vinvT,
+                               const double* __restrict__ cvel, float* __restrict__ coef32)
+{
+    constexpr int d = D, M = (D + 1) * (D + 2) / 2;
+    __shared__ double u[3 * kMaxM];
+    const int64_t ncl = *nclu;
+    for (int64_t cs = blockIdx.x; cs < ncl; cs += gridDim.x) {
+        if (!has[cs]) continue;
+        const double* g = geom + 13 * (int64_t)cnode[cs];
+        __syncthreads();  // u of the previous cluster is no longer read
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
+            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
+            double rd = 1.0;
+            for (int e = 0; e < d; e++) rd *= rho;
+            const double* v = cvel + 3 * (cs * M + m);
+            u[3 * m] = rd * v[0];
+            u[3 * m + 1] = rd * v[1];
+            u[3 * m + 2] = rd * v[2];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            for (int m = 0; m < M; m++) {
+                const double w = vinvT[m * M + k];
+                ax += w * u[3 * m];
+                ay += w * u[3 * m + 1];
+                az += w * u[3 * m + 2];
+            }
+            float* o = coef32 + 3 * (cs * M + k);
+            o[0] = (float)ax;
+            o[1] = (float)ay;
+            o[2] = (float)az;
+        }
+    }
+}
+
+// Mixed precision: adds to every particle x (sorted slot) x crossed with the sum of the
+// interpolants of its ancestor clusters that have CP or CC pairs (its leaf included when that is
+// such a cluster), each evaluated in FP32 (Sec. 3.3: each target cluster's polynomial at every
+// particle below it).  Barycentric coordinates come from the FP32 frame about the cluster
+// centre and x - c formed from the hi/lo pairs, so they carry no cancellation; the
+// coefficients describe a smooth interpolant in a basis that is non-negative on the triangle,
+// so the evaluation carries none of the contraction's.
+template <int D>
+__global__ void k_downward32(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
+                             const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
+                             const uint8_t* __restrict__ has, const float* __restrict__ frame32,
+                             const double4* __restrict__ src64, const float4* __restrict__ src_hl,
+                             const int32_t* __restrict__ perm, const float* __restrict__ coef32,
+                             double* __restrict__ vel)
+{
+    constexpr int M = (D + 1) * (D + 2) / 2;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
+    float fx = 0.f, fy = 0.f, fz = 0.f;  // the interpolated -(1/4 pi) S
+    bool any = false;
+    for (int32_t a = leaves[slot_leaf[j]]; a >= 0; a = parent[a]) {
+        const int32_t cs = cluster_slot[a];
+        if (cs < 0 || !has[cs]) continue;
         const float* h = frame32 + 18 * (int64_t)cs;
-        float b1, b2, b3, fx = 0.f, fy = 0.f, fz = 0.f;
+        float b1, b2, b3;
         bary32(h, (hi.x - h[12]) + (lo.x - h[15]), (hi.y - h[13]) + (lo.y - h[16]), (hi.z - h[14]) + (lo.z - h[17]),
                b1, b2, b3);
         eval_poly<D, float>(b1, b2, b3, coef32 + 3 * (int64_t)cs * M, fx, fy, fz);
-        ax = fx;
-        ay = fy;
-        az = fz;
-    } else {
-        double b1, b2, b3;
-        bary64(frame + 12 * (int64_t)cs, x.x, x.y, x.z, b1, b2, b3);
-        eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)cs * M, ax, ay, az);
+        any = true;
     }
+    if (!any) return;
+    const double4 x = src64[j];
+    const double ax = fx, ay = fy, az = fz;
     const int64_t i = perm[j];
     vel[3 * i] += x.y * az - x.z * ay;
     vel[3 * i + 1] += x.z * ax - x.x * az;
@@ -1126,30 +1193,29 @@ __global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, con
 
 namespace {
 
-template <int D, bool MIXED>
-void launch_down_p(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, cudaStream_t s)
-{
-    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
-    for (int l = 0; l < levels; l++)
-        (k_down_level<D, MIXED><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p,
-                                                  c->chas.p, c->cacc.p, c->nd_geom.p, c->up_frame.p,
-                                                  c->prx64.p, ref->d_beta.p, ref->d_vinv.p,
-                                                  c->cvel.p, c->cdown.p, c->cdown32.p),
-         note_launch());
-    (k_downward<D, MIXED><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                             c->cluster_slot.p, c->cacc.p, c->up_frame.p,
-                                                             c->up_frame32.p, c->src64.p, c->src_hl.p, c->perm.p,
-                                                             c->cdown.p, c->cdown32.p, vel),
-     note_launch());
-}
-
 template <int D>
 void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, bool mixed, cudaStream_t s)
 {
-    if (mixed)
-        launch_down_p<D, true>(c, ref, levels, C, vel, s);
-    else
-        launch_down_p<D, false>(c, ref, levels, C, vel, s);
+    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
+    if (mixed) {
+        (k_cluster_coef<D><<<gl, 64, 0, s>>>(c->dc.p + kDcClusters, c->cluster_node.p, c->chas.p, c->nd_geom.p,
+                                             ref->d_beta.p, ref->d_vinvT.p, c->cvel.p, c->cdown32.p),
+         note_launch());
+        (k_downward32<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
+                                                            c->cluster_slot.p, c->chas.p, c->up_frame32.p,
+                                                            c->src64.p, c->src_hl.p, c->perm.p, c->cdown32.p, vel),
+         note_launch());
+        return;
+    }
+    for (int l = 0; l < levels; l++)
+        (k_down_level<D><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
+                                           c->cacc.p, c->nd_geom.p, c->up_frame.p, c->prx64.p, ref->d_beta.p,
+                                           ref->d_vinvT.p, c->cvel.p, c->cdown.p),
+         note_launch());
+    (k_downward<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
+                                                      c->cluster_slot.p, c->cacc.p, c->up_frame.p, c->src64.p,
+                                                      c->perm.p, c->cdown.p, vel),
+     note_launch());
 }
 
 }  // namespace
@@ -1188,7 +1254,8 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     ls.ntargets = C * M;
     phase_begin(c, kPhCluster, s);
     if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s, -1))) return rc;
-    // interpolants passed down level by level, then evaluated at the particles
+    // the interpolants (FP64: passed down level by level; mixed: one per cluster, every
+    // ancestor's evaluated at each particle), then evaluated at the particles
     const int levels = (cap ? c->plan.depth : (int)c->deepest) + 1;
     const bool mixed = precision != STS_FP64;
     switch (degree) {

@@ -96,6 +96,7 @@ struct RefTable {
     std::vector<double> beta;  // [M,3] barycentric proxy points on the reference simplex
     std::vector<double> vinv;  // [M,M], vinv[k*M+m] = (V_ref^{-1})[k][m]
     DevBuf<double> d_beta, d_vinv;
+    DevBuf<double> d_vinvT;    // [M,M], d_vinvT[m*M+k] = (V_ref^{-1})[k][m] (threads over k read rows)
 };
 
 // Far-field list entry as the evaluation kernel reads it: proxy block of cluster `slot`

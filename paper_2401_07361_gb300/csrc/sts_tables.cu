@@ -210,14 +210,20 @@ RefTable* get_ref(sts_ctx* ctx, int d)
         set_error("proxy reference table for degree %d failed", d);
         return nullptr;
     }
+    std::vector<double> vt(t->vinv.size());
+    for (int k = 0; k < t->M; k++)
+        for (int m = 0; m < t->M; m++) vt[(size_t)m * t->M + k] = t->vinv[(size_t)k * t->M + m];
     if (t->d_beta.reserve(t->beta.size()) != cudaSuccess ||
         t->d_vinv.reserve(t->vinv.size()) != cudaSuccess ||
+        t->d_vinvT.reserve(vt.size()) != cudaSuccess ||
         cudaMemcpy(t->d_beta.p, t->beta.data(), t->beta.size() * sizeof(double),
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t->d_vinv.p, t->vinv.data(), t->vinv.size() * sizeof(double),
-                   cudaMemcpyHostToDevice) != cudaSuccess) {
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_vinvT.p, vt.data(), vt.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         t->d_beta.release();
         t->d_vinv.release();
+        t->d_vinvT.release();
         delete t;
         set_error("uploading the degree-%d proxy table failed", d);
         return nullptr;
