@@ -211,13 +211,18 @@ def sh_coefficients(lmax: int, seed: int):
     return coef
 
 
-def sh_series_vorticity(pos: np.ndarray, lmax: int, seed: int = 0) -> np.ndarray:
-    """Random zero-mean vorticity sum_{l=1..lmax} sum_m c_lm Y_lm with c_lm ~ N(0,1)/l."""
+def sh_series_vorticity(pos: np.ndarray, lmax: int, seed: int = 0, chunk: int = 1 << 16) -> np.ndarray:
+    """Random zero-mean vorticity sum_{l=1..lmax} sum_m c_lm Y_lm with c_lm ~ N(0,1)/l.  The
+    points are taken in chunks that stay in cache; every value is computed elementwise in the
+    same order whatever the chunk, so the result does not depend on it."""
     coef = sh_coefficients(lmax, seed)
-    zeta = np.zeros(np.asarray(pos).shape[0])
-    for key, y in _real_sh_iter(pos, lmax):
-        if key[0] >= 1:
-            zeta += coef[key] * y
+    pos = np.asarray(pos, dtype=np.float64)
+    zeta = np.zeros(pos.shape[0])
+    for c0 in range(0, pos.shape[0], chunk):
+        zc = zeta[c0:c0 + chunk]
+        for key, y in _real_sh_iter(pos[c0:c0 + chunk], lmax):
+            if key[0] >= 1:
+                zc += coef[key] * y
     return zeta
 
 
