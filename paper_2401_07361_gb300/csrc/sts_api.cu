@@ -112,6 +112,9 @@ sts_ctx::~sts_ctx()
     for (int p = 0; p < kNumPhases; p++)
         for (int q = 0; q < 2; q++)
             if (ev[p][q]) cudaEventDestroy(ev[p][q]);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     if (rk_exec) cudaGraphExecDestroy(rk_exec);
     if (ev_exec) cudaGraphExecDestroy(ev_exec);
     if (d_status) cudaFree(d_status);
@@ -184,6 +187,48 @@ int check_n(int64_t n, const char* fn)
 int velocity_dual_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p, double* vel,
                        cudaStream_t s);
 
+// The sorted sources and the proxy weights (upward pass) on s, and, when the tree or theta
+// changed, the interaction lists (target-leaf lists or the dual traversal's pairs) on the
+// side stream: both read only the tree (the cluster table and the upward tasks are made with
+// it), write disjoint buffers and device counters, and meet again before the evaluation.  The
+// sources and weights are issued first, so that an eager list build, which reads its counts
+// on the host, overlaps them too.  The side stream is joined back to s on every return.
+int sources_and_lists(sts_ctx* c, const double* zeta, const double* area, const sts_params* p,
+                      int up_precision, bool dual, cudaStream_t s)
+{
+    const bool lists = dual ? (!c->have_dual || c->dual_theta != p->theta)
+                            : (!c->have_lists || c->list_theta != p->theta);
+    if (lists) {
+        STS_CUDA(cudaEventRecord(c->ev_fork, s));
+        STS_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    int rc;
+    phase_begin(c, kPhPrep, s);
+    rc = prepare_sources(c, zeta, area, s);
+    phase_end(c, kPhPrep, s);
+    if (rc == STS_OK) {
+        phase_begin(c, kPhUpward, s);
+        rc = upward_pass(c, p->degree, up_precision, s);
+        phase_end(c, kPhUpward, s);
+    }
+    if (lists) {
+        int rl = STS_OK;
+        if (rc == STS_OK) {
+            phase_begin(c, kPhLists, c->side);
+            rl = dual ? build_dual(c, p->theta, c->side) : build_lists(c, p->theta, c->side);
+            phase_end(c, kPhLists, c->side);
+        }
+        const cudaError_t e1 = cudaEventRecord(c->ev_join, c->side);
+        const cudaError_t e2 = cudaStreamWaitEvent(s, c->ev_join, 0);
+        if (rc == STS_OK) rc = rl;
+        if (rc == STS_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) {
+            set_error("joining the lists' stream: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+            rc = STS_ERR_CUDA;
+        }
+    }
+    return rc;
+}
+
 int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_params* p,
                   double* vel, cudaStream_t s)
 {
@@ -195,17 +240,7 @@ int velocity_impl(sts_ctx* c, const double* zeta, const double* area, const sts_
         return STS_OK;
     }
     int rc;
-    phase_begin(c, kPhPrep, s);
-    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
-    phase_end(c, kPhPrep, s);
-    if (!c->have_lists || c->list_theta != p->theta) {
-        phase_begin(c, kPhLists, s);
-        if ((rc = build_lists(c, p->theta, s))) return rc;
-        phase_end(c, kPhLists, s);
-    }
-    phase_begin(c, kPhUpward, s);
-    if ((rc = upward_pass(c, p->degree, p->precision, s))) return rc;
-    phase_end(c, kPhUpward, s);
+    if ((rc = sources_and_lists(c, zeta, area, p, p->precision, false, s))) return rc;
     if ((rc = evaluate(c, p->degree, p->precision, p->near_fp64_tau, vel, s))) return rc;
     c->list_degree = p->degree;
     return STS_OK;
@@ -223,17 +258,7 @@ int potential_impl(sts_ctx* c, const double* zeta, const double* area, const sts
         return STS_OK;
     }
     int rc;
-    phase_begin(c, kPhPrep, s);
-    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
-    phase_end(c, kPhPrep, s);
-    if (!c->have_lists || c->list_theta != p->theta) {
-        phase_begin(c, kPhLists, s);
-        if ((rc = build_lists(c, p->theta, s))) return rc;
-        phase_end(c, kPhLists, s);
-    }
-    phase_begin(c, kPhUpward, s);
-    if ((rc = upward_pass(c, p->degree, STS_FP64, s))) return rc;
-    phase_end(c, kPhUpward, s);
+    if ((rc = sources_and_lists(c, zeta, area, p, STS_FP64, false, s))) return rc;
     if ((rc = evaluate_potential(c, p->degree, psi, s))) return rc;
     c->list_degree = p->degree;
     return STS_OK;
@@ -252,17 +277,7 @@ int velocity_dual_impl(sts_ctx* c, const double* zeta, const double* area, const
         return STS_OK;
     }
     int rc;
-    phase_begin(c, kPhPrep, s);
-    if ((rc = prepare_sources(c, zeta, area, s))) return rc;
-    phase_end(c, kPhPrep, s);
-    if (!c->have_dual || c->dual_theta != p->theta) {
-        phase_begin(c, kPhLists, s);
-        if ((rc = build_dual(c, p->theta, s))) return rc;
-        phase_end(c, kPhLists, s);
-    }
-    phase_begin(c, kPhUpward, s);
-    if ((rc = upward_pass(c, p->degree, p->precision, s))) return rc;
-    phase_end(c, kPhUpward, s);
+    if ((rc = sources_and_lists(c, zeta, area, p, p->precision, true, s))) return rc;
     if ((rc = evaluate_dual(c, p->degree, p->precision, p->near_fp64_tau, vel, s))) return rc;
     c->list_degree = p->degree;
     return STS_OK;
@@ -652,6 +667,9 @@ int sts_create(sts_ctx** out)
     // inspecting a context between graph replays moves no buffer the recordings use
     if (e == cudaSuccess) e = c->d_stats.reserve(8);
     if (e == cudaSuccess) e = c->dual_cnt.reserve(128);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_error("sts_create: %s", cudaGetErrorString(e));
         delete c;

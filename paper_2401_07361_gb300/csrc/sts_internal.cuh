@@ -294,6 +294,13 @@ struct sts_ctx {
     bool phase_in_graph[sts::kNumPhases] = {};  // phases recorded inside the current graphs
 
     std::vector<sts::RefTable*> refs;    // by degree
+
+    // ---- the lists' side stream --------------------------------------------------------
+    // The interaction lists and the sources / proxy weights depend only on the tree, so the
+    // lists are built on a stream of their own, forked from and joined back to the caller's
+    // stream by events (graph recordings included).
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~sts_ctx();
 };
 
