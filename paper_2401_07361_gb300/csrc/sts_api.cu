@@ -100,7 +100,7 @@ sts_ctx::~sts_ctx()
     dual_scan.release(); cfar_off.release(); cnear_off.release(); cnear_coff.release(); cfar_ent.release();
     cnear_ent.release(); ctasks.release(); cvel.release(); ccorr.release(); cdown.release(); cdown32.release();
     chas.release();
-    cacc.release();
+    cacc.release(); leaf_anc.release();
     if (amr) amr_free(amr);
     for (RefTable* t : refs)
         if (t) {

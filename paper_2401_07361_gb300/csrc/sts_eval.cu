@@ -6,17 +6,19 @@
 // (Eq. altkernel) and x_i x x_j = x_i x d.  The kernels accumulate S_i = sum_j 2 w_j d /
 // |d|^2 and the epilogue forms u_i = -(1/4 pi) x_i x S_i in FP64.
 //
-// Evaluation layout: one warp per task (up to 32 consecutive targets of one leaf, lane =
-// target).  When a task has 16 or fewer targets, 2 or 4 lanes share a target and split its
-// sources; they are summed with shuffles at the end.  Source blocks (a cluster's M proxy
-// points, a near leaf's particles) are staged in shared memory by the warp with coalesced
-// 16-byte loads, each lane then streams the block with broadcast shared-memory reads.
+// Evaluation layout: one warp per task (up to 64 consecutive targets of one leaf, two per
+// lane); S = 1..8 lanes share a pair of targets and split its sources, summed with shuffles at
+// the end.  Persistent CTAs take the tasks from a device queue.  Consecutive source blocks (a
+// cluster's M proxy points, a chunk of a near leaf's particles) are staged as a group in one
+// of two shared-memory stages by TMA bulk copies against the stage's mbarrier, padded to a
+// multiple of 4 S entries; each lane then streams the stage with broadcast shared-memory reads.
 //
 // Mixed precision (STS_MIXED): targets, sources and proxy points are stored in FP32
 // relative to the circumcentre of their own leaf or cluster; the FP32 offset between the two
-// centres (rounded once from FP64 per list entry) is added when a block is staged, so that
-// d keeps FP32 relative accuracy at every distance the tree produces.  Per block the lane
-// sums in FP32, and the block partials go into a TwoSum-compensated accumulator.  Near pairs
+// centres (rounded once from FP64 per list entry) is folded into the two targets once per
+// block, so that d keeps FP32 relative accuracy at every distance the tree produces.  Per
+// group the lane sums in FP32, and the group partials go into a TwoSum-compensated
+// accumulator.  Near pairs
 // with |d|^2 / 2 < tau are evaluated in FP64 from the FP64 positions instead.  A zero d
 // (the target itself, or a coincident particle) contributes nothing, as in the oracle:
 // |d|^2 carries an additive 1e-30 so that 2w / |d|^2 stays finite and is multiplied by 0.
@@ -843,21 +845,6 @@ int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
 
 namespace {
 
-// One list set for the evaluation kernels: the leaf lists (targets: the sorted particles,
-// results to vel in the caller's order) or the cluster lists of the dual traversal (targets:
-// the proxy points of the target clusters, results in proxy order).
-struct ListSet {
-    const Task* tasks;
-    const int64_t* ntasks_d;
-    int64_t ntasks;
-    const int64_t *far_off, *near_coff;
-    const FarEntry* far_ent;
-    const NearEntry* near_ent;
-    const float4* tgt32;
-    const double4* tgt64;
-    const int32_t* perm;  // target slot -> output row, or nullptr for the identity
-    int64_t ntargets;     // rows of corr
-};
 
 int eval_blocks(sts_ctx* c)
 {
@@ -874,9 +861,11 @@ int eval_blocks(sts_ctx* c)
     return STS_OK;
 }
 
+}  // namespace
+
 // corr: FP64 close-pair scratch of at least 3 * ls.ntargets doubles (mixed precision).
 int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, double tau, DevBuf<double>& corrbuf,
-                   double* vel, cudaStream_t s, int phase = kPhEval)
+                   double* vel, cudaStream_t s, int phase)
 {
     const int M = nbasis(degree);
     if (ls.ntasks <= 0) return STS_OK;
@@ -919,8 +908,6 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
     return STS_OK;
 }
 
-}  // namespace
-
 int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
 {
     ListSet ls;
@@ -936,349 +923,6 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
     ls.perm = c->perm.p;
     ls.ntargets = c->n;
     return evaluate_lists(c, ls, degree, precision, tau, c->corr, vel, s);
-}
-
-// ------------------------------------------------------------------------ dual: downward
-namespace {
-
-// The interpolating polynomial of a cluster (degree D, M = (D+1)(D+2)/2 coefficients
-// cf[M][3]) at a point with spherical barycentric coordinates b in the cluster's triangle
-// (Sec. 3.2, x = b1 v1 + b2 v2 + b3 v3): sum_k B_k(b) c_k with B_k(b) = b1^a b2^b b3^c in the
-// order a = D..0, b = D - a..0, summed per a and then over a.  D is a template parameter so
-// that the powers stay in registers.  T = double, or float for the particles of the mixed path:
-// the coefficients come from the FP64 contraction and describe a smooth interpolant, so the
-// evaluation carries none of the contraction's cancellation (its error is eps32 times the
-// Bernstein coefficients, which track the interpolated values).
-template <int D, class T>
-__device__ __forceinline__ void eval_poly(T b1, T b2, T b3, const T* __restrict__ cf, T& ax, T& ay, T& az)
-{
-    T p1[D + 1], p2[D + 1], p3[D + 1];
-    p1[0] = p2[0] = p3[0] = T(1);
-#pragma unroll
-    for (int e = 1; e <= D; e++) {
-        p1[e] = p1[e - 1] * b1;
-        p2[e] = p2[e - 1] * b2;
-        p3[e] = p3[e - 1] * b3;
-    }
-    int k = 0;
-#pragma unroll
-    for (int ea = D; ea >= 0; ea--) {
-        T sx = T(0), sy = T(0), sz = T(0);
-#pragma unroll
-        for (int eb = D - ea; eb >= 0; eb--, k++) {
-            const T B = p2[eb] * p3[D - ea - eb];
-            sx += B * cf[3 * k];
-            sy += B * cf[3 * k + 1];
-            sz += B * cf[3 * k + 2];
-        }
-        ax += p1[ea] * sx;
-        ay += p1[ea] * sy;
-        az += p1[ea] * sz;
-    }
-}
-
-// Barycentric coordinates from the FP64 frame (rows n_i / D of Cramer's rule: n1 = v2 x v3,
-// n2 = v3 x v1, n3 = v1 x v2, D = v1 . n1) ...
-__device__ __forceinline__ void bary64(const double* __restrict__ f, double x, double y, double z, double& b1,
-                                       double& b2, double& b3)
-{
-    b1 = f[0] * x + f[1] * y + f[2] * z;
-    b2 = f[3] * x + f[4] * y + f[5] * z;
-    b3 = f[6] * x + f[7] * y + f[8] * z;
-}
-
-// ... and from the FP32 frame about the centre: b = b(c) + (n_i / D) . (x - c), with x - c
-// already formed accurately (hi/lo pairs or an FP64 difference).
-__device__ __forceinline__ void bary32(const float* __restrict__ h, float dx, float dy, float dz, float& b1,
-                                       float& b2, float& b3)
-{
-    b1 = h[9] + (h[0] * dx + h[1] * dy + h[2] * dz);
-    b2 = h[10] + (h[3] * dx + h[4] * dy + h[5] * dz);
-    b3 = h[11] + (h[6] * dx + h[7] * dy + h[8] * dz);
-}
-
-// FP64 precision: interpolants of the clusters of level l (Sec. 3.3, CP and CC: the kernel sum
-// -(1/4 pi) S at the target cluster's proxy points, interpolated over the cluster; the velocity
-// at a particle x is then x x the interpolant, tangent to the sphere), passed down the tree.
-// U_T = the sum of T's own CP and CC pairs at its proxy points (cvel; zero without such pairs)
-// plus the interpolant of its parent, which already holds every ancestor's, evaluated there.  A
-// degree-d polynomial in one triangle's barycentric coordinates is one in any other's (both are
-// the homogeneous degree-d polynomials in x), so interpolating the parent's at T's M proxy
-// points reproduces it exactly: a particle then evaluates its lowest cluster's interpolant only,
-// which equals the sum of all its ancestors' interpolants.  Coefficients: with proxy points
-// x~_m = s_m / rho_m, s_m = sum_i beta_mi v_i, rho_m = |s_m|, the barycentric coordinates of
-// x~_m are beta_m / rho_m, so V_T = diag(rho^-d) V_ref and c = V_ref^-1 diag(rho^d) U.
-// acc[c]: cluster c holds an interpolant.  One CTA per cluster of the level.
-template <int D>
-__global__ void k_down_level(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ parent,
-                             const int32_t* __restrict__ cluster_slot, const uint8_t* __restrict__ has,
-                             uint8_t* __restrict__ acc, const double* __restrict__ geom,
-                             const double* __restrict__ frame, const double4* __restrict__ prx64,
-                             const double* __restrict__ beta, const double* __restrict__ vinvT,
-                             const double* __restrict__ cvel, double* __restrict__ coef)
-{
-    constexpr int d = D, M = (D + 1) * (D + 2) / 2;
-    __shared__ double u[3 * kMaxM];
-    const int64_t lb = lvl[l], le = lvl[l + 1];
-    for (int64_t p = lb + blockIdx.x; p < le; p += gridDim.x) {
-        const int32_t cs = cluster_slot[p];
-        if (cs < 0) continue;
-        const int32_t par = parent[p];
-        const int32_t ps = par >= 0 ? cluster_slot[par] : -1;
-        const bool from_parent = ps >= 0 && acc[ps];
-        const bool own = has[cs] != 0;
-        if (threadIdx.x == 0) acc[cs] = (own || from_parent) ? 1 : 0;
-        if (!own && !from_parent) continue;
-        const double* g = geom + 13 * p;
-        __syncthreads();  // u of the previous cluster is no longer read
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            double vx = 0.0, vy = 0.0, vz = 0.0;
-            if (own) {
-                const double* v = cvel + 3 * ((int64_t)cs * M + m);
-                vx = v[0];
-                vy = v[1];
-                vz = v[2];
-            }
-            if (from_parent) {
-                const double4 x = prx64[(int64_t)cs * M + m];
-                double b1, b2, b3;
-                bary64(frame + 12 * (int64_t)ps, x.x, x.y, x.z, b1, b2, b3);
-                eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)ps * M, vx, vy, vz);
-            }
-            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
-            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
-            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
-            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
-            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
-            double rd = 1.0;
-            for (int e = 0; e < d; e++) rd *= rho;
-            u[3 * m] = rd * vx;
-            u[3 * m + 1] = rd * vy;
-            u[3 * m + 2] = rd * vz;
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int m = 0; m < M; m++) {
-                const double w = vinvT[m * M + k];
-                ax += w * u[3 * m];
-                ay += w * u[3 * m + 1];
-                az += w * u[3 * m + 2];
-            }
-            double* o = coef + 3 * ((int64_t)cs * M + k);
-            o[0] = ax;
-            o[1] = ay;
-            o[2] = az;
-        }
-    }
-}
-
-// FP64 precision: adds to every particle x (sorted slot) x crossed with the interpolant of its
-// lowest cluster: its leaf when that is a cluster (at the depth limit), else the leaf's parent.
-template <int D>
-__global__ void k_downward(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
-                           const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
-                           const uint8_t* __restrict__ acc, const double* __restrict__ frame,
-                           const double4* __restrict__ src64, const int32_t* __restrict__ perm,
-                           const double* __restrict__ coef, double* __restrict__ vel)
-{
-    constexpr int M = (D + 1) * (D + 2) / 2;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int32_t a = leaves[slot_leaf[j]];
-    if (cluster_slot[a] < 0) a = parent[a];
-    if (a < 0) return;  // a root leaf: no cluster above it
-    const int32_t cs = cluster_slot[a];
-    if (cs < 0 || !acc[cs]) return;
-    const double4 x = src64[j];
-    double ax = 0.0, ay = 0.0, az = 0.0;  // the interpolated -(1/4 pi) S
-    double b1, b2, b3;
-    bary64(frame + 12 * (int64_t)cs, x.x, x.y, x.z, b1, b2, b3);
-    eval_poly<D, double>(b1, b2, b3, coef + 3 * (int64_t)cs * M, ax, ay, az);
-    const int64_t i = perm[j];
-    vel[3 * i] += x.y * az - x.z * ay;
-    vel[3 * i + 1] += x.z * ax - x.x * az;
-    vel[3 * i + 2] += x.x * ay - x.y * ax;
-}
-
-// Mixed precision: the interpolant of every cluster with CP or CC pairs (Sec. 3.3), each from
-// its own U_T only: c = V_ref^-1 diag(rho^d) U_T in FP64 (V_ref^-1 carries cond(V_ref), so
-// FP32 would lose the coefficients), rounded to FP32 once for the particles.  The clusters are
-// independent (no parent's interpolant is carried down), so one launch takes all of them: a
-// fixed grid strides over the clusters, whose count is on the device.
-template <int D>
-__global__ void k_cluster_coef(const int64_t* __restrict__ nclu, const int32_t* __restrict__ cnode,
-                               const uint8_t* __restrict__ has, const double* __restrict__ geom,
-                               const double* __restrict__ beta, const double* __restrict__ vinvT,
-                               const double* __restrict__ cvel, float* __restrict__ coef32)
-{
-    constexpr int d = D, M = (D + 1) * (D + 2) / 2;
-    __shared__ double u[3 * kMaxM];
-    const int64_t ncl = *nclu;
-    for (int64_t cs = blockIdx.x; cs < ncl; cs += gridDim.x) {
-        if (!has[cs]) continue;
-        const double* g = geom + 13 * (int64_t)cnode[cs];
-        __syncthreads();  // u of the previous cluster is no longer read
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
-            const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
-            const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
-            const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
-            const double rho = sqrt((sx * sx + sy * sy) + sz * sz);
-            double rd = 1.0;
-            for (int e = 0; e < d; e++) rd *= rho;
-            const double* v = cvel + 3 * (cs * M + m);
-            u[3 * m] = rd * v[0];
-            u[3 * m + 1] = rd * v[1];
-            u[3 * m + 2] = rd * v[2];
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
-            double ax = 0.0, ay = 0.0, az = 0.0;
-            for (int m = 0; m < M; m++) {
-                const double w = vinvT[m * M + k];
-                ax += w * u[3 * m];
-                ay += w * u[3 * m + 1];
-                az += w * u[3 * m + 2];
-            }
-            float* o = coef32 + 3 * (cs * M + k);
-            o[0] = (float)ax;
-            o[1] = (float)ay;
-            o[2] = (float)az;
-        }
-    }
-}
-
-// Mixed precision: adds to every particle x (sorted slot) x crossed with the sum of the
-// interpolants of its ancestor clusters that have CP or CC pairs (its leaf included when that is
-// such a cluster), each evaluated in FP32 (Sec. 3.3: each target cluster's polynomial at every
-// particle below it).  Barycentric coordinates come from the FP32 frame about the cluster
-// centre and x - c formed from the hi/lo pairs, so they carry no cancellation; the
-// coefficients describe a smooth interpolant in a basis that is non-negative on the triangle,
-// so the evaluation carries none of the contraction's.
-template <int D>
-__global__ void k_downward32(int64_t n, const int32_t* __restrict__ slot_leaf, const int32_t* __restrict__ leaves,
-                             const int32_t* __restrict__ parent, const int32_t* __restrict__ cluster_slot,
-                             const uint8_t* __restrict__ has, const float* __restrict__ frame32,
-                             const double4* __restrict__ src64, const float4* __restrict__ src_hl,
-                             const int32_t* __restrict__ perm, const float* __restrict__ coef32,
-                             double* __restrict__ vel)
-{
-    constexpr int M = (D + 1) * (D + 2) / 2;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
-    float fx = 0.f, fy = 0.f, fz = 0.f;  // the interpolated -(1/4 pi) S
-    bool any = false;
-    for (int32_t a = leaves[slot_leaf[j]]; a >= 0; a = parent[a]) {
-        const int32_t cs = cluster_slot[a];
-        if (cs < 0 || !has[cs]) continue;
-        const float* h = frame32 + 18 * (int64_t)cs;
-        float b1, b2, b3;
-        bary32(h, (hi.x - h[12]) + (lo.x - h[15]), (hi.y - h[13]) + (lo.y - h[16]), (hi.z - h[14]) + (lo.z - h[17]),
-               b1, b2, b3);
-        eval_poly<D, float>(b1, b2, b3, coef32 + 3 * (int64_t)cs * M, fx, fy, fz);
-        any = true;
-    }
-    if (!any) return;
-    const double4 x = src64[j];
-    const double ax = fx, ay = fy, az = fz;
-    const int64_t i = perm[j];
-    vel[3 * i] += x.y * az - x.z * ay;
-    vel[3 * i + 1] += x.z * ax - x.x * az;
-    vel[3 * i + 2] += x.x * ay - x.y * ax;
-}
-
-}  // namespace
-
-namespace {
-
-template <int D>
-void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, double* vel, bool mixed, cudaStream_t s)
-{
-    const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
-    if (mixed) {
-        (k_cluster_coef<D><<<gl, 64, 0, s>>>(c->dc.p + kDcClusters, c->cluster_node.p, c->chas.p, c->nd_geom.p,
-                                             ref->d_beta.p, ref->d_vinvT.p, c->cvel.p, c->cdown32.p),
-         note_launch());
-        (k_downward32<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                            c->cluster_slot.p, c->chas.p, c->up_frame32.p,
-                                                            c->src64.p, c->src_hl.p, c->perm.p, c->cdown32.p, vel),
-         note_launch());
-        return;
-    }
-    for (int l = 0; l < levels; l++)
-        (k_down_level<D><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
-                                           c->cacc.p, c->nd_geom.p, c->up_frame.p, c->prx64.p, ref->d_beta.p,
-                                           ref->d_vinvT.p, c->cvel.p, c->cdown.p),
-         note_launch());
-    (k_downward<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, c->leaves.p, c->nd_parent.p,
-                                                      c->cluster_slot.p, c->cacc.p, c->up_frame.p, c->src64.p,
-                                                      c->perm.p, c->cdown.p, vel),
-     note_launch());
-}
-
-}  // namespace
-
-int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel, cudaStream_t s)
-{
-    // PP and PC: the leaf lists hold the dual traversal's pairs of the target leaves
-    int rc = evaluate(c, degree, precision, tau, vel, s);
-    if (rc) return rc;
-    const bool cap = c->capturing;
-    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
-    if (C == 0 || c->n < 2) return STS_OK;
-    if (!cap && c->dual_n[2] == 0 && c->dual_n[3] == 0) return STS_OK;  // no CP or CC pairs
-    RefTable* ref = get_ref(c, degree);
-    if (!ref) return STS_ERR_CUDA;
-    const int M = ref->M;
-    if ((rc = cluster_tasks(c, M, s))) return rc;
-    if (!cap) {
-        STS_CUDA(c->cvel.reserve(3 * C * M + 3));
-        STS_CUDA(c->cdown.reserve(3 * C * M + 3));
-        STS_CUDA(c->cdown32.reserve(3 * C * M + 3));
-        STS_CUDA(c->cacc.reserve(C + 1));
-    }
-    // CP and CC: the velocity at the proxy points of the target clusters
-    ListSet ls;
-    ls.tasks = c->ctasks.p;
-    ls.ntasks_d = cluster_task_count(c);
-    ls.ntasks = c->nctasks;
-    ls.far_off = c->cfar_off.p;
-    ls.near_coff = c->cnear_coff.p;
-    ls.far_ent = c->cfar_ent.p;
-    ls.near_ent = c->cnear_ent.p;
-    ls.tgt32 = c->prx32.p;
-    ls.tgt64 = c->prx64.p;
-    ls.perm = nullptr;
-    ls.ntargets = C * M;
-    phase_begin(c, kPhCluster, s);
-    if ((rc = evaluate_lists(c, ls, degree, precision, tau, c->ccorr, c->cvel.p, s, -1))) return rc;
-    // the interpolants (FP64: passed down level by level; mixed: one per cluster, every
-    // ancestor's evaluated at each particle), then evaluated at the particles
-    const int levels = (cap ? c->plan.depth : (int)c->deepest) + 1;
-    const bool mixed = precision != STS_FP64;
-    switch (degree) {
-        case 1: launch_down<1>(c, ref, levels, C, vel, mixed, s); break;
-        case 2: launch_down<2>(c, ref, levels, C, vel, mixed, s); break;
-        case 3: launch_down<3>(c, ref, levels, C, vel, mixed, s); break;
-        case 4: launch_down<4>(c, ref, levels, C, vel, mixed, s); break;
-        case 5: launch_down<5>(c, ref, levels, C, vel, mixed, s); break;
-        case 6: launch_down<6>(c, ref, levels, C, vel, mixed, s); break;
-        case 7: launch_down<7>(c, ref, levels, C, vel, mixed, s); break;
-        case 8: launch_down<8>(c, ref, levels, C, vel, mixed, s); break;
-        case 9: launch_down<9>(c, ref, levels, C, vel, mixed, s); break;
-        case 10: launch_down<10>(c, ref, levels, C, vel, mixed, s); break;
-        case 11: launch_down<11>(c, ref, levels, C, vel, mixed, s); break;
-        case 12: launch_down<12>(c, ref, levels, C, vel, mixed, s); break;
-        case 13: launch_down<13>(c, ref, levels, C, vel, mixed, s); break;
-        case 14: launch_down<14>(c, ref, levels, C, vel, mixed, s); break;
-        case 15: launch_down<15>(c, ref, levels, C, vel, mixed, s); break;
-        default: launch_down<16>(c, ref, levels, C, vel, mixed, s); break;
-    }
-    phase_end(c, kPhCluster, s);
-    STS_LAUNCH_CHECK();
-    return STS_OK;
 }
 
 int wait_selftest(sts_ctx* c, int spins, cudaStream_t s)

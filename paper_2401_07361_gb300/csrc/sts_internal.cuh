@@ -268,9 +268,10 @@ struct sts_ctx {
     sts::DevBuf<double> cvel;            // [C, M, 3] velocity at the proxy points of target clusters
     sts::DevBuf<double> ccorr;           // [C, M, 3] FP64 close-pair sums of the proxy targets
     sts::DevBuf<double> cdown;           // [C, M, 3] coefficients of the interpolating polynomials
-    sts::DevBuf<float> cdown32;          // [C, M, 3] the same rounded to FP32 (mixed precision)
+    sts::DevBuf<float> cdown32;          // [C, M, 4] FP32 coefficients, one float4 per basis function (mixed)
     sts::DevBuf<uint8_t> chas;           // [C] the cluster is the target of CP or CC pairs
     sts::DevBuf<uint8_t> cacc;           // [C] the cluster holds an interpolant (its own or an ancestor's)
+    sts::DevBuf<int32_t> leaf_anc;       // [L, A] per leaf: count, then its ancestor clusters with CP / CC pairs
 
     // ---- adaptive mesh refinement (Appendix A) -----------------------------------------
     sts::AmrState* amr = nullptr;
@@ -372,10 +373,26 @@ int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
 
 // ---- evaluation (sts_eval.cu) ---------------------------------------------------------
 int evaluate(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
-// Dual-traversal velocity: PP and PC at the particles of the target leaves, CP and CC at the
-// proxy points of the target clusters, then the interpolating polynomial of every target
-// cluster evaluated at its particles and added (Sec. 3.3, 3.4).
-int evaluate_dual(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
+// One list set for the evaluation kernels: the leaf lists (targets: the sorted particles,
+// results to vel in the caller's order) or the cluster lists of the dual traversal (targets:
+// the proxy points of the target clusters, results in proxy order).
+struct ListSet {
+    const Task* tasks;
+    const int64_t* ntasks_d;
+    int64_t ntasks;
+    const int64_t *far_off, *near_coff;
+    const FarEntry* far_ent;
+    const NearEntry* near_ent;
+    const float4* tgt32;
+    const double4* tgt64;
+    const int32_t* perm;  // target slot -> output row, or nullptr for the identity
+    int64_t ntargets;     // rows of corr
+};
+// The mixed or FP64 evaluation kernel over one list set; corrbuf: the FP64 close-pair scratch
+// (grown to 3 * ls.ntargets doubles eagerly); phase: the timed phase (-1: inside the caller's).
+int evaluate_lists(sts_ctx* ctx, const ListSet& ls, int degree, int precision, double tau, DevBuf<double>& corrbuf,
+                   double* vel, cudaStream_t s, int phase = kPhEval);
+
 int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
                      double* psi, cudaStream_t s);
 int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s);
@@ -384,6 +401,13 @@ int count_interactions(sts_ctx* ctx, int degree, cudaStream_t s);
 int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
                int64_t n, const int64_t* targets, int64_t nt, int precision, double* vel,
                cudaStream_t s);
+
+
+// ---- dual traversal: CP / CC evaluation and the downward pass (sts_down.cu) -----------
+// Dual-traversal velocity: PP and PC at the particles of the target leaves, CP and CC at the
+// proxy points of the target clusters, then the interpolating polynomial of every target
+// cluster evaluated at its particles and added (Sec. 3.3, 3.4).
+int evaluate_dual(sts_ctx* ctx, int degree, int precision, double tau, double* vel, cudaStream_t s);
 
 // ---- RK4 (sts_rk4.cu) -----------------------------------------------------------------
 double forcing_ramp(double t, double Tp, double Tf);

@@ -1899,9 +1899,10 @@ int reserve_dual_for_capture(sts_ctx* c, int degree, cudaStream_t s)
     STS_CUDA(c->ctasks.reserve(C * ((M + kTaskTargets - 1) / kTaskTargets + 3) + 1));
     STS_CUDA(c->cvel.reserve(3 * C * M + 3));
     STS_CUDA(c->cdown.reserve(3 * C * M + 3));
-    STS_CUDA(c->cdown32.reserve(3 * C * M + 3));
+    STS_CUDA(c->cdown32.reserve(4 * C * M + 4));
     STS_CUDA(c->ccorr.reserve(3 * C * M + 3));
     STS_CUDA(c->cacc.reserve(C + 1));
+    STS_CUDA(c->leaf_anc.reserve(L * (c->plan.depth + 2) + 1));
     return STS_OK;
 }
 
