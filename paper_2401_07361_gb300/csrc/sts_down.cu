@@ -277,46 +277,75 @@ __global__ void k_leaf_anc(const int64_t* __restrict__ nleaves, int64_t lcap, co
 // Mixed precision: adds to every particle x (sorted slot) x crossed with the sum of the
 // interpolants of its ancestor clusters that have CP or CC pairs (its leaf included when that is
 // such a cluster), each evaluated in FP32 (Sec. 3.3: each target cluster's polynomial at every
-// particle below it).  Barycentric coordinates come from the FP32 frame about the cluster
-// centre and x - c formed from the hi/lo pairs, so they carry no cancellation; the
+// particle below it).  One CTA per leaf: its clusters' coefficients and frames are staged in
+// shared memory by all threads at once (one round of independent loads), then each thread
+// takes particles of the leaf.  Barycentric coordinates come from the FP32 frame about the
+// cluster centre and x - c formed from the hi/lo pairs, so they carry no cancellation; the
 // coefficients describe a smooth interpolant in a basis that is non-negative on the triangle,
 // so the evaluation carries none of the contraction's.
+constexpr int kFrame32 = 18;  // floats per FP32 cluster frame
+
 template <int D>
-__global__ void k_downward32(int64_t n, const int32_t* __restrict__ slot_leaf, int64_t lcap,
-                             const int32_t* __restrict__ anc, int A, const float* __restrict__ frame32,
-                             const double4* __restrict__ src64, const float4* __restrict__ src_hl,
-                             const int32_t* __restrict__ perm, const float* __restrict__ coef32,
-                             double* __restrict__ vel)
+__global__ void __launch_bounds__(128) k_downward32(const int64_t* __restrict__ nleaves, int64_t lcap,
+                                                    const int32_t* __restrict__ leaves,
+                                                    const int32_t* __restrict__ start,
+                                                    const int32_t* __restrict__ count,
+                                                    const int32_t* __restrict__ anc, int A,
+                                                    const float* __restrict__ frame32,
+                                                    const double4* __restrict__ src64,
+                                                    const float4* __restrict__ src_hl,
+                                                    const int32_t* __restrict__ perm,
+                                                    const float4* __restrict__ coef4, double* __restrict__ vel)
 {
     constexpr int M = (D + 1) * (D + 2) / 2;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int32_t L = slot_leaf[j];
-    if (L >= lcap) return;  // a recorded step whose leaves outgrew the plan is redone eagerly
-    const int32_t* o = anc + (int64_t)L * A;
-    const int na = o[0];
-    if (na == 0) return;
-    const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
-    float fx = 0.f, fy = 0.f, fz = 0.f;  // the interpolated -(1/4 pi) S
-    for (int i = 1; i <= na; i++) {
-        const int32_t cs = o[i];
-        const float* h = frame32 + 18 * (int64_t)cs;
-        float b1, b2, b3;
-        bary32(h, (hi.x - h[12]) + (lo.x - h[15]), (hi.y - h[13]) + (lo.y - h[16]), (hi.z - h[14]) + (lo.z - h[17]),
-               b1, b2, b3);
-        eval_poly4<D>(b1, b2, b3, reinterpret_cast<const float4*>(coef32) + (int64_t)cs * M, fx, fy, fz);
+    extern __shared__ float4 sh[];  // [A - 1][M] coefficients, then [A - 1][18] frame floats
+    float* fr = reinterpret_cast<float*>(sh + (int64_t)(A - 1) * M);
+    const int64_t nl = min(*nleaves, lcap);  // a recorded step with more leaves is redone
+    for (int64_t L = blockIdx.x; L < nl; L += gridDim.x) {
+        const int32_t* o = anc + L * A;
+        const int na = o[0];
+        if (na == 0) continue;
+        const int32_t node = leaves[L];
+        const int32_t st = start[node], cnt = count[node];
+        __syncthreads();  // the previous leaf's staged clusters are no longer read
+        for (int t = threadIdx.x; t < na * M; t += blockDim.x) {
+            const int i = t / M;
+            sh[t] = coef4[(int64_t)o[1 + i] * M + (t - i * M)];
+        }
+        for (int t = threadIdx.x; t < na * kFrame32; t += blockDim.x) {
+            const int i = t / kFrame32;
+            fr[t] = frame32[(int64_t)o[1 + i] * kFrame32 + (t - i * kFrame32)];
+        }
+        __syncthreads();
+        for (int64_t j = st + threadIdx.x; j < (int64_t)st + cnt; j += blockDim.x) {
+            const float4 hi = src_hl[2 * j], lo = src_hl[2 * j + 1];
+            float fx = 0.f, fy = 0.f, fz = 0.f;  // the interpolated -(1/4 pi) S
+            for (int i = 0; i < na; i++) {
+                const float* h = fr + kFrame32 * i;
+                float b1, b2, b3;
+                bary32(h, (hi.x - h[12]) + (lo.x - h[15]), (hi.y - h[13]) + (lo.y - h[16]),
+                       (hi.z - h[14]) + (lo.z - h[17]), b1, b2, b3);
+                eval_poly4<D>(b1, b2, b3, sh + i * M, fx, fy, fz);
+            }
+            const double4 x = src64[j];
+            const double ax = fx, ay = fy, az = fz;
+            const int64_t r = perm[j];
+            vel[3 * r] += x.y * az - x.z * ay;
+            vel[3 * r + 1] += x.z * ax - x.x * az;
+            vel[3 * r + 2] += x.x * ay - x.y * ax;
+        }
     }
-    const double4 x = src64[j];
-    const double ax = fx, ay = fy, az = fz;
-    const int64_t i = perm[j];
-    vel[3 * i] += x.y * az - x.z * ay;
-    vel[3 * i + 1] += x.z * ax - x.x * az;
-    vel[3 * i + 2] += x.x * ay - x.y * ax;
 }
 
 template <int D>
-void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, int64_t lcap, double* vel, bool mixed,
-                 cudaStream_t s)
+constexpr int M_of()
+{
+    return (D + 1) * (D + 2) / 2;
+}
+
+template <int D>
+int launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, int64_t lcap, double* vel, bool mixed,
+                cudaStream_t s)
 {
     const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
     if (mixed) {
@@ -329,11 +358,18 @@ void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, int64_t
             (k_leaf_anc<<<blocks(lcap, 128), 128, 0, s>>>(c->dc.p + kDcLeaves, lcap, c->leaves.p, c->nd_parent.p,
                                                           c->cluster_slot.p, c->chas.p, A, c->leaf_anc.p),
              note_launch());
-        (k_downward32<D><<<blocks(c->n, 128), 128, 0, s>>>(c->n, c->slot_leaf.p, lcap, c->leaf_anc.p, A,
-                                                            c->up_frame32.p, c->src64.p, c->src_hl.p, c->perm.p,
-                                                            c->cdown32.p, vel),
-         note_launch());
-        return;
+        const size_t smem = (size_t)(A - 1) * (M_of<D>() * sizeof(float4) + kFrame32 * sizeof(float));
+        if (!c->capturing) {  // the largest a recording can ask for: every level of the deepest tree
+            const size_t smax = (size_t)(kMaxLevel + 2) * (M_of<D>() * sizeof(float4) + kFrame32 * sizeof(float));
+            STS_CUDA(cudaFuncSetAttribute(k_downward32<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+        }
+        if (lcap > 0)
+            (k_downward32<D><<<(unsigned)std::min<int64_t>(lcap, 1 << 30), 128, smem, s>>>(
+                 c->dc.p + kDcLeaves, lcap, c->leaves.p, c->nd_start.p, c->nd_count.p, c->leaf_anc.p, A,
+                 c->up_frame32.p, c->src64.p, c->src_hl.p, c->perm.p,
+                 reinterpret_cast<const float4*>(c->cdown32.p), vel),
+             note_launch());
+        return STS_OK;
     }
     for (int l = 0; l < levels; l++)
         (k_down_level<D><<<gl, 64, 0, s>>>(c->dc.p + kDcLevel, l, c->nd_parent.p, c->cluster_slot.p, c->chas.p,
@@ -344,6 +380,7 @@ void launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, int64_t
                                                       c->cluster_slot.p, c->cacc.p, c->up_frame.p, c->src64.p,
                                                       c->perm.p, c->cdown.p, vel),
      note_launch());
+    return STS_OK;
 }
 
 }  // namespace
@@ -391,23 +428,24 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     const int64_t lcap = cap ? std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64) : c->nleaves;
     if (!cap && mixed) STS_CUDA(c->leaf_anc.reserve(lcap * (levels + 1) + 1));
     switch (degree) {
-        case 1: launch_down<1>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 2: launch_down<2>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 3: launch_down<3>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 4: launch_down<4>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 5: launch_down<5>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 6: launch_down<6>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 7: launch_down<7>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 8: launch_down<8>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 9: launch_down<9>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 10: launch_down<10>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 11: launch_down<11>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 12: launch_down<12>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 13: launch_down<13>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 14: launch_down<14>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        case 15: launch_down<15>(c, ref, levels, C, lcap, vel, mixed, s); break;
-        default: launch_down<16>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 1: rc = launch_down<1>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 2: rc = launch_down<2>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 3: rc = launch_down<3>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 4: rc = launch_down<4>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 5: rc = launch_down<5>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 6: rc = launch_down<6>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 7: rc = launch_down<7>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 8: rc = launch_down<8>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 9: rc = launch_down<9>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 10: rc = launch_down<10>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 11: rc = launch_down<11>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 12: rc = launch_down<12>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 13: rc = launch_down<13>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 14: rc = launch_down<14>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        case 15: rc = launch_down<15>(c, ref, levels, C, lcap, vel, mixed, s); break;
+        default: rc = launch_down<16>(c, ref, levels, C, lcap, vel, mixed, s); break;
     }
+    if (rc) return rc;
     phase_end(c, kPhCluster, s);
     STS_LAUNCH_CHECK();
     return STS_OK;
