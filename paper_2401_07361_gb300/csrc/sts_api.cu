@@ -97,6 +97,7 @@ sts_ctx::~sts_ctx()
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
+    dual_bkt.release(); dual_bcnt.release(); dual_boff.release();
     dual_scan.release(); cfar_off.release(); cnear_off.release(); cnear_coff.release(); cfar_ent.release();
     cnear_ent.release(); ctasks.release(); cvel.release(); ccorr.release(); cdown.release(); cdown32.release();
     chas.release();

@@ -258,6 +258,8 @@ struct sts_ctx {
     sts::DevBuf<int32_t> dual_t, dual_s;    // terminal pairs sorted
     sts::DevBuf<uint32_t> dual_key, dual_ktmp;
     sts::DevBuf<int32_t> dual_perm, dual_ptmp, dual_chunk;
+    sts::DevBuf<int32_t> dual_bkt, dual_bcnt;  // per pair: bucket (kind, target key); per bucket: pairs
+    sts::DevBuf<int64_t> dual_boff;            // per bucket: first pair in the sorted order
     sts::DevBuf<int64_t> dual_cnt;       // counters of the traversal (layout in sts_tree.cu)
     sts::DevBuf<int64_t> dual_scan;      // chunk offsets of the sorted pairs
     sts::DevBuf<int64_t> cfar_off, cnear_off, cnear_coff;  // [C + 1] per target cluster slot

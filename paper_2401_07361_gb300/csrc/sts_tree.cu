@@ -1127,7 +1127,7 @@ __global__ void k_dual_level(int l, const int32_t* __restrict__ ft, const int32_
 }
 
 // After the last level: the traversal must have ended (an empty frontier), and the pairs kept
-// are the found ones up to the capacity.  Sort keys of the first pass: the source node.
+// are the found ones up to the capacity.
 __global__ void k_dual_close(int levels, int64_t tcap, int64_t* __restrict__ du, unsigned long long* __restrict__ over)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1135,28 +1135,61 @@ __global__ void k_dual_close(int levels, int64_t tcap, int64_t* __restrict__ du,
     du[kDuP] = min(du[kDuTerms], tcap);
 }
 
-__global__ void k_dual_keys_src(const int32_t* __restrict__ ts, const int64_t* __restrict__ du, int64_t cap,
-                                uint32_t* __restrict__ key, int32_t* __restrict__ perm)
+// The pairs are put in the order of the lists, (kind, target key, source node), by a counting
+// sort on the bucket (kind, target key) followed by ranking within each bucket: the target key
+// is the depth-first leaf index of a leaf target and the cluster slot of a cluster target, and
+// the sources of one target are distinct (ties would go by the pair's index).  Buckets are
+// small (the pairs of one target), so the ranking is a count over the bucket.
+__global__ void k_dual_bucket(const int32_t* __restrict__ tt, const uint8_t* __restrict__ tk,
+                              const int64_t* __restrict__ du, int64_t cap, int64_t KT,
+                              const int32_t* __restrict__ start, const int32_t* __restrict__ slot_leaf,
+                              const int32_t* __restrict__ cluster_slot, int32_t* __restrict__ bucket,
+                              int32_t* __restrict__ bcnt, int32_t* __restrict__ arrive)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= min(du[kDuP], cap)) return;
-    key[i] = (uint32_t)ts[i];
-    perm[i] = (int32_t)i;
+    const int32_t t = tt[i];
+    const int k = tk[i];
+    const int64_t tkey = leaf_kind(k) ? slot_leaf[start[t]] : cluster_slot[t];
+    const int32_t b = (int32_t)(k * KT + tkey);
+    bucket[i] = b;
+    arrive[i] = atomicAdd(bcnt + b, 1);
 }
 
-// Second pass keys: kind << bits_t | target key (depth-first leaf index of a leaf target,
-// cluster slot of a cluster target).
-__global__ void k_dual_keys_tgt(const int32_t* __restrict__ tt, const uint8_t* __restrict__ tk,
-                                const int32_t* __restrict__ perm, const int64_t* __restrict__ du, int64_t cap,
-                                int bits_t, const int32_t* __restrict__ start, const int32_t* __restrict__ slot_leaf,
-                                const int32_t* __restrict__ cluster_slot, uint32_t* __restrict__ key)
+// Each pair at its arrival slot in its bucket: its source and index, for the ranking.
+__global__ void k_dual_scatter(const int64_t* __restrict__ du, int64_t cap, const int32_t* __restrict__ bucket,
+                               const int32_t* __restrict__ arrive, const int64_t* __restrict__ boff,
+                               const int32_t* __restrict__ ts, uint32_t* __restrict__ bsrc, int32_t* __restrict__ bidx)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= min(du[kDuP], cap)) return;
-    const int32_t q = perm[i], t = tt[q];
-    const int k = tk[q];
-    const uint32_t tkey = (uint32_t)(leaf_kind(k) ? slot_leaf[start[t]] : cluster_slot[t]);
-    key[i] = ((uint32_t)k << bits_t) | tkey;
+    const int64_t q = boff[bucket[i]] + arrive[i];
+    bsrc[q] = (uint32_t)ts[i];
+    bidx[q] = (int32_t)i;
+}
+
+// The pair's place in the sorted order: its bucket's start plus the number of pairs of the
+// bucket before it by (source, index); key = kind << bits_t | target key, perm = pair index.
+__global__ void k_dual_rank(const int64_t* __restrict__ du, int64_t cap, int64_t KT, int bits_t,
+                            const int32_t* __restrict__ bucket, const int64_t* __restrict__ boff,
+                            const int32_t* __restrict__ bcnt, const int32_t* __restrict__ ts,
+                            const uint32_t* __restrict__ bsrc, const int32_t* __restrict__ bidx,
+                            uint32_t* __restrict__ key, int32_t* __restrict__ perm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= min(du[kDuP], cap)) return;
+    const int32_t b = bucket[i];
+    const int64_t lo = boff[b];
+    const int n = bcnt[b];
+    const uint32_t s = (uint32_t)ts[i];
+    int r = 0;
+    for (int j = 0; j < n; j++) {
+        const uint32_t sj = bsrc[lo + j];
+        r += (sj < s || (sj == s && bidx[lo + j] < (int32_t)i)) ? 1 : 0;
+    }
+    const int64_t kind = b / KT;
+    key[lo + r] = ((uint32_t)kind << bits_t) | (uint32_t)(b - kind * KT);
+    perm[lo + r] = (int32_t)i;
 }
 
 // Sorted pairs, and the near chunks of every pair (0 for far kinds).
@@ -1707,10 +1740,11 @@ static int reserve_dual(sts_ctx* c, const DualCaps& k, int64_t L, int64_t C, int
     STS_CUDA(c->dual_ptmp.reserve(k.terms));
     STS_CUDA(c->dual_chunk.reserve(k.terms));
     STS_CUDA(c->dual_scan.reserve(k.terms + 1));
-    const int64_t hs = radix_hist_size(k.terms);
-    STS_CUDA(c->hist.reserve(hs));
-    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(k.terms + 1) + scan_scratch(nodes + 1) +
-                                 64));
+    const int64_t KT = std::max<int64_t>(std::max(L, C), 1);
+    STS_CUDA(c->dual_bkt.reserve(k.terms));
+    STS_CUDA(c->dual_bcnt.reserve(4 * KT + 1));
+    STS_CUDA(c->dual_boff.reserve(4 * KT + 2));
+    STS_CUDA(c->scan_tmp.reserve(scan_scratch(4 * KT + 1) + scan_scratch(k.terms + 1) + scan_scratch(nodes + 1) + 64));
     STS_CUDA(c->far_off.reserve(L + 1));
     STS_CUDA(c->near_off.reserve(L + 1));
     STS_CUDA(c->near_coff.reserve(L + 1));
@@ -1751,20 +1785,22 @@ static int launch_dual(sts_ctx* c, double theta, int levels, int64_t L, int64_t 
          note_launch());
     }
     (k_dual_close<<<1, 32, 0, s>>>(levels, tcap, du, over), note_launch());
-    // sort by (kind, target key, source): stable passes on the source, then on kind | target
-    const int bits_t = bits_for(std::max<int64_t>(std::max(L, C), 1));
-    const int bits_n = bits_for(std::max<int64_t>(nodes, 1));
-    const int64_t hs = radix_hist_size(tcap);
-    int64_t* scan_out = c->scan_tmp.p;
-    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
+    // sort by (kind, target key, source): counting sort on (kind, target key), then the rank
+    // of each pair within its bucket by source
+    const int64_t KT = std::max<int64_t>(std::max(L, C), 1);
+    const int bits_t = bits_for(KT);
     const unsigned gt = blocks(tcap, T);
-    (k_dual_keys_src<<<gt, T, 0, s>>>(c->dual_ts.p, du, tcap, c->dual_key.p, c->dual_perm.p), note_launch());
-    radix_sort_pairs(c->dual_key.p, c->dual_perm.p, c->dual_ktmp.p, c->dual_ptmp.p, tcap, bits_n, c->hist.p, scan_out,
-                     scan_scr, s, du + kDuP);
-    (k_dual_keys_tgt<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_tk.p, c->dual_perm.p, du, tcap, bits_t, c->nd_start.p,
-                                      c->slot_leaf.p, c->cluster_slot.p, c->dual_key.p), note_launch());
-    radix_sort_pairs(c->dual_key.p, c->dual_perm.p, c->dual_ktmp.p, c->dual_ptmp.p, tcap, bits_t + 2, c->hist.p,
-                     scan_out, scan_scr, s, du + kDuP);
+    STS_CUDA(cudaMemsetAsync(c->dual_bcnt.p, 0, 4 * KT * sizeof(int32_t), s));
+    (k_dual_bucket<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_tk.p, du, tcap, KT, c->nd_start.p, c->slot_leaf.p,
+                                    c->cluster_slot.p, c->dual_bkt.p, c->dual_bcnt.p, c->dual_ptmp.p),
+     note_launch());
+    exclusive_scan_i32(c->dual_bcnt.p, c->dual_boff.p, 4 * KT, c->scan_tmp.p, s);
+    (k_dual_scatter<<<gt, T, 0, s>>>(du, tcap, c->dual_bkt.p, c->dual_ptmp.p, c->dual_boff.p, c->dual_ts.p,
+                                     c->dual_ktmp.p, c->dual_chunk.p),
+     note_launch());
+    (k_dual_rank<<<gt, T, 0, s>>>(du, tcap, KT, bits_t, c->dual_bkt.p, c->dual_boff.p, c->dual_bcnt.p, c->dual_ts.p,
+                                  c->dual_ktmp.p, c->dual_chunk.p, c->dual_key.p, c->dual_perm.p),
+     note_launch());
     (k_dual_gather<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_ts.p, c->dual_perm.p, c->dual_key.p, bits_t, du, tcap,
                                     c->nd_count.p, c->dual_t.p, c->dual_s.p, c->dual_chunk.p), note_launch());
     exclusive_scan_i32(c->dual_chunk.p, c->dual_scan.p, tcap, c->scan_tmp.p, s, du + kDuP);
