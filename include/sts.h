@@ -196,8 +196,9 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
  * velocity is -(1/4 pi) x x S) at the target cluster's proxy points; the polynomial of degree
  * d interpolating it over the cluster (solve V_T c = U_T, V_T[m][k] = B_k(b(x~_m))) is
  * evaluated at every particle x below it, and -(1/4 pi) x x (that value) is added, so the
- * velocity stays tangent to the sphere.  Uses p->theta, p->degree, p->precision and p->near_fp64_tau (mixed precision: the
- * pair sums in FP32 as in sts_velocity, the interpolation in FP64).  Builds the pair lists when
+ * velocity stays tangent to the sphere.  Uses p->theta, p->degree, p->precision and
+ * p->near_fp64_tau.  Mixed precision: the pair sums in FP32 as in sts_velocity, the
+ * coefficients c in FP64, rounded to FP32 for the evaluation at the particles.  Builds the pair lists when
  * theta or the tree changed (synchronises `stream` once), which replaces the lists of
  * sts_velocity (the next sts_velocity rebuilds them).  STS_ERR_STATE without a tree. */
 int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
