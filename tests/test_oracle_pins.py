@@ -152,6 +152,20 @@ def test_real_sh_orthonormal():
     assert np.max(np.abs(G - np.eye(len(keys)))) < 1e-12
 
 
+def test_sh_series_independent_of_chunking():
+    """The harmonic-series inputs are made in cache-sized chunks of points; every value is an
+    elementwise expression, so the result must not depend on the chunk (bit for bit), and the
+    series must equal the sum of its terms built from the table."""
+    pos = W.uniform_points(5001, seed=11)
+    whole = W.sh_series_vorticity(pos, 8, seed=3, chunk=1 << 40)
+    for chunk in (1, 7, 1000, 1 << 16):
+        assert np.array_equal(W.sh_series_vorticity(pos, 8, seed=3, chunk=chunk), whole), chunk
+    Y = W.real_sh_table(pos, 8)
+    c = W.sh_coefficients(8, 3)
+    ref = sum(c[k] * Y[k] for k in Y if k[0] >= 1)
+    assert np.max(np.abs(whole - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
 # ---------------------------------------------------------------------------------- tree
 def test_icosahedron_is_regular_and_oriented():
     V, F = O.icosahedron()
