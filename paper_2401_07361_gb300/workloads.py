@@ -212,9 +212,12 @@ def sh_coefficients(lmax: int, seed: int):
 
 
 def sh_series_vorticity(pos: np.ndarray, lmax: int, seed: int = 0, chunk: int = 1 << 16) -> np.ndarray:
-    """Random zero-mean vorticity sum_{l=1..lmax} sum_m c_lm Y_lm with c_lm ~ N(0,1)/l.  The
-    points are taken in chunks that stay in cache; every value is computed elementwise in the
-    same order whatever the chunk, so the result does not depend on it."""
+    """Random vorticity sum_{l=1..lmax} sum_m c_lm Y_lm with c_lm ~ N(0,1)/l.  With no l = 0
+    term its integral over the sphere is zero (the zero total circulation of Sec. 2); the
+    discrete circulation sum_j zeta_j A_j of a point set is that integral's quadrature error
+    and is left as it is.  The points are taken in chunks that stay in cache; every value is
+    computed elementwise in the same order whatever the chunk, so the result does not depend
+    on it."""
     coef = sh_coefficients(lmax, seed)
     pos = np.asarray(pos, dtype=np.float64)
     zeta = np.zeros(pos.shape[0])
