@@ -137,9 +137,12 @@ int sts_direct_targets(sts_ctx* ctx, const double* pos, const double* zeta,
  * scratch is one fixed device array of about 7.4 MB inside the library, held on every GPU
  * that loads the library until the process exits.  n is limited to 65536 (larger n returns
  * STS_ERR_CAPACITY without touching the GPU).  The first call on a device looks up that
- * array's device address, so make it before any stream capture.  All calls share the
- * array: calls that overlap on the GPU race; order them on one stream.  Results equal
- * sts_direct's for the same inputs and precision. */
+ * array's device address, so make it before any stream capture; the address is then kept
+ * for the life of the process, so after a cudaDeviceReset (or any other teardown of the
+ * device's primary context) this entry point must not be called again in that process.
+ * All calls share the array: calls that overlap on the GPU race; order them on one stream.
+ * Results equal sts_direct's bit for bit for the same inputs and precision (same source
+ * split, same kernels). */
 int sts_direct_noalloc(const double* pos, const double* zeta, const double* area, int64_t n,
                        int32_t precision, double* vel, void* stream);
 

@@ -9,14 +9,16 @@
 // Evaluation layout: one warp per task (up to 64 consecutive targets of one leaf, two per
 // lane); S = 1..8 lanes share a pair of targets and split its sources, summed with shuffles at
 // the end.  Persistent CTAs take the tasks from a device queue.  Consecutive source blocks (a
-// cluster's M proxy points, a chunk of a near leaf's particles) are staged as a group in one
-// of two shared-memory stages by TMA bulk copies against the stage's mbarrier, padded to a
-// multiple of 4 S entries; each lane then streams the stage with broadcast shared-memory reads.
+// cluster's M proxy points, a chunk of a near leaf's particles) of one kind are staged back
+// to back as a group in one of two shared-memory stages by TMA bulk copies against the
+// stage's mbarrier; one pass then moves every source into the task leaf's frame, the group is
+// padded once to a multiple of 4 S entries, and each lane streams the whole stage with
+// broadcast shared-memory reads.
 //
 // Mixed precision (STS_MIXED): targets, sources and proxy points are stored in FP32
 // relative to the circumcentre of their own leaf or cluster; the FP32 offset between the two
-// centres (rounded once from FP64 per list entry) is folded into the two targets once per
-// block, so that d keeps FP32 relative accuracy at every distance the tree produces.  Per
+// centres (rounded once from FP64 per list entry) is added to the staged sources, so that
+// d = (y + delta) - x keeps FP32 relative accuracy at every distance the tree produces.  Per
 // group the lane sums in FP32, and the group partials go into a TwoSum-compensated
 // accumulator.  Near pairs
 // with |d|^2 / 2 < tau are evaluated in FP64 from the FP64 positions instead.  A zero d
@@ -163,8 +165,9 @@ __device__ __forceinline__ float sqdist(const float4 s, float ax, float ay, floa
     return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, kEps)));
 }
 
-// The FP32 pair loop of one block for a lane's two targets: entries ph, ph + S, ... of a block
-// padded to a multiple of 4 S (padding entries carry w = 0 far away), four per trip.  TEST:
+// The FP32 pair loop of one staged group for a lane's two targets: entries ph, ph + S, ... of
+// the group padded to a multiple of 4 S (padding entries carry w = 0 far away), four per trip.
+// TEST:
 // pairs with |d|^2 < 2 tau contribute nothing here and set `hit`; the caller then evaluates
 // them in FP64.
 template <bool TEST, int S>
@@ -198,8 +201,9 @@ __device__ __forceinline__ void block_pairs(const float4* sb, int cntp, int ph, 
     }
 }
 
-// Second pass over a tested block for a lane that hit: the same FP32 squared distances pick
-// the same pairs, which are evaluated in FP64 from the FP64 positions.
+// Second pass over a tested block for a lane that hit (its entries ph, ph + S, ...; slot
+// base + i): the same FP32 squared distances pick the same pairs, which are evaluated in FP64
+// from the FP64 positions.
 template <int S>
 __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int ph, float ax, float ay, float az,
                                                   float bx, float by, float bz, float tau2, int64_t base,
@@ -214,9 +218,20 @@ __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int
 }
 
 // ------------------------------------------------------------------------ mixed tree
-constexpr int kStagePad = kStage + 32;  // one stage: a group of padded blocks
+// A group: consecutive blocks of one kind (untested, or near blocks tested for close pairs)
+// with at most kGroupMax sources in all, staged back to back and padded once, at its end, to
+// a multiple of 4 S entries (at most 31 more).
+// Groups of up to 352 sources (two 384-entry stages, 12 KB, per warp) at two CTAs of 8
+// warps per SM: measured at 655k targets, 2.37 ms against 2.41 ms for 192-source groups at
+// three CTAs per SM (the per-group work is amortised over twice the pairs; occupancy 16 warps).
+#ifndef STS_GROUP_MAX
+#define STS_GROUP_MAX 352
+#endif
+constexpr int kGroupMax = STS_GROUP_MAX;
+constexpr int kStagePad = kGroupMax + 32;
+static_assert(kStage <= kGroupMax, "one proxy block or near chunk must fit a group");
 #ifndef STS_EVAL_MIN_BLOCKS
-#define STS_EVAL_MIN_BLOCKS 3  // resident blocks per SM asked of the register allocator
+#define STS_EVAL_MIN_BLOCKS 2  // resident blocks per SM asked of the register allocator
 #endif
 constexpr int kRing = 64;               // block descriptors per warp: two windows of 32
 
@@ -224,27 +239,32 @@ constexpr int kRing = 64;               // block descriptors per warp: two windo
 struct EvalSmem {
     float4 stage[2][kStagePad];
     float4 off[kRing];  // source offset (dx, dy, dz) of the block
-    int4 info[kRing];   // first source (slot or cluster), count, kind, padded start in its window
+    int4 info[kRing];   // first source (slot or cluster), count, kind (0 far, 1 near, 2 tested near),
+                        // start of the block within its window (sum of the counts before it)
     uint64_t bar[2];    // mbarriers of the two stages
 };
 
-// A group of consecutive blocks staged together: [e0, e1) of the task's list, whose padded
-// counts (multiples of 4 S) add up to at most one stage; base = padded start of e0.
 struct Group {
-    int e0, e1, base;
+    int e0, e1;  // ring positions [e0, e1)
+    int base;    // window start of e0
+    int cnt;     // sources of the group
+    bool tested;
 };
 
-// Loads the descriptors of list blocks [wb, wb + 32) into the ring (lane j: block wb + j) and
-// returns the lane's inclusive prefix of padded counts within the window.
-template <int S>
+// Loads the descriptors of list blocks [wb, wb + 32) into the ring at positions wb .. wb + 31:
+// the untested blocks first, then the near blocks whose gap bound is below tau_r (the ones
+// tested for close pairs), each part in list order, so that a window holds at most two runs of
+// one kind.  Returns the inclusive prefix of the counts at the lane's position and sets the
+// position's tested flag.
 __device__ __forceinline__ int load_window(EvalSmem& sm, int wb, int lane, int nf, int nbt,
                                            const FarEntry* __restrict__ fe, const NearEntry* __restrict__ ne,
-                                           int M, float tau_r)
+                                           int M, float tau_r, bool& tested)
 {
     const int e = wb + lane;
+    const bool valid = e < nbt;
     int idx = 0, cnt = 0, kind = 0;
     float dx = 0.f, dy = 0.f, dz = 0.f;
-    if (e < nbt) {
+    if (valid) {
         if (e < nf) {
             const FarEntry f = fe[e];
             idx = f.slot;
@@ -262,69 +282,82 @@ __device__ __forceinline__ int load_window(EvalSmem& sm, int wb, int lane, int n
             kind = q.gap < tau_r ? 2 : 1;
         }
     }
-    const int pc = (cnt + 4 * S - 1) / (4 * S) * (4 * S);
-    int inc = pc;
+    const unsigned um = __ballot_sync(kFull, valid && kind != 2);
+    const unsigned tm = __ballot_sync(kFull, valid && kind == 2);
+    const unsigned lt = (1u << lane) - 1u;
+    // invalid lanes are the top ones (e >= nbt) and keep their positions
+    const int pos = !valid ? lane : (kind == 2 ? __popc(um) + __popc(tm & lt) : __popc(um & lt));
+    const int r = (wb + pos) & (kRing - 1);
+    sm.off[r] = make_float4(dx, dy, dz, 0.f);
+    sm.info[r] = make_int4(idx, cnt, kind, 0);
+    __syncwarp();
+    const int me = (wb + lane) & (kRing - 1);
+    const int c = sm.info[me].y;
+    tested = sm.info[me].z == 2;
+    int inc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc += v;
     }
-    sm.off[e & (kRing - 1)] = make_float4(dx, dy, dz, 0.f);
-    sm.info[e & (kRing - 1)] = make_int4(idx, cnt, kind, inc - pc);
+    sm.info[me].w = inc - c;
     __syncwarp();
     return inc;
 }
 
-// The largest group of consecutive blocks from e0 on that fits one stage; loads the next window
-// of descriptors when e0 starts it.  An empty group (e0 == e1) ends the task.
-template <int S>
-__device__ __forceinline__ Group form_group(EvalSmem& sm, int e0, int& wb, int& winc, int lane, int nf, int nbt,
-                                            const FarEntry* __restrict__ fe, const NearEntry* __restrict__ ne,
-                                            int M, float tau_r)
+// The largest run of blocks of one kind from ring position e0 on, within e0's window, whose
+// sources fit one group; loads the next window when e0 starts it.  An empty group (e0 == e1)
+// ends the task.
+__device__ __forceinline__ Group form_group(EvalSmem& sm, int e0, int& wb, int& winc, bool& wtest, int lane, int nf,
+                                            int nbt, const FarEntry* __restrict__ fe,
+                                            const NearEntry* __restrict__ ne, int M, float tau_r)
 {
     Group g;
     g.e0 = g.e1 = e0;
-    g.base = 0;
+    g.base = g.cnt = 0;
+    g.tested = false;
     if (e0 >= nbt) return g;
     if (e0 >= wb + 32) {
         wb += 32;
-        winc = load_window<S>(sm, wb, lane, nf, nbt, fe, ne, M, tau_r);
+        winc = load_window(sm, wb, lane, nf, nbt, fe, ne, M, tau_r, wtest);
     }
     const int r = e0 - wb;
     const int prev = __shfl_sync(kFull, winc, (r + 31) & 31);
     g.base = r > 0 ? prev : 0;
-    const bool in = lane >= r && wb + lane < nbt && winc - g.base <= kStagePad;
-    g.e1 = e0 + __popc(__ballot_sync(kFull, in));
+    g.tested = __shfl_sync(kFull, (int)wtest, r) != 0;
+    const unsigned other = __ballot_sync(kFull, lane >= r && wtest != g.tested);
+    const int end = other ? __ffs(other) - 1 : 32;
+    const bool in = lane >= r && lane < end && wb + lane < nbt && winc - g.base <= kGroupMax;
+    const int k = __popc(__ballot_sync(kFull, in));
+    g.e1 = e0 + k;
+    g.cnt = __shfl_sync(kFull, winc, r + k - 1) - g.base;
     return g;
 }
 
-// Copies the blocks of a group into a stage: one bulk copy per block (each at its padded start,
-// issued by its own lane) against the stage's mbarrier, and pads each block with zero-weight
-// entries far from every target up to a multiple of 4 S.
+// Copies the blocks of a group into a stage, back to back: one bulk copy per block, issued by
+// its own lane, against the stage's mbarrier (lane 0 arms it with the group's byte count; a
+// copy that lands first leaves the count transiently negative, which the barrier allows), and
+// pads the group with zero-weight entries far from every target up to a multiple of 4 S.
 template <int S>
-__device__ __forceinline__ void issue_group(EvalSmem& sm, const Group& g, int stg, int lane, int nf,
+__device__ __forceinline__ void issue_group(EvalSmem& sm, const Group& g, int stg, int lane,
                                             const float4* __restrict__ prx32, const float4* __restrict__ src32,
                                             int M)
 {
     if (g.e1 == g.e0) return;
     float4* st = sm.stage[stg];
-    // lane k copies block e0 + k; lane 0 arms the barrier with the group's byte count (a copy
-    // that lands first leaves the count transiently negative, which the barrier allows)
+    // the stage's earlier generic reads and writes (two groups ago) come before the copies
+    fence_proxy_async();
+    __syncwarp();
     const int e = g.e0 + lane;
-    int cnt = 0;
+    int bytes = 0;
     if (e < g.e1) {
         const int4 in = sm.info[e & (kRing - 1)];
-        cnt = in.y;
-        const float4* src = e < nf ? prx32 + (int64_t)in.x * M : src32 + in.x;
-        fence_proxy_async();  // the stage's earlier reads and writes come before the copies
-        if (cnt > 0) bulk_g2s(st + (in.w - g.base), src, 16u * (unsigned)cnt, &sm.bar[stg]);
+        const float4* src = in.z == 0 ? prx32 + (int64_t)in.x * M : src32 + in.x;
+        bytes = 16 * in.y;
+        if (in.y > 0) bulk_g2s(st + (in.w - g.base), src, (unsigned)bytes, &sm.bar[stg]);
     }
-    for (int f = g.e0; f < g.e1; f++) {
-        const int4 in = sm.info[f & (kRing - 1)];
-        const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
-        if (in.y + lane < cntp) st[in.w - g.base + in.y + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
-    }
-    int bytes = 16 * cnt;
+    const int gp = (g.cnt + 4 * S - 1) / (4 * S) * (4 * S);
+    if (g.cnt + lane < gp) st[g.cnt + lane] = make_float4(1e3f, 1e3f, 1e3f, 0.f);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(kFull, bytes, o);
     if (lane == 0) mbar_arrive_expect_tx(&sm.bar[stg], (unsigned)bytes);
@@ -365,13 +398,14 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
     const NearEntry* ne = near_ent + co;
 
     int wb = 0;
-    int winc = load_window<S>(sm, 0, lane, nf, nbt, fe, ne, M, tau_r);
-    Group cur = form_group<S>(sm, 0, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
-    issue_group<S>(sm, cur, 0, lane, nf, prx32, src32, M);
-    Group nxt = form_group<S>(sm, cur.e1, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
+    bool wtest = false;
+    int winc = load_window(sm, 0, lane, nf, nbt, fe, ne, M, tau_r, wtest);
+    Group cur = form_group(sm, 0, wb, winc, wtest, lane, nf, nbt, fe, ne, M, tau_r);
+    issue_group<S>(sm, cur, 0, lane, prx32, src32, M);
+    Group nxt = form_group(sm, cur.e1, wb, winc, wtest, lane, nf, nbt, fe, ne, M, tau_r);
     for (int b = 0; cur.e1 > cur.e0; b++) {
         const int stg = b & 1;
-        issue_group<S>(sm, nxt, stg ^ 1, lane, nf, prx32, src32, M);
+        issue_group<S>(sm, nxt, stg ^ 1, lane, prx32, src32, M);
         if (!mbar_wait(&sm.bar[stg], (par >> stg) & 1u)) {
             if (lane == 0) atomicOr(status, kStatusTimeout);
             if (nxt.e1 > nxt.e0) mbar_wait(&sm.bar[stg ^ 1], (par >> (stg ^ 1)) & 1u);
@@ -379,26 +413,42 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
             return false;
         }
         par ^= 1u << stg;
-        __syncwarp();  // the padding written by the other lanes
-        const float4* st = sm.stage[stg];
-        float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
-        for (int e = cur.e0; e < cur.e1; e++) {
-            const float4 o = sm.off[e & (kRing - 1)];
-            const int4 in = sm.info[e & (kRing - 1)];
-            const float4* sb = st + (in.w - cur.base);
-            const int cntp = (in.y + 4 * S - 1) / (4 * S) * (4 * S);
-            // the source offset is folded into the targets: (y + delta) - x = y - (x - delta)
-            const float ax = t0x - o.x, ay = t0y - o.y, az = t0z - o.z;
-            const float bx = t1x - o.x, by = t1y - o.y, bz = t1z - o.z;
-            bool hit = false;
-            if (in.z == 2) {
-                block_pairs<true, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
-                if (hit)
-                    block_close_pairs<S>(sb, in.y, ph, ax, ay, az, bx, by, bz, tau2, in.x, tk0, tk1, src64, tgt64,
-                                         corr);
-            } else {
-                block_pairs<false, S>(sb, cntp, ph, ax, ay, az, bx, by, bz, p0x, p0y, p0z, p1x, p1y, p1z, tau2, hit);
+        float4* st = sm.stage[stg];
+        // every source moves into the task leaf's frame: y + delta, delta = c_source - c_leaf
+        // (FP32, rounded once per list entry), so that d = (y + delta) - x over the whole group
+        for (int f = cur.e0; f < cur.e1; f++) {
+            const int4 in = sm.info[f & (kRing - 1)];
+            const float4 o = sm.off[f & (kRing - 1)];
+            float4* sb = st + (in.w - cur.base);
+            for (int k = lane; k < in.y; k += 32) {
+                float4 v = sb[k];
+                v.x += o.x;
+                v.y += o.y;
+                v.z += o.z;
+                sb[k] = v;
             }
+        }
+        __syncwarp();  // the moved sources and the padding written by the other lanes
+        const int gp = (cur.cnt + 4 * S - 1) / (4 * S) * (4 * S);
+        float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
+        bool hit = false;
+        if (cur.tested) {
+            block_pairs<true, S>(st, gp, ph, t0x, t0y, t0z, t1x, t1y, t1z, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
+                                 hit);
+            if (hit) {
+                // the pairs left out above, in FP64; stage entry q belongs to phase q mod S
+                for (int f = cur.e0; f < cur.e1; f++) {
+                    const int4 in = sm.info[f & (kRing - 1)];
+                    const int b0 = in.w - cur.base;
+                    int i0 = (ph - b0) % S;
+                    if (i0 < 0) i0 += S;
+                    block_close_pairs<S>(st + b0, in.y, i0, t0x, t0y, t0z, t1x, t1y, t1z, tau2, in.x, tk0, tk1,
+                                         src64, tgt64, corr);
+                }
+            }
+        } else {
+            block_pairs<false, S>(st, gp, ph, t0x, t0y, t0z, t1x, t1y, t1z, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
+                                  hit);
         }
         two_sum_add(h0x, l0x, p0x);
         two_sum_add(h0y, l0y, p0y);
@@ -408,7 +458,7 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
         two_sum_add(h1z, l1z, p1z);
         __syncwarp();
         cur = nxt;
-        nxt = form_group<S>(sm, cur.e1, wb, winc, lane, nf, nbt, fe, ne, M, tau_r);
+        nxt = form_group(sm, cur.e1, wb, winc, wtest, lane, nf, nbt, fe, ne, M, tau_r);
     }
     double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
                    (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};

@@ -1,8 +1,10 @@
 """sts_direct_noalloc: the direct sum for callers that cannot allocate device memory
 (inside someone else's graph capture, under another allocator, or in a loop that must not
 enter cudaMalloc).  It is called here straight through the C ABI and checked against the
-allocating entry point sts_direct, within the tolerances the parity tests use, on two calls
-in a row with different inputs: the shared fixed scratch must not carry anything over."""
+allocating entry point sts_direct on two calls in a row with different inputs: the shared
+fixed scratch must not carry anything over.  Both entry points split the sources the same
+way and run the same kernels, so the results are compared bit for bit (and, redundantly,
+within the tolerances the parity tests use)."""
 import ctypes as C
 import math
 
@@ -46,6 +48,7 @@ def test_noalloc_direct_matches_allocating_direct_twice(prec, tol):
             got = _noalloc(lib, pos, zeta, area, prec)
             ref = sts.sts_direct(ctx.h, pos, zeta, area, prec).cpu().numpy()
             assert np.all(np.isfinite(got))
+            assert np.array_equal(got, ref), (n, np.max(np.abs(got - ref)))
             a = area.cpu().numpy()
             err = np.sqrt(np.sum(np.sum((got - ref) ** 2, 1) * a) / np.sum(np.sum(ref ** 2, 1) * a))
             assert err <= tol, (n, err)
