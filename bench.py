@@ -66,6 +66,10 @@ def parse(argv=None):
                          "(Appendix A; level-5 icosahedral mesh, eps1 0.0025, eps2 0.2, dt 0.01 day)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every kernel from the host instead of replaying the recorded step")
+    ap.add_argument("--shard", action="store_true",
+                    help="one instance spread over the ranks (strong scaling): every rank builds the tree, "
+                         "evaluates a range of target leaves balanced by interaction counts, and the ranks "
+                         "all-gather the velocities (NCCL)")
     ap.add_argument("--profile", action="store_true",
                     help="timed device steps only (no e2e, FP64 or CPU legs): the command profiled by ncu")
     return ap.parse_args(argv)
@@ -542,10 +546,94 @@ def run_potential(args):
     return 0
 
 
+def run_shard(args):
+    """One tree-code velocity of the workload spread over the job's ranks: a step is the tree
+    build (every rank), the rank's leaf range and the all-gather of the velocities, so the
+    work per step is fixed as ranks are added (strong scaling)."""
+    import numpy as np
+    import torch
+
+    from paper_2401_07361_gb300 import shard, sts
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    wl = load_workload(args.workload)
+    if "offsets" in wl:
+        raise SystemExit("--shard takes a single-instance workload")
+    n = len(wl["pos"])
+    leaf = args.leaf or wl["leaf_size"]
+    p = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_MIXED,
+                   near_fp64_tau=args.tau_c * 4.0 * math.pi / n)
+    pos, zeta, area = (torch.from_numpy(wl[k]).to(dev) for k in ("pos", "zeta", "area"))
+    vel = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = sts.Context()
+
+    def step():
+        sts.sts_tree_build(ctx.h, pos, p)
+        shard.sharded_velocity(ctx.h, zeta, area, p, rank, ws, vel=vel)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = sts.sts_launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = sts.sts_launch_count() - l0
+    total_ms = max_over_ranks(sum(times), ws, dev)
+    got = vel.cpu().numpy()
+    full = sts.sts_velocity(ctx.h, zeta, area, p).cpu().numpy()
+    a = wl["area"]
+    err = float(np.sqrt(np.sum(np.sum((got - full) ** 2, 1) * a) / np.sum(np.sum(full**2, 1) * a)))
+    parts = shard.partition(sts.sts_leaf_work(ctx.h, args.degree), ws)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n * args.steps / (total_ms / 1e3), "unit": "targets/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / max(1, args.steps),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree,
+                       "leaf_size": leaf, "precision": "mixed", "parallelism": f"leaf-range shards x{ws}",
+                       "launch": "host launches", "l2": "flushed between timed steps (256 MiB write)"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "shards": [{"leaves": [lo, hi]} for lo, hi in parts],
+            "error": {"sharded_vs_one_gpu_rel_l2": err},
+        }), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.shard:
+        return run_shard(args)
     if args.amr > 0:
         return run_amr(args)
     if args.rk4 > 0:

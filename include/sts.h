@@ -207,6 +207,42 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
 int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
                       double* vel, void* stream);
 
+/* One GPU's share of a sharded tree-code velocity (Sec. 4.1 spreads the same convolution over
+ * MPI ranks; here each GPU builds the whole tree and evaluates a contiguous range of target
+ * leaves).  Evaluates sts_velocity's PC + PP sums (Sec. 3.3, lists of Sec. 3.4; same sources,
+ * proxy weights, lists and arithmetic, so every row written is bit-identical to
+ * sts_velocity's) for the targets of depth-first leaves [leaf_begin, leaf_end) only, 0 <=
+ * leaf_begin <= leaf_end <= the tree's leaf count (sts_tree_info info[2]).  out_sorted = 0:
+ * rows vel[i,3] in the caller's order, rows of other targets left untouched; out_sorted = 1:
+ * vel[(slot_end - slot_begin), 3], row r = the target in sorted slot slot_begin + r
+ * (sts_leaf_range), the compact block that GPUs all-gather and sts_unpermute puts back in
+ * order.  Uses the target-leaf lists only (STS_ERR_STATE after sts_set_traversal(ctx, 1) or
+ * while recording); builds the lists when theta or the tree changed (an empty range with
+ * vel = NULL only builds them).  Synchronises `stream` (it reads the leaf count, and the slot
+ * range when out_sorted = 1). */
+int sts_velocity_range(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
+                       int64_t leaf_begin, int64_t leaf_end, int32_t out_sorted, double* vel,
+                       void* stream);
+
+/* Work of each depth-first target leaf under the current target-leaf lists: work[nleaves]
+ * (HOST int64 array, nleaves = sts_tree_info info[2]) = the leaf's targets x (its far
+ * clusters x M + the particles of its near leaves), i.e. its PC + PP interactions at degree
+ * `degree` (M = (d + 1)(d + 2) / 2), the cost a partition of the leaves between GPUs
+ * balances.  STS_ERR_STATE without lists (call sts_velocity or sts_velocity_range first).
+ * Synchronises `stream`. */
+int sts_leaf_work(sts_ctx* ctx, int32_t degree, int64_t* work, void* stream);
+
+/* The sorted slots [*slot_begin, *slot_end) holding the targets of depth-first leaves
+ * [leaf_begin, leaf_end) (leaves own consecutive slots in depth-first order).  Synchronises
+ * `stream`.  STS_ERR_ARG for a range outside [0, leaf count]. */
+int sts_leaf_range(sts_ctx* ctx, int64_t leaf_begin, int64_t leaf_end, int64_t* slot_begin,
+                   int64_t* slot_end, void* stream);
+
+/* Puts rows in sorted slot order back into the caller's order: vel[perm[t], :] =
+ * vel_sorted[t, :] for t < n (device arrays [n,3]; perm the current tree's slot -> particle
+ * map).  Asynchronous on `stream`.  STS_ERR_STATE without a tree. */
+int sts_unpermute(sts_ctx* ctx, const double* vel_sorted, double* vel, void* stream);
+
 /* One classical RK4 step (Sec. 4) of the Sec. 2 system dx_i/dt = u_i,
  * dzeta_i/dt = -2 Omega u_z,i, in place on pos[n,3] and zeta[n]; area[n] is constant.
  * Every stage evaluates the tree-code velocity (parameters p, tree rebuilt) at the stage

@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
@@ -641,6 +641,34 @@ int copy_out(H* host, const D* dev, int64_t n, cudaStream_t s)
     return STS_OK;
 }
 
+// Sorted slots [slot_lo, slot_hi) of the targets of depth-first leaves [leaf_lo, leaf_hi)
+// (leaves hold consecutive slots in depth-first order); synchronises `s`.
+int leaf_range_slots(sts_ctx* c, int64_t leaf_lo, int64_t leaf_hi, int64_t* slot_lo, int64_t* slot_hi,
+                     cudaStream_t s)
+{
+    *slot_lo = *slot_hi = 0;
+    if (leaf_hi <= leaf_lo) {
+        if (leaf_lo < c->nleaves) {
+            int32_t node = 0, st = 0;
+            int rc = copy_out(&node, c->leaves.p + leaf_lo, 1, s);
+            if (rc || (rc = copy_out(&st, c->nd_start.p + node, 1, s))) return rc;
+            *slot_lo = *slot_hi = st;
+        } else {
+            *slot_lo = *slot_hi = c->n;
+        }
+        return STS_OK;
+    }
+    int32_t a = 0, b = 0, sa = 0, sb = 0, cb = 0;
+    int rc = copy_out(&a, c->leaves.p + leaf_lo, 1, s);
+    if (rc || (rc = copy_out(&b, c->leaves.p + leaf_hi - 1, 1, s))) return rc;
+    if ((rc = copy_out(&sa, c->nd_start.p + a, 1, s)) || (rc = copy_out(&sb, c->nd_start.p + b, 1, s)) ||
+        (rc = copy_out(&cb, c->nd_count.p + b, 1, s)))
+        return rc;
+    *slot_lo = sa;
+    *slot_hi = (int64_t)sb + cb;
+    return STS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -850,6 +878,110 @@ int sts_velocity_dual(sts_ctx* ctx, const double* zeta, const double* area, cons
         return STS_ERR_ARG;
     }
     return velocity_dual_impl(ctx, zeta, area, p, vel, S(stream));
+}
+
+int sts_velocity_range(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
+                       int64_t leaf_begin, int64_t leaf_end, int32_t out_sorted, double* vel, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_velocity_range");
+    if (rc || (rc = check_params(p, "sts_velocity_range"))) return rc;
+    if (!ctx->have_tree) {
+        set_error("sts_velocity_range: no tree (call sts_tree_build first)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->capturing || ctx->use_dual) {
+        set_error("sts_velocity_range: needs eager calls on the target-leaf lists (traversal 0)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->n > 0 && (!zeta || !area || (!vel && leaf_end > leaf_begin))) {
+        set_error("sts_velocity_range: NULL array");
+        return STS_ERR_ARG;
+    }
+    cudaStream_t s = S(stream);
+    const int64_t n = ctx->n;
+    if (n < 2) {
+        if (leaf_begin < 0 || leaf_end < leaf_begin || leaf_end > (n > 0 ? 1 : 0)) {
+            set_error("sts_velocity_range: leaf range [%lld, %lld) outside [0, %lld)", (long long)leaf_begin,
+                      (long long)leaf_end, (long long)(n > 0 ? 1 : 0));
+            return STS_ERR_ARG;
+        }
+        if (n == 1 && leaf_end > leaf_begin) STS_CUDA(cudaMemsetAsync(vel, 0, 3 * sizeof(double), s));
+        return STS_OK;
+    }
+    if ((rc = sources_and_lists(ctx, zeta, area, p, p->precision, false, s))) return rc;
+    ctx->list_degree = p->degree;
+    if ((rc = refresh_counts(ctx, s))) return rc;
+    if (leaf_begin < 0 || leaf_end < leaf_begin || leaf_end > ctx->nleaves) {
+        set_error("sts_velocity_range: leaf range [%lld, %lld) outside [0, %lld)", (long long)leaf_begin,
+                  (long long)leaf_end, (long long)ctx->nleaves);
+        return STS_ERR_ARG;
+    }
+    int64_t base = -1;
+    if (out_sorted) {
+        int64_t hi = 0;
+        if ((rc = leaf_range_slots(ctx, leaf_begin, leaf_end, &base, &hi, s))) return rc;
+    }
+    if (leaf_end == leaf_begin) return STS_OK;
+    return evaluate_range(ctx, p->degree, p->precision, p->near_fp64_tau, leaf_begin, leaf_end, base, vel, s);
+}
+
+int sts_leaf_work(sts_ctx* ctx, int32_t degree, int64_t* work, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_leaf_work");
+    if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
+    if (!ctx->have_lists) {
+        set_error("sts_leaf_work: no target-leaf lists (call sts_velocity first)");
+        return STS_ERR_STATE;
+    }
+    if (degree < 1 || degree > kMaxDegree || (!work && ctx->nleaves > 0)) {
+        set_error("sts_leaf_work: degree must be in [1, %d] and work non-NULL", kMaxDegree);
+        return STS_ERR_ARG;
+    }
+    return leaf_work(ctx, degree, work, S(stream));
+}
+
+int sts_leaf_range(sts_ctx* ctx, int64_t leaf_begin, int64_t leaf_end, int64_t* slot_begin, int64_t* slot_end,
+                   void* stream)
+{
+    int rc = check_ctx(ctx, "sts_leaf_range");
+    if (rc) return rc;
+    if ((rc = refresh_counts(ctx, S(stream)))) return rc;
+    if (!ctx->have_tree || !slot_begin || !slot_end) {
+        set_error("sts_leaf_range: no tree, or NULL output");
+        return ctx->have_tree ? STS_ERR_ARG : STS_ERR_STATE;
+    }
+    const int64_t L = ctx->n < 2 ? (ctx->n > 0 ? 1 : 0) : ctx->nleaves;
+    if (leaf_begin < 0 || leaf_end < leaf_begin || leaf_end > L) {
+        set_error("sts_leaf_range: leaf range [%lld, %lld) outside [0, %lld)", (long long)leaf_begin,
+                  (long long)leaf_end, (long long)L);
+        return STS_ERR_ARG;
+    }
+    if (ctx->n < 2) {
+        *slot_begin = leaf_begin;
+        *slot_end = leaf_end;
+        return STS_OK;
+    }
+    return leaf_range_slots(ctx, leaf_begin, leaf_end, slot_begin, slot_end, S(stream));
+}
+
+int sts_unpermute(sts_ctx* ctx, const double* vel_sorted, double* vel, void* stream)
+{
+    int rc = check_ctx(ctx, "sts_unpermute");
+    if (rc) return rc;
+    if (!ctx->have_tree) {
+        set_error("sts_unpermute: no tree (call sts_tree_build first)");
+        return STS_ERR_STATE;
+    }
+    if (ctx->n > 0 && (!vel_sorted || !vel)) {
+        set_error("sts_unpermute: NULL array");
+        return STS_ERR_ARG;
+    }
+    if (ctx->n == 1) {
+        STS_CUDA(cudaMemcpyAsync(vel, vel_sorted, 3 * sizeof(double), cudaMemcpyDeviceToDevice, S(stream)));
+        return STS_OK;
+    }
+    return unpermute(ctx, vel_sorted, vel, S(stream));
 }
 
 int sts_dual_export(sts_ctx* ctx, int32_t kind, int64_t* npairs, int32_t* tgt, int32_t* src, void* stream)

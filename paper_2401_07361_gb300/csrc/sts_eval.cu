@@ -86,6 +86,12 @@ __device__ __forceinline__ void pot64(const double4 s, double tx, double ty, dou
 constexpr int kEvalWarps = 8;
 constexpr int kEvalWarps64 = 4;
 
+// The tasks a launch evaluates (those of leaves [leaf_lo, leaf_hi)) and where the targets'
+// rows go: out_base < 0, row perm[t] (the caller's order); else row t - out_base.
+struct EvalRange {
+    int64_t leaf_lo, leaf_hi, out_base;
+};
+
 // Bulk copies (the TMA engine's 1-D form) into shared memory, completed on an mbarrier.
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
@@ -377,7 +383,8 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
                                                 const float4* __restrict__ src32, const double4* __restrict__ src64,
                                                 const float4* __restrict__ tgt32, const double4* __restrict__ tgt64,
                                                 const int32_t* __restrict__ perm, float tau2, float tau_r,
-                                                double* __restrict__ corr, double* __restrict__ vel)
+                                                double* __restrict__ corr, double* __restrict__ vel,
+                                                int64_t out_base)
 {
     const int p = (tk.nt + 1) >> 1;
     const int j = lane % p;
@@ -490,7 +497,7 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
                 continue;
             }
             const double4 x = tgt64[t];
-            const int64_t i = perm[t];
+            const int64_t i = out_base >= 0 ? t - out_base : (int64_t)perm[t];
             vel[3 * i] = -kInv4Pi * (x.y * Sz - x.z * Sy);
             vel[3 * i + 1] = -kInv4Pi * (x.z * Sx - x.x * Sz);
             vel[3 * i + 2] = -kInv4Pi * (x.x * Sy - x.y * Sx);
@@ -507,7 +514,8 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
              const float4* __restrict__ tgt32, const double4* __restrict__ tgt64,
              const int32_t* __restrict__ perm, float tau2, float tau_r, double* __restrict__ corr,
              double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
-             unsigned long long* __restrict__ queue, int* __restrict__ status, const int64_t* __restrict__ over)
+             unsigned long long* __restrict__ queue, int* __restrict__ status, const int64_t* __restrict__ over,
+             EvalRange rg)
 {
     extern __shared__ __align__(16) EvalSmem sbuf[];  // kEvalWarps of them
     // a recorded step whose lists outgrew their capacities evaluates nothing (the host redoes it)
@@ -527,39 +535,40 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
         const int64_t ti = (int64_t)__shfl_sync(kFull, t, 0);
         if (ti >= nt) break;
         const Task tk = tasks[ti];
+        if (tk.leaf < rg.leaf_lo || tk.leaf >= rg.leaf_hi) continue;
         bool ok;
         switch (tk.S) {
             case 1:
                 ok = eval_task_mixed<1>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 2:
                 ok = eval_task_mixed<2>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 3:
                 ok = eval_task_mixed<3>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 4:
                 ok = eval_task_mixed<4>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 5:
                 ok = eval_task_mixed<5>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 6:
                 ok = eval_task_mixed<6>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 7:
                 ok = eval_task_mixed<7>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             default:
                 ok = eval_task_mixed<8>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
-                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel);
+                                         M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
         }
         if (!ok) break;
@@ -576,7 +585,8 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
                                                const NearEntry* __restrict__ near_ent,
                                                const double4* __restrict__ prx64, int M,
                                                const double4* __restrict__ src64, const double4* __restrict__ tgt64,
-                                               const int32_t* __restrict__ perm, double* __restrict__ vel)
+                                               const int32_t* __restrict__ perm, double* __restrict__ vel,
+                                               int64_t out_base = -1)
 {
     const int p = (tk.nt + 1) >> 1, S = tk.S;
     const int j = lane % p;
@@ -635,13 +645,13 @@ __device__ __forceinline__ void eval_task_fp64(const Task& tk, double4* sb, int 
             for (int c = 0; c < 3; c++) vel[3 * tk1 + c] = -kInv4Pi * a[3 + c];
     } else if (lane < p) {
         if (v0) {
-            const int64_t i = perm[tk0];
+            const int64_t i = out_base >= 0 ? tk0 - out_base : (int64_t)perm[tk0];
             vel[3 * i] = -kInv4Pi * (x0.y * a[2] - x0.z * a[1]);
             vel[3 * i + 1] = -kInv4Pi * (x0.z * a[0] - x0.x * a[2]);
             vel[3 * i + 2] = -kInv4Pi * (x0.x * a[1] - x0.y * a[0]);
         }
         if (v1) {
-            const int64_t i = perm[tk1];
+            const int64_t i = out_base >= 0 ? tk1 - out_base : (int64_t)perm[tk1];
             vel[3 * i] = -kInv4Pi * (x1.y * a[5] - x1.z * a[4]);
             vel[3 * i + 1] = -kInv4Pi * (x1.z * a[3] - x1.x * a[5]);
             vel[3 * i + 2] = -kInv4Pi * (x1.x * a[4] - x1.y * a[3]);
@@ -667,15 +677,44 @@ k_eval_fp64(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
             const NearEntry* __restrict__ near_ent, const double4* __restrict__ prx64, int M,
             const double4* __restrict__ src64, const double4* __restrict__ tgt64, const int32_t* __restrict__ perm,
             double* __restrict__ vel, const int64_t* __restrict__ ntasks_d, int64_t cap,
-            unsigned long long* __restrict__ queue, const int64_t* __restrict__ over)
+            unsigned long long* __restrict__ queue, const int64_t* __restrict__ over, EvalRange rg)
 {
     __shared__ double4 sbuf[kEvalWarps64][kStage];
     if (*over) return;  // lists past their recorded capacities: the host redoes the step
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nt = min(*ntasks_d, cap);
-    for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane))
-        eval_task_fp64<POT>(tasks[ti], sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, tgt64,
-                            perm, vel);
+    for (int64_t ti = next_task(queue, lane); ti < nt; ti = next_task(queue, lane)) {
+        const Task tk = tasks[ti];
+        if (tk.leaf < rg.leaf_lo || tk.leaf >= rg.leaf_hi) continue;
+        eval_task_fp64<POT>(tk, sbuf[w], lane, far_off, far_ent, near_coff, near_ent, prx64, M, src64, tgt64,
+                            perm, vel, rg.out_base);
+    }
+}
+
+// Per-leaf work of the target-leaf lists: targets x (far entries x M + near sources), the PC +
+// PP interactions of each depth-first leaf (the self pair included).
+__global__ void k_leaf_work(const int64_t* __restrict__ nleaves_p, const int32_t* __restrict__ leaves,
+                            const int32_t* __restrict__ count, const int64_t* __restrict__ far_off,
+                            const int64_t* __restrict__ near_coff, const NearEntry* __restrict__ near_ent, int M,
+                            int64_t* __restrict__ work)
+{
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= *nleaves_p) return;
+    int64_t ns = 0;
+    for (int64_t q = near_coff[L]; q < near_coff[L + 1]; q++) ns += near_ent[q].count;
+    work[L] = (int64_t)count[leaves[L]] * ((int64_t)M * (far_off[L + 1] - far_off[L]) + ns);
+}
+
+// vel[perm[t]] = vs[t]: rows in sorted slot order back to the caller's order.
+__global__ void k_unpermute(const double* __restrict__ vs, const int32_t* __restrict__ perm, int64_t n,
+                            double* __restrict__ vel)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t i = perm[t];
+    vel[3 * i] = vs[3 * t];
+    vel[3 * i + 1] = vs[3 * t + 1];
+    vel[3 * i + 2] = vs[3 * t + 2];
 }
 
 // ------------------------------------------------------------------------ counts
@@ -886,7 +925,7 @@ int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
     (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
                                                        c->near_ent.p, c->prx64.p, M, c->src64.p, c->src64.p,
                                                        c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue,
-                                                       c->dc.p + kDcOver),
+                                                       c->dc.p + kDcOver, EvalRange{0, INT64_MAX, -1}),
      note_launch());
     phase_end(c, kPhEval, s);
     STS_LAUNCH_CHECK();
@@ -929,7 +968,8 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
         (k_eval_fp64<false><<<g, kEvalWarps64 * 32, 0, s>>>(ls.tasks, ls.far_off, ls.far_ent, ls.near_coff,
                                                             ls.near_ent, c->prx64.p, M, c->src64.p, ls.tgt64,
                                                             ls.perm, vel, ls.ntasks_d, ls.ntasks, queue,
-                                                            c->dc.p + kDcOver),
+                                                            c->dc.p + kDcOver,
+                                                            EvalRange{ls.leaf_lo, ls.leaf_hi, ls.out_base}),
          note_launch());
         phase_end(c, phase, s);
     } else {
@@ -950,7 +990,7 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
         (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
              ls.tasks, ls.far_off, ls.far_ent, ls.near_coff, ls.near_ent, c->prx32.p, M, c->src32.p, c->src64.p,
              ls.tgt32, ls.tgt64, ls.perm, tau2, tau_r, corr, vel, ls.ntasks_d, ls.ntasks, queue, c->d_status,
-             c->dc.p + kDcOver),
+             c->dc.p + kDcOver, EvalRange{ls.leaf_lo, ls.leaf_hi, ls.out_base}),
          note_launch());
         phase_end(c, phase, s);
     }
@@ -973,6 +1013,49 @@ int evaluate(sts_ctx* c, int degree, int precision, double tau, double* vel, cud
     ls.perm = c->perm.p;
     ls.ntargets = c->n;
     return evaluate_lists(c, ls, degree, precision, tau, c->corr, vel, s);
+}
+
+int evaluate_range(sts_ctx* c, int degree, int precision, double tau, int64_t leaf_lo, int64_t leaf_hi,
+                   int64_t out_base, double* vel, cudaStream_t s)
+{
+    ListSet ls;
+    ls.tasks = c->tasks.p;
+    ls.ntasks_d = c->dc.p + kDcTasks;
+    ls.ntasks = c->ntasks;
+    ls.far_off = c->far_off.p;
+    ls.near_coff = c->near_coff.p;
+    ls.far_ent = c->far_ent.p;
+    ls.near_ent = c->near_ent.p;
+    ls.tgt32 = c->src32.p;
+    ls.tgt64 = c->src64.p;
+    ls.perm = c->perm.p;
+    ls.ntargets = c->n;
+    ls.leaf_lo = leaf_lo;
+    ls.leaf_hi = leaf_hi;
+    ls.out_base = out_base;
+    return evaluate_lists(c, ls, degree, precision, tau, c->corr, vel, s);
+}
+
+int leaf_work(sts_ctx* c, int degree, int64_t* work, cudaStream_t s)
+{
+    const int64_t L = c->nleaves;
+    if (L <= 0) return STS_OK;
+    STS_CUDA(c->d_work.reserve(L));
+    (k_leaf_work<<<blocks(L, 128), 128, 0, s>>>(c->dc.p + kDcLeaves, c->leaves.p, c->nd_count.p, c->far_off.p,
+                                                c->near_coff.p, c->near_ent.p, nbasis(degree), c->d_work.p),
+     note_launch());
+    STS_LAUNCH_CHECK();
+    STS_CUDA(cudaMemcpyAsync(work, c->d_work.p, L * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    STS_CUDA(cudaStreamSynchronize(s));
+    return STS_OK;
+}
+
+int unpermute(sts_ctx* c, const double* vs, double* vel, cudaStream_t s)
+{
+    if (c->n <= 0) return STS_OK;
+    (k_unpermute<<<blocks(c->n, 256), 256, 0, s>>>(vs, c->perm.p, c->n, vel), note_launch());
+    STS_LAUNCH_CHECK();
+    return STS_OK;
 }
 
 int wait_selftest(sts_ctx* c, int spins, cudaStream_t s)

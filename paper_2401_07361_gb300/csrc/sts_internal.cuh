@@ -289,6 +289,7 @@ struct sts_ctx {
 
     // ---- stats and phase timing -------------------------------------------------------
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
+    sts::DevBuf<int64_t> d_work;              // [nleaves] per-leaf interactions (sts_leaf_work)
     bool timing = false;
     cudaEvent_t ev[sts::kNumPhases][2] = {};
     float phase_ms[sts::kNumPhases] = {};
@@ -389,6 +390,9 @@ struct ListSet {
     const double4* tgt64;
     const int32_t* perm;  // target slot -> output row, or nullptr for the identity
     int64_t ntargets;     // rows of corr
+    // only the tasks of leaves [leaf_lo, leaf_hi); out_base >= 0: target slot t goes to output
+    // row t - out_base (sorted order) instead of perm[t]
+    int64_t leaf_lo = 0, leaf_hi = INT64_MAX, out_base = -1;
 };
 // The mixed or FP64 evaluation kernel over one list set; corrbuf: the FP64 close-pair scratch
 // (grown to 3 * ls.ntargets doubles eagerly); phase: the timed phase (-1: inside the caller's).
@@ -399,6 +403,14 @@ int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const do
                      double* psi, cudaStream_t s);
 int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s);
 int wait_selftest(sts_ctx* c, int spins, cudaStream_t s);
+// The evaluation of the targets of depth-first leaves [leaf_lo, leaf_hi) only (lists, sources
+// and proxy weights already in place); out_base >= 0: sorted-slot rows t - out_base.
+int evaluate_range(sts_ctx* c, int degree, int precision, double tau, int64_t leaf_lo, int64_t leaf_hi,
+                   int64_t out_base, double* vel, cudaStream_t s);
+// Per-leaf PC + PP interactions of the current lists into host work[nleaves] (synchronises).
+int leaf_work(sts_ctx* c, int degree, int64_t* work, cudaStream_t s);
+// vel[perm[t]] = vs[t] for every sorted slot t.
+int unpermute(sts_ctx* c, const double* vs, double* vel, cudaStream_t s);
 int count_interactions(sts_ctx* ctx, int degree, cudaStream_t s);
 int direct_sum(sts_ctx* ctx, const double* pos, const double* zeta, const double* area,
                int64_t n, const int64_t* targets, int64_t nt, int precision, double* vel,

@@ -81,6 +81,10 @@ def load(build_if_needed: bool = True):
             "sts_potential": (i32, [P, P, P, PP, P, P]),
             "sts_velocity_dual": (i32, [P, P, P, PP, P, P]),
             "sts_dual_export": (i32, [P, i32, P, P, P, P]),
+            "sts_velocity_range": (i32, [P, P, P, PP, i64, i64, i32, P, P]),
+            "sts_leaf_work": (i32, [P, i32, P, P]),
+            "sts_leaf_range": (i32, [P, i64, i64, P, P, P]),
+            "sts_unpermute": (i32, [P, P, P, P]),
             "sts_dual_stats": (i32, [P, i32, P, P]),
             "sts_set_traversal": (i32, [P, i32]),
             "sts_amr_init": (i32, [P, P, i64, i64, P, P, i32, P]),
@@ -240,6 +244,56 @@ def sts_velocity_dual(ctx, zeta, area, p, vel=None, stream=None):
                                     _dev(area, torch.float64, n, "area"), C.byref(p),
                                     _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)),
            "sts_velocity_dual")
+    return vel
+
+
+def sts_velocity_range(ctx, zeta, area, p, leaf_begin, leaf_end, out_sorted=False, vel=None, stream=None):
+    """Velocities of the targets of depth-first leaves [leaf_begin, leaf_end) only.  With
+    out_sorted, returns the compact block of those targets in sorted slot order (one GPU's
+    share, see sts_leaf_range); else writes their rows of vel[n,3] (caller's order)."""
+    import torch
+
+    n = zeta.numel()
+    if vel is None:
+        if out_sorted:
+            s0, s1 = sts_leaf_range(ctx, leaf_begin, leaf_end, stream)
+            vel = torch.empty((s1 - s0, 3), dtype=torch.float64, device=zeta.device)
+        else:
+            vel = torch.zeros((n, 3), dtype=torch.float64, device=zeta.device)
+    _check(load().sts_velocity_range(ctx, _dev(zeta, torch.float64, n, "zeta"), _dev(area, torch.float64, n, "area"),
+                                     C.byref(p), int(leaf_begin), int(leaf_end), int(bool(out_sorted)),
+                                     _dev(vel, torch.float64, vel.numel(), "vel"), _stream(stream)),
+           "sts_velocity_range")
+    return vel
+
+
+def sts_leaf_work(ctx, degree, stream=None):
+    """Per-leaf PC + PP interactions (numpy int64[nleaves]) of the current target-leaf lists."""
+    import numpy as np
+
+    nl = sts_tree_info(ctx, stream)["leaves"]
+    work = np.zeros(max(nl, 1), dtype=np.int64)
+    _check(load().sts_leaf_work(ctx, int(degree), _host(work), _stream(stream)), "sts_leaf_work")
+    return work[:nl]
+
+
+def sts_leaf_range(ctx, leaf_begin, leaf_end, stream=None):
+    """(slot_begin, slot_end) of the targets of depth-first leaves [leaf_begin, leaf_end)."""
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(load().sts_leaf_range(ctx, int(leaf_begin), int(leaf_end), C.byref(a), C.byref(b), _stream(stream)),
+           "sts_leaf_range")
+    return a.value, b.value
+
+
+def sts_unpermute(ctx, vel_sorted, vel=None, stream=None):
+    """vel[perm[t]] = vel_sorted[t]: sorted slot order back to the caller's order."""
+    import torch
+
+    n = vel_sorted.shape[0]
+    if vel is None:
+        vel = torch.empty((n, 3), dtype=torch.float64, device=vel_sorted.device)
+    _check(load().sts_unpermute(ctx, _dev(vel_sorted, torch.float64, 3 * n, "vel_sorted"),
+                                _dev(vel, torch.float64, 3 * n, "vel"), _stream(stream)), "sts_unpermute")
     return vel
 
 
