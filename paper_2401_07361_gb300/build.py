@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsts.so")
 
 SOURCES = ["sts_api.cu", "sts_tables.cu", "sts_scan.cu", "sts_tree.cu", "sts_upward.cu",
-           "sts_eval.cu", "sts_down.cu", "sts_rk4.cu", "sts_amr.cu"]
+           "sts_eval.cu", "sts_down.cu", "sts_rk4.cu", "sts_amr.cu", "sts_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-Xptxas", "-v"]

@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
@@ -108,6 +108,9 @@ sts_ctx::~sts_ctx()
             t->d_beta.release();
             t->d_vinv.release();
             t->d_vinvT.release();
+            t->d_tcB.release();
+            t->d_tcF.release();
+            t->d_tcE.release();
             delete t;
         }
     for (int p = 0; p < kNumPhases; p++)

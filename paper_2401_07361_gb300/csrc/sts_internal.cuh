@@ -97,7 +97,24 @@ struct RefTable {
     std::vector<double> vinv;  // [M,M], vinv[k*M+m] = (V_ref^{-1})[k][m]
     DevBuf<double> d_beta, d_vinv;
     DevBuf<double> d_vinvT;    // [M,M], d_vinvT[m*M+k] = (V_ref^{-1})[k][m] (threads over k read rows)
+    // The tensor-core contraction's operand B: V_ref^{-1} with row k scaled by 2^-E[k] and
+    // column m by 2^-F[m] (into (-1/2, 1/2)), split into kTcSlices balanced base-256 digits,
+    // slice b (1-based) = digit b; each slice is an [Np, Kp] bf16 matrix (row n = proxy point
+    // m, K = basis index k, zero padded) in the tcgen05 no-swizzle K-major layout (8 x 8 core
+    // matrices, K-adjacent ones 128 bytes apart, row groups Kp * 16 bytes apart).
+    int tcKp = 0, tcNp = 0;
+    DevBuf<uint16_t> d_tcB;    // [kTcSlices][Np * Kp]
+    DevBuf<int32_t> d_tcF;     // [Np]
+    DevBuf<int32_t> d_tcE;     // [Kp] moment scales (powers of two)
 };
+// Digits of the tensor-core contraction: kTcSlices x 8 bits hold every bit of an FP64 entry
+// (below 2^-57 of its column's largest).
+constexpr int kTcSlices = 7;
+// Byte offset of element (r, k) of a K-major [rows, Kp] bf16 matrix in the no-swizzle layout.
+__host__ __device__ inline unsigned tc_kmajor_offset(int r, int k, int Kp)
+{
+    return (unsigned)((r >> 3) * (Kp * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
 
 // Far-field list entry as the evaluation kernel reads it: proxy block of cluster `slot`
 // and the offset c_cluster - c_target_leaf rounded to FP32 (mixed precision).
@@ -290,6 +307,7 @@ struct sts_ctx {
     // ---- stats and phase timing -------------------------------------------------------
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
     sts::DevBuf<int64_t> d_work;              // [nleaves] per-leaf interactions (sts_leaf_work)
+    sts::DevBuf<double> up_wtc;               // [clusters, M] tensor-core contraction (mixed)
     bool timing = false;
     cudaEvent_t ev[sts::kNumPhases][2] = {};
     float phase_ms[sts::kNumPhases] = {};
@@ -314,6 +332,10 @@ namespace sts {
 void icosahedron(double V[12][3], int F[20][3], double C[20][3]);
 int build_ref_table(int d, RefTable* t);
 RefTable* get_ref(sts_ctx* ctx, int d);
+// The contraction sum_k omega_k Vinv[k][m] of the upward pass on the tensor cores, for the
+// clusters of the current tree (counted on the device, at most nclu) into wout[cluster, M].
+bool proxy_weights_tc_supported(int degree);
+int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s);
 
 // ---- scans and sorting (sts_scan.cu) -----------------------------------------------
 // out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total.  scratch: >= scan_scratch(n)

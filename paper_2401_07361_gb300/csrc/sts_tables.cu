@@ -6,6 +6,9 @@
 // Compiled without FMA contraction (-ffp-contract=off): the icosahedron values decide
 // which face owns each particle, so every operation below is a plain IEEE double op in
 // the order written.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -226,6 +229,64 @@ RefTable* get_ref(sts_ctx* ctx, int d)
         t->d_vinvT.release();
         delete t;
         set_error("uploading the degree-%d proxy table failed", d);
+        return nullptr;
+    }
+    // operand B of the tensor-core contraction.  Row k of V_ref^-1 is divided by 2^E[k], E[k]
+    // the power of two nearest the integral of basis function k over the reference simplex
+    // (a! b! c! 2 / (d + 2)!), by which the kernel multiplies moment k: the moments then have
+    // comparable sizes, so 32 bits of the largest keep every moment's leading bits.  Column m
+    // is then scaled into (-1/2, 1/2) by 2^-F[m] and cut into kTcSlices balanced base-256
+    // digits (each in [-128, 128]; every exact operation, the last remainder below 2^-57 of
+    // the column's largest entry).
+    const int M = t->M;
+    t->tcKp = (M + 15) / 16 * 16;
+    t->tcNp = t->tcKp;
+    std::vector<uint16_t> B((size_t)kTcSlices * t->tcNp * t->tcKp, 0);
+    std::vector<int32_t> F((size_t)t->tcNp, 0), Ek((size_t)t->tcKp, 0);
+    {
+        double fact[2 * kMaxDegree + 3];
+        fact[0] = 1.0;
+        for (int i = 1; i <= 2 * kMaxDegree + 2; i++) fact[i] = fact[i - 1] * i;
+        int k = 0;
+        for (int i = d; i >= 0; i--)
+            for (int j = d - i; j >= 0; j--) {
+                const double mono = fact[i] * fact[j] * fact[d - i - j] * 2.0 / fact[d + 2];
+                Ek[k++] = -(int32_t)std::lround(std::log2(mono));
+            }
+    }
+    for (int m = 0; m < M; m++) {
+        double mx = 0.0;
+        for (int k = 0; k < M; k++) mx = std::max(mx, std::fabs(std::ldexp(t->vinv[(size_t)k * M + m], -Ek[k])));
+        int e = 0;
+        if (mx > 0.0) std::frexp(mx, &e);  // mx < 2^e
+        F[m] = e + 1;                      // entries below 2^(F - 1) = 1/2 of 2^F
+        for (int k = 0; k < M; k++) {
+            double x = std::ldexp(t->vinv[(size_t)k * M + m], -Ek[k] - F[m]);  // |x| < 1/2, exact
+            for (int b = 0; b < kTcSlices; b++) {
+                x *= 256.0;                       // exact
+                const double dg = std::nearbyint(x);  // |dg| <= 128
+                x -= dg;                          // exact, |x| <= 1/2
+                const float f = (float)dg;
+                uint32_t u;
+                std::memcpy(&u, &f, 4);
+                const size_t off = (size_t)b * t->tcNp * t->tcKp * 2 + tc_kmajor_offset(m, k, t->tcKp);
+                B[off / 2] = (uint16_t)(u >> 16);  // an integer of at most 8 bits: exact in bf16
+            }
+        }
+    }
+    if (t->d_tcB.reserve(B.size()) != cudaSuccess || t->d_tcF.reserve(F.size()) != cudaSuccess ||
+        t->d_tcE.reserve(Ek.size()) != cudaSuccess ||
+        cudaMemcpy(t->d_tcB.p, B.data(), B.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_tcF.p, F.data(), F.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_tcE.p, Ek.data(), Ek.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        t->d_beta.release();
+        t->d_vinv.release();
+        t->d_vinvT.release();
+        t->d_tcB.release();
+        t->d_tcF.release();
+        t->d_tcE.release();
+        delete t;
+        set_error("uploading the degree-%d tensor-core table failed", d);
         return nullptr;
     }
     ctx->refs[d] = t;

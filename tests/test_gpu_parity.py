@@ -230,6 +230,50 @@ def test_proxy_weights_match_oracle(ctx, name):
         assert np.all(np.abs(Wg[q] - oW[q]) <= bound), q
 
 
+@pytest.mark.parametrize("name", ["rand3000", "ico4", "clustered"])
+@pytest.mark.parametrize("d", [6, 8, 10, 11])
+def test_proxy_weights_tensor_core_match_oracle(ctx, name, d):
+    # Mixed precision forms sum_k omega_k Vinv[k][m] on the tensor cores from exact 8-bit digit
+    # products (moment k scaled by 2^E_k, E_k = -round(log2(simplex integral of B_k)), then
+    # kept to 32 bits of the largest scaled moment; Vinv to every FP64 bit; d = 10 and 11 take
+    # two rounds of tensor-memory columns).  W_m = rho_m^d sum_k Vinv[k][m] omega_k then
+    # differs from the oracle's FP64 weights only through omega: its FP32 moments (the FP64
+    # bound of test_proxy_weights_match_oracle with FP32's epsilon) and that truncation.  A
+    # wrong operand layout, digit or scale misses this by orders of magnitude.
+    pos, leaf, ml = _case(name)
+    n = len(pos)
+    zeta, area = _fields(n, 4)
+    p = sts.params(theta=0.7, degree=d, leaf_size=leaf, max_level=ml, precision=sts.STS_MIXED,
+                   near_fp64_tau=0.0)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    sts.sts_velocity(ctx, dev(zeta), dev(area), p)
+    ids, yt, Wg = sts.sts_clusters_export(ctx, d)
+    tr = O.Tree(pos, leaf, ml)
+    oids, oyt, oW = tr.clusters(zeta, area, d)
+    assert np.array_equal(ids, oids) and len(ids) > 0
+    ex = tr.export()
+    vinv = np.abs(O.vref_inverse(d))
+    beta, _ = O.proxy_reference(d)
+    aw = np.abs(zeta * area)
+    e32 = float(np.finfo(np.float32).eps)
+    fact = math.factorial
+    Ek = np.array([-round(math.log2(fact(a) * fact(b) * fact(d - a - b) * 2 / fact(d + 2)))
+                   for a in range(d, -1, -1) for b in range(d - a, -1, -1)], dtype=float)
+    for q, node in enumerate(oids):
+        v = ex["geom"][node, :9].reshape(3, 3)
+        cnt = ex["count"][node]
+        idx = ex["perm"][ex["start"][node]:ex["start"][node] + cnt]
+        _, _, om_abs = O.cluster(v.ravel(), d, pos[idx], aw[idx])
+        rows = np.array([np.cross(v[1], v[2]), np.cross(v[2], v[0]), np.cross(v[0], v[1])])
+        rows /= np.dot(v[0], rows[0])
+        db = 6 * e32 * np.linalg.norm(rows, axis=1).sum()
+        dom = (cnt + 2 * d + 16) * e32 * om_abs + 2 * d * db * aw[idx].sum()
+        dom = dom + 2.0 ** -31 * np.max((om_abs + dom) * 2.0 ** Ek) * 2.0 ** -Ek
+        rho = np.linalg.norm(beta @ v, axis=1)
+        bound = rho ** d * (vinv.T @ dom)
+        assert np.all(np.abs(Wg[q] - oW[q]) <= bound), (q, np.max(np.abs(Wg[q] - oW[q]) / bound))
+
+
 @pytest.mark.parametrize("n", [2, 3, 129, 1000, 4099])
 @pytest.mark.parametrize("prec", [sts.STS_FP64, sts.STS_MIXED])
 def test_direct_matches_oracle(ctx, n, prec):
