@@ -220,7 +220,8 @@ int refresh(sts_ctx* c, AmrState* m, cudaStream_t s)
     (k_amr_clear<<<blocks(m->nv, T), T, 0, s>>>(m->nv, m->valive.p, m->pos.p, m->zeta.p, m->area.p, m->flags.p),
      note_launch());
     (k_amr_area<<<blocks(m->nt, T), T, 0, s>>>(m->nt, m->tstate.p, m->tv.p, m->pos.p, m->area.p), note_launch());
-    exclusive_scan_i32(m->flags.p, m->scan.p, m->nv, c->scan_tmp.p, s);
+    if (scan_state_reserve(c->scan_state, m->nv + 1, s)) return STS_ERR_CUDA;
+    exclusive_scan_i32(m->flags.p, m->scan.p, m->nv, c->scan_state, s, c->d_status);
     STS_LAUNCH_CHECK();
     STS_CUDA(cudaMemcpyAsync(c->h_pinned, m->scan.p + m->nv, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     STS_CUDA(cudaStreamSynchronize(s));

@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); scan_state.release(); scan_state_side.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
@@ -437,6 +437,10 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->wover.reserve(n + 1));
     STS_CUDA(c->corr.reserve(3 * n + 3));
     STS_CUDA(c->scan_tmp.reserve(radix_hist_size(n) + 1 + scan_scratch(radix_hist_size(n)) + 2 * scan_scratch(big) + 64));
+    // every scan a recorded step runs (capacities included) fits its stream's state
+    if (scan_state_reserve(c->scan_state, std::max<int64_t>(radix_hist_size(n), big) + 1, s) ||
+        scan_state_reserve(c->scan_state_side, big + 1, s))
+        return STS_ERR_CUDA;
     if (c->use_dual && (rc = reserve_dual_for_capture(c, p->degree, s))) return rc;
     return STS_OK;
 }

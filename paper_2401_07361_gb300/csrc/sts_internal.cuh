@@ -308,6 +308,8 @@ struct sts_ctx {
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
     sts::DevBuf<int64_t> d_work;              // [nleaves] per-leaf interactions (sts_leaf_work)
     sts::DevBuf<double> up_wtc;               // [clusters, M] tensor-core contraction (mixed)
+    sts::DevBuf<int64_t> scan_state;          // single-pass scan state of the main stream
+    sts::DevBuf<int64_t> scan_state_side;     // ... of the side stream (lists)
     bool timing = false;
     cudaEvent_t ev[sts::kNumPhases][2] = {};
     float phase_ms[sts::kNumPhases] = {};
@@ -338,18 +340,24 @@ bool proxy_weights_tc_supported(int degree);
 int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s);
 
 // ---- scans and sorting (sts_scan.cu) -----------------------------------------------
-// out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total.  scratch: >= scan_scratch(n)
 int64_t scan_scratch(int64_t n);
-// n_dev: optional device count (then n is its upper bound, used to size the grid).
-void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, int64_t* scratch,
-                        cudaStream_t s, const int64_t* n_dev = nullptr);
+// out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total: one single-pass launch.
+// state: the scan state of the stream it runs on (scans on one state run one after another),
+// at least scan_state_size(n) int64 and zero when allocated (scan_state_reserve); a
+// look-back that gives up sets STS_ERR_TIMEOUT in *status.  n_dev: optional device count
+// (then n is its upper bound, used to size the grid).
+int64_t scan_state_size(int64_t n);
+int scan_state_reserve(DevBuf<int64_t>& state, int64_t n, cudaStream_t s);
+void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, DevBuf<int64_t>& state, cudaStream_t s,
+                        const int* status, const int64_t* n_dev = nullptr);
 // Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.  Result in
-// key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n).
+// key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n); the
+// scan state must hold scan_state_size(radix_hist_size(n)).
 // n_dev: optional device count (n is then its upper bound and sizes the grids).
 int64_t radix_hist_size(int64_t n);
 void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* val_tmp,
-                      int64_t n, int bits, uint32_t* hist, int64_t* scan_out,
-                      int64_t* scan_scratch_buf, cudaStream_t s, const int64_t* n_dev = nullptr);
+                      int64_t n, int bits, uint32_t* hist, int64_t* scan_out, DevBuf<int64_t>& state,
+                      const int* status, cudaStream_t s, const int64_t* n_dev = nullptr);
 
 // ---- tree and lists (sts_tree.cu) ----------------------------------------------------
 // inst_off: device offsets [ninst + 1] of the instances (NULL: one instance)

@@ -1481,6 +1481,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_CUDA(c->root_id.reserve(nkeys + 1));
     STS_CUDA(c->root_start.reserve(nkeys + 1));
     STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1) + scan_scratch(nkeys + 1)));
+    if (!c->capturing && scan_state_reserve(c->scan_state, std::max<int64_t>(std::max<int64_t>(hs, n + 1), nkeys + 1), s))
+        return STS_ERR_CUDA;
     c->ninst = ninst;
 
     const int T = 256;
@@ -1489,8 +1491,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     (k_faces<<<blocks(n, T), T, 0, s>>>(c->pos.p, n, inst_off, ninst, c->nodeof.p, face_count, c->d_status),
      note_launch());
     (k_root_flags<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_flag.p), note_launch());
-    exclusive_scan_i32(c->root_flag.p, c->root_id.p, nkeys, c->scan_tmp.p, s);
-    exclusive_scan_i32(face_count, c->root_start.p, nkeys, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->root_flag.p, c->root_id.p, nkeys, c->scan_state, s, c->d_status);
+    exclusive_scan_i32(face_count, c->root_start.p, nkeys, c->scan_state, s, c->d_status);
     (k_roots<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_id.p, c->root_start.p, c->face_node.p,
                                             c->nd_level.p, c->nd_key.p, c->nd_parent.p, c->nd_first_child.p,
                                             c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->nd_leaf.p,
@@ -1545,8 +1547,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
          note_launch());
         (k_level_nch<<<g, T, 0, s>>>(lvl, level, c->nd_leaf.p, c->nd_cc.p, c->flags.p, dc + kDcTmp),
          note_launch());
-        exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_tmp.p, s,
-                           dc + kDcTmp);
+        exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_state, s,
+                           c->d_status, dc + kDcTmp);
         (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn, c->nd_cc.p, c->nd_level.p,
                                           c->nd_key.p, c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p,
                                           c->nd_start.p, c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p,
@@ -1580,11 +1582,10 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     int bits = 0;
     while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
     int64_t* scan_out = c->scan_tmp.p;
-    int64_t* scan_scr = c->scan_tmp.p + hs + 1;
     radix_sort_pairs(c->skey.p, c->perm.p, c->skey_tmp.p, c->perm_tmp.p, n, bits, c->hist.p,
-                     scan_out, scan_scr, s);
+                     scan_out, c->scan_state, c->d_status, s);
     (k_leaf_flags<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->nd_start.p, n, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_state, s, c->d_status);
     (k_copy_count<<<1, 32, 0, s>>>(c->offs.p + n, c->dc.p + kDcLeaves), note_launch());
     STS_CUDA(c->leaves.reserve(n + 1));
     (k_leaf_list<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->flags.p, c->offs.p, n,
@@ -1615,6 +1616,7 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
         STS_CUDA(c->flags.reserve(L + 1));
         STS_CUDA(c->offs.reserve(L + 1));
         STS_CUDA(c->scan_tmp.reserve(scan_scratch(L + 1) + 8));
+        if (scan_state_reserve(c->scan_state_side, std::max<int64_t>(c->n, L) + 1, s)) return STS_ERR_CUDA;
     }
     int64_t* far_po = c->far_off.p;
     int64_t* near_po = c->near_off.p;
@@ -1635,9 +1637,9 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
                              c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->cluster_slot.p, c->list_cnt.p, nullptr,
                              nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, L, c->wover.p,
                              c->d_status, dc + kDcOver), note_launch());  // list_cnt: three rows of stride L
-    exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
-    exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
-    exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_tmp.p, s, dc + kDcLeaves);
+    exclusive_scan_i32(c->list_cnt.p, far_po, L, c->scan_state_side, s, c->d_status, dc + kDcLeaves);
+    exclusive_scan_i32(c->list_cnt.p + L, near_po, L, c->scan_state_side, s, c->d_status, dc + kDcLeaves);
+    exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_state_side, s, c->d_status, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
     STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
     (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
@@ -1745,6 +1747,8 @@ static int reserve_dual(sts_ctx* c, const DualCaps& k, int64_t L, int64_t C, int
     STS_CUDA(c->dual_bcnt.reserve(4 * KT + 1));
     STS_CUDA(c->dual_boff.reserve(4 * KT + 2));
     STS_CUDA(c->scan_tmp.reserve(scan_scratch(4 * KT + 1) + scan_scratch(k.terms + 1) + scan_scratch(nodes + 1) + 64));
+    // the traversal's scans run on the side stream: its state, zeroed there
+    if (scan_state_reserve(c->scan_state_side, std::max<int64_t>(4 * KT, k.terms) + 1, c->side)) return STS_ERR_CUDA;
     STS_CUDA(c->far_off.reserve(L + 1));
     STS_CUDA(c->near_off.reserve(L + 1));
     STS_CUDA(c->near_coff.reserve(L + 1));
@@ -1794,7 +1798,7 @@ static int launch_dual(sts_ctx* c, double theta, int levels, int64_t L, int64_t 
     (k_dual_bucket<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_tk.p, du, tcap, KT, c->nd_start.p, c->slot_leaf.p,
                                     c->cluster_slot.p, c->dual_bkt.p, c->dual_bcnt.p, c->dual_ptmp.p),
      note_launch());
-    exclusive_scan_i32(c->dual_bcnt.p, c->dual_boff.p, 4 * KT, c->scan_tmp.p, s);
+    exclusive_scan_i32(c->dual_bcnt.p, c->dual_boff.p, 4 * KT, c->scan_state_side, s, c->d_status);
     (k_dual_scatter<<<gt, T, 0, s>>>(du, tcap, c->dual_bkt.p, c->dual_ptmp.p, c->dual_boff.p, c->dual_ts.p,
                                      c->dual_ktmp.p, c->dual_chunk.p),
      note_launch());
@@ -1803,7 +1807,7 @@ static int launch_dual(sts_ctx* c, double theta, int levels, int64_t L, int64_t 
      note_launch());
     (k_dual_gather<<<gt, T, 0, s>>>(c->dual_tt.p, c->dual_ts.p, c->dual_perm.p, c->dual_key.p, bits_t, du, tcap,
                                     c->nd_count.p, c->dual_t.p, c->dual_s.p, c->dual_chunk.p), note_launch());
-    exclusive_scan_i32(c->dual_chunk.p, c->dual_scan.p, tcap, c->scan_tmp.p, s, du + kDuP);
+    exclusive_scan_i32(c->dual_chunk.p, c->dual_scan.p, tcap, c->scan_state_side, s, c->d_status, du + kDuP);
     // CSR per kind, then the entries
     DualCsr csr;
     csr.off[kPP] = c->near_off.p;

@@ -322,15 +322,16 @@ int build_clusters(sts_ctx* c, cudaStream_t s)
         STS_CUDA(c->up_toff.reserve(nn + 2));
         STS_CUDA(c->list_cnt.reserve(nn + 1));
         STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
+        if (scan_state_reserve(c->scan_state, nn + 1, s)) return STS_ERR_CUDA;
         STS_CUDA(c->up_frame.reserve(12 * nn + 12));
         STS_CUDA(c->up_frame32.reserve(18 * nn + 18));
     }
     const unsigned g = blocks(std::max<int64_t>(nn, 1), 256);
     (k_cluster_flags<<<g, 256, 0, s>>>(dc + kDcNodes, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_tmp.p, s, dc + kDcNodes);
+    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_state, s, c->d_status, dc + kDcNodes);
     (k_cluster_fill<<<g, 256, 0, s>>>(dc + kDcNodes, c->flags.p, c->offs.p, c->nd_count.p, c->cluster_slot.p,
                                       c->cluster_node.p, c->list_cnt.p), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_tmp.p, s, dc + kDcNodes);
+    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_state, s, c->d_status, dc + kDcNodes);
     (k_cluster_totals<<<1, 32, 0, s>>>(dc, c->offs.p, c->up_toff.p), note_launch());
     STS_LAUNCH_CHECK();
     if (!cap) {
