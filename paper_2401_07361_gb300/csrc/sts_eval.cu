@@ -172,7 +172,9 @@ __device__ __forceinline__ float sqdist(const float4 s, float ax, float ay, floa
 }
 
 // The FP32 pair loop of one staged group for a lane's two targets: entries ph, ph + S, ... of
-// the group padded to a multiple of 4 S (padding entries carry w = 0 far away), four per trip.
+// the group padded to a multiple of 4 S (padding entries carry w = 0 far away), four per trip,
+// the two targets in the two halves of paired FP32 instructions (f32x2: one FADD2 / FFMA2 /
+// FMUL2 does a step for both, halving the issued FP32 instructions of an issue-bound loop).
 // TEST:
 // pairs with |d|^2 < 2 tau contribute nothing here and set `hit`; the caller then evaluates
 // them in FP64.
@@ -181,30 +183,37 @@ __device__ __forceinline__ void block_pairs(const float4* sb, int cntp, int ph, 
                                             float bx, float by, float bz, float& p0x, float& p0y, float& p0z,
                                             float& p1x, float& p1y, float& p1z, float tau2, bool& hit)
 {
+    // the two targets as the halves of paired FP32 operations (f32x2: each half the scalar
+    // operation, so the squared distances are bit for bit those of the close-pair pass)
+    const float2 na = make_float2(-ax, -bx), nb = make_float2(-ay, -by), nc = make_float2(-az, -bz);
+    const float2 eps2 = make_float2(kEps, kEps);
+    float2 px = make_float2(p0x, p1x), py = make_float2(p0y, p1y), pz = make_float2(p0z, p1z);
     for (int i = ph; i < cntp; i += 4 * S) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const float4 s = sb[i + u * S];
-            const float d0x = s.x - ax, d0y = s.y - ay, d0z = s.z - az;
-            const float d1x = s.x - bx, d1y = s.y - by, d1z = s.z - bz;
-            const float r0 = fmaf(d0z, d0z, fmaf(d0y, d0y, fmaf(d0x, d0x, kEps)));
-            const float r1 = fmaf(d1z, d1z, fmaf(d1y, d1y, fmaf(d1x, d1x, kEps)));
-            float c0 = s.w * rcp_approx(r0);
-            float c1 = s.w * rcp_approx(r1);
+            const float2 dx = __fadd2_rn(make_float2(s.x, s.x), na);
+            const float2 dy = __fadd2_rn(make_float2(s.y, s.y), nb);
+            const float2 dz = __fadd2_rn(make_float2(s.z, s.z), nc);
+            const float2 r = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+            float2 c = __fmul2_rn(make_float2(s.w, s.w), make_float2(rcp_approx(r.x), rcp_approx(r.y)));
             if (TEST) {
-                const bool z0 = r0 < tau2, z1 = r1 < tau2;
-                c0 = z0 ? 0.f : c0;
-                c1 = z1 ? 0.f : c1;
+                const bool z0 = r.x < tau2, z1 = r.y < tau2;
+                c.x = z0 ? 0.f : c.x;
+                c.y = z1 ? 0.f : c.y;
                 hit = hit || z0 || z1;
             }
-            p0x = fmaf(c0, d0x, p0x);
-            p0y = fmaf(c0, d0y, p0y);
-            p0z = fmaf(c0, d0z, p0z);
-            p1x = fmaf(c1, d1x, p1x);
-            p1y = fmaf(c1, d1y, p1y);
-            p1z = fmaf(c1, d1z, p1z);
+            px = __ffma2_rn(c, dx, px);
+            py = __ffma2_rn(c, dy, py);
+            pz = __ffma2_rn(c, dz, pz);
         }
     }
+    p0x = px.x;
+    p1x = px.y;
+    p0y = py.x;
+    p1y = py.y;
+    p0z = pz.x;
+    p1z = pz.y;
 }
 
 // Second pass over a tested block for a lane that hit (its entries ph, ph + S, ...; slot
