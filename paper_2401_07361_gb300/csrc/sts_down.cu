@@ -350,10 +350,16 @@ int launch_down(sts_ctx* c, const RefTable* ref, int levels, int64_t C, int64_t 
     const unsigned gl = (unsigned)std::min<int64_t>(C, 16 * (int64_t)c->num_sms);
     if (mixed) {
         const int A = levels + 1;  // a leaf has at most `levels` ancestors (itself included)
-        (k_cluster_coef<D><<<gl, coef_threads<D>(), 0, s>>>(c->dc.p + kDcClusters, c->cluster_node.p, c->chas.p,
-                                                             c->nd_geom.p, ref->d_beta.p, ref->d_vinvT.p, c->cvel.p,
-                                                             c->cdown32.p),
-         note_launch());
+        if (proxy_weights_tc_supported(D)) {
+            // on the tensor cores (exact digit products, sts_tc.cu)
+            const int rc = cluster_coef_tc(c, ref, D, C, c->cvel.p, c->cdown32.p, s);
+            if (rc) return rc;
+        } else {
+            (k_cluster_coef<D><<<gl, coef_threads<D>(), 0, s>>>(c->dc.p + kDcClusters, c->cluster_node.p, c->chas.p,
+                                                                 c->nd_geom.p, ref->d_beta.p, ref->d_vinvT.p,
+                                                                 c->cvel.p, c->cdown32.p),
+             note_launch());
+        }
         if (lcap > 0)
             (k_leaf_anc<<<blocks(lcap, 128), 128, 0, s>>>(c->dc.p + kDcLeaves, lcap, c->leaves.p, c->nd_parent.p,
                                                           c->cluster_slot.p, c->chas.p, A, c->leaf_anc.p),

@@ -106,6 +106,10 @@ struct RefTable {
     DevBuf<uint16_t> d_tcB;    // [kTcSlices][Np * Kp]
     DevBuf<int32_t> d_tcF;     // [Np]
     DevBuf<int32_t> d_tcE;     // [Kp] moment scales (powers of two)
+    // The same for the dual traversal's coefficients c = V_ref^{-1} u: operand B holds the rows
+    // of V_ref^{-1} (row n = coefficient k, K = proxy point m), row k scaled by 2^-Fr[k].
+    DevBuf<uint16_t> d_tcBr;   // [kTcSlices][Np * Kp]
+    DevBuf<int32_t> d_tcFr;    // [Np]
 };
 // Digits of the tensor-core contraction: kTcSlices x 8 bits hold every bit of an FP64 entry
 // (below 2^-57 of its column's largest).
@@ -308,6 +312,7 @@ struct sts_ctx {
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
     sts::DevBuf<int64_t> d_work;              // [nleaves] per-leaf interactions (sts_leaf_work)
     sts::DevBuf<double> up_wtc;               // [clusters, M] tensor-core contraction (mixed)
+    sts::DevBuf<double> prx_rd;               // [clusters, M] rho_m^d of each proxy point
     sts::DevBuf<int64_t> scan_state;          // single-pass scan state of the main stream
     sts::DevBuf<int64_t> scan_state_side;     // ... of the side stream (lists)
     bool timing = false;
@@ -338,6 +343,11 @@ RefTable* get_ref(sts_ctx* ctx, int d);
 // clusters of the current tree (counted on the device, at most nclu) into wout[cluster, M].
 bool proxy_weights_tc_supported(int degree);
 int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s);
+// The dual traversal's mixed-precision interpolation coefficients c = V_ref^-1 diag(rho^d) U on
+// the tensor cores, for the clusters with CP / CC pairs (chas), cvel[cluster, M, 3] ->
+// coef32[cluster, M] as float4 (x, y, z, unused).
+int cluster_coef_tc(sts_ctx* c, const RefTable* ref, int degree, int64_t nclu, const double* cvel, float* coef32,
+                    cudaStream_t s);
 
 // ---- scans and sorting (sts_scan.cu) -----------------------------------------------
 int64_t scan_scratch(int64_t n);

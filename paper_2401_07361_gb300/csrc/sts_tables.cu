@@ -274,7 +274,34 @@ RefTable* get_ref(sts_ctx* ctx, int d)
             }
         }
     }
+    // operand B of the coefficient contraction: row k of V_ref^-1 scaled by 2^-Fr[k] into
+    // (-1/2, 1/2), the same balanced digits, stored as [Np rows k, Kp columns m]
+    std::vector<uint16_t> Br((size_t)kTcSlices * t->tcNp * t->tcKp, 0);
+    std::vector<int32_t> Fr((size_t)t->tcNp, 0);
+    for (int k = 0; k < M; k++) {
+        double mx = 0.0;
+        for (int m = 0; m < M; m++) mx = std::max(mx, std::fabs(t->vinv[(size_t)k * M + m]));
+        int e = 0;
+        if (mx > 0.0) std::frexp(mx, &e);
+        Fr[k] = e + 1;
+        for (int m = 0; m < M; m++) {
+            double x = std::ldexp(t->vinv[(size_t)k * M + m], -Fr[k]);
+            for (int b = 0; b < kTcSlices; b++) {
+                x *= 256.0;
+                const double dg = std::nearbyint(x);
+                x -= dg;
+                const float f = (float)dg;
+                uint32_t u;
+                std::memcpy(&u, &f, 4);
+                const size_t off = (size_t)b * t->tcNp * t->tcKp * 2 + tc_kmajor_offset(k, m, t->tcKp);
+                Br[off / 2] = (uint16_t)(u >> 16);
+            }
+        }
+    }
     if (t->d_tcB.reserve(B.size()) != cudaSuccess || t->d_tcF.reserve(F.size()) != cudaSuccess ||
+        t->d_tcBr.reserve(Br.size()) != cudaSuccess || t->d_tcFr.reserve(Fr.size()) != cudaSuccess ||
+        cudaMemcpy(t->d_tcBr.p, Br.data(), Br.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_tcFr.p, Fr.data(), Fr.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         t->d_tcE.reserve(Ek.size()) != cudaSuccess ||
         cudaMemcpy(t->d_tcB.p, B.data(), B.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t->d_tcF.p, F.data(), F.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -285,6 +312,8 @@ RefTable* get_ref(sts_ctx* ctx, int d)
         t->d_tcB.release();
         t->d_tcF.release();
         t->d_tcE.release();
+        t->d_tcBr.release();
+        t->d_tcFr.release();
         delete t;
         set_error("uploading the degree-%d tensor-core table failed", d);
         return nullptr;

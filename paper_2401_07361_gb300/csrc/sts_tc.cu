@@ -2,8 +2,8 @@
 //
 // Each cluster's weights are W = diag(rho^d) V_ref^-T omega (the proxy-weight form of the PC
 // interaction, with omega_k = sum_j B_k(b_j) zeta_j A_j the SBB moments of Sec. 3.2).  The
-// contraction W'_m = sum_k omega_k Vinv[k][m] over a batch of 128 clusters is a dense
-// [128, M] x [M, M] product, run here as tcgen05.mma (kind::f16, BF16 operands, FP32
+// contraction W'_m = sum_k omega_k Vinv[k][m] over a batch of R clusters is a dense
+// [R, M] x [M, M] product (R <= 128), run here as tcgen05.mma (kind::f16, BF16 operands, FP32
 // accumulators in tensor memory).  V_ref^-1 has entries up to ~5e4 of alternating sign at d = 8
 // (cond(V_ref) ~ 3.5e5), so a plain FP32 or TF32 product loses the weights; the product is
 // instead made exact by splitting both operands into balanced 8-bit integer digits (the idea of
@@ -15,18 +15,21 @@
 // span several decades, to comparable sizes, so that the 32 bits kept of the largest hold
 // every moment's leading bits.  A product of digit matrices has integer entries of at most
 // 80 * 128^2 < 2^21, and the (at most four) products of one level L = a + b accumulate below
-// 2^24 in their own tensor-memory columns, so every FP32 sum is exact; the FP64 epilogue adds
-// the levels:  W'_m = 2^(G + F_m) sum_L 2^-8L D_L[m].
+// 2^24 in their own tensor-memory columns, so every FP32 sum is exact; the epilogue adds the
+// levels with TwoSum and scales:  W'_m = 2^(G + F_m) sum_L 2^-8L D_L[m].
 //
-// Layout: batches of 32 clusters (the MMA's 128 rows, the last 96 zero: the FP64 sums of the
-// moments then spread over ~125 SMs), batch b = clusters b, b + nb, b + 2 nb, ... of the nb
-// batches; persistent CTAs of 4 warps, one per SM; warp 0 reads the accumulators
-// (tensor-memory lanes 0 .. 31).  Operands in shared memory in the no-swizzle K-major layout of
-// 8 x 8 core matrices (K-adjacent core matrices 128 bytes apart, row groups Kp * 16 bytes
-// apart); the digit table of V_ref^-1 is precomputed on the host in that layout.  One thread
-// issues the MMAs and commits them to an mbarrier; the wait is bounded.  Every CTA holds all
-// 512 tensor-memory columns: a second CTA on the same SM waits in tcgen05.alloc until the first
-// releases them (the holder waits on nothing of the other, so the wait always ends).
+// Layout: persistent CTAs of 8 warps, one per SM, looping over batches of rows (the MMA's 128
+// rows; the upward pass fills 32 of them, so that its FP64 sums of the moments spread over
+// ~125 SMs, the interpolation coefficients 126: 42 clusters x 3 components).  Operands in shared
+// memory in the no-swizzle K-major layout of 8 x 8 core matrices (K-adjacent core matrices 128
+// bytes apart, row groups Kp * 16 bytes apart); the digit table of V_ref^-1 is precomputed on
+// the host in that layout.  The row maxima and the digits are taken from the bits of the FP64
+// values with integer arithmetic (FP64 runs at 1/64 of the FP32 rate here).  One thread issues
+// the MMAs and commits them to an mbarrier; the wait is bounded.  Warps w and w + 4 read
+// tensor-memory lanes 32 (w % 4) .. 32 (w % 4) + 31 and leave the level sums in shared memory;
+// all threads then write the outputs, coalesced.  Every CTA holds all 512 tensor-memory
+// columns: a second CTA on the same SM waits in tcgen05.alloc until the first releases them
+// (the holder waits on nothing of the other, so the wait always ends).
 #include <algorithm>
 
 #include "sts_internal.cuh"
@@ -35,9 +38,10 @@ namespace sts {
 namespace {
 
 constexpr int kTcRows = 128;                 // rows of the MMA (M)
-constexpr int kTcUsed = 32;                  // clusters per CTA (rows 32 .. 127 stay zero): the
-                                             // FP64 moment sums spread over more SMs
-constexpr int kTcThreads = 128;              // 4 warps
+constexpr int kTcUp = 32;                    // rows of a batch of the upward pass (rows 32 .. 127
+                                             // stay zero): its FP64 moment sums spread over more SMs
+constexpr int kTcThreads = 256;              // 8 warps
+constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kTcCols = 512;                 // tensor-memory columns held by a CTA
 constexpr int kTcASlices = 4;                // digits of omega
 constexpr int kTcLevels = kTcASlices + kTcSlices - 1;  // L = 2 .. 11
@@ -99,9 +103,6 @@ __device__ __forceinline__ uint16_t bf16_of_digit(float v) { return (uint16_t)(_
 
 // 2^e as a double (e in the normal range), built from its bits: no FP64 instruction.
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
-// The exponent e of frexp (x = f 2^e, 0.5 <= f < 1) of a normal double x != 0, from its bits.
-__device__ __forceinline__ int frexp_exp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1022; }
-
 // Knuth's TwoSum in FP32: hi + lo += x with the add's rounding error kept in lo.
 __device__ __forceinline__ void tc_two_sum(float& hi, float& lo, float x)
 {
@@ -111,26 +112,84 @@ __device__ __forceinline__ void tc_two_sum(float& hi, float& lo, float x)
     hi = s;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict__ toff,
-                   const double* __restrict__ part, int M, int Kp, const uint4* __restrict__ tcB,
-                   const int32_t* __restrict__ tcF, const int32_t* __restrict__ tcE, double* __restrict__ wout,
-                   const int64_t* __restrict__ nclu, int* __restrict__ status)
+// The two contractions run by the kernel below.  MODE 0, the upward pass: row = cluster,
+// A = the moments omega_k (summed from the moment pass's partial sums, scaled by 2^E[k]),
+// B = the columns of V_ref^-1, out W'[cluster, m] (FP64).  MODE 1, the dual traversal's
+// interpolation coefficients (c = V_ref^-1 diag(rho^d) U_T, Sec. 3.3 CP / CC): row = (cluster,
+// velocity component), A = rho_m^d U_m (the kernel sum at the proxy points, comparable values:
+// no scaling), B = the rows of V_ref^-1, out c[cluster, k] as FP32 (x, y, z, -) per k.
+struct TcArgs {
+    int M, Kp, R;  // R: rows of a batch (at most 128)
+    const uint4* tcB;
+    const int32_t* tcF;
+    const int32_t* tcE;
+    const int64_t* nclu;
+    int* status;
+    // MODE 0
+    const int32_t* cnode;
+    const int64_t* toff;
+    const double* part;
+    double* wout;
+    // MODE 1
+    const uint8_t* has;
+    const double* rd;
+    const double* cvel;
+    float* coef32;
+};
+
+// Round-half-even of x 2^s to an integer, from the bits of x (integer arithmetic: FP64
+// instructions are scarce on this part).  Equal to __double2ll_rn(x * 2^s) whenever x 2^s is
+// below 2^62 in magnitude.
+__device__ __forceinline__ long long round_scaled(double x, int s)
+{
+    const long long b = __double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = (unsigned long long)b & 0xFFFFFFFFFFFFFull;
+    if (e == 0) {
+        if (mant == 0) return 0;
+        e = 1;  // subnormal: no implicit bit
+    } else {
+        mant |= 1ull << 52;
+    }
+    const int sh = 1075 - e - s;  // |x| 2^s = mant 2^-sh
+    unsigned long long q;
+    if (sh <= 0) {
+        q = mant << (-sh);
+    } else if (sh >= 64) {
+        q = 0;  // below 2^-11: rounds to zero
+    } else {
+        q = mant >> sh;
+        const unsigned long long rem = mant & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1))) q++;
+    }
+    return b < 0 ? -(long long)q : (long long)q;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(const TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int64_t ncl = *nclu;
-    // batch b holds clusters b, b + nb, b + 2 nb, ... (nb batches): the few large clusters of
-    // the top levels, whose moments come in many partial sums, spread over the batches
-    const int64_t nb = (ncl + kTcUsed - 1) / kTcUsed;
+    const int M = a.M, Kp = a.Kp, R = a.R;
+    const uint4* __restrict__ tcB = a.tcB;
+    const int32_t* __restrict__ tcF = a.tcF;
+    int* status = a.status;
+    const int64_t ncl = *a.nclu;
+    // MODE 0: row r of batch b = cluster b + r nb.  MODE 1: rows 3j .. 3j + 2 of batch b = the
+    // three components of cluster b + j nb (j < R / 3).  Strided so that the few large clusters
+    // of the top levels spread over the batches.
+    const int per = MODE == 0 ? R : R / 3;
+    const int64_t nb = (ncl + per - 1) / per;
     if ((int64_t)blockIdx.x >= nb) return;  // the whole CTA: no batch for it
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Np = Kp;
     const unsigned aBytes = (unsigned)(kTcRows * Kp * 2), bBytes = (unsigned)(Np * Kp * 2);
     unsigned char* A = smem;                        // kTcASlices digit matrices [128, Kp]
     unsigned char* B = smem + kTcASlices * aBytes;  // kTcSlices digit matrices [Np, Kp]
-    double* om = reinterpret_cast<double*>(B + kTcSlices * bBytes);  // [kTcUsed, Kp] scaled moments
-    int* gexp = reinterpret_cast<int*>(om + kTcUsed * Kp);           // [kTcUsed] row exponents
-    uint64_t* bar = reinterpret_cast<uint64_t*>(gexp + kTcUsed);
+    double* om = reinterpret_cast<double*>(B + kTcSlices * bBytes);  // [R, Kp] the rows (FP64)
+    float* hs = reinterpret_cast<float*>(om);       // [Np, R + 1] the level sums (aliases om),
+    float* ls = hs + Np * (R + 1);                  // hi and lo of TwoSum
+    int* gexp = reinterpret_cast<int*>(om + (size_t)Kp * (R + 1));  // [R] row exponents
+    uint64_t* bar = reinterpret_cast<uint64_t*>(gexp + R);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
     if (warp == 0) {
@@ -146,7 +205,7 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
     // operand B: the digit table, already in the MMA layout
     const int nB = (int)(kTcSlices * bBytes / 16);
     for (int i = tid; i < nB; i += kTcThreads) reinterpret_cast<uint4*>(B)[i] = tcB[i];
-    // A's rows past the batch's clusters stay zero
+    // A's rows past the batch's R stay zero
     const int nA = (int)(kTcASlices * aBytes / 16);
     for (int i = tid; i < nA; i += kTcThreads) reinterpret_cast<uint4*>(A)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
@@ -157,43 +216,72 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
     unsigned phase = 0;
     // persistent CTAs: batches blockIdx.x, blockIdx.x + gridDim.x, ...
     for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x) {
-        // the moments: warp w sums rows w, w + 4, ... (lanes over k, coalesced over the partial
-        // sums), scales moment k by 2^E[k] and keeps the row's largest magnitude's exponent
-        for (int r = warp; r < kTcUsed; r += kTcThreads / 32) {
-            const int64_t c = bt + (int64_t)r * nb;
-            double mx = 0.0;
-            if (c < ncl) {
-                const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
-                for (int k = lane; k < Kp; k += 32) {
-                    double v = 0.0;
-                    if (k < M) {
-                        // four interleaved sums (their loads overlap), added in a fixed order
-                        double v4[4] = {0.0, 0.0, 0.0, 0.0};
+        if (MODE == 0) {
+            // the moments, warp w rows w, w + 8, ...: each from its partial sums (lanes over k,
+            // two k per lane, four interleaved sums each), scaled by 2^E[k] (exactly)
+            for (int r = warp; r < R; r += kTcWarps) {
+                const int64_t c = bt + (int64_t)r * nb;
+                for (int k0 = 0; k0 < Kp; k0 += 64) {
+                    const int ka = k0 + lane, kb = k0 + 32 + lane;
+                    const bool va = c < ncl && ka < M, vb = c < ncl && kb < M;
+                    double sa[4] = {0.0, 0.0, 0.0, 0.0}, sb[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (c < ncl) {
+                        const int64_t q0 = a.toff[a.cnode[c]], q1 = a.toff[a.cnode[c] + 1];
                         int64_t q = q0;
                         for (; q + 4 <= q1; q += 4) {
 #pragma unroll
-                            for (int u = 0; u < 4; u++) v4[u] += part[(q + u) * M + k];
+                            for (int u = 0; u < 4; u++) {
+                                if (va) sa[u] += a.part[(q + u) * M + ka];
+                                if (vb) sb[u] += a.part[(q + u) * M + kb];
+                            }
                         }
-                        for (int u = 0; q + u < q1; u++) v4[u] += part[(q + u) * M + k];
-                        v = ((v4[0] + v4[1]) + (v4[2] + v4[3])) * pow2d(tcE[k]);  // the scaling is exact
+                        for (int u = 0; q + u < q1; u++) {
+                            if (va) sa[u] += a.part[(q + u) * M + ka];
+                            if (vb) sb[u] += a.part[(q + u) * M + kb];
+                        }
                     }
-                    om[r * Kp + k] = v;
-                    mx = fmax(mx, fabs(v));
+                    if (ka < Kp) om[r * Kp + ka] = va ? ((sa[0] + sa[1]) + (sa[2] + sa[3])) * pow2d(a.tcE[ka]) : 0.0;
+                    if (kb < Kp) om[r * Kp + kb] = vb ? ((sb[0] + sb[1]) + (sb[2] + sb[3])) * pow2d(a.tcE[kb]) : 0.0;
                 }
-            } else {
-                for (int k = lane; k < Kp; k += 32) om[r * Kp + k] = 0.0;
             }
-    #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            // every scaled moment below 2^(G - 1): the leading digit stays in [-128, 128]
-            if (lane == 0) gexp[r] = mx > 0.0 ? frexp_exp(mx) + 1 : 0;
+        } else {
+            // rho_m^d (kept by the upward pass) times the kernel sum at proxy point m, the three
+            // components at once (rows 3j .. 3j + 2)
+            const int nj = R / 3;
+            for (int e = tid; e < nj * Kp; e += kTcThreads) {
+                const int j = e / Kp, m = e - j * Kp;
+                const int64_t cs = bt + (int64_t)j * nb;
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+                if (m < M && cs < ncl && a.has[cs]) {
+                    const int64_t o = cs * M + m;
+                    const double rd = a.rd[o];
+                    v0 = rd * a.cvel[3 * o];
+                    v1 = rd * a.cvel[3 * o + 1];
+                    v2 = rd * a.cvel[3 * o + 2];
+                }
+                om[(3 * j) * Kp + m] = v0;
+                om[(3 * j + 1) * Kp + m] = v1;
+                om[(3 * j + 2) * Kp + m] = v2;
+            }
+            for (int e = 3 * nj * Kp + tid; e < R * Kp; e += kTcThreads) om[e] = 0.0;
         }
         __syncthreads();
-        // operand A: 32 bits of each scaled moment as four balanced base-256 digits
-        for (int e = tid; e < kTcUsed * Kp; e += kTcThreads) {
+        // each row's largest magnitude (compared as bits: no FP64 instruction); every scaled
+        // value below 2^(G - 1), so the leading digit stays in [-128, 128]
+        for (int r = warp; r < R; r += kTcWarps) {
+            unsigned long long mx = 0;
+            for (int k = lane; k < Kp; k += 32)
+                mx = max(mx, (unsigned long long)__double_as_longlong(om[r * Kp + k]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) gexp[r] = mx != 0 ? (int)(mx >> 52) - 1021 : 0;
+        }
+        __syncthreads();
+        // operand A: 32 bits of each row value as four balanced base-256 digits
+        for (int e = tid; e < R * Kp; e += kTcThreads) {
             const int r = e / Kp, k = e - r * Kp;
-            long long T = __double2ll_rn(om[e] * pow2d(32 - gexp[r]));  // |T| <= 2^31, exact scaling
-            const long long s1 = (T + (1ll << 23)) >> 24;  // floor division: round to nearest
+            long long T = round_scaled(om[e], 32 - gexp[r]);  // |T| <= 2^31
+            const long long s1 = (T + (1ll << 23)) >> 24;     // floor division: round to nearest
             T -= s1 * (1ll << 24);
             const long long s2 = (T + (1ll << 15)) >> 16;
             T -= s2 * (1ll << 16);
@@ -205,7 +293,8 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
             *reinterpret_cast<uint16_t*>(A + 2 * aBytes + off) = bf16_of_digit((float)s3);
             *reinterpret_cast<uint16_t*>(A + 3 * aBytes + off) = bf16_of_digit((float)s4);
         }
-        // the operands' generic writes before the tensor cores read them (async proxy)
+        // the operands' generic writes before the tensor cores read them (async proxy); om is
+        // dead from here (hs / ls take its place)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
         __syncthreads();
@@ -217,12 +306,12 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
                     const int L = li + 2;
                     const uint32_t dcol = tmem + (uint32_t)((li - l0) * Np);
                     int acc = 0;
-                    for (int a = 1; a <= kTcASlices; a++) {
-                        const int b = L - a;
-                        if (b < 1 || b > kTcSlices) continue;
+                    for (int sa = 1; sa <= kTcASlices; sa++) {
+                        const int sb = L - sa;
+                        if (sb < 1 || sb > kTcSlices) continue;
                         for (int kk = 0; kk < Kp / 16; kk++) {
-                            const uint64_t ad = tc_desc(aBase + (unsigned)(a - 1) * aBytes + 256u * kk, 128u, sbo);
-                            const uint64_t bd = tc_desc(bBase + (unsigned)(b - 1) * bBytes + 256u * kk, 128u, sbo);
+                            const uint64_t ad = tc_desc(aBase + (unsigned)(sa - 1) * aBytes + 256u * kk, 128u, sbo);
+                            const uint64_t bd = tc_desc(bBase + (unsigned)(sb - 1) * bBytes + 256u * kk, 128u, sbo);
                             tc_mma(dcol, ad, bd, idesc, acc);
                             acc = 1;
                         }
@@ -245,15 +334,20 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
             }
             phase ^= 1u;
             tc_fence_after();
-            // epilogue, warp 0 (tensor-memory lanes 0 .. 31 hold the CTA's clusters): the levels
-            // added in FP32 with TwoSum (each D_L is an exact integer below 2^24, scaled exactly by
-            // 2^-8L), then W' = (hi + lo) 2^(G + F_m) in FP64
-            if (warp == 0) {
-                const int64_t c = bt + (int64_t)lane * nb;
-                for (int m0 = 0; m0 < Np; m0 += 16) {
-                    float hs[16], ls[16];
-    #pragma unroll
-                    for (int j = 0; j < 16; j++) hs[j] = ls[j] = 0.f;
+            // epilogue, first half: warps w and w + 4 read tensor-memory lanes 32 (w % 4) ..
+            // (rows of the batch), each half of the 16-column chunks, and add the levels in FP32
+            // with TwoSum (each D_L an exact integer below 2^24, scaled exactly by 2^-8L),
+            // carrying hi / lo over the rounds in shared memory
+            const int quarter = warp & 3, r = 32 * quarter + lane;
+            if (32 * quarter < R) {
+                const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);
+                for (int m0 = 16 * (warp >> 2); m0 < Np; m0 += 32) {
+                    float h[16], l[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        h[j] = (l0 > 0 && r < R) ? hs[(m0 + j) * (R + 1) + r] : 0.f;
+                        l[j] = (l0 > 0 && r < R) ? ls[(m0 + j) * (R + 1) + r] : 0.f;
+                    }
                     for (int li = l0; li < l1; li++) {
                         uint32_t v[16];
                         asm volatile(
@@ -262,30 +356,56 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
                               "=r"(v[14]), "=r"(v[15])
-                            : "r"(tmem + (uint32_t)((li - l0) * Np + m0)));
+                            : "r"(tlane + (uint32_t)((li - l0) * Np + m0)));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                         const float sc = __uint_as_float((uint32_t)(127 - 8 * (li + 2)) << 23);  // 2^-8L
-    #pragma unroll
-                        for (int j = 0; j < 16; j++) tc_two_sum(hs[j], ls[j], __uint_as_float(v[j]) * sc);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) tc_two_sum(h[j], l[j], __uint_as_float(v[j]) * sc);
                     }
-                    if (c < ncl) {
-    #pragma unroll
+                    if (r < R) {
+#pragma unroll
                         for (int j = 0; j < 16; j++) {
-                            const int m = m0 + j;
-                            if (m >= M) break;
-                            const int64_t o = c * M + m;
-                            const double w = ((double)hs[j] + (double)ls[j]) * pow2d(gexp[lane] + tcF[m]);
-                            wout[o] = l0 > 0 ? wout[o] + w : w;
+                            hs[(m0 + j) * (R + 1) + r] = h[j];
+                            ls[(m0 + j) * (R + 1) + r] = l[j];
                         }
                     }
                 }
             }
             // the loads of these columns (and the products' reads of A) come before the next
-            // round's products and the next batch's operand writes
+            // round's products and the next batch's operand writes; hs / ls complete
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
         }
+        // epilogue, second half (every thread, coalesced over m): the value 2^(G + F_m) (hi + lo)
+        if (MODE == 0) {
+            // W' in FP64
+            for (int e = tid; e < R * M; e += kTcThreads) {
+                const int r = e / M, m = e - r * M;
+                const int64_t c = bt + (int64_t)r * nb;
+                if (c < ncl) {
+                    const int o = m * (R + 1) + r;
+                    a.wout[c * M + m] = ((double)hs[o] + (double)ls[o]) * pow2d(gexp[r] + tcF[m]);
+                }
+            }
+        } else {
+            // the coefficients in FP32: hi + lo rounded once, then scaled exactly
+            const int nj = R / 3;
+            for (int e = tid; e < nj * M; e += kTcThreads) {
+                const int j = e / M, m = e - j * M;
+                const int64_t cs = bt + (int64_t)j * nb;
+                if (cs < ncl && a.has[cs]) {
+                    float* o = a.coef32 + 4 * (cs * M + m);
+#pragma unroll
+                    for (int comp = 0; comp < 3; comp++) {
+                        const int r = 3 * j + comp, i = m * (R + 1) + r;
+                        o[comp] = ldexpf(hs[i] + ls[i], gexp[r] + tcF[m]);
+                    }
+                }
+            }
+        }
+        // hs / ls read before the next batch's rows overwrite them
+        __syncthreads();
     }
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
@@ -295,25 +415,77 @@ k_proxy_weights_tc(const int32_t* __restrict__ cnode, const int64_t* __restrict_
 
 bool proxy_weights_tc_supported(int degree) { return (nbasis(degree) + 15) / 16 * 16 <= kTcMaxKp; }
 
-int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s)
+namespace {
+
+// Shared memory of a CTA with batches of R rows: the digit matrices, then the rows (FP64) /
+// level sums (hi, lo), then R row exponents, the mbarrier and the tensor-memory address.
+size_t tc_smem(int Kp, int R)
 {
-    const int Kp = ref->tcKp;
-    const size_t need = (size_t)kTcASlices * kTcRows * Kp * 2 + (size_t)kTcSlices * Kp * Kp * 2 +
-                        (size_t)kTcUsed * Kp * 8 + kTcUsed * 4 + 64;
-    const size_t sm = need;
+    return (size_t)kTcASlices * kTcRows * Kp * 2 + (size_t)kTcSlices * Kp * Kp * 2 + (size_t)Kp * (R + 1) * 8 +
+           (size_t)R * 4 + 16;
+}
+
+template <int MODE>
+int launch_tc(sts_ctx* c, TcArgs a, int64_t nclu_cap, cudaStream_t s)
+{
+    const int Kp = a.Kp;
+    if (MODE == 0) {
+        a.R = kTcUp;
+    } else {
+        // the largest batch the shared memory holds (three rows per cluster)
+        int optin = 0;
+        STS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        a.R = 126;
+        while (a.R > 3 && tc_smem(Kp, a.R) > (size_t)optin) a.R -= 30;
+    }
+    const size_t sm = tc_smem(Kp, a.R);
     if (!c->capturing)
-        STS_CUDA(cudaFuncSetAttribute(k_proxy_weights_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    // persistent: at most one CTA per SM, each looping over batches of 32 clusters (batch b:
-    // clusters b, b + nb, ...)
-    const int64_t batches = (nclu + kTcUsed - 1) / kTcUsed;
+        STS_CUDA(cudaFuncSetAttribute(k_tc_contract<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // persistent: at most one CTA per SM, each looping over its batches
+    const int per = MODE == 0 ? a.R : a.R / 3;
+    const int64_t batches = (nclu_cap + per - 1) / per;
     const unsigned g = (unsigned)std::min<int64_t>(batches, c->num_sms);
     if (g == 0) return STS_OK;
-    (k_proxy_weights_tc<<<g, kTcThreads, sm, s>>>(c->cluster_node.p, c->up_toff.p, c->up_part.p, ref->M, Kp,
-                                                  reinterpret_cast<const uint4*>(ref->d_tcB.p), ref->d_tcF.p,
-                                                  ref->d_tcE.p, wout, c->dc.p + kDcClusters, c->d_status),
-     note_launch());
+    (k_tc_contract<MODE><<<g, kTcThreads, sm, s>>>(a), note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
+}
+
+}  // namespace
+
+int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s)
+{
+    TcArgs a{};
+    a.M = ref->M;
+    a.Kp = ref->tcKp;
+    a.tcB = reinterpret_cast<const uint4*>(ref->d_tcB.p);
+    a.tcF = ref->d_tcF.p;
+    a.tcE = ref->d_tcE.p;
+    a.nclu = c->dc.p + kDcClusters;
+    a.status = c->d_status;
+    a.cnode = c->cluster_node.p;
+    a.toff = c->up_toff.p;
+    a.part = c->up_part.p;
+    a.wout = wout;
+    return launch_tc<0>(c, a, nclu, s);
+}
+
+int cluster_coef_tc(sts_ctx* c, const RefTable* ref, int degree, int64_t nclu, const double* cvel, float* coef32,
+                    cudaStream_t s)
+{
+    TcArgs a{};
+    a.M = ref->M;
+    a.Kp = ref->tcKp;
+    a.tcB = reinterpret_cast<const uint4*>(ref->d_tcBr.p);
+    a.tcF = ref->d_tcFr.p;
+    a.nclu = c->dc.p + kDcClusters;
+    a.status = c->d_status;
+    a.cnode = c->cluster_node.p;
+    a.has = c->chas.p;
+    a.rd = c->prx_rd.p;
+    a.cvel = cvel;
+    a.coef32 = coef32;
+    return launch_tc<1>(c, a, nclu, s);
 }
 
 }  // namespace sts

@@ -236,7 +236,8 @@ __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __r
                            const double* __restrict__ part, const double* __restrict__ geom,
                            const double* __restrict__ beta, const double* __restrict__ vinv, int d,
                            int M, double4* __restrict__ prx64, float4* __restrict__ prx32,
-                           const int64_t* __restrict__ nclu, const double* __restrict__ wtc)
+                           const int64_t* __restrict__ nclu, const double* __restrict__ wtc,
+                           double* __restrict__ prx_rd)
 {
     __shared__ double om[kMaxM + 3];
     const int64_t ncl = *nclu;
@@ -286,6 +287,7 @@ __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __r
             }
             double rd = 1.0;
             for (int e = 0; e < d; e++) rd *= rho;
+            prx_rd[c * M + m] = rd;
             const double W2 = 2.0 * (rd * acc);
             prx64[c * M + m] = make_double4(yx, yy, yz, W2);
             prx32[c * M + m] = make_float4((float)(yx - g[9]), (float)(yy - g[10]), (float)(yz - g[11]), (float)W2);
@@ -367,6 +369,7 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
     if (!cap) {
         STS_CUDA(c->prx64.reserve(nclu * M + 1));
         STS_CUDA(c->prx32.reserve(nclu * M + 1));
+        STS_CUDA(c->prx_rd.reserve(nclu * M + 1));
         STS_CUDA(c->up_part.reserve(nupt * M + 1));
     }
     if (nclu == 0 || nupt == 0) {
@@ -400,7 +403,7 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
     (precision == STS_FP64 ? k_contract<false> : k_contract<true>)<<<(unsigned)std::min<int64_t>(nclu, 16 * (int64_t)c->num_sms),
                                                                    64, 0, s>>>(
         c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M,
-        c->prx64.p, c->prx32.p, dc + kDcClusters, wtc);
+        c->prx64.p, c->prx32.p, dc + kDcClusters, wtc, c->prx_rd.p);
     note_launch();
     STS_LAUNCH_CHECK();
     c->up_degree = degree;
