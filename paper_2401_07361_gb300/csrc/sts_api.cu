@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); prx_rd.release(); scan_state.release(); scan_state_side.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); prx_rd.release(); scan_state.release(); scan_state_side.release(); bld_tot.release(); bld_bar.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
@@ -700,7 +700,7 @@ int sts_create(sts_ctx** out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 64 * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, (kDcSize + 16) * sizeof(int64_t));
     if (e == cudaSuccess) e = c->dc.reserve(sts::kDcSize);
     if (e == cudaSuccess) e = cudaMemset(c->dc.p, 0, sts::kDcSize * sizeof(int64_t));
     // inspection counters and the dual traversal's counters: allocated once here, so that

@@ -173,7 +173,7 @@ struct AmrState;  // adaptive mesh refinement of the particle triangulation (sts
 struct sts_ctx {
     int device = 0;
     int* d_status = nullptr;  // device status word
-    int64_t* h_pinned = nullptr;  // small pinned host staging buffer [64]
+    int64_t* h_pinned = nullptr;  // small pinned host staging buffer [kDcSize + 16]
 
     // ---- tree over the current positions -------------------------------------------
     int64_t n = 0;
@@ -315,6 +315,10 @@ struct sts_ctx {
     sts::DevBuf<double> prx_rd;               // [clusters, M] rho_m^d of each proxy point
     sts::DevBuf<int64_t> scan_state;          // single-pass scan state of the main stream
     sts::DevBuf<int64_t> scan_state_side;     // ... of the side stream (lists)
+    sts::DevBuf<int64_t> bld_tot;             // [CTAs] children per CTA of the level build
+    sts::DevBuf<unsigned> bld_bar;            // [1] grid-barrier arrivals of the level build
+    int build_grid = 0;                       // CTAs of the level build (all resident)
+    int64_t node_hint = 0;                    // node capacity that an eager build starts from
     bool timing = false;
     cudaEvent_t ev[sts::kNumPhases][2] = {};
     float phase_ms[sts::kNumPhases] = {};

@@ -22,7 +22,8 @@
 //   level 0   face of every particle (warp-aggregated counts); root nodes in face order.
 //   level l   split flags and child-digit normals per node; child digit per particle and
 //             child counts; child nodes numbered in key order (scan); particles move to
-//             their child.  The host reads the number of new nodes once per level.
+//             their child.  All levels run in one cooperative launch with grid-wide
+//             barriers between the passes; the host reads the counts once, at the end.
 //   sort      a stable radix sort by the first slot of each particle's leaf gives the
 //             sorted order (leaves depth first, original order inside a leaf).
 #include <stdio.h>
@@ -210,55 +211,122 @@ __global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node,
     if (i < n) nodeof[i] = face_node[nodeof[i]];
 }
 
-// ------------------------------------------------------------------------- level l
-// The level kernels read the node range of level l from the device array lvl: level l holds
-// nodes [lvl[l], lvl[l + 1]).  Node kernels stride over that range, so any grid size works
-// and the launches need no host-side count (the whole build can be captured in a graph).
-//
-// Level nodes, four lanes per node (the FP64 square roots and divisions are long dependent
-// chains, so the work of one node is spread): lane a < 3 forms the edge midpoint m_a and the
-// child-digit normal n_a = m_a x m_(a+2 mod 3); lane 3 the circumcentre and radius (levels
-// below the roots).  Leaves get norm32.w = -1 (no digits).
-__global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_size, int max_level,
-                              const int32_t* __restrict__ level, const int32_t* __restrict__ count,
-                              double* __restrict__ geom, int32_t* __restrict__ leaf,
-                              double* __restrict__ norm, float4* __restrict__ norm32, int32_t* __restrict__ cc,
-                              double* __restrict__ mid)
+// ------------------------------------------------------------------------- levels
+// All levels below the roots in one cooperative launch (every CTA resident): per level l,
+// with nodes [lb, le) = [lvl[l], lvl[l + 1]),
+//   nodes      split flags, edge midpoints and child-digit normals (four lanes per node);
+//   particles  the move of level l - 1 and the child digit at level l, counted per (node,
+//              digit);
+//   totals     the number of children of each CTA's contiguous share of the nodes;
+//   children   numbered in key order (the CTA's offset from the totals before it, a block scan
+//              inside), with vertices, start and count; lvl[l + 2] = end of level l + 1;
+// with a grid-wide barrier after each.  Every CTA computes the level's total itself, so all
+// of them see the same next range and stop at the same level: after a level that adds no
+// node, or after nlev levels (while recording: the planned depth plus one that must come out
+// empty).  The arithmetic of every decision is that of the per-level passes it replaces.
+constexpr int kBuildThreads = 256;
+constexpr int kPrivNodes = 256;       // levels with at most this many nodes count in shared memory
+constexpr int kBarSpins = 1 << 22;    // x 64 ns sleeps: a barrier gives up after ~0.3 s
+constexpr int kCcRep = 8;             // copies of the (node, digit) counters: CTA b adds to copy
+                                      // b % 8, so that each counter takes 8x fewer same-address
+                                      // atomics (they serialise in L2)
+
+struct BuildArgs {
+    int64_t* lvl;
+    const int64_t* nroots;
+    int nlev, leaf_size, max_level;
+    int64_t cap;  // node capacity
+    const double* pos;
+    int64_t n;
+    int32_t* nodeof;
+    uint8_t* digit;
+    int32_t *level, *parent, *first_child, *nchild, *start, *count, *leaf, *child;
+    int32_t* cc;        // kCcRep copies of [cap, 4], cc_stride apart
+    int64_t cc_stride;  // 4 cap
+    uint64_t* key;
+    double *geom, *norm, *mid;
+    float4 *norm32, *c32;
+    int64_t *over, *nnodes, *tot;
+    unsigned* bar;  // arrival counter, zeroed before the launch
+    int* status;
+};
+
+// Grid-wide barrier of a cooperative launch: barrier k of the launch ends when the arrival
+// counter reaches k G.  A CTA that waits too long flags the timeout and sets the counter's top
+// bit, which releases every CTA, now and at later barriers; all of them then return.
+__device__ bool grid_sync(unsigned* cnt, unsigned& k, int* status, int* s_ok)
 {
-    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    const int64_t nt = ((int64_t)4 * (le - lb) + 31) & ~(int64_t)31;  // whole warps (shuffles below)
-    const int lane = threadIdx.x & 31;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = lb + (int32_t)(t >> 2);
-        const int a = (int)(t & 3);
-        const bool valid = p < le;
-        bool split = false;
-        g3 m = gmk(0.0, 0.0, 0.0);
-        if (valid) {
-            double* g = geom + 13 * (int64_t)p;
-            split = count[p] > leaf_size && level[p] < max_level;
-            if (a == 3) {
-                if (l > 0) node_geometry(g, gld(g), gld(g + 3), gld(g + 6));  // roots: k_roots
-                leaf[p] = split ? 0 : 1;
-                if (split)
-                    cc[4 * p] = cc[4 * p + 1] = cc[4 * p + 2] = cc[4 * p + 3] = 0;
-                else
-                    norm32[3 * (int64_t)p] = make_float4(0.f, 0.f, 0.f, -1.f);  // w < 0: a leaf
-            } else if (split) {
-                // m_0 = unit(v1 + v2), m_1 = unit(v2 + v3), m_2 = unit(v3 + v1)
-                const g3 va = gld(g + 3 * a), vb = gld(g + 3 * (a == 2 ? 0 : a + 1));
-                m = gunit(gadd(va, vb));
-                gst(mid + 9 * (int64_t)p + 3 * a, m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        k++;
+        const unsigned target = k * gridDim.x;
+        __threadfence();  // this CTA's writes before its arrival
+        unsigned v = atomicAdd(cnt, 1u) + 1u;
+        for (int spins = 0; v < target; spins++) {
+            if (spins > kBarSpins) {
+                atomicOr(status, kStatusTimeout);
+                v = atomicOr(cnt, 0x80000000u) | 0x80000000u;
+                break;
             }
+            __nanosleep(64);
+            v = *(volatile unsigned*)cnt;
         }
-        // m_(a+2 mod 3) from lane a + 2 (a = 0) or a - 1 (a = 1, 2) of the same node
-        const int src = (lane & ~3) + (a == 0 ? 2 : a - 1);
-        const g3 mp = gmk(__shfl_sync(kFull, m.x, src), __shfl_sync(kFull, m.y, src), __shfl_sync(kFull, m.z, src));
-        if (valid && split && a < 3) {
-            const g3 nv = gcross(m, mp);
-            gst(norm + 9 * (int64_t)p + 3 * a, nv);
-            const float thr = 1e-6f * (float)(fabs(nv.x) + fabs(nv.y) + fabs(nv.z));
-            norm32[3 * (int64_t)p + a] = make_float4((float)nv.x, (float)nv.y, (float)nv.z, thr);
+        __threadfence();  // the others' writes after the release
+        *s_ok = (v & 0x80000000u) ? 0 : 1;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Level nodes.  The FP64 square roots and divisions are long dependent chains, so the work of
+// one node is spread over four lanes, and the two kinds of lane sit in different warps (no
+// divergence between them): in the first ceil(nl / 10) warps, lanes 3 j + a (j < 10, a < 3)
+// form the edge midpoint m_a of node 10 w + j and its child-digit normal n_a = m_a x
+// m_(a+2 mod 3); in the next ceil(nl / 32) warps, lane j takes node 32 w + j: circumcentre
+// and radius (levels below the roots), split flag, counters.  Leaves get norm32.w = -1.
+__device__ void level_nodes(const BuildArgs& a, int l, int32_t lb, int32_t le, int64_t gt, int64_t gs)
+{
+    const int32_t nl = le - lb;
+    const int64_t wm = (nl + 9) / 10, wc = (nl + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w = gt >> 5; w < wm + wc; w += gs >> 5) {
+        if (w < wm) {
+            const int j = lane / 3, q = lane - 3 * j;
+            const int32_t p = lb + (int32_t)(10 * w) + j;
+            const bool valid = lane < 30 && p < le;
+            const bool split = valid && a.count[p] > a.leaf_size && a.level[p] < a.max_level;
+            g3 m = gmk(0.0, 0.0, 0.0);
+            if (split) {
+                // m_0 = unit(v1 + v2), m_1 = unit(v2 + v3), m_2 = unit(v3 + v1)
+                const double* g = a.geom + 13 * (int64_t)p;
+                const g3 va = gld(g + 3 * q), vb = gld(g + 3 * (q == 2 ? 0 : q + 1));
+                m = gunit(gadd(va, vb));
+                gst(a.mid + 9 * (int64_t)p + 3 * q, m);
+            }
+            // m_(a+2 mod 3) from lane 3 j + 2 (a = 0) or 3 j + a - 1 (a = 1, 2)
+            const int src = 3 * j + (q == 0 ? 2 : q - 1);
+            const g3 mp =
+                gmk(__shfl_sync(kFull, m.x, src), __shfl_sync(kFull, m.y, src), __shfl_sync(kFull, m.z, src));
+            if (split) {
+                const g3 nv = gcross(m, mp);
+                gst(a.norm + 9 * (int64_t)p + 3 * q, nv);
+                const float thr = 1e-6f * (float)(fabs(nv.x) + fabs(nv.y) + fabs(nv.z));
+                a.norm32[3 * (int64_t)p + q] = make_float4((float)nv.x, (float)nv.y, (float)nv.z, thr);
+            }
+        } else {
+            const int32_t p = lb + (int32_t)(32 * (w - wm)) + lane;
+            if (p < le) {
+                double* g = a.geom + 13 * (int64_t)p;
+                const bool split = a.count[p] > a.leaf_size && a.level[p] < a.max_level;
+                if (l > 0) node_geometry(g, gld(g), gld(g + 3), gld(g + 6));  // roots: k_roots
+                a.leaf[p] = split ? 0 : 1;
+                if (split) {
+                    for (int r = 0; r < kCcRep; r++)
+                        *reinterpret_cast<int4*>(a.cc + r * a.cc_stride + 4 * (int64_t)p) = make_int4(0, 0, 0, 0);
+                } else {
+                    a.norm32[3 * (int64_t)p] = make_float4(0.f, 0.f, 0.f, -1.f);  // w < 0: a leaf
+                }
+            }
         }
     }
 }
@@ -268,48 +336,42 @@ __global__ void k_level_nodes(const int64_t* __restrict__ lvl, int l, int leaf_s
 // node if that node of level l splits (norm32.w >= 0), counted per (node, digit) in cc.  The
 // loads of one particle form two dependent rounds (node, then child and normals).  Levels with
 // at most kPrivNodes nodes count in shared memory first (one global add per counter and
-// block): there every counter takes thousands of increments, which serialise in L2.
-constexpr int kPrivNodes = 256;
-
-__global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const double* __restrict__ pos,
-                                  int64_t n, int32_t* __restrict__ nodeof, const double* __restrict__ norm,
-                                  const float4* __restrict__ norm32, const int32_t* __restrict__ child,
-                                  uint8_t* __restrict__ digit, int32_t* __restrict__ cc)
+// CTA): there every counter takes thousands of increments, which serialise in L2.
+__device__ void level_particles(const BuildArgs& a, int32_t pb, int32_t lb, int32_t le, int64_t gt, int64_t gs,
+                                int32_t* shc)
 {
-    __shared__ int32_t shc[4 * kPrivNodes];
-    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    const int32_t pb = l > 0 ? (int32_t)lvl[l - 1] : 0;
     const bool priv = le - lb <= kPrivNodes;
+    int32_t* cc = a.cc + (blockIdx.x % kCcRep) * a.cc_stride;  // this CTA's copy of the counters
     if (priv) {
         for (int k = threadIdx.x; k < 4 * (le - lb); k += blockDim.x) shc[k] = 0;
         __syncthreads();
     }
     // kPU particles per thread and trip, their loads issued together round by round
     constexpr int kPU = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n = a.n;
     const int64_t nr = (n + 31) & ~(int64_t)31;  // whole warps run every trip (warp-wide counting)
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nr; i0 += kPU * stride) {
+    for (int64_t i0 = gt; i0 < nr; i0 += kPU * gs) {
         int p[kPU], dg[kPU];
         float fx[kPU], fy[kPU], fz[kPU];
 #pragma unroll
         for (int u = 0; u < kPU; u++) {
-            const int64_t i = i0 + u * stride;
+            const int64_t i = i0 + u * gs;
             p[u] = -1;
             dg[u] = 0;
             fx[u] = fy[u] = fz[u] = 0.f;
             if (i < n) {
-                p[u] = nodeof[i];
-                dg[u] = digit[i];
-                fx[u] = (float)pos[3 * i];
-                fy[u] = (float)pos[3 * i + 1];
-                fz[u] = (float)pos[3 * i + 2];
+                p[u] = a.nodeof[i];
+                dg[u] = a.digit[i];
+                fx[u] = (float)a.pos[3 * i];
+                fy[u] = (float)a.pos[3 * i + 1];
+                fz[u] = (float)a.pos[3 * i + 2];
             }
         }
 #pragma unroll
         for (int u = 0; u < kPU; u++) {
             if (p[u] >= pb && p[u] < lb) {
-                p[u] = child[4 * p[u] + dg[u]];
-                nodeof[i0 + u * stride] = p[u];
+                p[u] = a.child[4 * p[u] + dg[u]];
+                a.nodeof[i0 + u * gs] = p[u];
             }
         }
         float4 q3[kPU][3];
@@ -317,31 +379,31 @@ __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const 
         for (int u = 0; u < kPU; u++) {
             const int64_t pp = p[u] >= lb ? p[u] : 0;
 #pragma unroll
-            for (int a = 0; a < 3; a++) q3[u][a] = norm32[3 * pp + a];
+            for (int q = 0; q < 3; q++) q3[u][q] = a.norm32[3 * pp + q];
         }
 #pragma unroll
         for (int u = 0; u < kPU; u++) {
-            const int64_t i = i0 + u * stride;
-            const bool active = p[u] >= lb && q3[u][0].w >= 0.f;
+            const int64_t i = i0 + u * gs;
+            const bool active = p[u] >= lb && p[u] < le && q3[u][0].w >= 0.f;
             int d = 0;
             if (active) {
                 const float scale = fmaxf(1.f, fmaxf(fabsf(fx[u]), fmaxf(fabsf(fy[u]), fabsf(fz[u]))));
                 // digit = first a with n_a . x >= 0, else 3; decided in FP32 while unambiguous
                 d = -1;
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
+                for (int q = 0; q < 3; q++) {
                     if (d != -1) continue;
-                    const float t = fdot(q3[u][a].x, q3[u][a].y, q3[u][a].z, fx[u], fy[u], fz[u]);
-                    const float thr = q3[u][a].w * scale;
+                    const float t = fdot(q3[u][q].x, q3[u][q].y, q3[u][q].z, fx[u], fy[u], fz[u]);
+                    const float thr = q3[u][q].w * scale;
                     if (t > thr)
-                        d = a;
+                        d = q;
                     else if (!(t < -thr))
                         d = -2;  // too close to this boundary for FP32
                 }
                 if (d == -1) d = 3;
                 if (d == -2) {
-                    const g3 x = gld(pos + 3 * i);
-                    const double* nn = norm + 9 * (int64_t)p[u];
+                    const g3 x = gld(a.pos + 3 * i);
+                    const double* nn = a.norm + 9 * (int64_t)p[u];
                     if (gdot(gld(nn), x) >= 0.0)
                         d = 0;
                     else if (gdot(gld(nn + 3), x) >= 0.0)
@@ -351,7 +413,7 @@ __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const 
                     else
                         d = 3;
                 }
-                digit[i] = (uint8_t)d;
+                a.digit[i] = (uint8_t)d;
             }
             if (priv)
                 agg_inc(shc, 4 * (p[u] - lb) + d, active);
@@ -366,101 +428,193 @@ __global__ void k_level_particles(const int64_t* __restrict__ lvl, int l, const 
     }
 }
 
-// Number of children of every node of level l (0 for leaves) into nch[p - lb]; nl = nodes.
-__global__ void k_level_nch(const int64_t* __restrict__ lvl, int l, const int32_t* __restrict__ leaf,
-                            const int32_t* __restrict__ cc, int32_t* __restrict__ nch, int64_t* __restrict__ nl)
+// Particles of node p per child digit: the sum of the counter copies.
+__device__ __forceinline__ int4 level_counts(const BuildArgs& a, int32_t p)
 {
-    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *nl = le - lb;
-    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
-         p += (int32_t)(gridDim.x * blockDim.x)) {
-        int c = 0;
-        if (!leaf[p])
-            for (int d = 0; d < 4; d++) c += cc[4 * p + d] > 0;
-        nch[p - lb] = c;
+    int4 c = make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int r = 0; r < kCcRep; r++) {
+        const int4 v = *reinterpret_cast<const int4*>(a.cc + r * a.cc_stride + 4 * (int64_t)p);
+        c.x += v.x;
+        c.y += v.y;
+        c.z += v.z;
+        c.w += v.w;
     }
+    return c;
 }
 
-// Children of level l numbered in key order from le = lvl[l + 1] on (off = scan of nch).
-// A child beyond the node capacity is not created: its particles stay with the parent and
-// the overflow bit is set, so a captured build reports it instead of writing out of range.
-__global__ void k_level_children(int64_t* __restrict__ lvl, int l, const int64_t* __restrict__ off,
-                                 const int64_t* __restrict__ nl, int64_t cap, const int32_t* __restrict__ cc, int32_t* level, uint64_t* key,
-                                 int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
-                                 int32_t* count, int32_t* leaf, double* geom, int32_t* __restrict__ child,
-                                 int64_t* __restrict__ over, const double* __restrict__ mid)
+// Number of children of node p of the current level (0 for a leaf).
+__device__ __forceinline__ int level_nch(const BuildArgs& a, int32_t p)
 {
-    const int32_t lb = (int32_t)lvl[l], le = (int32_t)lvl[l + 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[l + 2] = min((int64_t)le + off[*nl], cap);  // end of level l + 1
-    for (int32_t p = lb + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x); p < le;
-         p += (int32_t)(gridDim.x * blockDim.x)) {
-        if (leaf[p]) {
-            first_child[p] = -1;
-            nchild[p] = 0;
-            child[4 * p] = child[4 * p + 1] = child[4 * p + 2] = child[4 * p + 3] = p;
+    if (a.leaf[p]) return 0;
+    const int4 c = level_counts(a, p);
+    return (c.x > 0) + (c.y > 0) + (c.z > 0) + (c.w > 0);
+}
+
+// The children of node p, numbered from id on in digit order.  A child beyond the node
+// capacity is not created: its particles stay with the parent and the overflow bit is set, so
+// a recorded build reports it instead of writing out of range.
+__device__ void level_children(const BuildArgs& a, int32_t p, int64_t id64)
+{
+    if (a.leaf[p]) {
+        a.first_child[p] = -1;
+        a.nchild[p] = 0;
+        a.child[4 * p] = a.child[4 * p + 1] = a.child[4 * p + 2] = a.child[4 * p + 3] = p;
+        return;
+    }
+    const double* g = a.geom + 13 * (int64_t)p;
+    const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
+    const double* mm = a.mid + 9 * (int64_t)p;
+    const g3 m12 = gld(mm), m23 = gld(mm + 3), m31 = gld(mm + 6);
+    const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
+    int32_t id = (int32_t)min(id64, a.cap);
+    const int32_t first = id;
+    int32_t st = a.start[p];
+    const int32_t lv = a.level[p] + 1;
+    const uint64_t kp = a.key[p];
+    const int4 c4 = level_counts(a, p);
+    const int32_t cd[4] = {c4.x, c4.y, c4.z, c4.w};
+    int nc = 0;
+    for (int d = 0; d < 4; d++) {
+        const int32_t c = cd[d];
+        if (c == 0) {
+            a.child[4 * p + d] = -1;
             continue;
         }
-        const double* g = geom + 13 * (int64_t)p;
-        const g3 v1 = gld(g), v2 = gld(g + 3), v3 = gld(g + 6);
-        const double* mm = mid + 9 * (int64_t)p;
-        const g3 m12 = gld(mm), m23 = gld(mm + 3), m31 = gld(mm + 6);
-        const g3 cv[4][3] = {{v1, m12, m31}, {m12, v2, m23}, {m31, m23, v3}, {m12, m23, m31}};
-        int32_t id = le + (int32_t)off[p - lb];
-        const int32_t first = id;
-        int32_t st = start[p];
-        const int32_t lv = level[p] + 1;
-        const uint64_t kp = key[p];
-        int nc = 0;
-        for (int d = 0; d < 4; d++) {
-            const int32_t c = cc[4 * p + d];
-            if (c == 0) {
-                child[4 * p + d] = -1;
-                continue;
-            }
-            if (id >= cap) {
-                child[4 * p + d] = p;
-                atomicOr((unsigned long long*)over, 1ull);
-                st += c;
-                continue;
-            }
-            child[4 * p + d] = id;
-            level[id] = lv;
-            key[id] = kp * 4u + (uint64_t)d;
-            parent[id] = p;
-            first_child[id] = -1;
-            nchild[id] = 0;
-            start[id] = st;
-            count[id] = c;
-            leaf[id] = 0;
-            double* gc = geom + 13 * (int64_t)id;  // vertices; centre and radius in k_level_nodes
-            gst(gc, cv[d][0]);
-            gst(gc + 3, cv[d][1]);
-            gst(gc + 6, cv[d][2]);
+        if (id >= a.cap) {
+            a.child[4 * p + d] = p;
+            atomicOr((unsigned long long*)a.over, 1ull);
             st += c;
-            id++;
-            nc++;
+            continue;
         }
-        first_child[p] = nc ? first : -1;
-        nchild[p] = nc;
+        a.child[4 * p + d] = id;
+        a.level[id] = lv;
+        a.key[id] = kp * 4u + (uint64_t)d;
+        a.parent[id] = p;
+        a.first_child[id] = -1;
+        a.nchild[id] = 0;
+        a.start[id] = st;
+        a.count[id] = c;
+        a.leaf[id] = 0;
+        double* gc = a.geom + 13 * (int64_t)id;  // vertices; centre and radius with the next level
+        gst(gc, cv[d][0]);
+        gst(gc + 3, cv[d][1]);
+        gst(gc + 6, cv[d][2]);
+        st += c;
+        id++;
+        nc++;
     }
+    a.first_child[p] = nc ? first : -1;
+    a.nchild[p] = nc;
 }
 
-// After the level loop: nodes = lvl[last]; a last level that still produced children means
-// the build ran out of planned levels (overflow).
-__global__ void k_levels_done(const int64_t* __restrict__ lvl, int last, int64_t* __restrict__ nnodes,
-                              int64_t* __restrict__ over)
+// Exclusive scan of one value per thread over a CTA of kBuildThreads; *total = the CTA's sum.
+__device__ int64_t build_block_scan(int64_t v, int64_t* sh, int64_t* total)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    *nnodes = lvl[last];
-    if (lvl[last + 1] > lvl[last]) atomicOr((unsigned long long*)over, 2ull);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    int64_t before = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < kBuildThreads / 32; k++) {
+        const int64_t s = sh[k];
+        if (k < w) before += s;
+        all += s;
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
 }
 
-// Level range of the roots: lvl[0] = 0, lvl[1] = number of roots.
-__global__ void k_level0(int64_t* __restrict__ lvl, const int64_t* __restrict__ nroots)
+__global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs a)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        lvl[0] = 0;
-        lvl[1] = *nroots;
+    __shared__ int32_t shc[4 * kPrivNodes];
+    __shared__ int64_t sh[kBuildThreads / 32];
+    __shared__ int64_t s_before, s_total;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
+    const int G = (int)gridDim.x;
+    unsigned bk = 0;
+    int32_t pb = 0, lb = 0, le = (int32_t)*a.nroots;
+    if (blockIdx.x == 0 && tid == 0) {
+        a.lvl[0] = 0;
+        a.lvl[1] = le;
+    }
+    bool stopped = false;  // a level added no node
+    int32_t nn = 0;
+    for (int l = 0; l < a.nlev; l++) {
+        level_nodes(a, l, lb, le, gt, gs);
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        level_particles(a, pb, lb, le, gt, gs, shc);
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        // this CTA's share of the nodes and its number of children
+        const int32_t nl = le - lb;
+        const int32_t chunk = (nl + G - 1) / G;
+        const int32_t c0 = lb + min(nl, (int32_t)blockIdx.x * chunk), c1 = lb + min(nl, ((int32_t)blockIdx.x + 1) * chunk);
+        int64_t mine = 0;
+        for (int32_t p = c0 + tid; p < c1; p += blockDim.x) mine += level_nch(a, p);
+        int64_t cta_total;
+        build_block_scan(mine, sh, &cta_total);
+        if (tid == 0) a.tot[blockIdx.x] = cta_total;
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        // the children before this CTA's share and in the whole level
+        if (tid < 32) {
+            int64_t before = 0, total = 0;
+            for (int b = lane; b < G; b += 32) {
+                const int64_t v = a.tot[b];
+                total += v;
+                if (b < (int)blockIdx.x) before += v;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                before += __shfl_xor_sync(kFull, before, o);
+                total += __shfl_xor_sync(kFull, total, o);
+            }
+            if (lane == 0) {
+                s_before = before;
+                s_total = total;
+            }
+        }
+        __syncthreads();
+        const int32_t next = (int32_t)min((int64_t)le + s_total, a.cap);
+        if (blockIdx.x == 0 && tid == 0) a.lvl[l + 2] = next;  // end of level l + 1
+        int64_t carry = s_before;
+        for (int32_t r0 = c0; r0 < c1; r0 += blockDim.x) {
+            const int32_t p = r0 + tid;
+            const int k = p < c1 ? level_nch(a, p) : 0;
+            int64_t rtot;
+            const int64_t ex = build_block_scan(k, sh, &rtot);
+            if (p < c1) level_children(a, p, (int64_t)le + carry + ex);
+            carry += rtot;
+        }
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        if (next == le) {
+            stopped = true;
+            nn = le;
+            break;
+        }
+        pb = lb;
+        lb = le;
+        le = next;
+    }
+    // nodes = lvl[last level + 1]; a last planned level that still produced children means the
+    // build ran out of levels (overflow): its new nodes are not part of the tree
+    if (!stopped) nn = lb;
+    if (blockIdx.x == 0 && tid == 0) {
+        *a.nnodes = nn;
+        if (!stopped && le > lb) atomicOr((unsigned long long*)a.over, 2ull);
+    }
+    // FP32 copies of the node centres and radii for the pre-filtered MAC
+    for (int64_t p = gt; p < nn; p += gs) {
+        const double* g = a.geom + 13 * p;
+        a.c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
     }
 }
 
@@ -908,16 +1062,6 @@ __global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restric
 __global__ void k_copy_count(const int64_t* __restrict__ src, int64_t* __restrict__ dst)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
-}
-
-// FP32 copies of the node centres and radii for the pre-filtered MAC.
-__global__ void k_node_f32(const int64_t* __restrict__ nnodes, const double* __restrict__ geom,
-                           float4* __restrict__ c32)
-{
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *nnodes) return;
-    const double* g = geom + 13 * p;
-    c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
 }
 
 // Lanes sharing a pair of targets: the largest S <= 8 with S * pairs <= 32.
@@ -1406,7 +1550,7 @@ int grow_nodes(sts_ctx* c, int64_t need, int64_t keep, cudaStream_t s)
     STS_CUDA(c->nd_norm32.grow(3 * need, 3 * keep, s));
     STS_CUDA(c->nd_c32.grow(need, keep, s));
     STS_CUDA(c->nd_mid.grow(9 * need, 9 * keep, s));
-    STS_CUDA(c->nd_cc.grow(4 * need, 4 * keep, s));
+    STS_CUDA(c->nd_cc.grow((size_t)kCcRep * 4 * c->nd_level.cap, 0, s));  // copies 4 cap apart
     STS_CUDA(c->nd_child.grow(4 * need, 4 * keep, s));
     return STS_OK;
 }
@@ -1419,6 +1563,21 @@ void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const i
                    int64_t* out, cudaStream_t s)
 {
     (k_gather<<<1, 32, 0, s>>>(a, b, c, d, status, out), note_launch());
+}
+
+// Nodes a tree can have: the roots plus four children of every split node, where a level
+// holds at most n / (N_T + 1) split nodes (disjoint, each with more than N_T particles) and at
+// most 20 instances 4^l nodes.  Without `full`, the bound is capped at 12 n / (N_T + 1) more
+// than the roots (a first guess several times the node count of uniform data).
+static int64_t tree_node_bound(int64_t n, int ninst, int leaf_size, int max_level, bool full)
+{
+    const int64_t roots = 20 * (int64_t)ninst, per = n / ((int64_t)leaf_size + 1);
+    int64_t b = roots, w = roots;
+    for (int l = 0; l < max_level; l++) {
+        b += 4 * std::min(w, per);
+        w = std::min(w * 4, per + 1);
+    }
+    return full ? b + 64 : std::min(b, roots + 12 * per) + 64;
 }
 
 int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off, int ninst, int leaf_size,
@@ -1474,7 +1633,10 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_CUDA(c->counters.reserve(64));
     STS_CUDA(c->small.reserve(16));
     const int32_t nkeys = 20 * ninst;
-    if (grow_nodes(c, nkeys + 80, 0, s)) return STS_ERR_CUDA;
+    // node capacity: while recording, the planned one; eagerly an estimate, raised to the
+    // proven bound (and the build redone) if a level runs out of it
+    if (grow_nodes(c, c->capturing ? nkeys + 80 : std::max(c->node_hint, tree_node_bound(n, ninst, leaf_size, max_level, false)), 0, s))
+        return STS_ERR_CUDA;
     STS_CUDA(c->root_cnt.reserve(nkeys + 1));
     STS_CUDA(c->root_flag.reserve(nkeys + 1));
     STS_CUDA(c->face_node.reserve(nkeys + 1));
@@ -1500,82 +1662,103 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_LAUNCH_CHECK();
     (k_assign_roots<<<blocks(n, T), T, 0, s>>>(n, c->face_node.p, c->nodeof.p), note_launch());
     int64_t* dc = c->dc.p;
-    int64_t* lvl = dc + kDcLevel;
     const bool cap = c->capturing;  // recording a graph: no host reads, planned capacities
     if (!cap) STS_CUDA(cudaMemsetAsync(dc + kDcOver, 0, sizeof(int64_t), s));
-    (k_level0<<<1, 32, 0, s>>>(lvl, c->root_id.p + nkeys), note_launch());
-    int64_t lb = 0, le = 0;
+    // the levels: one cooperative launch (its CTAs wait on one another at grid-wide barriers)
+    if (c->build_grid == 0) {
+        int per_sm = 0;
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_levels, kBuildThreads, 0));
+        c->build_grid = std::max(1, std::min(per_sm, 4)) * c->num_sms;
+    }
+    STS_CUDA(c->bld_tot.reserve(c->build_grid));
+    STS_CUDA(c->bld_bar.reserve(1));
+    STS_CUDA(cudaMemsetAsync(c->bld_bar.p, 0, sizeof(unsigned), s));
+    BuildArgs a;
+    a.lvl = dc + kDcLevel;
+    a.nroots = c->root_id.p + nkeys;
+    // eagerly every level up to the depth limit (the last one never splits); while recording,
+    // the planned number of levels plus one that must come out empty
+    a.nlev = cap ? std::min(c->plan.depth + 2, max_level + 1) : max_level + 1;
+    a.leaf_size = leaf_size;
+    a.max_level = max_level;
+    a.cap = (int64_t)c->nd_level.cap;
+    a.pos = c->pos.p;
+    a.n = n;
+    a.nodeof = c->nodeof.p;
+    a.digit = c->digit.p;
+    a.level = c->nd_level.p;
+    a.parent = c->nd_parent.p;
+    a.first_child = c->nd_first_child.p;
+    a.nchild = c->nd_nchild.p;
+    a.start = c->nd_start.p;
+    a.count = c->nd_count.p;
+    a.leaf = c->nd_leaf.p;
+    a.cc = c->nd_cc.p;
+    a.cc_stride = 4 * (int64_t)c->nd_level.cap;
+    a.child = c->nd_child.p;
+    a.key = c->nd_key.p;
+    a.geom = c->nd_geom.p;
+    a.norm = c->nd_norm.p;
+    a.mid = c->nd_mid.p;
+    a.norm32 = c->nd_norm32.p;
+    a.c32 = c->nd_c32.p;
+    a.over = dc + kDcOver;
+    a.nnodes = dc + kDcNodes;
+    a.tot = c->bld_tot.p;
+    a.bar = c->bld_bar.p;
+    a.status = c->d_status;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)c->build_grid);
+        cfg.blockDim = dim3(kBuildThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        STS_CUDA(cudaLaunchKernelEx(&cfg, k_build_levels, a));
+        note_launch();
+    }
     if (!cap) {
-        (k_gather<<<1, 32, 0, s>>>(c->root_id.p + nkeys, nullptr, nullptr, nullptr, c->d_status, c->small.p),
-         note_launch());
-        STS_CUDA(cudaMemcpyAsync(c->h_pinned, c->small.p, 5 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        // one read of the counters: errors, node overflow (redo with the proven bound), levels
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, kDcSize * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        STS_CUDA(cudaMemcpyAsync(c->h_pinned + kDcSize, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
         STS_CUDA(cudaStreamSynchronize(s));
-        le = c->h_pinned[0];
-        if (c->h_pinned[4] & kStatusNonfinite) {
+        const int64_t* h = c->h_pinned;
+        const int st = ((const int32_t*)(h + kDcSize))[0];
+        if (st & (kStatusNonfinite | kStatusTimeout)) {
             STS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
-            set_error("sts_tree_build: non-finite position");
-            return STS_ERR_NONFINITE;
+            if (st & kStatusNonfinite) {
+                set_error("sts_tree_build: non-finite position");
+                return STS_ERR_NONFINITE;
+            }
+            set_error("sts_tree_build: a grid-wide barrier of the level build gave up");
+            return STS_ERR_TIMEOUT;
         }
-    }
-    // levels: eagerly until a level adds no node (one host read per level), or, while
-    // recording, the planned number of levels plus one that must come out empty
-    const int nlev = cap ? std::min(c->plan.depth + 2, max_level + 1) : max_level + 1;
-    const int64_t node_cap = cap ? (int64_t)c->nd_level.cap : 0;
-    const unsigned gnode = cap ? (unsigned)std::min<int64_t>(4096, (node_cap + T - 1) / T) : 0;
-    int level = 0, last = 0;
-    c->level_begin.assign(1, 0);
-    // particle passes: a few resident blocks per SM, each striding over many particles
-    const unsigned gpart = (unsigned)std::min<int64_t>(blocks(n, 4 * T), 4 * (int64_t)c->num_sms);
-    for (level = 0; level < nlev; level++) {
-        int64_t capn;
-        unsigned g;
-        if (!cap) {
-            c->level_begin.push_back(le);
-            const int64_t nl = le - lb;
-            if (grow_nodes(c, le + 4 * nl, le, s)) return STS_ERR_CUDA;
-            capn = (int64_t)c->nd_level.cap;
-            g = blocks(std::max<int64_t>(nl, 1), T);
-        } else {
-            capn = node_cap;
-            g = gnode;
+        if (h[kDcOver] & 1) {
+            const int64_t bound = tree_node_bound(n, ninst, leaf_size, max_level, true);
+            if (c->node_hint >= bound) {
+                set_error("sts_tree_build: node capacity %lld exhausted", (long long)bound);
+                return STS_ERR_CUDA;
+            }
+            c->node_hint = bound;
+            return tree_build(c, pos, n, inst_off, ninst, leaf_size, max_level, s);
         }
-        (k_level_nodes<<<cap ? gnode : blocks(4 * std::max<int64_t>(le - lb, 1), T), T, 0, s>>>(
-             lvl, level, leaf_size, max_level, c->nd_level.p, c->nd_count.p, c->nd_geom.p, c->nd_leaf.p,
-             c->nd_norm.p, c->nd_norm32.p, c->nd_cc.p, c->nd_mid.p), note_launch());
-        (k_level_particles<<<gpart, T, 0, s>>>(lvl, level, c->pos.p, n, c->nodeof.p, c->nd_norm.p,
-                                                      c->nd_norm32.p, c->nd_child.p, c->digit.p, c->nd_cc.p),
-         note_launch());
-        (k_level_nch<<<g, T, 0, s>>>(lvl, level, c->nd_leaf.p, c->nd_cc.p, c->flags.p, dc + kDcTmp),
-         note_launch());
-        exclusive_scan_i32(c->flags.p, c->offs.p, cap ? std::min<int64_t>(capn, n) : le - lb, c->scan_state, s,
-                           c->d_status, dc + kDcTmp);
-        (k_level_children<<<g, T, 0, s>>>(lvl, level, c->offs.p, dc + kDcTmp, capn, c->nd_cc.p, c->nd_level.p,
-                                          c->nd_key.p, c->nd_parent.p, c->nd_first_child.p, c->nd_nchild.p,
-                                          c->nd_start.p, c->nd_count.p, c->nd_leaf.p, c->nd_geom.p, c->nd_child.p,
-                                          dc + kDcOver, c->nd_mid.p), note_launch());
-        STS_LAUNCH_CHECK();
-        if (!cap) {
-            int64_t next = 0;
-            if (read_i64(c, lvl + level + 2, &next, s)) return STS_ERR_CUDA;
-            if (next == le) break;
-            lb = le;
-            le = next;
+        c->nnodes = h[kDcNodes];
+        c->level_begin.assign(1, 0);
+        c->deepest = 0;
+        for (int l = 1; l <= kMaxLevel + 2 && h[kDcLevel + l] > h[kDcLevel + l - 1]; l++) {
+            c->level_begin.push_back(h[kDcLevel + l]);
+            c->deepest = l - 1;
         }
-    }
-    last = cap ? nlev : level + 1;
-    (k_levels_done<<<1, 32, 0, s>>>(lvl, last, dc + kDcNodes, dc + kDcOver), note_launch());
-    if (!cap) {
-        c->nnodes = le;
-        c->deepest = level;
-        c->plan.nodes = std::max(c->plan.nodes, le);
-        c->plan.depth = std::max(c->plan.depth, level);
+        c->plan.nodes = std::max(c->plan.nodes, c->nnodes);
+        c->plan.depth = std::max(c->plan.depth, (int)c->deepest);
     } else {
         c->nnodes = -1;  // known after the graph runs
         c->deepest = -1;
     }
-    const int64_t nodes_grid = cap ? node_cap : c->nnodes;
-    (k_node_f32<<<blocks(std::max<int64_t>(nodes_grid, 1), T), T, 0, s>>>(dc + kDcNodes, c->nd_geom.p, c->nd_c32.p),
-     note_launch());
 
     phase_begin(c, kPhSort, s);
     (k_sort_keys<<<blocks(n, T), T, 0, s>>>(c->nodeof.p, n, c->nd_start.p, c->skey.p, c->perm.p), note_launch());
