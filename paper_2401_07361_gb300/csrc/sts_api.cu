@@ -86,7 +86,7 @@ sts_ctx::~sts_ctx()
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
     nd_key.release(); nd_geom.release(); nd_norm.release(); nd_mid.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
-    root_flag.release(); face_node.release(); root_id.release(); root_start.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
+    face_node.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
     up_frame32.release(); src_hl.release(); lw_terms.release(); rk_zf.release();
     prx64.release(); prx32.release(); src64.release(); src32.release(); far_off.release(); near_coff.release(); corr.release();

@@ -206,8 +206,7 @@ struct sts_ctx {
     sts::DevBuf<int32_t> counters;       // small device counters
     int ninst = 1;                       // instances in the forest
     sts::DevBuf<int64_t> inst_off;       // [ninst + 1] instance offsets (batched builds)
-    sts::DevBuf<int32_t> root_cnt, root_flag, face_node;  // [20 * ninst] per (instance, face)
-    sts::DevBuf<int64_t> root_id, root_start;             // [20 * ninst + 1] scans
+    sts::DevBuf<int32_t> root_cnt, face_node;  // [20 * ninst] per (instance, face)
     sts::DevBuf<int64_t> small;          // [16] values gathered for one host read
     sts::DevBuf<int64_t> dc;             // [kDcSize] device counters
     bool capturing = false;              // recording a graph: no host reads or allocations

@@ -111,104 +111,54 @@ __device__ __forceinline__ void agg_inc(int32_t* ctr, int key, bool active)
 }
 
 // ------------------------------------------------------------------------- level 0
-// Root key of every particle: instance b (from the instance offsets, b = 0 without them) times
-// 20 plus its face; counts per root key.  The key goes to rkey[i].
-__global__ void k_faces(const double* __restrict__ pos, int64_t n, const int64_t* __restrict__ inst_off,
-                        int32_t ninst, int32_t* __restrict__ rkey, int32_t* __restrict__ face_count,
+// Root key of a particle: instance b (from the instance offsets, b = 0 without them) times 20
+// plus its face (the first face maximising x . C_f; decided in FP32 while the FP32 winner
+// leads by more than twice the FP32 error, else in FP64).
+__device__ int root_key(const double* __restrict__ pos, int64_t i, const int64_t* __restrict__ inst_off, int ninst,
                         int* __restrict__ status)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < n;
-    int best = 0, rk = 0;
-    if (active) {
-        const g3 x = gld(pos + 3 * i);
-        if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
-        const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
-        float b1 = fdot(fx, fy, fz, c_fc32[0][0], c_fc32[0][1], c_fc32[0][2]), b2 = -3.f;
-        int fb = 0;
+    const g3 x = gld(pos + 3 * i);
+    if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
+    const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
+    float b1 = fdot(fx, fy, fz, c_fc32[0][0], c_fc32[0][1], c_fc32[0][2]), b2 = -3.f;
+    int fb = 0, best = 0;
 #pragma unroll 4
+    for (int f = 1; f < 20; f++) {
+        const float d = fdot(fx, fy, fz, c_fc32[f][0], c_fc32[f][1], c_fc32[f][2]);
+        if (d > b1) {
+            b2 = b1;
+            b1 = d;
+            fb = f;
+        } else if (d > b2) {
+            b2 = d;
+        }
+    }
+    const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
+    if (b1 - b2 > 4e-6f * scale) {
+        best = fb;
+    } else {
+        double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
         for (int f = 1; f < 20; f++) {
-            const float d = fdot(fx, fy, fz, c_fc32[f][0], c_fc32[f][1], c_fc32[f][2]);
-            if (d > b1) {
-                b2 = b1;
-                b1 = d;
-                fb = f;
-            } else if (d > b2) {
-                b2 = d;
+            const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
+            if (d > bd) {
+                bd = d;
+                best = f;
             }
         }
-        const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
-        if (b1 - b2 > 4e-6f * scale) {
-            best = fb;  // the FP32 winner leads by more than twice the FP32 error
-        } else {
-            double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
-            for (int f = 1; f < 20; f++) {
-                const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
-                if (d > bd) {
-                    bd = d;
-                    best = f;
-                }
-            }
-        }
-        int b = 0;
-        if (inst_off) {  // largest b with inst_off[b] <= i
-            int lo = 0, hi = ninst - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (inst_off[mid] <= i)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            b = lo;
-        }
-        rk = 20 * b + best;
-        rkey[i] = rk;
     }
-    agg_inc(face_count, rk, active);
-}
-
-// Root nodes for the non-empty (instance, face) keys in key order, one thread per key:
-// id = number of non-empty keys before it, start = number of particles before it.
-// face_node[key] = node id or -1.
-__global__ void k_roots(int32_t nkeys, const int32_t* __restrict__ face_count, const int64_t* __restrict__ rid,
-                        const int64_t* __restrict__ rstart, int32_t* __restrict__ face_node, int32_t* level,
-                        uint64_t* key, int32_t* parent, int32_t* first_child, int32_t* nchild, int32_t* start,
-                        int32_t* count, int32_t* leaf, double* geom)
-{
-    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (rk >= nkeys) return;
-    const int c = face_count[rk];
-    if (c == 0) {
-        face_node[rk] = -1;
-        return;
+    int b = 0;
+    if (inst_off) {  // largest b with inst_off[b] <= i
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst_off[mid] <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        b = lo;
     }
-    const int f = rk % 20;
-    const int32_t id = (int32_t)rid[rk];
-    face_node[rk] = id;
-    level[id] = 0;
-    key[id] = (uint64_t)rk;
-    parent[id] = -1;
-    first_child[id] = -1;
-    nchild[id] = 0;
-    start[id] = (int32_t)rstart[rk];
-    count[id] = c;
-    leaf[id] = 0;
-    node_geometry(geom + 13 * (int64_t)id, gmk(c_fv[f][0][0], c_fv[f][0][1], c_fv[f][0][2]),
-                  gmk(c_fv[f][1][0], c_fv[f][1][1], c_fv[f][1][2]),
-                  gmk(c_fv[f][2][0], c_fv[f][2][1], c_fv[f][2][2]));
-}
-
-__global__ void k_root_flags(int32_t nkeys, const int32_t* __restrict__ face_count, int32_t* __restrict__ flags)
-{
-    const int rk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (rk < nkeys) flags[rk] = face_count[rk] > 0 ? 1 : 0;
-}
-
-__global__ void k_assign_roots(int64_t n, const int32_t* __restrict__ face_node, int32_t* __restrict__ nodeof)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) nodeof[i] = face_node[nodeof[i]];
+    return 20 * b + best;
 }
 
 // ------------------------------------------------------------------------- levels
@@ -233,7 +183,10 @@ constexpr int kCcRep = 8;             // copies of the (node, digit) counters: C
 
 struct BuildArgs {
     int64_t* lvl;
-    const int64_t* nroots;
+    const int64_t* inst_off;  // instance offsets (NULL: one instance)
+    int ninst;
+    int32_t* face_count;      // [20 ninst] particles per root key, zeroed before the launch
+    int32_t* face_node;       // [20 ninst] root node of each key, or -1
     int nlev, leaf_size, max_level;
     int64_t cap;  // node capacity
     const double* pos;
@@ -246,7 +199,7 @@ struct BuildArgs {
     uint64_t* key;
     double *geom, *norm, *mid;
     float4 *norm32, *c32;
-    int64_t *over, *nnodes, *tot;
+    int64_t *over, *nnodes, *tot;  // tot: [2 CTAs] per-CTA totals
     unsigned* bar;  // arrival counter, zeroed before the launch
     int* status;
 };
@@ -279,12 +232,12 @@ __device__ bool grid_sync(unsigned* cnt, unsigned& k, int* status, int* s_ok)
 }
 
 // Level nodes.  The FP64 square roots and divisions are long dependent chains, so the work of
-// one node is spread over four lanes, and the two kinds of lane sit in different warps (no
-// divergence between them): in the first ceil(nl / 10) warps, lanes 3 j + a (j < 10, a < 3)
+// a node is spread over lanes: in the first ceil(nl / 10) warps, lanes 3 j + a (j < 10, a < 3)
 // form the edge midpoint m_a of node 10 w + j and its child-digit normal n_a = m_a x
-// m_(a+2 mod 3); in the next ceil(nl / 32) warps, lane j takes node 32 w + j: circumcentre
-// and radius (levels below the roots), split flag, counters.  Leaves get norm32.w = -1.
-__device__ void level_nodes(const BuildArgs& a, int l, int32_t lb, int32_t le, int64_t gt, int64_t gs)
+// m_(a+2 mod 3); in the next ceil(nl / 32) warps, lane j sets the split flag and clears the
+// counters of node 32 w + j (leaves get norm32.w = -1).  Circumcentres and radii, which no
+// later level needs, are left to one pass over all nodes after the last level.
+__device__ void level_nodes(const BuildArgs& a, int32_t lb, int32_t le, int64_t gt, int64_t gs)
 {
     const int32_t nl = le - lb;
     const int64_t wm = (nl + 9) / 10, wc = (nl + 31) / 32;
@@ -316,9 +269,7 @@ __device__ void level_nodes(const BuildArgs& a, int l, int32_t lb, int32_t le, i
         } else {
             const int32_t p = lb + (int32_t)(32 * (w - wm)) + lane;
             if (p < le) {
-                double* g = a.geom + 13 * (int64_t)p;
                 const bool split = a.count[p] > a.leaf_size && a.level[p] < a.max_level;
-                if (l > 0) node_geometry(g, gld(g), gld(g + 3), gld(g + 6));  // roots: k_roots
                 a.leaf[p] = split ? 0 : 1;
                 if (split) {
                     for (int r = 0; r < kCcRep; r++)
@@ -337,8 +288,8 @@ __device__ void level_nodes(const BuildArgs& a, int l, int32_t lb, int32_t le, i
 // loads of one particle form two dependent rounds (node, then child and normals).  Levels with
 // at most kPrivNodes nodes count in shared memory first (one global add per counter and
 // CTA): there every counter takes thousands of increments, which serialise in L2.
-__device__ void level_particles(const BuildArgs& a, int32_t pb, int32_t lb, int32_t le, int64_t gt, int64_t gs,
-                                int32_t* shc)
+__device__ void level_particles(const BuildArgs& a, int l, int32_t pb, int32_t lb, int32_t le, int64_t gt,
+                                int64_t gs, int32_t* shc)
 {
     const bool priv = le - lb <= kPrivNodes;
     int32_t* cc = a.cc + (blockIdx.x % kCcRep) * a.cc_stride;  // this CTA's copy of the counters
@@ -369,7 +320,10 @@ __device__ void level_particles(const BuildArgs& a, int32_t pb, int32_t lb, int3
         }
 #pragma unroll
         for (int u = 0; u < kPU; u++) {
-            if (p[u] >= pb && p[u] < lb) {
+            if (l == 0 && p[u] >= 0) {  // the root key becomes the root node
+                p[u] = a.face_node[p[u]];
+                a.nodeof[i0 + u * gs] = p[u];
+            } else if (p[u] >= pb && p[u] < lb) {
                 p[u] = a.child[4 * p[u] + dg[u]];
                 a.nodeof[i0 + u * gs] = p[u];
             }
@@ -536,23 +490,124 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
 {
     __shared__ int32_t shc[4 * kPrivNodes];
     __shared__ int64_t sh[kBuildThreads / 32];
-    __shared__ int64_t s_before, s_total;
+    __shared__ int64_t s_before, s_total, s_cbefore;
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
     const int G = (int)gridDim.x;
     unsigned bk = 0;
-    int32_t pb = 0, lb = 0, le = (int32_t)*a.nroots;
-    if (blockIdx.x == 0 && tid == 0) {
-        a.lvl[0] = 0;
-        a.lvl[1] = le;
+    // faces: the root key of every particle (into nodeof) and the particles per key
+    const int nkeys = 20 * a.ninst;
+    {
+        const bool priv = nkeys <= 4 * kPrivNodes;
+        if (priv) {
+            for (int k = tid; k < nkeys; k += blockDim.x) shc[k] = 0;
+            __syncthreads();
+        }
+        const int64_t nr = (a.n + 31) & ~(int64_t)31;  // whole warps (warp-wide counting)
+        for (int64_t i = gt; i < nr; i += gs) {
+            const bool active = i < a.n;
+            int rk = 0;
+            if (active) {
+                rk = root_key(a.pos, i, a.inst_off, a.ninst, a.status);
+                a.nodeof[i] = rk;
+            }
+            agg_inc(priv ? shc : a.face_count, rk, active);
+        }
+        if (priv) {
+            __syncthreads();
+            for (int k = tid; k < nkeys; k += blockDim.x)
+                if (shc[k]) atomicAdd(&a.face_count[k], shc[k]);
+        }
     }
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    // roots: the non-empty keys in key order, numbered by a scan over the CTAs' shares of the
+    // keys (id = non-empty keys before, start = particles before)
+    const int kchunk = (nkeys + G - 1) / G;
+    const int k0 = min(nkeys, (int)blockIdx.x * kchunk), k1 = min(nkeys, ((int)blockIdx.x + 1) * kchunk);
+    {
+        int64_t nf = 0, nc = 0;
+        for (int k = k0 + tid; k < k1; k += blockDim.x) {
+            const int c = a.face_count[k];
+            nf += c > 0;
+            nc += c;
+        }
+        int64_t tf, tc;
+        build_block_scan(nf, sh, &tf);
+        build_block_scan(nc, sh, &tc);
+        if (tid == 0) {
+            a.tot[2 * blockIdx.x] = tf;
+            a.tot[2 * blockIdx.x + 1] = tc;
+        }
+    }
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    int32_t pb = 0, lb = 0, le = 0;
+    {
+        if (tid < 32) {
+            int64_t bf = 0, bc = 0, tf = 0;
+            for (int b = lane; b < G; b += 32) {
+                const int64_t f = a.tot[2 * b], c = a.tot[2 * b + 1];
+                tf += f;
+                if (b < (int)blockIdx.x) {
+                    bf += f;
+                    bc += c;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                bf += __shfl_xor_sync(kFull, bf, o);
+                bc += __shfl_xor_sync(kFull, bc, o);
+                tf += __shfl_xor_sync(kFull, tf, o);
+            }
+            if (lane == 0) {
+                s_before = bf;
+                s_total = tf;
+                s_cbefore = bc;
+            }
+        }
+        __syncthreads();
+        int64_t cf = s_before, cc = s_cbefore;
+        le = (int32_t)s_total;
+        for (int r0 = k0; r0 < k1; r0 += blockDim.x) {
+            const int rk = r0 + tid;
+            const int c = rk < k1 ? a.face_count[rk] : 0;
+            int64_t rf, rc;
+            const int64_t ef = build_block_scan(c > 0, sh, &rf);
+            const int64_t ec = build_block_scan(c, sh, &rc);
+            if (rk < k1) {
+                if (c == 0) {
+                    a.face_node[rk] = -1;
+                } else {
+                    const int f = rk % 20;
+                    const int32_t id = (int32_t)(cf + ef);
+                    a.face_node[rk] = id;
+                    a.level[id] = 0;
+                    a.key[id] = (uint64_t)rk;
+                    a.parent[id] = -1;
+                    a.first_child[id] = -1;
+                    a.nchild[id] = 0;
+                    a.start[id] = (int32_t)(cc + ec);
+                    a.count[id] = c;
+                    a.leaf[id] = 0;
+                    double* g = a.geom + 13 * (int64_t)id;  // vertices; centre and radius after the levels
+                    for (int v = 0; v < 3; v++) gst(g + 3 * v, gmk(c_fv[f][v][0], c_fv[f][v][1], c_fv[f][v][2]));
+                }
+            }
+            cf += rf;
+            cc += rc;
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            a.lvl[0] = 0;
+            a.lvl[1] = le;
+        }
+    }
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
     bool stopped = false;  // a level added no node
     int32_t nn = 0;
     for (int l = 0; l < a.nlev; l++) {
-        level_nodes(a, l, lb, le, gt, gs);
+        level_nodes(a, lb, le, gt, gs);
         if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
-        level_particles(a, pb, lb, le, gt, gs, shc);
+        level_particles(a, l, pb, lb, le, gt, gs, shc);
         if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
         // this CTA's share of the nodes and its number of children
         const int32_t nl = le - lb;
@@ -611,9 +666,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
         *a.nnodes = nn;
         if (!stopped && le > lb) atomicOr((unsigned long long*)a.over, 2ull);
     }
-    // FP32 copies of the node centres and radii for the pre-filtered MAC
+    // circumcentres and radii of all nodes, with their FP32 copies for the pre-filtered MAC
     for (int64_t p = gt; p < nn; p += gs) {
-        const double* g = a.geom + 13 * p;
+        double* g = a.geom + 13 * p;
+        node_geometry(g, gld(g), gld(g + 3), gld(g + 6));
         a.c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
     }
 }
@@ -1638,44 +1694,32 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     if (grow_nodes(c, c->capturing ? nkeys + 80 : std::max(c->node_hint, tree_node_bound(n, ninst, leaf_size, max_level, false)), 0, s))
         return STS_ERR_CUDA;
     STS_CUDA(c->root_cnt.reserve(nkeys + 1));
-    STS_CUDA(c->root_flag.reserve(nkeys + 1));
     STS_CUDA(c->face_node.reserve(nkeys + 1));
-    STS_CUDA(c->root_id.reserve(nkeys + 1));
-    STS_CUDA(c->root_start.reserve(nkeys + 1));
-    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1) + scan_scratch(nkeys + 1)));
-    if (!c->capturing && scan_state_reserve(c->scan_state, std::max<int64_t>(std::max<int64_t>(hs, n + 1), nkeys + 1), s))
-        return STS_ERR_CUDA;
+    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
+    if (!c->capturing && scan_state_reserve(c->scan_state, std::max<int64_t>(hs, n + 1), s)) return STS_ERR_CUDA;
     c->ninst = ninst;
 
     const int T = 256;
-    int32_t* face_count = c->root_cnt.p;  // [20 * instances]
-    STS_CUDA(cudaMemsetAsync(face_count, 0, nkeys * sizeof(int32_t), s));
-    (k_faces<<<blocks(n, T), T, 0, s>>>(c->pos.p, n, inst_off, ninst, c->nodeof.p, face_count, c->d_status),
-     note_launch());
-    (k_root_flags<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_flag.p), note_launch());
-    exclusive_scan_i32(c->root_flag.p, c->root_id.p, nkeys, c->scan_state, s, c->d_status);
-    exclusive_scan_i32(face_count, c->root_start.p, nkeys, c->scan_state, s, c->d_status);
-    (k_roots<<<blocks(nkeys, T), T, 0, s>>>(nkeys, face_count, c->root_id.p, c->root_start.p, c->face_node.p,
-                                            c->nd_level.p, c->nd_key.p, c->nd_parent.p, c->nd_first_child.p,
-                                            c->nd_nchild.p, c->nd_start.p, c->nd_count.p, c->nd_leaf.p,
-                                            c->nd_geom.p), note_launch());
-    STS_LAUNCH_CHECK();
-    (k_assign_roots<<<blocks(n, T), T, 0, s>>>(n, c->face_node.p, c->nodeof.p), note_launch());
+    STS_CUDA(cudaMemsetAsync(c->root_cnt.p, 0, nkeys * sizeof(int32_t), s));
     int64_t* dc = c->dc.p;
     const bool cap = c->capturing;  // recording a graph: no host reads, planned capacities
     if (!cap) STS_CUDA(cudaMemsetAsync(dc + kDcOver, 0, sizeof(int64_t), s));
-    // the levels: one cooperative launch (its CTAs wait on one another at grid-wide barriers)
+    // faces, roots and levels: one cooperative launch (its CTAs wait on one another at grid-wide
+    // barriers)
     if (c->build_grid == 0) {
         int per_sm = 0;
         STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_levels, kBuildThreads, 0));
         c->build_grid = std::max(1, std::min(per_sm, 4)) * c->num_sms;
     }
-    STS_CUDA(c->bld_tot.reserve(c->build_grid));
+    STS_CUDA(c->bld_tot.reserve(2 * (size_t)c->build_grid));
     STS_CUDA(c->bld_bar.reserve(1));
     STS_CUDA(cudaMemsetAsync(c->bld_bar.p, 0, sizeof(unsigned), s));
     BuildArgs a;
     a.lvl = dc + kDcLevel;
-    a.nroots = c->root_id.p + nkeys;
+    a.inst_off = inst_off;
+    a.ninst = ninst;
+    a.face_count = c->root_cnt.p;
+    a.face_node = c->face_node.p;
     // eagerly every level up to the depth limit (the last one never splits); while recording,
     // the planned number of levels plus one that must come out empty
     a.nlev = cap ? std::min(c->plan.depth + 2, max_level + 1) : max_level + 1;
