@@ -440,9 +440,9 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->leaves.reserve(n + 1));
     STS_CUDA(c->wover.reserve(n + 1));
     STS_CUDA(c->corr.reserve(3 * n + 3));
-    STS_CUDA(c->scan_tmp.reserve(radix_hist_size(n) + 1 + scan_scratch(radix_hist_size(n)) + 2 * scan_scratch(big) + 64));
+    STS_CUDA(c->scan_tmp.reserve(2 * scan_scratch(big) + 64));
     // every scan a recorded step runs (capacities included) fits its stream's state
-    if (scan_state_reserve(c->scan_state, std::max<int64_t>(radix_hist_size(n), big) + 1, s) ||
+    if (scan_state_reserve(c->scan_state, big + 1, s) ||
         scan_state_reserve(c->scan_state_side, big + 1, s))
         return STS_ERR_CUDA;
     if (c->use_dual && (rc = reserve_dual_for_capture(c, p->degree, s))) return rc;

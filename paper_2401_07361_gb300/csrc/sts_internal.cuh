@@ -185,7 +185,7 @@ struct sts_ctx {
     sts::DevBuf<int32_t> perm, perm_tmp; // [n] sorted slot -> original index
     sts::DevBuf<uint32_t> skey, skey_tmp;// [n] sort keys
     sts::DevBuf<int64_t> scan_tmp;       // scan scratch
-    sts::DevBuf<uint32_t> hist;          // radix histograms
+    sts::DevBuf<uint32_t> hist;          // digit counts of the sort inside the tree build
     sts::DevBuf<int32_t> flags;          // [n + 1] scratch
     sts::DevBuf<int64_t> offs;           // [n + 1] scratch
     // node table (level by level, key order within a level)
@@ -352,7 +352,7 @@ int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout
 int cluster_coef_tc(sts_ctx* c, const RefTable* ref, int degree, int64_t nclu, const double* cvel, float* coef32,
                     cudaStream_t s);
 
-// ---- scans and sorting (sts_scan.cu) -----------------------------------------------
+// ---- scans (sts_scan.cu) ----------------------------------------------------------
 int64_t scan_scratch(int64_t n);
 // out[i] = sum_{j < i} in[j] for i in [0, n]; out[n] is the total: one single-pass launch.
 // state: the scan state of the stream it runs on (scans on one state run one after another),
@@ -363,14 +363,6 @@ int64_t scan_state_size(int64_t n);
 int scan_state_reserve(DevBuf<int64_t>& state, int64_t n, cudaStream_t s);
 void exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, DevBuf<int64_t>& state, cudaStream_t s,
                         const int* status, const int64_t* n_dev = nullptr);
-// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of key.  Result in
-// key/val; key_tmp/val_tmp are scratch of the same size; hist >= radix_hist_size(n); the
-// scan state must hold scan_state_size(radix_hist_size(n)).
-// n_dev: optional device count (n is then its upper bound and sizes the grids).
-int64_t radix_hist_size(int64_t n);
-void radix_sort_pairs(uint32_t* key, int32_t* val, uint32_t* key_tmp, int32_t* val_tmp,
-                      int64_t n, int bits, uint32_t* hist, int64_t* scan_out, DevBuf<int64_t>& state,
-                      const int* status, cudaStream_t s, const int64_t* n_dev = nullptr);
 
 // ---- tree and lists (sts_tree.cu) ----------------------------------------------------
 // inst_off: device offsets [ninst + 1] of the instances (NULL: one instance)

@@ -25,7 +25,8 @@
 //             their child.  All levels run in one cooperative launch with grid-wide
 //             barriers between the passes; the host reads the counts once, at the end.
 //   sort      a stable radix sort by the first slot of each particle's leaf gives the
-//             sorted order (leaves depth first, original order inside a leaf).
+//             sorted order (leaves depth first, original order inside a leaf), in the same
+//             launch; then the leaf list in slot order.
 #include <stdio.h>
 
 #include <algorithm>
@@ -175,6 +176,7 @@ __device__ int root_key(const double* __restrict__ pos, int64_t i, const int64_t
 // node, or after nlev levels (while recording: the planned depth plus one that must come out
 // empty).  The arithmetic of every decision is that of the per-level passes it replaces.
 constexpr int kBuildThreads = 256;
+constexpr int kBuildWarps = kBuildThreads / 32;
 constexpr int kPrivNodes = 256;       // levels with at most this many nodes count in shared memory
 constexpr int kBarSpins = 1 << 22;    // x 64 ns sleeps: a barrier gives up after ~0.3 s
 constexpr int kCcRep = 8;             // copies of the (node, digit) counters: CTA b adds to copy
@@ -202,6 +204,13 @@ struct BuildArgs {
     int64_t *over, *nnodes, *tot;  // tot: [2 CTAs] per-CTA totals
     unsigned* bar;  // arrival counter, zeroed before the launch
     int* status;
+    // the sorted order
+    int sort_passes;             // 8-bit digits of the slot keys
+    int32_t *perm, *perm_tmp;    // sorted position -> particle
+    uint32_t *skey, *skey_tmp;   // keys between passes
+    int32_t* hist;               // [256 CTAs + 256] digit counts per CTA, then per digit
+    int32_t *leaves, *slot_leaf;
+    int64_t* nleaves;
 };
 
 // Grid-wide barrier of a cooperative launch: barrier k of the launch ends when the arrival
@@ -489,6 +498,7 @@ __device__ int64_t build_block_scan(int64_t v, int64_t* sh, int64_t* total)
 __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs a)
 {
     __shared__ int32_t shc[4 * kPrivNodes];
+    __shared__ int32_t hw[kBuildWarps * 256];  // per-warp digit counts, then positions
     __shared__ int64_t sh[kBuildThreads / 32];
     __shared__ int64_t s_before, s_total, s_cbefore;
     __shared__ int s_ok;
@@ -672,36 +682,151 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
         node_geometry(g, gld(g), gld(g + 3), gld(g + 6));
         a.c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
     }
-}
 
-// ------------------------------------------------------------------------- sorting
-__global__ void k_sort_keys(const int32_t* __restrict__ nodeof, int64_t n,
-                            const int32_t* __restrict__ start, uint32_t* __restrict__ skey,
-                            int32_t* __restrict__ perm)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    skey[i] = (uint32_t)start[nodeof[i]];
-    perm[i] = (int32_t)i;
-}
-
-__global__ void k_leaf_flags(const int32_t* __restrict__ perm, const int32_t* __restrict__ nodeof,
-                             const int32_t* __restrict__ start, int64_t n, int32_t* __restrict__ flags)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    flags[k] = start[nodeof[perm[k]]] == (int32_t)k ? 1 : 0;
-}
-
-__global__ void k_leaf_list(const int32_t* __restrict__ perm, const int32_t* __restrict__ nodeof,
-                            const int32_t* __restrict__ flags, const int64_t* __restrict__ off,
-                            int64_t n, int32_t* __restrict__ leaves, int32_t* __restrict__ slot_leaf)
-{
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int64_t li = off[k] + flags[k] - 1;
-    slot_leaf[k] = (int32_t)li;
-    if (flags[k]) leaves[li] = nodeof[perm[k]];
+    // ---- the sorted order: a stable LSD radix sort (8-bit digits) of the particles by the
+    // first slot of their leaf, which keeps the particles of a leaf in their original order.
+    // CTA b owns items [i0, i1) of every pass, its warp w the w-th part of them, so the rank of
+    // an item among equal digits follows (CTA, warp, round, lane), i.e. the item order.
+    const int64_t n = a.n;
+    const int64_t ich = (n + G - 1) / G;
+    const int64_t i0 = min(n, (int64_t)blockIdx.x * ich), i1 = min(n, i0 + ich);
+    const int w = tid >> 5;
+    const int64_t wch = (i1 - i0 + kBuildWarps - 1) / kBuildWarps;
+    const int64_t w0 = min(i1, i0 + w * wch), w1 = min(i1, w0 + wch);
+    const int P = a.sort_passes;
+    const unsigned lt = (1u << lane) - 1u;
+    if (P == 0) {  // a single particle
+        if (gt < n) a.perm[gt] = (int32_t)gt;
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    }
+    for (int pass = 0; pass < P; pass++) {
+        const int shift = 8 * pass;
+        // pass p writes the main buffers when P - 1 - p is even, so the last one ends there;
+        // pass 0 takes its keys from the tree
+        uint32_t* kout = ((P - 1 - pass) & 1) ? a.skey_tmp : a.skey;
+        int32_t* vout = ((P - 1 - pass) & 1) ? a.perm_tmp : a.perm;
+        const uint32_t* kin = ((P - pass) & 1) ? a.skey_tmp : a.skey;
+        const int32_t* vin = ((P - pass) & 1) ? a.perm_tmp : a.perm;
+        // digit counts per warp; this CTA's entry of every digit's row
+        for (int k = tid; k < kBuildWarps * 256; k += blockDim.x) hw[k] = 0;
+        __syncthreads();
+        for (int64_t i = w0 + lane; i < w1; i += 32) {
+            const uint32_t key = pass == 0 ? (uint32_t)a.start[a.nodeof[i]] : kin[i];
+            atomicAdd(&hw[w * 256 + (int)((key >> shift) & 255u)], 1);
+        }
+        __syncthreads();
+        for (int d = tid; d < 256; d += blockDim.x) {
+            int t = 0;
+            for (int ww = 0; ww < kBuildWarps; ww++) t += hw[ww * 256 + d];
+            a.hist[d * G + blockIdx.x] = t;
+        }
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        // rows d = b, b + G, ...: exclusive offsets along the row (over the CTAs), row totals
+        for (int d = blockIdx.x; d < 256; d += G) {
+            int64_t carry = 0;
+            for (int r0 = 0; r0 < G; r0 += blockDim.x) {
+                const int j = r0 + tid;
+                const int v = j < G ? a.hist[d * G + j] : 0;
+                int64_t rt;
+                const int64_t ex = build_block_scan(v, sh, &rt);
+                if (j < G) a.hist[d * G + j] = (int32_t)(carry + ex);
+                carry += rt;
+            }
+            if (tid == 0) a.hist[256 * G + d] = (int32_t)carry;
+        }
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        // the first position of each (digit, warp): digit base + CTA offset + earlier warps
+        for (int d0 = 0; d0 < 256; d0 += blockDim.x) {
+            const int d = d0 + tid;
+            int64_t tot;
+            const int64_t base = build_block_scan(d < 256 ? a.hist[256 * G + d] : 0, sh, &tot);
+            if (d < 256) {
+                int run = (int)base + a.hist[d * G + blockIdx.x];
+                for (int ww = 0; ww < kBuildWarps; ww++) {
+                    const int c = hw[ww * 256 + d];
+                    hw[ww * 256 + d] = run;
+                    run += c;
+                }
+            }
+        }
+        __syncthreads();
+        // scatter, 32 consecutive items per round: rank among equal digits of the round
+        const bool lastp = pass == P - 1;
+        for (int64_t i = w0; i < w1; i += 32) {
+            const int64_t ii = i + lane;
+            const bool valid = ii < w1;
+            uint32_t key = 0;
+            int32_t val = 0;
+            if (valid) {
+                if (pass == 0) {
+                    key = (uint32_t)a.start[a.nodeof[ii]];
+                    val = (int32_t)ii;
+                } else {
+                    key = kin[ii];
+                    val = vin[ii];
+                }
+            }
+            const int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;
+            const unsigned peers = __match_any_sync(kFull, d);
+            const int rk = __popc(peers & lt), cnt = __popc(peers);
+            const int prior = valid ? hw[w * 256 + d] : 0;
+            __syncwarp();
+            if (valid && rk == cnt - 1) hw[w * 256 + d] = prior + cnt;
+            __syncwarp();
+            if (valid) {
+                if (!lastp) kout[prior + rk] = key;
+                vout[prior + rk] = val;
+            }
+        }
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    }
+    // ---- the leaves in slot order: slot k starts a leaf when it is its leaf's first slot;
+    // slot_leaf = index of the slot's leaf (a scan over the CTAs' shares of the slots)
+    {
+        int64_t mine = 0;
+        for (int64_t k = i0 + tid; k < i1; k += blockDim.x) mine += a.start[a.nodeof[a.perm[k]]] == (int32_t)k;
+        int64_t t;
+        build_block_scan(mine, sh, &t);
+        if (tid == 0) a.tot[blockIdx.x] = t;
+    }
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    if (tid < 32) {
+        int64_t before = 0, total = 0;
+        for (int b = lane; b < G; b += 32) {
+            const int64_t v = a.tot[b];
+            total += v;
+            if (b < (int)blockIdx.x) before += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(kFull, before, o);
+            total += __shfl_xor_sync(kFull, total, o);
+        }
+        if (lane == 0) {
+            s_before = before;
+            s_total = total;
+        }
+    }
+    __syncthreads();
+    int64_t carry = s_before;
+    for (int64_t r0 = i0; r0 < i1; r0 += blockDim.x) {
+        const int64_t k = r0 + tid;
+        int f = 0;
+        int32_t node = 0;
+        if (k < i1) {
+            node = a.nodeof[a.perm[k]];
+            f = a.start[node] == (int32_t)k;
+        }
+        int64_t rt;
+        const int64_t ex = build_block_scan(f, sh, &rt);
+        if (k < i1) {
+            const int64_t li = carry + ex + f - 1;
+            a.slot_leaf[k] = (int32_t)li;
+            if (f) a.leaves[li] = node;
+        }
+        carry += rt;
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.nleaves = s_total;
 }
 
 // ------------------------------------------------------------------------- lists
@@ -1115,20 +1240,16 @@ __global__ void k_list_totals(int64_t* __restrict__ dc, const int64_t* __restric
     dc[kDcTasks] = t;
 }
 
-__global__ void k_copy_count(const int64_t* __restrict__ src, int64_t* __restrict__ dst)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
-}
 
 // Lanes sharing a pair of targets: the largest S <= 8 with S * pairs <= 32.
 __device__ __forceinline__ int lanes_per_pair(int pairs) { return min(8, 32 / pairs); }
 
-// Splits a leaf of nt targets into k warp tasks of nearly equal size, two targets per lane
-// and S lanes per pair of targets.  k maximises the fraction of useful interactions per warp
-// step, nt S / (64 k) (ties go to the smaller k).
-__device__ int task_split(int nt)
+// Splits a leaf of nt targets into k warp tasks of nearly equal size, at most tmax targets
+// each, two targets per lane and S lanes per pair of targets.  k maximises the fraction of
+// useful interactions per warp step, nt S / (64 k) (ties go to the smaller k).
+__device__ int task_split(int nt, int tmax)
 {
-    const int kmin = max(1, (nt + kTaskTargets - 1) / kTaskTargets);
+    const int kmin = max(1, (nt + tmax - 1) / tmax);
     int best = kmin;
     float be = -1.f;
     for (int k = kmin; k <= kmin + 3; k++) {
@@ -1146,12 +1267,12 @@ __device__ int task_split(int nt)
 
 // Counts the warp tasks of every leaf by lane class (S = 1 .. 8) into cls[0..7].
 __global__ void k_task_count(const int64_t* __restrict__ nleaves, int64_t ldc, const int32_t* __restrict__ leaves,
-                             const int32_t* __restrict__ count, unsigned long long* __restrict__ cls)
+                             const int32_t* __restrict__ count, int tmax, unsigned long long* __restrict__ cls)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= min(*nleaves, ldc)) return;
     const int32_t c = count[leaves[L]];
-    const int k = task_split(c);
+    const int k = task_split(c, tmax);
     for (int i = 0; i < k; i++) atomicAdd(cls + lanes_per_pair((c / k + (i < c % k ? 1 : 0) + 1) / 2) - 1, 1ull);
 }
 
@@ -1161,8 +1282,8 @@ __global__ void k_task_count(const int64_t* __restrict__ nleaves, int64_t ldc, c
 // is arbitrary; every task writes only its own targets, so the results do not depend on it.
 __global__ void k_task_fill(const int64_t* __restrict__ nleaves, int64_t ldc, const int32_t* __restrict__ leaves,
                             const int32_t* __restrict__ start, const int32_t* __restrict__ count,
-                            const int64_t* __restrict__ cls, unsigned long long* __restrict__ fill, int64_t cap,
-                            Task* __restrict__ tasks, int64_t* __restrict__ over)
+                            int tmax, const int64_t* __restrict__ cls, unsigned long long* __restrict__ fill,
+                            int64_t cap, Task* __restrict__ tasks, int64_t* __restrict__ over)
 {
     const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= min(*nleaves, ldc)) return;
@@ -1172,7 +1293,7 @@ __global__ void k_task_fill(const int64_t* __restrict__ nleaves, int64_t ldc, co
     for (int q = 1; q < 8; q++) base[q] = base[q - 1] + cls[q - 1];
     const int32_t id = leaves[L];
     const int32_t st = start[id], c = count[id];
-    const int k = task_split(c);
+    const int k = task_split(c, tmax);
     int32_t t0 = 0;
     for (int i = 0; i < k; i++) {
         const int32_t m = c / k + (i < c % k ? 1 : 0);
@@ -1532,7 +1653,7 @@ __global__ void k_cluster_tasks(const int64_t* __restrict__ dc, int64_t ccap, co
     const bool h = cfar_off[c + 1] > cfar_off[c] || cnear_off[c + 1] > cnear_off[c];
     has[c] = h ? 1 : 0;
     if (!h) return;
-    const int k = task_split(M);
+    const int k = task_split(M, kTaskTargets);
     const int64_t base = (int64_t)atomicAdd((unsigned long long*)(du + kDuCTasks), (unsigned long long)k);
     int32_t t0 = 0;
     for (int i = 0; i < k; i++) {
@@ -1683,9 +1804,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     STS_CUDA(c->flags.reserve(n + 1));
     STS_CUDA(c->offs.reserve(n + 1));
     STS_CUDA(c->slot_leaf.reserve(n));
-    const int64_t hs = radix_hist_size(n);
-    STS_CUDA(c->hist.reserve(hs));
-    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
+    STS_CUDA(c->leaves.reserve(n + 1));
     STS_CUDA(c->counters.reserve(64));
     STS_CUDA(c->small.reserve(16));
     const int32_t nkeys = 20 * ninst;
@@ -1695,8 +1814,6 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         return STS_ERR_CUDA;
     STS_CUDA(c->root_cnt.reserve(nkeys + 1));
     STS_CUDA(c->face_node.reserve(nkeys + 1));
-    STS_CUDA(c->scan_tmp.reserve(hs + 1 + scan_scratch(hs) + scan_scratch(n + 1)));
-    if (!c->capturing && scan_state_reserve(c->scan_state, std::max<int64_t>(hs, n + 1), s)) return STS_ERR_CUDA;
     c->ninst = ninst;
 
     const int T = 256;
@@ -1712,6 +1829,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         c->build_grid = std::max(1, std::min(per_sm, 4)) * c->num_sms;
     }
     STS_CUDA(c->bld_tot.reserve(2 * (size_t)c->build_grid));
+    STS_CUDA(c->hist.reserve(256 * (size_t)c->build_grid + 256));
     STS_CUDA(c->bld_bar.reserve(1));
     STS_CUDA(cudaMemsetAsync(c->bld_bar.p, 0, sizeof(unsigned), s));
     BuildArgs a;
@@ -1751,6 +1869,17 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.tot = c->bld_tot.p;
     a.bar = c->bld_bar.p;
     a.status = c->d_status;
+    int bits = 0;
+    while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
+    a.sort_passes = (bits + 7) / 8;
+    a.perm = c->perm.p;
+    a.perm_tmp = c->perm_tmp.p;
+    a.skey = c->skey.p;
+    a.skey_tmp = c->skey_tmp.p;
+    a.hist = (int32_t*)c->hist.p;
+    a.leaves = c->leaves.p;
+    a.slot_leaf = c->slot_leaf.p;
+    a.nleaves = dc + kDcLeaves;
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)c->build_grid);
@@ -1804,24 +1933,19 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         c->deepest = -1;
     }
 
-    phase_begin(c, kPhSort, s);
-    (k_sort_keys<<<blocks(n, T), T, 0, s>>>(c->nodeof.p, n, c->nd_start.p, c->skey.p, c->perm.p), note_launch());
-    int bits = 0;
-    while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
-    int64_t* scan_out = c->scan_tmp.p;
-    radix_sort_pairs(c->skey.p, c->perm.p, c->skey_tmp.p, c->perm_tmp.p, n, bits, c->hist.p,
-                     scan_out, c->scan_state, c->d_status, s);
-    (k_leaf_flags<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->nd_start.p, n, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, n, c->scan_state, s, c->d_status);
-    (k_copy_count<<<1, 32, 0, s>>>(c->offs.p + n, c->dc.p + kDcLeaves), note_launch());
-    STS_CUDA(c->leaves.reserve(n + 1));
-    (k_leaf_list<<<blocks(n, T), T, 0, s>>>(c->perm.p, c->nodeof.p, c->flags.p, c->offs.p, n,
-                                           c->leaves.p, c->slot_leaf.p), note_launch());
-    STS_LAUNCH_CHECK();
-    phase_end(c, kPhSort, s);
     c->nleaves = -1;  // set by build_clusters
     c->have_tree = true;
     return STS_OK;
+}
+
+// Targets per warp task: kTaskTargets, or fewer for small problems, where tasks of 64 targets
+// would leave most of the evaluation kernel's resident warps (16 per SM) idle: about two tasks
+// per resident warp, at least 8 targets per task (four pairs of eight lanes), a multiple of 8.
+static int task_targets(const sts_ctx* c)
+{
+    const int64_t warps = 16 * (int64_t)c->num_sms;
+    const int64_t want = (c->n + 2 * warps - 1) / (2 * warps);
+    return (int)std::min<int64_t>(kTaskTargets, std::max<int64_t>(8, (want + 7) / 8 * 8));
 }
 
 int build_lists(sts_ctx* c, double theta, cudaStream_t s)
@@ -1869,7 +1993,7 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
     exclusive_scan_i32(c->list_cnt.p + 2 * L, chunk_po, L, c->scan_state_side, s, c->d_status, dc + kDcLeaves);
     // evaluation tasks: each leaf's targets split into warp tasks
     STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
-    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
+    (k_task_count<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p, task_targets(c),
                                   (unsigned long long*)(dc + kDcClass)), note_launch());
     (k_list_totals<<<1, 32, 0, s>>>(dc, far_po, near_po, chunk_po, L), note_launch());
     STS_LAUNCH_CHECK();
@@ -1910,9 +2034,9 @@ int build_lists(sts_ctx* c, double theta, cudaStream_t s)
                              chunk_po, c->far_idx.p, c->near_idx.p, c->far_ent.p, c->near_ent.p,
                              (int64_t)c->far_ent.cap, (int64_t)c->near_idx.cap, (int64_t)c->near_ent.cap, L,
                              c->wover.p, c->d_status, dc + kDcOver), note_launch());
-    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
-                                 (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
-                                 dc + kDcOver), note_launch());
+    (k_task_fill<<<g, T, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, task_targets(c),
+                                 dc + kDcClass, (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap,
+                                 c->tasks.p, dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
     c->list_theta = theta;
     c->have_lists = true;
@@ -1988,7 +2112,7 @@ static int reserve_dual(sts_ctx* c, const DualCaps& k, int64_t L, int64_t C, int
     STS_CUDA(c->cnear_coff.reserve(C + 1));
     STS_CUDA(c->cfar_ent.reserve(k.cc));
     STS_CUDA(c->cnear_ent.reserve(k.cp_chunks));
-    STS_CUDA(c->tasks.reserve(c->n / kTaskTargets + 4 * L + 64));  // task_split's bound per leaf
+    STS_CUDA(c->tasks.reserve(c->n / task_targets(c) + 4 * L + 64));  // task_split's bound per leaf
     STS_CUDA(c->chas.reserve(C + 1));
     return STS_OK;
 }
@@ -2066,12 +2190,12 @@ static int launch_dual(sts_ctx* c, double theta, int levels, int64_t L, int64_t 
     // evaluation tasks of the target leaves (as for the leaf lists) and the list totals
     const unsigned g = blocks(std::max<int64_t>(L, 1), 128);
     STS_CUDA(cudaMemsetAsync(dc + kDcClass, 0, 16 * sizeof(int64_t), s));
-    (k_task_count<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p,
+    (k_task_count<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_count.p, task_targets(c),
                                     (unsigned long long*)(dc + kDcClass)), note_launch());
     (k_list_totals<<<1, 32, 0, s>>>(dc, c->far_off.p, c->near_off.p, c->near_coff.p, L), note_launch());
-    (k_task_fill<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, dc + kDcClass,
-                                   (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap, c->tasks.p,
-                                   dc + kDcOver), note_launch());
+    (k_task_fill<<<g, 128, 0, s>>>(dc + kDcLeaves, L, c->leaves.p, c->nd_start.p, c->nd_count.p, task_targets(c),
+                                   dc + kDcClass, (unsigned long long*)(dc + kDcClassFill), (int64_t)c->tasks.cap,
+                                   c->tasks.p, dc + kDcOver), note_launch());
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
