@@ -84,7 +84,7 @@ sts_ctx::~sts_ctx()
     skey.release(); skey_tmp.release(); scan_tmp.release(); hist.release(); flags.release();
     offs.release(); nd_level.release(); nd_parent.release(); nd_first_child.release();
     nd_nchild.release(); nd_start.release(); nd_count.release(); nd_leaf.release();
-    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_mid.release(); nd_norm32.release(); nd_c32.release(); nd_cc.release(); nd_child.release();
+    nd_key.release(); nd_geom.release(); nd_norm.release(); nd_mid.release(); nd_norm32.release(); nd_c32.release(); posf.release(); nd_cc.release(); nd_child.release();
     counters.release(); small.release(); dc.release(); inst_off.release(); root_cnt.release();
     face_node.release(); leaves.release(); slot_leaf.release(); cluster_slot.release();
     cluster_node.release(); up_toff.release(); up_tasks.release(); up_part.release(); up_frame.release();
@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); prx_rd.release(); scan_state.release(); scan_state_side.release(); bld_tot.release(); bld_bar.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); prx_rd.release(); scan_state.release(); scan_state_side.release(); bld_tot.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();

@@ -201,12 +201,14 @@ struct sts_ctx {
     int num_sms = 1;                                  // SMs of the context's device (sts_create)
     int eval_blocks_mixed = 0, eval_blocks_fp64 = 0;  // resident blocks of the persistent eval kernels
     sts::DevBuf<float4> nd_c32;          // [nodes]: circumcentre and chord radius in FP32
+    sts::DevBuf<float4> posf;            // [n]: positions rounded to FP32 (tree build)
     sts::DevBuf<int32_t> nd_cc;          // [nodes,4]: child counts by digit (scratch)
     sts::DevBuf<int32_t> nd_child;       // [nodes,4]: child id by digit (scratch)
     sts::DevBuf<int32_t> counters;       // small device counters
     int ninst = 1;                       // instances in the forest
     sts::DevBuf<int64_t> inst_off;       // [ninst + 1] instance offsets (batched builds)
-    sts::DevBuf<int32_t> root_cnt, face_node;  // [20 * ninst] per (instance, face)
+    sts::DevBuf<int32_t> root_cnt, face_node;  // [20 * ninst] per (instance, face); root_cnt[20 * ninst]
+                                               // is the tree build's grid-barrier counter
     sts::DevBuf<int64_t> small;          // [16] values gathered for one host read
     sts::DevBuf<int64_t> dc;             // [kDcSize] device counters
     bool capturing = false;              // recording a graph: no host reads or allocations
@@ -315,7 +317,6 @@ struct sts_ctx {
     sts::DevBuf<int64_t> scan_state;          // single-pass scan state of the main stream
     sts::DevBuf<int64_t> scan_state_side;     // ... of the side stream (lists)
     sts::DevBuf<int64_t> bld_tot;             // [CTAs] children per CTA of the level build
-    sts::DevBuf<unsigned> bld_bar;            // [1] grid-barrier arrivals of the level build
     int build_grid = 0;                       // CTAs of the level build (all resident)
     int64_t node_hint = 0;                    // node capacity that an eager build starts from
     bool timing = false;

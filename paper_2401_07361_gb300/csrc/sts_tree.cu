@@ -90,6 +90,21 @@ __device__ __forceinline__ float fdot(float ax, float ay, float az, float bx, fl
     return fmaf(az, bz, fmaf(ay, by, ax * bx));
 }
 
+// x rounded to the nearest FP32 value (ties to even), from its bits with integer arithmetic
+// (conversions run on GB300's narrow FP64 path); zero, and values outside FP32's normal range,
+// take the conversion instruction.
+__device__ __forceinline__ float f32_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    unsigned q = (unsigned)(m >> 29);
+    const unsigned long long r = m & ((1ull << 29) - 1), half = 1ull << 28;
+    q += (r > half || (r == half && (q & 1u))) ? 1u : 0u;  // a carry into the exponent is exact
+    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) + ((unsigned)(e - 1023 + 127) << 23) + q);
+}
+
 __device__ void node_geometry(double* g, g3 v1, g3 v2, g3 v3)
 {
     gst(g, v1);
@@ -113,37 +128,47 @@ __device__ __forceinline__ void agg_inc(int32_t* ctr, int key, bool active)
 
 // ------------------------------------------------------------------------- level 0
 // Root key of a particle: instance b (from the instance offsets, b = 0 without them) times 20
-// plus its face (the first face maximising x . C_f; decided in FP32 while the FP32 winner
-// leads by more than twice the FP32 error, else in FP64).
+// plus its face (the first face maximising x . C_f).  The dots are taken in FP32; the FP32
+// winner stands when it leads by more than twice the FP32 error, else FP64 decides among the
+// faces within that margin of the FP32 maximum (any other face is below the FP64 maximum, so
+// the first FP64 maximiser is the same as over all 20).
 __device__ int root_key(const double* __restrict__ pos, int64_t i, const int64_t* __restrict__ inst_off, int ninst,
-                        int* __restrict__ status)
+                        float4* __restrict__ posf, int* __restrict__ status)
 {
     const g3 x = gld(pos + 3 * i);
     if (!isfinite(x.x) || !isfinite(x.y) || !isfinite(x.z)) atomicOr(status, kStatusNonfinite);
-    const float fx = (float)x.x, fy = (float)x.y, fz = (float)x.z;
-    float b1 = fdot(fx, fy, fz, c_fc32[0][0], c_fc32[0][1], c_fc32[0][2]), b2 = -3.f;
+    const float fx = f32_rn(x.x), fy = f32_rn(x.y), fz = f32_rn(x.z);
+    posf[i] = make_float4(fx, fy, fz, 0.f);
+    float df[20];
+#pragma unroll
+    for (int f = 0; f < 20; f++) df[f] = fdot(fx, fy, fz, c_fc32[f][0], c_fc32[f][1], c_fc32[f][2]);
+    float b1 = df[0], b2 = -3.f;
     int fb = 0, best = 0;
-#pragma unroll 4
+#pragma unroll
     for (int f = 1; f < 20; f++) {
-        const float d = fdot(fx, fy, fz, c_fc32[f][0], c_fc32[f][1], c_fc32[f][2]);
-        if (d > b1) {
+        if (df[f] > b1) {
             b2 = b1;
-            b1 = d;
+            b1 = df[f];
             fb = f;
-        } else if (d > b2) {
-            b2 = d;
+        } else if (df[f] > b2) {
+            b2 = df[f];
         }
     }
     const float scale = fmaxf(1.f, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
-    if (b1 - b2 > 4e-6f * scale) {
+    const float margin = 4e-6f * scale;
+    if (b1 - b2 > margin) {
         best = fb;
     } else {
-        double bd = gdot(x, gmk(c_fc[0][0], c_fc[0][1], c_fc[0][2]));
-        for (int f = 1; f < 20; f++) {
+        double bd = 0.0;
+        bool any = false;
+#pragma unroll
+        for (int f = 0; f < 20; f++) {
+            if (!(df[f] >= b1 - margin)) continue;
             const double d = gdot(x, gmk(c_fc[f][0], c_fc[f][1], c_fc[f][2]));
-            if (d > bd) {
+            if (!any || d > bd) {
                 bd = d;
                 best = f;
+                any = true;
             }
         }
     }
@@ -191,7 +216,9 @@ struct BuildArgs {
     int32_t* face_node;       // [20 ninst] root node of each key, or -1
     int nlev, leaf_size, max_level;
     int64_t cap;  // node capacity
-    const double* pos;
+    const double* pos_in;  // the caller's positions, copied into pos by the faces pass
+    double* pos;
+    float4* posf;  // [n] the positions rounded to FP32 (written with the faces, read by the levels)
     int64_t n;
     int32_t* nodeof;
     uint8_t* digit;
@@ -322,9 +349,10 @@ __device__ void level_particles(const BuildArgs& a, int l, int32_t pb, int32_t l
             if (i < n) {
                 p[u] = a.nodeof[i];
                 dg[u] = a.digit[i];
-                fx[u] = (float)a.pos[3 * i];
-                fy[u] = (float)a.pos[3 * i + 1];
-                fz[u] = (float)a.pos[3 * i + 2];
+                const float4 q = a.posf[i];
+                fx[u] = q.x;
+                fy[u] = q.y;
+                fz[u] = q.z;
             }
         }
 #pragma unroll
@@ -519,8 +547,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
             const bool active = i < a.n;
             int rk = 0;
             if (active) {
-                rk = root_key(a.pos, i, a.inst_off, a.ninst, a.status);
+                rk = root_key(a.pos_in, i, a.inst_off, a.ninst, a.posf, a.status);
+                for (int q = 0; q < 3; q++) a.pos[3 * i + q] = a.pos_in[3 * i + q];
                 a.nodeof[i] = rk;
+                a.digit[i] = 0;  // a particle whose root is a leaf moves to child[4 p + 0] = p
             }
             agg_inc(priv ? shc : a.face_count, rk, active);
         }
@@ -1790,13 +1820,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         STS_CUDA(cudaMemcpyToSymbolAsync(c_fc32, C32, sizeof(C32), 0, cudaMemcpyHostToDevice, s));
     }
     STS_CUDA(c->pos.reserve(3 * n));
-    STS_CUDA(cudaMemcpyAsync(c->pos.p, pos, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     STS_CUDA(c->nodeof.reserve(n));
+    STS_CUDA(c->posf.reserve(n));
     STS_CUDA(c->digit.reserve(n));
-    // the particle pass moves every particle of a node of the previous level to child[4 p +
-    // digit]; a particle whose root is a leaf never gets a digit written, so it must read a
-    // valid one (0: a leaf's child table points at the leaf itself)
-    if (n > 0) STS_CUDA(cudaMemsetAsync(c->digit.p, 0, n * sizeof(uint8_t), s));
     STS_CUDA(c->perm.reserve(n));
     STS_CUDA(c->perm_tmp.reserve(n));
     STS_CUDA(c->skey.reserve(n));
@@ -1817,7 +1843,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     c->ninst = ninst;
 
     const int T = 256;
-    STS_CUDA(cudaMemsetAsync(c->root_cnt.p, 0, nkeys * sizeof(int32_t), s));
+    // the per-key counts and, right after them, the grid barrier's arrival counter: one memset
+    STS_CUDA(cudaMemsetAsync(c->root_cnt.p, 0, (nkeys + 1) * sizeof(int32_t), s));
     int64_t* dc = c->dc.p;
     const bool cap = c->capturing;  // recording a graph: no host reads, planned capacities
     if (!cap) STS_CUDA(cudaMemsetAsync(dc + kDcOver, 0, sizeof(int64_t), s));
@@ -1830,8 +1857,6 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     }
     STS_CUDA(c->bld_tot.reserve(2 * (size_t)c->build_grid));
     STS_CUDA(c->hist.reserve(256 * (size_t)c->build_grid + 256));
-    STS_CUDA(c->bld_bar.reserve(1));
-    STS_CUDA(cudaMemsetAsync(c->bld_bar.p, 0, sizeof(unsigned), s));
     BuildArgs a;
     a.lvl = dc + kDcLevel;
     a.inst_off = inst_off;
@@ -1844,7 +1869,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.leaf_size = leaf_size;
     a.max_level = max_level;
     a.cap = (int64_t)c->nd_level.cap;
+    a.pos_in = pos;
     a.pos = c->pos.p;
+    a.posf = c->posf.p;
     a.n = n;
     a.nodeof = c->nodeof.p;
     a.digit = c->digit.p;
@@ -1867,7 +1894,7 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.over = dc + kDcOver;
     a.nnodes = dc + kDcNodes;
     a.tot = c->bld_tot.p;
-    a.bar = c->bld_bar.p;
+    a.bar = reinterpret_cast<unsigned*>(c->root_cnt.p + nkeys);
     a.status = c->d_status;
     int bits = 0;
     while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
