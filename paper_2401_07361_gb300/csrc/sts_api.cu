@@ -294,7 +294,6 @@ int build_impl(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
 {
     phase_begin(c, kPhBuild, s);
     int rc = tree_build(c, pos, n, inst_off, ninst, p->leaf_size, p->max_level, s);
-    if (rc == STS_OK && n > 0) rc = build_clusters(c, s);
     phase_end(c, kPhBuild, s);
     return rc;
 }
@@ -407,6 +406,7 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     const int64_t n = c->n;
     auto grow = [](int64_t v, int64_t add) { return v + v / 4 + add; };
     const int64_t nodes = grow(c->plan.nodes, 64 + 20 * (int64_t)ninst);
+    c->nodes_rec = nodes;  // the node count a recorded step provides for
     const int M = nbasis(p->degree);
     const int64_t upt = grow(c->plan.up_tasks, 64);
     int rc = reserve_tree_nodes(c, nodes, s);
@@ -422,6 +422,7 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->up_frame32.reserve(18 * nodes + 18));
     STS_CUDA(c->src_hl.reserve(2 * n + 2));
     STS_CUDA(c->up_tasks.reserve(upt));
+    c->up_tasks_rec = upt;  // the recorded moment tasks: grid of the upward pass, overflow bound
     STS_CUDA(c->prx64.reserve(nodes * M + 1));
     STS_CUDA(c->prx32.reserve(nodes * M + 1));
     STS_CUDA(c->prx_rd.reserve(nodes * M + 1));

@@ -397,7 +397,7 @@ int evaluate_dual(sts_ctx* c, int degree, int precision, double tau, double* vel
     int rc = evaluate(c, degree, precision, tau, vel, s);
     if (rc) return rc;
     const bool cap = c->capturing;
-    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    const int64_t C = cap ? c->nodes_rec : c->nclusters;
     if (C == 0 || c->n < 2) return STS_OK;
     if (!cap && c->dual_n[2] == 0 && c->dual_n[3] == 0) return STS_OK;  // no CP or CC pairs
     RefTable* ref = get_ref(c, degree);

@@ -319,6 +319,8 @@ struct sts_ctx {
     sts::DevBuf<int64_t> bld_tot;             // [CTAs] children per CTA of the level build
     int build_grid = 0;                       // CTAs of the level build (all resident)
     int64_t node_hint = 0;                    // node capacity that an eager build starts from
+    int64_t up_tasks_rec = 0;                 // moment tasks a recorded step provides for
+    int64_t nodes_rec = 0;                    // nodes (and clusters) a recorded step provides for
     bool timing = false;
     cudaEvent_t ev[sts::kNumPhases][2] = {};
     float phase_ms[sts::kNumPhases] = {};
@@ -404,9 +406,9 @@ int reserve_tree_nodes(sts_ctx* ctx, int64_t nodes, cudaStream_t s);
 void gather_values(const int64_t* a, const int64_t* b, const int64_t* c, const int64_t* d,
                    const int* status, int64_t* out, cudaStream_t s);
 
-// ---- sorted sources, clusters, upward pass (sts_upward.cu) --------------------------
+// ---- sorted sources and upward pass (sts_upward.cu; the cluster table, its moment tasks
+// and frames are made by tree_build) ---------------------------------------------------
 int prepare_sources(sts_ctx* ctx, const double* zeta, const double* area, cudaStream_t s);
-int build_clusters(sts_ctx* ctx, cudaStream_t s);
 int upward_pass(sts_ctx* ctx, int degree, int precision, cudaStream_t s);
 int fill_far_slots(sts_ctx* ctx, cudaStream_t s);
 

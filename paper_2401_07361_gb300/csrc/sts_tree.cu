@@ -238,7 +238,40 @@ struct BuildArgs {
     int32_t* hist;               // [256 CTAs + 256] digit counts per CTA, then per digit
     int32_t *leaves, *slot_leaf;
     int64_t* nleaves;
+    // clusters (nodes with more than N_T particles) and the moment pass's tasks
+    int32_t *cluster_slot, *cluster_node;
+    int64_t* up_toff;  // [nodes + 1] first task of each node
+    int2* up_tasks;    // (cluster, first particle of the chunk)
+    int64_t up_cap;
+    double* up_frame;
+    float* up_frame32;
+    int64_t *nclusters, *nuptasks;
 };
+
+// Frame of cluster cl (node p) for the spherical barycentric coordinates of Sec. 3.2 (y =
+// b1 v1 + b2 v2 + b3 v3, Cramer's rule): rows n_i / D with n1 = v2 x v3, n2 = v3 x v1,
+// n3 = v1 x v2, D = v1 . n1, and b(c) = (n_i / D) . c at the circumcentre; frame32: the
+// frame in FP32 and the centre as an FP32 hi/lo pair (18 floats).
+__device__ void cluster_frame(const BuildArgs& a, int64_t cl, int32_t p)
+{
+    const double* g = a.geom + 13 * (int64_t)p;
+    const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
+    const double v3x = g[6], v3y = g[7], v3z = g[8];
+    const double n[9] = {v2y * v3z - v2z * v3y, v2z * v3x - v2x * v3z, v2x * v3y - v2y * v3x,
+                         v3y * v1z - v3z * v1y, v3z * v1x - v3x * v1z, v3x * v1y - v3y * v1x,
+                         v1y * v2z - v1z * v2y, v1z * v2x - v1x * v2z, v1x * v2y - v1y * v2x};
+    const double D = v1x * n[0] + v1y * n[1] + v1z * n[2];
+    double* f = a.up_frame + 12 * cl;
+    for (int q = 0; q < 9; q++) f[q] = n[q] / D;
+    for (int q = 0; q < 3; q++) f[9 + q] = f[3 * q] * g[9] + f[3 * q + 1] * g[10] + f[3 * q + 2] * g[11];
+    float* h = a.up_frame32 + 18 * cl;
+    for (int q = 0; q < 12; q++) h[q] = (float)f[q];
+    for (int q = 0; q < 3; q++) {
+        const float hi = (float)g[9 + q];
+        h[12 + q] = hi;
+        h[15 + q] = (float)(g[9 + q] - (double)hi);
+    }
+}
 
 // Grid-wide barrier of a cooperative launch: barrier k of the launch ends when the arrival
 // counter reaches k G.  A CTA that waits too long flags the timeout and sets the counter's top
@@ -523,6 +556,76 @@ __device__ int64_t build_block_scan(int64_t v, int64_t* sh, int64_t* total)
     return before + x - v;
 }
 
+// The cluster table from the per-CTA totals in tot (clusters, tasks): cluster number and first
+// task of every node of [q0, q1) (a block scan on top of the CTAs before), the node of every
+// cluster, its tasks and its frame; totals into the device counters.
+__device__ void cluster_table(const BuildArgs& a, int G, int32_t q0, int32_t q1, int32_t nn, int64_t* sh,
+                              int64_t* s_cf, int64_t* s_tf, int64_t* s_ct)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        int64_t bf = 0, bt = 0, tf = 0, tt = 0;
+        for (int b = lane; b < G; b += 32) {
+            const int64_t f = a.tot[2 * b], t = a.tot[2 * b + 1];
+            tf += f;
+            tt += t;
+            if (b < (int)blockIdx.x) {
+                bf += f;
+                bt += t;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bf += __shfl_xor_sync(kFull, bf, o);
+            bt += __shfl_xor_sync(kFull, bt, o);
+            tf += __shfl_xor_sync(kFull, tf, o);
+            tt += __shfl_xor_sync(kFull, tt, o);
+        }
+        if (lane == 0) {
+            *s_cf = bf;
+            *s_ct = bt;
+            *s_tf = tf;
+            if (blockIdx.x == 0) {
+                *a.nclusters = tf;
+                *a.nuptasks = tt;
+                a.up_toff[nn] = tt;
+            }
+        }
+    }
+    __syncthreads();
+    int64_t cf = *s_cf, ct = *s_ct;
+    __syncthreads();
+    for (int32_t r0 = q0; r0 < q1; r0 += blockDim.x) {
+        const int32_t p = r0 + tid;
+        const int32_t c = p < q1 ? a.count[p] : 0;
+        const int f = c > a.leaf_size ? 1 : 0;
+        const int nt = f ? (c + kUpChunk - 1) / kUpChunk : 0;
+        int64_t rf, rt;
+        const int64_t ef = build_block_scan(f, sh, &rf);
+        const int64_t et = build_block_scan(nt, sh, &rt);
+        if (p < q1) {
+            const int64_t t0 = ct + et;
+            a.up_toff[p] = t0;
+            if (f) {
+                const int64_t cl = cf + ef;
+                a.cluster_slot[p] = (int32_t)cl;
+                a.cluster_node[cl] = p;
+                for (int j = 0; j < nt; j++) {
+                    if (t0 + j < a.up_cap)
+                        a.up_tasks[t0 + j] = make_int2((int)cl, j * kUpChunk);
+                    else
+                        atomicOr((unsigned long long*)a.over, 4ull);
+                }
+                cluster_frame(a, cl, p);
+            } else {
+                a.cluster_slot[p] = -1;
+            }
+        }
+        cf += rf;
+        ct += rt;
+    }
+}
+
 __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs a)
 {
     __shared__ int32_t shc[4 * kPrivNodes];
@@ -713,6 +816,29 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
         a.c32[p] = make_float4((float)g[9], (float)g[10], (float)g[11], (float)g[12]);
     }
 
+    // ---- clusters: this CTA's share [q0, q1) of the nodes, its clusters and their tasks (one
+    // per kUpChunk particles), numbered in node order after the first sort barrier
+    const int32_t qch = (nn + G - 1) / G;
+    const int32_t q0 = min(nn, (int32_t)blockIdx.x * qch), q1 = min(nn, q0 + qch);
+    {
+        int64_t fc = 0, tc = 0;
+        for (int32_t p = q0 + tid; p < q1; p += blockDim.x) {
+            const int32_t c = a.count[p];
+            if (c > a.leaf_size) {
+                fc++;
+                tc += (c + kUpChunk - 1) / kUpChunk;
+            }
+        }
+        int64_t t1, t2;
+        build_block_scan(fc, sh, &t1);
+        build_block_scan(tc, sh, &t2);
+        if (tid == 0) {
+            a.tot[2 * blockIdx.x] = t1;
+            a.tot[2 * blockIdx.x + 1] = t2;
+        }
+    }
+    bool clusters_done = false;
+
     // ---- the sorted order: a stable LSD radix sort (8-bit digits) of the particles by the
     // first slot of their leaf, which keeps the particles of a leaf in their original order.
     // CTA b owns items [i0, i1) of every pass, its warp w the w-th part of them, so the rank of
@@ -727,6 +853,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
     const unsigned lt = (1u << lane) - 1u;
     if (P == 0) {  // a single particle
         if (gt < n) a.perm[gt] = (int32_t)gt;
+        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        cluster_table(a, G, q0, q1, nn, sh, &s_before, &s_total, &s_cbefore);
         if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
     }
     for (int pass = 0; pass < P; pass++) {
@@ -751,6 +879,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
             a.hist[d * G + blockIdx.x] = t;
         }
         if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        if (!clusters_done) {
+            cluster_table(a, G, q0, q1, nn, sh, &s_before, &s_total, &s_cbefore);
+            clusters_done = true;
+        }
         // rows d = b, b + G, ...: exclusive offsets along the row (over the CTAs), row totals
         for (int d = blockIdx.x; d < 256; d += G) {
             int64_t carry = 0;
@@ -1856,6 +1988,17 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         c->build_grid = std::max(1, std::min(per_sm, 4)) * c->num_sms;
     }
     STS_CUDA(c->bld_tot.reserve(2 * (size_t)c->build_grid));
+    if (!cap) {  // the cluster table for every node the capacity allows; the moment tasks for
+                 // the largest count possible: a cluster holds more than N_T particles of one
+                 // level, so there are at most (levels) n / kUpChunk + (clusters) tasks
+        const int64_t nc = (int64_t)c->nd_level.cap;
+        STS_CUDA(c->cluster_slot.reserve(nc + 1));
+        STS_CUDA(c->cluster_node.reserve(nc + 1));
+        STS_CUDA(c->up_toff.reserve(nc + 2));
+        STS_CUDA(c->up_frame.reserve(12 * nc + 12));
+        STS_CUDA(c->up_frame32.reserve(18 * nc + 18));
+        STS_CUDA(c->up_tasks.reserve((int64_t)(max_level + 1) * (n / kUpChunk + 1) + nc + 1));
+    }
     STS_CUDA(c->hist.reserve(256 * (size_t)c->build_grid + 256));
     BuildArgs a;
     a.lvl = dc + kDcLevel;
@@ -1868,7 +2011,12 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.nlev = cap ? std::min(c->plan.depth + 2, max_level + 1) : max_level + 1;
     a.leaf_size = leaf_size;
     a.max_level = max_level;
-    a.cap = (int64_t)c->nd_level.cap;
+    // nodes the node table and every node-indexed buffer of the cluster table can hold
+    // (while recording, also the recorded node count the later kernels are sized for)
+    a.cap = std::min<int64_t>({(int64_t)c->nd_level.cap, (int64_t)c->cluster_slot.cap - 1,
+                               (int64_t)c->cluster_node.cap - 1, (int64_t)c->up_toff.cap - 2,
+                               (int64_t)c->up_frame.cap / 12 - 1, (int64_t)c->up_frame32.cap / 18 - 1,
+                               cap ? c->nodes_rec : INT64_MAX});
     a.pos_in = pos;
     a.pos = c->pos.p;
     a.posf = c->posf.p;
@@ -1907,6 +2055,16 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.leaves = c->leaves.p;
     a.slot_leaf = c->slot_leaf.p;
     a.nleaves = dc + kDcLeaves;
+    a.cluster_slot = c->cluster_slot.p;
+    a.cluster_node = c->cluster_node.p;
+    a.up_toff = c->up_toff.p;
+    a.up_tasks = reinterpret_cast<int2*>(c->up_tasks.p);
+    // while recording, the tasks the upward pass's grid covers; eagerly, the whole buffer
+    a.up_cap = cap ? std::min<int64_t>((int64_t)c->up_tasks.cap, c->up_tasks_rec) : (int64_t)c->up_tasks.cap;
+    a.up_frame = c->up_frame.p;
+    a.up_frame32 = c->up_frame32.p;
+    a.nclusters = dc + kDcClusters;
+    a.nuptasks = dc + kDcUpTasks;
     {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)c->build_grid);
@@ -1946,7 +2104,17 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
             c->node_hint = bound;
             return tree_build(c, pos, n, inst_off, ninst, leaf_size, max_level, s);
         }
+        if (h[kDcOver] & 4) {  // the moment tasks are sized by a proven bound: not expected
+            set_error("sts_tree_build: moment task capacity %lld exhausted", (long long)c->up_tasks.cap);
+            return STS_ERR_CAPACITY;
+        }
         c->nnodes = h[kDcNodes];
+        c->nleaves = h[kDcLeaves];
+        c->nclusters = h[kDcClusters];
+        c->n_up_tasks = h[kDcUpTasks];
+        c->plan.clusters = std::max(c->plan.clusters, c->nclusters);
+        c->plan.leaves = std::max(c->plan.leaves, c->nleaves);
+        c->plan.up_tasks = std::max(c->plan.up_tasks, c->n_up_tasks);
         c->level_begin.assign(1, 0);
         c->deepest = 0;
         for (int l = 1; l <= kMaxLevel + 2 && h[kDcLevel + l] > h[kDcLevel + l - 1]; l++) {
@@ -1958,9 +2126,9 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     } else {
         c->nnodes = -1;  // known after the graph runs
         c->deepest = -1;
+        c->nclusters = c->n_up_tasks = c->nleaves = -1;
     }
 
-    c->nleaves = -1;  // set by build_clusters
     c->have_tree = true;
     return STS_OK;
 }
@@ -2236,8 +2404,8 @@ int build_dual(sts_ctx* c, double theta, cudaStream_t s)
     // leaf, cluster and node counts, or while recording their planned bounds (a replay that
     // exceeds them sets the overflow bit and is redone)
     const int64_t L = cap ? std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64) : c->nleaves;
-    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
-    const int64_t nodes = cap ? (int64_t)c->nd_level.cap : c->nnodes;
+    const int64_t C = cap ? c->nodes_rec : c->nclusters;
+    const int64_t nodes = cap ? c->nodes_rec : c->nnodes;
     const int depth = cap ? c->plan.depth : (int)c->deepest;
     // a pair's two levels each grow by one per refinement, up to the deepest level: at most
     // 2 depth + 1 levels, the last of which only has terminals
@@ -2310,7 +2478,7 @@ int reserve_dual_for_capture(sts_ctx* c, int degree, cudaStream_t s)
 {
     (void)s;
     const int64_t L = std::min<int64_t>(c->n, c->plan.leaves + c->plan.leaves / 4 + 64);
-    const int64_t C = (int64_t)c->nd_level.cap, nodes = (int64_t)c->nd_level.cap;
+    const int64_t C = c->nodes_rec, nodes = c->nodes_rec;
     int rc = reserve_dual(c, dual_caps(c, L, C, nodes), L, C, nodes);
     if (rc) return rc;
     const int M = (degree + 1) * (degree + 2) / 2;
@@ -2336,7 +2504,7 @@ int refresh_dual_counts(sts_ctx* c, cudaStream_t s)
 int cluster_tasks(sts_ctx* c, int M, cudaStream_t s)
 {
     const bool cap = c->capturing;
-    const int64_t C = cap ? (int64_t)c->nd_level.cap : c->nclusters;
+    const int64_t C = cap ? c->nodes_rec : c->nclusters;
     if (!cap) {
         STS_CUDA(c->chas.reserve(C + 1));
         STS_CUDA(c->ctasks.reserve(C * ((M + kTaskTargets - 1) / kTaskTargets + 3) + 1));

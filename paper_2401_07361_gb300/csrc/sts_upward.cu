@@ -14,10 +14,13 @@
 // The mixed path computes b = b(c) + T^{-1} (y - c) in FP32 from the FP64 offset y - c to
 // the cluster centre c, so b keeps FP32 relative accuracy however small the triangle.
 // Weights: one CTA per cluster sums the chunk partials in FP64 in a fixed order and applies
-// V_ref^{-1} in FP64.  The SBB monomial basis is badly conditioned (cond(V_ref) ~ 3.5e5 at
-// d = 8), so this contraction stays in FP64: rounding it to FP32 (or TF32) would put errors
-// of eps * |V_ref^{-1}| |omega| into W.  Rounding the moments themselves to FP32 is benign:
-// it perturbs W only along directions the interpolant maps back with norm ~1.
+// V_ref^{-1} in FP64; in mixed precision (degree <= 11) the contraction runs exactly on the
+// tensor cores instead (sts_tc.cu) and this kernel only forms the proxy points.  The SBB
+// monomial basis is badly conditioned (cond(V_ref) ~ 3.5e5 at d = 8), so the contraction is
+// never rounded to FP32 (or TF32): that would put errors of eps * |V_ref^{-1}| |omega| into W.
+// Rounding the moments themselves to FP32 is benign: it perturbs W only along directions the
+// interpolant maps back with norm ~1.  The cluster table (numbers, moment tasks, barycentric
+// frames) comes with the tree build.
 #include <algorithm>
 
 #include "sts_internal.cuh"
@@ -50,59 +53,6 @@ __global__ void k_prepare(const double* __restrict__ pos, const double* __restri
     src32[k] = make_float4((float)(x - c[0]), (float)(y - c[1]), (float)(z - c[2]), (float)w2);
 }
 
-__global__ void k_cluster_flags(const int64_t* __restrict__ nnodes, const int32_t* __restrict__ count, int leaf_size,
-                                int32_t* __restrict__ flags)
-{
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < *nnodes) flags[p] = count[p] > leaf_size ? 1 : 0;
-}
-
-// Cluster and upward-task totals: offsets scanned over the nodes, read at index nnodes.
-__global__ void k_cluster_totals(int64_t* __restrict__ dc, const int64_t* __restrict__ off,
-                                 const int64_t* __restrict__ toff)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const int64_t nn = dc[kDcNodes];
-    dc[kDcClusters] = off[nn];
-    dc[kDcUpTasks] = toff[nn];
-}
-
-__global__ void k_cluster_fill(const int64_t* __restrict__ nnodes_p, const int32_t* __restrict__ flags,
-                               const int64_t* __restrict__ off, const int32_t* __restrict__ count,
-                               int32_t* __restrict__ slot, int32_t* __restrict__ cnode,
-                               int32_t* __restrict__ nchunk)
-{
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *nnodes_p) return;
-    if (flags[p]) {
-        const int64_t c = off[p];
-        slot[p] = (int32_t)c;
-        cnode[c] = (int32_t)p;
-        nchunk[p] = (count[p] + kUpChunk - 1) / kUpChunk;
-    } else {
-        slot[p] = -1;
-        nchunk[p] = 0;
-    }
-}
-
-// toff is indexed by node: the tasks of node p are [toff[p], toff[p + 1]) (none unless p is a
-// cluster).
-__global__ void k_up_tasks(const int64_t* __restrict__ nnodes, const int32_t* __restrict__ slot,
-                           const int64_t* __restrict__ toff, int64_t cap, int2* __restrict__ tasks,
-                           int64_t* __restrict__ over)
-{
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= *nnodes || slot[p] < 0) return;
-    int32_t j = 0;
-    for (int64_t q = toff[p]; q < toff[p + 1]; q++, j += kUpChunk) {
-        if (q >= cap) {
-            atomicOr((unsigned long long*)over, 4ull);
-            return;
-        }
-        tasks[q] = make_int2(slot[p], j);
-    }
-}
-
 // Exponents (a, b, c) of SBB function k of degree d: a = d..0, then b = d - a..0.
 __device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int& c)
 {
@@ -112,35 +62,6 @@ __device__ __forceinline__ void sbb_exponents(int d, int k, int& a, int& b, int&
     a = d - q;
     b = q - r;
     c = r;
-}
-
-// Frame of each cluster for the spherical barycentric coordinates of Sec. 3.2 (y = b1 v1 +
-// b2 v2 + b3 v3, Cramer's rule): rows n_i / D with n1 = v2 x v3, n2 = v3 x v1, n3 = v1 x v2,
-// D = v1 . n1, and b(c) = (n_i / D) . c at the circumcentre.  frame[c][12] in FP64.
-// frame32: the frame in FP32 plus the centre as an FP32 hi/lo pair (18 floats per cluster).
-__global__ void k_cluster_frames(const int64_t* __restrict__ nclu, const int32_t* __restrict__ cnode,
-                                 const double* __restrict__ geom, double* __restrict__ frame,
-                                 float* __restrict__ frame32)
-{
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= *nclu) return;
-    const double* g = geom + 13 * (int64_t)cnode[c];
-    const double v1x = g[0], v1y = g[1], v1z = g[2], v2x = g[3], v2y = g[4], v2z = g[5];
-    const double v3x = g[6], v3y = g[7], v3z = g[8];
-    const double n[9] = {v2y * v3z - v2z * v3y, v2z * v3x - v2x * v3z, v2x * v3y - v2y * v3x,
-                         v3y * v1z - v3z * v1y, v3z * v1x - v3x * v1z, v3x * v1y - v3y * v1x,
-                         v1y * v2z - v1z * v2y, v1z * v2x - v1x * v2z, v1x * v2y - v1y * v2x};
-    const double D = v1x * n[0] + v1y * n[1] + v1z * n[2];
-    double* f = frame + 12 * c;
-    for (int q = 0; q < 9; q++) f[q] = n[q] / D;
-    for (int a = 0; a < 3; a++) f[9 + a] = f[3 * a] * g[9] + f[3 * a + 1] * g[10] + f[3 * a + 2] * g[11];
-    float* h = frame32 + 18 * c;
-    for (int q = 0; q < 12; q++) h[q] = (float)f[q];
-    for (int a = 0; a < 3; a++) {
-        const float hi = (float)g[9 + a];
-        h[12 + a] = hi;
-        h[15 + a] = (float)(g[9 + a] - (double)hi);
-    }
 }
 
 // Moments of one (cluster, chunk) task.  T = float (mixed) or double (FP64).  Each thread
@@ -311,61 +232,14 @@ int prepare_sources(sts_ctx* c, const double* zeta, const double* area, cudaStre
     return STS_OK;
 }
 
-int build_clusters(sts_ctx* c, cudaStream_t s)
-{
-    const bool cap = c->capturing;
-    const int64_t nn = cap ? (int64_t)c->nd_level.cap : c->nnodes;  // node count or its capacity
-    int64_t* dc = c->dc.p;
-    if (!cap) {
-        STS_CUDA(c->cluster_slot.reserve(nn + 1));
-        STS_CUDA(c->cluster_node.reserve(nn + 1));
-        STS_CUDA(c->flags.reserve(nn + 1));
-        STS_CUDA(c->offs.reserve(nn + 1));
-        STS_CUDA(c->up_toff.reserve(nn + 2));
-        STS_CUDA(c->list_cnt.reserve(nn + 1));
-        STS_CUDA(c->scan_tmp.reserve(scan_scratch(nn + 1) + 8));
-        if (scan_state_reserve(c->scan_state, nn + 1, s)) return STS_ERR_CUDA;
-        STS_CUDA(c->up_frame.reserve(12 * nn + 12));
-        STS_CUDA(c->up_frame32.reserve(18 * nn + 18));
-    }
-    const unsigned g = blocks(std::max<int64_t>(nn, 1), 256);
-    (k_cluster_flags<<<g, 256, 0, s>>>(dc + kDcNodes, c->nd_count.p, c->leaf_size, c->flags.p), note_launch());
-    exclusive_scan_i32(c->flags.p, c->offs.p, nn, c->scan_state, s, c->d_status, dc + kDcNodes);
-    (k_cluster_fill<<<g, 256, 0, s>>>(dc + kDcNodes, c->flags.p, c->offs.p, c->nd_count.p, c->cluster_slot.p,
-                                      c->cluster_node.p, c->list_cnt.p), note_launch());
-    exclusive_scan_i32(c->list_cnt.p, c->up_toff.p, nn, c->scan_state, s, c->d_status, dc + kDcNodes);
-    (k_cluster_totals<<<1, 32, 0, s>>>(dc, c->offs.p, c->up_toff.p), note_launch());
-    STS_LAUNCH_CHECK();
-    if (!cap) {
-        STS_CUDA(cudaMemcpyAsync(c->h_pinned, dc, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        STS_CUDA(cudaStreamSynchronize(s));
-        c->nclusters = c->h_pinned[kDcClusters];
-        c->n_up_tasks = c->h_pinned[kDcUpTasks];
-        c->nleaves = c->h_pinned[kDcLeaves];
-        c->plan.clusters = std::max(c->plan.clusters, c->nclusters);
-        c->plan.leaves = std::max(c->plan.leaves, c->nleaves);
-        c->plan.up_tasks = std::max(c->plan.up_tasks, c->n_up_tasks);
-        STS_CUDA(c->up_tasks.reserve(c->n_up_tasks + 1));
-    } else {
-        c->nclusters = c->n_up_tasks = c->nleaves = -1;  // known after the graph runs
-    }
-    (k_cluster_frames<<<g, 256, 0, s>>>(dc + kDcClusters, c->cluster_node.p, c->nd_geom.p, c->up_frame.p,
-                                        c->up_frame32.p),
-     note_launch());
-    (k_up_tasks<<<g, 256, 0, s>>>(dc + kDcNodes, c->cluster_slot.p, c->up_toff.p, (int64_t)c->up_tasks.cap,
-                                  c->up_tasks.p, dc + kDcOver), note_launch());
-    STS_LAUNCH_CHECK();
-    return STS_OK;
-}
-
 int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
 {
     RefTable* ref = get_ref(c, degree);
     if (!ref) return STS_ERR_CUDA;
     const int M = ref->M;
     const bool cap = c->capturing;
-    const int64_t nclu = cap ? (int64_t)c->nd_level.cap : c->nclusters;
-    const int64_t nupt = cap ? (int64_t)c->up_tasks.cap : c->n_up_tasks;
+    const int64_t nclu = cap ? c->nodes_rec : c->nclusters;
+    const int64_t nupt = cap ? c->up_tasks_rec : c->n_up_tasks;
     if (!cap) {
         STS_CUDA(c->prx64.reserve(nclu * M + 1));
         STS_CUDA(c->prx32.reserve(nclu * M + 1));
