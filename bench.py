@@ -57,7 +57,8 @@ def parse(argv=None):
                     help="with --rk4: the forced system of Sec. 4.4 with this zonal wavenumber (0: none)")
     ap.add_argument("--t0", type=float, default=0.0, help="with --forcing: start time of the run (days)")
     ap.add_argument("--potential", action="store_true",
-                    help="time the FP64 tree-code stream function (build + potential) instead")
+                    help="time the mixed-precision tree-code stream function (build + potential) instead, "
+                         "the FP64 tree code beside")
     ap.add_argument("--dual", action="store_true",
                     help="the tree code by the dual traversal of Sec. 3.4 (PP, PC, CP, CC) instead of the "
                          "target-leaf lists (PC, PP)")
@@ -445,9 +446,11 @@ def run_amr(args):
 
 def run_potential(args):
     """The stream function psi_i = -(1/4pi) sum_{j != i} log(1 - x_i.x_j) zeta_j A_j by the
-    FP64 tree code (tree build + potential per step, same lists and proxies as the velocity),
-    timed like the velocity bench; roofline against the FP64 peak with 10 flop per interaction
-    (3 FSUB, 3 FMA for |d|^2 = 5, 1/2, log counted as 1, FMA = 2), the oracle tree code beside."""
+    mixed-precision tree code (tree build + potential per step, same lists and proxies as the
+    velocity), timed like the velocity bench; roofline against the derived FP32 peak with 12
+    flop per interaction (3 FSUB, |d|^2 = 5, 1/2, log2 counted as 1, the weight, the sum; the
+    TwoSum compensation is not counted), the FP64 tree code (median of 3 steps) and the oracle
+    tree code beside."""
     import numpy as np
     import torch
 
@@ -461,22 +464,25 @@ def run_potential(args):
     leaf = args.leaf or wl["leaf_size"]
     offsets = wl.get("offsets")
     p64 = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_FP64)
+    pm = sts.params(theta=args.theta, degree=args.degree, leaf_size=leaf, max_level=16, precision=sts.STS_MIXED,
+                    near_fp64_tau=args.tau_c * 4 * math.pi / n)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     pos = torch.from_numpy(wl["pos"]).to(dev)
     zeta = torch.from_numpy(wl["zeta"]).to(dev)
     area = torch.from_numpy(wl["area"]).to(dev)
     psi = torch.empty(n, dtype=torch.float64, device=dev)
+    psi64 = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = sts.Context()
     h = ctx.h
 
-    def step():
+    def step(p=pm, out=psi):
         if offsets is None:
-            sts.sts_tree_build(h, pos, p64)
+            sts.sts_tree_build(h, pos, p)
         else:
-            sts.sts_tree_build_batched(h, pos, offsets, p64)
-        sts.sts_potential(h, zeta, area, p64, psi)
+            sts.sts_tree_build_batched(h, pos, offsets, p)
+        sts.sts_potential(h, zeta, area, p, out)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -506,22 +512,42 @@ def run_potential(args):
     inter = stats["pc"] + stats["pp"]
     peaks = measured_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0)) if isinstance(peaks, dict) else 2070.0
-    peak_fp64 = 152 * 2 * 2 * mhz * 1e6 / 1e12  # TFLOP/s: 2 FP64 FMA lanes per SM per clock
-    achieved = 10.0 * inter / (eval_ms / 1e3) / 1e12
+    peak_fp32 = 152 * 128 * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    achieved = 12.0 * inter / (eval_ms / 1e3) / 1e12
+    # the FP64 tree code on the same workload: median of 3 timed steps after one warm-up
+    step(p64, psi64)
+    t64 = []
+    for _ in range(3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(p64, psi64)
+        e1.record()
+        e1.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    ms64 = float(np.median(t64))
+    step()  # psi back from the mixed path (the tree is rebuilt identically)
+    torch.cuda.synchronize()
+    got, got64 = psi.cpu().numpy(), psi64.cpu().numpy()
+    a = wl["area"]
     line = {
-        "metric": "stream function targets/s, FP64 tree code", "value": ws * n / (ms / 1e3), "unit": "targets/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "metric": "stream function targets/s, mixed tree code (FP64 tree code beside)", "value": ws * n / (ms / 1e3),
+        "unit": "targets/s", "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "N": n, "theta": args.theta, "degree": args.degree, "leaf_size": leaf,
-                   "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)",
+                   "precision": "mixed (f32 log2 terms, compensated sums, f64 close pairs below tau)",
+                   "near_fp64_tau": pm.near_fp64_tau, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": "host launches (build + potential)"},
-        "roofline": {"bound": "fp64", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp64, "traffic": None, "kernel": "k_eval_fp64<true>",
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x sm_max_mhz (nominal 1.25 TFLOP/s); "
-                                    "10 flop per interaction", "kernel_ms": eval_ms},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": None, "kernel": "k_eval_mixed<true>",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz; 12 flop per interaction",
+                     "kernel_ms": eval_ms},
         "gpu_launches": int(launches), "clocks": clocks,
         "phases_ms_per_step": {k: v[0] / max(1, v[1]) for k, v in phases.items() if v[1]},
         "interactions_per_step": stats,
+        "fp64_tree": {"value": n / (ms64 / 1e3), "unit": "targets/s", "ms": ms64, "ms_samples": t64},
+        "error": {"mixed_vs_fp64_gpu_tree_rel_l2": float(np.sqrt(np.sum((got - got64) ** 2 * a) / np.sum(got64**2 * a)))},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and n <= 3_000_000:
         from oracle import oracle as O
@@ -534,9 +560,9 @@ def run_potential(args):
                                                                          args.degree)
                                   for a, b in zip(offsets[:-1], offsets[1:]) if b > a])
         cpu_s = time.perf_counter() - t0
-        got = psi.cpu().numpy()
-        a = wl["area"]
-        line["error"] = {"vs_fp64_oracle_tree_rel_l2": float(np.sqrt(np.sum((got - ref) ** 2 * a) / np.sum(ref**2 * a)))}
+        line["error"]["vs_fp64_oracle_tree_rel_l2"] = float(np.sqrt(np.sum((got - ref) ** 2 * a) / np.sum(ref**2 * a)))
+        line["error"]["fp64_gpu_vs_fp64_oracle_tree_rel_l2"] = float(
+            np.sqrt(np.sum((got64 - ref) ** 2 * a) / np.sum(ref**2 * a)))
         line["cpu_baseline"] = {"value": n / cpu_s, "unit": "targets/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"full workload: oracle tree build + FP64 tree-code stream function of all "
                                           f"{n} targets, OpenMP over target leaves"}

@@ -182,8 +182,12 @@ int sts_velocity(sts_ctx* ctx, const double* zeta, const double* area, const sts
  * sts_velocity (the weights do not depend on the kernel).  zeta[n], area[n] in, psi[n] out in
  * the caller's order; a distinct particle at a target's position adds nothing.  With this G,
  * u = grad psi x x is the velocity of sts_velocity and Lap psi = -zeta for zero-mean zeta.
- * Only p->precision = STS_FP64 is implemented (STS_ERR_ARG otherwise).  STS_ERR_STATE
- * without a tree.  Synchronises `stream` when the lists are (re)built. */
+ * p->precision: STS_FP64, or STS_MIXED: FP32 log terms (log2 of |d|^2 / 2 on leaf-local
+ * coordinates, as the velocity's pair terms) summed per target in TwoSum-compensated FP32
+ * pairs, the pairs closer than p->near_fp64_tau in FP64, ln 2 and the sum scaled in FP64 (the
+ * log terms of a zero-mean vorticity cancel by ~100, which plain FP32 sums would not
+ * survive).  STS_ERR_STATE without a tree.  Synchronises `stream` when the lists are
+ * (re)built. */
 int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const sts_params* p,
                   double* psi, void* stream);
 

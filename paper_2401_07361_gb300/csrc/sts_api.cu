@@ -264,8 +264,8 @@ int potential_impl(sts_ctx* c, const double* zeta, const double* area, const sts
         return STS_OK;
     }
     int rc;
-    if ((rc = sources_and_lists(c, zeta, area, p, STS_FP64, false, s))) return rc;
-    if ((rc = evaluate_potential(c, p->degree, psi, s))) return rc;
+    if ((rc = sources_and_lists(c, zeta, area, p, p->precision, false, s))) return rc;
+    if ((rc = evaluate_potential(c, p->degree, p->precision, p->near_fp64_tau, psi, s))) return rc;
     c->list_degree = p->degree;
     return STS_OK;
 }
@@ -770,10 +770,6 @@ int sts_potential(sts_ctx* ctx, const double* zeta, const double* area, const st
 {
     int rc = check_ctx(ctx, "sts_potential");
     if (rc || (rc = check_params(p, "sts_potential"))) return rc;
-    if (p->precision != STS_FP64) {
-        set_error("sts_potential: only precision STS_FP64 is implemented");
-        return STS_ERR_ARG;
-    }
     if (!ctx->have_tree) {
         set_error("sts_potential: no tree (call sts_tree_build first)");
         return STS_ERR_STATE;

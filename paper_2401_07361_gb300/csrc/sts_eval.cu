@@ -36,6 +36,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 constexpr float kEps = 1e-30f;
 constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
+constexpr double kLn2 = 0.6931471805599453;  // ln 2 rounded to FP64
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -232,6 +233,72 @@ __device__ __forceinline__ void block_close_pairs(const float4* sb, int cnt, int
     }
 }
 
+// The potential's FP64 close pair: corr[tk] += (2 w) log(|d|^2 / 2) (pot64's term).
+__device__ __forceinline__ void close_pot(const double4* __restrict__ src64, const double4* __restrict__ tgt64,
+                                          int64_t j, int64_t tk, double* __restrict__ corr)
+{
+    double a = 0.0;
+    const double4 x = tgt64[tk];
+    pot64(src64[j], x.x, x.y, x.z, a);
+    if (a != 0.0) atomicAdd(corr + tk, a);
+}
+
+// The potential's FP32 pair loop (Sec. 2 Green's function) over one staged group, as
+// block_pairs: (2 w) log2(|d|^2 / 2) per pair, the two targets in the halves of paired FP32
+// instructions.  The log terms of a zero-mean vorticity cancel by ~100 across a target's
+// sources, so the running sums are TwoSum-compensated pairs (hi, lo) per target: FP32 sums of
+// the uncancelled partials would lose the result.  log2 by the FP32 hardware approximation
+// (absolute error ~2^-22 whatever the argument); the caller scales by ln 2 in FP64.  TEST:
+// pairs with |d|^2 below tau2 are left out (the close-pair pass takes them in FP64).
+template <bool TEST, int S>
+__device__ __forceinline__ void block_pot(const float4* sb, int cntp, int ph, float ax, float ay, float az,
+                                          float bx, float by, float bz, float2& hi, float2& lo, float tau2,
+                                          bool& hit)
+{
+    const float2 na = make_float2(-ax, -bx), nb = make_float2(-ay, -by), nc = make_float2(-az, -bz);
+    const float2 eps2 = make_float2(kEps, kEps), half = make_float2(0.5f, 0.5f);
+    for (int i = ph; i < cntp; i += 4 * S) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float4 s = sb[i + u * S];
+            const float2 dx = __fadd2_rn(make_float2(s.x, s.x), na);
+            const float2 dy = __fadd2_rn(make_float2(s.y, s.y), nb);
+            const float2 dz = __fadd2_rn(make_float2(s.z, s.z), nc);
+            const float2 r = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __ffma2_rn(dx, dx, eps2)));
+            const float2 h = __fmul2_rn(r, half);
+            float2 t = __fmul2_rn(make_float2(s.w, s.w), make_float2(__log2f(h.x), __log2f(h.y)));
+            if (TEST) {
+                const bool z0 = r.x < tau2, z1 = r.y < tau2;
+                t.x = z0 ? 0.f : t.x;
+                t.y = z1 ? 0.f : t.y;
+                hit = hit || z0 || z1;
+            }
+            // Knuth's TwoSum: hi + t = sum + e exactly; lo collects e
+            const float2 sum = __fadd2_rn(hi, t);
+            const float2 bv = __fadd2_rn(sum, make_float2(-hi.x, -hi.y));
+            const float2 av = __fadd2_rn(sum, make_float2(-bv.x, -bv.y));
+            const float2 ea = __fadd2_rn(hi, make_float2(-av.x, -av.y));
+            const float2 eb = __fadd2_rn(t, make_float2(-bv.x, -bv.y));
+            lo = __fadd2_rn(lo, __fadd2_rn(ea, eb));
+            hi = sum;
+        }
+    }
+}
+
+// The potential's close pairs of one tested block for a lane that hit, as block_close_pairs.
+template <int S>
+__device__ __forceinline__ void block_close_pot(const float4* sb, int cnt, int ph, float ax, float ay, float az,
+                                                float bx, float by, float bz, float tau2, int64_t base, int64_t tk0,
+                                                int64_t tk1, const double4* __restrict__ src64,
+                                                const double4* __restrict__ tgt64, double* __restrict__ corr)
+{
+    for (int i = ph; i < cnt; i += S) {
+        const float4 s = sb[i];
+        if (sqdist(s, ax, ay, az) < tau2) close_pot(src64, tgt64, base + i, tk0, corr);
+        if (sqdist(s, bx, by, bz) < tau2) close_pot(src64, tgt64, base + i, tk1, corr);
+    }
+}
+
 // ------------------------------------------------------------------------ mixed tree
 // A group: consecutive blocks of one kind (untested, or near blocks tested for close pairs)
 // with at most kGroupMax sources in all, staged back to back and padded once, at its end, to
@@ -381,7 +448,7 @@ __device__ __forceinline__ void issue_group(EvalSmem& sm, const Group& g, int st
 // One warp task of the mixed tree code.  Returns false if a staging wait gave up (status
 // flagged STS_ERR_TIMEOUT after the copies in flight were given a bounded time to land).
 // par: the parity bits of the two stage barriers, carried from task to task.
-template <int S>
+template <int S, bool POT>
 __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, int lane, unsigned& par,
                                                 int* __restrict__ status,
                                                 const int64_t* __restrict__ far_off,
@@ -406,6 +473,7 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
     const float t1x = v1 ? q.x : -1e3f, t1y = v1 ? q.y : -1e3f, t1z = v1 ? q.z : -1e3f;
     float h0x = 0.f, h0y = 0.f, h0z = 0.f, l0x = 0.f, l0y = 0.f, l0z = 0.f;
     float h1x = 0.f, h1y = 0.f, h1z = 0.f, l1x = 0.f, l1y = 0.f, l1z = 0.f;
+    float2 phi = make_float2(0.f, 0.f), plo = make_float2(0.f, 0.f);  // POT: the two targets' sums
 
     const int64_t fo = far_off[tk.leaf], co = near_coff[tk.leaf];
     const int nf = (int)(far_off[tk.leaf + 1] - fo);
@@ -448,7 +516,23 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
         const int gp = (cur.cnt + 4 * S - 1) / (4 * S) * (4 * S);
         float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
         bool hit = false;
-        if (cur.tested) {
+        if (POT) {
+            if (cur.tested) {
+                block_pot<true, S>(st, gp, ph, t0x, t0y, t0z, t1x, t1y, t1z, phi, plo, tau2, hit);
+                if (hit) {
+                    for (int f = cur.e0; f < cur.e1; f++) {
+                        const int4 in = sm.info[f & (kRing - 1)];
+                        const int b0 = in.w - cur.base;
+                        int i0 = (ph - b0) % S;
+                        if (i0 < 0) i0 += S;
+                        block_close_pot<S>(st + b0, in.y, i0, t0x, t0y, t0z, t1x, t1y, t1z, tau2, in.x, tk0, tk1,
+                                           src64, tgt64, corr);
+                    }
+                }
+            } else {
+                block_pot<false, S>(st, gp, ph, t0x, t0y, t0z, t1x, t1y, t1z, phi, plo, tau2, hit);
+            }
+        } else if (cur.tested) {
             block_pairs<true, S>(st, gp, ph, t0x, t0y, t0z, t1x, t1y, t1z, p0x, p0y, p0z, p1x, p1y, p1z, tau2,
                                  hit);
             if (hit) {
@@ -478,6 +562,10 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
     }
     double a[6] = {(double)h0x + (double)l0x, (double)h0y + (double)l0y, (double)h0z + (double)l0z,
                    (double)h1x + (double)l1x, (double)h1y + (double)l1y, (double)h1z + (double)l1z};
+    if (POT) {
+        a[0] = (double)phi.x + (double)plo.x;
+        a[3] = (double)phi.y + (double)plo.y;
+    }
 #pragma unroll
     for (int s2 = 1; s2 < S; s2++) {
         const int src = (lane + s2 * p) & 31;
@@ -488,6 +576,21 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
         }
     }
     __syncwarp();
+    if (POT) {
+        // psi = -(1/4 pi) sum w log(|d|^2 / 2) = -(1/8 pi) (ln 2 sum 2w log2(.) + the FP64 close pairs)
+        if (lane < p) {
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int64_t t = u == 0 ? tk0 : tk1;
+                if (!(u == 0 ? v0 : v1)) continue;
+                double acc = kLn2 * a[3 * u];
+                if (corr) acc += __ldcg(corr + t);
+                const int64_t i = out_base >= 0 ? t - out_base : (int64_t)perm[t];
+                vel[i] = -0.5 * kInv4Pi * acc;
+            }
+        }
+        return true;
+    }
     if (lane < p) {
 #pragma unroll
         for (int u = 0; u < 2; u++) {
@@ -515,6 +618,7 @@ __device__ __forceinline__ bool eval_task_mixed(const Task& tk, EvalSmem& sm, in
     return true;
 }
 
+template <bool POT>
 __global__ void __launch_bounds__(kEvalWarps * 32, STS_EVAL_MIN_BLOCKS)
 k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off,
              const FarEntry* __restrict__ far_ent, const int64_t* __restrict__ near_coff,
@@ -548,35 +652,35 @@ k_eval_mixed(const Task* __restrict__ tasks, const int64_t* __restrict__ far_off
         bool ok;
         switch (tk.S) {
             case 1:
-                ok = eval_task_mixed<1>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<1, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 2:
-                ok = eval_task_mixed<2>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<2, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 3:
-                ok = eval_task_mixed<3>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<3, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 4:
-                ok = eval_task_mixed<4>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<4, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 5:
-                ok = eval_task_mixed<5>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<5, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 6:
-                ok = eval_task_mixed<6>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<6, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             case 7:
-                ok = eval_task_mixed<7>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<7, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
             default:
-                ok = eval_task_mixed<8>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
+                ok = eval_task_mixed<8, POT>(tk, sbuf[w], lane, par, status, far_off, far_ent, near_coff, near_ent, prx32,
                                          M, src32, src64, tgt32, tgt64, perm, tau2, tau_r, corr, vel, rg.out_base);
                 break;
         }
@@ -917,26 +1021,48 @@ int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const do
     return STS_OK;
 }
 
-int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s)
+namespace {
+int eval_blocks(sts_ctx* c);
+}  // namespace
+
+int evaluate_potential(sts_ctx* c, int degree, int precision, double tau, double* psi, cudaStream_t s)
 {
     const int M = nbasis(degree);
     const int64_t ntasks = c->capturing ? (int64_t)c->tasks.cap : c->ntasks;
     if (ntasks <= 0) return STS_OK;
-    if (c->eval_blocks_fp64 <= 0) {
-        int b64 = 0;
-        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<true>, kEvalWarps64 * 32, 0));
-        c->eval_blocks_fp64 = std::max(1, c->num_sms * b64);
-    }
+    int rc = eval_blocks(c);
+    if (rc) return rc;
     unsigned long long* queue = (unsigned long long*)(c->dc.p + kDcQueue);
     STS_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s));
-    const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
-    phase_begin(c, kPhEval, s);
-    (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
-                                                       c->near_ent.p, c->prx64.p, M, c->src64.p, c->src64.p,
-                                                       c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue,
-                                                       c->dc.p + kDcOver, EvalRange{0, INT64_MAX, -1}),
-     note_launch());
-    phase_end(c, kPhEval, s);
+    if (precision == STS_FP64) {
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps64), c->eval_blocks_fp64);
+        phase_begin(c, kPhEval, s);
+        (k_eval_fp64<true><<<g, kEvalWarps64 * 32, 0, s>>>(c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p,
+                                                           c->near_ent.p, c->prx64.p, M, c->src64.p, c->src64.p,
+                                                           c->perm.p, psi, c->dc.p + kDcTasks, ntasks, queue,
+                                                           c->dc.p + kDcOver, EvalRange{0, INT64_MAX, -1}),
+         note_launch());
+        phase_end(c, kPhEval, s);
+    } else {
+        // mixed: the FP32 log terms (compensated sums) with the close pairs below tau in FP64,
+        // as the velocity (one correction per target).  The log has no finite value at
+        // coincident points (a target and itself, duplicates), so a tau of at least 1e-20 always
+        // sends those pairs to the FP64 pass, which leaves them out
+        tau = std::min(std::max(tau, 1e-20), 2.0);
+        if (!c->capturing) STS_CUDA(c->corr.reserve(3 * c->n + 3));
+        STS_CUDA(cudaMemsetAsync(c->corr.p, 0, c->n * sizeof(double), s));
+        double* corr = c->corr.p;
+        const float tau2 = (float)(2.0 * tau);
+        const float tau_r = (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6);
+        const unsigned g = (unsigned)std::min<int64_t>(blocks(ntasks, kEvalWarps), c->eval_blocks_mixed);
+        phase_begin(c, kPhEval, s);
+        (k_eval_mixed<true><<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
+             c->tasks.p, c->far_off.p, c->far_ent.p, c->near_coff.p, c->near_ent.p, c->prx32.p, M, c->src32.p,
+             c->src64.p, c->src32.p, c->src64.p, c->perm.p, tau2, tau_r, corr, psi, c->dc.p + kDcTasks, ntasks,
+             queue, c->d_status, c->dc.p + kDcOver, EvalRange{0, INT64_MAX, -1}),
+         note_launch());
+        phase_end(c, kPhEval, s);
+    }
     STS_LAUNCH_CHECK();
     return STS_OK;
 }
@@ -949,9 +1075,11 @@ int eval_blocks(sts_ctx* c)
     if (c->eval_blocks_mixed > 0) return STS_OK;
     // persistent grids: as many blocks as stay resident on all SMs at once
     int b32 = 0, b64 = 0;
-    STS_CUDA(cudaFuncSetAttribute(k_eval_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    STS_CUDA(cudaFuncSetAttribute(k_eval_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(kEvalWarps * sizeof(EvalSmem))));
-    STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed, kEvalWarps * 32,
+    STS_CUDA(cudaFuncSetAttribute(k_eval_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(kEvalWarps * sizeof(EvalSmem))));
+    STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_eval_mixed<false>, kEvalWarps * 32,
                                                            kEvalWarps * sizeof(EvalSmem)));
     STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_eval_fp64<false>, kEvalWarps64 * 32, 0));
     c->eval_blocks_mixed = std::max(1, c->num_sms * b32);
@@ -996,7 +1124,7 @@ int evaluate_lists(sts_ctx* c, const ListSet& ls, int degree, int precision, dou
         const float tau_r = corr ? (float)(sqrt(2.0 * tau) * (1.0 + 1e-3) + 1e-6) : -1.f;
         const unsigned g = (unsigned)std::min<int64_t>(blocks(ls.ntasks, kEvalWarps), c->eval_blocks_mixed);
         phase_begin(c, phase, s);
-        (k_eval_mixed<<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
+        (k_eval_mixed<false><<<g, kEvalWarps * 32, kEvalWarps * sizeof(EvalSmem), s>>>(
              ls.tasks, ls.far_off, ls.far_ent, ls.near_coff, ls.near_ent, c->prx32.p, M, c->src32.p, c->src64.p,
              ls.tgt32, ls.tgt64, ls.perm, tau2, tau_r, corr, vel, ls.ntasks_d, ls.ntasks, queue, c->d_status,
              c->dc.p + kDcOver, EvalRange{ls.leaf_lo, ls.leaf_hi, ls.out_base}),

@@ -439,7 +439,7 @@ int evaluate_lists(sts_ctx* ctx, const ListSet& ls, int degree, int precision, d
 
 int direct_potential(sts_ctx* c, const double* pos, const double* zeta, const double* area, int64_t n,
                      double* psi, cudaStream_t s);
-int evaluate_potential(sts_ctx* c, int degree, double* psi, cudaStream_t s);
+int evaluate_potential(sts_ctx* c, int degree, int precision, double tau, double* psi, cudaStream_t s);
 int wait_selftest(sts_ctx* c, int spins, cudaStream_t s);
 // The evaluation of the targets of depth-first leaves [leaf_lo, leaf_hi) only (lists, sources
 // and proxy weights already in place); out_base >= 0: sorted-slot rows t - out_base.

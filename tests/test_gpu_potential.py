@@ -1,7 +1,8 @@
 """GPU stream function (the Green's function of Sec. 2 as the kernel) against the FP64
 oracle: direct sum and tree code (same lists and proxy weights as the velocity) within
 1e-12, interaction counts identical, and psi consistent with the velocity (u = grad psi x x)
-through the kinetic-energy identity."""
+through the kinetic-energy identity; the mixed-precision tree code within 1e-6 of the FP64
+oracle tree code, with and without the close-pair threshold, and at full size."""
 import math
 
 import numpy as np
@@ -120,7 +121,54 @@ def test_potential_arguments(ctx):
     with pytest.raises(sts.StsError):
         sts.sts_direct_potential(ctx, dev(pos), dev(z), dev(a), precision=sts.STS_MIXED)
     sts.sts_tree_build(ctx, dev(pos), sts.params(leaf_size=16))
-    with pytest.raises(sts.StsError):
-        sts.sts_potential(ctx, dev(z), dev(a), sts.params(precision=sts.STS_MIXED))
     one = sts.sts_direct_potential(ctx, dev(pos[:1]), dev(z[:1]), dev(a[:1])).cpu().numpy()
     assert one[0] == 0.0
+
+
+def _check_mixed(psi, ref, pos, zeta, area):
+    # the mixed bar (1e-6 rel l2), and every target within 1e-6 of its terms' size
+    assert _rel(psi, ref, area) <= 1e-6
+    assert np.max(np.abs(psi - ref) / _abs_sum(pos, zeta, area)) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["rand3000", "ico4", "clustered", "duplicates"])
+@pytest.mark.parametrize("tau_c", [0.0, 0.01])
+def test_tree_potential_mixed_matches_oracle(ctx, case, tau_c):
+    """Mixed precision (FP32 log2 terms in compensated sums, close pairs in FP64) against the
+    FP64 oracle tree code on the same tree; coincident points (the target itself, duplicates)
+    add nothing even without a close-pair threshold."""
+    if case == "rand3000":
+        pos, leaf = W.uniform_points(3000, 61), 16
+    elif case == "ico4":
+        pos, leaf = W.icosahedral_points(4), 32
+    elif case == "clustered":
+        pos, leaf = _clustered(62), 24
+    else:
+        p = W.uniform_points(900, 63)
+        pos, leaf = np.vstack([p, p[:100]]), 8
+    n = len(pos)
+    rng = np.random.default_rng(65)
+    zeta = rng.standard_normal(n)
+    zeta -= np.mean(zeta)  # zero mean: the log terms cancel, as for a vorticity on the sphere
+    area = rng.uniform(0.5, 1.5, n) * (4 * math.pi / n)
+    p = sts.params(theta=0.7, degree=8, leaf_size=leaf, precision=sts.STS_MIXED,
+                   near_fp64_tau=tau_c * 4 * math.pi / n)
+    sts.sts_tree_build(ctx, dev(pos), p)
+    psi = sts.sts_potential(ctx, dev(zeta), dev(area), p).cpu().numpy()
+    ref = O.Tree(pos, leaf).potential(zeta, area, 0.7, 8)
+    _check_mixed(psi, ref, pos, zeta, area)
+
+
+def test_tree_potential_mixed_fullsize(ctx):
+    """rand655k_sh16 (N = 655362, theta 0.7, d 8, N_T 128): the mixed stream function within
+    1e-6 (rel l2) of the FP64 tree code on the same tree (which the tests above hold to the
+    oracle's tree code within 1e-11)."""
+    wl = W.workload("rand655k_sh16")
+    pos, zeta, area = wl["pos"], wl["zeta"], wl["area"]
+    n = len(pos)
+    pm = sts.params(theta=0.7, degree=8, leaf_size=128, precision=sts.STS_MIXED, near_fp64_tau=0.01 * 4 * math.pi / n)
+    p64 = sts.params(theta=0.7, degree=8, leaf_size=128, precision=sts.STS_FP64)
+    sts.sts_tree_build(ctx, dev(pos), pm)
+    psi = sts.sts_potential(ctx, dev(zeta), dev(area), pm).cpu().numpy()
+    psi64 = sts.sts_potential(ctx, dev(zeta), dev(area), p64).cpu().numpy()
+    assert _rel(psi, psi64, area) <= 1e-6
