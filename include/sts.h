@@ -150,8 +150,11 @@ int sts_direct_noalloc(const double* pos, const double* zeta, const double* area
  * each particle is assigned to one of the 20 faces, and every triangle holding more than
  * p->leaf_size particles below p->max_level is split into its four children.  Particles
  * keep their original relative order inside every leaf.  Uses p->leaf_size and
- * p->max_level; the other fields are checked but not used.  Synchronises `stream` (it reads
- * the number of nodes of each level).  Replaces any previous tree of the context. */
+ * p->max_level; the other fields are checked but not used.  Synchronises `stream` once (it
+ * reads the node, leaf and cluster counts after the build, which runs as one cooperative
+ * launch; if the node table it started with ran out, it is enlarged to the proven bound and
+ * the build redone).  STS_ERR_TIMEOUT if a grid-wide barrier of that launch gave up.
+ * Replaces any previous tree of the context. */
 int sts_tree_build(sts_ctx* ctx, const double* pos, int64_t n, const sts_params* p,
                    void* stream);
 
