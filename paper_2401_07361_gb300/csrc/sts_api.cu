@@ -93,7 +93,7 @@ sts_ctx::~sts_ctx()
     near_off.release(); far_idx.release(); near_idx.release(); far_ent.release();
     near_ent.release(); list_cnt.release(); wover.release(); tasks.release(); dsrc64.release(); dsrc32.release();
     dpart.release(); rk_x0.release(); rk_z0.release(); rk_xs.release(); rk_zs.release();
-    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); up_wtc.release(); prx_rd.release(); scan_state.release(); scan_state_side.release(); bld_tot.release();
+    rk_k.release(); rk_ksum.release(); d_stats.release(); d_work.release(); prx_rd.release(); scan_state.release(); scan_state_side.release(); bld_tot.release();
     dual_ft.release(); dual_fs.release(); dual_gt.release(); dual_gs.release(); dual_tt.release();
     dual_ts.release(); dual_tk.release(); dual_t.release(); dual_s.release(); dual_key.release();
     dual_ktmp.release(); dual_perm.release(); dual_ptmp.release(); dual_chunk.release(); dual_cnt.release();
@@ -426,7 +426,6 @@ int reserve_for_capture(sts_ctx* c, const sts_params* p, int ninst, cudaStream_t
     STS_CUDA(c->prx64.reserve(nodes * M + 1));
     STS_CUDA(c->prx32.reserve(nodes * M + 1));
     STS_CUDA(c->prx_rd.reserve(nodes * M + 1));
-    STS_CUDA(c->up_wtc.reserve(nodes * M + 1));
     STS_CUDA(c->up_part.reserve(upt * M + 1));
     STS_CUDA(c->far_idx.reserve(grow(c->plan.far, 1024)));
     STS_CUDA(c->far_ent.reserve(grow(c->plan.far, 1024)));

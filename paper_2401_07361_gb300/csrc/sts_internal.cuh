@@ -312,7 +312,6 @@ struct sts_ctx {
     // ---- stats and phase timing -------------------------------------------------------
     sts::DevBuf<unsigned long long> d_stats;  // [2] PC, PP interactions
     sts::DevBuf<int64_t> d_work;              // [nleaves] per-leaf interactions (sts_leaf_work)
-    sts::DevBuf<double> up_wtc;               // [clusters, M] tensor-core contraction (mixed)
     sts::DevBuf<double> prx_rd;               // [clusters, M] rho_m^d of each proxy point
     sts::DevBuf<int64_t> scan_state;          // single-pass scan state of the main stream
     sts::DevBuf<int64_t> scan_state_side;     // ... of the side stream (lists)
@@ -348,7 +347,7 @@ RefTable* get_ref(sts_ctx* ctx, int d);
 // The contraction sum_k omega_k Vinv[k][m] of the upward pass on the tensor cores, for the
 // clusters of the current tree (counted on the device, at most nclu) into wout[cluster, M].
 bool proxy_weights_tc_supported(int degree);
-int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s);
+int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int degree, int64_t nclu, cudaStream_t s);
 // The dual traversal's mixed-precision interpolation coefficients c = V_ref^-1 diag(rho^d) U on
 // the tensor cores, for the clusters with CP / CC pairs (chas), cvel[cluster, M, 3] ->
 // coef32[cluster, M] as float4 (x, y, z, unused).

@@ -20,7 +20,8 @@
 //
 // Layout: persistent CTAs of 8 warps, one per SM, looping over batches of rows (the MMA's 128
 // rows; the upward pass fills 32 of them, so that its FP64 sums of the moments spread over
-// ~125 SMs, the interpolation coefficients 126: 42 clusters x 3 components).  Operands in shared
+// ~125 SMs, a row with many partial sums split over all eight warps; the interpolation
+// coefficients 126: 42 clusters x 3 components).  Operands in shared
 // memory in the no-swizzle K-major layout of 8 x 8 core matrices (K-adjacent core matrices 128
 // bytes apart, row groups Kp * 16 bytes apart); the digit table of V_ref^-1 is precomputed on
 // the host in that layout.  The row maxima and the digits are taken from the bits of the FP64
@@ -47,6 +48,7 @@ constexpr int kTcASlices = 4;                // digits of omega
 constexpr int kTcLevels = kTcASlices + kTcSlices - 1;  // L = 2 .. 11
 constexpr int kTcMaxKp = 80;                 // M <= 80 (degree <= 11): the operands fit shared memory
 constexpr int kTcWaitSpins = 1 << 20;
+constexpr int kTcHeavy = 32;                 // a row with more partial sums is summed by all warps
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -114,7 +116,8 @@ __device__ __forceinline__ void tc_two_sum(float& hi, float& lo, float x)
 
 // The two contractions run by the kernel below.  MODE 0, the upward pass: row = cluster,
 // A = the moments omega_k (summed from the moment pass's partial sums, scaled by 2^E[k]),
-// B = the columns of V_ref^-1, out W'[cluster, m] (FP64).  MODE 1, the dual traversal's
+// B = the columns of V_ref^-1, out W'[cluster, m] (FP64), turned into the proxy points and
+// weights W2 = 2 rho_m^d W'_m in the epilogue.  MODE 1, the dual traversal's
 // interpolation coefficients (c = V_ref^-1 diag(rho^d) U_T, Sec. 3.3 CP / CC): row = (cluster,
 // velocity component), A = rho_m^d U_m (the kernel sum at the proxy points, comparable values:
 // no scaling), B = the rows of V_ref^-1, out c[cluster, k] as FP32 (x, y, z, -) per k.
@@ -125,11 +128,17 @@ struct TcArgs {
     const int32_t* tcE;
     const int64_t* nclu;
     int* status;
-    // MODE 0
+    // MODE 0: the moments' partial sums in, the proxy points and weights out (as the upward
+    // pass's FP64 path forms them: y~_m, rho_m^d, W2 = 2 rho_m^d W'_m)
     const int32_t* cnode;
     const int64_t* toff;
     const double* part;
-    double* wout;
+    const double* geom;
+    const double* beta;
+    int d;
+    double4* prx64;
+    float4* prx32;
+    double* prx_rd;
     // MODE 1
     const uint8_t* has;
     const double* rd;
@@ -188,7 +197,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(const TcArgs a)
     double* om = reinterpret_cast<double*>(B + kTcSlices * bBytes);  // [R, Kp] the rows (FP64)
     float* hs = reinterpret_cast<float*>(om);       // [Np, R + 1] the level sums (aliases om),
     float* ls = hs + Np * (R + 1);                  // hi and lo of TwoSum
-    int* gexp = reinterpret_cast<int*>(om + (size_t)Kp * (R + 1));  // [R] row exponents
+    double* part8 = om + (size_t)Kp * (R + 1);                      // [8, Kp] warps' partial sums
+    int* gexp = reinterpret_cast<int*>(part8 + (size_t)kTcWarps * Kp);  // [R] row exponents
     uint64_t* bar = reinterpret_cast<uint64_t*>(gexp + R);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
 
@@ -217,25 +227,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(const TcArgs a)
     // persistent CTAs: batches blockIdx.x, blockIdx.x + gridDim.x, ...
     for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x) {
         if (MODE == 0) {
-            // the moments, warp w rows w, w + 8, ...: each from its partial sums (lanes over k,
-            // two k per lane, four interleaved sums each), scaled by 2^E[k] (exactly)
+            // the moments, each from its partial sums, scaled by 2^E[k] (exactly): warp w sums
+            // the rows w, w + 8, ... with at most kTcHeavy partial sums (lanes over k, two k per
+            // lane, four interleaved sums each); the few larger rows (the top levels' clusters)
+            // come next, each split over all warps
             for (int r = warp; r < R; r += kTcWarps) {
                 const int64_t c = bt + (int64_t)r * nb;
+                int64_t q0 = 0, q1 = 0;
+                if (c < ncl) {
+                    q0 = a.toff[a.cnode[c]];
+                    q1 = a.toff[a.cnode[c] + 1];
+                    if (q1 - q0 > kTcHeavy) continue;  // below
+                }
                 for (int k0 = 0; k0 < Kp; k0 += 64) {
                     const int ka = k0 + lane, kb = k0 + 32 + lane;
                     const bool va = c < ncl && ka < M, vb = c < ncl && kb < M;
                     double sa[4] = {0.0, 0.0, 0.0, 0.0}, sb[4] = {0.0, 0.0, 0.0, 0.0};
-                    if (c < ncl) {
-                        const int64_t q0 = a.toff[a.cnode[c]], q1 = a.toff[a.cnode[c] + 1];
-                        int64_t q = q0;
-                        for (; q + 4 <= q1; q += 4) {
+                    int64_t q = q0;
+                    for (; q + 4 <= q1; q += 4) {
 #pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                if (va) sa[u] += a.part[(q + u) * M + ka];
-                                if (vb) sb[u] += a.part[(q + u) * M + kb];
-                            }
+                        for (int u = 0; u < 4; u++) {
+                            if (va) sa[u] += a.part[(q + u) * M + ka];
+                            if (vb) sb[u] += a.part[(q + u) * M + kb];
                         }
-                        for (int u = 0; q + u < q1; u++) {
+                    }
+#pragma unroll
+                    for (int u = 0; u < 3; u++) {
+                        if (q + u < q1) {
                             if (va) sa[u] += a.part[(q + u) * M + ka];
                             if (vb) sb[u] += a.part[(q + u) * M + kb];
                         }
@@ -243,6 +261,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(const TcArgs a)
                     if (ka < Kp) om[r * Kp + ka] = va ? ((sa[0] + sa[1]) + (sa[2] + sa[3])) * pow2d(a.tcE[ka]) : 0.0;
                     if (kb < Kp) om[r * Kp + kb] = vb ? ((sb[0] + sb[1]) + (sb[2] + sb[3])) * pow2d(a.tcE[kb]) : 0.0;
                 }
+            }
+            for (int r = 0; r < R; r++) {  // the same branch in every thread
+                const int64_t c = bt + (int64_t)r * nb;
+                if (c >= ncl) continue;
+                const int64_t q0 = a.toff[a.cnode[c]], q1 = a.toff[a.cnode[c] + 1];
+                if (q1 - q0 <= kTcHeavy) continue;
+                // warp w: partial sums q0 + w, q0 + w + 8, ... (four interleaved), then the eight
+                // warps' sums added in warp order
+                for (int k0 = 0; k0 < Kp; k0 += 64) {
+                    const int ka = k0 + lane, kb = k0 + 32 + lane;
+                    const bool va = ka < M, vb = kb < M;
+                    double sa[4] = {0.0, 0.0, 0.0, 0.0}, sb[4] = {0.0, 0.0, 0.0, 0.0};
+                    int64_t q = q0 + warp;
+                    for (; q + 3 * kTcWarps < q1; q += 4 * kTcWarps) {
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            if (va) sa[u] += a.part[(q + u * kTcWarps) * M + ka];
+                            if (vb) sb[u] += a.part[(q + u * kTcWarps) * M + kb];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 3; u++) {
+                        if (q + u * kTcWarps < q1) {
+                            if (va) sa[u] += a.part[(q + u * kTcWarps) * M + ka];
+                            if (vb) sb[u] += a.part[(q + u * kTcWarps) * M + kb];
+                        }
+                    }
+                    if (ka < Kp) part8[warp * Kp + ka] = (sa[0] + sa[1]) + (sa[2] + sa[3]);
+                    if (kb < Kp) part8[warp * Kp + kb] = (sb[0] + sb[1]) + (sb[2] + sb[3]);
+                }
+                __syncthreads();
+                for (int k = tid; k < Kp; k += kTcThreads) {
+                    double v = 0.0;
+                    for (int w8 = 0; w8 < kTcWarps; w8++) v += part8[w8 * Kp + k];
+                    om[r * Kp + k] = k < M ? v * pow2d(a.tcE[k]) : 0.0;
+                }
+                __syncthreads();
             }
         } else {
             // rho_m^d (kept by the upward pass) times the kernel sum at proxy point m, the three
@@ -379,13 +434,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_contract(const TcArgs a)
         }
         // epilogue, second half (every thread, coalesced over m): the value 2^(G + F_m) (hi + lo)
         if (MODE == 0) {
-            // W' in FP64
+            // W' in FP64, then proxy point m of the cluster: y~_m = unit(beta_m . corners),
+            // rho_m = |beta_m . corners|, W2 = 2 rho_m^d W'_m (the FP32 copy relative to the centre)
             for (int e = tid; e < R * M; e += kTcThreads) {
                 const int r = e / M, m = e - r * M;
                 const int64_t c = bt + (int64_t)r * nb;
                 if (c < ncl) {
                     const int o = m * (R + 1) + r;
-                    a.wout[c * M + m] = ((double)hs[o] + (double)ls[o]) * pow2d(gexp[r] + tcF[m]);
+                    const double wv = ((double)hs[o] + (double)ls[o]) * pow2d(gexp[r] + tcF[m]);
+                    const double* g = a.geom + 13 * (int64_t)a.cnode[c];
+                    const double b1 = a.beta[3 * m], b2 = a.beta[3 * m + 1], b3 = a.beta[3 * m + 2];
+                    const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
+                    const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
+                    const double sz = (b1 * g[2] + b2 * g[5]) + b3 * g[8];
+                    const double ss = (sx * sx + sy * sy) + sz * sz;
+                    const double ri = rsqrt(ss);
+                    const double yx = sx * ri, yy = sy * ri, yz = sz * ri, rho = ss * ri;
+                    double rd = 1.0;
+                    for (int q = 0; q < a.d; q++) rd *= rho;
+                    const double W2 = 2.0 * (rd * wv);
+                    const int64_t i = c * M + m;
+                    a.prx_rd[i] = rd;
+                    a.prx64[i] = make_double4(yx, yy, yz, W2);
+                    a.prx32[i] = make_float4((float)(yx - g[9]), (float)(yy - g[10]), (float)(yz - g[11]), (float)W2);
                 }
             }
         } else {
@@ -422,7 +493,7 @@ namespace {
 size_t tc_smem(int Kp, int R)
 {
     return (size_t)kTcASlices * kTcRows * Kp * 2 + (size_t)kTcSlices * Kp * Kp * 2 + (size_t)Kp * (R + 1) * 8 +
-           (size_t)R * 4 + 16;
+           (size_t)kTcWarps * Kp * 8 + (size_t)R * 4 + 16;
 }
 
 template <int MODE>
@@ -453,7 +524,7 @@ int launch_tc(sts_ctx* c, TcArgs a, int64_t nclu_cap, cudaStream_t s)
 
 }  // namespace
 
-int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout, cudaStream_t s)
+int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int degree, int64_t nclu, cudaStream_t s)
 {
     TcArgs a{};
     a.M = ref->M;
@@ -466,7 +537,12 @@ int proxy_weights_tc(sts_ctx* c, const RefTable* ref, int64_t nclu, double* wout
     a.cnode = c->cluster_node.p;
     a.toff = c->up_toff.p;
     a.part = c->up_part.p;
-    a.wout = wout;
+    a.geom = c->nd_geom.p;
+    a.beta = ref->d_beta.p;
+    a.d = degree;
+    a.prx64 = c->prx64.p;
+    a.prx32 = c->prx32.p;
+    a.prx_rd = c->prx_rd.p;
     return launch_tc<0>(c, a, nclu, s);
 }
 

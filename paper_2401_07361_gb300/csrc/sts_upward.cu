@@ -149,21 +149,20 @@ k_upward(const int2* __restrict__ tasks, const int32_t* __restrict__ cnode,
 // d = 8, so FP32 rounding of the products would put errors ~1e-5 into the far field.  Four
 // interleaved partial sums shorten the dependent FP64 chain.  MIXED: the proxy points are
 // normalised with a reciprocal square root (FP32 copies only need the FP64 point to an ulp or
-// so).  A fixed grid strides over the clusters (their count is on the device).
-// wtc: the contraction sum_k omega_k Vinv[k][m] already formed on the tensor cores
-// (sts_tc.cu), [cluster, M]; nullptr: formed here in FP64.
+// so).  A fixed grid strides over the clusters (their count is on the device).  Used in FP64
+// precision, and in mixed precision above the tensor-core tables' degree; otherwise the
+// tensor-core contraction (sts_tc.cu) forms the weights and places the proxy points itself.
 template <bool MIXED>
 __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __restrict__ toff,
                            const double* __restrict__ part, const double* __restrict__ geom,
                            const double* __restrict__ beta, const double* __restrict__ vinv, int d,
                            int M, double4* __restrict__ prx64, float4* __restrict__ prx32,
-                           const int64_t* __restrict__ nclu, const double* __restrict__ wtc,
-                           double* __restrict__ prx_rd)
+                           const int64_t* __restrict__ nclu, double* __restrict__ prx_rd)
 {
     __shared__ double om[kMaxM + 3];
     const int64_t ncl = *nclu;
     for (int64_t c = blockIdx.x; c < ncl; c += gridDim.x) {
-        if (!wtc) {
+        {
             const int64_t q0 = toff[cnode[c]], q1 = toff[cnode[c] + 1];
             __syncthreads();  // om of the previous cluster is no longer read
             for (int k = threadIdx.x; k < M + 3; k += blockDim.x) {
@@ -176,18 +175,13 @@ __global__ void k_contract(const int32_t* __restrict__ cnode, const int64_t* __r
         }
         const double* g = geom + 13 * (int64_t)cnode[c];
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            double acc;
-            if (wtc) {
-                acc = wtc[c * M + m];
-            } else {
-                double a4[4] = {0.0, 0.0, 0.0, 0.0};
-                for (int k = 0; k < M; k += 4) {
+            double a4[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = 0; k < M; k += 4) {
 #pragma unroll
-                    for (int u = 0; u < 4; u++)
-                        if (k + u < M) a4[u] += vinv[(k + u) * M + m] * om[k + u];
-                }
-                acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+                for (int u = 0; u < 4; u++)
+                    if (k + u < M) a4[u] += vinv[(k + u) * M + m] * om[k + u];
             }
+            const double acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
             const double b1 = beta[3 * m], b2 = beta[3 * m + 1], b3 = beta[3 * m + 2];
             const double sx = (b1 * g[0] + b2 * g[3]) + b3 * g[6];
             const double sy = (b1 * g[1] + b2 * g[4]) + b3 * g[7];
@@ -266,19 +260,18 @@ int upward_pass(sts_ctx* c, int degree, int precision, cudaStream_t s)
             c->up_tasks.p, c->cluster_node.p, c->nd_start.p, c->nd_count.p, c->nd_geom.p, c->up_frame.p,
             c->up_frame32.p, c->src64.p, c->src_hl.p, degree, M, c->up_part.p, dc + kDcUpTasks), note_launch());
     }
-    // mixed precision: the contraction on the tensor cores (exact digit products, sts_tc.cu)
-    const double* wtc = nullptr;
     if (precision == STS_MIXED && proxy_weights_tc_supported(degree)) {
-        if (!cap) STS_CUDA(c->up_wtc.reserve(nclu * M + 1));
-        int rc = proxy_weights_tc(c, ref, nclu, c->up_wtc.p, s);
+        // mixed precision: the contraction on the tensor cores (exact digit products,
+        // sts_tc.cu), which also places the proxy points
+        int rc = proxy_weights_tc(c, ref, degree, nclu, s);
         if (rc) return rc;
-        wtc = c->up_wtc.p;
+    } else {
+        (precision == STS_FP64 ? k_contract<false> : k_contract<true>)<<<
+            (unsigned)std::min<int64_t>(nclu, 16 * (int64_t)c->num_sms), 64, 0, s>>>(
+            c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M,
+            c->prx64.p, c->prx32.p, dc + kDcClusters, c->prx_rd.p);
+        note_launch();
     }
-    (precision == STS_FP64 ? k_contract<false> : k_contract<true>)<<<(unsigned)std::min<int64_t>(nclu, 16 * (int64_t)c->num_sms),
-                                                                   64, 0, s>>>(
-        c->cluster_node.p, c->up_toff.p, c->up_part.p, c->nd_geom.p, ref->d_beta.p, ref->d_vinv.p, degree, M,
-        c->prx64.p, c->prx32.p, dc + kDcClusters, wtc, c->prx_rd.p);
-    note_launch();
     STS_LAUNCH_CHECK();
     c->up_degree = degree;
     c->up_precision = precision;
