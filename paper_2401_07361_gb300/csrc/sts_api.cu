@@ -120,6 +120,7 @@ sts_ctx::~sts_ctx()
             if (ev[p][q]) cudaEventDestroy(ev[p][q]);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    if (ev_tree) cudaEventDestroy(ev_tree);
     if (side) cudaStreamDestroy(side);
     if (rk_exec) cudaGraphExecDestroy(rk_exec);
     if (ev_exec) cudaGraphExecDestroy(ev_exec);
@@ -205,9 +206,16 @@ int sources_and_lists(sts_ctx* c, const double* zeta, const double* area, const 
     const bool lists = dual ? (!c->have_dual || c->dual_theta != p->theta)
                             : (!c->have_lists || c->list_theta != p->theta);
     if (lists) {
-        STS_CUDA(cudaEventRecord(c->ev_fork, s));
-        STS_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        if (c->tree_event) {
+            // a tree built just before: the lists need only the tree, so they start when it is
+            // complete, beside the particle sort that follows it on s
+            STS_CUDA(cudaStreamWaitEvent(c->side, c->ev_tree, 0));
+        } else {
+            STS_CUDA(cudaEventRecord(c->ev_fork, s));
+            STS_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        }
     }
+    c->tree_event = false;
     int rc;
     phase_begin(c, kPhPrep, s);
     rc = prepare_sources(c, zeta, area, s);
@@ -710,6 +718,7 @@ int sts_create(sts_ctx** out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_tree, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         set_error("sts_create: %s", cudaGetErrorString(e));
         delete c;

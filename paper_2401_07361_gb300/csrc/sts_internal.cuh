@@ -335,6 +335,8 @@ struct sts_ctx {
     // stream by events (graph recordings included).
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_tree = nullptr;  // recorded when the tree (not yet the sorted order) is built
+    bool tree_event = false;        // ev_tree recorded by the last build, not yet waited on
     ~sts_ctx();
 };
 

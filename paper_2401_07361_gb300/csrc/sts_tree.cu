@@ -229,7 +229,9 @@ struct BuildArgs {
     double *geom, *norm, *mid;
     float4 *norm32, *c32;
     int64_t *over, *nnodes, *tot;  // tot: [2 CTAs] per-CTA totals
-    unsigned* bar;  // arrival counter, zeroed before the launch
+    unsigned* bar;   // arrival counter, zeroed before the launch
+    unsigned* bar2;  // the sort launch's arrival counter, zeroed by the tree launch
+    int32_t* mark;   // [n] scratch: node + 1 at each leaf's first slot, else 0
     int* status;
     // the sorted order
     int sort_passes;             // 8-bit digits of the slot keys
@@ -629,7 +631,6 @@ __device__ void cluster_table(const BuildArgs& a, int G, int32_t q0, int32_t q1,
 __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs a)
 {
     __shared__ int32_t shc[4 * kPrivNodes];
-    __shared__ int32_t hw[kBuildWarps * 256];  // per-warp digit counts, then positions
     __shared__ int64_t sh[kBuildThreads / 32];
     __shared__ int64_t s_before, s_total, s_cbefore;
     __shared__ int s_ok;
@@ -637,6 +638,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid, gs = (int64_t)gridDim.x * blockDim.x;
     const int G = (int)gridDim.x;
     unsigned bk = 0;
+    if (blockIdx.x == 0 && tid == 0) *a.bar2 = 0;
     // faces: the root key of every particle (into nodeof) and the particles per key
     const int nkeys = 20 * a.ninst;
     {
@@ -654,6 +656,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
                 for (int q = 0; q < 3; q++) a.pos[3 * i + q] = a.pos_in[3 * i + q];
                 a.nodeof[i] = rk;
                 a.digit[i] = 0;  // a particle whose root is a leaf moves to child[4 p + 0] = p
+                a.mark[i] = 0;
             }
             agg_inc(priv ? shc : a.face_count, rk, active);
         }
@@ -837,12 +840,75 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
             a.tot[2 * blockIdx.x + 1] = t2;
         }
     }
-    bool clusters_done = false;
+    // the first slot of every leaf, marked with its node (+1): the leaf list in slot order
+    // needs no particle sort
+    for (int32_t p = q0 + tid; p < q1; p += blockDim.x)
+        if (a.leaf[p]) a.mark[a.start[p]] = p + 1;
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    cluster_table(a, G, q0, q1, nn, sh, &s_before, &s_total, &s_cbefore);
+    // ---- the leaves in slot order; slot_leaf = index of the slot's leaf (a scan over the
+    // CTAs' shares of the slots)
+    const int64_t n = a.n;
+    const int64_t ich = (n + G - 1) / G;
+    const int64_t i0 = min(n, (int64_t)blockIdx.x * ich), i1 = min(n, i0 + ich);
+    {
+        int64_t mine = 0;
+        for (int64_t k = i0 + tid; k < i1; k += blockDim.x) mine += a.mark[k] != 0;
+        int64_t t;
+        build_block_scan(mine, sh, &t);
+        if (tid == 0) a.tot[2 * G + blockIdx.x] = t;
+    }
+    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+    if (tid < 32) {
+        int64_t before = 0, total = 0;
+        for (int b = lane; b < G; b += 32) {
+            const int64_t v = a.tot[2 * G + b];
+            total += v;
+            if (b < (int)blockIdx.x) before += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            before += __shfl_xor_sync(kFull, before, o);
+            total += __shfl_xor_sync(kFull, total, o);
+        }
+        if (lane == 0) {
+            s_before = before;
+            s_total = total;
+        }
+    }
+    __syncthreads();
+    int64_t carry = s_before;
+    for (int64_t r0 = i0; r0 < i1; r0 += blockDim.x) {
+        const int64_t k = r0 + tid;
+        const int32_t mk = k < i1 ? a.mark[k] : 0;
+        const int f = mk != 0;
+        int64_t rt;
+        const int64_t ex = build_block_scan(f, sh, &rt);
+        if (k < i1) {
+            const int64_t li = carry + ex + f - 1;
+            a.slot_leaf[k] = (int32_t)li;
+            if (f) a.leaves[li] = mk - 1;
+        }
+        carry += rt;
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.nleaves = s_total;
+}
 
-    // ---- the sorted order: a stable LSD radix sort (8-bit digits) of the particles by the
-    // first slot of their leaf, which keeps the particles of a leaf in their original order.
-    // CTA b owns items [i0, i1) of every pass, its warp w the w-th part of them, so the rank of
-    // an item among equal digits follows (CTA, warp, round, lane), i.e. the item order.
+// The sorted order, a second cooperative launch after the tree (the interaction lists, which
+// need only the tree, start beside it on the side stream): a stable LSD radix sort (8-bit
+// digits) of the particles by the first slot of their leaf, which keeps the particles of a
+// leaf in their original order.  CTA b owns items [i0, i1) of every pass, its warp w the w-th
+// part of them, so the rank of an item among equal digits follows (CTA, warp, round, lane),
+// i.e. the item order.  Its barrier counter (bar2) is cleared by the tree launch.
+__global__ void __launch_bounds__(kBuildThreads) k_build_sort(const BuildArgs a)
+{
+    __shared__ int32_t hw[kBuildWarps * 256];  // per-warp digit counts, then positions
+    __shared__ int64_t sh[kBuildThreads / 32];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + tid;
+    const int G = (int)gridDim.x;
+    unsigned bk = 0;
     const int64_t n = a.n;
     const int64_t ich = (n + G - 1) / G;
     const int64_t i0 = min(n, (int64_t)blockIdx.x * ich), i1 = min(n, i0 + ich);
@@ -853,9 +919,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
     const unsigned lt = (1u << lane) - 1u;
     if (P == 0) {  // a single particle
         if (gt < n) a.perm[gt] = (int32_t)gt;
-        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
-        cluster_table(a, G, q0, q1, nn, sh, &s_before, &s_total, &s_cbefore);
-        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
     }
     for (int pass = 0; pass < P; pass++) {
         const int shift = 8 * pass;
@@ -878,11 +941,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
             for (int ww = 0; ww < kBuildWarps; ww++) t += hw[ww * 256 + d];
             a.hist[d * G + blockIdx.x] = t;
         }
-        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
-        if (!clusters_done) {
-            cluster_table(a, G, q0, q1, nn, sh, &s_before, &s_total, &s_cbefore);
-            clusters_done = true;
-        }
+        if (!grid_sync(a.bar2, bk, a.status, &s_ok)) return;
         // rows d = b, b + G, ...: exclusive offsets along the row (over the CTAs), row totals
         for (int d = blockIdx.x; d < 256; d += G) {
             int64_t carry = 0;
@@ -896,7 +955,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
             }
             if (tid == 0) a.hist[256 * G + d] = (int32_t)carry;
         }
-        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        if (!grid_sync(a.bar2, bk, a.status, &s_ok)) return;
         // the first position of each (digit, warp): digit base + CTA offset + earlier warps
         for (int d0 = 0; d0 < 256; d0 += blockDim.x) {
             const int d = d0 + tid;
@@ -940,56 +999,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_levels(const BuildArgs 
                 vout[prior + rk] = val;
             }
         }
-        if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
+        if (!grid_sync(a.bar2, bk, a.status, &s_ok)) return;
     }
-    // ---- the leaves in slot order: slot k starts a leaf when it is its leaf's first slot;
-    // slot_leaf = index of the slot's leaf (a scan over the CTAs' shares of the slots)
-    {
-        int64_t mine = 0;
-        for (int64_t k = i0 + tid; k < i1; k += blockDim.x) mine += a.start[a.nodeof[a.perm[k]]] == (int32_t)k;
-        int64_t t;
-        build_block_scan(mine, sh, &t);
-        if (tid == 0) a.tot[blockIdx.x] = t;
-    }
-    if (!grid_sync(a.bar, bk, a.status, &s_ok)) return;
-    if (tid < 32) {
-        int64_t before = 0, total = 0;
-        for (int b = lane; b < G; b += 32) {
-            const int64_t v = a.tot[b];
-            total += v;
-            if (b < (int)blockIdx.x) before += v;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            before += __shfl_xor_sync(kFull, before, o);
-            total += __shfl_xor_sync(kFull, total, o);
-        }
-        if (lane == 0) {
-            s_before = before;
-            s_total = total;
-        }
-    }
-    __syncthreads();
-    int64_t carry = s_before;
-    for (int64_t r0 = i0; r0 < i1; r0 += blockDim.x) {
-        const int64_t k = r0 + tid;
-        int f = 0;
-        int32_t node = 0;
-        if (k < i1) {
-            node = a.nodeof[a.perm[k]];
-            f = a.start[node] == (int32_t)k;
-        }
-        int64_t rt;
-        const int64_t ex = build_block_scan(f, sh, &rt);
-        if (k < i1) {
-            const int64_t li = carry + ex + f - 1;
-            a.slot_leaf[k] = (int32_t)li;
-            if (f) a.leaves[li] = node;
-        }
-        carry += rt;
-    }
-    if (blockIdx.x == 0 && tid == 0) *a.nleaves = s_total;
 }
+
+
 
 // ------------------------------------------------------------------------- lists
 constexpr int kStack = 128;
@@ -1970,24 +1984,26 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     // proven bound (and the build redone) if a level runs out of it
     if (grow_nodes(c, c->capturing ? nkeys + 80 : std::max(c->node_hint, tree_node_bound(n, ninst, leaf_size, max_level, false)), 0, s))
         return STS_ERR_CUDA;
-    STS_CUDA(c->root_cnt.reserve(nkeys + 1));
+    STS_CUDA(c->root_cnt.reserve(nkeys + 2));
     STS_CUDA(c->face_node.reserve(nkeys + 1));
     c->ninst = ninst;
 
     const int T = 256;
-    // the per-key counts and, right after them, the grid barrier's arrival counter: one memset
+    // the per-key counts and, right after them, the tree launch's grid-barrier counter: one
+    // memset (the sort launch's counter, next, is cleared by the tree launch)
     STS_CUDA(cudaMemsetAsync(c->root_cnt.p, 0, (nkeys + 1) * sizeof(int32_t), s));
     int64_t* dc = c->dc.p;
     const bool cap = c->capturing;  // recording a graph: no host reads, planned capacities
     if (!cap) STS_CUDA(cudaMemsetAsync(dc + kDcOver, 0, sizeof(int64_t), s));
     // faces, roots and levels: one cooperative launch (its CTAs wait on one another at grid-wide
     // barriers)
-    if (c->build_grid == 0) {
-        int per_sm = 0;
+    if (c->build_grid == 0) {  // both launches co-resident at this grid
+        int per_sm = 0, per_sm2 = 0;
         STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_levels, kBuildThreads, 0));
-        c->build_grid = std::max(1, std::min(per_sm, 4)) * c->num_sms;
+        STS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k_build_sort, kBuildThreads, 0));
+        c->build_grid = std::max(1, std::min(std::min(per_sm, per_sm2), 4)) * c->num_sms;
     }
-    STS_CUDA(c->bld_tot.reserve(2 * (size_t)c->build_grid));
+    STS_CUDA(c->bld_tot.reserve(3 * (size_t)c->build_grid));
     if (!cap) {  // the cluster table for every node the capacity allows; the moment tasks for
                  // the largest count possible: a cluster holds more than N_T particles of one
                  // level, so there are at most (levels) n / kUpChunk + (clusters) tasks
@@ -2043,6 +2059,8 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
     a.nnodes = dc + kDcNodes;
     a.tot = c->bld_tot.p;
     a.bar = reinterpret_cast<unsigned*>(c->root_cnt.p + nkeys);
+    a.bar2 = reinterpret_cast<unsigned*>(c->root_cnt.p + nkeys + 1);
+    a.mark = reinterpret_cast<int32_t*>(c->skey_tmp.p);  // free until the sort launch
     a.status = c->d_status;
     int bits = 0;
     while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
@@ -2077,6 +2095,11 @@ int tree_build(sts_ctx* c, const double* pos, int64_t n, const int64_t* inst_off
         cfg.attrs = at;
         cfg.numAttrs = 1;
         STS_CUDA(cudaLaunchKernelEx(&cfg, k_build_levels, a));
+        note_launch();
+        // the tree is complete here: the interaction lists may start (sources_and_lists)
+        STS_CUDA(cudaEventRecord(c->ev_tree, s));
+        c->tree_event = true;
+        STS_CUDA(cudaLaunchKernelEx(&cfg, k_build_sort, a));
         note_launch();
     }
     if (!cap) {
